@@ -1,0 +1,28 @@
+"""Build the C oracle into oracle/libstokes_oracle.so (plain gcc, FP64).
+
+Test infrastructure only: the oracle is loaded by the tests, the smoke check
+and the CPU-baseline leg of the benchmark, never by the product path.
+"""
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "stokes_oracle.c")
+LIB = os.path.join(HERE, "libstokes_oracle.so")
+
+# -ffp-contract=off: every product and sum is rounded exactly where it is written.
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-Wall", "-Wextra"]
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile the oracle if the library is missing or older than its source."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        tmp = LIB + ".tmp.%d" % os.getpid()
+        subprocess.run(["gcc", *CFLAGS, "-o", tmp, SRC, "-lm"], check=True)
+        os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build_oracle(force="--force" in sys.argv))

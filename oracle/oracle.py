@@ -1,0 +1,250 @@
+"""ctypes front end of the C oracle (test infrastructure only).
+
+Every array is a float64 numpy array in the natural staggered layout
+(see stokes_oracle.c): vx, fx, bx are ny x (nx+1); vy, fy, by are
+(ny+1) x nx; p and eta_c are ny x nx; eta_n is (ny+1) x (nx+1).
+Functions return new arrays and never modify their inputs.
+"""
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from .build import build_oracle
+
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+_i, _d, _u64 = ctypes.c_int, ctypes.c_double, ctypes.c_uint64
+
+_SIGS = {
+    "ora_apply_M": (None, [_i, _i, _d, _d, _D, _D, _D, _D, _D, _D]),
+    "ora_apply_G": (None, [_i, _i, _d, _d, _D, _D, _D]),
+    "ora_apply_D": (None, [_i, _i, _d, _d, _D, _D, _D]),
+    "ora_diag_M": (None, [_i, _i, _d, _d, _D, _D, _D, _D]),
+    "ora_rhs": (None, [_i, _i, _d, _d, _D, _D, _D, _D, _D]),
+    "ora_jacobi": (None, [_i, _i, _d, _d, _D, _D, _D, _D, _d, _i, _D, _D]),
+    "ora_rbgs": (None, [_i, _i, _d, _d, _D, _D, _D, _D, _d, _i, _D, _D]),
+    "ora_splitmix64": (ctypes.c_uint64, [_u64, _u64]),
+    "ora_ras": (_i, [_i, _i, _d, _d, _D, _D, _D, _D, _d, _i, _i, _i, _i, _i, _i, _u64, _I, _u64, _D, _D, _I]),
+    "ora_ras_shift": (None, [_i, _u64, _i, _i, _i, _I]),
+    "ora_energy": (None, [_i, _i, _d, _d, _D, _D, _D, _D, _D, _D, _D, _D]),
+    "ora_mg_levels": (_i, [_i, _i, _i, _i]),
+    "ora_mg_sweeps": (_i, [_i, _d, _i]),
+    "ora_mg_prolong_add": (None, [_i, _i, _D, _D, _D, _D]),
+    "ora_mg_restrict": (None, [_i, _i, _D, _D, _D, _D]),
+    "ora_dense_solve": (_i, [_i, _i, _d, _d, _D, _D, _D, _D, _D, _D]),
+    "ora_vcycle": (_i, [_i, _i, _d, _d, _D, _D, _D, _D, _i, _i, _i, _i, _d, _i, _d, _i, _i, _i, _i, _u64, _i, _D, _D]),
+    "ora_mg_solve": (_i, [_i, _i, _d, _d, _D, _D, _D, _D, _D, _i, _i, _i, _i, _d, _i, _d, _i, _i, _i, _i, _u64,
+                          _d, _i, _D, _D, _D, _D]),
+}
+
+
+def lib():
+    """Load (building first if needed) the oracle shared library."""
+    global _lib
+    if _lib is None:
+        h = ctypes.CDLL(build_oracle())
+        for name, (res, args) in _SIGS.items():
+            f = getattr(h, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = h
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"], "oracle arrays must be C-contiguous float64"
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+@dataclass
+class Grid:
+    """A staggered grid with its viscosity fields (natural layouts)."""
+    nx: int
+    ny: int
+    hx: float
+    hy: float
+    eta_c: np.ndarray  # ny x nx
+    eta_n: np.ndarray  # (ny+1) x (nx+1)
+
+    def __post_init__(self):
+        self.eta_c = _f64(self.eta_c)
+        self.eta_n = _f64(self.eta_n)
+        assert self.eta_c.shape == (self.ny, self.nx)
+        assert self.eta_n.shape == (self.ny + 1, self.nx + 1)
+
+    @property
+    def head(self):
+        return (self.nx, self.ny, self.hx, self.hy, _p(self.eta_c), _p(self.eta_n))
+
+    def zeros_vx(self):
+        return np.zeros((self.ny, self.nx + 1))
+
+    def zeros_vy(self):
+        return np.zeros((self.ny + 1, self.nx))
+
+
+def apply_M(g: Grid, vx, vy):
+    vx, vy = _f64(vx), _f64(vy)
+    ox, oy = g.zeros_vx(), g.zeros_vy()
+    lib().ora_apply_M(*g.head, _p(vx), _p(vy), _p(ox), _p(oy))
+    return ox, oy
+
+
+def apply_G(g: Grid, p):
+    p = _f64(p)
+    ox, oy = g.zeros_vx(), g.zeros_vy()
+    lib().ora_apply_G(g.nx, g.ny, g.hx, g.hy, _p(p), _p(ox), _p(oy))
+    return ox, oy
+
+
+def apply_D(g: Grid, vx, vy):
+    vx, vy = _f64(vx), _f64(vy)
+    out = np.zeros((g.ny, g.nx))
+    lib().ora_apply_D(g.nx, g.ny, g.hx, g.hy, _p(vx), _p(vy), _p(out))
+    return out
+
+
+def diag_M(g: Grid):
+    ox, oy = g.zeros_vx(), g.zeros_vy()
+    lib().ora_diag_M(*g.head, _p(ox), _p(oy))
+    return ox, oy
+
+
+def rhs(g: Grid, fx, fy, p=None):
+    fx, fy = _f64(fx), _f64(fy)
+    p = None if p is None else _f64(p)
+    bx, by = g.zeros_vx(), g.zeros_vy()
+    lib().ora_rhs(g.nx, g.ny, g.hx, g.hy, _p(fx), _p(fy), _p(p), _p(bx), _p(by))
+    return bx, by
+
+
+def jacobi(g: Grid, bx, by, omega, sweeps, vx, vy):
+    vx, vy = _f64(vx).copy(), _f64(vy).copy()
+    lib().ora_jacobi(*g.head, _p(_f64(bx)), _p(_f64(by)), omega, sweeps, _p(vx), _p(vy))
+    return vx, vy
+
+
+def rbgs(g: Grid, bx, by, omega, sweeps, vx, vy):
+    vx, vy = _f64(vx).copy(), _f64(vy).copy()
+    lib().ora_rbgs(*g.head, _p(_f64(bx)), _p(_f64(by)), omega, sweeps, _p(vx), _p(vy))
+    return vx, vy
+
+
+def splitmix64(seed: int, c: int) -> int:
+    return int(lib().ora_splitmix64(seed & (2**64 - 1), c & (2**64 - 1)))
+
+
+def ras_shift(shift_mode, seed, t, ti, tj):
+    out = (ctypes.c_int * 2)()
+    lib().ora_ras_shift(shift_mode, seed & (2**64 - 1), t, ti, tj, out)
+    return int(out[0]), int(out[1])
+
+
+def ras(g: Grid, bx, by, omega, sweeps, ti, tj, k, overlap, shift_mode=1, seed=0, shifts=None, order_seed=0,
+        vx=None, vy=None, return_counts=False):
+    """RAS-Jacobi (Algorithm 2).  Returns (vx, vy) or (vx, vy, counts_x, counts_y)."""
+    vx = g.zeros_vx() if vx is None else _f64(vx).copy()
+    vy = g.zeros_vy() if vy is None else _f64(vy).copy()
+    sh = None
+    if shifts is not None:
+        arr = np.ascontiguousarray(np.asarray(shifts, dtype=np.int32).reshape(-1))
+        sh = arr.ctypes.data_as(_I)
+    counts = np.zeros(vx.size + vy.size, dtype=np.int32) if return_counts else None
+    st = lib().ora_ras(*g.head, _p(_f64(bx)), _p(_f64(by)), omega, sweeps, ti, tj, k, overlap, shift_mode,
+                       seed & (2**64 - 1), sh, order_seed & (2**64 - 1), _p(vx), _p(vy),
+                       None if counts is None else counts.ctypes.data_as(_I))
+    if st != 0:
+        raise ValueError("ora_ras: bad arguments")
+    if return_counts:
+        return vx, vy, counts[:vx.size].reshape(vx.shape), counts[vx.size:].reshape(vy.shape)
+    return vx, vy
+
+
+def energy(g: Grid, fx, fy, p, vx, vy):
+    """(sum r_v^2/(-diag M), sum r_p^2 eta_c/(2/hx^2+2/hy^2), sum f^2/(-diag M))."""
+    out = (ctypes.c_double * 3)()
+    p = None if p is None else _f64(p)
+    lib().ora_energy(*g.head, _p(_f64(fx)), _p(_f64(fy)), _p(p), _p(_f64(vx)), _p(_f64(vy)), out)
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def mg_levels(nx, ny, max_levels, coarsest):
+    return int(lib().ora_mg_levels(nx, ny, max_levels, coarsest))
+
+
+def mg_sweeps(nu0, growth, level):
+    return int(lib().ora_mg_sweeps(nu0, growth, level))
+
+
+def mg_prolong_add(nxf, nyf, cx, cy, fx, fy):
+    fx, fy = _f64(fx).copy(), _f64(fy).copy()
+    lib().ora_mg_prolong_add(nxf, nyf, _p(_f64(cx)), _p(_f64(cy)), _p(fx), _p(fy))
+    return fx, fy
+
+
+def mg_restrict(nxf, nyf, fx, fy):
+    cx = np.zeros((nyf // 2, nxf // 2 + 1))
+    cy = np.zeros((nyf // 2 + 1, nxf // 2))
+    lib().ora_mg_restrict(nxf, nyf, _p(_f64(fx)), _p(_f64(fy)), _p(cx), _p(cy))
+    return cx, cy
+
+
+def dense_solve(g: Grid, bx, by):
+    vx, vy = g.zeros_vx(), g.zeros_vy()
+    st = lib().ora_dense_solve(*g.head, _p(_f64(bx)), _p(_f64(by)), _p(vx), _p(vy))
+    if st != 0:
+        raise ValueError("ora_dense_solve: -M is not positive definite")
+    return vx, vy
+
+
+@dataclass
+class MG:
+    """Multigrid settings (Sec. 6.2 defaults: 5 pre / 5 post sweeps, growth 2.5)."""
+    max_levels: int = 16
+    coarsest: int = 16
+    nu_pre: int = 5
+    nu_post: int = 5
+    growth: float = 2.5
+    variant: int = 0
+    omega: float = 0.3
+    ti: int = 32
+    tj: int = 32
+    k: int = 4
+    overlap: int = 3
+    seed: int = 0
+
+    def args(self):
+        return (self.max_levels, self.coarsest, self.nu_pre, self.nu_post, self.growth, self.variant, self.omega,
+                self.ti, self.tj, self.k, self.overlap, self.seed & (2**64 - 1))
+
+
+def vcycle(g: Grid, bx, by, mg: MG, vx=None, vy=None, cycle=0):
+    vx = g.zeros_vx() if vx is None else _f64(vx).copy()
+    vy = g.zeros_vy() if vy is None else _f64(vy).copy()
+    st = lib().ora_vcycle(*g.head, _p(_f64(bx)), _p(_f64(by)), *mg.args(), cycle, _p(vx), _p(vy))
+    if st != 0:
+        raise ValueError("ora_vcycle failed")
+    return vx, vy
+
+
+def mg_solve(g: Grid, fx, fy, p, mg: MG, tol, max_cycles, vx=None, vy=None):
+    """Defect-correction multigrid solve.  Returns (vx, vy, cycles, final_E, history)."""
+    vx = g.zeros_vx() if vx is None else _f64(vx).copy()
+    vy = g.zeros_vy() if vy is None else _f64(vy).copy()
+    fe = ctypes.c_double(0.0)
+    hist = np.zeros(max_cycles + 1)
+    p = None if p is None else _f64(p)
+    c = lib().ora_mg_solve(*g.head, _p(_f64(fx)), _p(_f64(fy)), _p(p), *mg.args(), tol, max_cycles, _p(vx), _p(vy),
+                           ctypes.byref(fe), _p(hist))
+    if c < 0:
+        raise ValueError("ora_mg_solve failed")
+    return vx, vy, c, fe.value, hist[:c + 1].copy()

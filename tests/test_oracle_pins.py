@@ -1,0 +1,495 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a continuum
+identity, a symmetry, a textbook special case, a brute-force evaluation or a
+published value.  No GPU is needed.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2509_19061_gb300 import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def grid_from(ora, prob):
+    return ora.Grid(prob.nx, prob.ny, prob.hx, prob.hy, prob.eta_c, prob.eta_n)
+
+
+def rand_grid(ora, nx, ny, seed, lx=1.0, ly=1.0, rng=(-2.0, 2.0)):
+    ec, en = inputs.random_viscosity(nx, ny, seed, rng)
+    return ora.Grid(nx, ny, lx / nx, ly / ny, ec, en)
+
+
+def unknown_masks(nx, ny):
+    mx = np.zeros((ny, nx + 1), bool)
+    mx[:, 1:nx] = True
+    my = np.zeros((ny + 1, nx), bool)
+    my[1:ny, :] = True
+    return mx, my
+
+
+def coords(nx, ny, hx, hy):
+    xc = (np.arange(nx) + 0.5) * hx
+    yc = (np.arange(ny) + 0.5) * hy
+    xn = np.arange(nx + 1) * hx
+    yn = np.arange(ny + 1) * hy
+    return xc, yc, xn, yn
+
+
+# --------------------------------------------------------------------------
+# operator M of Eq. (1)-(3)
+# --------------------------------------------------------------------------
+def test_operator_manufactured_polynomial(ora):
+    """Affine viscosity, quadratic velocity: the staggered central differences
+    are exact, so M v equals div(eta (grad v + grad v^T)) at every unknown whose
+    stencil touches no boundary node (Eq. (1)-(3), hx != hy)."""
+    nx, ny, lx, ly = 13, 9, 1.3, 0.7
+    hx, hy = lx / nx, ly / ny
+    e0, ex, ey = 2.0, 0.7, -0.4
+    a = np.array([0.3, -1.1, 0.5, 0.8, -0.6, 1.7])  # vx = a . [1, x, y, x^2, xy, y^2]
+    b = np.array([-0.2, 0.9, 1.3, -0.5, 1.1, 0.4])  # vy = b . [...]
+
+    def poly(c, x, y):
+        return c[0] + c[1] * x + c[2] * y + c[3] * x * x + c[4] * x * y + c[5] * y * y
+
+    xc, yc, xn, yn = coords(nx, ny, hx, hy)
+    eta = lambda x, y: e0 + ex * x + ey * y
+    eta_c = eta(xc[None, :], yc[:, None])
+    eta_n = eta(xn[None, :], yn[:, None])
+    vx = poly(a, xn[None, :], yc[:, None])  # vx at (i hx, (j+1/2) hy), walls included
+    vy = poly(b, xc[None, :], yn[:, None])  # vy at ((i+1/2) hx, j hy)
+    g = ora.Grid(nx, ny, hx, hy, eta_c, eta_n)
+    mx, my = ora.apply_M(g, vx, vy)
+
+    def cont_M(x, y):
+        # product rule on the continuum operator
+        et = eta(x, y)
+        ux = a[1] + 2 * a[3] * x + a[4] * y
+        uy = a[2] + a[4] * x + 2 * a[5] * y
+        wx = b[1] + 2 * b[3] * x + b[4] * y
+        wy = b[2] + b[4] * x + 2 * b[5] * y
+        uxx, uxy, uyy = 2 * a[3], a[4], 2 * a[5]
+        wxx, wxy, wyy = 2 * b[3], b[4], 2 * b[5]
+        fx = 2 * ex * ux + 2 * et * uxx + ey * (uy + wx) + et * (uyy + wxy)
+        fy = ex * (uy + wx) + et * (uxy + wxx) + 2 * ey * wy + 2 * et * wyy
+        return fx, fy
+
+    X, Y = np.meshgrid(xn, yc)
+    ex_x, _ = cont_M(X, Y)
+    X, Y = np.meshgrid(xc, yn)
+    _, ex_y = cont_M(X, Y)
+    sl_x = (slice(1, ny - 1), slice(1, nx))  # vx unknowns away from boundary nodes
+    sl_y = (slice(1, ny), slice(1, nx - 1))
+    scale = np.abs(ex_x[sl_x]).max() + np.abs(ex_y[sl_y]).max()
+    np.testing.assert_allclose(mx[sl_x], ex_x[sl_x], rtol=0, atol=1e-10 * scale)
+    np.testing.assert_allclose(my[sl_y], ex_y[sl_y], rtol=0, atol=1e-10 * scale)
+
+
+@pytest.mark.parametrize("nx,ny,lx,ly", [(7, 5, 1.0, 1.0), (12, 9, 2.0, 0.5), (16, 16, 1.0, 1.0)])
+def test_operator_symmetric_negative_definite(ora, nx, ny, lx, ly):
+    """<M u, w> = <u, M w> and <M u, u> < 0 over the unknowns (Sec. 6.4: M is
+    symmetric negative definite), random viscosity, hx != hy."""
+    g = rand_grid(ora, nx, ny, 11, lx, ly)
+    ux, uy = inputs.random_velocity(nx, ny, 1)
+    wx, wy = inputs.random_velocity(nx, ny, 2)
+    mux, muy = ora.apply_M(g, ux, uy)
+    mwx, mwy = ora.apply_M(g, wx, wy)
+    lhs = np.sum(mux * wx) + np.sum(muy * wy)
+    rhs = np.sum(ux * mwx) + np.sum(uy * mwy)
+    scale = np.sqrt(np.sum(mux**2) + np.sum(muy**2)) * np.sqrt(np.sum(wx**2) + np.sum(wy**2))
+    assert abs(lhs - rhs) <= 1e-13 * scale
+    assert np.sum(mux * ux) + np.sum(muy * uy) < 0.0
+
+
+def test_operator_walls_zero_and_ignored(ora):
+    """M v is reported only at unknowns; the result is zero on wall entries."""
+    g = rand_grid(ora, 6, 5, 3)
+    vx, vy = inputs.random_velocity(6, 5, 4)
+    mx, my = ora.apply_M(g, vx, vy)
+    assert np.all(mx[:, 0] == 0) and np.all(mx[:, 6] == 0)
+    assert np.all(my[0, :] == 0) and np.all(my[5, :] == 0)
+
+
+def test_diag_is_operator_diagonal(ora):
+    """diag(M) equals the diagonal of M obtained column by column from unit vectors."""
+    nx, ny = 5, 4
+    g = rand_grid(ora, nx, ny, 5, 1.0, 0.6)
+    dx, dy = ora.diag_M(g)
+    for j in range(ny):
+        for i in range(1, nx):
+            ux, uy = g.zeros_vx(), g.zeros_vy()
+            ux[j, i] = 1.0
+            mx, _ = ora.apply_M(g, ux, uy)
+            assert dx[j, i] == pytest.approx(mx[j, i], rel=1e-14)
+    for j in range(1, ny):
+        for i in range(nx):
+            ux, uy = g.zeros_vx(), g.zeros_vy()
+            uy[j, i] = 1.0
+            _, my = ora.apply_M(g, ux, uy)
+            assert dy[j, i] == pytest.approx(my[j, i], rel=1e-14)
+
+
+def stream_velocity(nx, ny, hx, hy, seed):
+    """Discretely divergence-free velocity from a nodal stream function psi
+    vanishing on the boundary: vx = dpsi/dy, vy = -dpsi/dx."""
+    rng = np.random.default_rng(seed)
+    psi = np.zeros((ny + 1, nx + 1))
+    psi[1:ny, 1:nx] = rng.standard_normal((ny - 1, nx - 1))
+    vx = (psi[1:, :] - psi[:-1, :]) / hy  # ny x (nx+1)
+    vy = -(psi[:, 1:] - psi[:, :-1]) / hx  # (ny+1) x nx
+    return vx, vy
+
+
+def test_constant_viscosity_reduces_to_laplacian(ora):
+    """Constant eta and a discretely divergence-free v: M v = eta * (5-point
+    Laplacian of each component) at unknowns whose stencil has no boundary node."""
+    nx, ny, lx, ly = 11, 8, 1.0, 0.8
+    hx, hy = lx / nx, ly / ny
+    eta = 3.5
+    g = ora.Grid(nx, ny, hx, hy, np.full((ny, nx), eta), np.full((ny + 1, nx + 1), eta))
+    vx, vy = stream_velocity(nx, ny, hx, hy, 7)
+    assert np.abs(ora.apply_D(g, vx, vy)).max() < 1e-12 * np.abs(vx).max() / hx
+    mx, my = ora.apply_M(g, vx, vy)
+    lap_x = np.zeros_like(vx)
+    lap_x[1:-1, 1:-1] = ((vx[1:-1, 2:] - 2 * vx[1:-1, 1:-1] + vx[1:-1, :-2]) / hx**2
+                         + (vx[2:, 1:-1] - 2 * vx[1:-1, 1:-1] + vx[:-2, 1:-1]) / hy**2)
+    lap_y = np.zeros_like(vy)
+    lap_y[1:-1, 1:-1] = ((vy[1:-1, 2:] - 2 * vy[1:-1, 1:-1] + vy[1:-1, :-2]) / hx**2
+                         + (vy[2:, 1:-1] - 2 * vy[1:-1, 1:-1] + vy[:-2, 1:-1]) / hy**2)
+    sx = (slice(1, ny - 1), slice(1, nx))
+    sy = (slice(1, ny), slice(1, nx - 1))
+    scale = np.abs(mx).max()
+    np.testing.assert_allclose(mx[sx], eta * lap_x[sx], rtol=0, atol=1e-12 * scale)
+    np.testing.assert_allclose(my[sy], eta * lap_y[sy], rtol=0, atol=1e-12 * scale)
+
+
+def test_gradient_is_divergence_transpose(ora):
+    """G = D^T over the unknowns (the block system of Eq. (5) is symmetric), which
+    fixes the sign of the pressure term of Eq. (1)-(2)."""
+    nx, ny = 9, 7
+    g = rand_grid(ora, nx, ny, 8, 1.0, 1.4)
+    p = inputs.random_pressure(nx, ny, 1)
+    vx, vy = inputs.random_velocity(nx, ny, 2)
+    gx, gy = ora.apply_G(g, p)
+    dv = ora.apply_D(g, vx, vy)
+    lhs = np.sum(gx * vx) + np.sum(gy * vy)
+    rhs = np.sum(p * dv)
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+    # a pressure increasing in x gives (G p)_x = -dp/dx < 0
+    px = np.tile(np.arange(nx, dtype=float), (ny, 1))
+    gx, _ = ora.apply_G(g, px)
+    assert np.all(gx[:, 1:nx] == pytest.approx(-1.0 / g.hx))
+
+
+def test_rhs_formation(ora):
+    nx, ny = 6, 5
+    g = rand_grid(ora, nx, ny, 9)
+    prob = inputs.sinker_problem(nx, ny)
+    p = inputs.random_pressure(nx, ny, 3)
+    bx, by = ora.rhs(g, prob.fx, prob.fy, p)
+    gx, gy = ora.apply_G(g, p)
+    mx, my = unknown_masks(nx, ny)
+    np.testing.assert_array_equal(bx[mx], (prob.fx - gx)[mx])
+    np.testing.assert_array_equal(by[my], (prob.fy - gy)[my])
+    bx0, by0 = ora.rhs(g, prob.fx, prob.fy, None)
+    np.testing.assert_array_equal(bx0[mx], prob.fx[mx])
+
+
+# --------------------------------------------------------------------------
+# sign of gravity and symmetry on the sinker (Sec. 6.1)
+# --------------------------------------------------------------------------
+def test_sinker_sinks_and_is_mirror_symmetric(ora):
+    prob = inputs.sinker_problem(64, eta_in=1e3, eta_out=1.0, rho_in=2.0, rho_out=1.0, radius=0.1, g_y=-1.0)
+    g = grid_from(ora, prob)
+    bx, by = ora.rhs(g, prob.fx, prob.fy, None)
+    vx, vy = ora.jacobi(g, bx, by, 0.3, 10, g.zeros_vx(), g.zeros_vy())
+    inside = prob.rho > 1.5
+    assert vy[inside].mean() < 0.0  # same sign as g_y
+    # mirror x -> 1 - x: vx is odd, vy is even
+    np.testing.assert_allclose(vx, -vx[:, ::-1], atol=1e-12 * np.abs(vx).max())
+    np.testing.assert_allclose(vy, vy[:, ::-1], atol=1e-12 * np.abs(vy).max())
+    # flipping gravity flips the flow
+    prob2 = inputs.sinker_problem(64, g_y=+1.0)
+    bx2, by2 = ora.rhs(g, prob2.fx, prob2.fy, None)
+    vx2, vy2 = ora.jacobi(g, bx2, by2, 0.3, 10, g.zeros_vx(), g.zeros_vy())
+    np.testing.assert_allclose(vy2, -vy, atol=1e-12 * np.abs(vy).max())
+
+
+# --------------------------------------------------------------------------
+# Jacobi (Sec. 5 (ii)-(iv)) and RBGS (Sec. 5 (i))
+# --------------------------------------------------------------------------
+def test_jacobi_single_point_closed_form(ora):
+    """From v = 0 with b = unit vector at one unknown, one damped Jacobi sweep
+    gives omega / diag(M) there and zero elsewhere; from v = unit vector and
+    b = 0 it gives 1 - omega there and -omega M_ik / M_ii at the neighbours."""
+    nx, ny, omega = 6, 5, 0.37
+    g = rand_grid(ora, nx, ny, 12)
+    dx, dy = ora.diag_M(g)
+    bx, by = g.zeros_vx(), g.zeros_vy()
+    bx[2, 3] = 1.0
+    vx, vy = ora.jacobi(g, bx, by, omega, 1, g.zeros_vx(), g.zeros_vy())
+    assert vx[2, 3] == pytest.approx(omega / dx[2, 3], rel=1e-15)
+    vx[2, 3] = 0.0
+    assert np.all(vx == 0) and np.all(vy == 0)
+    ux, uy = g.zeros_vx(), g.zeros_vy()
+    uy[2, 4] = 1.0
+    mx, my = ora.apply_M(g, ux, uy)
+    vx, vy = ora.jacobi(g, g.zeros_vx(), g.zeros_vy(), omega, 1, ux, uy)
+    mxm, mym = unknown_masks(nx, ny)
+    np.testing.assert_allclose(vx[mxm], (-omega * mx / np.where(mxm, dx, 1.0))[mxm], rtol=1e-14, atol=1e-300)
+    exp_y = uy - omega * my / np.where(mym, dy, 1.0)
+    np.testing.assert_allclose(vy[mym], exp_y[mym], rtol=1e-14, atol=1e-300)
+    assert vy[2, 4] == pytest.approx(1.0 - omega, rel=1e-14)
+
+
+def test_jacobi_contracts_at_0p3_and_diverges_at_0p9(ora):
+    """Constant viscosity, square cells: lambda_max(diag(M)^-1 M) = 16/6, so
+    damped Jacobi is stable for omega < 0.75 (omega_u = 0.3 of Sec. 6.3) and
+    unstable for omega = 0.9."""
+    n = 16
+    g = ora.Grid(n, n, 1.0 / n, 1.0 / n, np.ones((n, n)), np.ones((n + 1, n + 1)))
+    vx, vy = inputs.random_velocity(n, n, 5)
+    z = (g.zeros_vx(), g.zeros_vy())
+    nrm = lambda a, b: np.sqrt(np.sum(a * a) + np.sum(b * b))
+    n0 = nrm(vx, vy)
+    ax, ay = ora.jacobi(g, *z, 0.3, 200, vx, vy)
+    bx_, by_ = ora.jacobi(g, *z, 0.9, 200, vx, vy)
+    assert nrm(ax, ay) < 0.5 * n0
+    assert nrm(bx_, by_) > 100.0 * n0
+
+
+def brute_force_rbgs(ora, g, bx, by, omega, sweeps, vx, vy):
+    """Sequential point-by-point Gauss-Seidel over one colour at a time, each
+    update using the freshest values, M re-applied from scratch every time."""
+    vx, vy = vx.copy(), vy.copy()
+    dx, dy = ora.diag_M(g)
+    for _ in range(sweeps):
+        for colour in (0, 1):
+            for j in range(g.ny):
+                for i in range(1, g.nx):
+                    if (i + j) % 2 == colour:
+                        mx, _ = ora.apply_M(g, vx, vy)
+                        vx[j, i] += omega * (bx[j, i] - mx[j, i]) / dx[j, i]
+        for colour in (0, 1):
+            for j in range(1, g.ny):
+                for i in range(g.nx):
+                    if (i + j) % 2 == colour:
+                        _, my = ora.apply_M(g, vx, vy)
+                        vy[j, i] += omega * (by[j, i] - my[j, i]) / dy[j, i]
+    return vx, vy
+
+
+@pytest.mark.parametrize("nx,ny", [(5, 7), (6, 6), (13, 9)])
+def test_rbgs_matches_sequential_brute_force(ora, nx, ny):
+    g = rand_grid(ora, nx, ny, 20 + nx, 1.0, 1.0 * ny / nx)
+    bx, by = inputs.random_velocity(nx, ny, 21)
+    vx, vy = inputs.random_velocity(nx, ny, 22)
+    ox, oy = ora.rbgs(g, bx, by, 0.8, 2, vx, vy)
+    rx, ry = brute_force_rbgs(ora, g, bx, by, 0.8, 2, vx, vy)
+    scale = np.abs(rx).max() + np.abs(ry).max()
+    np.testing.assert_allclose(ox, rx, rtol=0, atol=1e-13 * scale)
+    np.testing.assert_allclose(oy, ry, rtol=0, atol=1e-13 * scale)
+
+
+# --------------------------------------------------------------------------
+# RAS-type temporal blocking (Sec. 4.3, Algorithm 2)
+# --------------------------------------------------------------------------
+def ras_case(ora, nx=23, ny=17, seed=30):
+    prob = inputs.sinker_problem(nx, ny, eta_in=1e2, radius=0.2)
+    g = grid_from(ora, prob)
+    bx, by = ora.rhs(g, prob.fx, prob.fy, None)
+    vx, vy = inputs.random_velocity(nx, ny, seed, 0.01)
+    return g, bx, by, vx, vy
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_ras_whole_domain_tile_equals_k_jacobi_sweeps(ora, k):
+    g, bx, by, vx, vy = ras_case(ora)
+    rx, ry = ora.ras(g, bx, by, 0.3, k, 64, 64, k, 0, shift_mode=0, vx=vx, vy=vy)
+    jx, jy = ora.jacobi(g, bx, by, 0.3, k, vx, vy)
+    np.testing.assert_array_equal(rx, jx)
+    np.testing.assert_array_equal(ry, jy)
+
+
+@pytest.mark.parametrize("k,sweeps", [(2, 7), (3, 9), (4, 10)])
+def test_ras_overlap_threshold_is_k_minus_1(ora, k, sweeps):
+    """The Jacobi stencil couples unknowns of cells at Chebyshev distance one,
+    so with overlap o >= k-1 the owned unknowns see no frozen value during the
+    k local sweeps and RAS reproduces global Jacobi exactly; o = k-2 does not."""
+    g, bx, by, vx, vy = ras_case(ora)
+    jx, jy = ora.jacobi(g, bx, by, 0.3, sweeps, vx, vy)
+    for o in (k - 1, k + 1):
+        rx, ry = ora.ras(g, bx, by, 0.3, sweeps, 6, 5, k, o, shift_mode=1, seed=9, vx=vx, vy=vy)
+        np.testing.assert_array_equal(rx, jx)
+        np.testing.assert_array_equal(ry, jy)
+    rx, ry = ora.ras(g, bx, by, 0.3, sweeps, 6, 5, k, k - 2, shift_mode=1, seed=9, vx=vx, vy=vy)
+    assert np.abs(rx - jx).max() + np.abs(ry - jy).max() > 1e-6 * (np.abs(jx).max() + np.abs(jy).max())
+
+
+def test_ras_tile_order_invariant_and_single_writer(ora):
+    """All tiles read the same snapshot and each unknown has exactly one owner
+    (Sec. 4.3's boundary-ownership convention), so the tile order is irrelevant."""
+    g, bx, by, vx, vy = ras_case(ora)
+    a = ora.ras(g, bx, by, 0.3, 8, 5, 4, 3, 1, shift_mode=1, seed=4, vx=vx, vy=vy, return_counts=True)
+    b = ora.ras(g, bx, by, 0.3, 8, 5, 4, 3, 1, shift_mode=1, seed=4, order_seed=77, vx=vx, vy=vy)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    mx, my = unknown_masks(g.nx, g.ny)
+    assert np.all(a[2][mx] == 1) and np.all(a[2][~mx] == 0)
+    assert np.all(a[3][my] == 1) and np.all(a[3][~my] == 0)
+
+
+def test_ras_explicit_shifts_match_drawn_shifts(ora):
+    g, bx, by, vx, vy = ras_case(ora)
+    sweeps, k, ti, tj, seed = 10, 3, 7, 6, 12345
+    n_outer = -(-sweeps // k)
+    drawn = [ora.ras_shift(1, seed, t, ti, tj) for t in range(n_outer)]
+    assert all(0 <= s < ti and 0 <= r < tj for s, r in drawn)
+    a = ora.ras(g, bx, by, 0.3, sweeps, ti, tj, k, 0, shift_mode=1, seed=seed, vx=vx, vy=vy)
+    b = ora.ras(g, bx, by, 0.3, sweeps, ti, tj, k, 0, shift_mode=2, shifts=np.array(drawn), vx=vx, vy=vy)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_ras_is_a_convergent_smoother(ora):
+    """With o = 0 (the paper's ring-only tiles) RAS differs from Jacobi but
+    reduces the energy residual about as much as the same number of Jacobi
+    sweeps on the sinker."""
+    prob = inputs.sinker_problem(48, eta_in=1e3)
+    g = grid_from(ora, prob)
+    bx, by = ora.rhs(g, prob.fx, prob.fy, None)
+    rx, ry = ora.ras(g, bx, by, 0.3, 40, 8, 8, 4, 0, shift_mode=1, seed=1)
+    jx, jy = ora.jacobi(g, bx, by, 0.3, 40, g.zeros_vx(), g.zeros_vy())
+    er = ora.energy(g, prob.fx, prob.fy, None, rx, ry)
+    ej = ora.energy(g, prob.fx, prob.fy, None, jx, jy)
+    e_ras, e_jac = np.sqrt(er[0] / er[2]), np.sqrt(ej[0] / ej[2])
+    assert np.abs(rx - jx).max() > 1e-3 * np.abs(jx).max()
+    assert e_ras < 1.0 and e_ras < 1.02 * e_jac
+
+
+def test_splitmix64_published_vector(ora):
+    with open(os.path.join(HERE, "golden", "splitmix64_seed1234567.txt")) as f:
+        want = [int(t) for t in f.read().split("\n") if t.strip() and not t.startswith("#")]
+    assert [ora.splitmix64(1234567, c) for c in range(5)] == want
+
+
+# --------------------------------------------------------------------------
+# energy norm (Sec. 6.4)
+# --------------------------------------------------------------------------
+def test_energy_norm_is_one_at_zero_state(ora):
+    prob = inputs.sinker_problem(20)
+    g = grid_from(ora, prob)
+    rv, rp, ff = ora.energy(g, prob.fx, prob.fy, None, g.zeros_vx(), g.zeros_vy())
+    assert rp == 0.0 and rv == pytest.approx(ff, rel=1e-15) and ff > 0
+
+
+def test_energy_norm_vanishes_at_exact_solution(ora):
+    """The dense solve of M v = f gives r_v = 0 to round-off, and a
+    divergence-free v has r_p = 0."""
+    prob = inputs.sinker_problem(14, 10, eta_in=1e3)
+    g = grid_from(ora, prob)
+    vx, vy = ora.dense_solve(g, prob.fx, prob.fy)
+    mx, my = ora.apply_M(g, vx, vy)
+    mxm, mym = unknown_masks(14, 10)
+    scale = np.abs(prob.fy).max()
+    np.testing.assert_allclose(mx[mxm], prob.fx[mxm], atol=1e-10 * scale)
+    np.testing.assert_allclose(my[mym], prob.fy[mym], atol=1e-10 * scale)
+    rv, rp, ff = ora.energy(g, prob.fx, prob.fy, None, vx, vy)
+    assert rv / ff < 1e-20
+    sx, sy = stream_velocity(14, 10, g.hx, g.hy, 3)
+    _, rp2, _ = ora.energy(g, prob.fx, prob.fy, None, sx, sy)
+    assert rp2 < 1e-20 * np.sum(sx * sx)
+
+
+def test_energy_norm_pressure_weight(ora):
+    """A uniform expansion vx = c x gives D v = c in every cell, so the pressure
+    part is c^2 sum(eta_c) / (2/hx^2 + 2/hy^2)."""
+    nx, ny, lx, ly = 8, 6, 1.0, 0.75
+    g = rand_grid(ora, nx, ny, 40, lx, ly)
+    c = 0.3
+    vx = np.tile(c * np.arange(nx + 1) * g.hx, (ny, 1))
+    vy = g.zeros_vy()
+    _, rp, _ = ora.energy(g, g.zeros_vx(), g.zeros_vy(), None, vx, vy)
+    want = c * c * g.eta_c.sum() / (2 / g.hx**2 + 2 / g.hy**2)
+    assert rp == pytest.approx(want, rel=1e-13)
+
+
+# --------------------------------------------------------------------------
+# multigrid (Sec. 3.2, Sec. 6.2)
+# --------------------------------------------------------------------------
+def test_mg_level_count_and_sweeps(ora):
+    assert ora.mg_levels(64, 64, 16, 16) == 3
+    assert ora.mg_levels(4096, 4096, 16, 16) == 9
+    assert ora.mg_levels(80, 80, 16, 16) == 4  # 80, 40, 20, 10
+    assert ora.mg_levels(64, 48, 2, 16) == 2
+    # Sec. 6.2: five sweeps on the finest level, times 2.5 per coarser level
+    assert [ora.mg_sweeps(5, 2.5, l) for l in range(4)] == [5, 13, 32, 79]
+
+
+def test_restriction_is_scaled_adjoint_of_prolongation(ora):
+    nxf, nyf = 12, 10
+    rng = np.random.default_rng(3)
+    fx, fy = rng.standard_normal((nyf, nxf + 1)), rng.standard_normal((nyf + 1, nxf))
+    fx[:, 0] = fx[:, nxf] = 0
+    fy[0, :] = fy[nyf, :] = 0
+    cx, cy = inputs.random_velocity(nxf // 2, nyf // 2, 4)
+    rcx, rcy = ora.mg_restrict(nxf, nyf, fx, fy)
+    pfx, pfy = ora.mg_prolong_add(nxf, nyf, cx, cy, np.zeros_like(fx), np.zeros_like(fy))
+    lhs = np.sum(rcx * cx) + np.sum(rcy * cy)
+    rhs = (np.sum(fx * pfx) + np.sum(fy * pfy)) / 4.0
+    assert lhs == pytest.approx(rhs, rel=1e-13)
+
+
+def test_prolongation_reproduces_linear_fields(ora):
+    """Bilinear interpolation is exact for fields linear in the staggered
+    coordinates (checked away from the walls, where mirror ghosts apply)."""
+    nxf, nyf = 16, 12
+    nxc, nyc = nxf // 2, nyf // 2
+    f = lambda x, y: 0.3 + 1.7 * x - 0.9 * y
+    H = 2.0
+    # coarse vx at (I H, (J+1/2) H), fine at (i h, (j+1/2) h), h = 1
+    Xc, Yc = np.meshgrid(np.arange(nxc + 1) * H, (np.arange(nyc) + 0.5) * H)
+    cx = f(Xc, Yc)
+    cx[:, 0] = cx[:, nxc] = 0.0
+    Xf, Yf = np.meshgrid(np.arange(nxf + 1) * 1.0, np.arange(nyf) + 0.5)
+    pfx, _ = ora.mg_prolong_add(nxf, nyf, cx, np.zeros((nyc + 1, nxc)), np.zeros((nyf, nxf + 1)),
+                                np.zeros((nyf + 1, nxf)))
+    sl = (slice(1, nyf - 1), slice(2, nxf - 1))
+    np.testing.assert_allclose(pfx[sl], f(Xf, Yf)[sl], rtol=1e-13)
+    # coarse vy at ((I+1/2) H, J H)
+    Xc, Yc = np.meshgrid((np.arange(nxc) + 0.5) * H, np.arange(nyc + 1) * H)
+    cy = f(Xc, Yc)
+    cy[0, :] = cy[nyc, :] = 0.0
+    Xf, Yf = np.meshgrid(np.arange(nxf) + 0.5, np.arange(nyf + 1) * 1.0)
+    _, pfy = ora.mg_prolong_add(nxf, nyf, np.zeros((nyc, nxc + 1)), cy, np.zeros((nyf, nxf + 1)),
+                                np.zeros((nyf + 1, nxf)))
+    sl = (slice(2, nyf - 1), slice(1, nxf - 1))
+    np.testing.assert_allclose(pfy[sl], f(Xf, Yf)[sl], rtol=1e-13)
+
+
+def test_vcycle_single_level_is_exact_solve(ora):
+    prob = inputs.sinker_problem(12, 10, eta_in=1e2)
+    g = grid_from(ora, prob)
+    mg = ora.MG(max_levels=1)
+    vx, vy = ora.vcycle(g, prob.fx, prob.fy, mg)
+    dx, dy = ora.dense_solve(g, prob.fx, prob.fy)
+    np.testing.assert_allclose(vx, dx, atol=1e-12 * np.abs(dx).max())
+    np.testing.assert_allclose(vy, dy, atol=1e-12 * np.abs(dy).max())
+
+
+@pytest.mark.parametrize("variant", [0, 3, 4])
+def test_vcycle_converges_to_dense_solution(ora, variant):
+    """Constant-contrast-free case first: every cycle reduces the residual and
+    the iteration reaches the dense direct solution (32^2, three levels)."""
+    prob = inputs.sinker_problem(32, eta_in=10.0)
+    g = grid_from(ora, prob)
+    mg = ora.MG(variant=variant, ti=8, tj=8, k=2, overlap=0, seed=3)
+    vx, vy, c, fe, hist = ora.mg_solve(g, prob.fx, prob.fy, None, mg, 1e-10, 60)
+    assert fe <= 1e-10
+    assert np.all(np.diff(hist) < 0)
+    dx, dy = ora.dense_solve(g, prob.fx, prob.fy)
+    np.testing.assert_allclose(vx, dx, atol=1e-8 * np.abs(dx).max())
+    np.testing.assert_allclose(vy, dy, atol=1e-8 * np.abs(dy).max())
