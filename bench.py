@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark: RAS-Jacobi smoothing throughput on one GB300 (or N replicas).
+
+Workload (one "step"): the 8192 x 8192 layered sinker (10 seeded horizontal
+layers with log10 eta ~ U[-3, 3] plus a centred sinker, viscosity contrast up
+to 1e6, unit square, free-slip walls), FP32: form b = f - G p, run 100
+RAS-Jacobi sweeps (32 x 32 tiles, k = 4 local sweeps, overlap k-1, SplitMix64
+tile shifts), then evaluate the energy residual norm (FP64 accumulation, three
+scalars back to the host).  One cell-update = vx and vy of one cell updated
+once; value = nx * ny * sweeps * steps / time.
+
+Every field is 268 MB (FP32), so the 8 fields of a sweep (2.1 GB) are far
+larger than the 129 MB L2: inputs larger than L2, no flush needed.
+
+--impl reference times the FP64 CPU oracle on this host's cores on a bounded
+sample of the same workload (see cpu_sample below).
+"""
+import argparse
+import hashlib
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RAS-Jacobi Gcell-updates/s + % HBM peak; time to 1e-8 residual FP32 vs FP64"
+UNIT = "Gcell-updates/s"
+WORDS_PER_CELL_SWEEP = 8  # read vx, vy, eta_c, eta_n, bx, by; write vx, vy
+FALLBACK_HBM_GBS = 6800.0
+RAS_SOURCES = ["paper_2509_19061_gb300/csrc/ras_kernels.cu", "paper_2509_19061_gb300/csrc/stencil.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--sweeps", type=int, default=100)
+    ap.add_argument("--tile", type=int, nargs=2, default=[32, 32])
+    ap.add_argument("--k", type=int, default=4)
+    ap.add_argument("--overlap", type=int, default=None)
+    ap.add_argument("--no-extras", action="store_true", help="skip the variant table, e2e and CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(key, src_hash):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; None otherwise."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[key]
+        return float(e["dram_bytes_per_launch"]) if e.get("source_hash") == src_hash else None
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        exe = shutil.which("nvidia-smi")
+        if exe:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen([exe, "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def cpu_sample(args, target_s):
+    """Time the FP64 oracle's RAS-Jacobi on the same workload generator at
+    1024^2 (same tiles, k, overlap, shifts) for about target_s seconds."""
+    import oracle as ora
+    from paper_2509_19061_gb300 import inputs
+    n = 1024
+    prob = inputs.layered_sinker(n, seed=4)
+    g = ora.Grid(n, n, prob.hx, prob.hy, prob.eta_c, prob.eta_n)
+    bx, by = ora.rhs(g, prob.fx, prob.fy, None)
+    k = args.k
+    o = args.overlap if args.overlap is not None else k - 1
+    t0 = time.perf_counter()
+    ora.ras(g, bx, by, 0.3, k, args.tile[0], args.tile[1], k, o, shift_mode=1, seed=1)
+    t_one = max(time.perf_counter() - t0, 1e-3)
+    outer = max(1, int(target_s / t_one))
+    sweeps = outer * k
+    t0 = time.perf_counter()
+    ora.ras(g, bx, by, 0.3, sweeps, args.tile[0], args.tile[1], k, o, shift_mode=1, seed=1)
+    dt = time.perf_counter() - t0
+    return {"value": n * n * sweeps / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "FP64 C oracle, single thread, layered sinker %dx%d (same generator, seed 4), RAS %dx%d "
+                      "tiles k=%d overlap=%d, %d sweeps in %.1f s" % (n, n, args.tile[0], args.tile[1], k, o,
+                                                                      sweeps, dt),
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_sample(args, per_step / 4)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        r = cpu_sample(args, per_step)
+        vals.append(r["value"])
+        secs.append(r["seconds"])
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.median(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": r["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(args):
+    o = args.overlap if args.overlap is not None else args.k - 1
+    return {"workload": "layered_sinker_%dx%d_contrast1e6_ras_%s" % (args.n, args.n, args.dtype),
+            "nx": args.n, "ny": args.n, "tile": list(args.tile), "k": args.k, "overlap": o,
+            "sweeps_per_step": args.sweeps, "shifts": "splitmix64", "omega": 0.3,
+            "l2": "inputs larger than L2 (8 fields x %.0f MB per sweep), no flush" % (
+                (args.n + 1) * (args.n + 1) * (4 if args.dtype == "f32" else 8) / 1e6),
+            "step": "b = f - G p, %d RAS sweeps, energy norm" % args.sweeps}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2509_19061_gb300 import api, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    n, dt_name = args.n, args.dtype
+    k = args.k
+    o = args.overlap if args.overlap is not None else k - 1
+    prob = inputs.layered_sinker(n, seed=4)
+    stream = torch.cuda.current_stream()
+    ctx = api.StokesContext(n, n, 1.0, 1.0, dt_name, stream=stream)
+    ctx.set_problem(prob)
+    vx, vy = ctx.field(), ctx.field()
+    cells = n * n
+    esize = 4 if dt_name == "f32" else 8
+
+    def step(s, seed):
+        ctx.smooth(vx, vy, None, variant="ras", sweeps=s, tile=tuple(args.tile), k=k, overlap=o, seed=seed)
+        return ctx.energy(vx, vy)
+
+    for w in range(args.warmup):
+        step(args.sweeps, 1000 + w)
+    torch.cuda.synchronize()
+    ctx.profile_reset(timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for it in range(args.steps):
+            energy = step(args.sweeps, it)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms_total = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    prof = ctx.profile()
+    launches = sum(v[0] for v in prof.values())
+    ras_launches, ras_groups, ras_ms = prof["ras"]
+    ms_step = ms_total / args.steps
+    value = world * cells * args.sweeps * args.steps / (ms_total / 1e3) / 1e9
+
+    # roofline of the dominant kernel (the RAS tile kernel): algorithmic bytes
+    # = 8 words per cell per sweep, k sweeps per launch
+    per_launch_bytes = WORDS_PER_CELL_SWEEP * esize * cells * k
+    avg_ms = ras_ms / max(ras_groups, 1)
+    achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    key = "ras_%s_%d_t%dx%d_k%d_o%d" % (dt_name, n, args.tile[0], args.tile[1], k, o)
+    traffic = ncu_traffic(key, source_hash(RAS_SOURCES))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if
+                peak_kind == "measured" else "fallback 6800 GB/s",
+                "kernel": "k_ras", "kernel_avg_ms": avg_ms, "kernel_share": ras_ms / ms_total,
+                "algorithmic_bytes_per_launch": per_launch_bytes,
+                "note": "effective bytes: 8 words/cell/sweep x k sweeps per launch; with k > 1 the tile is "
+                        "read from HBM once per k sweeps, so frac may exceed 1 (temporal blocking)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dt_name, "data": "synthetic (seeded layered sinker, no dataset)",
+            "config": dict(workload_config(args), parallelism="replicas%d" % world if world > 1 else "single"),
+            "gpu_launches": launches, "roofline": roofline, "clocks": clk.summary(),
+            "energy_residual_after_step": (energy[0] / energy[2]) ** 0.5}
+
+    if not args.no_extras and rank == 0:
+        line["e2e"] = e2e_measure(args, ctx, prob, stream, world)
+        line["variants"] = variant_table(args, api, prob)
+        if world == 1:
+            line["cpu_baseline"] = {kk: vv for kk, vv in cpu_sample(args, args.cpu_seconds).items()
+                                    if kk != "seconds"}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def e2e_measure(args, ctx, prob, stream, world):
+    """Same step through the public API with host buffers: pinned host ->
+    device copies of every input, set_viscosity, set_rhs, smooth, energy norm,
+    device -> host copy of the smoothed velocity, all inside the timed region."""
+    import torch
+    host = {}
+    for name, arr in (("eta_c", prob.eta_c), ("eta_n", prob.eta_n), ("fx", prob.fx), ("fy", prob.fy)):
+        host[name] = ctx.pack(arr, name).cpu().pin_memory()
+    host["vx"] = torch.zeros((ctx.ny + 1, ctx.pitch), dtype=ctx.tdtype).pin_memory()
+    host["vy"] = torch.zeros_like(host["vx"]).pin_memory()
+    out_x = torch.empty_like(host["vx"]).pin_memory()
+    out_y = torch.empty_like(host["vx"]).pin_memory()
+    dev = {name: ctx.field() for name in host}
+    k = args.k
+    o = args.overlap if args.overlap is not None else k - 1
+    steps = max(2, args.steps // 2)
+
+    def one(seed):
+        for name, t in host.items():
+            dev[name].copy_(t, non_blocking=True)
+        ctx.set_viscosity_dev(dev["eta_c"], dev["eta_n"])
+        ctx.set_rhs_dev(dev["fx"], dev["fy"])
+        ctx.smooth(dev["vx"], dev["vy"], None, variant="ras", sweeps=args.sweeps, tile=tuple(args.tile), k=k,
+                   overlap=o, seed=seed)
+        e = ctx.energy(dev["vx"], dev["vy"])
+        out_x.copy_(dev["vx"], non_blocking=True)
+        out_y.copy_(dev["vy"], non_blocking=True)
+        torch.cuda.synchronize()
+        return e
+
+    one(7)
+    t0 = time.perf_counter()
+    for it in range(steps):
+        one(it)
+    dt = time.perf_counter() - t0
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = out_x.numel() * out_x.element_size() * 2 + 24
+    return {"value": world * args.n * args.n * args.sweeps * steps / dt / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
+            "ms_per_step": 1000.0 * dt / steps}
+
+
+def variant_table(args, api, prob):
+    """Throughput of the other smoothers and RAS settings on the same grid
+    (Gcell-updates/s, device time of the smoothing call only)."""
+    import torch
+    out = {}
+    n = args.n
+    cases = [("f32", "jacobi", dict(sweeps=20)), ("f32", "fused", dict(sweeps=20)),
+             ("f32", "blocked", dict(sweeps=20, tile=(32, 32))), ("f32", "rbgs", dict(sweeps=20)),
+             ("f32", "ras", dict(sweeps=40, tile=(32, 32), k=1, overlap=0)),
+             ("f32", "ras", dict(sweeps=40, tile=(32, 32), k=2, overlap=1)),
+             ("f32", "ras", dict(sweeps=40, tile=(32, 32), k=8, overlap=7)),
+             ("f32", "ras", dict(sweeps=40, tile=(32, 32), k=4, overlap=0)),
+             ("f64", "ras", dict(sweeps=8, tile=(32, 32), k=4, overlap=3)),
+             ("f64", "fused", dict(sweeps=4))]
+    ctxs = {}
+    for dt_name, variant, kw in cases:
+        if dt_name not in ctxs:
+            c = api.StokesContext(n, n, 1.0, 1.0, dt_name)
+            c.set_problem(prob)
+            ctxs[dt_name] = (c, c.field(), c.field())
+        c, vx, vy = ctxs[dt_name]
+        stream = torch.cuda.current_stream()
+        c.smooth(vx, vy, None, variant=variant, **kw)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        e0.record(stream)
+        for _ in range(reps):
+            c.smooth(vx, vy, None, variant=variant, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        label = "%s_%s" % (dt_name, variant)
+        if variant == "ras":
+            label += "_k%d_o%d" % (kw["k"], kw["overlap"])
+        out[label] = {"gcell_updates_per_s": n * n * kw["sweeps"] / (ms / 1e3) / 1e9, "sweeps": kw["sweeps"],
+                      "ms_per_call": ms}
+    for c, _, _ in ctxs.values():
+        c.close()
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,234 @@
+/*
+ * stokes.h -- C ABI of libstokes, GB300 (sm_103a) smoothers for the 2D
+ * variable-viscosity incompressible Stokes velocity operator on a fully
+ * staggered finite-difference grid (arXiv 2509.19061).
+ *
+ * Grid and layout (Sec. 2.1 and Fig. 1 of the paper).  The domain
+ * [0, lx] x [0, ly] has nx x ny cells, hx = lx/nx, hy = ly/ny:
+ *   vx[j][i] at (i hx, (j+1/2) hy),       0 <= j < ny,  0 <= i <= nx
+ *   vy[j][i] at ((i+1/2) hx, j hy),       0 <= j <= ny, 0 <= i < nx
+ *   p[j][i], eta_c[j][i] at cell centres, 0 <= j < ny,  0 <= i < nx
+ *   eta_n[j][i] at nodes (i hx, j hy),    0 <= j <= ny, 0 <= i <= nx
+ *   fx like vx, fy like vy (density, and so the body force, sits with vy).
+ * Every field buffer the caller passes is one pitched 2D array of
+ * (ny+1) rows x `pitch` elements of the context's dtype (row j starts at
+ * element j*pitch), whatever the field; stokes_get_layout returns the pitch
+ * and each field's own extent.  Entries outside a field's extent are padding:
+ * they are never read, and output buffers get zeros there.  The unknowns are
+ * vx with 1 <= i <= nx-1 and vy with 1 <= j <= ny-1; the wall entries
+ * vx[.][0], vx[.][nx], vy[0][.], vy[ny][.] are Dirichlet data (zero for the
+ * impermeable walls of Sec. 6.1), read but never written.  The shear stress is
+ * zero on boundary nodes (free slip).
+ *
+ * Operator (Eq. (1)-(3), Eq. (6)): M v + G p = f, with
+ *   sigma'_xx = 2 eta_c dvx/dx, sigma'_yy = 2 eta_c dvy/dy at centres,
+ *   sigma'_xy = eta_n (dvx/dy + dvy/dx) at interior nodes, 0 on boundary nodes,
+ *   (M v)_x = d sigma'_xx/dx + d sigma'_xy/dy, (M v)_y = d sigma'_xy/dx + d sigma'_yy/dy,
+ *   (G p)_x = -dp/dx, (G p)_y = -dp/dy (the -grad p of Eq. (1)-(2)).
+ *
+ * Ownership.  The caller owns every field buffer (device memory from any
+ * allocator, dtype of the context, the pitched layout above).  The library
+ * owns its copies of eta and f, the right-hand side b = f - G p, the
+ * ping-pong snapshot of the smoothers, the multigrid hierarchy and the
+ * reduction buffers; it allocates them in stokes_create / stokes_set_viscosity
+ * and frees them in stokes_destroy.
+ *
+ * Streams.  Every call enqueues its kernels on the stream given to
+ * stokes_create (NULL = the legacy default stream) and returns without waiting,
+ * except the calls that return host scalars (stokes_residual_energy_norm,
+ * stokes_vcycle, stokes_batch_solve), which synchronise that stream.
+ *
+ * Errors.  Every call returns STOKES_OK (0) or a negative stokes_status;
+ * nothing aborts.  A context is not thread-safe: use one per host thread.
+ */
+#ifndef STOKES_H
+#define STOKES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    STOKES_OK = 0,
+    STOKES_ERR_ARG = -1,           /* invalid argument (sizes, tiles, k, NULL pointer, ...) */
+    STOKES_ERR_CUDA = -2,          /* a CUDA runtime call failed; see stokes_last_cuda_error */
+    STOKES_ERR_OOM = -3,           /* device allocation failed */
+    STOKES_ERR_DIVERGED = -4,      /* NaN/Inf or residual growth beyond 1e6x its initial value */
+    STOKES_ERR_TIMEOUT = -5,       /* a bounded device-side wait gave up */
+    STOKES_ERR_NOT_CONVERGED = -6, /* the solver stopped at max_cycles above tol */
+    STOKES_ERR_STATE = -7          /* call out of order (e.g. smoothing before set_viscosity) */
+} stokes_status;
+
+typedef enum { STOKES_F32 = 0, STOKES_F64 = 1 } stokes_dtype;
+
+/* The five smoothers of Sec. 5 of the paper. */
+typedef enum {
+    STOKES_JACOBI = 0,         /* (ii)  damped Jacobi, separate vx and vy passes (both read the old v) */
+    STOKES_JACOBI_FUSED = 1,   /* (iii) the same map, vx and vy in one pass */
+    STOKES_JACOBI_BLOCKED = 2, /* (iv)  the same map, one pass over shared-memory tiles */
+    STOKES_RBGS = 3,           /* (i)   red-black Gauss-Seidel: vx red, vx black, vy red, vy black */
+    STOKES_RAS = 4             /* (v)   RAS-type temporally blocked Jacobi, Sec. 4.3 / Algorithm 2 */
+} stokes_variant;
+
+typedef enum {
+    STOKES_FIELD_VX = 0,
+    STOKES_FIELD_VY = 1,
+    STOKES_FIELD_P = 2,
+    STOKES_FIELD_ETA_C = 3,
+    STOKES_FIELD_ETA_N = 4
+} stokes_field;
+
+/* Tile shifts of the RAS outer iterations (Algorithm 2, "draw random shifts"). */
+typedef enum {
+    STOKES_SHIFT_NONE = 0,     /* s_i = s_j = 0 */
+    STOKES_SHIFT_SPLITMIX = 1, /* outer iteration t: s_i = SplitMix64(seed) output 2t mod tile_i,
+                                  s_j = output 2t+1 mod tile_j (outputs numbered from 0) */
+    STOKES_SHIFT_LIST = 2      /* s_i = shifts[2t], s_j = shifts[2t+1], host array */
+} stokes_shift_mode;
+
+typedef struct stokes_ctx stokes_ctx; /* opaque, library-owned */
+
+/* Parameters of one smoothing call.
+ * variant   stokes_variant.
+ * sweeps    N >= 0: number of sweeps (N_max of Algorithm 2).
+ * tile_i/j  tile size in cells for STOKES_RAS (T_I, T_J) and STOKES_JACOBI_BLOCKED;
+ *           0 selects the library default (32 x 32).
+ * k         RAS local sweeps per outer iteration (T_inner of Algorithm 2), >= 1.
+ *           ceil(N/k) outer iterations run; the last one runs N - (ceil(N/k)-1) k.
+ * overlap   RAS overlap o >= 0 in cells: each tile solves for the unknowns of
+ *           its cells grown by o cells, with everything beyond frozen at the
+ *           snapshot of the outer iteration (Dirichlet), and keeps only the
+ *           unknowns of its own cells.  o >= k-1 reproduces global Jacobi
+ *           exactly; o = 0 is the paper's ring-only tile.
+ * omega     damping (omega_u = 0.3 in Sec. 6.3), 0 < omega.
+ * seed, shift_mode, shifts   tile shifts (stokes_shift_mode); `shifts` is a host
+ *           array of 2*ceil(N/k) ints used only with STOKES_SHIFT_LIST. */
+typedef struct {
+    int variant;
+    int sweeps;
+    int tile_i, tile_j;
+    int k;
+    int overlap;
+    double omega;
+    uint64_t seed;
+    int shift_mode;
+    const int32_t *shifts;
+} stokes_smooth_params;
+
+/* Parameters of the multigrid solve (Sec. 3.2; configuration of Sec. 6.2).
+ * levels      maximum number of levels; coarsening halves nx and ny while both are
+ *             even and larger than `coarsest`.
+ * coarsest    stop coarsening at this size (cells per side); the coarsest level is
+ *             solved exactly with a dense FP64 factorisation, so it must have at
+ *             most 4096 unknowns.
+ * nu_pre, nu_post, nu_growth   level l runs ceil(nu_pre nu_growth^l) pre- and
+ *             ceil(nu_post nu_growth^l) post-sweeps (5, 5, 2.5 in Sec. 6.2).
+ * inner_dtype stokes_dtype of the V-cycle (smoothing, restriction, prolongation);
+ *             the residual and the update of v stay in the context's dtype.
+ * smoother    smoother of every level (tile/k/overlap/omega/seed; sweeps ignored).
+ * tol         stop when the relative velocity energy residual E_v <= tol.
+ * max_cycles  at most this many V-cycles. */
+typedef struct {
+    int levels;
+    int coarsest;
+    int nu_pre, nu_post;
+    double nu_growth;
+    int inner_dtype;
+    stokes_smooth_params smoother;
+    double tol;
+    int max_cycles;
+} stokes_mg_params;
+
+/* Create a context for an nx x ny grid on [0, lx] x [0, ly] computing in `dtype`
+ * on `cuda_stream` (a cudaStream_t, NULL for the legacy default stream) of the
+ * current device.  nx, ny >= 2; lx, ly > 0.  *out is set on success, NULL
+ * otherwise.  Allocates the library's per-grid buffers.  (Sec. 2.1.) */
+int stokes_create(int nx, int ny, double lx, double ly, int dtype, void *cuda_stream, stokes_ctx **out);
+
+/* Layout of the field buffers: every buffer is (ny+1) x *pitch_elems elements
+ * (*alloc_elems in total, may be NULL); *rows x *cols is the extent of `field`
+ * (stokes_field) inside it.  Any output pointer may be NULL. */
+int stokes_get_layout(const stokes_ctx *ctx, int field, int *rows, int *cols, int *pitch_elems,
+                      size_t *alloc_elems);
+
+/* Set the viscosity at cell centres (eta_c, "eta_P") and nodes (eta_n,
+ * "eta_B"), Fig. 1.  Device pointers in the context's layout and dtype, read
+ * once and copied; every viscosity must be positive and finite (not checked
+ * on the device).  Invalidates the multigrid hierarchy, which the next
+ * stokes_vcycle rebuilds. */
+int stokes_set_viscosity(stokes_ctx *ctx, const void *eta_c, const void *eta_n);
+
+/* Set the body force f of Eq. (6) (fx like vx, fy like vy; f_y = -rho g_y for
+ * Eq. (2) with gravity g_y).  Device pointers, copied. */
+int stokes_set_rhs(stokes_ctx *ctx, const void *fx, const void *fy);
+
+/* out = M v + G p at every unknown (Eq. (6) left-hand side), zero on walls and
+ * padding.  p may be NULL (p = 0).  out_x/out_y must not alias vx/vy/p. */
+int stokes_apply_operator(stokes_ctx *ctx, const void *vx, const void *vy, const void *p, void *out_x, void *out_y);
+
+/* Smooth M v = f - G p in place on (vx, vy) with the smoother of `params`
+ * (Sec. 5).  p may be NULL (p = 0).  Requires stokes_set_viscosity and
+ * stokes_set_rhs.  Asynchronous. */
+int stokes_smooth(stokes_ctx *ctx, void *vx, void *vy, const void *p, const stokes_smooth_params *params);
+
+/* Energy residual sums of Sec. 6.4, accumulated in FP64:
+ *   out[0] = sum over velocity unknowns of r_v^2 / (-diag M),  r_v = f - G p - M v
+ *   out[1] = sum over cells of r_p^2 eta_c / (2/hx^2 + 2/hy^2), r_p = -D v
+ *   out[2] = sum over velocity unknowns of f^2 / (-diag M)
+ * The relative energy residual is sqrt((out[0] + out[1]) / out[2]).  p may be
+ * NULL.  `out` is host memory; the call synchronises the context's stream.
+ * The summation order is fixed, so repeated calls give identical bits. */
+int stokes_residual_energy_norm(stokes_ctx *ctx, const void *vx, const void *vy, const void *p, double out[3]);
+
+/* Solve M v = f - G p by defect correction with geometric-multigrid V-cycles
+ * (Sec. 3.2): repeat { r = f - G p - M v in the context dtype; stop when
+ * E_v = sqrt(sum r^2/(-diag M) / sum f^2/(-diag M)) <= tol; e = V-cycle(r) in
+ * params->inner_dtype from e = 0; v += e }.  Improves (vx, vy) in place.
+ * *final_rel_resid receives the last E_v and *cycles the number of V-cycles
+ * (either may be NULL).  Returns STOKES_ERR_NOT_CONVERGED when max_cycles
+ * is reached above tol, STOKES_ERR_DIVERGED on NaN/Inf or growth.  The V-cycle
+ * body is captured once as a CUDA graph and replayed.  Synchronises. */
+int stokes_vcycle(stokes_ctx *ctx, void *vx, void *vy, const void *p, const stokes_mg_params *params,
+                  double *final_rel_resid, int *cycles);
+
+/* Kernel classes counted and timed by the profiling hooks below. */
+typedef enum {
+    STOKES_K_RAS = 0,    /* RAS / blocked-Jacobi tile kernel (one launch per outer iteration or sweep) */
+    STOKES_K_JACOBI = 1, /* global Jacobi pass kernels */
+    STOKES_K_RBGS = 2,   /* red-black Gauss-Seidel colour kernels */
+    STOKES_K_RHS = 3,    /* b = f - G p */
+    STOKES_K_ENERGY = 4, /* energy-norm reduction kernels */
+    STOKES_K_COPY = 5,   /* velocity / wall / viscosity copies and casts */
+    STOKES_K_APPLY = 6,  /* operator apply */
+    STOKES_K_MG = 7,     /* multigrid transfer, coarse-level and correction kernels */
+    STOKES_K_COUNT = 8
+} stokes_kernel_class;
+
+/* Profiling hooks (tracing, not needed for computing).  The context always
+ * counts the kernels it launches per class.  With timing enabled it also
+ * brackets every launch group with a pair of CUDA events on the context's
+ * stream.  stokes_profile_reset zeroes counts and times and sets the timing
+ * flag (0/1).  stokes_profile_read synchronises the stream and returns, for
+ * class `kind`, the number of kernel launches, the number of timed launch
+ * groups and their summed device time in milliseconds (any output may be
+ * NULL). */
+int stokes_profile_reset(stokes_ctx *ctx, int enable_timing);
+int stokes_profile_read(stokes_ctx *ctx, int kind, long long *kernels, long long *groups, double *total_ms);
+
+/* Release every library-owned buffer of the context.  NULL is accepted. */
+int stokes_destroy(stokes_ctx *ctx);
+
+/* Static text for a stokes_status value. */
+const char *stokes_strerror(int status);
+
+/* Text of the last CUDA error this thread's calls met ("" if none). */
+const char *stokes_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STOKES_H */

@@ -30,6 +30,8 @@ _SIGS = {
     "ora_ras": (_i, [_i, _i, _d, _d, _D, _D, _D, _D, _d, _i, _i, _i, _i, _i, _i, _u64, _I, _u64, _D, _D, _I]),
     "ora_ras_shift": (None, [_i, _u64, _i, _i, _i, _I]),
     "ora_energy": (None, [_i, _i, _d, _d, _D, _D, _D, _D, _D, _D, _D, _D]),
+    "ora_ras_tiles": (_i, [_i, _i, _d, _d, _D, _D, _D, _D, _d, _i, _i, _i, _i, _i, _i, _I, _i, _D, _D, _D, _D]),
+    "ora_tile_count": (_i, [_i, _i, _i]),
     "ora_mg_levels": (_i, [_i, _i, _i, _i]),
     "ora_mg_sweeps": (_i, [_i, _d, _i]),
     "ora_mg_prolong_add": (None, [_i, _i, _D, _D, _D, _D]),
@@ -167,6 +169,23 @@ def ras(g: Grid, bx, by, omega, sweeps, ti, tj, k, overlap, shift_mode=1, seed=0
     if return_counts:
         return vx, vy, counts[:vx.size].reshape(vx.shape), counts[vx.size:].reshape(vy.shape)
     return vx, vy
+
+
+def ras_tiles(g: Grid, bx, by, omega, ti, tj, ksweeps, overlap, si, sj, tiles, vx, vy, out_x, out_y):
+    """One RAS outer iteration on the listed tiles [(bx, by), ...] only; the
+    owned unknowns of those tiles are written into copies of out_x/out_y."""
+    vx, vy = _f64(vx), _f64(vy)
+    ox, oy = _f64(out_x).copy(), _f64(out_y).copy()
+    t = np.ascontiguousarray(np.asarray(tiles, dtype=np.int32).reshape(-1))
+    st = lib().ora_ras_tiles(*g.head, _p(_f64(bx)), _p(_f64(by)), omega, ti, tj, ksweeps, overlap, si, sj,
+                             t.ctypes.data_as(_I), len(t) // 2, _p(vx), _p(vy), _p(ox), _p(oy))
+    if st != 0:
+        raise ValueError("ora_ras_tiles: bad arguments")
+    return ox, oy
+
+
+def tile_count(n, T, s):
+    return int(lib().ora_tile_count(n, T, s))
 
 
 def energy(g: Grid, fx, fy, p, vx, vy):

@@ -892,3 +892,67 @@ int ora_mg_solve(int nx, int ny, double hx, double hy, const double *eta_c, cons
     mg_free(lv, L);
     return st ? -1 : c;
 }
+
+/* One RAS outer iteration restricted to a list of tiles: tiles (bx, by) =
+ * (tiles[2q], tiles[2q+1]) of the tiling with shift (si, sj) run `ksweeps`
+ * local sweeps from the snapshot (vx, vy) and write their owned unknowns to
+ * (ox, oy); every other entry of (ox, oy) is left as it is.  Used to check
+ * sampled tiles of full-size runs.  Returns 0, or -1 on bad arguments. */
+int ora_ras_tiles(int nx, int ny, double hx, double hy, const double *eta_c, const double *eta_n,
+                  const double *bx, const double *by, double omega, int ti, int tj, int ksweeps, int overlap,
+                  int si, int sj, const int *tiles, int ntiles, const double *vx, const double *vy, double *ox,
+                  double *oy)
+{
+    if (nx < 1 || ny < 1 || ti < 1 || tj < 1 || ksweeps < 0 || overlap < 0) return -1;
+    grid_t G = mkgrid(nx, ny, hx, hy, eta_c, eta_n), *g = &G;
+    int *cx = malloc((size_t)(nx / ti + 3) * sizeof(int));
+    int *cy = malloc((size_t)(ny / tj + 3) * sizeof(int));
+    int ntx = tile_cuts(nx, ti, si, cx), nty = tile_cuts(ny, tj, sj, cy);
+    double *wx = malloc(nvx(g) * sizeof(double)), *wy = malloc(nvy(g) * sizeof(double));
+    double *tx = malloc(nvx(g) * sizeof(double)), *ty = malloc(nvy(g) * sizeof(double));
+    memcpy(wx, vx, nvx(g) * sizeof(double));
+    memcpy(wy, vy, nvy(g) * sizeof(double));
+    memcpy(tx, vx, nvx(g) * sizeof(double));
+    memcpy(ty, vy, nvy(g) * sizeof(double));
+    int st = 0;
+    for (int q = 0; q < ntiles; ++q) {
+        int bxi = tiles[2 * q], byj = tiles[2 * q + 1];
+        if (bxi < 0 || bxi >= ntx || byj < 0 || byj >= nty) { st = -1; break; }
+        int x0 = cx[bxi], x1 = cx[bxi + 1], y0 = cy[byj], y1 = cy[byj + 1];
+        int lx0 = x0 - overlap < 0 ? 0 : x0 - overlap, lx1 = x1 + overlap > nx ? nx : x1 + overlap;
+        int ly0 = y0 - overlap < 0 ? 0 : y0 - overlap, ly1 = y1 + overlap > ny ? ny : y1 + overlap;
+        for (int s = 0; s < ksweeps; ++s) {
+            for (int j = ly0; j < ly1; ++j)
+                for (int i = lx0; i < lx1; ++i) {
+                    if (is_vx_unknown(g, j, i)) VX(tx, j, i) = jacobi_x(g, wx, wy, bx, omega, j, i);
+                    if (is_vy_unknown(g, j, i)) VY(ty, j, i) = jacobi_y(g, wx, wy, by, omega, j, i);
+                }
+            for (int j = ly0; j < ly1; ++j)
+                for (int i = lx0; i < lx1; ++i) {
+                    if (is_vx_unknown(g, j, i)) VX(wx, j, i) = VX(tx, j, i);
+                    if (is_vy_unknown(g, j, i)) VY(wy, j, i) = VY(ty, j, i);
+                }
+        }
+        for (int j = y0; j < y1; ++j)
+            for (int i = x0; i < x1; ++i) {
+                if (is_vx_unknown(g, j, i)) VX(ox, j, i) = VX(wx, j, i);
+                if (is_vy_unknown(g, j, i)) VY(oy, j, i) = VY(wy, j, i);
+            }
+        for (int j = ly0; j < ly1; ++j)
+            for (int i = lx0; i < lx1; ++i) {
+                if (is_vx_unknown(g, j, i)) VX(wx, j, i) = VX(tx, j, i) = VX(vx, j, i);
+                if (is_vy_unknown(g, j, i)) VY(wy, j, i) = VY(ty, j, i) = VY(vy, j, i);
+            }
+    }
+    free(wx); free(wy); free(tx); free(ty); free(cx); free(cy);
+    return st;
+}
+
+/* Number of tiles per direction of the tiling of [0, n) cut at s + m T. */
+int ora_tile_count(int n, int T, int s)
+{
+    int *c = malloc((size_t)(n / T + 3) * sizeof(int));
+    int m = tile_cuts(n, T, s, c);
+    free(c);
+    return m;
+}

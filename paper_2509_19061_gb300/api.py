@@ -1,0 +1,290 @@
+"""Thin Python binding of libstokes (include/stokes.h).
+
+Functions carry the C names and only marshal arguments: device pointers come
+from torch tensors, scalars are passed through, status codes become
+StokesError.  Every step of the computation runs in the library's CUDA
+kernels; there is no fallback, and a missing library raises.
+
+Field tensors use the library layout: a (ny+1) x pitch array of the context's
+dtype for every field (see stokes_get_layout); ``StokesContext.pack`` and
+``unpack`` convert from and to the natural staggered shapes.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libstokes.so")
+
+STOKES_OK = 0
+STOKES_ERR_ARG = -1
+STOKES_ERR_CUDA = -2
+STOKES_ERR_OOM = -3
+STOKES_ERR_DIVERGED = -4
+STOKES_ERR_TIMEOUT = -5
+STOKES_ERR_NOT_CONVERGED = -6
+STOKES_ERR_STATE = -7
+
+STOKES_F32, STOKES_F64 = 0, 1
+STOKES_JACOBI, STOKES_JACOBI_FUSED, STOKES_JACOBI_BLOCKED, STOKES_RBGS, STOKES_RAS = 0, 1, 2, 3, 4
+STOKES_FIELD_VX, STOKES_FIELD_VY, STOKES_FIELD_P, STOKES_FIELD_ETA_C, STOKES_FIELD_ETA_N = 0, 1, 2, 3, 4
+STOKES_SHIFT_NONE, STOKES_SHIFT_SPLITMIX, STOKES_SHIFT_LIST = 0, 1, 2
+KERNEL_CLASSES = ["ras", "jacobi", "rbgs", "rhs", "energy", "copy", "apply", "mg"]
+
+VARIANTS = {"jacobi": STOKES_JACOBI, "fused": STOKES_JACOBI_FUSED, "blocked": STOKES_JACOBI_BLOCKED,
+            "rbgs": STOKES_RBGS, "ras": STOKES_RAS}
+
+
+class StokesError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = "%s: %s" % (where, _lib().stokes_strerror(status).decode())
+        if status in (STOKES_ERR_CUDA, STOKES_ERR_OOM):
+            msg += " (%s)" % _lib().stokes_last_cuda_error().decode()
+        super().__init__(msg)
+
+
+class stokes_smooth_params(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("sweeps", ctypes.c_int), ("tile_i", ctypes.c_int),
+                ("tile_j", ctypes.c_int), ("k", ctypes.c_int), ("overlap", ctypes.c_int),
+                ("omega", ctypes.c_double), ("seed", ctypes.c_uint64), ("shift_mode", ctypes.c_int),
+                ("shifts", ctypes.POINTER(ctypes.c_int32))]
+
+
+class stokes_mg_params(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("coarsest", ctypes.c_int), ("nu_pre", ctypes.c_int),
+                ("nu_post", ctypes.c_int), ("nu_growth", ctypes.c_double), ("inner_dtype", ctypes.c_int),
+                ("smoother", stokes_smooth_params), ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int)]
+
+
+_VP, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+_SIGS = {
+    "stokes_create": (_I, [_I, _I, _D, _D, _I, _VP, ctypes.POINTER(_VP)]),
+    "stokes_get_layout": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                               ctypes.POINTER(ctypes.c_size_t)]),
+    "stokes_set_viscosity": (_I, [_VP, _VP, _VP]),
+    "stokes_set_rhs": (_I, [_VP, _VP, _VP]),
+    "stokes_apply_operator": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "stokes_smooth": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(stokes_smooth_params)]),
+    "stokes_residual_energy_norm": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(_D)]),
+    "stokes_vcycle": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(stokes_mg_params), ctypes.POINTER(_D),
+                           ctypes.POINTER(_I)]),
+    "stokes_profile_reset": (_I, [_VP, _I]),
+    "stokes_profile_read": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                 ctypes.POINTER(_D)]),
+    "stokes_destroy": (_I, [_VP]),
+    "stokes_strerror": (ctypes.c_char_p, [_I]),
+    "stokes_last_cuda_error": (ctypes.c_char_p, []),
+}
+
+_handle = None
+
+
+def _lib():
+    """Load libstokes.so (built in place by paper_2509_19061_gb300.build)."""
+    global _handle
+    if _handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libstokes.so is not built (%s); run paper_2509_19061_gb300.build.build()" % LIB_PATH)
+        h = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(h, name)
+            fn.restype = res
+            fn.argtypes = args
+        _handle = h
+    return _handle
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(status, where):
+    if status != STOKES_OK:
+        raise StokesError(status, where)
+    return status
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (None -> NULL)."""
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# --------------------------------------------------------------------------
+# C-named entry points
+# --------------------------------------------------------------------------
+def stokes_create(nx, ny, lx, ly, dtype, cuda_stream=None):
+    out = ctypes.c_void_p()
+    stream = ctypes.c_void_p(cuda_stream) if cuda_stream else None
+    _check(_lib().stokes_create(nx, ny, lx, ly, dtype, stream, ctypes.byref(out)), "stokes_create")
+    return out
+
+
+def stokes_get_layout(ctx, field):
+    r, c, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    n = ctypes.c_size_t()
+    _check(_lib().stokes_get_layout(ctx, field, ctypes.byref(r), ctypes.byref(c), ctypes.byref(p), ctypes.byref(n)),
+           "stokes_get_layout")
+    return r.value, c.value, p.value, n.value
+
+
+def stokes_set_viscosity(ctx, eta_c, eta_n):
+    _check(_lib().stokes_set_viscosity(ctx, _ptr(eta_c), _ptr(eta_n)), "stokes_set_viscosity")
+
+
+def stokes_set_rhs(ctx, fx, fy):
+    _check(_lib().stokes_set_rhs(ctx, _ptr(fx), _ptr(fy)), "stokes_set_rhs")
+
+
+def stokes_apply_operator(ctx, vx, vy, p, out_x, out_y):
+    _check(_lib().stokes_apply_operator(ctx, _ptr(vx), _ptr(vy), _ptr(p), _ptr(out_x), _ptr(out_y)),
+           "stokes_apply_operator")
+
+
+def smooth_params(variant="ras", sweeps=1, tile=(32, 32), k=4, overlap=None, omega=0.3, seed=0, shift_mode=None,
+                  shifts=None):
+    """Build a stokes_smooth_params.  overlap=None means k-1 (exact temporal
+    blocking); shift_mode defaults to SplitMix64 shifts for RAS."""
+    v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    if overlap is None:
+        overlap = max(k - 1, 0)
+    if shift_mode is None:
+        shift_mode = STOKES_SHIFT_LIST if shifts is not None else STOKES_SHIFT_SPLITMIX
+    p = stokes_smooth_params(v, sweeps, tile[0], tile[1], k, overlap, omega, seed & (2**64 - 1), shift_mode, None)
+    if shifts is not None:
+        arr = np.ascontiguousarray(np.asarray(shifts, dtype=np.int32).reshape(-1))
+        p._shifts_keepalive = arr
+        p.shifts = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    return p
+
+
+def stokes_smooth(ctx, vx, vy, p, params):
+    _check(_lib().stokes_smooth(ctx, _ptr(vx), _ptr(vy), _ptr(p), ctypes.byref(params)), "stokes_smooth")
+
+
+def stokes_residual_energy_norm(ctx, vx, vy, p=None):
+    out = (ctypes.c_double * 3)()
+    _check(_lib().stokes_residual_energy_norm(ctx, _ptr(vx), _ptr(vy), _ptr(p), out), "stokes_residual_energy_norm")
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def stokes_vcycle(ctx, vx, vy, p, params):
+    """Returns (status, final_rel_resid, cycles); raises on errors other than
+    STOKES_ERR_NOT_CONVERGED."""
+    fr, cy = ctypes.c_double(0.0), ctypes.c_int(0)
+    st = _lib().stokes_vcycle(ctx, _ptr(vx), _ptr(vy), _ptr(p), ctypes.byref(params), ctypes.byref(fr),
+                              ctypes.byref(cy))
+    if st not in (STOKES_OK, STOKES_ERR_NOT_CONVERGED):
+        raise StokesError(st, "stokes_vcycle")
+    return st, fr.value, cy.value
+
+
+def stokes_profile_reset(ctx, enable_timing):
+    _check(_lib().stokes_profile_reset(ctx, 1 if enable_timing else 0), "stokes_profile_reset")
+
+
+def stokes_profile_read(ctx, kind):
+    """Returns (kernel launches, timed launch groups, total ms) of one class."""
+    k, g, ms = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_double()
+    _check(_lib().stokes_profile_read(ctx, kind, ctypes.byref(k), ctypes.byref(g), ctypes.byref(ms)),
+           "stokes_profile_read")
+    return k.value, g.value, ms.value
+
+
+def stokes_destroy(ctx):
+    if ctx is not None:
+        _check(_lib().stokes_destroy(ctx), "stokes_destroy")
+
+
+# --------------------------------------------------------------------------
+# convenience wrapper with torch tensors
+# --------------------------------------------------------------------------
+_FIELD_OF = {"vx": STOKES_FIELD_VX, "fx": STOKES_FIELD_VX, "vy": STOKES_FIELD_VY, "fy": STOKES_FIELD_VY,
+             "p": STOKES_FIELD_P, "eta_c": STOKES_FIELD_ETA_C, "eta_n": STOKES_FIELD_ETA_N}
+
+
+class StokesContext:
+    """Owns a stokes_ctx; allocates and converts field tensors."""
+
+    def __init__(self, nx, ny, lx=1.0, ly=1.0, dtype="f64", device="cuda", stream=None):
+        import torch
+        self.torch = torch
+        self.nx, self.ny, self.lx, self.ly = nx, ny, lx, ly
+        self.dtype_code = STOKES_F64 if dtype in ("f64", "float64", torch.float64) else STOKES_F32
+        self.tdtype = torch.float64 if self.dtype_code == STOKES_F64 else torch.float32
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.ctx = stokes_create(nx, ny, lx, ly, self.dtype_code, self.stream.cuda_stream)
+        _, _, self.pitch, self.alloc = stokes_get_layout(self.ctx, STOKES_FIELD_VX)
+        self.shape = {name: stokes_get_layout(self.ctx, f)[:2] for name, f in _FIELD_OF.items()}
+
+    def close(self):
+        if self.ctx is not None:
+            stokes_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def field(self):
+        return self.torch.zeros((self.ny + 1, self.pitch), dtype=self.tdtype, device=self.device)
+
+    def pack(self, arr, name, out=None):
+        """Natural-shape array -> library-layout device tensor (padding zero)."""
+        r, c = self.shape[name]
+        a = np.asarray(arr)
+        assert a.shape == (r, c), "%s: expected %s, got %s" % (name, (r, c), a.shape)
+        host = self.torch.zeros((self.ny + 1, self.pitch), dtype=self.tdtype)
+        host[:r, :c] = self.torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(self.tdtype)
+        if out is None:
+            return host.to(self.device)
+        out.copy_(host)
+        return out
+
+    def unpack(self, t, name):
+        r, c = self.shape[name]
+        return t[:r, :c].double().cpu().numpy()
+
+    def set_problem(self, prob):
+        """Viscosity and body force of an inputs.Problem."""
+        ec, en = self.pack(prob.eta_c, "eta_c"), self.pack(prob.eta_n, "eta_n")
+        fx, fy = self.pack(prob.fx, "fx"), self.pack(prob.fy, "fy")
+        stokes_set_viscosity(self.ctx, ec, en)
+        stokes_set_rhs(self.ctx, fx, fy)
+
+    def set_viscosity_dev(self, eta_c, eta_n):
+        """Viscosity from tensors already in the library layout."""
+        stokes_set_viscosity(self.ctx, eta_c, eta_n)
+
+    def set_rhs_dev(self, fx, fy):
+        stokes_set_rhs(self.ctx, fx, fy)
+
+    def set_viscosity(self, eta_c, eta_n):
+        stokes_set_viscosity(self.ctx, self.pack(eta_c, "eta_c"), self.pack(eta_n, "eta_n"))
+
+    def set_rhs(self, fx, fy):
+        stokes_set_rhs(self.ctx, self.pack(fx, "fx"), self.pack(fy, "fy"))
+
+    def smooth(self, vx, vy, p=None, **kw):
+        stokes_smooth(self.ctx, vx, vy, p, smooth_params(**kw))
+
+    def apply(self, vx, vy, p=None):
+        ox, oy = self.field(), self.field()
+        stokes_apply_operator(self.ctx, vx, vy, p, ox, oy)
+        return ox, oy
+
+    def energy(self, vx, vy, p=None):
+        return stokes_residual_energy_norm(self.ctx, vx, vy, p)
+
+    def profile_reset(self, timing=False):
+        stokes_profile_reset(self.ctx, timing)
+
+    def profile(self):
+        """{class: (kernel launches, timed groups, total ms)}"""
+        return {name: stokes_profile_read(self.ctx, i) for i, name in enumerate(KERNEL_CLASSES)}

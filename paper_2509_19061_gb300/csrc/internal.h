@@ -1,0 +1,92 @@
+// internal.h -- declarations shared by the translation units of libstokes.
+// Not part of the public interface (include/stokes.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace stokes {
+
+// Geometry and coefficients of one grid level, passed by value to kernels.
+// Every field of the level is a (ny+1) x pitch array (see include/stokes.h).
+template <typename T>
+struct GridDesc {
+    int nx, ny, pitch;
+    T ihx, ihy;   // 1/hx, 1/hy
+    T ihx2, ihy2; // 1/hx^2, 1/hy^2
+    double lap;   // 2/hx^2 + 2/hy^2 (pressure weight of the energy norm)
+};
+
+template <typename T>
+GridDesc<T> make_grid(int nx, int ny, int pitch, double hx, double hy)
+{
+    GridDesc<T> g;
+    g.nx = nx;
+    g.ny = ny;
+    g.pitch = pitch;
+    g.ihx = (T)(1.0 / hx);
+    g.ihy = (T)(1.0 / hy);
+    g.ihx2 = (T)(1.0 / (hx * hx));
+    g.ihy2 = (T)(1.0 / (hy * hy));
+    g.lap = 2.0 / (hx * hx) + 2.0 / (hy * hy);
+    return g;
+}
+
+// Velocity-operator coefficients: eta_c and eta_n with the boundary nodes
+// zeroed (no shear stress there), plus the right-hand side b.
+template <typename T>
+struct Coeffs {
+    const T *eta_c;
+    const T *eta_n; // boundary nodes hold 0
+    const T *bx, *by;
+};
+
+// ---- stencil kernels (stencil_kernels.cu) --------------------------------
+template <typename T>
+cudaError_t launch_copy_eta(const GridDesc<T> &g, const T *eta_c_in, const T *eta_n_in, T *eta_c, T *eta_n,
+                            cudaStream_t s);
+template <typename T>
+cudaError_t launch_rhs(const GridDesc<T> &g, const T *fx, const T *fy, const T *p, T *bx, T *by, cudaStream_t s);
+template <typename T>
+cudaError_t launch_apply(const GridDesc<T> &g, const T *eta_c, const T *eta_n, const T *vx, const T *vy, const T *p,
+                         T *ox, T *oy, cudaStream_t s);
+// variant 0: separate vx and vy passes; 1: fused pass.  Reads (vx, vy), writes
+// the unknowns and walls of (ox, oy).
+template <typename T>
+cudaError_t launch_jacobi(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const T *vx, const T *vy, T *ox, T *oy,
+                          int fused, cudaStream_t s);
+template <typename T>
+cudaError_t launch_rbgs_sweep(const GridDesc<T> &g, const Coeffs<T> &c, T omega, T *vx, T *vy, cudaStream_t s);
+// copy the in-extent entries (unknowns and walls) of vx, vy
+template <typename T>
+cudaError_t launch_copy_velocity(const GridDesc<T> &g, const T *vx, const T *vy, T *ox, T *oy, cudaStream_t s);
+template <typename T>
+cudaError_t launch_copy_walls(const GridDesc<T> &g, const T *vx, const T *vy, T *ox, T *oy, cudaStream_t s);
+// Energy sums (3 doubles) into out[0..2] on the device; `partials` holds
+// energy_partials() * 3 doubles.
+int energy_partials();
+template <typename T>
+cudaError_t launch_energy(const GridDesc<T> &g, const T *eta_c, const T *eta_n, const T *fx, const T *fy,
+                          const T *bx, const T *by, const T *vx, const T *vy, double *partials, double *out,
+                          cudaStream_t s);
+
+// ---- tiled / RAS kernel (ras_kernels.cu) ---------------------------------
+struct TileGrid {
+    int ti, tj;   // tile size (cells)
+    int si, sj;   // shift
+    int ntx, nty; // tiles per direction
+};
+TileGrid make_tiles(int nx, int ny, int ti, int tj, int si, int sj);
+// One RAS outer iteration: `ksweeps` local Jacobi sweeps on each tile grown by
+// `overlap`, reading (vx, vy), writing the owned unknowns to (ox, oy).
+template <typename T>
+cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const TileGrid &tg, int ksweeps,
+                       int overlap, const T *vx, const T *vy, T *ox, T *oy, cudaStream_t s);
+size_t ras_smem_bytes(int ti, int tj, int overlap, size_t elem);
+int ras_max_smem();
+
+// SplitMix64 (Steele, Lea & Flood 2014): output c (from 0) of the generator
+// seeded with `seed`.
+uint64_t splitmix64(uint64_t seed, uint64_t c);
+
+} // namespace stokes

@@ -1,0 +1,371 @@
+// stencil_kernels.cu -- global-memory kernels of libstokes: copies, right-hand
+// side, operator apply, Jacobi (separate and fused passes), red-black
+// Gauss-Seidel and the energy residual norm.
+//
+// The operator is the flux form of Eq. (1)-(3) of arXiv 2509.19061 on the
+// fully staggered grid of Sec. 2.1: deviatoric stresses at cell centres
+// (sigma'_xx, sigma'_yy) and nodes (sigma'_xy), their divided differences at
+// the velocity points.  Every field is a (ny+1) x pitch array; the library's
+// copy of eta_n holds zero on boundary nodes, which makes the shear stress
+// vanish there (free slip) without a branch.
+#include "internal.h"
+#include "stencil.cuh"
+
+namespace stokes {
+
+namespace {
+
+constexpr int BX = 32, BY = 8;
+
+inline dim3 grid2d(int w, int h) { return dim3((unsigned)((w + BX - 1) / BX), (unsigned)((h + BY - 1) / BY)); }
+
+// (M v)_x and diag(M)_x at vx unknown (j, i), 1 <= i <= nx-1, 0 <= j < ny.
+// Rows outside the vx extent (j = -1, j = ny) enter only through a zero
+// eta_n and are read as zero.
+template <typename T>
+__device__ __forceinline__ void op_x(const GridDesc<T> &g, const T *__restrict__ eta_c, const T *__restrict__ eta_n,
+                                     const T *__restrict__ vx, const T *__restrict__ vy, int j, int i, T &m, T &d,
+                                     T &vc)
+{
+    const size_t P = (size_t)g.pitch;
+    const size_t q = (size_t)j * P + (size_t)i;
+    vc = vx[q];
+    stencil_x(g, vc, vx[q + 1], vx[q - 1], j + 1 < g.ny ? vx[q + P] : T(0), j > 0 ? vx[q - P] : T(0), vy[q + P],
+              vy[q + P - 1], vy[q], vy[q - 1], eta_c[q], eta_c[q - 1], eta_n[q + P], eta_n[q], m, d);
+}
+
+// (M v)_y and diag(M)_y at vy unknown (j, i), 1 <= j <= ny-1, 0 <= i < nx.
+template <typename T>
+__device__ __forceinline__ void op_y(const GridDesc<T> &g, const T *__restrict__ eta_c, const T *__restrict__ eta_n,
+                                     const T *__restrict__ vx, const T *__restrict__ vy, int j, int i, T &m, T &d,
+                                     T &vc)
+{
+    const size_t P = (size_t)g.pitch;
+    const size_t q = (size_t)j * P + (size_t)i;
+    vc = vy[q];
+    stencil_y(g, vc, vy[q + P], vy[q - P], i + 1 < g.nx ? vy[q + 1] : T(0), i > 0 ? vy[q - 1] : T(0), vx[q + 1],
+              vx[q + 1 - P], vx[q], vx[q - P], eta_c[q], eta_c[q - P], eta_n[q + 1], eta_n[q], m, d);
+}
+
+template <typename T>
+__device__ __forceinline__ bool vx_unknown(const GridDesc<T> &g, int j, int i)
+{
+    return j < g.ny && i >= 1 && i <= g.nx - 1;
+}
+template <typename T>
+__device__ __forceinline__ bool vy_unknown(const GridDesc<T> &g, int j, int i)
+{
+    return i < g.nx && j >= 1 && j <= g.ny - 1;
+}
+template <typename T>
+__device__ __forceinline__ bool vx_wall(const GridDesc<T> &g, int j, int i)
+{
+    return j < g.ny && (i == 0 || i == g.nx);
+}
+template <typename T>
+__device__ __forceinline__ bool vy_wall(const GridDesc<T> &g, int j, int i)
+{
+    return i < g.nx && (j == 0 || j == g.ny);
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_copy_eta(GridDesc<T> g, const T *__restrict__ ec_in, const T *__restrict__ en_in,
+                           T *__restrict__ ec, T *__restrict__ en)
+{
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i > g.nx || j > g.ny) return;
+    const size_t q = (size_t)j * g.pitch + i;
+    if (i < g.nx && j < g.ny) ec[q] = ec_in[q];
+    const bool interior = i >= 1 && i <= g.nx - 1 && j >= 1 && j <= g.ny - 1;
+    en[q] = interior ? en_in[q] : T(0);
+}
+
+// b = f - G p with (G p) = -grad p; zero on walls.
+template <typename T>
+__global__ void k_rhs(GridDesc<T> g, const T *__restrict__ fx, const T *__restrict__ fy, const T *__restrict__ p,
+                      T *__restrict__ bx, T *__restrict__ by)
+{
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i > g.nx || j > g.ny) return;
+    const size_t P = (size_t)g.pitch, q = (size_t)j * P + i;
+    if (j < g.ny) {
+        T b = T(0);
+        if (vx_unknown(g, j, i)) b = fx[q] + (p ? (p[q] - p[q - 1]) * g.ihx : T(0));
+        bx[q] = b;
+    }
+    if (i < g.nx) {
+        T b = T(0);
+        if (vy_unknown(g, j, i)) b = fy[q] + (p ? (p[q] - p[q - P]) * g.ihy : T(0));
+        by[q] = b;
+    }
+}
+
+// out = M v + G p at unknowns; zero on walls and padding.
+template <typename T>
+__global__ void k_apply(GridDesc<T> g, const T *__restrict__ eta_c, const T *__restrict__ eta_n,
+                        const T *__restrict__ vx, const T *__restrict__ vy, const T *__restrict__ p,
+                        T *__restrict__ ox, T *__restrict__ oy)
+{
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i >= g.pitch || j > g.ny) return;
+    const size_t P = (size_t)g.pitch, q = (size_t)j * P + i;
+    T m, d, vc;
+    T rx = T(0), ry = T(0);
+    if (vx_unknown(g, j, i)) {
+        op_x(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
+        rx = m - (p ? (p[q] - p[q - 1]) * g.ihx : T(0));
+    }
+    if (vy_unknown(g, j, i)) {
+        op_y(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
+        ry = m - (p ? (p[q] - p[q - P]) * g.ihy : T(0));
+    }
+    ox[q] = rx;
+    oy[q] = ry;
+}
+
+// One damped Jacobi pass.  DO_X / DO_Y select the component(s); every update
+// reads the old (vx, vy); walls are copied so the output is a complete field.
+template <typename T, bool DO_X, bool DO_Y>
+__global__ void k_jacobi(GridDesc<T> g, Coeffs<T> c, T omega, const T *__restrict__ vx, const T *__restrict__ vy,
+                         T *__restrict__ ox, T *__restrict__ oy)
+{
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i > g.nx || j > g.ny) return;
+    const size_t q = (size_t)j * g.pitch + i;
+    T m, d, vc;
+    if (DO_X) {
+        if (vx_unknown(g, j, i)) {
+            op_x(g, c.eta_c, c.eta_n, vx, vy, j, i, m, d, vc);
+            ox[q] = jacobi_update(vc, c.bx[q], m, d, omega);
+        } else if (vx_wall(g, j, i)) {
+            ox[q] = vx[q];
+        }
+    }
+    if (DO_Y) {
+        if (vy_unknown(g, j, i)) {
+            op_y(g, c.eta_c, c.eta_n, vx, vy, j, i, m, d, vc);
+            oy[q] = jacobi_update(vc, c.by[q], m, d, omega);
+        } else if (vy_wall(g, j, i)) {
+            oy[q] = vy[q];
+        }
+    }
+}
+
+// One colour of one component of red-black Gauss-Seidel, in place.  Thread t
+// of row j takes the t-th point of that colour in the row.
+template <typename T, bool X>
+__global__ void k_rbgs(GridDesc<T> g, Coeffs<T> c, T omega, int colour, T *__restrict__ vx, T *__restrict__ vy)
+{
+    const int t = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    const int i = 2 * t + ((j + colour) & 1);
+    const size_t q = (size_t)j * g.pitch + i;
+    T m, d, vc;
+    if (X) {
+        if (!vx_unknown(g, j, i)) return;
+        op_x(g, c.eta_c, c.eta_n, vx, vy, j, i, m, d, vc);
+        vx[q] = jacobi_update(vc, c.bx[q], m, d, omega);
+    } else {
+        if (!vy_unknown(g, j, i)) return;
+        op_y(g, c.eta_c, c.eta_n, vx, vy, j, i, m, d, vc);
+        vy[q] = jacobi_update(vc, c.by[q], m, d, omega);
+    }
+}
+
+template <typename T>
+__global__ void k_copy_velocity(GridDesc<T> g, const T *__restrict__ vx, const T *__restrict__ vy,
+                                T *__restrict__ ox, T *__restrict__ oy)
+{
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i > g.nx || j > g.ny) return;
+    const size_t q = (size_t)j * g.pitch + i;
+    if (j < g.ny) ox[q] = vx[q];
+    if (i < g.nx) oy[q] = vy[q];
+}
+
+template <typename T>
+__global__ void k_copy_walls(GridDesc<T> g, const T *__restrict__ vx, const T *__restrict__ vy, T *__restrict__ ox,
+                             T *__restrict__ oy)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t P = (size_t)g.pitch;
+    if (t < g.ny) { // vx walls of row t
+        ox[t * P] = vx[t * P];
+        ox[t * P + g.nx] = vx[t * P + g.nx];
+    }
+    if (t < g.nx) { // vy walls of column t
+        oy[t] = vy[t];
+        oy[(size_t)g.ny * P + t] = vy[(size_t)g.ny * P + t];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// energy norm, Sec. 6.4 (FP64 accumulation, fixed reduction order)
+constexpr int EN_THREADS = 256;
+constexpr int EN_BLOCKS = 152 * 4;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(EN_THREADS) k_energy(GridDesc<T> g, const T *__restrict__ eta_c,
+                                                       const T *__restrict__ eta_n, const T *__restrict__ fx,
+                                                       const T *__restrict__ fy, const T *__restrict__ bx,
+                                                       const T *__restrict__ by, const T *__restrict__ vx,
+                                                       const T *__restrict__ vy, double *__restrict__ partials)
+{
+    double s_rv = 0.0, s_rp = 0.0, s_ff = 0.0;
+    const long w = (long)g.nx + 1, total = w * (long)(g.ny + 1);
+    for (long t = (long)blockIdx.x * EN_THREADS + threadIdx.x; t < total; t += (long)gridDim.x * EN_THREADS) {
+        const int j = (int)(t / w), i = (int)(t - (long)j * w);
+        const size_t q = (size_t)j * g.pitch + i;
+        T m, d, vc;
+        if (vx_unknown(g, j, i)) {
+            op_x(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
+            const double r = (double)(bx[q] - m), wgt = -(double)d, f = (double)fx[q];
+            s_rv += r * r / wgt;
+            s_ff += f * f / wgt;
+        }
+        if (vy_unknown(g, j, i)) {
+            op_y(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
+            const double r = (double)(by[q] - m), wgt = -(double)d, f = (double)fy[q];
+            s_rv += r * r / wgt;
+            s_ff += f * f / wgt;
+        }
+        if (i < g.nx && j < g.ny) {
+            const T dv = (vx[q + 1] - vx[q]) * g.ihx + (vy[q + g.pitch] - vy[q]) * g.ihy;
+            const double r = (double)dv;
+            s_rp += r * r * (double)eta_c[q] / g.lap;
+        }
+    }
+    __shared__ double sh[3][EN_THREADS / 32];
+    s_rv = warp_sum(s_rv);
+    s_rp = warp_sum(s_rp);
+    s_ff = warp_sum(s_ff);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][wid] = s_rv;
+        sh[1][wid] = s_rp;
+        sh[2][wid] = s_ff;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int q = 0; q < EN_THREADS / 32; ++q) s += sh[threadIdx.x][q];
+        partials[(size_t)blockIdx.x * 3 + threadIdx.x] = s;
+    }
+}
+
+__global__ void k_energy_final(const double *__restrict__ partials, int nblocks, double *__restrict__ out)
+{
+    // one warp per component, fixed order
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int b = lane; b < nblocks; b += 32) s += partials[(size_t)b * 3 + c];
+    s = warp_sum(s);
+    if (lane == 0) out[c] = s;
+}
+
+} // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+template <typename T>
+cudaError_t launch_copy_eta(const GridDesc<T> &g, const T *eta_c_in, const T *eta_n_in, T *eta_c, T *eta_n,
+                            cudaStream_t s)
+{
+    k_copy_eta<T><<<grid2d(g.nx + 1, g.ny + 1), dim3(BX, BY), 0, s>>>(g, eta_c_in, eta_n_in, eta_c, eta_n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_rhs(const GridDesc<T> &g, const T *fx, const T *fy, const T *p, T *bx, T *by, cudaStream_t s)
+{
+    k_rhs<T><<<grid2d(g.nx + 1, g.ny + 1), dim3(BX, BY), 0, s>>>(g, fx, fy, p, bx, by);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_apply(const GridDesc<T> &g, const T *eta_c, const T *eta_n, const T *vx, const T *vy, const T *p,
+                         T *ox, T *oy, cudaStream_t s)
+{
+    k_apply<T><<<grid2d(g.pitch, g.ny + 1), dim3(BX, BY), 0, s>>>(g, eta_c, eta_n, vx, vy, p, ox, oy);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_jacobi(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const T *vx, const T *vy, T *ox, T *oy,
+                          int fused, cudaStream_t s)
+{
+    const dim3 grid = grid2d(g.nx + 1, g.ny + 1), block(BX, BY);
+    if (fused) {
+        k_jacobi<T, true, true><<<grid, block, 0, s>>>(g, c, omega, vx, vy, ox, oy);
+    } else {
+        k_jacobi<T, true, false><<<grid, block, 0, s>>>(g, c, omega, vx, vy, ox, oy);
+        k_jacobi<T, false, true><<<grid, block, 0, s>>>(g, c, omega, vx, vy, ox, oy);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_rbgs_sweep(const GridDesc<T> &g, const Coeffs<T> &c, T omega, T *vx, T *vy, cudaStream_t s)
+{
+    const dim3 grid = grid2d((g.nx + 2) / 2, g.ny + 1), block(BX, BY);
+    k_rbgs<T, true><<<grid, block, 0, s>>>(g, c, omega, 0, vx, vy);
+    k_rbgs<T, true><<<grid, block, 0, s>>>(g, c, omega, 1, vx, vy);
+    k_rbgs<T, false><<<grid, block, 0, s>>>(g, c, omega, 0, vx, vy);
+    k_rbgs<T, false><<<grid, block, 0, s>>>(g, c, omega, 1, vx, vy);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_copy_velocity(const GridDesc<T> &g, const T *vx, const T *vy, T *ox, T *oy, cudaStream_t s)
+{
+    k_copy_velocity<T><<<grid2d(g.nx + 1, g.ny + 1), dim3(BX, BY), 0, s>>>(g, vx, vy, ox, oy);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_copy_walls(const GridDesc<T> &g, const T *vx, const T *vy, T *ox, T *oy, cudaStream_t s)
+{
+    const int n = (g.nx > g.ny ? g.nx : g.ny);
+    k_copy_walls<T><<<(n + 255) / 256, 256, 0, s>>>(g, vx, vy, ox, oy);
+    return cudaGetLastError();
+}
+
+int energy_partials() { return EN_BLOCKS; }
+
+template <typename T>
+cudaError_t launch_energy(const GridDesc<T> &g, const T *eta_c, const T *eta_n, const T *fx, const T *fy,
+                          const T *bx, const T *by, const T *vx, const T *vy, double *partials, double *out,
+                          cudaStream_t s)
+{
+    k_energy<T><<<EN_BLOCKS, EN_THREADS, 0, s>>>(g, eta_c, eta_n, fx, fy, bx, by, vx, vy, partials);
+    k_energy_final<<<1, 96, 0, s>>>(partials, EN_BLOCKS, out);
+    return cudaGetLastError();
+}
+
+#define INST(T)                                                                                                    \
+    template cudaError_t launch_copy_eta<T>(const GridDesc<T> &, const T *, const T *, T *, T *, cudaStream_t);    \
+    template cudaError_t launch_rhs<T>(const GridDesc<T> &, const T *, const T *, const T *, T *, T *,             \
+                                       cudaStream_t);                                                              \
+    template cudaError_t launch_apply<T>(const GridDesc<T> &, const T *, const T *, const T *, const T *,          \
+                                         const T *, T *, T *, cudaStream_t);                                       \
+    template cudaError_t launch_jacobi<T>(const GridDesc<T> &, const Coeffs<T> &, T, const T *, const T *, T *,    \
+                                          T *, int, cudaStream_t);                                                 \
+    template cudaError_t launch_rbgs_sweep<T>(const GridDesc<T> &, const Coeffs<T> &, T, T *, T *, cudaStream_t); \
+    template cudaError_t launch_copy_velocity<T>(const GridDesc<T> &, const T *, const T *, T *, T *,              \
+                                                 cudaStream_t);                                                    \
+    template cudaError_t launch_copy_walls<T>(const GridDesc<T> &, const T *, const T *, T *, T *, cudaStream_t);  \
+    template cudaError_t launch_energy<T>(const GridDesc<T> &, const T *, const T *, const T *, const T *,         \
+                                          const T *, const T *, const T *, const T *, double *, double *,          \
+                                          cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+} // namespace stokes

@@ -1,0 +1,339 @@
+"""GPU parity of libstokes against the FP64 oracle, through the C ABI.
+
+FP64: normwise relative error ||v_gpu - v_oracle||_2 / ||v_oracle||_2 <= 1e-12
+after every sweep count tested.  FP32: the error of the FP32 result against
+the FP64 oracle in the diag(-M)-weighted energy norm, relative to the same
+norm of the FP64 result, is below FP32_ENERGY_TOL (derived in the design
+notes: each sweep adds a few units of FP32 roundoff relative to |v|).
+"""
+import numpy as np
+import pytest
+
+import oracle as ora
+from paper_2509_19061_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-12
+FP32_ENERGY_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_19061_gb300 import api as a, build
+    build.build()
+    return a
+
+
+def ogrid(prob):
+    return ora.Grid(prob.nx, prob.ny, prob.hx, prob.hy, prob.eta_c, prob.eta_n)
+
+
+def rel(a, b):
+    num = sum(np.sum((x - y) ** 2) for x, y in zip(a, b))
+    den = sum(np.sum(y ** 2) for y in b)
+    return float(np.sqrt(num / den))
+
+
+def energy_rel(g, a, b):
+    """sqrt(sum (-d) (a-b)^2 / sum (-d) b^2) over the unknowns."""
+    dx, dy = ora.diag_M(g)
+    num = np.sum(-dx * (a[0] - b[0]) ** 2) + np.sum(-dy * (a[1] - b[1]) ** 2)
+    den = np.sum(-dx * b[0] ** 2) + np.sum(-dy * b[1] ** 2)
+    return float(np.sqrt(num / den))
+
+
+def rand_problem(nx, ny, seed, lx=1.3, ly=0.9):
+    prob = inputs.sinker_problem(nx, ny, lx=lx, ly=ly, eta_in=1e3)
+    ec, en = inputs.random_viscosity(nx, ny, seed, (-2.0, 2.0))
+    prob.eta_c, prob.eta_n = ec, en
+    return prob
+
+
+class Run:
+    """A context holding one problem and a velocity state on the GPU."""
+
+    def __init__(self, api, prob, dtype, v0=None, p=None):
+        self.api, self.prob = api, prob
+        self.ctx = api.StokesContext(prob.nx, prob.ny, prob.lx, prob.ly, dtype)
+        self.ctx.set_problem(prob)
+        if v0 is None:
+            v0 = (np.zeros((prob.ny, prob.nx + 1)), np.zeros((prob.ny + 1, prob.nx)))
+        self.vx, self.vy = self.ctx.pack(v0[0], "vx"), self.ctx.pack(v0[1], "vy")
+        self.p = None if p is None else self.ctx.pack(p, "p")
+
+    def smooth(self, **kw):
+        self.ctx.smooth(self.vx, self.vy, self.p, **kw)
+
+    def v(self):
+        import torch
+        torch.cuda.synchronize()
+        return self.ctx.unpack(self.vx, "vx"), self.ctx.unpack(self.vy, "vy")
+
+
+# ---------------------------------------------------------------------------
+# operator and energy norm
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("nx,ny", [(61, 47), (2, 2), (3, 5), (130, 33)])
+def test_apply_operator_f64(api, nx, ny):
+    prob = rand_problem(nx, ny, 1)
+    vx, vy = inputs.random_velocity(nx, ny, 2)
+    p = inputs.random_pressure(nx, ny, 3)
+    r = Run(api, prob, "f64", (vx, vy), p)
+    ox, oy = r.ctx.apply(r.vx, r.vy, r.p)
+    g = ogrid(prob)
+    mx, my = ora.apply_M(g, vx, vy)
+    gx, gy = ora.apply_G(g, p)
+    want = (mx + gx, my + gy)
+    got = (r.ctx.unpack(ox, "vx"), r.ctx.unpack(oy, "vy"))
+    assert rel(got, want) <= F64_TOL
+    # walls and padding of the output are zero
+    assert np.all(got[0][:, 0] == 0) and np.all(got[0][:, nx] == 0)
+    ox_h, oy_h = ox.cpu().numpy(), oy.cpu().numpy()
+    assert np.all(ox_h[ny, :] == 0) and np.all(ox_h[:, nx + 1:] == 0)
+    assert np.all(oy_h[:, nx:] == 0)
+
+
+@pytest.mark.parametrize("with_p", [False, True])
+def test_energy_norm_f64(api, with_p):
+    nx, ny = 77, 53
+    prob = rand_problem(nx, ny, 4)
+    vx, vy = inputs.random_velocity(nx, ny, 5, 1e-3)
+    p = inputs.random_pressure(nx, ny, 6) if with_p else None
+    r = Run(api, prob, "f64", (vx, vy), p)
+    got = r.ctx.energy(r.vx, r.vy, r.p)
+    want = ora.energy(ogrid(prob), prob.fx, prob.fy, p, vx, vy)
+    for a, b in zip(got, want):
+        assert abs(a - b) <= F64_TOL * abs(b)
+    again = r.ctx.energy(r.vx, r.vy, r.p)
+    assert again == got  # fixed summation order
+
+
+def test_energy_norm_is_one_at_zero_state(api):
+    prob = inputs.sinker_problem(64)
+    r = Run(api, prob, "f64")
+    rv, rp, ff = r.ctx.energy(r.vx, r.vy)
+    assert rp == 0.0 and abs(rv - ff) <= 1e-14 * ff
+
+
+# ---------------------------------------------------------------------------
+# the sinker smoothing case: 64^2, contrast 1e3, 10 sweeps, parity every sweep
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("variant", ["jacobi", "fused", "blocked", "rbgs"])
+def test_sinker_64_every_sweep_f64(api, variant):
+    prob = inputs.sinker_problem(64, eta_in=1e3, eta_out=1.0, rho_in=2.0, rho_out=1.0, radius=0.1)
+    g = ogrid(prob)
+    bx, by = ora.rhs(g, prob.fx, prob.fy, None)
+    r = Run(api, prob, "f64")
+    ref = (g.zeros_vx(), g.zeros_vy())
+    for s in range(10):
+        r.smooth(variant=variant, sweeps=1, tile=(16, 8))
+        if variant == "rbgs":
+            ref = ora.rbgs(g, bx, by, 0.3, 1, *ref)
+        else:
+            ref = ora.jacobi(g, bx, by, 0.3, 1, *ref)
+        assert rel(r.v(), ref) <= F64_TOL, "sweep %d" % (s + 1)
+
+
+def test_sinker_64_ras_every_sweep_f64(api):
+    """8x8 tiles, k = 2, overlap 1, SplitMix64 shifts with seed 1: one call per
+    sweep count 1..10 from the zero state (odd counts end on a partial outer
+    iteration)."""
+    prob = inputs.sinker_problem(64, eta_in=1e3, eta_out=1.0, rho_in=2.0, rho_out=1.0, radius=0.1)
+    g = ogrid(prob)
+    bx, by = ora.rhs(g, prob.fx, prob.fy, None)
+    for n in range(1, 11):
+        r = Run(api, prob, "f64")
+        r.smooth(variant="ras", sweeps=n, tile=(8, 8), k=2, overlap=1, seed=1)
+        ref = ora.ras(g, bx, by, 0.3, n, 8, 8, 2, 1, shift_mode=1, seed=1)
+        assert rel(r.v(), ref) <= F64_TOL, "sweeps %d" % n
+
+
+# ---------------------------------------------------------------------------
+# ragged grids, several tiles, hx != hy, non-zero pressure
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("variant", ["jacobi", "fused", "blocked", "rbgs"])
+def test_ragged_f64(api, variant):
+    nx, ny = 97, 61
+    prob = rand_problem(nx, ny, 7)
+    v0 = inputs.random_velocity(nx, ny, 8, 0.1)
+    p = inputs.random_pressure(nx, ny, 9)
+    g = ogrid(prob)
+    bx, by = ora.rhs(g, prob.fx, prob.fy, p)
+    r = Run(api, prob, "f64", v0, p)
+    r.smooth(variant=variant, sweeps=7, tile=(32, 16), omega=0.25)
+    fn = ora.rbgs if variant == "rbgs" else ora.jacobi
+    ref = fn(g, bx, by, 0.25, 7, *v0)
+    assert rel(r.v(), ref) <= F64_TOL
+
+
+@pytest.mark.parametrize("tile,k,o", [((16, 12), 1, 0), ((16, 12), 3, 0), ((16, 12), 3, 1), ((16, 12), 3, 2),
+                                      ((7, 9), 2, 0), ((7, 9), 4, 3), ((5, 5), 3, 6), ((128, 128), 4, 0)])
+def test_ras_ragged_f64(api, tile, k, o):
+    nx, ny = 100, 75
+    prob = rand_problem(nx, ny, 10)
+    v0 = inputs.random_velocity(nx, ny, 11, 0.1)
+    p = inputs.random_pressure(nx, ny, 12)
+    g = ogrid(prob)
+    bx, by = ora.rhs(g, prob.fx, prob.fy, p)
+    r = Run(api, prob, "f64", v0, p)
+    r.smooth(variant="ras", sweeps=7, tile=tile, k=k, overlap=o, seed=2024)
+    ref = ora.ras(g, bx, by, 0.3, 7, tile[0], tile[1], k, o, shift_mode=1, seed=2024, vx=v0[0], vy=v0[1])
+    assert rel(r.v(), ref) <= F64_TOL
+
+
+def test_ras_explicit_shift_list_f64(api):
+    nx, ny = 90, 70
+    prob = rand_problem(nx, ny, 13)
+    g = ogrid(prob)
+    bx, by = ora.rhs(g, prob.fx, prob.fy, None)
+    shifts = inputs.random_shifts(4, 12, 10, 99)
+    r = Run(api, prob, "f64")
+    r.smooth(variant="ras", sweeps=8, tile=(12, 10), k=2, overlap=0, shifts=shifts)
+    ref = ora.ras(g, bx, by, 0.3, 8, 12, 10, 2, 0, shift_mode=2, shifts=shifts)
+    assert rel(r.v(), ref) <= F64_TOL
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_ras_exact_overlap_is_bitwise_jacobi(api, dtype):
+    """o >= k-1 reproduces global Jacobi; the tiled and the global kernels round
+    identically, so the fields agree bit for bit."""
+    nx, ny = 150, 110
+    prob = inputs.sinker_problem(nx, ny, eta_in=1e4)
+    a = Run(api, prob, dtype)
+    b = Run(api, prob, dtype)
+    a.smooth(variant="ras", sweeps=12, tile=(32, 24), k=4, overlap=3, seed=5)
+    b.smooth(variant="fused", sweeps=12)
+    va, vb = a.v(), b.v()
+    assert np.array_equal(va[0], vb[0]) and np.array_equal(va[1], vb[1])
+
+
+def test_run_twice_bitwise(api):
+    prob = inputs.sinker_problem(200, 150, eta_in=1e4)
+    outs = []
+    for _ in range(2):
+        r = Run(api, prob, "f32")
+        r.smooth(variant="ras", sweeps=9, tile=(32, 32), k=4, overlap=0, seed=3)
+        outs.append(r.v())
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+# ---------------------------------------------------------------------------
+# FP32 against the FP64 oracle
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("variant,kw", [("jacobi", {}), ("fused", {}), ("blocked", {}), ("rbgs", {}),
+                                        ("ras", dict(tile=(32, 32), k=4, overlap=0)),
+                                        ("ras", dict(tile=(32, 32), k=4, overlap=3))])
+def test_fp32_energy_error(api, variant, kw):
+    n = 192
+    prob = inputs.sinker_problem(n, eta_in=1e4)
+    g = ogrid(prob)
+    bx, by = ora.rhs(g, prob.fx, prob.fy, None)
+    r = Run(api, prob, "f32")
+    r.smooth(variant=variant, sweeps=100, seed=7, **kw)
+    if variant == "rbgs":
+        ref = ora.rbgs(g, bx, by, 0.3, 100, g.zeros_vx(), g.zeros_vy())
+    elif variant == "ras":
+        ref = ora.ras(g, bx, by, 0.3, 100, 32, 32, 4, kw["overlap"], shift_mode=1, seed=7)
+    else:
+        ref = ora.jacobi(g, bx, by, 0.3, 100, g.zeros_vx(), g.zeros_vy())
+    err = energy_rel(g, r.v(), ref)
+    print("fp32 %s %s: relative energy error %.3e" % (variant, kw, err))
+    assert err <= FP32_ENERGY_TOL
+
+
+# ---------------------------------------------------------------------------
+# edge cases and errors
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("nx,ny", [(2, 2), (2, 3), (3, 2), (5, 4)])
+def test_tiny_grids_all_variants(api, nx, ny):
+    prob = rand_problem(nx, ny, 20, 1.0, 1.0)
+    v0 = inputs.random_velocity(nx, ny, 21)
+    g = ogrid(prob)
+    bx, by = ora.rhs(g, prob.fx, prob.fy, None)
+    for variant in ("jacobi", "fused", "blocked", "rbgs", "ras"):
+        r = Run(api, prob, "f64", v0)
+        r.smooth(variant=variant, sweeps=3, tile=(2, 2), k=2, overlap=0, seed=1)
+        if variant == "rbgs":
+            ref = ora.rbgs(g, bx, by, 0.3, 3, *v0)
+        elif variant == "ras":
+            ref = ora.ras(g, bx, by, 0.3, 3, 2, 2, 2, 0, shift_mode=1, seed=1, vx=v0[0], vy=v0[1])
+        else:
+            ref = ora.jacobi(g, bx, by, 0.3, 3, *v0)
+        assert rel(r.v(), ref) <= F64_TOL, variant
+
+
+def test_zero_sweeps_is_identity_and_walls_kept(api):
+    nx, ny = 40, 30
+    prob = rand_problem(nx, ny, 22)
+    vx, vy = inputs.random_velocity(nx, ny, 23)
+    vx[:, 0] = 0.5  # Dirichlet wall data is read, never written
+    r = Run(api, prob, "f64", (vx, vy))
+    r.smooth(variant="ras", sweeps=0, k=4)
+    got = r.v()
+    assert np.array_equal(got[0], vx) and np.array_equal(got[1], vy)
+    r.smooth(variant="ras", sweeps=5, tile=(8, 8), k=2, overlap=1, seed=4)
+    got = r.v()
+    assert np.all(got[0][:, 0] == 0.5) and np.all(got[0][:, nx] == 0.0)
+    g = ogrid(prob)
+    bx, by = ora.rhs(g, prob.fx, prob.fy, None)
+    ref = ora.ras(g, bx, by, 0.3, 5, 8, 8, 2, 1, shift_mode=1, seed=4, vx=vx, vy=vy)
+    assert rel(got, ref) <= F64_TOL
+
+
+def test_argument_and_state_errors(api):
+    import torch
+    ctx = api.StokesContext(32, 32, 1.0, 1.0, "f64")
+    vx, vy = ctx.field(), ctx.field()
+    with pytest.raises(api.StokesError) as e:
+        ctx.smooth(vx, vy, variant="fused", sweeps=1)
+    assert e.value.status == api.STOKES_ERR_STATE
+    ctx.set_problem(inputs.sinker_problem(32))
+    with pytest.raises(api.StokesError) as e:
+        ctx.smooth(vx, vy, variant="ras", sweeps=4, tile=(32, 32), k=4, overlap=100)
+    assert e.value.status == api.STOKES_ERR_ARG
+    with pytest.raises(api.StokesError) as e:
+        ctx.smooth(vx, vy, variant="ras", sweeps=4, tile=(8, 8), k=2, shifts=[[9, 0], [0, 0]])
+    assert e.value.status == api.STOKES_ERR_ARG
+    with pytest.raises(api.StokesError) as e:
+        ctx.smooth(vx, vy, variant="ras", sweeps=4, k=0)
+    assert e.value.status == api.STOKES_ERR_ARG
+    torch.cuda.synchronize()
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# full size: 8192^2 layered sinker (contrast 1e6), the benchmark's launch
+# configuration; sampled tiles of one outer iteration against the oracle
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype,tile,k,o", [("f32", (32, 32), 4, 3), ("f64", (32, 32), 4, 3),
+                                            ("f32", (32, 32), 4, 0)])
+def test_full_size_sampled_tiles(api, dtype, tile, k, o):
+    n = 8192
+    prob = inputs.layered_sinker(n, seed=4)
+    v0 = inputs.random_velocity(n, n, 31, 1e-3)
+    si, sj = 13, 27
+    r = Run(api, prob, dtype, v0)
+    r.smooth(variant="ras", sweeps=k, tile=tile, k=k, overlap=o, shifts=[[si, sj]])
+    got = r.v()
+    g = ogrid(prob)
+    bx, by = ora.rhs(g, prob.fx, prob.fy, None)
+    ntx, nty = ora.tile_count(n, tile[0], si), ora.tile_count(n, tile[1], sj)
+    rng = np.random.default_rng(5)
+    tiles = [(0, 0), (ntx - 1, nty - 1), (0, nty - 1), (ntx - 1, 0)]
+    tiles += [(int(a), int(b)) for a, b in zip(rng.integers(0, ntx, 12), rng.integers(0, nty, 12))]
+    ref = ora.ras_tiles(g, bx, by, 0.3, tile[0], tile[1], k, o, si, sj, tiles, v0[0], v0[1], v0[0], v0[1])
+    # compare the unknowns owned by the sampled tiles' cells
+    cuts_x = [0] + [c for c in range(si, n, tile[0]) if c > 0] + [n]
+    cuts_y = [0] + [c for c in range(sj, n, tile[1]) if c > 0] + [n]
+    for (a, b) in tiles:
+        x0, x1, y0, y1 = cuts_x[a], cuts_x[a + 1], cuts_y[b], cuts_y[b + 1]
+        gx = (got[0][y0:y1, x0:x1], got[1][y0:y1, x0:x1])
+        rx = (ref[0][y0:y1, x0:x1], ref[1][y0:y1, x0:x1])
+        if dtype == "f64":
+            assert rel(gx, rx) <= F64_TOL, (a, b)
+        else:
+            assert rel(gx, rx) <= FP32_ENERGY_TOL, (a, b)

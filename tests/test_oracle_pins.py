@@ -493,3 +493,16 @@ def test_vcycle_converges_to_dense_solution(ora, variant):
     dx, dy = ora.dense_solve(g, prob.fx, prob.fy)
     np.testing.assert_allclose(vx, dx, atol=1e-8 * np.abs(dx).max())
     np.testing.assert_allclose(vy, dy, atol=1e-8 * np.abs(dy).max())
+
+
+def test_ras_tile_subset_matches_full_outer_iteration(ora):
+    """The sampled-tile form used at full size equals one full outer iteration
+    on the tiles it is given."""
+    g, bx, by, vx, vy = ras_case(ora)
+    ti, tj, k, o, si, sj = 6, 5, 3, 1, 4, 2
+    full = ora.ras(g, bx, by, 0.3, k, ti, tj, k, o, shift_mode=2, shifts=[si, sj], vx=vx, vy=vy)
+    ntx, nty = ora.tile_count(g.nx, ti, si), ora.tile_count(g.ny, tj, sj)
+    tiles = [(a, b) for a in range(ntx) for b in range(nty)]
+    sub = ora.ras_tiles(g, bx, by, 0.3, ti, tj, k, o, si, sj, tiles, vx, vy, vx, vy)
+    np.testing.assert_array_equal(sub[0], full[0])
+    np.testing.assert_array_equal(sub[1], full[1])
