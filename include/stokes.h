@@ -194,6 +194,27 @@ int stokes_residual_energy_norm(stokes_ctx *ctx, const void *vx, const void *vy,
 int stokes_vcycle(stokes_ctx *ctx, void *vx, void *vy, const void *p, const stokes_mg_params *params,
                   double *final_rel_resid, int *cycles);
 
+/* Context options (stokes_set_option). */
+typedef enum {
+    STOKES_OPT_USE_TMA = 0,          /* 1 (default): the tile smoothers stage windows with TMA bulk
+                                        tensor copies in a persistent kernel when the window fits;
+                                        0: they read windows straight from global memory.  The
+                                        results are identical either way. */
+    STOKES_OPT_WAIT_LIMIT_CYCLES = 1 /* SM clock cycles a device-side wait for a staged window may
+                                        take before the kernel gives up, records STOKES_ERR_TIMEOUT
+                                        and exits (default 2e9, about one second; 0 = one try;
+                                        negative = give up at once, which tests use to exercise the
+                                        timeout path). */
+} stokes_option;
+
+int stokes_set_option(stokes_ctx *ctx, int option, long long value);
+
+/* Synchronise the context's stream and report (then clear) any error a kernel
+ * recorded on the device since the last check: STOKES_ERR_TIMEOUT if a
+ * bounded wait gave up (the smoothing result is then unspecified).
+ * stokes_residual_energy_norm and stokes_vcycle perform the same check. */
+int stokes_synchronize(stokes_ctx *ctx);
+
 /* Kernel classes counted and timed by the profiling hooks below. */
 typedef enum {
     STOKES_K_RAS = 0,    /* RAS / blocked-Jacobi tile kernel (one launch per outer iteration or sweep) */

@@ -30,6 +30,7 @@ STOKES_F32, STOKES_F64 = 0, 1
 STOKES_JACOBI, STOKES_JACOBI_FUSED, STOKES_JACOBI_BLOCKED, STOKES_RBGS, STOKES_RAS = 0, 1, 2, 3, 4
 STOKES_FIELD_VX, STOKES_FIELD_VY, STOKES_FIELD_P, STOKES_FIELD_ETA_C, STOKES_FIELD_ETA_N = 0, 1, 2, 3, 4
 STOKES_SHIFT_NONE, STOKES_SHIFT_SPLITMIX, STOKES_SHIFT_LIST = 0, 1, 2
+STOKES_OPT_USE_TMA, STOKES_OPT_WAIT_LIMIT_CYCLES = 0, 1
 KERNEL_CLASSES = ["ras", "jacobi", "rbgs", "rhs", "energy", "copy", "apply", "mg"]
 
 VARIANTS = {"jacobi": STOKES_JACOBI, "fused": STOKES_JACOBI_FUSED, "blocked": STOKES_JACOBI_BLOCKED,
@@ -70,6 +71,8 @@ _SIGS = {
     "stokes_residual_energy_norm": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(_D)]),
     "stokes_vcycle": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(stokes_mg_params), ctypes.POINTER(_D),
                            ctypes.POINTER(_I)]),
+    "stokes_set_option": (_I, [_VP, _I, ctypes.c_longlong]),
+    "stokes_synchronize": (_I, [_VP]),
     "stokes_profile_reset": (_I, [_VP, _I]),
     "stokes_profile_read": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(_D)]),
@@ -182,6 +185,14 @@ def stokes_vcycle(ctx, vx, vy, p, params):
     return st, fr.value, cy.value
 
 
+def stokes_set_option(ctx, option, value):
+    _check(_lib().stokes_set_option(ctx, option, int(value)), "stokes_set_option")
+
+
+def stokes_synchronize(ctx):
+    _check(_lib().stokes_synchronize(ctx), "stokes_synchronize")
+
+
 def stokes_profile_reset(ctx, enable_timing):
     _check(_lib().stokes_profile_reset(ctx, 1 if enable_timing else 0), "stokes_profile_reset")
 
@@ -281,6 +292,12 @@ class StokesContext:
 
     def energy(self, vx, vy, p=None):
         return stokes_residual_energy_norm(self.ctx, vx, vy, p)
+
+    def set_option(self, option, value):
+        stokes_set_option(self.ctx, option, value)
+
+    def synchronize(self):
+        stokes_synchronize(self.ctx)
 
     def profile_reset(self, timing=False):
         stokes_profile_reset(self.ctx, timing)

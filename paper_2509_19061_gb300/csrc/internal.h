@@ -14,6 +14,7 @@ struct GridDesc {
     int nx, ny, pitch;
     T ihx, ihy;   // 1/hx, 1/hy
     T ihx2, ihy2; // 1/hx^2, 1/hy^2
+    T two_ihx2, two_ihy2; // 2/hx^2, 2/hy^2
     double lap;   // 2/hx^2 + 2/hy^2 (pressure weight of the energy norm)
 };
 
@@ -28,6 +29,8 @@ GridDesc<T> make_grid(int nx, int ny, int pitch, double hx, double hy)
     g.ihy = (T)(1.0 / hy);
     g.ihx2 = (T)(1.0 / (hx * hx));
     g.ihy2 = (T)(1.0 / (hy * hy));
+    g.two_ihx2 = g.ihx2 + g.ihx2;
+    g.two_ihy2 = g.ihy2 + g.ihy2;
     g.lap = 2.0 / (hx * hx) + 2.0 / (hy * hy);
     return g;
 }
@@ -77,12 +80,19 @@ struct TileGrid {
     int ntx, nty; // tiles per direction
 };
 TileGrid make_tiles(int nx, int ny, int ti, int tj, int si, int sj);
+// Per-launch options of the tile kernels.
+struct RasRun {
+    bool allow_tma;        // use the persistent TMA-staged kernel when the window fits
+    int *status;           // device word set to 1 when a bounded wait gives up
+    long long wait_limit;  // SM cycles a wait may take
+};
 // One RAS outer iteration: `ksweeps` local Jacobi sweeps on each tile grown by
 // `overlap`, reading (vx, vy), writing the owned unknowns to (ox, oy).
 template <typename T>
 cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const TileGrid &tg, int ksweeps,
-                       int overlap, const T *vx, const T *vy, T *ox, T *oy, cudaStream_t s);
-size_t ras_smem_bytes(int ti, int tj, int overlap, size_t elem);
+                       int overlap, const T *vx, const T *vy, T *ox, T *oy, const RasRun &run, cudaStream_t s);
+// shared memory a RAS launch needs for this grid, tile and overlap
+size_t ras_smem_bytes(int nx, int ny, int ti, int tj, int overlap, size_t elem);
 int ras_max_smem();
 
 // SplitMix64 (Steele, Lea & Flood 2014): output c (from 0) of the generator

@@ -2,35 +2,51 @@
 // Algorithm 2 of arXiv 2509.19061) and, as its one-sweep case, the spatially
 // blocked fused Jacobi smoother (Sec. 4.2, Sec. 5 (iv)).
 //
-// One CTA per tile of the shifted tiling.  The CTA stages the tile grown by
-// overlap+1 cells (the overlap plus the Dirichlet ring) of every field into
-// shared memory, runs the local Jacobi sweeps there with a shared-memory
-// ping-pong, and writes back only the unknowns of the tile's own cells.  All
-// tiles read the snapshot (vx, vy) and write (ox, oy), so the result does not
-// depend on the order in which tiles run and every unknown has one writer
-// (the in-place benign race of the CPU original is gone).
+// A CTA works on one tile of the shifted tiling at a time: the tile grown by
+// h = overlap + 1 cells (the overlap plus the Dirichlet ring, the "window").
+// It runs the local Jacobi sweeps on chip and writes back only the unknowns of
+// the tile's own cells.  All tiles read the snapshot (vx, vy) and write
+// (ox, oy), so the result does not depend on the order in which tiles run
+// and every unknown has one writer (the in-place benign race of the CPU
+// original is gone).
 //
 // Sweep s of ks only updates the cells within min(overlap, ks - s) of the
 // tile: the owned unknowns after ks sweeps depend on sweep s only through
 // that region (the stencil reaches one cell per sweep), so skipping the rest
 // leaves the result unchanged.
+//
+// Kernels, all with the arithmetic of stencil.cuh and so identical results:
+//  k_ras_tma  persistent: each CTA loops over tiles; the window of the next
+//             tile is staged into shared memory by 2D bulk tensor copies (TMA,
+//             cp.async.bulk.tensor) while the current tile is swept.  Thread
+//             (column, strip) owns R cells of one window column; their
+//             coefficients (2 eta_c/h^2, eta_n, omega/diag, b) and velocities
+//             stay in registers for all sweeps.  Per sweep, phase A computes
+//             each cell's fluxes (Txx, Tyy and the shear at its node), phase B
+//             forms M v from own and neighbour fluxes and updates; shared
+//             memory holds only velocities and fluxes.
+//  k_ras_reg  the same compute with the window read straight from global
+//             memory (used when the staging buffers do not fit).
+//  k_ras      general kernel for windows too large for the register layout:
+//             every field of the window lives in shared memory.
 #include <algorithm>
 
 #include "internal.h"
 #include "stencil.cuh"
+#include "tma.h"
 
 namespace stokes {
 
 namespace {
 
 constexpr int RAS_THREADS = 256;
-constexpr int RAS_PLANES = 8; // vx, vy ping-pong (4), eta_c, eta_n, bx, by
+constexpr int RAS_PLANES = 8;  // vx, vy ping-pong (4), eta_c, eta_n, bx, by
+constexpr int REG_MAX_THREADS = 512;
+constexpr int REG_R = 4;       // cells per thread (strip height)
+constexpr int REG_PLANES = 6;  // vx, vy, Txx, Sy, Tyy (strip ends), Sx (strip ends)
+constexpr int STAGE_FIELDS = 6; // vx, vy, eta_c, eta_n, bx, by
 
-struct TileRange {
-    int x0, x1, y0, y1;
-};
-
-// Tile (bx, by) of the tiling cut at s + m T, clipped to [0, n).
+// Tile b of the tiling of [0, n) cut at s + m T.
 __host__ __device__ __forceinline__ void tile_interval(int n, int T, int s, int b, int &lo, int &hi)
 {
     const int first = s > 0 ? s : T;
@@ -48,31 +64,302 @@ struct RasArgs {
     T *ox, *oy;
     TileGrid tg;
     int ks, overlap;
-    int wxp; // shared-memory row pitch (elements)
-    int plane;
+    int wxm, wym; // largest window extent (cells)
+    int wp;       // shared-memory row pitch of the compute planes (elements)
+    int plane;    // compute-plane size (elements)
+    int bw;       // staging box width (elements); box height is wym
+    int stage;    // staging-plane size (elements, 128-byte multiple)
+    int *status;  // device status word (timeout)
+    long long wait_limit; // cycles a TMA wait may take before giving up
+};
+
+struct TmaMaps {
+    CUtensorMap vx, vy, ec, en, bx, by;
+};
+
+// geometry of one tile's window
+struct Window {
+    int x0, x1, y0, y1; // owned cells
+    int ox0, oy0;       // window origin (global cell index)
+    int WX, WY;         // window extent
 };
 
 template <typename T>
+__device__ __forceinline__ Window window_of(const RasArgs<T> &a, int tile)
+{
+    Window w;
+    tile_interval(a.g.nx, a.tg.ti, a.tg.si, tile % a.tg.ntx, w.x0, w.x1);
+    tile_interval(a.g.ny, a.tg.tj, a.tg.sj, tile / a.tg.ntx, w.y0, w.y1);
+    const int h = a.overlap + 1;
+    w.ox0 = w.x0 - h;
+    w.oy0 = w.y0 - h;
+    w.WX = w.x1 - w.x0 + 2 * h;
+    w.WY = w.y1 - w.y0 + 2 * h;
+    return w;
+}
+
+// per-thread state of the register-resident layout
+template <typename T, int R>
+struct CellRegs {
+    T vx[R], vy[R], ax[R], ay[R], en[R], bx[R], by[R], wx[R], wy[R];
+    unsigned ux, uy; // bit r: cell r is a vx / vy unknown that may be updated
+};
+
+// True if window cell (wx, wy) may ever be updated: not in the outer ring.
+__device__ __forceinline__ bool inner(const Window &w, int wx, int wy)
+{
+    return wx >= 1 && wx < w.WX - 1 && wy >= 1 && wy < w.WY - 1;
+}
+
+// Zero the compute-plane velocities outside the window (border included), so
+// that fluxes of window-edge cells read finite values (they are never used).
+template <typename T>
+__device__ __forceinline__ void zero_outside(const Window &w, int wym, int WP, T *Vx, T *Vy)
+{
+    for (int t = threadIdx.x; t < (wym + 2) * WP; t += blockDim.x) {
+        const int wy = t / WP - 1, wx = t - (wy + 1) * WP - 1;
+        if (wy < 0 || wy >= w.WY || wx < 0 || wx >= w.WX) {
+            Vx[wy * WP + wx] = T(0);
+            Vy[wy * WP + wx] = T(0);
+        }
+    }
+}
+
+// ks local sweeps on the window (registers + shared planes), then write back
+// the unknowns of the tile's own cells.  Ends with a barrier.
+template <typename T, int R>
+__device__ __forceinline__ void sweep_and_store(const RasArgs<T> &a, const Window &w, CellRegs<T, R> &c, int col,
+                                                int strip, bool colok, int WP, T *Vx, T *Vy, T *Fxx, T *Fsy, T *Fyy,
+                                                T *Fsx)
+{
+    const GridDesc<T> &g = a.g;
+    T txx[R], tyy[R], sx[R], sy[R];
+    for (int s = 1; s <= a.ks; ++s) {
+        const int rr = min(a.overlap, a.ks - s);
+        // updated region, window coordinates; fluxes are needed one cell further
+        const int rx0 = max(w.x0 - rr, 0) - w.ox0, rx1 = min(w.x1 + rr, g.nx) - w.ox0;
+        const int ry0 = max(w.y0 - rr, 0) - w.oy0, ry1 = min(w.y1 + rr, g.ny) - w.oy0;
+        const bool cx_in = colok && col >= rx0 && col < rx1;
+        const bool cx_flux = colok && col >= rx0 - 1 && col <= rx1;
+        // ---- phase A: fluxes of the own cells
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int wy = strip * R + r;
+            if (cx_flux && wy >= ry0 - 1 && wy <= ry1) {
+                const int q = wy * WP + col;
+                const T vx_s = r > 0 ? c.vx[r - 1] : Vx[q - WP];
+                const T vy_n = r < R - 1 ? c.vy[r + 1] : Vy[q + WP];
+                txx[r] = flux_n(c.ax[r], Vx[q + 1], c.vx[r]);
+                tyy[r] = flux_n(c.ay[r], vy_n, c.vy[r]);
+                const T sh = shear(g, c.en[r], c.vx[r], vx_s, c.vy[r], Vy[q - 1]);
+                sx[r] = r_mul(sh, g.ihy);
+                sy[r] = r_mul(sh, g.ihx);
+                Fxx[q] = txx[r];
+                Fsy[q] = sy[r];
+                if (r == R - 1) Fyy[q] = tyy[r];
+                if (r == 0) Fsx[q] = sx[r];
+            }
+        }
+        __syncthreads();
+        // ---- phase B: M v from own and neighbour fluxes, damped update
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int wy = strip * R + r;
+            if (cx_in && wy >= ry0 && wy < ry1) {
+                const int q = wy * WP + col;
+                if (c.ux & (1u << r)) {
+                    const T sx_n = r < R - 1 ? sx[r + 1] : Fsx[q + WP];
+                    c.vx[r] = jacobi_update(c.vx[r], c.bx[r], m_x(txx[r], Fxx[q - 1], sx_n, sx[r]), c.wx[r]);
+                    Vx[q] = c.vx[r];
+                }
+                if (c.uy & (1u << r)) {
+                    const T tyy_s = r > 0 ? tyy[r - 1] : Fyy[q - WP];
+                    c.vy[r] = jacobi_update(c.vy[r], c.by[r], m_y(Fsy[q + 1], sy[r], tyy[r], tyy_s), c.wy[r]);
+                    Vy[q] = c.vy[r];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // ---- write back the unknowns of the tile's own cells
+    const int gx = w.ox0 + col;
+    if (colok && gx >= w.x0 && gx < w.x1) {
+        const size_t P = (size_t)g.pitch;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int gy = w.oy0 + strip * R + r;
+            if (gy >= w.y0 && gy < w.y1) {
+                const size_t q = (size_t)gy * P + (size_t)gx;
+                if (c.ux & (1u << r)) a.ox[q] = c.vx[r];
+                if (c.uy & (1u << r)) a.oy[q] = c.vy[r];
+            }
+        }
+    }
+}
+
+// Fill the own cells' registers from per-cell values; `ld(field, wy, wx)`
+// returns the window value of field 0..5 (vx, vy, eta_c, eta_n, bx, by),
+// zero outside the field's extent.
+template <typename T, int R, class LD>
+__device__ __forceinline__ void setup_cells(const RasArgs<T> &a, const Window &w, CellRegs<T, R> &c, int col,
+                                            int strip, bool colok, int WP, T *Vx, T *Vy, LD &&ld)
+{
+    const GridDesc<T> &g = a.g;
+    const int gx = w.ox0 + col;
+    c.ux = 0;
+    c.uy = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int wy = strip * R + r, gy = w.oy0 + wy;
+        T vxv = T(0), vyv = T(0), ec = T(0), env = T(0), bxv = T(0), byv = T(0), wxv = T(0), wyv = T(0);
+        if (colok && wy < w.WY) {
+            vxv = ld(0, wy, col);
+            vyv = ld(1, wy, col);
+            ec = ld(2, wy, col);
+            env = ld(3, wy, col);
+            bxv = ld(4, wy, col);
+            byv = ld(5, wy, col);
+            if (inner(w, col, wy)) {
+                if (gy >= 0 && gy < g.ny && gx >= 1 && gx <= g.nx - 1) {
+                    c.ux |= 1u << r;
+                    wxv = jacobi_weight(a.omega, diag_x(g, ec, ld(2, wy, col - 1), ld(3, wy + 1, col), env));
+                }
+                if (gx >= 0 && gx < g.nx && gy >= 1 && gy <= g.ny - 1) {
+                    c.uy |= 1u << r;
+                    wyv = jacobi_weight(a.omega, diag_y(g, ec, ld(2, wy - 1, col), ld(3, wy, col + 1), env));
+                }
+            }
+            Vx[wy * WP + col] = vxv;
+            Vy[wy * WP + col] = vyv;
+        }
+        c.vx[r] = vxv;
+        c.vy[r] = vyv;
+        c.ax[r] = coef_x(g, ec);
+        c.ay[r] = coef_y(g, ec);
+        c.en[r] = env;
+        c.bx[r] = bxv;
+        c.by[r] = byv;
+        c.wx[r] = wxv;
+        c.wy[r] = wyv;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// persistent TMA-staged kernel
+// ---------------------------------------------------------------------------
+template <typename T, int R>
+__global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_tma(const __grid_constant__ TmaMaps maps, RasArgs<T> a)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    // TMA destinations must be 128-byte aligned shared addresses
+    const uint32_t off = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
+    T *const stage = reinterpret_cast<T *>(smem_raw + off);
+    const int WP = a.wp, PL = a.plane, BW = a.bw, SP = a.stage;
+    T *const base = stage + STAGE_FIELDS * SP + WP + 1;
+    T *const Vx = base, *const Vy = base + PL, *const Fxx = base + 2 * PL, *const Fsy = base + 3 * PL;
+    T *const Fyy = base + 4 * PL, *const Fsx = base + 5 * PL;
+    const CUtensorMap *const mp[STAGE_FIELDS] = {&maps.vx, &maps.vy, &maps.ec, &maps.en, &maps.bx, &maps.by};
+    constexpr int ALIGN = 16 / (int)sizeof(T); // TMA x coordinates are multiples of 16 bytes
+
+    const int ntiles = a.tg.ntx * a.tg.nty;
+    const int col = threadIdx.x % a.wxm, strip = threadIdx.x / a.wxm;
+    const uint32_t box_bytes = (uint32_t)(BW * a.wym * (int)sizeof(T));
+
+    auto issue = [&](int tile) {
+        const Window w = window_of(a, tile);
+        const int xs = w.ox0 & ~(ALIGN - 1);
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&bar, STAGE_FIELDS * box_bytes);
+#pragma unroll
+        for (int f = 0; f < STAGE_FIELDS; ++f) tma_load_2d(stage + f * SP, mp[f], xs, w.oy0, &bar);
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_proxy_async();
+    }
+    __syncthreads();
+    int tile = blockIdx.x;
+    if (threadIdx.x == 0 && tile < ntiles) issue(tile);
+    uint32_t phase = 0;
+    while (tile < ntiles) {
+        const bool ok = mbar_wait_bounded(&bar, phase, a.wait_limit);
+        if (!__syncthreads_and(ok)) {
+            // give up: record the timeout, let the copy in flight land, leave
+            if (threadIdx.x == 0) {
+                atomicExch(a.status, 1);
+                mbar_wait_bounded(&bar, phase, 4000000000LL);
+            }
+            __syncthreads();
+            return;
+        }
+        const Window w = window_of(a, tile);
+        const int dx = w.ox0 - (w.ox0 & ~(ALIGN - 1));
+        const bool colok = col < w.WX && strip * R < w.WY;
+        zero_outside(w, a.wym, WP, Vx, Vy);
+        CellRegs<T, R> c;
+        setup_cells<T, R>(a, w, c, col, strip, colok, WP, Vx, Vy,
+                          [&](int f, int wy, int wx) { return stage[f * SP + wy * BW + wx + dx]; });
+        __syncthreads(); // staging consumed: refill it with the next tile
+        const int next = tile + (int)gridDim.x;
+        if (threadIdx.x == 0 && next < ntiles) issue(next);
+        phase ^= 1u;
+        sweep_and_store<T, R>(a, w, c, col, strip, colok, WP, Vx, Vy, Fxx, Fsy, Fyy, Fsx);
+        tile = next;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// register-resident kernel reading the window from global memory
+// ---------------------------------------------------------------------------
+template <typename T, int R>
+__global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_reg(RasArgs<T> a)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int WP = a.wp, PL = a.plane;
+    T *const base = reinterpret_cast<T *>(smem_raw) + WP + 1;
+    T *const Vx = base, *const Vy = base + PL, *const Fxx = base + 2 * PL, *const Fsy = base + 3 * PL;
+    T *const Fyy = base + 4 * PL, *const Fsx = base + 5 * PL;
+
+    const GridDesc<T> &g = a.g;
+    const Window w = window_of(a, (int)blockIdx.x);
+    const int col = threadIdx.x % a.wxm, strip = threadIdx.x / a.wxm;
+    const bool colok = col < w.WX && strip * R < w.WY;
+    const size_t P = (size_t)g.pitch;
+    const T *const src[STAGE_FIELDS] = {a.vx, a.vy, a.c.eta_c, a.c.eta_n, a.c.bx, a.c.by};
+    zero_outside(w, a.wym, WP, Vx, Vy);
+    CellRegs<T, R> c;
+    setup_cells<T, R>(a, w, c, col, strip, colok, WP, Vx, Vy, [&](int f, int wy, int wx) {
+        const int gy = w.oy0 + wy, gx = w.ox0 + wx;
+        // extents: vx, bx ny x (nx+1); vy, by (ny+1) x nx; eta_c ny x nx; eta_n (ny+1) x (nx+1)
+        const int ey = (f == 0 || f == 2 || f == 4) ? g.ny : g.ny + 1;
+        const int ex = (f == 1 || f == 2 || f == 5) ? g.nx : g.nx + 1;
+        return (gy >= 0 && gy < ey && gx >= 0 && gx < ex) ? src[f][(size_t)gy * P + (size_t)gx] : T(0);
+    });
+    __syncthreads();
+    sweep_and_store<T, R>(a, w, c, col, strip, colok, WP, Vx, Vy, Fxx, Fsy, Fyy, Fsx);
+}
+
+// ---------------------------------------------------------------------------
+// general kernel: every field of the window in shared memory
+// ---------------------------------------------------------------------------
+template <typename T>
 __global__ void __launch_bounds__(RAS_THREADS) k_ras(RasArgs<T> a)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
-    const int plane = a.plane, W = a.wxp;
+    const int plane = a.plane, W = a.wp;
     T *Ax = sm, *Ay = sm + plane, *Bx = sm + 2 * plane, *By = sm + 3 * plane;
     T *Ec = sm + 4 * plane, *En = sm + 5 * plane, *Rx = sm + 6 * plane, *Ry = sm + 7 * plane;
 
     const GridDesc<T> &g = a.g;
     const int nx = g.nx, ny = g.ny;
     const size_t P = (size_t)g.pitch;
-    const int btx = blockIdx.x % a.tg.ntx, bty = blockIdx.x / a.tg.ntx;
-    int x0, x1, y0, y1;
-    tile_interval(nx, a.tg.ti, a.tg.si, btx, x0, x1);
-    tile_interval(ny, a.tg.tj, a.tg.sj, bty, y0, y1);
-    const int h = a.overlap + 1;
-    const int ox0 = x0 - h, oy0 = y0 - h;             // window origin (global cell index)
-    const int wx = x1 - x0 + 2 * h, wy = y1 - y0 + 2 * h; // window extent
+    const Window win = window_of(a, (int)blockIdx.x);
+    const int x0 = win.x0, x1 = win.x1, y0 = win.y0, y1 = win.y1, ox0 = win.ox0, oy0 = win.oy0;
+    const int wx = win.WX, wy = win.WY;
 
-    // ---- stage the window; entries outside each field's extent are zero
     for (int p = threadIdx.x; p < wx * wy; p += RAS_THREADS) {
         const int ly = p / wx, lx = p - ly * wx;
         const int gy = oy0 + ly, gx = ox0 + lx;
@@ -102,7 +389,6 @@ __global__ void __launch_bounds__(RAS_THREADS) k_ras(RasArgs<T> a)
     }
     __syncthreads();
 
-    // ---- ks local sweeps, shrinking to the region that still matters
     T *cx = Ax, *cy = Ay, *nxv = Bx, *nyv = By;
     for (int s = 1; s <= a.ks; ++s) {
         const int r = min(a.overlap, a.ks - s);
@@ -113,16 +399,23 @@ __global__ void __launch_bounds__(RAS_THREADS) k_ras(RasArgs<T> a)
             const int yy = p / w;
             const int gx = cx0 + (p - yy * w), gy = cy0 + yy;
             const int q = (gy - oy0) * W + (gx - ox0);
-            T m, d;
             if (gx >= 1 && gx <= nx - 1) { // vx unknown (gy < ny holds)
-                stencil_x(g, cx[q], cx[q + 1], cx[q - 1], cx[q + W], cx[q - W], cy[q + W], cy[q + W - 1], cy[q],
-                          cy[q - 1], Ec[q], Ec[q - 1], En[q + W], En[q], m, d);
-                nxv[q] = jacobi_update(cx[q], Rx[q], m, d, a.omega);
+                const T vc = cx[q];
+                const T txx_c = flux_n(coef_x(g, Ec[q]), cx[q + 1], vc);
+                const T txx_w = flux_n(coef_x(g, Ec[q - 1]), vc, cx[q - 1]);
+                const T sx_n = r_mul(shear(g, En[q + W], cx[q + W], vc, cy[q + W], cy[q + W - 1]), g.ihy);
+                const T sx_c = r_mul(shear(g, En[q], vc, cx[q - W], cy[q], cy[q - 1]), g.ihy);
+                const T d = diag_x(g, Ec[q], Ec[q - 1], En[q + W], En[q]);
+                nxv[q] = jacobi_update(vc, Rx[q], m_x(txx_c, txx_w, sx_n, sx_c), jacobi_weight(a.omega, d));
             }
             if (gy >= 1 && gy <= ny - 1) { // vy unknown (gx < nx holds)
-                stencil_y(g, cy[q], cy[q + W], cy[q - W], cy[q + 1], cy[q - 1], cx[q + 1], cx[q + 1 - W], cx[q],
-                          cx[q - W], Ec[q], Ec[q - W], En[q + 1], En[q], m, d);
-                nyv[q] = jacobi_update(cy[q], Ry[q], m, d, a.omega);
+                const T vc = cy[q];
+                const T tyy_c = flux_n(coef_y(g, Ec[q]), cy[q + W], vc);
+                const T tyy_s = flux_n(coef_y(g, Ec[q - W]), vc, cy[q - W]);
+                const T sy_e = r_mul(shear(g, En[q + 1], cx[q + 1], cx[q + 1 - W], cy[q + 1], vc), g.ihx);
+                const T sy_c = r_mul(shear(g, En[q], cx[q], cx[q - W], vc, cy[q - 1]), g.ihx);
+                const T d = diag_y(g, Ec[q], Ec[q - W], En[q + 1], En[q]);
+                nyv[q] = jacobi_update(vc, Ry[q], m_y(sy_e, sy_c, tyy_c, tyy_s), jacobi_weight(a.omega, d));
             }
         }
         __syncthreads();
@@ -134,7 +427,6 @@ __global__ void __launch_bounds__(RAS_THREADS) k_ras(RasArgs<T> a)
         nyv = t1;
     }
 
-    // ---- write back the unknowns of the tile's own cells
     const int tw = x1 - x0, npts = tw * (y1 - y0);
     for (int p = threadIdx.x; p < npts; p += RAS_THREADS) {
         const int yy = p / tw;
@@ -144,6 +436,56 @@ __global__ void __launch_bounds__(RAS_THREADS) k_ras(RasArgs<T> a)
         if (gx >= 1 && gx <= nx - 1) a.ox[gq] = cx[q];
         if (gy >= 1 && gy <= ny - 1) a.oy[gq] = cy[q];
     }
+}
+
+// which kernel a configuration uses, and its launch shape
+enum { PLAN_TMA = 0, PLAN_REG = 1, PLAN_SMEM = 2 };
+struct RasPlan {
+    int kind;
+    int wxm, wym, wp, plane, threads, bw, stage;
+    size_t smem;
+};
+
+RasPlan plan_ras(int nx, int ny, int ti, int tj, int overlap, size_t elem, bool allow_tma)
+{
+    RasPlan p;
+    const int h = overlap + 1;
+    // a tile never spans more than min(T, n) cells
+    p.wxm = std::min(ti, nx) + 2 * h;
+    p.wym = std::min(tj, ny) + 2 * h;
+    const int strips = (p.wym + REG_R - 1) / REG_R;
+    const long threads = (long)p.wxm * strips;
+    const size_t maxs = (size_t)ras_max_smem();
+    p.wp = p.wxm + 2;
+    p.plane = p.wp * (p.wym + 2);
+    const int align = 16 / (int)elem;
+    p.bw = (p.wxm + align - 1 + align - 1) / align * align; // room for the alignment shift of x
+    p.stage = (int)((((size_t)p.bw * p.wym * elem + 127) / 128 * 128) / elem);
+    const size_t reg_smem = (size_t)REG_PLANES * (size_t)p.plane * elem;
+    const size_t tma_smem = (size_t)STAGE_FIELDS * (size_t)p.stage * elem + reg_smem + 128;
+    p.threads = (int)((threads + 31) / 32 * 32);
+    if (threads <= REG_MAX_THREADS && allow_tma && p.bw <= 256 && p.wym <= 256 && tma_smem <= maxs) {
+        p.kind = PLAN_TMA;
+        p.smem = tma_smem;
+    } else if (threads <= REG_MAX_THREADS && reg_smem <= maxs) {
+        p.kind = PLAN_REG;
+        p.smem = reg_smem;
+    } else {
+        p.kind = PLAN_SMEM;
+        p.wp = p.wxm;
+        p.plane = p.wxm * p.wym;
+        p.smem = (size_t)RAS_PLANES * (size_t)p.plane * elem;
+        p.threads = RAS_THREADS;
+    }
+    return p;
+}
+
+int sm_count()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v;
 }
 
 } // namespace
@@ -161,10 +503,9 @@ TileGrid make_tiles(int nx, int ny, int ti, int tj, int si, int sj)
     return t;
 }
 
-size_t ras_smem_bytes(int ti, int tj, int overlap, size_t elem)
+size_t ras_smem_bytes(int nx, int ny, int ti, int tj, int overlap, size_t elem)
 {
-    const size_t h = (size_t)overlap + 1;
-    return (size_t)RAS_PLANES * ((size_t)ti + 2 * h) * ((size_t)tj + 2 * h) * elem;
+    return plan_ras(nx, ny, ti, tj, overlap, elem, false).smem;
 }
 
 int ras_max_smem()
@@ -177,8 +518,9 @@ int ras_max_smem()
 
 template <typename T>
 cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const TileGrid &tg, int ksweeps,
-                       int overlap, const T *vx, const T *vy, T *ox, T *oy, cudaStream_t s)
+                       int overlap, const T *vx, const T *vy, T *ox, T *oy, const RasRun &run, cudaStream_t s)
 {
+    const RasPlan p = plan_ras(g.nx, g.ny, tg.ti, tg.tj, overlap, sizeof(T), run.allow_tma);
     RasArgs<T> a;
     a.g = g;
     a.c = c;
@@ -190,21 +532,52 @@ cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const 
     a.tg = tg;
     a.ks = ksweeps;
     a.overlap = overlap;
-    // a tile never spans more than min(T, n) cells
-    const int ex = tg.ti < g.nx ? tg.ti : g.nx, ey = tg.tj < g.ny ? tg.tj : g.ny;
-    a.wxp = ex + 2 * (overlap + 1);
-    a.plane = a.wxp * (ey + 2 * (overlap + 1));
-    const size_t smem = ras_smem_bytes(ex, ey, overlap, sizeof(T));
-    cudaError_t e = cudaFuncSetAttribute(k_ras<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const unsigned nblocks = (unsigned)tg.ntx * (unsigned)tg.nty;
-    k_ras<T><<<nblocks, RAS_THREADS, smem, s>>>(a);
+    a.wxm = p.wxm;
+    a.wym = p.wym;
+    a.wp = p.wp;
+    a.plane = p.plane;
+    a.bw = p.bw;
+    a.stage = p.stage;
+    a.status = run.status;
+    a.wait_limit = run.wait_limit;
+    const int ntiles = tg.ntx * tg.nty;
+    cudaError_t e;
+    if (p.kind == PLAN_TMA) {
+        TmaMaps m;
+        const int es = (int)sizeof(T);
+        const long pb = (long)g.pitch * es;
+        const void *ptrs[STAGE_FIELDS] = {vx, vy, c.eta_c, c.eta_n, c.bx, c.by};
+        const int widths[STAGE_FIELDS] = {g.nx + 1, g.nx, g.nx, g.nx + 1, g.nx + 1, g.nx};
+        const int heights[STAGE_FIELDS] = {g.ny, g.ny + 1, g.ny, g.ny + 1, g.ny, g.ny + 1};
+        CUtensorMap *dst[STAGE_FIELDS] = {&m.vx, &m.vy, &m.ec, &m.en, &m.bx, &m.by};
+        for (int f = 0; f < STAGE_FIELDS; ++f) {
+            e = make_tmap_2d(dst[f], ptrs[f], es, widths[f], heights[f], pb, p.bw, p.wym);
+            if (e != cudaSuccess) return e;
+        }
+        e = cudaFuncSetAttribute(k_ras_tma<T, REG_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ras_tma<T, REG_R>, p.threads, p.smem);
+        if (e != cudaSuccess) return e;
+        const int grid = std::min(ntiles, std::max(per_sm, 1) * sm_count());
+        k_ras_tma<T, REG_R><<<grid, p.threads, p.smem, s>>>(m, a);
+    } else if (p.kind == PLAN_REG) {
+        e = cudaFuncSetAttribute(k_ras_reg<T, REG_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+        if (e != cudaSuccess) return e;
+        k_ras_reg<T, REG_R><<<ntiles, p.threads, p.smem, s>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(k_ras<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+        if (e != cudaSuccess) return e;
+        k_ras<T><<<ntiles, RAS_THREADS, p.smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
 template cudaError_t launch_ras<float>(const GridDesc<float> &, const Coeffs<float> &, float, const TileGrid &, int,
-                                       int, const float *, const float *, float *, float *, cudaStream_t);
+                                       int, const float *, const float *, float *, float *, const RasRun &,
+                                       cudaStream_t);
 template cudaError_t launch_ras<double>(const GridDesc<double> &, const Coeffs<double> &, double, const TileGrid &,
-                                        int, int, const double *, const double *, double *, double *, cudaStream_t);
+                                        int, int, const double *, const double *, double *, double *, const RasRun &,
+                                        cudaStream_t);
 
 } // namespace stokes

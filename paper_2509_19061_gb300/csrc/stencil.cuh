@@ -1,52 +1,102 @@
-// stencil.cuh -- the velocity-operator stencil of arXiv 2509.19061 as pure
-// arithmetic on already-loaded values, shared by the global-memory and the
-// shared-memory kernels so that both round identically.
+// stencil.cuh -- the velocity-operator stencil of arXiv 2509.19061 in flux
+// form, as pure arithmetic shared by every kernel of the library.
 //
 // Eq. (3): sigma'_xx = 2 eta_c dvx/dx and sigma'_yy = 2 eta_c dvy/dy at cell
 // centres, sigma'_xy = eta_n (dvx/dy + dvy/dx) at nodes (eta_n = 0 on
-// boundary nodes); Eq. (1)-(2): (M v)_x = d sigma'_xx/dx + d sigma'_xy/dy,
-// (M v)_y = d sigma'_xy/dx + d sigma'_yy/dy.  d is diag(M), the coefficient of
-// the centre value.
+// boundary nodes); Eq. (1)-(2): (M v)_x = d sigma'_xx/dx + d sigma'_xy/dy and
+// (M v)_y = d sigma'_xy/dx + d sigma'_yy/dy.  With the scaled fluxes
+//   Txx(c) = sigma'_xx(c)/hx = ax(c) (vx(j,i+1) - vx(j,i)),  ax = 2 eta_c / hx^2
+//   Tyy(c) = sigma'_yy(c)/hy = ay(c) (vy(j+1,i) - vy(j,i)),  ay = 2 eta_c / hy^2
+//   Sx(n)  = sigma'_xy(n)/hy,  Sy(n) = sigma'_xy(n)/hx
+// the operator is (M v)_x(j,i) = [Txx(j,i) - Txx(j,i-1)] + [Sx(j+1,i) - Sx(j,i)]
+// and (M v)_y(j,i) = [Sy(j,i+1) - Sy(j,i)] + [Tyy(j,i) - Tyy(j-1,i)].
+//
+// Every operation below is an explicitly rounded intrinsic, so the compiler
+// cannot contract or reorder it: a cell computed by the global-memory
+// kernels and the same cell computed by the shared-memory tile kernel get
+// identical bits.
 #pragma once
 #include "internal.h"
 
 namespace stokes {
 
-// vx unknown at (j, i).  vC/vE/vW/vN/vS: vx at (j,i), (j,i+1), (j,i-1),
-// (j+1,i), (j-1,i); yNE/yNW/ySE/ySW: vy at (j+1,i), (j+1,i-1), (j,i), (j,i-1);
-// ecE/ecW: eta_c at (j,i), (j,i-1); enN/enS: eta_n at (j+1,i), (j,i).
+__device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float r_div(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double r_div(double a, double b) { return __ddiv_rn(a, b); }
+
+// ax = 2 eta_c / hx^2 and ay = 2 eta_c / hy^2
 template <typename T>
-__device__ __forceinline__ void stencil_x(const GridDesc<T> &g, T vC, T vE, T vW, T vN, T vS, T yNE, T yNW, T ySE,
-                                          T ySW, T ecE, T ecW, T enN, T enS, T &m, T &d)
+__device__ __forceinline__ T coef_x(const GridDesc<T> &g, T ec)
 {
-    const T txxE = T(2) * ecE * (vE - vC) * g.ihx;
-    const T txxW = T(2) * ecW * (vC - vW) * g.ihx;
-    const T sN = enN * ((vN - vC) * g.ihy + (yNE - yNW) * g.ihx);
-    const T sS = enS * ((vC - vS) * g.ihy + (ySE - ySW) * g.ihx);
-    m = (txxE - txxW) * g.ihx + (sN - sS) * g.ihy;
-    d = -T(2) * (ecE + ecW) * g.ihx2 - (enN + enS) * g.ihy2;
+    return r_mul(r_add(ec, ec), g.ihx2);
+}
+template <typename T>
+__device__ __forceinline__ T coef_y(const GridDesc<T> &g, T ec)
+{
+    return r_mul(r_add(ec, ec), g.ihy2);
 }
 
-// vy unknown at (j, i).  vC/vN/vS/vE/vW: vy at (j,i), (j+1,i), (j-1,i),
-// (j,i+1), (j,i-1); xNE/xSE/xNW/xSW: vx at (j,i+1), (j-1,i+1), (j,i), (j-1,i);
-// ecN/ecS: eta_c at (j,i), (j-1,i); enE/enW: eta_n at (j,i+1), (j,i).
+// Txx = ax (vx_E - vx_C), Tyy = ay (vy_N - vy_C)
 template <typename T>
-__device__ __forceinline__ void stencil_y(const GridDesc<T> &g, T vC, T vN, T vS, T vE, T vW, T xNE, T xSE, T xNW,
-                                          T xSW, T ecN, T ecS, T enE, T enW, T &m, T &d)
+__device__ __forceinline__ T flux_n(T a, T v_next, T v_c)
 {
-    const T tyyN = T(2) * ecN * (vN - vC) * g.ihy;
-    const T tyyS = T(2) * ecS * (vC - vS) * g.ihy;
-    const T sE = enE * ((xNE - xSE) * g.ihy + (vE - vC) * g.ihx);
-    const T sW = enW * ((xNW - xSW) * g.ihy + (vC - vW) * g.ihx);
-    m = (sE - sW) * g.ihx + (tyyN - tyyS) * g.ihy;
-    d = -T(2) * (ecN + ecS) * g.ihy2 - (enE + enW) * g.ihx2;
+    return r_mul(a, r_sub(v_next, v_c));
 }
 
-// damped Jacobi update v + omega (b - M v) / diag(M)
+// sigma'_xy at node (i, j) from vx(j,i), vx(j-1,i), vy(j,i), vy(j,i-1)
 template <typename T>
-__device__ __forceinline__ T jacobi_update(T vc, T b, T m, T d, T omega)
+__device__ __forceinline__ T shear(const GridDesc<T> &g, T en, T vx_c, T vx_s, T vy_c, T vy_w)
 {
-    return vc + omega * (b - m) / d;
+    return r_mul(en, r_fma(r_sub(vx_c, vx_s), g.ihy, r_mul(r_sub(vy_c, vy_w), g.ihx)));
+}
+
+// (M v)_x from Txx(j,i), Txx(j,i-1), Sx(j+1,i), Sx(j,i)
+template <typename T>
+__device__ __forceinline__ T m_x(T txx_c, T txx_w, T sx_n, T sx_c)
+{
+    return r_add(r_sub(txx_c, txx_w), r_sub(sx_n, sx_c));
+}
+
+// (M v)_y from Sy(j,i+1), Sy(j,i), Tyy(j,i), Tyy(j-1,i)
+template <typename T>
+__device__ __forceinline__ T m_y(T sy_e, T sy_c, T tyy_c, T tyy_s)
+{
+    return r_add(r_sub(sy_e, sy_c), r_sub(tyy_c, tyy_s));
+}
+
+// diag(M) at vx (j,i): -(2 (eta_c(j,i) + eta_c(j,i-1)) / hx^2 + (eta_n(j+1,i) + eta_n(j,i)) / hy^2)
+template <typename T>
+__device__ __forceinline__ T diag_x(const GridDesc<T> &g, T ec_c, T ec_w, T en_n, T en_s)
+{
+    return -r_fma(r_add(ec_c, ec_w), g.two_ihx2, r_mul(r_add(en_n, en_s), g.ihy2));
+}
+
+// diag(M) at vy (j,i): -(2 (eta_c(j,i) + eta_c(j-1,i)) / hy^2 + (eta_n(j,i+1) + eta_n(j,i)) / hx^2)
+template <typename T>
+__device__ __forceinline__ T diag_y(const GridDesc<T> &g, T ec_c, T ec_s, T en_e, T en_w)
+{
+    return -r_fma(r_add(ec_c, ec_s), g.two_ihy2, r_mul(r_add(en_e, en_w), g.ihx2));
+}
+
+// damped-Jacobi weight omega / diag(M)
+template <typename T>
+__device__ __forceinline__ T jacobi_weight(T omega, T d)
+{
+    return r_mul(omega, r_div(T(1), d));
+}
+
+// v + (b - M v) omega / diag(M)
+template <typename T>
+__device__ __forceinline__ T jacobi_update(T v, T b, T m, T w)
+{
+    return r_fma(r_sub(b, m), w, v);
 }
 
 } // namespace stokes

@@ -30,8 +30,16 @@ __device__ __forceinline__ void op_x(const GridDesc<T> &g, const T *__restrict__
     const size_t P = (size_t)g.pitch;
     const size_t q = (size_t)j * P + (size_t)i;
     vc = vx[q];
-    stencil_x(g, vc, vx[q + 1], vx[q - 1], j + 1 < g.ny ? vx[q + P] : T(0), j > 0 ? vx[q - P] : T(0), vy[q + P],
-              vy[q + P - 1], vy[q], vy[q - 1], eta_c[q], eta_c[q - 1], eta_n[q + P], eta_n[q], m, d);
+    const T vE = vx[q + 1], vW = vx[q - 1];
+    const T vN = j + 1 < g.ny ? vx[q + P] : T(0);
+    const T vS = j > 0 ? vx[q - P] : T(0);
+    const T ecC = eta_c[q], ecW = eta_c[q - 1], enN = eta_n[q + P], enS = eta_n[q];
+    const T txx_c = flux_n(coef_x(g, ecC), vE, vc);
+    const T txx_w = flux_n(coef_x(g, ecW), vc, vW);
+    const T sx_n = r_mul(shear(g, enN, vN, vc, vy[q + P], vy[q + P - 1]), g.ihy);
+    const T sx_c = r_mul(shear(g, enS, vc, vS, vy[q], vy[q - 1]), g.ihy);
+    m = m_x(txx_c, txx_w, sx_n, sx_c);
+    d = diag_x(g, ecC, ecW, enN, enS);
 }
 
 // (M v)_y and diag(M)_y at vy unknown (j, i), 1 <= j <= ny-1, 0 <= i < nx.
@@ -43,8 +51,16 @@ __device__ __forceinline__ void op_y(const GridDesc<T> &g, const T *__restrict__
     const size_t P = (size_t)g.pitch;
     const size_t q = (size_t)j * P + (size_t)i;
     vc = vy[q];
-    stencil_y(g, vc, vy[q + P], vy[q - P], i + 1 < g.nx ? vy[q + 1] : T(0), i > 0 ? vy[q - 1] : T(0), vx[q + 1],
-              vx[q + 1 - P], vx[q], vx[q - P], eta_c[q], eta_c[q - P], eta_n[q + 1], eta_n[q], m, d);
+    const T vN = vy[q + P], vS = vy[q - P];
+    const T vE = i + 1 < g.nx ? vy[q + 1] : T(0);
+    const T vW = i > 0 ? vy[q - 1] : T(0);
+    const T ecC = eta_c[q], ecS = eta_c[q - P], enE = eta_n[q + 1], enW = eta_n[q];
+    const T tyy_c = flux_n(coef_y(g, ecC), vN, vc);
+    const T tyy_s = flux_n(coef_y(g, ecS), vc, vS);
+    const T sy_e = r_mul(shear(g, enE, vx[q + 1], vx[q + 1 - P], vE, vc), g.ihx);
+    const T sy_c = r_mul(shear(g, enW, vx[q], vx[q - P], vc, vW), g.ihx);
+    m = m_y(sy_e, sy_c, tyy_c, tyy_s);
+    d = diag_y(g, ecC, ecS, enE, enW);
 }
 
 template <typename T>
@@ -137,7 +153,7 @@ __global__ void k_jacobi(GridDesc<T> g, Coeffs<T> c, T omega, const T *__restric
     if (DO_X) {
         if (vx_unknown(g, j, i)) {
             op_x(g, c.eta_c, c.eta_n, vx, vy, j, i, m, d, vc);
-            ox[q] = jacobi_update(vc, c.bx[q], m, d, omega);
+            ox[q] = jacobi_update(vc, c.bx[q], m, jacobi_weight(omega, d));
         } else if (vx_wall(g, j, i)) {
             ox[q] = vx[q];
         }
@@ -145,7 +161,7 @@ __global__ void k_jacobi(GridDesc<T> g, Coeffs<T> c, T omega, const T *__restric
     if (DO_Y) {
         if (vy_unknown(g, j, i)) {
             op_y(g, c.eta_c, c.eta_n, vx, vy, j, i, m, d, vc);
-            oy[q] = jacobi_update(vc, c.by[q], m, d, omega);
+            oy[q] = jacobi_update(vc, c.by[q], m, jacobi_weight(omega, d));
         } else if (vy_wall(g, j, i)) {
             oy[q] = vy[q];
         }
@@ -164,11 +180,11 @@ __global__ void k_rbgs(GridDesc<T> g, Coeffs<T> c, T omega, int colour, T *__res
     if (X) {
         if (!vx_unknown(g, j, i)) return;
         op_x(g, c.eta_c, c.eta_n, vx, vy, j, i, m, d, vc);
-        vx[q] = jacobi_update(vc, c.bx[q], m, d, omega);
+        vx[q] = jacobi_update(vc, c.bx[q], m, jacobi_weight(omega, d));
     } else {
         if (!vy_unknown(g, j, i)) return;
         op_y(g, c.eta_c, c.eta_n, vx, vy, j, i, m, d, vc);
-        vy[q] = jacobi_update(vc, c.by[q], m, d, omega);
+        vy[q] = jacobi_update(vc, c.by[q], m, jacobi_weight(omega, d));
     }
 }
 
@@ -226,13 +242,13 @@ __global__ void __launch_bounds__(EN_THREADS) k_energy(GridDesc<T> g, const T *_
         T m, d, vc;
         if (vx_unknown(g, j, i)) {
             op_x(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
-            const double r = (double)(bx[q] - m), wgt = -(double)d, f = (double)fx[q];
+            const double r = (double)r_sub(bx[q], m), wgt = -(double)d, f = (double)fx[q];
             s_rv += r * r / wgt;
             s_ff += f * f / wgt;
         }
         if (vy_unknown(g, j, i)) {
             op_y(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
-            const double r = (double)(by[q] - m), wgt = -(double)d, f = (double)fy[q];
+            const double r = (double)r_sub(by[q], m), wgt = -(double)d, f = (double)fy[q];
             s_rv += r * r / wgt;
             s_ff += f * f / wgt;
         }

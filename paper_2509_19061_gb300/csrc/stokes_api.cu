@@ -65,6 +65,10 @@ struct stokes_ctx {
     void *bx = nullptr, *by = nullptr, *sx = nullptr, *sy = nullptr;
     double *partials = nullptr, *dsum = nullptr, *hsum = nullptr;
     bool have_eta = false, have_f = false;
+    int *dstatus = nullptr;              // device status word of the bounded waits
+    int *hstatus = nullptr;              // pinned host copy
+    bool use_tma = true;                 // STOKES_OPT_USE_TMA
+    long long wait_limit = 2000000000LL; // STOKES_OPT_WAIT_LIMIT_CYCLES (about 1 s)
     MgHierarchy *mg = nullptr;
     Profiler prof;
 };
@@ -162,12 +166,33 @@ int check_smooth_params(const stokes_ctx *c, const stokes_smooth_params *p, int 
         const int k = p->variant == STOKES_RAS ? p->k : 1;
         const int o = p->variant == STOKES_RAS ? p->overlap : 0;
         if (k < 1 || o < 0 || o > 4096) return STOKES_ERR_ARG;
-        const int ex = *ti < c->nx ? *ti : c->nx, ey = *tj < c->ny ? *tj : c->ny;
-        if (ras_smem_bytes(ex, ey, o, c->esize) > (size_t)ras_max_smem()) return STOKES_ERR_ARG;
+        if (ras_smem_bytes(c->nx, c->ny, *ti, *tj, o, c->esize) > (size_t)ras_max_smem()) return STOKES_ERR_ARG;
         if (p->variant == STOKES_RAS) {
             if (p->shift_mode < STOKES_SHIFT_NONE || p->shift_mode > STOKES_SHIFT_LIST) return STOKES_ERR_ARG;
             if (p->shift_mode == STOKES_SHIFT_LIST && p->sweeps > 0 && !p->shifts) return STOKES_ERR_ARG;
         }
+    }
+    return STOKES_OK;
+}
+
+RasRun run_opts(const stokes_ctx *c)
+{
+    RasRun r;
+    r.allow_tma = c->use_tma;
+    r.status = c->dstatus;
+    r.wait_limit = c->wait_limit;
+    return r;
+}
+
+// Reads (and clears) the device status word; synchronises the stream.
+int device_status(stokes_ctx *c)
+{
+    CK(cudaMemcpyAsync(c->hstatus, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (*c->hstatus != 0) {
+        CK(cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        return STOKES_ERR_TIMEOUT;
     }
     return STOKES_OK;
 }
@@ -203,7 +228,7 @@ int smooth_impl(stokes_ctx *c, T *vx, T *vy, const stokes_smooth_params *p, int 
                 if (si < 0 || si >= ti || sj < 0 || sj >= tj) return STOKES_ERR_ARG;
             }
             const TileGrid tg = make_tiles(c->nx, c->ny, ti, tj, si, sj);
-            RUN(STOKES_K_RAS, 1, launch_ras<T>(g, k, omega, tg, ks, p->overlap, ax, ay, bxp, byp, s));
+            RUN(STOKES_K_RAS, 1, launch_ras<T>(g, k, omega, tg, ks, p->overlap, ax, ay, bxp, byp, run_opts(c), s));
             T *t0 = ax; ax = bxp; bxp = t0;
             T *t1 = ay; ay = byp; byp = t1;
             ++passes;
@@ -212,7 +237,7 @@ int smooth_impl(stokes_ctx *c, T *vx, T *vy, const stokes_smooth_params *p, int 
         for (int it = 0; it < p->sweeps; ++it) {
             if (p->variant == STOKES_JACOBI_BLOCKED) {
                 const TileGrid tg = make_tiles(c->nx, c->ny, ti, tj, 0, 0);
-                RUN(STOKES_K_RAS, 1, launch_ras<T>(g, k, omega, tg, 1, 0, ax, ay, bxp, byp, s));
+                RUN(STOKES_K_RAS, 1, launch_ras<T>(g, k, omega, tg, 1, 0, ax, ay, bxp, byp, run_opts(c), s));
             } else {
                 RUN(STOKES_K_JACOBI, p->variant == STOKES_JACOBI_FUSED ? 1 : 2,
                     launch_jacobi<T>(g, k, omega, ax, ay, bxp, byp, p->variant == STOKES_JACOBI_FUSED, s));
@@ -235,9 +260,9 @@ int energy_impl(stokes_ctx *c, const T *vx, const T *vy, const T *p, double out[
         launch_energy<T>(g, (const T *)c->eta_c, (const T *)c->eta_n, (const T *)c->fx, (const T *)c->fy,
                          (const T *)c->bx, (const T *)c->by, vx, vy, c->partials, c->dsum, c->stream));
     CK(cudaMemcpyAsync(c->hsum, c->dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    const int st = device_status(c);
     std::memcpy(out, c->hsum, 3 * sizeof(double));
-    return STOKES_OK;
+    return st;
 }
 
 } // namespace
@@ -291,6 +316,9 @@ int stokes_create(int nx, int ny, double lx, double ly, int dtype, void *cuda_st
         cudaError_t e = cudaMalloc(&c->partials, (size_t)energy_partials() * 3 * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&c->dsum, 3 * sizeof(double));
         if (e == cudaSuccess) e = cudaMallocHost(&c->hsum, 3 * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&c->dstatus, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream);
+        if (e == cudaSuccess) e = cudaMallocHost(&c->hstatus, sizeof(int));
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "stokes_create");
     }
@@ -310,10 +338,11 @@ int stokes_destroy(stokes_ctx *c)
     mg_destroy(c->mg);
     prof_flush(c);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
-    void *fields[] = {c->eta_c, c->eta_n, c->fx, c->fy, c->bx, c->by, c->sx, c->sy, c->partials, c->dsum};
+    void *fields[] = {c->eta_c, c->eta_n, c->fx, c->fy, c->bx, c->by, c->sx, c->sy, c->partials, c->dsum, c->dstatus};
     for (void *f : fields)
         if (f) cudaFree(f);
     if (c->hsum) cudaFreeHost(c->hsum);
+    if (c->hstatus) cudaFreeHost(c->hstatus);
     delete c;
     return STOKES_OK;
 }
@@ -406,6 +435,22 @@ int stokes_vcycle(stokes_ctx *c, void *vx, void *vy, const void *p, const stokes
     if (!c || !vx || !vy || !params) return STOKES_ERR_ARG;
     if (!c->have_eta || !c->have_f) return STOKES_ERR_STATE;
     return STOKES_ERR_STATE; // multigrid solve: not yet available
+}
+
+int stokes_set_option(stokes_ctx *c, int option, long long value)
+{
+    if (!c) return STOKES_ERR_ARG;
+    switch (option) {
+    case STOKES_OPT_USE_TMA: c->use_tma = value != 0; return STOKES_OK;
+    case STOKES_OPT_WAIT_LIMIT_CYCLES: c->wait_limit = value; return STOKES_OK;
+    default: return STOKES_ERR_ARG;
+    }
+}
+
+int stokes_synchronize(stokes_ctx *c)
+{
+    if (!c) return STOKES_ERR_ARG;
+    return device_status(c);
 }
 
 int stokes_profile_reset(stokes_ctx *c, int enable_timing)

@@ -171,7 +171,7 @@ def test_ragged_f64(api, variant):
 
 
 @pytest.mark.parametrize("tile,k,o", [((16, 12), 1, 0), ((16, 12), 3, 0), ((16, 12), 3, 1), ((16, 12), 3, 2),
-                                      ((7, 9), 2, 0), ((7, 9), 4, 3), ((5, 5), 3, 6), ((128, 128), 4, 0)])
+                                      ((7, 9), 2, 0), ((7, 9), 4, 3), ((5, 5), 3, 6), ((128, 20), 4, 0), ((60, 40), 2, 1)])
 def test_ras_ragged_f64(api, tile, k, o):
     nx, ny = 100, 75
     prob = rand_problem(nx, ny, 10)
@@ -337,3 +337,51 @@ def test_full_size_sampled_tiles(api, dtype, tile, k, o):
             assert rel(gx, rx) <= F64_TOL, (a, b)
         else:
             assert rel(gx, rx) <= FP32_ENERGY_TOL, (a, b)
+
+
+# ---------------------------------------------------------------------------
+# the three tile-kernel paths give the same bits; failure detection
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("tile,k,o", [((32, 32), 4, 3), ((32, 32), 4, 0), ((24, 16), 3, 1), ((40, 40), 1, 0),
+                                      ((13, 7), 2, 5)])
+def test_tma_and_global_staging_agree(api, dtype, tile, k, o):
+    nx, ny = 301, 207
+    prob = rand_problem(nx, ny, 40)
+    v0 = inputs.random_velocity(nx, ny, 41, 0.1)
+    outs = []
+    for use_tma in (1, 0):
+        r = Run(api, prob, dtype, v0)
+        r.ctx.set_option(api.STOKES_OPT_USE_TMA, use_tma)
+        r.smooth(variant="ras", sweeps=9, tile=tile, k=k, overlap=o, seed=77)
+        outs.append(r.v())
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    if dtype == "f64":
+        g = ogrid(prob)
+        bx, by = ora.rhs(g, prob.fx, prob.fy, None)
+        ref = ora.ras(g, bx, by, 0.3, 9, tile[0], tile[1], k, o, shift_mode=1, seed=77, vx=v0[0], vy=v0[1])
+        assert rel(outs[0], ref) <= F64_TOL
+
+
+def test_staging_wait_timeout_is_reported_and_context_recovers(api):
+    """A staged-window wait that gives up records STOKES_ERR_TIMEOUT on the
+    device (after letting its copy land); the host reads it at the next check
+    and the context keeps working."""
+    nx, ny = 128, 96
+    prob = rand_problem(nx, ny, 42)
+    g = ogrid(prob)
+    bx, by = ora.rhs(g, prob.fx, prob.fy, None)
+    r = Run(api, prob, "f64")
+    r.ctx.set_option(api.STOKES_OPT_WAIT_LIMIT_CYCLES, -1)
+    r.smooth(variant="ras", sweeps=4, tile=(32, 32), k=4, overlap=3, seed=1)
+    with pytest.raises(api.StokesError) as e:
+        r.ctx.synchronize()
+    assert e.value.status == api.STOKES_ERR_TIMEOUT
+    r.ctx.synchronize()  # cleared
+    r.ctx.set_option(api.STOKES_OPT_WAIT_LIMIT_CYCLES, 2_000_000_000)
+    r2 = Run(api, prob, "f64")
+    r2.smooth(variant="ras", sweeps=4, tile=(32, 32), k=4, overlap=3, seed=1)
+    ref = ora.ras(g, bx, by, 0.3, 4, 32, 32, 4, 3, shift_mode=1, seed=1)
+    assert rel(r2.v(), ref) <= F64_TOL
+    r.smooth(variant="ras", sweeps=4, tile=(32, 32), k=4, overlap=3, seed=1)
+    r.ctx.synchronize()
