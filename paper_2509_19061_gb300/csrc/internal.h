@@ -42,11 +42,16 @@ struct Coeffs {
     const T *eta_c;
     const T *eta_n; // boundary nodes hold 0
     const T *bx, *by;
+    const T *inv_dx, *inv_dy; // 1 / diag(M) at the unknowns (zero elsewhere), or NULL
 };
 
 // ---- stencil kernels (stencil_kernels.cu) --------------------------------
 template <typename T>
 cudaError_t launch_copy_eta(const GridDesc<T> &g, const T *eta_c_in, const T *eta_n_in, T *eta_c, T *eta_n,
+                            cudaStream_t s);
+// inv_dx, inv_dy = 1 / diag(M) at the unknowns, zero elsewhere
+template <typename T>
+cudaError_t launch_inv_diag(const GridDesc<T> &g, const T *eta_c, const T *eta_n, T *inv_dx, T *inv_dy,
                             cudaStream_t s);
 template <typename T>
 cudaError_t launch_rhs(const GridDesc<T> &g, const T *fx, const T *fy, const T *p, T *bx, T *by, cudaStream_t s);

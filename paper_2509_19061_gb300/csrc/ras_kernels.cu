@@ -42,9 +42,31 @@ namespace {
 constexpr int RAS_THREADS = 256;
 constexpr int RAS_PLANES = 8;  // vx, vy ping-pong (4), eta_c, eta_n, bx, by
 constexpr int REG_MAX_THREADS = 512;
-constexpr int REG_R = 4;       // cells per thread (strip height)
+constexpr int SMALL_THREADS = 320;
 constexpr int REG_PLANES = 6;  // vx, vy, Txx, Sy, Tyy (strip ends), Sx (strip ends)
-constexpr int STAGE_FIELDS = 6; // vx, vy, eta_c, eta_n, bx, by
+
+// Per-precision shape of the register-resident kernels.
+//  R     cells per thread (strip height)
+//  TRAP  sweep s updates only the region that still matters (per-cell tests);
+//        otherwise every cell of the window is swept (no tests, ring and
+//        non-unknown cells have weight 0), which costs more arithmetic but
+//        far fewer instructions: FP32 is issue-bound, FP64 is FP64-pipe-bound
+//  INVD  1/diag(M) is staged from the library's precomputed arrays instead
+//        of being computed per tile
+template <typename T>
+struct KCfg;
+template <>
+struct KCfg<float> {
+    static constexpr int R = 5;
+    static constexpr bool TRAP = false;
+    static constexpr bool INVD = false;
+};
+template <>
+struct KCfg<double> {
+    static constexpr int R = 4;
+    static constexpr bool TRAP = true;
+    static constexpr bool INVD = true;
+};
 
 // Tile b of the tiling of [0, n) cut at s + m T.
 __host__ __device__ __forceinline__ void tile_interval(int n, int T, int s, int b, int &lo, int &hi)
@@ -65,6 +87,7 @@ struct RasArgs {
     TileGrid tg;
     int ks, overlap;
     int wxm, wym; // largest window extent (cells)
+    int strips;   // strips per column (register kernels)
     int wp;       // shared-memory row pitch of the compute planes (elements)
     int plane;    // compute-plane size (elements)
     int bw;       // staging box width (elements); box height is wym
@@ -73,8 +96,9 @@ struct RasArgs {
     long long wait_limit; // cycles a TMA wait may take before giving up
 };
 
+constexpr int MAX_STAGE_FIELDS = 8;
 struct TmaMaps {
-    CUtensorMap vx, vy, ec, en, bx, by;
+    CUtensorMap m[MAX_STAGE_FIELDS]; // vx, vy, eta_c, eta_n, bx, by[, 1/dx, 1/dy]
 };
 
 // geometry of one tile's window
@@ -102,109 +126,61 @@ __device__ __forceinline__ Window window_of(const RasArgs<T> &a, int tile)
 template <typename T, int R>
 struct CellRegs {
     T vx[R], vy[R], ax[R], ay[R], en[R], bx[R], by[R], wx[R], wy[R];
-    unsigned ux, uy; // bit r: cell r is a vx / vy unknown that may be updated
+    unsigned ux, uy; // bit r: cell r is a vx / vy unknown inside the ring
 };
 
-// True if window cell (wx, wy) may ever be updated: not in the outer ring.
-__device__ __forceinline__ bool inner(const Window &w, int wx, int wy)
-{
-    return wx >= 1 && wx < w.WX - 1 && wy >= 1 && wy < w.WY - 1;
-}
-
-// Zero the compute-plane velocities outside the window (border included), so
-// that fluxes of window-edge cells read finite values (they are never used).
+// Compute planes: Vx, Vy, Fxx, Fsy, Fyy, Fsx, each (rows + 2) x WP with a
+// one-cell border; index (wy, wx), -1 <= wy <= rows, -1 <= wx <= wp - 2.
 template <typename T>
-__device__ __forceinline__ void zero_outside(const Window &w, int wym, int WP, T *Vx, T *Vy)
+struct Planes {
+    T *Vx, *Vy, *Fxx, *Fsy, *Fyy, *Fsx;
+    __device__ Planes(T *raw, int WP, int PL)
+    {
+        T *b = raw + WP + 1;
+        Vx = b;
+        Vy = b + PL;
+        Fxx = b + 2 * PL;
+        Fsy = b + 3 * PL;
+        Fyy = b + 4 * PL;
+        Fsx = b + 5 * PL;
+    }
+};
+
+// Zero the one-cell border of every compute plane (it is never written
+// afterwards): the fluxes of window-edge cells then read finite values.
+template <typename T>
+__device__ __forceinline__ void zero_borders(const RasArgs<T> &a, const Planes<T> &pl)
 {
-    for (int t = threadIdx.x; t < (wym + 2) * WP; t += blockDim.x) {
-        const int wy = t / WP - 1, wx = t - (wy + 1) * WP - 1;
-        if (wy < 0 || wy >= w.WY || wx < 0 || wx >= w.WX) {
-            Vx[wy * WP + wx] = T(0);
-            Vy[wy * WP + wx] = T(0);
+    const int rows = a.strips * KCfg<T>::R, WP = a.wp, cols = a.wxm;
+    const int n = 2 * (cols + 2) + 2 * rows;
+    T *const ps[REG_PLANES] = {pl.Vx, pl.Vy, pl.Fxx, pl.Fsy, pl.Fyy, pl.Fsx};
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        int wy, wx;
+        if (t < cols + 2) {
+            wy = -1;
+            wx = t - 1;
+        } else if (t < 2 * (cols + 2)) {
+            wy = rows;
+            wx = t - (cols + 2) - 1;
+        } else {
+            wy = (t - 2 * (cols + 2)) >> 1;
+            wx = (t & 1) ? cols : -1;
         }
+#pragma unroll
+        for (int f = 0; f < REG_PLANES; ++f) ps[f][wy * WP + wx] = T(0);
     }
 }
 
-// ks local sweeps on the window (registers + shared planes), then write back
-// the unknowns of the tile's own cells.  Ends with a barrier.
-template <typename T, int R>
-__device__ __forceinline__ void sweep_and_store(const RasArgs<T> &a, const Window &w, CellRegs<T, R> &c, int col,
-                                                int strip, bool colok, int WP, T *Vx, T *Vy, T *Fxx, T *Fsy, T *Fyy,
-                                                T *Fsx)
-{
-    const GridDesc<T> &g = a.g;
-    T txx[R], tyy[R], sx[R], sy[R];
-    for (int s = 1; s <= a.ks; ++s) {
-        const int rr = min(a.overlap, a.ks - s);
-        // updated region, window coordinates; fluxes are needed one cell further
-        const int rx0 = max(w.x0 - rr, 0) - w.ox0, rx1 = min(w.x1 + rr, g.nx) - w.ox0;
-        const int ry0 = max(w.y0 - rr, 0) - w.oy0, ry1 = min(w.y1 + rr, g.ny) - w.oy0;
-        const bool cx_in = colok && col >= rx0 && col < rx1;
-        const bool cx_flux = colok && col >= rx0 - 1 && col <= rx1;
-        // ---- phase A: fluxes of the own cells
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int wy = strip * R + r;
-            if (cx_flux && wy >= ry0 - 1 && wy <= ry1) {
-                const int q = wy * WP + col;
-                const T vx_s = r > 0 ? c.vx[r - 1] : Vx[q - WP];
-                const T vy_n = r < R - 1 ? c.vy[r + 1] : Vy[q + WP];
-                txx[r] = flux_n(c.ax[r], Vx[q + 1], c.vx[r]);
-                tyy[r] = flux_n(c.ay[r], vy_n, c.vy[r]);
-                const T sh = shear(g, c.en[r], c.vx[r], vx_s, c.vy[r], Vy[q - 1]);
-                sx[r] = r_mul(sh, g.ihy);
-                sy[r] = r_mul(sh, g.ihx);
-                Fxx[q] = txx[r];
-                Fsy[q] = sy[r];
-                if (r == R - 1) Fyy[q] = tyy[r];
-                if (r == 0) Fsx[q] = sx[r];
-            }
-        }
-        __syncthreads();
-        // ---- phase B: M v from own and neighbour fluxes, damped update
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int wy = strip * R + r;
-            if (cx_in && wy >= ry0 && wy < ry1) {
-                const int q = wy * WP + col;
-                if (c.ux & (1u << r)) {
-                    const T sx_n = r < R - 1 ? sx[r + 1] : Fsx[q + WP];
-                    c.vx[r] = jacobi_update(c.vx[r], c.bx[r], m_x(txx[r], Fxx[q - 1], sx_n, sx[r]), c.wx[r]);
-                    Vx[q] = c.vx[r];
-                }
-                if (c.uy & (1u << r)) {
-                    const T tyy_s = r > 0 ? tyy[r - 1] : Fyy[q - WP];
-                    c.vy[r] = jacobi_update(c.vy[r], c.by[r], m_y(Fsy[q + 1], sy[r], tyy[r], tyy_s), c.wy[r]);
-                    Vy[q] = c.vy[r];
-                }
-            }
-        }
-        __syncthreads();
-    }
-    // ---- write back the unknowns of the tile's own cells
-    const int gx = w.ox0 + col;
-    if (colok && gx >= w.x0 && gx < w.x1) {
-        const size_t P = (size_t)g.pitch;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int gy = w.oy0 + strip * R + r;
-            if (gy >= w.y0 && gy < w.y1) {
-                const size_t q = (size_t)gy * P + (size_t)gx;
-                if (c.ux & (1u << r)) a.ox[q] = c.vx[r];
-                if (c.uy & (1u << r)) a.oy[q] = c.vy[r];
-            }
-        }
-    }
-}
-
-// Fill the own cells' registers from per-cell values; `ld(field, wy, wx)`
-// returns the window value of field 0..5 (vx, vy, eta_c, eta_n, bx, by),
-// zero outside the field's extent.
+// Fill the own cells' registers and the velocity planes; `ld(field, wy, wx)`
+// returns the window value of field 0..7 (vx, vy, eta_c, eta_n, bx, by,
+// 1/dx, 1/dy), zero outside the field's extent.  Cells outside the window get
+// zero state.
 template <typename T, int R, class LD>
 __device__ __forceinline__ void setup_cells(const RasArgs<T> &a, const Window &w, CellRegs<T, R> &c, int col,
-                                            int strip, bool colok, int WP, T *Vx, T *Vy, LD &&ld)
+                                            int strip, bool active, const Planes<T> &pl, LD &&ld)
 {
     const GridDesc<T> &g = a.g;
+    const int WP = a.wp;
     const int gx = w.ox0 + col;
     c.ux = 0;
     c.uy = 0;
@@ -212,25 +188,30 @@ __device__ __forceinline__ void setup_cells(const RasArgs<T> &a, const Window &w
     for (int r = 0; r < R; ++r) {
         const int wy = strip * R + r, gy = w.oy0 + wy;
         T vxv = T(0), vyv = T(0), ec = T(0), env = T(0), bxv = T(0), byv = T(0), wxv = T(0), wyv = T(0);
-        if (colok && wy < w.WY) {
+        if (active && col < w.WX && wy < w.WY) {
             vxv = ld(0, wy, col);
             vyv = ld(1, wy, col);
             ec = ld(2, wy, col);
             env = ld(3, wy, col);
             bxv = ld(4, wy, col);
             byv = ld(5, wy, col);
-            if (inner(w, col, wy)) {
-                if (gy >= 0 && gy < g.ny && gx >= 1 && gx <= g.nx - 1) {
-                    c.ux |= 1u << r;
-                    wxv = jacobi_weight(a.omega, diag_x(g, ec, ld(2, wy, col - 1), ld(3, wy + 1, col), env));
-                }
-                if (gx >= 0 && gx < g.nx && gy >= 1 && gy <= g.ny - 1) {
-                    c.uy |= 1u << r;
-                    wyv = jacobi_weight(a.omega, diag_y(g, ec, ld(2, wy - 1, col), ld(3, wy, col + 1), env));
-                }
+            const bool inner = col >= 1 && col < w.WX - 1 && wy >= 1 && wy < w.WY - 1;
+            if (inner && gy >= 0 && gy < g.ny && gx >= 1 && gx <= g.nx - 1) {
+                c.ux |= 1u << r;
+                const T inv = KCfg<T>::INVD ? ld(6, wy, col)
+                                            : inv_diag(diag_x(g, ec, ld(2, wy, col - 1), ld(3, wy + 1, col), env));
+                wxv = jacobi_weight(a.omega, inv);
             }
-            Vx[wy * WP + col] = vxv;
-            Vy[wy * WP + col] = vyv;
+            if (inner && gx >= 0 && gx < g.nx && gy >= 1 && gy <= g.ny - 1) {
+                c.uy |= 1u << r;
+                const T inv = KCfg<T>::INVD ? ld(7, wy, col)
+                                            : inv_diag(diag_y(g, ec, ld(2, wy - 1, col), ld(3, wy, col + 1), env));
+                wyv = jacobi_weight(a.omega, inv);
+            }
+        }
+        if (active) {
+            pl.Vx[wy * WP + col] = vxv;
+            pl.Vy[wy * WP + col] = vyv;
         }
         c.vx[r] = vxv;
         c.vy[r] = vyv;
@@ -244,41 +225,141 @@ __device__ __forceinline__ void setup_cells(const RasArgs<T> &a, const Window &w
     }
 }
 
+// phase A for one cell: its fluxes into registers and the planes
+template <typename T, int R>
+__device__ __forceinline__ void cell_fluxes(const GridDesc<T> &g, const CellRegs<T, R> &c, const Planes<T> &pl,
+                                            int r, int q, int WP, T *txx, T *tyy, T *sx, T *sy)
+{
+    const T vx_s = r > 0 ? c.vx[r - 1] : pl.Vx[q - WP];
+    const T vy_n = r < R - 1 ? c.vy[r + 1] : pl.Vy[q + WP];
+    txx[r] = flux_n(c.ax[r], pl.Vx[q + 1], c.vx[r]);
+    tyy[r] = flux_n(c.ay[r], vy_n, c.vy[r]);
+    const T sh = shear(g, c.en[r], c.vx[r], vx_s, c.vy[r], pl.Vy[q - 1]);
+    sx[r] = r_mul(sh, g.ihy);
+    sy[r] = r_mul(sh, g.ihx);
+    pl.Fxx[q] = txx[r];
+    pl.Fsy[q] = sy[r];
+    if (r == R - 1) pl.Fyy[q] = tyy[r];
+    if (r == 0) pl.Fsx[q] = sx[r];
+}
+
+// ks local sweeps on the window (registers + shared planes), then write back
+// the unknowns of the tile's own cells.  Ends with a barrier.
+template <typename T, int R>
+__device__ __forceinline__ void sweep_and_store(const RasArgs<T> &a, const Window &w, CellRegs<T, R> &c, int col,
+                                                int strip, bool active, const Planes<T> &pl)
+{
+    const GridDesc<T> &g = a.g;
+    const int WP = a.wp;
+    T txx[R], tyy[R], sx[R], sy[R];
+    for (int s = 1; s <= a.ks; ++s) {
+        if (!KCfg<T>::TRAP) {
+            // every cell of the window; non-updatable cells have weight 0
+            if (active) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    cell_fluxes<T, R>(g, c, pl, r, (strip * R + r) * WP + col, WP, txx, tyy, sx, sy);
+            }
+            __syncthreads();
+            if (active) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int q = (strip * R + r) * WP + col;
+                    const T sx_n = r < R - 1 ? sx[r + 1] : pl.Fsx[q + WP];
+                    const T tyy_s = r > 0 ? tyy[r - 1] : pl.Fyy[q - WP];
+                    c.vx[r] = jacobi_update(c.vx[r], c.bx[r], m_x(txx[r], pl.Fxx[q - 1], sx_n, sx[r]), c.wx[r]);
+                    c.vy[r] = jacobi_update(c.vy[r], c.by[r], m_y(pl.Fsy[q + 1], sy[r], tyy[r], tyy_s), c.wy[r]);
+                    pl.Vx[q] = c.vx[r];
+                    pl.Vy[q] = c.vy[r];
+                }
+            }
+            __syncthreads();
+        } else {
+            const int rr = min(a.overlap, a.ks - s);
+            // updated region, window coordinates; fluxes are needed one cell further
+            const int rx0 = max(w.x0 - rr, 0) - w.ox0, rx1 = min(w.x1 + rr, g.nx) - w.ox0;
+            const int ry0 = max(w.y0 - rr, 0) - w.oy0, ry1 = min(w.y1 + rr, g.ny) - w.oy0;
+            const bool cx_in = active && col >= rx0 && col < rx1;
+            const bool cx_flux = active && col >= rx0 - 1 && col <= rx1;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int wy = strip * R + r;
+                if (cx_flux && wy >= ry0 - 1 && wy <= ry1)
+                    cell_fluxes<T, R>(g, c, pl, r, wy * WP + col, WP, txx, tyy, sx, sy);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int wy = strip * R + r;
+                if (cx_in && wy >= ry0 && wy < ry1) {
+                    const int q = wy * WP + col;
+                    if (c.ux & (1u << r)) {
+                        const T sx_n = r < R - 1 ? sx[r + 1] : pl.Fsx[q + WP];
+                        c.vx[r] = jacobi_update(c.vx[r], c.bx[r], m_x(txx[r], pl.Fxx[q - 1], sx_n, sx[r]), c.wx[r]);
+                        pl.Vx[q] = c.vx[r];
+                    }
+                    if (c.uy & (1u << r)) {
+                        const T tyy_s = r > 0 ? tyy[r - 1] : pl.Fyy[q - WP];
+                        c.vy[r] = jacobi_update(c.vy[r], c.by[r], m_y(pl.Fsy[q + 1], sy[r], tyy[r], tyy_s), c.wy[r]);
+                        pl.Vy[q] = c.vy[r];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // ---- write back the unknowns of the tile's own cells
+    const int gx = w.ox0 + col;
+    if (active && gx >= w.x0 && gx < w.x1) {
+        const size_t P = (size_t)g.pitch;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int gy = w.oy0 + strip * R + r;
+            if (gy >= w.y0 && gy < w.y1) {
+                const size_t q = (size_t)gy * P + (size_t)gx;
+                if (c.ux & (1u << r)) a.ox[q] = c.vx[r];
+                if (c.uy & (1u << r)) a.oy[q] = c.vy[r];
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // persistent TMA-staged kernel
 // ---------------------------------------------------------------------------
-template <typename T, int R>
-__global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_tma(const __grid_constant__ TmaMaps maps, RasArgs<T> a)
+template <typename T, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_ras_tma(const __grid_constant__ TmaMaps maps, RasArgs<T> a)
 {
+    constexpr int R = KCfg<T>::R;
+    constexpr int NF = KCfg<T>::INVD ? 8 : 6;
+    constexpr int ALIGN = 16 / (int)sizeof(T); // TMA x coordinates are multiples of 16 bytes
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     // TMA destinations must be 128-byte aligned shared addresses
     const uint32_t off = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
     T *const stage = reinterpret_cast<T *>(smem_raw + off);
-    const int WP = a.wp, PL = a.plane, BW = a.bw, SP = a.stage;
-    T *const base = stage + STAGE_FIELDS * SP + WP + 1;
-    T *const Vx = base, *const Vy = base + PL, *const Fxx = base + 2 * PL, *const Fsy = base + 3 * PL;
-    T *const Fyy = base + 4 * PL, *const Fsx = base + 5 * PL;
-    const CUtensorMap *const mp[STAGE_FIELDS] = {&maps.vx, &maps.vy, &maps.ec, &maps.en, &maps.bx, &maps.by};
-    constexpr int ALIGN = 16 / (int)sizeof(T); // TMA x coordinates are multiples of 16 bytes
+    const int BW = a.bw, SP = a.stage;
+    const Planes<T> pl(stage + NF * SP, a.wp, a.plane);
 
     const int ntiles = a.tg.ntx * a.tg.nty;
     const int col = threadIdx.x % a.wxm, strip = threadIdx.x / a.wxm;
+    const bool active = (int)threadIdx.x < a.wxm * a.strips;
     const uint32_t box_bytes = (uint32_t)(BW * a.wym * (int)sizeof(T));
 
     auto issue = [&](int tile) {
         const Window w = window_of(a, tile);
         const int xs = w.ox0 & ~(ALIGN - 1);
         fence_proxy_async();
-        mbar_arrive_expect_tx(&bar, STAGE_FIELDS * box_bytes);
+        mbar_arrive_expect_tx(&bar, NF * box_bytes);
 #pragma unroll
-        for (int f = 0; f < STAGE_FIELDS; ++f) tma_load_2d(stage + f * SP, mp[f], xs, w.oy0, &bar);
+        for (int f = 0; f < NF; ++f) tma_load_2d(stage + f * SP, &maps.m[f], xs, w.oy0, &bar);
     };
 
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_proxy_async();
     }
+    zero_borders(a, pl);
     __syncthreads();
     int tile = blockIdx.x;
     if (threadIdx.x == 0 && tile < ntiles) issue(tile);
@@ -296,16 +377,14 @@ __global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_tma(const __grid_consta
         }
         const Window w = window_of(a, tile);
         const int dx = w.ox0 - (w.ox0 & ~(ALIGN - 1));
-        const bool colok = col < w.WX && strip * R < w.WY;
-        zero_outside(w, a.wym, WP, Vx, Vy);
         CellRegs<T, R> c;
-        setup_cells<T, R>(a, w, c, col, strip, colok, WP, Vx, Vy,
+        setup_cells<T, R>(a, w, c, col, strip, active, pl,
                           [&](int f, int wy, int wx) { return stage[f * SP + wy * BW + wx + dx]; });
         __syncthreads(); // staging consumed: refill it with the next tile
         const int next = tile + (int)gridDim.x;
         if (threadIdx.x == 0 && next < ntiles) issue(next);
         phase ^= 1u;
-        sweep_and_store<T, R>(a, w, c, col, strip, colok, WP, Vx, Vy, Fxx, Fsy, Fyy, Fsx);
+        sweep_and_store<T, R>(a, w, c, col, strip, active, pl);
         tile = next;
     }
 }
@@ -313,32 +392,29 @@ __global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_tma(const __grid_consta
 // ---------------------------------------------------------------------------
 // register-resident kernel reading the window from global memory
 // ---------------------------------------------------------------------------
-template <typename T, int R>
+template <typename T>
 __global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_reg(RasArgs<T> a)
 {
+    constexpr int R = KCfg<T>::R;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int WP = a.wp, PL = a.plane;
-    T *const base = reinterpret_cast<T *>(smem_raw) + WP + 1;
-    T *const Vx = base, *const Vy = base + PL, *const Fxx = base + 2 * PL, *const Fsy = base + 3 * PL;
-    T *const Fyy = base + 4 * PL, *const Fsx = base + 5 * PL;
-
+    const Planes<T> pl(reinterpret_cast<T *>(smem_raw), a.wp, a.plane);
     const GridDesc<T> &g = a.g;
     const Window w = window_of(a, (int)blockIdx.x);
     const int col = threadIdx.x % a.wxm, strip = threadIdx.x / a.wxm;
-    const bool colok = col < w.WX && strip * R < w.WY;
+    const bool active = (int)threadIdx.x < a.wxm * a.strips;
     const size_t P = (size_t)g.pitch;
-    const T *const src[STAGE_FIELDS] = {a.vx, a.vy, a.c.eta_c, a.c.eta_n, a.c.bx, a.c.by};
-    zero_outside(w, a.wym, WP, Vx, Vy);
+    const T *const src[8] = {a.vx, a.vy, a.c.eta_c, a.c.eta_n, a.c.bx, a.c.by, a.c.inv_dx, a.c.inv_dy};
+    zero_borders(a, pl);
     CellRegs<T, R> c;
-    setup_cells<T, R>(a, w, c, col, strip, colok, WP, Vx, Vy, [&](int f, int wy, int wx) {
+    setup_cells<T, R>(a, w, c, col, strip, active, pl, [&](int f, int wy, int wx) {
         const int gy = w.oy0 + wy, gx = w.ox0 + wx;
-        // extents: vx, bx ny x (nx+1); vy, by (ny+1) x nx; eta_c ny x nx; eta_n (ny+1) x (nx+1)
-        const int ey = (f == 0 || f == 2 || f == 4) ? g.ny : g.ny + 1;
-        const int ex = (f == 1 || f == 2 || f == 5) ? g.nx : g.nx + 1;
+        // extents: vx, bx, 1/dx ny x (nx+1); vy, by, 1/dy (ny+1) x nx; eta_c ny x nx; eta_n (ny+1) x (nx+1)
+        const int ey = (f == 0 || f == 2 || f == 4 || f == 6) ? g.ny : g.ny + 1;
+        const int ex = (f == 1 || f == 2 || f == 5 || f == 7) ? g.nx : g.nx + 1;
         return (gy >= 0 && gy < ey && gx >= 0 && gx < ex) ? src[f][(size_t)gy * P + (size_t)gx] : T(0);
     });
     __syncthreads();
-    sweep_and_store<T, R>(a, w, c, col, strip, colok, WP, Vx, Vy, Fxx, Fsy, Fyy, Fsx);
+    sweep_and_store<T, R>(a, w, c, col, strip, active, pl);
 }
 
 // ---------------------------------------------------------------------------
@@ -406,7 +482,7 @@ __global__ void __launch_bounds__(RAS_THREADS) k_ras(RasArgs<T> a)
                 const T sx_n = r_mul(shear(g, En[q + W], cx[q + W], vc, cy[q + W], cy[q + W - 1]), g.ihy);
                 const T sx_c = r_mul(shear(g, En[q], vc, cx[q - W], cy[q], cy[q - 1]), g.ihy);
                 const T d = diag_x(g, Ec[q], Ec[q - 1], En[q + W], En[q]);
-                nxv[q] = jacobi_update(vc, Rx[q], m_x(txx_c, txx_w, sx_n, sx_c), jacobi_weight(a.omega, d));
+                nxv[q] = jacobi_update(vc, Rx[q], m_x(txx_c, txx_w, sx_n, sx_c), jacobi_weight(a.omega, inv_diag(d)));
             }
             if (gy >= 1 && gy <= ny - 1) { // vy unknown (gx < nx holds)
                 const T vc = cy[q];
@@ -415,7 +491,7 @@ __global__ void __launch_bounds__(RAS_THREADS) k_ras(RasArgs<T> a)
                 const T sy_e = r_mul(shear(g, En[q + 1], cx[q + 1], cx[q + 1 - W], cy[q + 1], vc), g.ihx);
                 const T sy_c = r_mul(shear(g, En[q], cx[q], cx[q - W], vc, cy[q - 1]), g.ihx);
                 const T d = diag_y(g, Ec[q], Ec[q - W], En[q + 1], En[q]);
-                nyv[q] = jacobi_update(vc, Ry[q], m_y(sy_e, sy_c, tyy_c, tyy_s), jacobi_weight(a.omega, d));
+                nyv[q] = jacobi_update(vc, Ry[q], m_y(sy_e, sy_c, tyy_c, tyy_s), jacobi_weight(a.omega, inv_diag(d)));
             }
         }
         __syncthreads();
@@ -442,7 +518,7 @@ __global__ void __launch_bounds__(RAS_THREADS) k_ras(RasArgs<T> a)
 enum { PLAN_TMA = 0, PLAN_REG = 1, PLAN_SMEM = 2 };
 struct RasPlan {
     int kind;
-    int wxm, wym, wp, plane, threads, bw, stage;
+    int wxm, wym, strips, wp, plane, threads, bw, stage;
     size_t smem;
 };
 
@@ -450,19 +526,21 @@ RasPlan plan_ras(int nx, int ny, int ti, int tj, int overlap, size_t elem, bool 
 {
     RasPlan p;
     const int h = overlap + 1;
+    const int R = elem == 8 ? KCfg<double>::R : KCfg<float>::R;
+    const int nf = (elem == 8 ? KCfg<double>::INVD : KCfg<float>::INVD) ? 8 : 6;
     // a tile never spans more than min(T, n) cells
     p.wxm = std::min(ti, nx) + 2 * h;
     p.wym = std::min(tj, ny) + 2 * h;
-    const int strips = (p.wym + REG_R - 1) / REG_R;
-    const long threads = (long)p.wxm * strips;
+    p.strips = (p.wym + R - 1) / R;
+    const long threads = (long)p.wxm * p.strips;
     const size_t maxs = (size_t)ras_max_smem();
     p.wp = p.wxm + 2;
-    p.plane = p.wp * (p.wym + 2);
+    p.plane = p.wp * (p.strips * R + 2);
     const int align = 16 / (int)elem;
     p.bw = (p.wxm + align - 1 + align - 1) / align * align; // room for the alignment shift of x
     p.stage = (int)((((size_t)p.bw * p.wym * elem + 127) / 128 * 128) / elem);
     const size_t reg_smem = (size_t)REG_PLANES * (size_t)p.plane * elem;
-    const size_t tma_smem = (size_t)STAGE_FIELDS * (size_t)p.stage * elem + reg_smem + 128;
+    const size_t tma_smem = (size_t)nf * (size_t)p.stage * elem + reg_smem + 128;
     p.threads = (int)((threads + 31) / 32 * 32);
     if (threads <= REG_MAX_THREADS && allow_tma && p.bw <= 256 && p.wym <= 256 && tma_smem <= maxs) {
         p.kind = PLAN_TMA;
@@ -520,6 +598,8 @@ template <typename T>
 cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const TileGrid &tg, int ksweeps,
                        int overlap, const T *vx, const T *vy, T *ox, T *oy, const RasRun &run, cudaStream_t s)
 {
+    constexpr int NF = KCfg<T>::INVD ? 8 : 6;
+    const bool have_inv = c.inv_dx && c.inv_dy;
     const RasPlan p = plan_ras(g.nx, g.ny, tg.ti, tg.tj, overlap, sizeof(T), run.allow_tma);
     RasArgs<T> a;
     a.g = g;
@@ -534,6 +614,7 @@ cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const 
     a.overlap = overlap;
     a.wxm = p.wxm;
     a.wym = p.wym;
+    a.strips = p.strips;
     a.wp = p.wp;
     a.plane = p.plane;
     a.bw = p.bw;
@@ -542,29 +623,34 @@ cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const 
     a.wait_limit = run.wait_limit;
     const int ntiles = tg.ntx * tg.nty;
     cudaError_t e;
+    if (KCfg<T>::INVD && !have_inv && p.kind != PLAN_SMEM) return cudaErrorInvalidValue;
     if (p.kind == PLAN_TMA) {
         TmaMaps m;
         const int es = (int)sizeof(T);
         const long pb = (long)g.pitch * es;
-        const void *ptrs[STAGE_FIELDS] = {vx, vy, c.eta_c, c.eta_n, c.bx, c.by};
-        const int widths[STAGE_FIELDS] = {g.nx + 1, g.nx, g.nx, g.nx + 1, g.nx + 1, g.nx};
-        const int heights[STAGE_FIELDS] = {g.ny, g.ny + 1, g.ny, g.ny + 1, g.ny, g.ny + 1};
-        CUtensorMap *dst[STAGE_FIELDS] = {&m.vx, &m.vy, &m.ec, &m.en, &m.bx, &m.by};
-        for (int f = 0; f < STAGE_FIELDS; ++f) {
-            e = make_tmap_2d(dst[f], ptrs[f], es, widths[f], heights[f], pb, p.bw, p.wym);
+        const void *ptrs[8] = {vx, vy, c.eta_c, c.eta_n, c.bx, c.by, c.inv_dx, c.inv_dy};
+        const int widths[8] = {g.nx + 1, g.nx, g.nx, g.nx + 1, g.nx + 1, g.nx, g.nx + 1, g.nx};
+        const int heights[8] = {g.ny, g.ny + 1, g.ny, g.ny + 1, g.ny, g.ny + 1, g.ny, g.ny + 1};
+        for (int f = 0; f < NF; ++f) {
+            e = make_tmap_2d(&m.m[f], ptrs[f], es, widths[f], heights[f], pb, p.bw, p.wym);
             if (e != cudaSuccess) return e;
         }
-        e = cudaFuncSetAttribute(k_ras_tma<T, REG_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+        // FP32 windows of up to 320 threads: registers capped so that two CTAs
+        // share an SM (FP64 is bound by its FP64 pipe and keeps 128 registers)
+        void (*kern)(TmaMaps, RasArgs<T>) = k_ras_tma<T, REG_MAX_THREADS, 1>;
+        if constexpr (sizeof(T) == 4)
+            if (p.threads <= SMALL_THREADS) kern = k_ras_tma<T, SMALL_THREADS, 2>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ras_tma<T, REG_R>, p.threads, p.smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, p.threads, p.smem);
         if (e != cudaSuccess) return e;
         const int grid = std::min(ntiles, std::max(per_sm, 1) * sm_count());
-        k_ras_tma<T, REG_R><<<grid, p.threads, p.smem, s>>>(m, a);
+        kern<<<grid, p.threads, p.smem, s>>>(m, a);
     } else if (p.kind == PLAN_REG) {
-        e = cudaFuncSetAttribute(k_ras_reg<T, REG_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+        e = cudaFuncSetAttribute(k_ras_reg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
         if (e != cudaSuccess) return e;
-        k_ras_reg<T, REG_R><<<ntiles, p.threads, p.smem, s>>>(a);
+        k_ras_reg<T><<<ntiles, p.threads, p.smem, s>>>(a);
     } else {
         e = cudaFuncSetAttribute(k_ras<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
         if (e != cudaSuccess) return e;

@@ -28,8 +28,9 @@ __device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b
 __device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
-__device__ __forceinline__ float r_div(float a, float b) { return __fdiv_rn(a, b); }
-__device__ __forceinline__ double r_div(double a, double b) { return __ddiv_rn(a, b); }
+// correctly rounded reciprocal (the same value as 1/x with IEEE division)
+__device__ __forceinline__ float r_rcp(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ double r_rcp(double a) { return __drcp_rn(a); }
 
 // ax = 2 eta_c / hx^2 and ay = 2 eta_c / hy^2
 template <typename T>
@@ -85,11 +86,18 @@ __device__ __forceinline__ T diag_y(const GridDesc<T> &g, T ec_c, T ec_s, T en_e
     return -r_fma(r_add(ec_c, ec_s), g.two_ihy2, r_mul(r_add(en_e, en_w), g.ihx2));
 }
 
-// damped-Jacobi weight omega / diag(M)
+// 1 / diag(M)
 template <typename T>
-__device__ __forceinline__ T jacobi_weight(T omega, T d)
+__device__ __forceinline__ T inv_diag(T d)
 {
-    return r_mul(omega, r_div(T(1), d));
+    return r_rcp(d);
+}
+
+// damped-Jacobi weight omega / diag(M), from 1 / diag(M)
+template <typename T>
+__device__ __forceinline__ T jacobi_weight(T omega, T inv_d)
+{
+    return r_mul(omega, inv_d);
 }
 
 // v + (b - M v) omega / diag(M)

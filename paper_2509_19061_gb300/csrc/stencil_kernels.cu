@@ -97,6 +97,18 @@ __global__ void k_copy_eta(GridDesc<T> g, const T *__restrict__ ec_in, const T *
     en[q] = interior ? en_in[q] : T(0);
 }
 
+// 1 / diag(M) at the unknowns, zero elsewhere
+template <typename T>
+__global__ void k_inv_diag(GridDesc<T> g, const T *__restrict__ ec, const T *__restrict__ en, T *__restrict__ ix,
+                           T *__restrict__ iy)
+{
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i > g.nx || j > g.ny) return;
+    const size_t P = (size_t)g.pitch, q = (size_t)j * P + i;
+    if (j < g.ny) ix[q] = vx_unknown(g, j, i) ? inv_diag(diag_x(g, ec[q], ec[q - 1], en[q + P], en[q])) : T(0);
+    if (i < g.nx) iy[q] = vy_unknown(g, j, i) ? inv_diag(diag_y(g, ec[q], ec[q - P], en[q + 1], en[q])) : T(0);
+}
+
 // b = f - G p with (G p) = -grad p; zero on walls.
 template <typename T>
 __global__ void k_rhs(GridDesc<T> g, const T *__restrict__ fx, const T *__restrict__ fy, const T *__restrict__ p,
@@ -153,7 +165,8 @@ __global__ void k_jacobi(GridDesc<T> g, Coeffs<T> c, T omega, const T *__restric
     if (DO_X) {
         if (vx_unknown(g, j, i)) {
             op_x(g, c.eta_c, c.eta_n, vx, vy, j, i, m, d, vc);
-            ox[q] = jacobi_update(vc, c.bx[q], m, jacobi_weight(omega, d));
+            const T inv = c.inv_dx ? c.inv_dx[q] : inv_diag(d);
+            ox[q] = jacobi_update(vc, c.bx[q], m, jacobi_weight(omega, inv));
         } else if (vx_wall(g, j, i)) {
             ox[q] = vx[q];
         }
@@ -161,7 +174,8 @@ __global__ void k_jacobi(GridDesc<T> g, Coeffs<T> c, T omega, const T *__restric
     if (DO_Y) {
         if (vy_unknown(g, j, i)) {
             op_y(g, c.eta_c, c.eta_n, vx, vy, j, i, m, d, vc);
-            oy[q] = jacobi_update(vc, c.by[q], m, jacobi_weight(omega, d));
+            const T inv = c.inv_dy ? c.inv_dy[q] : inv_diag(d);
+            oy[q] = jacobi_update(vc, c.by[q], m, jacobi_weight(omega, inv));
         } else if (vy_wall(g, j, i)) {
             oy[q] = vy[q];
         }
@@ -180,11 +194,13 @@ __global__ void k_rbgs(GridDesc<T> g, Coeffs<T> c, T omega, int colour, T *__res
     if (X) {
         if (!vx_unknown(g, j, i)) return;
         op_x(g, c.eta_c, c.eta_n, vx, vy, j, i, m, d, vc);
-        vx[q] = jacobi_update(vc, c.bx[q], m, jacobi_weight(omega, d));
+        const T inv = c.inv_dx ? c.inv_dx[q] : inv_diag(d);
+        vx[q] = jacobi_update(vc, c.bx[q], m, jacobi_weight(omega, inv));
     } else {
         if (!vy_unknown(g, j, i)) return;
         op_y(g, c.eta_c, c.eta_n, vx, vy, j, i, m, d, vc);
-        vy[q] = jacobi_update(vc, c.by[q], m, jacobi_weight(omega, d));
+        const T inv = c.inv_dy ? c.inv_dy[q] : inv_diag(d);
+        vy[q] = jacobi_update(vc, c.by[q], m, jacobi_weight(omega, inv));
     }
 }
 
@@ -299,6 +315,14 @@ cudaError_t launch_copy_eta(const GridDesc<T> &g, const T *eta_c_in, const T *et
 }
 
 template <typename T>
+cudaError_t launch_inv_diag(const GridDesc<T> &g, const T *eta_c, const T *eta_n, T *inv_dx, T *inv_dy,
+                            cudaStream_t s)
+{
+    k_inv_diag<T><<<grid2d(g.nx + 1, g.ny + 1), dim3(BX, BY), 0, s>>>(g, eta_c, eta_n, inv_dx, inv_dy);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_rhs(const GridDesc<T> &g, const T *fx, const T *fy, const T *p, T *bx, T *by, cudaStream_t s)
 {
     k_rhs<T><<<grid2d(g.nx + 1, g.ny + 1), dim3(BX, BY), 0, s>>>(g, fx, fy, p, bx, by);
@@ -367,6 +391,7 @@ cudaError_t launch_energy(const GridDesc<T> &g, const T *eta_c, const T *eta_n, 
 
 #define INST(T)                                                                                                    \
     template cudaError_t launch_copy_eta<T>(const GridDesc<T> &, const T *, const T *, T *, T *, cudaStream_t);    \
+    template cudaError_t launch_inv_diag<T>(const GridDesc<T> &, const T *, const T *, T *, T *, cudaStream_t);    \
     template cudaError_t launch_rhs<T>(const GridDesc<T> &, const T *, const T *, const T *, T *, T *,             \
                                        cudaStream_t);                                                              \
     template cudaError_t launch_apply<T>(const GridDesc<T> &, const T *, const T *, const T *, const T *,          \
