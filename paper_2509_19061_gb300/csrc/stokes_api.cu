@@ -63,6 +63,7 @@ struct stokes_ctx {
     cudaStream_t stream;
     void *eta_c = nullptr, *eta_n = nullptr, *fx = nullptr, *fy = nullptr;
     void *bx = nullptr, *by = nullptr, *sx = nullptr, *sy = nullptr;
+    void *ivx = nullptr, *ivy = nullptr; // 1/diag(M) (FP64 contexts: the FP64 pipe is the bottleneck)
     double *partials = nullptr, *dsum = nullptr, *hsum = nullptr;
     bool have_eta = false, have_f = false;
     int *dstatus = nullptr;              // device status word of the bounded waits
@@ -153,6 +154,8 @@ Coeffs<T> coeffs_of(const stokes_ctx *c)
     k.eta_n = (const T *)c->eta_n;
     k.bx = (const T *)c->bx;
     k.by = (const T *)c->by;
+    k.inv_dx = (const T *)c->ivx;
+    k.inv_dy = (const T *)c->ivy;
     return k;
 }
 
@@ -312,6 +315,10 @@ int stokes_create(int nx, int ny, double lx, double ly, int dtype, void *cuda_st
     void **fields[] = {&c->eta_c, &c->eta_n, &c->fx, &c->fy, &c->bx, &c->by, &c->sx, &c->sy};
     for (void **f : fields)
         if ((st = alloc_field(c, f)) != STOKES_OK) break;
+    if (st == STOKES_OK && dtype == STOKES_F64) {
+        st = alloc_field(c, &c->ivx);
+        if (st == STOKES_OK) st = alloc_field(c, &c->ivy);
+    }
     if (st == STOKES_OK) {
         cudaError_t e = cudaMalloc(&c->partials, (size_t)energy_partials() * 3 * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&c->dsum, 3 * sizeof(double));
@@ -338,7 +345,8 @@ int stokes_destroy(stokes_ctx *c)
     mg_destroy(c->mg);
     prof_flush(c);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
-    void *fields[] = {c->eta_c, c->eta_n, c->fx, c->fy, c->bx, c->by, c->sx, c->sy, c->partials, c->dsum, c->dstatus};
+    void *fields[] = {c->eta_c, c->eta_n, c->fx, c->fy, c->bx, c->by, c->sx, c->sy, c->ivx, c->ivy, c->partials,
+                      c->dsum, c->dstatus};
     for (void *f : fields)
         if (f) cudaFree(f);
     if (c->hsum) cudaFreeHost(c->hsum);
@@ -369,9 +377,13 @@ int stokes_get_layout(const stokes_ctx *c, int field, int *rows, int *cols, int 
 int stokes_set_viscosity(stokes_ctx *c, const void *eta_c, const void *eta_n)
 {
     if (!c || !eta_c || !eta_n) return STOKES_ERR_ARG;
-    if (c->dtype == STOKES_F64)
+    if (c->dtype == STOKES_F64) {
         RUN(STOKES_K_COPY, 1, launch_copy_eta<double>(grid_of<double>(c), (const double *)eta_c, (const double *)eta_n,
                                    (double *)c->eta_c, (double *)c->eta_n, c->stream));
+        RUN(STOKES_K_COPY, 1,
+            launch_inv_diag<double>(grid_of<double>(c), (const double *)c->eta_c, (const double *)c->eta_n,
+                                    (double *)c->ivx, (double *)c->ivy, c->stream));
+    }
     else
         RUN(STOKES_K_COPY, 1, launch_copy_eta<float>(grid_of<float>(c), (const float *)eta_c, (const float *)eta_n, (float *)c->eta_c,
                                   (float *)c->eta_n, c->stream));
