@@ -73,10 +73,11 @@ cudaError_t launch_copy_walls(const GridDesc<T> &g, const T *vx, const T *vy, T 
 // Energy sums (3 doubles) into out[0..2] on the device; `partials` holds
 // energy_partials() * 3 doubles.
 int energy_partials();
+// b = f - G p is formed on the fly (p may be NULL); inv_dx/inv_dy may be NULL
 template <typename T>
-cudaError_t launch_energy(const GridDesc<T> &g, const T *eta_c, const T *eta_n, const T *fx, const T *fy,
-                          const T *bx, const T *by, const T *vx, const T *vy, double *partials, double *out,
-                          cudaStream_t s);
+cudaError_t launch_energy(const GridDesc<T> &g, const T *eta_c, const T *eta_n, const T *inv_dx, const T *inv_dy,
+                          const T *fx, const T *fy, const T *p, const T *vx, const T *vy, double *partials,
+                          double *out, cudaStream_t s);
 
 // ---- tiled / RAS kernel (ras_kernels.cu) ---------------------------------
 struct TileGrid {

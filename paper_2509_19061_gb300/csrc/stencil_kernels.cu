@@ -119,12 +119,12 @@ __global__ void k_rhs(GridDesc<T> g, const T *__restrict__ fx, const T *__restri
     const size_t P = (size_t)g.pitch, q = (size_t)j * P + i;
     if (j < g.ny) {
         T b = T(0);
-        if (vx_unknown(g, j, i)) b = fx[q] + (p ? (p[q] - p[q - 1]) * g.ihx : T(0));
+        if (vx_unknown(g, j, i)) b = p ? r_fma(r_sub(p[q], p[q - 1]), g.ihx, fx[q]) : fx[q];
         bx[q] = b;
     }
     if (i < g.nx) {
         T b = T(0);
-        if (vy_unknown(g, j, i)) b = fy[q] + (p ? (p[q] - p[q - P]) * g.ihy : T(0));
+        if (vy_unknown(g, j, i)) b = p ? r_fma(r_sub(p[q], p[q - P]), g.ihy, fy[q]) : fy[q];
         by[q] = b;
     }
 }
@@ -245,12 +245,16 @@ __device__ __forceinline__ double warp_sum(double v)
 
 template <typename T>
 __global__ void __launch_bounds__(EN_THREADS) k_energy(GridDesc<T> g, const T *__restrict__ eta_c,
-                                                       const T *__restrict__ eta_n, const T *__restrict__ fx,
-                                                       const T *__restrict__ fy, const T *__restrict__ bx,
-                                                       const T *__restrict__ by, const T *__restrict__ vx,
-                                                       const T *__restrict__ vy, double *__restrict__ partials)
+                                                       const T *__restrict__ eta_n, const T *__restrict__ inv_dx,
+                                                       const T *__restrict__ inv_dy, const T *__restrict__ fx,
+                                                       const T *__restrict__ fy, const T *__restrict__ p,
+                                                       const T *__restrict__ vx, const T *__restrict__ vy,
+                                                       double *__restrict__ partials)
 {
+    // r_v = f - G p - M v with b = f - G p formed on the fly; the weights
+    // 1/(-diag M) come from the context's 1/diag arrays when it has them
     double s_rv = 0.0, s_rp = 0.0, s_ff = 0.0;
+    const double ilap = 1.0 / g.lap;
     const long w = (long)g.nx + 1, total = w * (long)(g.ny + 1);
     for (long t = (long)blockIdx.x * EN_THREADS + threadIdx.x; t < total; t += (long)gridDim.x * EN_THREADS) {
         const int j = (int)(t / w), i = (int)(t - (long)j * w);
@@ -258,20 +262,24 @@ __global__ void __launch_bounds__(EN_THREADS) k_energy(GridDesc<T> g, const T *_
         T m, d, vc;
         if (vx_unknown(g, j, i)) {
             op_x(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
-            const double r = (double)r_sub(bx[q], m), wgt = -(double)d, f = (double)fx[q];
-            s_rv += r * r / wgt;
-            s_ff += f * f / wgt;
+            const T b = p ? r_fma(r_sub(p[q], p[q - 1]), g.ihx, fx[q]) : fx[q];
+            const double r = (double)r_sub(b, m), f = (double)fx[q];
+            const double wi = -(double)(inv_dx ? inv_dx[q] : inv_diag(d));
+            s_rv = fma(r * r, wi, s_rv);
+            s_ff = fma(f * f, wi, s_ff);
         }
         if (vy_unknown(g, j, i)) {
             op_y(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
-            const double r = (double)r_sub(by[q], m), wgt = -(double)d, f = (double)fy[q];
-            s_rv += r * r / wgt;
-            s_ff += f * f / wgt;
+            const T b = p ? r_fma(r_sub(p[q], p[q - g.pitch]), g.ihy, fy[q]) : fy[q];
+            const double r = (double)r_sub(b, m), f = (double)fy[q];
+            const double wi = -(double)(inv_dy ? inv_dy[q] : inv_diag(d));
+            s_rv = fma(r * r, wi, s_rv);
+            s_ff = fma(f * f, wi, s_ff);
         }
         if (i < g.nx && j < g.ny) {
-            const T dv = (vx[q + 1] - vx[q]) * g.ihx + (vy[q + g.pitch] - vy[q]) * g.ihy;
+            const T dv = r_fma(r_sub(vx[q + 1], vx[q]), g.ihx, r_mul(r_sub(vy[q + g.pitch], vy[q]), g.ihy));
             const double r = (double)dv;
-            s_rp += r * r * (double)eta_c[q] / g.lap;
+            s_rp = fma(r * r, (double)eta_c[q] * ilap, s_rp);
         }
     }
     __shared__ double sh[3][EN_THREADS / 32];
@@ -380,11 +388,11 @@ cudaError_t launch_copy_walls(const GridDesc<T> &g, const T *vx, const T *vy, T 
 int energy_partials() { return EN_BLOCKS; }
 
 template <typename T>
-cudaError_t launch_energy(const GridDesc<T> &g, const T *eta_c, const T *eta_n, const T *fx, const T *fy,
-                          const T *bx, const T *by, const T *vx, const T *vy, double *partials, double *out,
-                          cudaStream_t s)
+cudaError_t launch_energy(const GridDesc<T> &g, const T *eta_c, const T *eta_n, const T *inv_dx, const T *inv_dy,
+                          const T *fx, const T *fy, const T *p, const T *vx, const T *vy, double *partials,
+                          double *out, cudaStream_t s)
 {
-    k_energy<T><<<EN_BLOCKS, EN_THREADS, 0, s>>>(g, eta_c, eta_n, fx, fy, bx, by, vx, vy, partials);
+    k_energy<T><<<EN_BLOCKS, EN_THREADS, 0, s>>>(g, eta_c, eta_n, inv_dx, inv_dy, fx, fy, p, vx, vy, partials);
     k_energy_final<<<1, 96, 0, s>>>(partials, EN_BLOCKS, out);
     return cudaGetLastError();
 }
@@ -403,8 +411,8 @@ cudaError_t launch_energy(const GridDesc<T> &g, const T *eta_c, const T *eta_n, 
                                                  cudaStream_t);                                                    \
     template cudaError_t launch_copy_walls<T>(const GridDesc<T> &, const T *, const T *, T *, T *, cudaStream_t);  \
     template cudaError_t launch_energy<T>(const GridDesc<T> &, const T *, const T *, const T *, const T *,         \
-                                          const T *, const T *, const T *, const T *, double *, double *,          \
-                                          cudaStream_t);
+                                          const T *, const T *, const T *, const T *, const T *, double *,         \
+                                          double *, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -258,10 +258,9 @@ template <typename T>
 int energy_impl(stokes_ctx *c, const T *vx, const T *vy, const T *p, double out[3])
 {
     const GridDesc<T> g = grid_of<T>(c);
-    RUN(STOKES_K_RHS, 1, launch_rhs<T>(g, (const T *)c->fx, (const T *)c->fy, p, (T *)c->bx, (T *)c->by, c->stream));
     RUN(STOKES_K_ENERGY, 2,
-        launch_energy<T>(g, (const T *)c->eta_c, (const T *)c->eta_n, (const T *)c->fx, (const T *)c->fy,
-                         (const T *)c->bx, (const T *)c->by, vx, vy, c->partials, c->dsum, c->stream));
+        launch_energy<T>(g, (const T *)c->eta_c, (const T *)c->eta_n, (const T *)c->ivx, (const T *)c->ivy,
+                         (const T *)c->fx, (const T *)c->fy, p, vx, vy, c->partials, c->dsum, c->stream));
     CK(cudaMemcpyAsync(c->hsum, c->dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     const int st = device_status(c);
     std::memcpy(out, c->hsum, 3 * sizeof(double));
