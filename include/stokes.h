@@ -239,6 +239,38 @@ typedef enum {
 int stokes_profile_reset(stokes_ctx *ctx, int enable_timing);
 int stokes_profile_read(stokes_ctx *ctx, int kind, long long *kernels, long long *groups, double *total_ms);
 
+/* Energy residual sums without allocating.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, for instance
+ * code that runs inside a framework's device-memory budget that forbids side
+ * allocations, that hands every byte of the GPU to its own pools, or that
+ * must not risk the device-wide synchronisation cudaMalloc and cudaFree can
+ * cause.  Such callers cannot create a stokes_ctx (which allocates), so this
+ * call takes everything as arguments and allocates nothing.
+ *
+ * It computes the three sums of stokes_residual_energy_norm for the grid
+ * nx x ny on [0, lx] x [0, ly] in `dtype`: every field pointer is a device
+ * buffer of (ny+1) rows x `pitch` elements in the layout described at the top
+ * of this file (eta_n is the caller's own array, its boundary nodes are
+ * ignored); p may be NULL (p = 0).  out_dev is a device pointer to 3 doubles
+ * that receives the sums.  The work is enqueued on `cuda_stream` (NULL = the
+ * legacy default stream) and the call returns without waiting.
+ *
+ * Scratch: the per-block partial sums live in a file-scope device array of
+ * 608 x 3 doubles (14,592 bytes) that every GPU loading the library holds
+ * until the process exits.  Each call overwrites all of it before reading it,
+ * so nothing carries over between calls, but every call shares the one array:
+ * calls whose work overlaps on the GPU (on different streams, or from
+ * different host threads) race and return wrong sums.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.
+ *
+ * Limits: 2 <= nx, ny <= 46340, pitch >= nx + 1 and (ny + 1) * pitch < 2^31;
+ * anything else returns STOKES_ERR_ARG, as do NULL inputs or a bad dtype.
+ * CUDA failures return STOKES_ERR_CUDA. */
+int stokes_energy_norm_noalloc(int nx, int ny, double lx, double ly, int dtype, int pitch, const void *eta_c,
+                               const void *eta_n, const void *fx, const void *fy, const void *p, const void *vx,
+                               const void *vy, double *out_dev, void *cuda_stream);
+
 /* Release every library-owned buffer of the context.  NULL is accepted. */
 int stokes_destroy(stokes_ctx *ctx);
 

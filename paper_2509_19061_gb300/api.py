@@ -76,6 +76,7 @@ _SIGS = {
     "stokes_profile_reset": (_I, [_VP, _I]),
     "stokes_profile_read": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(_D)]),
+    "stokes_energy_norm_noalloc": (_I, [_I, _I, _D, _D, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "stokes_destroy": (_I, [_VP]),
     "stokes_strerror": (ctypes.c_char_p, [_I]),
     "stokes_last_cuda_error": (ctypes.c_char_p, []),
@@ -203,6 +204,16 @@ def stokes_profile_read(ctx, kind):
     _check(_lib().stokes_profile_read(ctx, kind, ctypes.byref(k), ctypes.byref(g), ctypes.byref(ms)),
            "stokes_profile_read")
     return k.value, g.value, ms.value
+
+
+def stokes_energy_norm_noalloc(nx, ny, lx, ly, dtype, pitch, eta_c, eta_n, fx, fy, p, vx, vy, out_dev,
+                               cuda_stream=None):
+    """Energy sums into the device tensor out_dev (3 float64) without any
+    allocation by the library; asynchronous on cuda_stream."""
+    stream = ctypes.c_void_p(cuda_stream) if cuda_stream else None
+    _check(_lib().stokes_energy_norm_noalloc(nx, ny, lx, ly, dtype, pitch, _ptr(eta_c), _ptr(eta_n), _ptr(fx),
+                                             _ptr(fy), _ptr(p), _ptr(vx), _ptr(vy), _ptr(out_dev), stream),
+           "stokes_energy_norm_noalloc")
 
 
 def stokes_destroy(ctx):

@@ -79,6 +79,13 @@ cudaError_t launch_energy(const GridDesc<T> &g, const T *eta_c, const T *eta_n, 
                           const T *fx, const T *fy, const T *p, const T *vx, const T *vy, double *partials,
                           double *out, cudaStream_t s);
 
+// The same sums from the caller's raw viscosity (boundary nodes of eta_n
+// zeroed on the fly, 1/diag computed in the kernel); `partials` holds
+// energy_partials() * 3 doubles.
+template <typename T>
+cudaError_t launch_energy_raw(const GridDesc<T> &g, const T *eta_c, const T *eta_n, const T *fx, const T *fy,
+                              const T *p, const T *vx, const T *vy, double *partials, double *out, cudaStream_t s);
+
 // ---- tiled / RAS kernel (ras_kernels.cu) ---------------------------------
 struct TileGrid {
     int ti, tj;   // tile size (cells)

@@ -22,7 +22,9 @@ inline dim3 grid2d(int w, int h) { return dim3((unsigned)((w + BX - 1) / BX), (u
 // (M v)_x and diag(M)_x at vx unknown (j, i), 1 <= i <= nx-1, 0 <= j < ny.
 // Rows outside the vx extent (j = -1, j = ny) enter only through a zero
 // eta_n and are read as zero.
-template <typename T>
+// MASK: eta_n is the caller's raw array, so boundary nodes are zeroed here
+// (the library's own copy already holds zeros there).
+template <typename T, bool MASK = false>
 __device__ __forceinline__ void op_x(const GridDesc<T> &g, const T *__restrict__ eta_c, const T *__restrict__ eta_n,
                                      const T *__restrict__ vx, const T *__restrict__ vy, int j, int i, T &m, T &d,
                                      T &vc)
@@ -33,7 +35,9 @@ __device__ __forceinline__ void op_x(const GridDesc<T> &g, const T *__restrict__
     const T vE = vx[q + 1], vW = vx[q - 1];
     const T vN = j + 1 < g.ny ? vx[q + P] : T(0);
     const T vS = j > 0 ? vx[q - P] : T(0);
-    const T ecC = eta_c[q], ecW = eta_c[q - 1], enN = eta_n[q + P], enS = eta_n[q];
+    const T ecC = eta_c[q], ecW = eta_c[q - 1];
+    const T enN = (MASK && j + 1 == g.ny) ? T(0) : eta_n[q + P];
+    const T enS = (MASK && j == 0) ? T(0) : eta_n[q];
     const T txx_c = flux_n(coef_x(g, ecC), vE, vc);
     const T txx_w = flux_n(coef_x(g, ecW), vc, vW);
     const T sx_n = r_mul(shear(g, enN, vN, vc, vy[q + P], vy[q + P - 1]), g.ihy);
@@ -43,7 +47,7 @@ __device__ __forceinline__ void op_x(const GridDesc<T> &g, const T *__restrict__
 }
 
 // (M v)_y and diag(M)_y at vy unknown (j, i), 1 <= j <= ny-1, 0 <= i < nx.
-template <typename T>
+template <typename T, bool MASK = false>
 __device__ __forceinline__ void op_y(const GridDesc<T> &g, const T *__restrict__ eta_c, const T *__restrict__ eta_n,
                                      const T *__restrict__ vx, const T *__restrict__ vy, int j, int i, T &m, T &d,
                                      T &vc)
@@ -54,7 +58,9 @@ __device__ __forceinline__ void op_y(const GridDesc<T> &g, const T *__restrict__
     const T vN = vy[q + P], vS = vy[q - P];
     const T vE = i + 1 < g.nx ? vy[q + 1] : T(0);
     const T vW = i > 0 ? vy[q - 1] : T(0);
-    const T ecC = eta_c[q], ecS = eta_c[q - P], enE = eta_n[q + 1], enW = eta_n[q];
+    const T ecC = eta_c[q], ecS = eta_c[q - P];
+    const T enE = (MASK && i + 1 == g.nx) ? T(0) : eta_n[q + 1];
+    const T enW = (MASK && i == 0) ? T(0) : eta_n[q];
     const T tyy_c = flux_n(coef_y(g, ecC), vN, vc);
     const T tyy_s = flux_n(coef_y(g, ecS), vc, vS);
     const T sy_e = r_mul(shear(g, enE, vx[q + 1], vx[q + 1 - P], vE, vc), g.ihx);
@@ -243,7 +249,7 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-template <typename T>
+template <typename T, bool MASK = false>
 __global__ void __launch_bounds__(EN_THREADS) k_energy(GridDesc<T> g, const T *__restrict__ eta_c,
                                                        const T *__restrict__ eta_n, const T *__restrict__ inv_dx,
                                                        const T *__restrict__ inv_dy, const T *__restrict__ fx,
@@ -261,7 +267,7 @@ __global__ void __launch_bounds__(EN_THREADS) k_energy(GridDesc<T> g, const T *_
         const size_t q = (size_t)j * g.pitch + i;
         T m, d, vc;
         if (vx_unknown(g, j, i)) {
-            op_x(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
+            op_x<T, MASK>(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
             const T b = p ? r_fma(r_sub(p[q], p[q - 1]), g.ihx, fx[q]) : fx[q];
             const double r = (double)r_sub(b, m), f = (double)fx[q];
             const double wi = -(double)(inv_dx ? inv_dx[q] : inv_diag(d));
@@ -269,7 +275,7 @@ __global__ void __launch_bounds__(EN_THREADS) k_energy(GridDesc<T> g, const T *_
             s_ff = fma(f * f, wi, s_ff);
         }
         if (vy_unknown(g, j, i)) {
-            op_y(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
+            op_y<T, MASK>(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
             const T b = p ? r_fma(r_sub(p[q], p[q - g.pitch]), g.ihy, fy[q]) : fy[q];
             const double r = (double)r_sub(b, m), f = (double)fy[q];
             const double wi = -(double)(inv_dy ? inv_dy[q] : inv_diag(d));
@@ -397,6 +403,16 @@ cudaError_t launch_energy(const GridDesc<T> &g, const T *eta_c, const T *eta_n, 
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_energy_raw(const GridDesc<T> &g, const T *eta_c, const T *eta_n, const T *fx, const T *fy,
+                              const T *p, const T *vx, const T *vy, double *partials, double *out, cudaStream_t s)
+{
+    k_energy<T, true><<<EN_BLOCKS, EN_THREADS, 0, s>>>(g, eta_c, eta_n, nullptr, nullptr, fx, fy, p, vx, vy,
+                                                       partials);
+    k_energy_final<<<1, 96, 0, s>>>(partials, EN_BLOCKS, out);
+    return cudaGetLastError();
+}
+
 #define INST(T)                                                                                                    \
     template cudaError_t launch_copy_eta<T>(const GridDesc<T> &, const T *, const T *, T *, T *, cudaStream_t);    \
     template cudaError_t launch_inv_diag<T>(const GridDesc<T> &, const T *, const T *, T *, T *, cudaStream_t);    \
@@ -412,7 +428,9 @@ cudaError_t launch_energy(const GridDesc<T> &g, const T *eta_c, const T *eta_n, 
     template cudaError_t launch_copy_walls<T>(const GridDesc<T> &, const T *, const T *, T *, T *, cudaStream_t);  \
     template cudaError_t launch_energy<T>(const GridDesc<T> &, const T *, const T *, const T *, const T *,         \
                                           const T *, const T *, const T *, const T *, const T *, double *,         \
-                                          double *, cudaStream_t);
+                                          double *, cudaStream_t);                                                 \
+    template cudaError_t launch_energy_raw<T>(const GridDesc<T> &, const T *, const T *, const T *, const T *,     \
+                                              const T *, const T *, const T *, double *, double *, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST
