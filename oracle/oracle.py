@@ -33,12 +33,13 @@ _SIGS = {
     "ora_ras_tiles": (_i, [_i, _i, _d, _d, _D, _D, _D, _D, _d, _i, _i, _i, _i, _i, _i, _I, _i, _D, _D, _D, _D]),
     "ora_tile_count": (_i, [_i, _i, _i]),
     "ora_mg_levels": (_i, [_i, _i, _i, _i]),
-    "ora_mg_sweeps": (_i, [_i, _d, _i]),
+    "ora_mg_sweeps": (_i, [_i, _d, _i, _i]),
     "ora_mg_prolong_add": (None, [_i, _i, _D, _D, _D, _D]),
     "ora_mg_restrict": (None, [_i, _i, _D, _D, _D, _D]),
     "ora_dense_solve": (_i, [_i, _i, _d, _d, _D, _D, _D, _D, _D, _D]),
-    "ora_vcycle": (_i, [_i, _i, _d, _d, _D, _D, _D, _D, _i, _i, _i, _i, _d, _i, _d, _i, _i, _i, _i, _u64, _i, _D, _D]),
-    "ora_mg_solve": (_i, [_i, _i, _d, _d, _D, _D, _D, _D, _D, _i, _i, _i, _i, _d, _i, _d, _i, _i, _i, _i, _u64,
+    "ora_vcycle": (_i, [_i, _i, _d, _d, _D, _D, _D, _D, _i, _i, _i, _i, _d, _i, _i, _d, _i, _i, _i, _i, _u64, _D,
+                        _D]),
+    "ora_mg_solve": (_i, [_i, _i, _d, _d, _D, _D, _D, _D, _D, _i, _i, _i, _i, _d, _i, _i, _d, _i, _i, _i, _i, _u64,
                           _d, _i, _D, _D, _D, _D]),
 }
 
@@ -200,8 +201,8 @@ def mg_levels(nx, ny, max_levels, coarsest):
     return int(lib().ora_mg_levels(nx, ny, max_levels, coarsest))
 
 
-def mg_sweeps(nu0, growth, level):
-    return int(lib().ora_mg_sweeps(nu0, growth, level))
+def mg_sweeps(nu0, growth, level, nu_max=0):
+    return int(lib().ora_mg_sweeps(nu0, growth, level, nu_max))
 
 
 def mg_prolong_add(nxf, nyf, cx, cy, fx, fy):
@@ -233,6 +234,7 @@ class MG:
     nu_pre: int = 5
     nu_post: int = 5
     growth: float = 2.5
+    nu_max: int = 0
     variant: int = 0
     omega: float = 0.3
     ti: int = 32
@@ -242,14 +244,14 @@ class MG:
     seed: int = 0
 
     def args(self):
-        return (self.max_levels, self.coarsest, self.nu_pre, self.nu_post, self.growth, self.variant, self.omega,
-                self.ti, self.tj, self.k, self.overlap, self.seed & (2**64 - 1))
+        return (self.max_levels, self.coarsest, self.nu_pre, self.nu_post, self.growth, self.nu_max, self.variant,
+                self.omega, self.ti, self.tj, self.k, self.overlap, self.seed & (2**64 - 1))
 
 
-def vcycle(g: Grid, bx, by, mg: MG, vx=None, vy=None, cycle=0):
+def vcycle(g: Grid, bx, by, mg: MG, vx=None, vy=None):
     vx = g.zeros_vx() if vx is None else _f64(vx).copy()
     vy = g.zeros_vy() if vy is None else _f64(vy).copy()
-    st = lib().ora_vcycle(*g.head, _p(_f64(bx)), _p(_f64(by)), *mg.args(), cycle, _p(vx), _p(vy))
+    st = lib().ora_vcycle(*g.head, _p(_f64(bx)), _p(_f64(by)), *mg.args(), _p(vx), _p(vy))
     if st != 0:
         raise ValueError("ora_vcycle failed")
     return vx, vy

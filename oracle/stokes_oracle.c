@@ -499,7 +499,11 @@ void ora_energy(int nx, int ny, double hx, double hy, const double *eta_c, const
  *    mirror ghosts (free slip) for the tangential direction, zero walls;
  *  - restriction R = P^T / 4 (the adjoint of P, rows summing to one inside);
  *  - the coarsest level is solved exactly (dense Cholesky of -M);
- *  - level l runs ceil(nu_pre g^l) pre- and ceil(nu_post g^l) post-sweeps. */
+ *  - level l runs ceil(nu_pre g^l) pre- and ceil(nu_post g^l) post-sweeps
+ *    (Sec. 6.2), each capped at nu_max when nu_max > 0;
+ *  - a RAS smoother on level l, phase ph (0 pre, 1 post) draws its tile
+ *    shifts from SplitMix64 seeded with splitmix64(seed, 2 l + ph): the same
+ *    in every cycle, so one V-cycle is one fixed linear map. */
 
 typedef struct {
     int nx, ny;
@@ -560,12 +564,13 @@ int ora_mg_levels(int nx, int ny, int max_levels, int coarsest)
     return L;
 }
 
-/* sweeps on level l: ceil(nu0 * growth^l) */
-int ora_mg_sweeps(int nu0, double growth, int l)
+/* sweeps on level l: ceil(nu0 * growth^l), capped at nu_max when nu_max > 0 */
+int ora_mg_sweeps(int nu0, double growth, int l, int nu_max)
 {
     double f = (double)nu0;
     for (int q = 0; q < l; ++q) f *= growth;
-    return (int)ceil(f);
+    int nu = (int)ceil(f);
+    return (nu_max > 0 && nu > nu_max) ? nu_max : nu;
 }
 
 /* 1D interpolation weights of the prolongation.
@@ -750,6 +755,7 @@ typedef struct {
     int variant, ti, tj, k, overlap;
     double omega;
     uint64_t seed;
+    int nu_max;
 } smoother_t;
 
 static void run_smoother(const level_t *lv, const smoother_t *sm, const double *bx, const double *by, int sweeps,
@@ -784,7 +790,7 @@ static void residual(const level_t *lv, const double *bx, const double *by, cons
 }
 
 static int vcycle_rec(level_t *lv, int L, int l, const smoother_t *sm, int nu_pre, int nu_post, double growth,
-                      int cycle, const double *bx, const double *by, double *vx, double *vy)
+                      const double *bx, const double *by, double *vx, double *vy)
 {
     level_t *F = &lv[l];
     if (l == L - 1) {
@@ -799,8 +805,8 @@ static int vcycle_rec(level_t *lv, int L, int l, const smoother_t *sm, int nu_pr
         free(ex); free(ey); free(rx); free(ry);
         return st;
     }
-    uint64_t base = ((uint64_t)cycle * (uint64_t)L + (uint64_t)l) * 2u;
-    run_smoother(F, sm, bx, by, ora_mg_sweeps(nu_pre, growth, l), base, vx, vy);
+    uint64_t base = (uint64_t)l * 2u;
+    run_smoother(F, sm, bx, by, ora_mg_sweeps(nu_pre, growth, l, sm->nu_max), base, vx, vy);
     level_t *C = &lv[l + 1];
     size_t fnx = (size_t)F->ny * (F->nx + 1), fny = (size_t)(F->ny + 1) * F->nx;
     size_t cnx = (size_t)C->ny * (C->nx + 1), cny = (size_t)(C->ny + 1) * C->nx;
@@ -809,28 +815,25 @@ static int vcycle_rec(level_t *lv, int L, int l, const smoother_t *sm, int nu_pr
     double *cvx = calloc(cnx, sizeof(double)), *cvy = calloc(cny, sizeof(double));
     residual(F, bx, by, vx, vy, rx, ry);
     mg_restrict(F, C, rx, ry, cbx, cby);
-    int st = vcycle_rec(lv, L, l + 1, sm, nu_pre, nu_post, growth, cycle, cbx, cby, cvx, cvy);
+    int st = vcycle_rec(lv, L, l + 1, sm, nu_pre, nu_post, growth, cbx, cby, cvx, cvy);
     mg_prolong_add(F, C, cvx, cvy, vx, vy);
-    run_smoother(F, sm, bx, by, ora_mg_sweeps(nu_post, growth, l), base + 1u, vx, vy);
+    run_smoother(F, sm, bx, by, ora_mg_sweeps(nu_post, growth, l, sm->nu_max), base + 1u, vx, vy);
     free(rx); free(ry); free(cbx); free(cby); free(cvx); free(cvy);
     return st;
 }
 
-/* One V-cycle for M v = b, improving (vx, vy) in place.  `cycle` numbers the
- * cycle within a solve; RAS smoothing on level l, phase ph (0 pre, 1 post)
- * draws its tile shifts from SplitMix64 with seed
- * splitmix64(seed, 2 (cycle L + l) + ph).  Returns 0, or -1 if the coarsest
+/* One V-cycle for M v = b, improving (vx, vy) in place (the shift seeds are
+ * described at the top of this section).  Returns 0, or -1 if the coarsest
  * matrix is not positive definite / the arguments are bad. */
 int ora_vcycle(int nx, int ny, double hx, double hy, const double *eta_c, const double *eta_n, const double *bx,
-               const double *by, int max_levels, int coarsest, int nu_pre, int nu_post, double growth,
-               int variant, double omega, int ti, int tj, int k, int overlap, uint64_t seed, int cycle,
-               double *vx, double *vy)
+               const double *by, int max_levels, int coarsest, int nu_pre, int nu_post, double growth, int nu_max,
+               int variant, double omega, int ti, int tj, int k, int overlap, uint64_t seed, double *vx, double *vy)
 {
     if (max_levels < 1 || max_levels > 32) return -1;
     level_t lv[32];
     int L = mg_build(nx, ny, hx, hy, eta_c, eta_n, max_levels, coarsest, lv);
-    smoother_t sm = {variant, ti, tj, k, overlap, omega, seed};
-    int st = vcycle_rec(lv, L, 0, &sm, nu_pre, nu_post, growth, cycle, bx, by, vx, vy);
+    smoother_t sm = {variant, ti, tj, k, overlap, omega, seed, nu_max};
+    int st = vcycle_rec(lv, L, 0, &sm, nu_pre, nu_post, growth, bx, by, vx, vy);
     mg_free(lv, L);
     return st;
 }
@@ -861,13 +864,14 @@ static double energy_v(const level_t *lv, const double *fx, const double *fy, co
  * or -1 on failure; *final_e receives the last E_v. */
 int ora_mg_solve(int nx, int ny, double hx, double hy, const double *eta_c, const double *eta_n, const double *fx,
                  const double *fy, const double *p, int max_levels, int coarsest, int nu_pre, int nu_post,
-                 double growth, int variant, double omega, int ti, int tj, int k, int overlap, uint64_t seed,
-                 double tol, int max_cycles, double *vx, double *vy, double *final_e, double *history)
+                 double growth, int nu_max, int variant, double omega, int ti, int tj, int k, int overlap,
+                 uint64_t seed, double tol, int max_cycles, double *vx, double *vy, double *final_e,
+                 double *history)
 {
     if (max_levels < 1 || max_levels > 32) return -1;
     level_t lv[32];
     int L = mg_build(nx, ny, hx, hy, eta_c, eta_n, max_levels, coarsest, lv);
-    smoother_t sm = {variant, ti, tj, k, overlap, omega, seed};
+    smoother_t sm = {variant, ti, tj, k, overlap, omega, seed, nu_max};
     size_t snx = (size_t)ny * (nx + 1), sny = (size_t)(ny + 1) * nx;
     double *bx = malloc(snx * sizeof(double)), *by = malloc(sny * sizeof(double));
     double *rx = malloc(snx * sizeof(double)), *ry = malloc(sny * sizeof(double));
@@ -882,7 +886,7 @@ int ora_mg_solve(int nx, int ny, double hx, double hy, const double *eta_c, cons
         if (e <= tol || c >= max_cycles) break;
         memset(ex, 0, snx * sizeof(double));
         memset(ey, 0, sny * sizeof(double));
-        if (vcycle_rec(lv, L, 0, &sm, nu_pre, nu_post, growth, c, rx, ry, ex, ey)) { st = -1; break; }
+        if (vcycle_rec(lv, L, 0, &sm, nu_pre, nu_post, growth, rx, ry, ex, ey)) { st = -1; break; }
         for (size_t q = 0; q < snx; ++q) vx[q] += ex[q];
         for (size_t q = 0; q < sny; ++q) vy[q] += ey[q];
         ++c;

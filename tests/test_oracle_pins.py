@@ -427,6 +427,7 @@ def test_mg_level_count_and_sweeps(ora):
     assert ora.mg_levels(64, 48, 2, 16) == 2
     # Sec. 6.2: five sweeps on the finest level, times 2.5 per coarser level
     assert [ora.mg_sweeps(5, 2.5, l) for l in range(4)] == [5, 13, 32, 79]
+    assert [ora.mg_sweeps(5, 2.5, l, 40) for l in range(5)] == [5, 13, 32, 40, 40]
 
 
 def test_restriction_is_scaled_adjoint_of_prolongation(ora):
