@@ -493,8 +493,12 @@ void ora_energy(int nx, int ny, double hx, double hy, const double *eta_c, const
  * level; the transfer operators below are this implementation's reading:
  *  - coarsening halves nx and ny while both are even and larger than
  *    `coarsest`, up to `max_levels` levels;
- *  - coarse eta_c = mean of its four children, coarse eta_n = the coincident
- *    fine node; the coarse operator is the same stencil on the coarse grid;
+ *  - coarse eta_c = mean of its four children; coarse eta_n at an interior
+ *    node = full-weighting mean of the 3 x 3 fine nodes around the coincident
+ *    fine node (weights 4 centre, 2 edges, 1 corners, over 16), boundary
+ *    nodes 0 (injecting eta_n makes the coarse operator too soft next to
+ *    stiff inclusions and the cycle diverges at high viscosity contrast);
+ *    the coarse operator is the same stencil on the coarse grid;
  *  - prolongation P: bilinear interpolation in the staggered coordinates,
  *    mirror ghosts (free slip) for the tangential direction, zero walls;
  *  - restriction R = P^T / 4 (the adjoint of P, rows summing to one inside);
@@ -537,8 +541,19 @@ static int mg_build(int nx, int ny, double hx, double hy, const double *eta_c, c
                 c->eta_c[J * c->nx + I] = 0.25 * s;
             }
         for (int J = 0; J <= c->ny; ++J)
-            for (int I = 0; I <= c->nx; ++I)
-                c->eta_n[J * (c->nx + 1) + I] = f->eta_n[(2 * J) * (f->nx + 1) + 2 * I];
+            for (int I = 0; I <= c->nx; ++I) {
+                double v = 0.0;
+                if (I >= 1 && I <= c->nx - 1 && J >= 1 && J <= c->ny - 1) {
+                    const double *e = f->eta_n;
+                    int fn = f->nx + 1, j = 2 * J, i = 2 * I;
+                    double centre = e[j * fn + i];
+                    double edges = e[(j - 1) * fn + i] + e[(j + 1) * fn + i] + e[j * fn + i - 1] + e[j * fn + i + 1];
+                    double corners = e[(j - 1) * fn + i - 1] + e[(j - 1) * fn + i + 1] + e[(j + 1) * fn + i - 1]
+                                     + e[(j + 1) * fn + i + 1];
+                    v = (4.0 * centre + 2.0 * edges + corners) / 16.0;
+                }
+                c->eta_n[J * (c->nx + 1) + I] = v;
+            }
         ++L;
     }
     return L;

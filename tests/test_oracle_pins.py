@@ -481,6 +481,42 @@ def test_vcycle_single_level_is_exact_solve(ora):
     np.testing.assert_allclose(vy, dy, atol=1e-12 * np.abs(dy).max())
 
 
+def test_coarse_viscosity_restriction(ora):
+    """Coarse eta_c is the mean of the four children; coarse eta_n at an
+    interior node is the full-weighting mean of the 3 x 3 fine nodes: both
+    reproduce a viscosity that is linear in space exactly (checked through
+    the two-level hierarchy's coarsest dense solve of a constant-force problem
+    against the same solve with analytically coarsened viscosity)."""
+    nx = ny = 8
+    f = lambda x, y: 1.0 + 0.5 * x + 0.25 * y
+    h = 1.0 / nx
+    xc, yc = (np.arange(nx) + 0.5) * h, (np.arange(ny) + 0.5) * h
+    xn, yn = np.arange(nx + 1) * h, np.arange(ny + 1) * h
+    g = ora.Grid(nx, ny, h, h, f(xc[None, :], yc[:, None]), f(xn[None, :], yn[:, None]))
+    H = 2 * h
+    Xc, Yc = (np.arange(nx // 2) + 0.5) * H, (np.arange(ny // 2) + 0.5) * H
+    Xn, Yn = np.arange(nx // 2 + 1) * H, np.arange(ny // 2 + 1) * H
+    gc = ora.Grid(nx // 2, ny // 2, H, H, f(Xc[None, :], Yc[:, None]), f(Xn[None, :], Yn[:, None]))
+    bx, by = inputs.random_velocity(nx, ny, 5)
+    cbx, cby = ora.mg_restrict(nx, ny, bx, by)
+    # V-cycle with two levels and no smoothing = prolongated coarse solve
+    mg = ora.MG(max_levels=2, coarsest=4, nu_pre=0, nu_post=0, variant=0)
+    vx, vy = ora.vcycle(g, bx, by, mg)
+    ex, ey = ora.dense_solve(gc, cbx, cby)
+    px, py = ora.mg_prolong_add(nx, ny, ex, ey, g.zeros_vx(), g.zeros_vy())
+    np.testing.assert_allclose(vx, px, atol=1e-12 * np.abs(px).max())
+    np.testing.assert_allclose(vy, py, atol=1e-12 * np.abs(py).max())
+
+
+def test_vcycle_contracts_at_contrast_1e6(ora):
+    """The defect-correction iteration contracts on the 1e6-contrast sinker
+    (with injected node viscosity it diverges)."""
+    prob = inputs.sinker_problem(64, eta_in=1e6)
+    g = grid_from(ora, prob)
+    vx, vy, c, fe, hist = ora.mg_solve(g, prob.fx, prob.fy, None, ora.MG(nu_max=40, variant=0), 0.0, 12)
+    assert hist[-1] < 0.2 * hist[2] and np.all(np.isfinite(hist))
+
+
 @pytest.mark.parametrize("variant", [0, 3, 4])
 def test_vcycle_converges_to_dense_solution(ora, variant):
     """Constant-contrast-free case first: every cycle reduces the residual and
