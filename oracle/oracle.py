@@ -39,6 +39,8 @@ _SIGS = {
     "ora_dense_solve": (_i, [_i, _i, _d, _d, _D, _D, _D, _D, _D, _D]),
     "ora_vcycle": (_i, [_i, _i, _d, _d, _D, _D, _D, _D, _i, _i, _i, _i, _d, _i, _i, _d, _i, _i, _i, _i, _u64, _D,
                         _D]),
+    "ora_mg_fcg": (_i, [_i, _i, _d, _d, _D, _D, _D, _D, _D, _i, _i, _i, _i, _d, _i, _i, _d, _i, _i, _i, _i, _u64,
+                        _d, _i, _D, _D, _D, _D]),
     "ora_mg_solve": (_i, [_i, _i, _d, _d, _D, _D, _D, _D, _D, _i, _i, _i, _i, _d, _i, _i, _d, _i, _i, _i, _i, _u64,
                           _d, _i, _D, _D, _D, _D]),
 }
@@ -268,4 +270,18 @@ def mg_solve(g: Grid, fx, fy, p, mg: MG, tol, max_cycles, vx=None, vy=None):
                            ctypes.byref(fe), _p(hist))
     if c < 0:
         raise ValueError("ora_mg_solve failed")
+    return vx, vy, c, fe.value, hist[:c + 1].copy()
+
+
+def mg_fcg(g: Grid, fx, fy, p, mg: MG, tol, max_its, vx=None, vy=None):
+    """Flexible CG preconditioned by one V-cycle.  Returns (vx, vy, its, final_E, history)."""
+    vx = g.zeros_vx() if vx is None else _f64(vx).copy()
+    vy = g.zeros_vy() if vy is None else _f64(vy).copy()
+    fe = ctypes.c_double(0.0)
+    hist = np.zeros(max_its + 1)
+    p = None if p is None else _f64(p)
+    c = lib().ora_mg_fcg(*g.head, _p(_f64(fx)), _p(_f64(fy)), _p(p), *mg.args(), tol, max_its, _p(vx), _p(vy),
+                         ctypes.byref(fe), _p(hist))
+    if c < 0:
+        raise ValueError("ora_mg_fcg failed")
     return vx, vy, c, fe.value, hist[:c + 1].copy()

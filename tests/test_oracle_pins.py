@@ -543,3 +543,24 @@ def test_ras_tile_subset_matches_full_outer_iteration(ora):
     sub = ora.ras_tiles(g, bx, by, 0.3, ti, tj, k, o, si, sj, tiles, vx, vy, vx, vy)
     np.testing.assert_array_equal(sub[0], full[0])
     np.testing.assert_array_equal(sub[1], full[1])
+
+
+def test_flexible_cg_reaches_1e8_and_the_dense_solution(ora):
+    """Flexible CG with the V-cycle as preconditioner reaches E_v <= 1e-8 on the
+    1e6-contrast multi-sinker in far fewer cycles than plain defect
+    correction, and converges to the dense direct solution on a small grid."""
+    prob = inputs.multi_sinker(64, seed=3)
+    g = grid_from(ora, prob)
+    mg = ora.MG(nu_max=40, variant=0, seed=1)
+    vx, vy, its, fe, hist = ora.mg_fcg(g, prob.fx, prob.fy, None, mg, 1e-8, 80)
+    assert fe <= 1e-8 and its <= 60
+    _, _, c, fe_dc, _ = ora.mg_solve(g, prob.fx, prob.fy, None, mg, 1e-8, its)
+    assert fe_dc > 100 * fe
+    small = inputs.sinker_problem(32, eta_in=1e4)
+    gs = grid_from(ora, small)
+    vx, vy, its, fe, hist = ora.mg_fcg(gs, small.fx, small.fy, None, ora.MG(variant=4, ti=8, tj=8, k=2, overlap=0,
+                                                                          seed=2), 1e-12, 100)
+    dx, dy = ora.dense_solve(gs, small.fx, small.fy)
+    # the dense factorisation itself carries cond(M) * eps ~ 1e-8 of error here
+    np.testing.assert_allclose(vx, dx, atol=1e-7 * np.abs(dx).max())
+    np.testing.assert_allclose(vy, dy, atol=1e-7 * np.abs(dy).max())
