@@ -122,22 +122,32 @@ typedef struct {
  * levels      maximum number of levels; coarsening halves nx and ny while both are
  *             even and larger than `coarsest`.
  * coarsest    stop coarsening at this size (cells per side); the coarsest level is
- *             solved exactly with a dense FP64 factorisation, so it must have at
- *             most 4096 unknowns.
- * nu_pre, nu_post, nu_growth   level l runs ceil(nu_pre nu_growth^l) pre- and
- *             ceil(nu_post nu_growth^l) post-sweeps (5, 5, 2.5 in Sec. 6.2).
+ *             solved exactly with a dense FP64 inverse of -M computed on the GPU,
+ *             so it must have at most 1024 unknowns.
+ * nu_pre, nu_post, nu_growth, nu_max   level l runs ceil(nu_pre nu_growth^l) pre- and
+ *             ceil(nu_post nu_growth^l) post-sweeps (5, 5, 2.5 in Sec. 6.2), each
+ *             capped at nu_max when nu_max > 0.
  * inner_dtype stokes_dtype of the V-cycle (smoothing, restriction, prolongation);
  *             the residual and the update of v stay in the context's dtype.
- * smoother    smoother of every level (tile/k/overlap/omega/seed; sweeps ignored).
+ * smoother    smoother of every level (variant, tiles, k, overlap, omega, seed;
+ *             `sweeps`, `shift_mode` and `shifts` are ignored: a RAS smoother on
+ *             level l, phase ph (0 pre, 1 post) draws SplitMix64 shifts seeded
+ *             with output 2 l + ph of SplitMix64(seed), the same in every cycle).
+ * krylov      0: defect correction, v += B (f - G p - M v) per cycle; 1: flexible
+ *             conjugate gradients (one-term recurrence) with B as the
+ *             preconditioner, which keeps converging at high viscosity
+ *             contrast where defect correction stagnates.  B is one V-cycle.
  * tol         stop when the relative velocity energy residual E_v <= tol.
- * max_cycles  at most this many V-cycles. */
+ * max_cycles  at most this many V-cycles (applications of B). */
 typedef struct {
     int levels;
     int coarsest;
     int nu_pre, nu_post;
     double nu_growth;
+    int nu_max;
     int inner_dtype;
     stokes_smooth_params smoother;
+    int krylov;
     double tol;
     int max_cycles;
 } stokes_mg_params;
@@ -183,14 +193,21 @@ int stokes_smooth(stokes_ctx *ctx, void *vx, void *vy, const void *p, const stok
  * The summation order is fixed, so repeated calls give identical bits. */
 int stokes_residual_energy_norm(stokes_ctx *ctx, const void *vx, const void *vy, const void *p, double out[3]);
 
-/* Solve M v = f - G p by defect correction with geometric-multigrid V-cycles
- * (Sec. 3.2): repeat { r = f - G p - M v in the context dtype; stop when
- * E_v = sqrt(sum r^2/(-diag M) / sum f^2/(-diag M)) <= tol; e = V-cycle(r) in
- * params->inner_dtype from e = 0; v += e }.  Improves (vx, vy) in place.
+/* Solve M v = f - G p with a geometric-multigrid V-cycle B (Sec. 3.2) as the
+ * preconditioner of an outer iteration in the context's dtype: the residual
+ * r = f - G p - M v, the energy residual E_v = sqrt(sum r^2/(-diag M) /
+ * sum f^2/(-diag M)) and the update of v stay in the context's dtype, while
+ * B (smoothing, restriction, prolongation) runs in params->inner_dtype from a
+ * zero guess; the outer iteration is defect correction (v += B r) or flexible
+ * CG (params->krylov).  Stops when E_v <= tol.  Improves (vx, vy) in place.
  * *final_rel_resid receives the last E_v and *cycles the number of V-cycles
  * (either may be NULL).  Returns STOKES_ERR_NOT_CONVERGED when max_cycles
- * is reached above tol, STOKES_ERR_DIVERGED on NaN/Inf or growth.  The V-cycle
- * body is captured once as a CUDA graph and replayed.  Synchronises. */
+ * is reached above tol, STOKES_ERR_DIVERGED on NaN/Inf or growth of E_v beyond
+ * 1e6 times its first value.  The hierarchy is built on the first call after
+ * stokes_set_viscosity (or after a change of levels, coarsest or inner_dtype).
+ * The V-cycle is captured once as a CUDA graph (on context-owned work
+ * buffers) and replayed on a context-owned stream ordered after the context's
+ * stream.  Synchronises. */
 int stokes_vcycle(stokes_ctx *ctx, void *vx, void *vy, const void *p, const stokes_mg_params *params,
                   double *final_rel_resid, int *cycles);
 

@@ -55,8 +55,9 @@ class stokes_smooth_params(ctypes.Structure):
 
 class stokes_mg_params(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("coarsest", ctypes.c_int), ("nu_pre", ctypes.c_int),
-                ("nu_post", ctypes.c_int), ("nu_growth", ctypes.c_double), ("inner_dtype", ctypes.c_int),
-                ("smoother", stokes_smooth_params), ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int)]
+                ("nu_post", ctypes.c_int), ("nu_growth", ctypes.c_double), ("nu_max", ctypes.c_int),
+                ("inner_dtype", ctypes.c_int), ("smoother", stokes_smooth_params), ("krylov", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int)]
 
 
 _VP, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
@@ -163,6 +164,16 @@ def smooth_params(variant="ras", sweeps=1, tile=(32, 32), k=4, overlap=None, ome
         p._shifts_keepalive = arr
         p.shifts = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
     return p
+
+
+def mg_params(levels=16, coarsest=16, nu_pre=5, nu_post=5, nu_growth=2.5, nu_max=0, inner="f32", krylov=True,
+              tol=1e-8, max_cycles=100, **smoother):
+    """Build a stokes_mg_params (Sec. 6.2 defaults: 5/5 sweeps, growth 2.5)."""
+    smoother.setdefault("variant", "ras")
+    sm = smooth_params(**smoother)
+    inner_code = STOKES_F64 if inner in ("f64", "float64") else STOKES_F32
+    return stokes_mg_params(levels, coarsest, nu_pre, nu_post, nu_growth, nu_max, inner_code, sm,
+                            1 if krylov else 0, tol, max_cycles)
 
 
 def stokes_smooth(ctx, vx, vy, p, params):
@@ -309,6 +320,10 @@ class StokesContext:
 
     def synchronize(self):
         stokes_synchronize(self.ctx)
+
+    def vcycle(self, vx, vy, p=None, **kw):
+        """Defect-correction multigrid solve; returns (status, E_v, cycles)."""
+        return stokes_vcycle(self.ctx, vx, vy, p, mg_params(**kw))
 
     def profile_reset(self, timing=False):
         stokes_profile_reset(self.ctx, timing)

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
+
 namespace stokes {
 
 // Geometry and coefficients of one grid level, passed by value to kernels.
@@ -111,5 +113,27 @@ int ras_max_smem();
 // SplitMix64 (Steele, Lea & Flood 2014): output c (from 0) of the generator
 // seeded with `seed`.
 uint64_t splitmix64(uint64_t seed, uint64_t c);
+
+// ---- smoother schedules (smooth.cu) ---------------------------------------
+// Where kernel launches go: counts (and, for a context with timing on, times)
+// each launch group of `nk` kernels of class `kind` (stokes_kernel_class).
+struct LaunchHook {
+    virtual int run(int kind, int nk, const std::function<cudaError_t()> &launch) = 0;
+    virtual ~LaunchHook() = default;
+};
+
+// One smoothing call (the fields of stokes_smooth_params, tiles resolved).
+struct SmoothSpec {
+    int variant, sweeps, ti, tj, k, overlap, shift_mode;
+    double omega;
+    uint64_t seed;
+    const int32_t *shifts;
+};
+
+// Smooth M v = b in place on (vx, vy) with the coefficients `k` (b included),
+// ping-ponging through the scratch pair (sx, sy).  Returns a stokes_status.
+template <typename T>
+int smooth_buffers(const GridDesc<T> &g, const Coeffs<T> &k, T *vx, T *vy, T *sx, T *sy, const SmoothSpec &p,
+                   const RasRun &run, cudaStream_t s, LaunchHook &hook);
 
 } // namespace stokes

@@ -1,0 +1,203 @@
+// krylov.cu -- vector kernels of the outer solve around the multigrid cycle:
+// fused updates and inner products over the velocity unknowns (FP64
+// accumulation, fixed reduction order) for flexible CG and defect correction.
+#include "../../include/stokes.h"
+#include "internal.h"
+#include "mg.h"
+#include "stencil.cuh"
+
+namespace stokes {
+
+namespace {
+
+constexpr int RD_THREADS = 256;
+constexpr int RD_BLOCKS = 152 * 4;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-reduce two sums and write them to partials[2 * blockIdx.x + {0, 1}].
+__device__ __forceinline__ void block_store2(double s0, double s1, double *partials)
+{
+    __shared__ double sh[2][RD_THREADS / 32];
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][wid] = s0;
+        sh[1][wid] = s1;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double s = 0.0;
+        for (int q = 0; q < RD_THREADS / 32; ++q) s += sh[threadIdx.x][q];
+        partials[2 * blockIdx.x + threadIdx.x] = s;
+    }
+}
+
+// Visit every velocity unknown once: f(q, component) with q the element offset.
+template <class F>
+__device__ __forceinline__ void for_unknowns(int nx, int ny, int pitch, F &&f)
+{
+    const long w = (long)nx + 1, total = w * (long)(ny + 1);
+    for (long t = (long)blockIdx.x * RD_THREADS + threadIdx.x; t < total; t += (long)gridDim.x * RD_THREADS) {
+        const int j = (int)(t / w), i = (int)(t - (long)j * w);
+        const size_t q = (size_t)j * pitch + i;
+        if (j < ny && i >= 1 && i <= nx - 1) f(q, 0);
+        if (i < nx && j >= 1 && j <= ny - 1) f(q, 1);
+    }
+}
+
+// (<a, b>, <a, c>)
+template <typename T>
+__global__ void __launch_bounds__(RD_THREADS) k_dot2(int nx, int ny, int pitch, const T *__restrict__ ax,
+                                                     const T *__restrict__ ay, const T *__restrict__ bx,
+                                                     const T *__restrict__ by, const T *__restrict__ cx,
+                                                     const T *__restrict__ cy, double *__restrict__ partials)
+{
+    double s0 = 0.0, s1 = 0.0;
+    for_unknowns(nx, ny, pitch, [&](size_t q, int comp) {
+        const double a = (double)(comp ? ay[q] : ax[q]);
+        s0 = fma(a, (double)(comp ? by[q] : bx[q]), s0);
+        if (cx) s1 = fma(a, (double)(comp ? cy[q] : cx[q]), s1);
+    });
+    block_store2(s0, s1, partials);
+}
+
+// (sum r^2 w, sum f^2 w) with w = -1/diag(M)
+template <typename T>
+__global__ void __launch_bounds__(RD_THREADS) k_energy_r(int nx, int ny, int pitch, const T *__restrict__ rx,
+                                                         const T *__restrict__ ry, const T *__restrict__ fx,
+                                                         const T *__restrict__ fy, const T *__restrict__ ix,
+                                                         const T *__restrict__ iy, double *__restrict__ partials)
+{
+    double s0 = 0.0, s1 = 0.0;
+    for_unknowns(nx, ny, pitch, [&](size_t q, int comp) {
+        const double wgt = -(double)(comp ? iy[q] : ix[q]);
+        const double r = (double)(comp ? ry[q] : rx[q]), f = (double)(comp ? fy[q] : fx[q]);
+        s0 = fma(r * r, wgt, s0);
+        s1 = fma(f * f, wgt, s1);
+    });
+    block_store2(s0, s1, partials);
+}
+
+// v += a p, r -= a q; returns (sum r_new^2 w, 0)
+template <typename T>
+__global__ void __launch_bounds__(RD_THREADS) k_cg_update(int nx, int ny, int pitch, double a, const T *__restrict__ px,
+                                                          const T *__restrict__ py, const T *__restrict__ qx,
+                                                          const T *__restrict__ qy, T *__restrict__ vx,
+                                                          T *__restrict__ vy, T *__restrict__ rx, T *__restrict__ ry,
+                                                          const T *__restrict__ ix, const T *__restrict__ iy,
+                                                          double *__restrict__ partials)
+{
+    const T at = (T)a;
+    double s0 = 0.0;
+    for_unknowns(nx, ny, pitch, [&](size_t q, int comp) {
+        T *v = comp ? vy : vx;
+        T *r = comp ? ry : rx;
+        v[q] = r_fma(at, (comp ? py : px)[q], v[q]);
+        const T rn = r_fma(-at, (comp ? qy : qx)[q], r[q]);
+        r[q] = rn;
+        s0 = fma((double)rn * (double)rn, -(double)(comp ? iy[q] : ix[q]), s0);
+    });
+    block_store2(s0, 0.0, partials);
+}
+
+// p = z + beta p at the unknowns
+template <typename T>
+__global__ void __launch_bounds__(RD_THREADS) k_cg_direction(int nx, int ny, int pitch, double beta,
+                                                             const T *__restrict__ zx, const T *__restrict__ zy,
+                                                             T *__restrict__ px, T *__restrict__ py)
+{
+    const T bt = (T)beta;
+    for_unknowns(nx, ny, pitch, [&](size_t q, int comp) {
+        T *p = comp ? py : px;
+        p[q] = r_fma(bt, p[q], (comp ? zy : zx)[q]);
+    });
+}
+
+// v += z at the unknowns
+template <typename T>
+__global__ void __launch_bounds__(RD_THREADS) k_add(int nx, int ny, int pitch, const T *__restrict__ zx,
+                                                    const T *__restrict__ zy, T *__restrict__ vx, T *__restrict__ vy)
+{
+    for_unknowns(nx, ny, pitch, [&](size_t q, int comp) {
+        T *v = comp ? vy : vx;
+        v[q] = r_add(v[q], (comp ? zy : zx)[q]);
+    });
+}
+
+__global__ void k_final2(const double *__restrict__ partials, int nblocks, double *__restrict__ out)
+{
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int b = lane; b < nblocks; b += 32) s += partials[2 * b + c];
+    s = warp_sum(s);
+    if (lane == 0) out[c] = s;
+}
+
+} // namespace
+
+int krylov_partials() { return RD_BLOCKS; }
+
+template <typename T>
+cudaError_t kry_dot2(const KrylovView &k, const T *ax, const T *ay, const T *bx, const T *by, const T *cx,
+                     const T *cy, cudaStream_t s)
+{
+    k_dot2<T><<<RD_BLOCKS, RD_THREADS, 0, s>>>(k.nx, k.ny, k.pitch, ax, ay, bx, by, cx, cy, k.partials);
+    k_final2<<<1, 64, 0, s>>>(k.partials, RD_BLOCKS, k.out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t kry_energy(const KrylovView &k, const T *rx, const T *ry, const T *fx, const T *fy, const T *ix,
+                       const T *iy, cudaStream_t s)
+{
+    k_energy_r<T><<<RD_BLOCKS, RD_THREADS, 0, s>>>(k.nx, k.ny, k.pitch, rx, ry, fx, fy, ix, iy, k.partials);
+    k_final2<<<1, 64, 0, s>>>(k.partials, RD_BLOCKS, k.out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t kry_update(const KrylovView &k, double a, const T *px, const T *py, const T *qx, const T *qy, T *vx,
+                       T *vy, T *rx, T *ry, const T *ix, const T *iy, cudaStream_t s)
+{
+    k_cg_update<T><<<RD_BLOCKS, RD_THREADS, 0, s>>>(k.nx, k.ny, k.pitch, a, px, py, qx, qy, vx, vy, rx, ry, ix, iy,
+                                                    k.partials);
+    k_final2<<<1, 64, 0, s>>>(k.partials, RD_BLOCKS, k.out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t kry_direction(const KrylovView &k, double beta, const T *zx, const T *zy, T *px, T *py, cudaStream_t s)
+{
+    k_cg_direction<T><<<RD_BLOCKS, RD_THREADS, 0, s>>>(k.nx, k.ny, k.pitch, beta, zx, zy, px, py);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t kry_add(const KrylovView &k, const T *zx, const T *zy, T *vx, T *vy, cudaStream_t s)
+{
+    k_add<T><<<RD_BLOCKS, RD_THREADS, 0, s>>>(k.nx, k.ny, k.pitch, zx, zy, vx, vy);
+    return cudaGetLastError();
+}
+
+#define INST(T)                                                                                                    \
+    template cudaError_t kry_dot2<T>(const KrylovView &, const T *, const T *, const T *, const T *, const T *,    \
+                                     const T *, cudaStream_t);                                                     \
+    template cudaError_t kry_energy<T>(const KrylovView &, const T *, const T *, const T *, const T *, const T *,  \
+                                       const T *, cudaStream_t);                                                   \
+    template cudaError_t kry_update<T>(const KrylovView &, double, const T *, const T *, const T *, const T *,     \
+                                       T *, T *, T *, T *, const T *, const T *, cudaStream_t);                    \
+    template cudaError_t kry_direction<T>(const KrylovView &, double, const T *, const T *, T *, T *,             \
+                                          cudaStream_t);                                                           \
+    template cudaError_t kry_add<T>(const KrylovView &, const T *, const T *, T *, T *, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+} // namespace stokes

@@ -1,0 +1,415 @@
+// mg_kernels.cu -- kernels of the geometric-multigrid V-cycle used for the
+// velocity solve of the inexact Uzawa method (Sec. 3.2, configuration in
+// Sec. 6.2): coarse viscosity, residual, restriction, prolongation, precision
+// casts and the dense FP64 coarsest solve.
+//
+// Transfer operators (the paper does not state them): bilinear prolongation
+// P in the staggered coordinates with mirror ghosts for the tangential
+// direction and zero walls; restriction R = P^T / 4.
+#include "../../include/stokes.h"
+#include "gstencil.cuh"
+#include "internal.h"
+#include "mg.h"
+
+namespace stokes {
+
+namespace {
+
+constexpr int BX = 32, BY = 8;
+inline dim3 grid2d(int w, int h) { return dim3((unsigned)((w + BX - 1) / BX), (unsigned)((h + BY - 1) / BY)); }
+
+// coarse eta_c = mean of the four children; coarse eta_n at an interior node =
+// full-weighting mean of the 3 x 3 fine nodes around the coincident node
+// (4 centre, 2 edges, 1 corners, over 16), 0 on boundary nodes.  Injecting
+// eta_n would make the coarse operator too soft next to stiff inclusions.
+template <typename T>
+__global__ void k_coarsen_eta(int ncx, int ncy, int fp, int cp, const T *__restrict__ fec, const T *__restrict__ fen,
+                              T *__restrict__ cec, T *__restrict__ cen)
+{
+    const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y;
+    if (I > ncx || J > ncy) return;
+    const size_t cq = (size_t)J * cp + I, f0 = (size_t)(2 * J) * fp + 2 * I;
+    if (I < ncx && J < ncy) {
+        const T s = r_add(r_add(r_add(fec[f0], fec[f0 + 1]), fec[f0 + fp]), fec[f0 + fp + 1]);
+        cec[cq] = r_mul(T(0.25), s);
+    }
+    T v = T(0);
+    if (I >= 1 && I <= ncx - 1 && J >= 1 && J <= ncy - 1) {
+        const T centre = fen[f0];
+        const T edges = r_add(r_add(r_add(fen[f0 - fp], fen[f0 + fp]), fen[f0 - 1]), fen[f0 + 1]);
+        const T corners = r_add(r_add(r_add(fen[f0 - fp - 1], fen[f0 - fp + 1]), fen[f0 + fp - 1]), fen[f0 + fp + 1]);
+        v = r_mul(r_add(r_add(r_mul(T(4), centre), r_mul(T(2), edges)), corners), T(0.0625));
+    }
+    cen[cq] = v;
+}
+
+template <typename Ts, typename Td>
+__global__ void k_cast(size_t n, const Ts *__restrict__ s, Td *__restrict__ d)
+{
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        d[t] = (Td)s[t];
+}
+
+// r = b - M v at unknowns, zero elsewhere (rows up to ny, columns up to nx)
+template <typename T>
+__global__ void k_residual(GridDesc<T> g, const T *__restrict__ ec, const T *__restrict__ en,
+                           const T *__restrict__ bx, const T *__restrict__ by, const T *__restrict__ vx,
+                           const T *__restrict__ vy, T *__restrict__ rx, T *__restrict__ ry)
+{
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i > g.nx || j > g.ny) return;
+    const size_t q = (size_t)j * g.pitch + i;
+    T m, d, vc;
+    if (j < g.ny) {
+        T r = T(0);
+        if (vx_unknown(g, j, i)) {
+            op_x(g, ec, en, vx, vy, j, i, m, d, vc);
+            r = r_sub(bx[q], m);
+        }
+        rx[q] = r;
+    }
+    if (i < g.nx) {
+        T r = T(0);
+        if (vy_unknown(g, j, i)) {
+            op_y(g, ec, en, vx, vy, j, i, m, d, vc);
+            r = r_sub(by[q], m);
+        }
+        ry[q] = r;
+    }
+}
+
+// Weights of one fine index a in the cell-centred direction: fine point at
+// coarse position (a - 1/2)/2, nearest coarse 3/4, next 1/4, mirrored at the
+// walls (nc coarse cells).
+__device__ __forceinline__ void w_cell(int a, int nc, int &A, int &B)
+{
+    A = a >> 1;
+    B = (a & 1) ? A + 1 : A - 1;
+    B = B < 0 ? 0 : (B > nc - 1 ? nc - 1 : B);
+}
+
+// fine += P coarse at the fine unknowns
+template <typename T>
+__global__ void k_prolong_add(int nfx, int nfy, int fp, int ncx, int ncy, int cp, const T *__restrict__ cx,
+                              const T *__restrict__ cy, T *__restrict__ fx, T *__restrict__ fy)
+{
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i > nfx || j > nfy) return;
+    const size_t q = (size_t)j * fp + i;
+    const T c34 = T(0.75), c14 = T(0.25), c12 = T(0.5);
+    if (j < nfy && i >= 1 && i <= nfx - 1) { // vx: cell-centred in y, node-centred in x
+        int A, B;
+        w_cell(j, ncy, A, B);
+        T s = T(0);
+        const int ys[2] = {A, B};
+        const T wy[2] = {c34, c14};
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const T *row = cx + (size_t)ys[a] * cp;
+            if ((i & 1) == 0) {
+                s = r_add(s, r_mul(r_mul(wy[a], T(1)), row[i >> 1]));
+            } else {
+                s = r_add(s, r_mul(r_mul(wy[a], c12), row[i >> 1]));
+                s = r_add(s, r_mul(r_mul(wy[a], c12), row[(i >> 1) + 1]));
+            }
+        }
+        fx[q] = r_add(fx[q], s);
+    }
+    if (i < nfx && j >= 1 && j <= nfy - 1) { // vy: node-centred in y, cell-centred in x
+        int A, B;
+        w_cell(i, ncx, A, B);
+        T s = T(0);
+        const int nrow = (j & 1) ? 2 : 1;
+        const int ys[2] = {j >> 1, (j >> 1) + 1};
+        const T wy[2] = {(j & 1) ? c12 : T(1), c12};
+        for (int a = 0; a < nrow; ++a) {
+            const T *row = cy + (size_t)ys[a] * cp;
+            s = r_add(s, r_mul(r_mul(wy[a], c34), row[A]));
+            s = r_add(s, r_mul(r_mul(wy[a], c14), row[B]));
+        }
+        fy[q] = r_add(fy[q], s);
+    }
+}
+
+// coarse b = P^T r / 4 at the coarse unknowns (gather form), zero elsewhere
+template <typename T>
+__global__ void k_restrict(int nfx, int nfy, int fp, int ncx, int ncy, int cp, const T *__restrict__ rx,
+                           const T *__restrict__ ry, T *__restrict__ bx, T *__restrict__ by)
+{
+    const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y;
+    if (I > ncx || J > ncy) return;
+    const size_t cq = (size_t)J * cp + I;
+    const T c34 = T(0.75), c14 = T(0.25), c12 = T(0.5);
+    if (J < ncy) { // vx
+        T s = T(0);
+        if (I >= 1 && I <= ncx - 1) {
+            // fine rows (cell-centred in y) and their weights toward coarse row J
+            int rows[4];
+            T wr[4];
+            int nr = 0;
+            if (J >= 1) { rows[nr] = 2 * J - 1; wr[nr++] = c14; }
+            rows[nr] = 2 * J; wr[nr++] = J == 0 ? T(1) : c34;
+            rows[nr] = 2 * J + 1; wr[nr++] = J == ncy - 1 ? T(1) : c34;
+            if (J + 1 <= ncy - 1) { rows[nr] = 2 * J + 2; wr[nr++] = c14; }
+            for (int a = 0; a < nr; ++a) {
+                const T *row = rx + (size_t)rows[a] * fp;
+                s = r_add(s, r_mul(r_mul(wr[a], c12), row[2 * I - 1]));
+                s = r_add(s, r_mul(wr[a], row[2 * I]));
+                s = r_add(s, r_mul(r_mul(wr[a], c12), row[2 * I + 1]));
+            }
+            s = r_mul(c14, s);
+        }
+        bx[cq] = s;
+    }
+    if (I < ncx) { // vy
+        T s = T(0);
+        if (J >= 1 && J <= ncy - 1) {
+            int cols[4];
+            T wc[4];
+            int nc = 0;
+            if (I >= 1) { cols[nc] = 2 * I - 1; wc[nc++] = c14; }
+            cols[nc] = 2 * I; wc[nc++] = I == 0 ? T(1) : c34;
+            cols[nc] = 2 * I + 1; wc[nc++] = I == ncx - 1 ? T(1) : c34;
+            if (I + 1 <= ncx - 1) { cols[nc] = 2 * I + 2; wc[nc++] = c14; }
+            const int rows[3] = {2 * J - 1, 2 * J, 2 * J + 1};
+            const T wr[3] = {c12, T(1), c12};
+            for (int a = 0; a < 3; ++a) {
+                const T *row = ry + (size_t)rows[a] * fp;
+                for (int b = 0; b < nc; ++b) s = r_add(s, r_mul(r_mul(wr[a], wc[b]), row[cols[b]]));
+            }
+            s = r_mul(c14, s);
+        }
+        by[cq] = s;
+    }
+}
+
+// ---- dense coarsest solve --------------------------------------------------
+// Unknown numbering: vx unknowns row-major (j, i = 1..nx-1), then vy unknowns
+// row-major (j = 1..ny-1, i).
+__device__ __forceinline__ void unknown_pos(int u, int nx, int ny, int &comp, int &j, int &i)
+{
+    const int nvx = ny * (nx - 1);
+    if (u < nvx) {
+        comp = 0;
+        j = u / (nx - 1);
+        i = u - j * (nx - 1) + 1;
+    } else {
+        u -= nvx;
+        comp = 1;
+        j = u / nx + 1;
+        i = u - (j - 1) * nx;
+    }
+}
+
+// A[r][c] = -(M e_c)_r in FP64 from the level's viscosity (boundary nodes of
+// eta_n hold zero)
+template <typename T>
+__global__ void k_assemble(int nx, int ny, int pitch, double ihx, double ihy, const T *__restrict__ ec,
+                           const T *__restrict__ en, int n, double *__restrict__ A)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)n * n) return;
+    const int r = (int)(t / n), c = (int)(t - (long)r * n);
+    int rc, rj, ri, cc, cj, ci;
+    unknown_pos(r, nx, ny, rc, rj, ri);
+    unknown_pos(c, nx, ny, cc, cj, ci);
+    // value of the unit vector e_c at (component, j, i)
+    auto ux = [&](int j, int i) { return (cc == 0 && cj == j && ci == i) ? 1.0 : 0.0; };
+    auto uy = [&](int j, int i) { return (cc == 1 && cj == j && ci == i) ? 1.0 : 0.0; };
+    auto EC = [&](int j, int i) { return (double)ec[(size_t)j * pitch + i]; };
+    auto EN = [&](int j, int i) { return (double)en[(size_t)j * pitch + i]; };
+    double m;
+    if (rc == 0) {
+        const int j = rj, i = ri;
+        const double txe = 2.0 * EC(j, i) * (ux(j, i + 1) - ux(j, i)) * ihx;
+        const double txw = 2.0 * EC(j, i - 1) * (ux(j, i) - ux(j, i - 1)) * ihx;
+        const double sn = EN(j + 1, i) * ((ux(j + 1, i) - ux(j, i)) * ihy + (uy(j + 1, i) - uy(j + 1, i - 1)) * ihx);
+        const double ss = EN(j, i) * ((ux(j, i) - ux(j - 1, i)) * ihy + (uy(j, i) - uy(j, i - 1)) * ihx);
+        m = (txe - txw) * ihx + (sn - ss) * ihy;
+    } else {
+        const int j = rj, i = ri;
+        const double tyn = 2.0 * EC(j, i) * (uy(j + 1, i) - uy(j, i)) * ihy;
+        const double tys = 2.0 * EC(j - 1, i) * (uy(j, i) - uy(j - 1, i)) * ihy;
+        const double se = EN(j, i + 1) * ((ux(j, i + 1) - ux(j - 1, i + 1)) * ihy + (uy(j, i + 1) - uy(j, i)) * ihx);
+        const double sw = EN(j, i) * ((ux(j, i) - ux(j - 1, i)) * ihy + (uy(j, i) - uy(j, i - 1)) * ihx);
+        m = (se - sw) * ihx + (tyn - tys) * ihy;
+    }
+    A[(size_t)r * n + c] = -m;
+}
+
+// In-place Cholesky A = L L^T (lower triangle) by one CTA; status = 1 if a
+// pivot is not positive.
+__global__ void k_cholesky(int n, double *__restrict__ A, int *__restrict__ status)
+{
+    __shared__ double piv;
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (threadIdx.x == 0) {
+            const double d = A[(size_t)k * n + k];
+            if (!(d > 0.0)) bad = 1;
+            piv = d > 0.0 ? sqrt(d) : 1.0;
+            A[(size_t)k * n + k] = piv;
+        }
+        __syncthreads();
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[(size_t)i * n + k] /= piv;
+        __syncthreads();
+        const int m = n - k - 1; // trailing lower triangle, rows/cols k+1..n-1
+        for (long t = threadIdx.x; t < (long)m * m; t += blockDim.x) {
+            const int i = k + 1 + (int)(t / m), j = k + 1 + (int)(t % m);
+            if (j <= i) A[(size_t)i * n + j] -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && bad) *status = 1;
+}
+
+// W = L^{-1}, column c by thread c (forward substitution), lower triangle
+__global__ void k_tri_inverse(int n, const double *__restrict__ L, double *__restrict__ W)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    for (int i = 0; i < c; ++i) W[(size_t)i * n + c] = 0.0;
+    W[(size_t)c * n + c] = 1.0 / L[(size_t)c * n + c];
+    for (int i = c + 1; i < n; ++i) {
+        double s = 0.0;
+        for (int m = c; m < i; ++m) s += L[(size_t)i * n + m] * W[(size_t)m * n + c];
+        W[(size_t)i * n + c] = -s / L[(size_t)i * n + i];
+    }
+}
+
+// Ainv = W^T W
+__global__ void k_gram(int n, const double *__restrict__ W, double *__restrict__ Ainv)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)n * n) return;
+    const int i = (int)(t / n), j = (int)(t - (long)i * n);
+    const int m0 = i > j ? i : j;
+    double s = 0.0;
+    for (int m = m0; m < n; ++m) s += W[(size_t)m * n + i] * W[(size_t)m * n + j];
+    Ainv[(size_t)i * n + j] = s;
+}
+
+// pack the coarsest right-hand side into a dense FP64 vector
+template <typename T>
+__global__ void k_pack(int nx, int ny, int pitch, int n, const T *__restrict__ bx, const T *__restrict__ by,
+                       double *__restrict__ b)
+{
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    int comp, j, i;
+    unknown_pos(u, nx, ny, comp, j, i);
+    b[u] = (double)(comp == 0 ? bx : by)[(size_t)j * pitch + i];
+}
+
+// x = -Ainv b (solution of M x = b), one warp per row
+__global__ void k_dense_solve(int n, const double *__restrict__ Ainv, const double *__restrict__ b,
+                              double *__restrict__ x)
+{
+    const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+    if (row >= n) return;
+    double s = 0.0;
+    for (int c = lane; c < n; c += 32) s += Ainv[(size_t)row * n + c] * b[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) x[row] = -s;
+}
+
+template <typename T>
+__global__ void k_unpack(int nx, int ny, int pitch, int n, const double *__restrict__ x, T *__restrict__ vx,
+                         T *__restrict__ vy)
+{
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    int comp, j, i;
+    unknown_pos(u, nx, ny, comp, j, i);
+    (comp == 0 ? vx : vy)[(size_t)j * pitch + i] = (T)x[u];
+}
+
+} // namespace
+
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t mg_coarsen_eta(const MgLevel &f, const MgLevel &c, cudaStream_t s)
+{
+    k_coarsen_eta<T><<<grid2d(c.nx + 1, c.ny + 1), dim3(BX, BY), 0, s>>>(
+        c.nx, c.ny, f.pitch, c.pitch, (const T *)f.ec, (const T *)f.en, (T *)c.ec, (T *)c.en);
+    return cudaGetLastError();
+}
+
+template <typename Ts, typename Td>
+cudaError_t mg_cast(size_t n, const void *src, void *dst, cudaStream_t s)
+{
+    k_cast<Ts, Td><<<1216, 256, 0, s>>>(n, (const Ts *)src, (Td *)dst);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t mg_residual(const MgLevel &l, cudaStream_t s)
+{
+    const GridDesc<T> g = make_grid<T>(l.nx, l.ny, l.pitch, l.hx, l.hy);
+    k_residual<T><<<grid2d(l.nx + 1, l.ny + 1), dim3(BX, BY), 0, s>>>(g, (const T *)l.ec, (const T *)l.en,
+                                                                       (const T *)l.bx, (const T *)l.by,
+                                                                       (const T *)l.vx, (const T *)l.vy, (T *)l.rx,
+                                                                       (T *)l.ry);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t mg_restrict(const MgLevel &f, const MgLevel &c, cudaStream_t s)
+{
+    k_restrict<T><<<grid2d(c.nx + 1, c.ny + 1), dim3(BX, BY), 0, s>>>(f.nx, f.ny, f.pitch, c.nx, c.ny, c.pitch,
+                                                                       (const T *)f.rx, (const T *)f.ry, (T *)c.bx,
+                                                                       (T *)c.by);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t mg_prolong_add(const MgLevel &f, const MgLevel &c, cudaStream_t s)
+{
+    k_prolong_add<T><<<grid2d(f.nx + 1, f.ny + 1), dim3(BX, BY), 0, s>>>(f.nx, f.ny, f.pitch, c.nx, c.ny,
+                                                                          c.pitch, (const T *)c.vx,
+                                                                          (const T *)c.vy, (T *)f.vx, (T *)f.vy);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t mg_dense_setup(const MgLevel &l, int n, double *A, double *W, double *Ainv, int *status,
+                           cudaStream_t s)
+{
+    const long nn = (long)n * n;
+    k_assemble<T><<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(l.nx, l.ny, l.pitch, 1.0 / l.hx, 1.0 / l.hy,
+                                                               (const T *)l.ec, (const T *)l.en, n, A);
+    k_cholesky<<<1, 1024, 0, s>>>(n, A, status);
+    k_tri_inverse<<<(n + 127) / 128, 128, 0, s>>>(n, A, W);
+    k_gram<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(n, W, Ainv);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t mg_dense_solve(const MgLevel &l, int n, const double *Ainv, double *bvec, double *xvec, cudaStream_t s)
+{
+    k_pack<T><<<(n + 255) / 256, 256, 0, s>>>(l.nx, l.ny, l.pitch, n, (const T *)l.bx, (const T *)l.by, bvec);
+    k_dense_solve<<<(n + 7) / 8, 256, 0, s>>>(n, Ainv, bvec, xvec);
+    k_unpack<T><<<(n + 255) / 256, 256, 0, s>>>(l.nx, l.ny, l.pitch, n, xvec, (T *)l.vx, (T *)l.vy);
+    return cudaGetLastError();
+}
+
+#define INST(T)                                                                                                    \
+    template cudaError_t mg_coarsen_eta<T>(const MgLevel &, const MgLevel &, cudaStream_t);                        \
+    template cudaError_t mg_residual<T>(const MgLevel &, cudaStream_t);                                            \
+    template cudaError_t mg_restrict<T>(const MgLevel &, const MgLevel &, cudaStream_t);                           \
+    template cudaError_t mg_prolong_add<T>(const MgLevel &, const MgLevel &, cudaStream_t);                        \
+    template cudaError_t mg_dense_setup<T>(const MgLevel &, int, double *, double *, double *, int *,              \
+                                           cudaStream_t);                                                          \
+    template cudaError_t mg_dense_solve<T>(const MgLevel &, int, const double *, double *, double *, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+template cudaError_t mg_cast<double, float>(size_t, const void *, void *, cudaStream_t);
+template cudaError_t mg_cast<float, double>(size_t, const void *, void *, cudaStream_t);
+template cudaError_t mg_cast<double, double>(size_t, const void *, void *, cudaStream_t);
+template cudaError_t mg_cast<float, float>(size_t, const void *, void *, cudaStream_t);
+
+} // namespace stokes

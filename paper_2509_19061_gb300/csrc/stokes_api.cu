@@ -3,6 +3,7 @@
 // outer iterations with their tile shifts, ping-pong buffers) and the energy
 // norm.  Every arithmetic step runs in the kernels of stencil_kernels.cu and
 // ras_kernels.cu.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -72,6 +73,15 @@ struct stokes_ctx {
     long long wait_limit = 2000000000LL; // STOKES_OPT_WAIT_LIMIT_CYCLES (about 1 s)
     MgHierarchy *mg = nullptr;
     Profiler prof;
+    // outer solve: work vectors r, z, p, q (x and y each), reduction buffers,
+    // and the preconditioner z = B r as a CUDA graph replayed on gstream
+    void *kw[8] = {};
+    double *kpartials = nullptr, *kout = nullptr, *hout = nullptr;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec = nullptr;
+    unsigned char gkey[sizeof(stokes_mg_params)] = {};
+    long long gkernels[STOKES_K_COUNT] = {};
 };
 
 namespace {
@@ -154,12 +164,14 @@ Coeffs<T> coeffs_of(const stokes_ctx *c)
     k.eta_n = (const T *)c->eta_n;
     k.bx = (const T *)c->bx;
     k.by = (const T *)c->by;
-    k.inv_dx = (const T *)c->ivx;
-    k.inv_dy = (const T *)c->ivy;
+    // FP64 kernels read 1/diag(M) (the FP64 pipe is their bottleneck); FP32
+    // kernels recompute it (HBM is theirs)
+    k.inv_dx = c->dtype == STOKES_F64 ? (const T *)c->ivx : nullptr;
+    k.inv_dy = c->dtype == STOKES_F64 ? (const T *)c->ivy : nullptr;
     return k;
 }
 
-int check_smooth_params(const stokes_ctx *c, const stokes_smooth_params *p, int *ti, int *tj)
+int check_smooth_params(int nx, int ny, size_t esize, const stokes_smooth_params *p, int *ti, int *tj)
 {
     if (!p || p->sweeps < 0 || !(p->omega > 0.0)) return STOKES_ERR_ARG;
     if (p->variant < STOKES_JACOBI || p->variant > STOKES_RAS) return STOKES_ERR_ARG;
@@ -169,7 +181,7 @@ int check_smooth_params(const stokes_ctx *c, const stokes_smooth_params *p, int 
         const int k = p->variant == STOKES_RAS ? p->k : 1;
         const int o = p->variant == STOKES_RAS ? p->overlap : 0;
         if (k < 1 || o < 0 || o > 4096) return STOKES_ERR_ARG;
-        if (ras_smem_bytes(c->nx, c->ny, *ti, *tj, o, c->esize) > (size_t)ras_max_smem()) return STOKES_ERR_ARG;
+        if (ras_smem_bytes(nx, ny, *ti, *tj, o, esize) > (size_t)ras_max_smem()) return STOKES_ERR_ARG;
         if (p->variant == STOKES_RAS) {
             if (p->shift_mode < STOKES_SHIFT_NONE || p->shift_mode > STOKES_SHIFT_LIST) return STOKES_ERR_ARG;
             if (p->shift_mode == STOKES_SHIFT_LIST && p->sweeps > 0 && !p->shifts) return STOKES_ERR_ARG;
@@ -200,58 +212,39 @@ int device_status(stokes_ctx *c)
     return STOKES_OK;
 }
 
+// the context as a launch hook: counts launches, times them when enabled
+struct CtxHook : LaunchHook {
+    stokes_ctx *c;
+    explicit CtxHook(stokes_ctx *cc) : c(cc) {}
+    int run(int kind, int nk, const std::function<cudaError_t()> &launch) override
+    {
+        return ::run(c, kind, nk, launch);
+    }
+};
+
+SmoothSpec spec_of(const stokes_smooth_params *p, int ti, int tj)
+{
+    SmoothSpec s;
+    s.variant = p->variant;
+    s.sweeps = p->sweeps;
+    s.ti = ti;
+    s.tj = tj;
+    s.k = p->k;
+    s.overlap = p->overlap;
+    s.shift_mode = p->shift_mode;
+    s.omega = p->omega;
+    s.seed = p->seed;
+    s.shifts = p->shifts;
+    return s;
+}
+
 // Runs the smoother of `p` on (vx, vy) with b already formed.
 template <typename T>
 int smooth_impl(stokes_ctx *c, T *vx, T *vy, const stokes_smooth_params *p, int ti, int tj)
 {
-    const GridDesc<T> g = grid_of<T>(c);
-    const Coeffs<T> k = coeffs_of<T>(c);
-    const T omega = (T)p->omega;
-    cudaStream_t s = c->stream;
-    if (p->sweeps == 0) return STOKES_OK;
-    if (p->variant == STOKES_RBGS) {
-        for (int it = 0; it < p->sweeps; ++it) RUN(STOKES_K_RBGS, 4, launch_rbgs_sweep<T>(g, k, omega, vx, vy, s));
-        return STOKES_OK;
-    }
-    // ping-pong between the caller's buffers (A) and the library's (B)
-    T *ax = vx, *ay = vy, *bxp = (T *)c->sx, *byp = (T *)c->sy;
-    RUN(STOKES_K_COPY, 1, launch_copy_walls<T>(g, vx, vy, bxp, byp, s));
-    int passes = 0;
-    if (p->variant == STOKES_RAS) {
-        const int n_outer = (p->sweeps + p->k - 1) / p->k;
-        for (int t = 0; t < n_outer; ++t) {
-            const int ks = (t == n_outer - 1) ? p->sweeps - (n_outer - 1) * p->k : p->k;
-            int si = 0, sj = 0;
-            if (p->shift_mode == STOKES_SHIFT_SPLITMIX) {
-                si = (int)(splitmix64(p->seed, 2u * (uint64_t)t) % (uint64_t)ti);
-                sj = (int)(splitmix64(p->seed, 2u * (uint64_t)t + 1u) % (uint64_t)tj);
-            } else if (p->shift_mode == STOKES_SHIFT_LIST) {
-                si = p->shifts[2 * t];
-                sj = p->shifts[2 * t + 1];
-                if (si < 0 || si >= ti || sj < 0 || sj >= tj) return STOKES_ERR_ARG;
-            }
-            const TileGrid tg = make_tiles(c->nx, c->ny, ti, tj, si, sj);
-            RUN(STOKES_K_RAS, 1, launch_ras<T>(g, k, omega, tg, ks, p->overlap, ax, ay, bxp, byp, run_opts(c), s));
-            T *t0 = ax; ax = bxp; bxp = t0;
-            T *t1 = ay; ay = byp; byp = t1;
-            ++passes;
-        }
-    } else {
-        for (int it = 0; it < p->sweeps; ++it) {
-            if (p->variant == STOKES_JACOBI_BLOCKED) {
-                const TileGrid tg = make_tiles(c->nx, c->ny, ti, tj, 0, 0);
-                RUN(STOKES_K_RAS, 1, launch_ras<T>(g, k, omega, tg, 1, 0, ax, ay, bxp, byp, run_opts(c), s));
-            } else {
-                RUN(STOKES_K_JACOBI, p->variant == STOKES_JACOBI_FUSED ? 1 : 2,
-                    launch_jacobi<T>(g, k, omega, ax, ay, bxp, byp, p->variant == STOKES_JACOBI_FUSED, s));
-            }
-            T *t0 = ax; ax = bxp; bxp = t0;
-            T *t1 = ay; ay = byp; byp = t1;
-            ++passes;
-        }
-    }
-    if (passes & 1) RUN(STOKES_K_COPY, 1, launch_copy_velocity<T>(g, ax, ay, vx, vy, s));
-    return STOKES_OK;
+    CtxHook hook(c);
+    return smooth_buffers<T>(grid_of<T>(c), coeffs_of<T>(c), vx, vy, (T *)c->sx, (T *)c->sy, spec_of(p, ti, tj),
+                             run_opts(c), c->stream, hook);
 }
 
 template <typename T>
@@ -265,6 +258,208 @@ int energy_impl(stokes_ctx *c, const T *vx, const T *vy, const T *p, double out[
     const int st = device_status(c);
     std::memcpy(out, c->hsum, 3 * sizeof(double));
     return st;
+}
+
+// counts the kernels of a launch sequence without timing it (graph capture)
+struct CountHook : LaunchHook {
+    long long k[STOKES_K_COUNT] = {};
+    int run(int kind, int nk, const std::function<cudaError_t()> &launch) override
+    {
+        const cudaError_t e = launch();
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        k[kind] += nk;
+        return STOKES_OK;
+    }
+};
+
+int check_mg_params(const stokes_ctx *c, const stokes_mg_params *p)
+{
+    if (!p || p->levels < 1 || p->coarsest < 2 || p->nu_pre < 0 || p->nu_post < 0 || !(p->nu_growth > 0.0) ||
+        p->nu_max < 0 || p->max_cycles < 0 || !(p->tol >= 0.0))
+        return STOKES_ERR_ARG;
+    if (p->inner_dtype != STOKES_F32 && p->inner_dtype != STOKES_F64) return STOKES_ERR_ARG;
+    if (p->krylov != 0 && p->krylov != 1) return STOKES_ERR_ARG;
+    stokes_smooth_params sm = p->smoother;
+    sm.sweeps = 0;
+    sm.shift_mode = STOKES_SHIFT_SPLITMIX;
+    sm.shifts = nullptr;
+    int ti, tj;
+    // the window must fit on the finest level in the inner precision
+    return check_smooth_params(c->nx, c->ny, p->inner_dtype == STOKES_F64 ? 8 : 4, &sm, &ti, &tj);
+}
+
+MgOuter outer_of(const stokes_ctx *c)
+{
+    MgOuter o;
+    o.nx = c->nx;
+    o.ny = c->ny;
+    o.pitch = c->pitch;
+    o.dtype = c->dtype;
+    o.hx = c->hx;
+    o.hy = c->hy;
+    o.eta_c = c->eta_c;
+    o.eta_n = c->eta_n;
+    o.bx = c->bx;
+    o.by = c->by;
+    return o;
+}
+
+// work vectors of the outer solve, allocated on first use
+int ensure_work(stokes_ctx *c)
+{
+    if (c->kw[0]) return STOKES_OK;
+    for (void *&w : c->kw) {
+        const int st = alloc_field(c, &w);
+        if (st != STOKES_OK) return st;
+    }
+    CK(cudaMalloc(&c->kpartials, (size_t)krylov_partials() * 2 * sizeof(double)));
+    CK(cudaMalloc(&c->kout, 2 * sizeof(double)));
+    CK(cudaMallocHost(&c->hout, 2 * sizeof(double)));
+    return STOKES_OK;
+}
+
+// (Re)capture the preconditioner z = B r (fixed work buffers) for these parameters.
+int ensure_graph(stokes_ctx *c, const stokes_mg_params *p)
+{
+    if (c->gexec && std::memcmp(p, c->gkey, sizeof *p) == 0) return STOKES_OK;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (!c->gstream) {
+        CK(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->gev[0], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->gev[1], cudaEventDisableTiming));
+    }
+    CountHook hook;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+    const int st = mg_enqueue_precond(c->mg, c->dtype, c->kw[0], c->kw[1], c->kw[2], c->kw[3], p, run_opts(c),
+                                      c->gstream, hook);
+    const cudaError_t e = cudaStreamEndCapture(c->gstream, &graph);
+    if (st != STOKES_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    const cudaError_t ei = cudaGraphInstantiate(&c->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        c->gexec = nullptr;
+        return cuda_fail(ei, "cudaGraphInstantiate");
+    }
+    std::memcpy(c->gkey, p, sizeof *p);
+    for (int k = 0; k < STOKES_K_COUNT; ++k) c->gkernels[k] = hook.k[k];
+    return STOKES_OK;
+}
+
+// one replay of the preconditioner, ordered after the context stream's work
+int replay_graph(stokes_ctx *c)
+{
+    CK(cudaEventRecord(c->gev[0], c->stream));
+    CK(cudaStreamWaitEvent(c->gstream, c->gev[0], 0));
+    CK(cudaGraphLaunch(c->gexec, c->gstream));
+    CK(cudaEventRecord(c->gev[1], c->gstream));
+    CK(cudaStreamWaitEvent(c->stream, c->gev[1], 0));
+    for (int k = 0; k < STOKES_K_COUNT; ++k) c->prof.kernels[k] += c->gkernels[k];
+    return STOKES_OK;
+}
+
+// the two reduction results, synchronising the context stream
+int read2(stokes_ctx *c, double *a, double *b)
+{
+    CK(cudaMemcpyAsync(c->hout, c->kout, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    const int st = device_status(c);
+    if (a) *a = c->hout[0];
+    if (b) *b = c->hout[1];
+    return st;
+}
+
+// Outer solve of M v = f - G p (Sec. 3.2): flexible CG or defect correction
+// with the V-cycle preconditioner z = B r.
+template <typename T>
+int vcycle_impl(stokes_ctx *c, T *vx, T *vy, const T *p, const stokes_mg_params *params, double *final_e,
+                int *cycles)
+{
+    const GridDesc<T> g = grid_of<T>(c);
+    RUN(STOKES_K_RHS, 1, launch_rhs<T>(g, (const T *)c->fx, (const T *)c->fy, p, (T *)c->bx, (T *)c->by, c->stream));
+    int st = mg_ensure(&c->mg, outer_of(c), params, c->stream);
+    if (st == STOKES_OK) st = ensure_work(c);
+    if (st == STOKES_OK) st = ensure_graph(c, params);
+    if (st != STOKES_OK) return st;
+    T *rx = (T *)c->kw[0], *ry = (T *)c->kw[1], *zx = (T *)c->kw[2], *zy = (T *)c->kw[3];
+    T *px = (T *)c->kw[4], *py = (T *)c->kw[5], *qx = (T *)c->kw[6], *qy = (T *)c->kw[7];
+    const T *ix = (const T *)c->ivx, *iy = (const T *)c->ivy;
+    const KrylovView kv{c->nx, c->ny, c->pitch, c->kpartials, c->kout};
+    MgLevel top{};
+    top.nx = c->nx;
+    top.ny = c->ny;
+    top.pitch = c->pitch;
+    top.elems = c->elems;
+    top.hx = c->hx;
+    top.hy = c->hy;
+    top.ec = c->eta_c;
+    top.en = c->eta_n;
+    top.bx = c->bx;
+    top.by = c->by;
+    top.vx = vx;
+    top.vy = vy;
+    top.rx = rx;
+    top.ry = ry;
+    // r = b - M v and E_v
+    RUN(STOKES_K_MG, 1, mg_residual<T>(top, c->stream));
+    RUN(STOKES_K_ENERGY, 2, kry_energy<T>(kv, rx, ry, (const T *)c->fx, (const T *)c->fy, ix, iy, c->stream));
+    double num = 0.0, den = 1.0;
+    st = read2(c, &num, &den);
+    if (st != STOKES_OK) return st;
+    double e = std::sqrt(num / den);
+    const double e0 = e;
+    int it = 0;
+    auto check = [&]() -> int {
+        if (!std::isfinite(e) || e > 1e6 * e0) return STOKES_ERR_DIVERGED;
+        if (e <= params->tol) return 1;
+        if (it >= params->max_cycles) return STOKES_ERR_NOT_CONVERGED;
+        return 0;
+    };
+    int verdict = check();
+    if (params->krylov && verdict == 0) {
+        st = replay_graph(c);
+        if (st != STOKES_OK) return st;
+        CK(cudaMemcpyAsync(px, zx, c->elems * c->esize, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(py, zy, c->elems * c->esize, cudaMemcpyDeviceToDevice, c->stream));
+        for (;;) {
+            RUN(STOKES_K_APPLY, 1,
+                launch_apply<T>(g, (const T *)c->eta_c, (const T *)c->eta_n, px, py, nullptr, qx, qy, c->stream));
+            RUN(STOKES_K_MG, 2, kry_dot2<T>(kv, px, py, qx, qy, rx, ry, c->stream));
+            double pq = 0.0, pr = 0.0;
+            if ((st = read2(c, &pq, &pr)) != STOKES_OK) return st;
+            const double a = pr / pq;
+            RUN(STOKES_K_MG, 2, kry_update<T>(kv, a, px, py, qx, qy, vx, vy, rx, ry, ix, iy, c->stream));
+            if ((st = read2(c, &num, nullptr)) != STOKES_OK) return st;
+            ++it;
+            e = std::sqrt(num / den);
+            if ((verdict = check()) != 0) break;
+            if ((st = replay_graph(c)) != STOKES_OK) return st;
+            RUN(STOKES_K_MG, 2, kry_dot2<T>(kv, zx, zy, qx, qy, (const T *)nullptr, (const T *)nullptr, c->stream));
+            double zq = 0.0;
+            if ((st = read2(c, &zq, nullptr)) != STOKES_OK) return st;
+            RUN(STOKES_K_MG, 1, kry_direction<T>(kv, -zq / pq, zx, zy, px, py, c->stream));
+        }
+    } else {
+        while (verdict == 0) {
+            if ((st = replay_graph(c)) != STOKES_OK) return st;
+            RUN(STOKES_K_MG, 1, kry_add<T>(kv, zx, zy, vx, vy, c->stream));
+            RUN(STOKES_K_MG, 1, mg_residual<T>(top, c->stream));
+            RUN(STOKES_K_ENERGY, 2, kry_energy<T>(kv, rx, ry, (const T *)c->fx, (const T *)c->fy, ix, iy, c->stream));
+            if ((st = read2(c, &num, nullptr)) != STOKES_OK) return st;
+            ++it;
+            e = std::sqrt(num / den);
+            verdict = check();
+        }
+    }
+    if (final_e) *final_e = e;
+    if (cycles) *cycles = it;
+    return verdict < 0 ? verdict : STOKES_OK;
 }
 
 } // namespace
@@ -314,10 +509,8 @@ int stokes_create(int nx, int ny, double lx, double ly, int dtype, void *cuda_st
     void **fields[] = {&c->eta_c, &c->eta_n, &c->fx, &c->fy, &c->bx, &c->by, &c->sx, &c->sy};
     for (void **f : fields)
         if ((st = alloc_field(c, f)) != STOKES_OK) break;
-    if (st == STOKES_OK && dtype == STOKES_F64) {
-        st = alloc_field(c, &c->ivx);
-        if (st == STOKES_OK) st = alloc_field(c, &c->ivy);
-    }
+    if (st == STOKES_OK) st = alloc_field(c, &c->ivx);
+    if (st == STOKES_OK) st = alloc_field(c, &c->ivy);
     if (st == STOKES_OK) {
         cudaError_t e = cudaMalloc(&c->partials, (size_t)energy_partials() * 3 * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&c->dsum, 3 * sizeof(double));
@@ -341,6 +534,16 @@ int stokes_destroy(stokes_ctx *c)
     if (!c) return STOKES_OK;
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->gstream) cudaStreamSynchronize(c->gstream);
+    for (void *w : c->kw)
+        if (w) cudaFree(w);
+    if (c->kpartials) cudaFree(c->kpartials);
+    if (c->kout) cudaFree(c->kout);
+    if (c->hout) cudaFreeHost(c->hout);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
+    for (cudaEvent_t e : c->gev)
+        if (e) cudaEventDestroy(e);
     mg_destroy(c->mg);
     prof_flush(c);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
@@ -382,12 +585,19 @@ int stokes_set_viscosity(stokes_ctx *c, const void *eta_c, const void *eta_n)
         RUN(STOKES_K_COPY, 1,
             launch_inv_diag<double>(grid_of<double>(c), (const double *)c->eta_c, (const double *)c->eta_n,
                                     (double *)c->ivx, (double *)c->ivy, c->stream));
-    }
-    else
+    } else {
         RUN(STOKES_K_COPY, 1, launch_copy_eta<float>(grid_of<float>(c), (const float *)eta_c, (const float *)eta_n, (float *)c->eta_c,
                                   (float *)c->eta_n, c->stream));
+        RUN(STOKES_K_COPY, 1,
+            launch_inv_diag<float>(grid_of<float>(c), (const float *)c->eta_c, (const float *)c->eta_n,
+                                   (float *)c->ivx, (float *)c->ivy, c->stream));
+    }
     c->have_eta = true;
     mg_invalidate(c->mg);
+    if (c->gexec) { // the graph holds the old hierarchy's buffers
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
     return STOKES_OK;
 }
 
@@ -419,7 +629,7 @@ int stokes_apply_operator(stokes_ctx *c, const void *vx, const void *vy, const v
 int stokes_smooth(stokes_ctx *c, void *vx, void *vy, const void *p, const stokes_smooth_params *params)
 {
     if (!c || !vx || !vy) return STOKES_ERR_ARG;
-    int ti, tj, st = check_smooth_params(c, params, &ti, &tj);
+    int ti, tj, st = check_smooth_params(c->nx, c->ny, c->esize, params, &ti, &tj);
     if (st != STOKES_OK) return st;
     if (!c->have_eta || !c->have_f) return STOKES_ERR_STATE;
     if (c->dtype == STOKES_F64) {
@@ -444,8 +654,12 @@ int stokes_vcycle(stokes_ctx *c, void *vx, void *vy, const void *p, const stokes
                   double *final_rel_resid, int *cycles)
 {
     if (!c || !vx || !vy || !params) return STOKES_ERR_ARG;
+    const int st = check_mg_params(c, params);
+    if (st != STOKES_OK) return st;
     if (!c->have_eta || !c->have_f) return STOKES_ERR_STATE;
-    return STOKES_ERR_STATE; // multigrid solve: not yet available
+    if (c->dtype == STOKES_F64)
+        return vcycle_impl<double>(c, (double *)vx, (double *)vy, (const double *)p, params, final_rel_resid, cycles);
+    return vcycle_impl<float>(c, (float *)vx, (float *)vy, (const float *)p, params, final_rel_resid, cycles);
 }
 
 int stokes_set_option(stokes_ctx *c, int option, long long value)
