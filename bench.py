@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--overlap", type=int, default=None)
     ap.add_argument("--no-extras", action="store_true", help="skip the variant table, e2e and CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--solve-n", type=int, default=4096, help="grid of the time-to-1e-8 solve")
     return ap.parse_args()
 
 
@@ -287,6 +288,7 @@ def run_ours(args):
     if not args.no_extras and rank == 0:
         line["e2e"] = e2e_measure(args, ctx, prob, stream, world)
         line["variants"] = variant_table(args, api, prob)
+        line["time_to_1e-8"] = solve_times(args, api)
         if world == 1:
             line["cpu_baseline"] = {kk: vv for kk, vv in cpu_sample(args, args.cpu_seconds).items()
                                     if kk != "seconds"}
@@ -338,6 +340,37 @@ def e2e_measure(args, ctx, prob, stream, world):
     return {"value": world * args.n * args.n * args.sweeps * steps / dt / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
             "ms_per_step": 1000.0 * dt / steps}
+
+
+def solve_times(args, api):
+    """Time to a 1e-8 velocity energy residual on the 4096^2 multi-sinker
+    (20 seeded inclusions, log10 eta ~ U[-3, 3]): FP64 outer flexible CG
+    around a V-cycle (RAS 32x32, k = 4, overlap 3, 5/5 sweeps x2.5 per level
+    capped at 40, dense FP64 coarsest) whose sweeps run in FP32 or FP64."""
+    import torch
+    from paper_2509_19061_gb300 import inputs
+    n = args.solve_n
+    prob = inputs.multi_sinker(n, seed=3)
+    ctx = api.StokesContext(n, n, 1.0, 1.0, "f64")
+    ctx.set_problem(prob)
+    out = {"workload": "multi_sinker_%dx%d_seed3" % (n, n), "tol": 1e-8, "outer": "f64 flexible CG",
+           "smoother": "ras 32x32 k4 o3", "nu": "5/5 x2.5 per level, cap 40"}
+    for inner in ("f32", "f64"):
+        kw = dict(variant="ras", tile=(32, 32), k=4, overlap=3, seed=1, nu_max=40, inner=inner, krylov=True,
+                  tol=1e-8, max_cycles=200)
+        vx, vy = ctx.field(), ctx.field()
+        ctx.vcycle(vx, vy, None, **kw)  # builds the hierarchy and the graph
+        vx.zero_()
+        vy.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, e, cyc = ctx.vcycle(vx, vy, None, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[inner + "_inner"] = {"seconds": dt, "cycles": cyc, "final_energy_residual": e, "status": st}
+    out["speedup_f32_over_f64"] = out["f64_inner"]["seconds"] / out["f32_inner"]["seconds"]
+    ctx.close()
+    return out
 
 
 def variant_table(args, api, prob):
