@@ -108,6 +108,27 @@ cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const 
                        int overlap, const T *vx, const T *vy, T *ox, T *oy, const RasRun &run, cudaStream_t s);
 // shared memory a RAS launch needs for this grid, tile and overlap
 size_t ras_smem_bytes(int nx, int ny, int ti, int tj, int overlap, size_t elem);
+
+// One instance's share of a batched tile launch: its grid, coefficients,
+// snapshot (vx, vy) -> output (ox, oy), tiling, and the index of its first
+// tile in the launch's tile list.
+template <typename T>
+struct BatchTiles {
+    GridDesc<T> g;
+    Coeffs<T> c;
+    const T *vx, *vy;
+    T *ox, *oy;
+    TileGrid tg;
+    int tile_begin;
+};
+// One RAS outer iteration (ksweeps local sweeps) for every instance of the
+// device table `tab` (count entries, tiles numbered consecutively, `total`
+// tiles), all with tile size (ti, tj) and `overlap`: one persistent launch.
+template <typename T>
+cudaError_t launch_ras_batched(const BatchTiles<T> *tab, int count, int total, int ti, int tj, int ksweeps,
+                               int overlap, T omega, cudaStream_t s);
+// Shared memory one batched launch needs (tile size and overlap only).
+size_t ras_batched_smem_bytes(int ti, int tj, int overlap, size_t elem);
 int ras_max_smem();
 
 // SplitMix64 (Steele, Lea & Flood 2014): output c (from 0) of the generator

@@ -418,6 +418,53 @@ __global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_reg(RasArgs<T> a)
 }
 
 // ---------------------------------------------------------------------------
+// batched persistent kernel: the tiles of many instances in one launch
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_batched(const BatchTiles<T> *__restrict__ tab, int count,
+                                                                 int total, RasArgs<T> shape)
+{
+    constexpr int R = KCfg<T>::R;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const Planes<T> pl(reinterpret_cast<T *>(smem_raw), shape.wp, shape.plane);
+    const int col = threadIdx.x % shape.wxm, strip = threadIdx.x / shape.wxm;
+    const bool active = (int)threadIdx.x < shape.wxm * shape.strips;
+    zero_borders(shape, pl);
+    __syncthreads();
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        // instance owning tile t: last entry with tile_begin <= t
+        int lo = 0, hi = count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tab[mid].tile_begin <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchTiles<T> &e = tab[lo];
+        RasArgs<T> a = shape;
+        a.g = e.g;
+        a.c = e.c;
+        a.vx = e.vx;
+        a.vy = e.vy;
+        a.ox = e.ox;
+        a.oy = e.oy;
+        a.tg = e.tg;
+        const Window w = window_of(a, t - e.tile_begin);
+        const GridDesc<T> &g = a.g;
+        const size_t P = (size_t)g.pitch;
+        const T *const src[8] = {a.vx, a.vy, a.c.eta_c, a.c.eta_n, a.c.bx, a.c.by, a.c.inv_dx, a.c.inv_dy};
+        CellRegs<T, R> c;
+        setup_cells<T, R>(a, w, c, col, strip, active, pl, [&](int f, int wy, int wx) {
+            const int gy = w.oy0 + wy, gx = w.ox0 + wx;
+            const int ey = (f == 0 || f == 2 || f == 4 || f == 6) ? g.ny : g.ny + 1;
+            const int ex = (f == 1 || f == 2 || f == 5 || f == 7) ? g.nx : g.nx + 1;
+            return (gy >= 0 && gy < ey && gx >= 0 && gx < ex) ? src[f][(size_t)gy * P + (size_t)gx] : T(0);
+        });
+        __syncthreads();
+        sweep_and_store<T, R>(a, w, c, col, strip, active, pl);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // general kernel: every field of the window in shared memory
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -658,6 +705,43 @@ cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const 
     }
     return cudaGetLastError();
 }
+
+size_t ras_batched_smem_bytes(int ti, int tj, int overlap, size_t elem)
+{
+    const RasPlan p = plan_ras(ti, tj, ti, tj, overlap, elem, false);
+    return p.kind == PLAN_SMEM ? (size_t)-1 : p.smem;
+}
+
+template <typename T>
+cudaError_t launch_ras_batched(const BatchTiles<T> *tab, int count, int total, int ti, int tj, int ksweeps,
+                               int overlap, T omega, cudaStream_t s)
+{
+    // the register layout sized for a full window (instances at least one tile wide)
+    const RasPlan p = plan_ras(ti, tj, ti, tj, overlap, sizeof(T), false);
+    if (p.kind == PLAN_SMEM) return cudaErrorInvalidValue;
+    RasArgs<T> a{};
+    a.omega = omega;
+    a.ks = ksweeps;
+    a.overlap = overlap;
+    a.wxm = p.wxm;
+    a.wym = p.wym;
+    a.strips = p.strips;
+    a.wp = p.wp;
+    a.plane = p.plane;
+    cudaError_t e = cudaFuncSetAttribute(k_ras_batched<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ras_batched<T>, p.threads, p.smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(total, std::max(per_sm, 1) * sm_count());
+    if (grid > 0) k_ras_batched<T><<<grid, p.threads, p.smem, s>>>(tab, count, total, a);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_ras_batched<float>(const BatchTiles<float> *, int, int, int, int, int, int, float,
+                                               cudaStream_t);
+template cudaError_t launch_ras_batched<double>(const BatchTiles<double> *, int, int, int, int, int, int, double,
+                                                cudaStream_t);
 
 template cudaError_t launch_ras<float>(const GridDesc<float> &, const Coeffs<float> &, float, const TileGrid &, int,
                                        int, const float *, const float *, float *, float *, const RasRun &,
