@@ -288,6 +288,73 @@ int stokes_energy_norm_noalloc(int nx, int ny, double lx, double ly, int dtype, 
                                const void *eta_n, const void *fx, const void *fy, const void *p, const void *vx,
                                const void *vy, double *out_dev, void *cuda_stream);
 
+/* ---- Batches: many independent problems of different sizes ---------------
+ * A batch holds `count` instances, instance i an nx[i] x ny[i] grid on
+ * [0, lx[i]] x [0, ly[i]], all in one dtype, and advances them together: each
+ * step of a smoothing call, of the V-cycle and of the outer iteration is one
+ * kernel launch over every instance taking part in it, and the V-cycle of the
+ * whole batch is one CUDA graph.  Each instance follows exactly the schedule
+ * of a context of its own with the same parameters, so its smoothing and
+ * V-cycle results match that context's bit for bit (the outer iteration's
+ * FP64 sums are accumulated in another fixed order, so a solve agrees to
+ * rounding).
+ *
+ * Layout: every field of a batch is one device "slab" holding the instances
+ * back to back; instance i occupies (ny[i]+1) rows x pitch_i elements starting
+ * at element offset_i of the slab, in the single-context layout described at
+ * the top of this file (stokes_batch_get_layout).  The caller owns the slabs
+ * it passes (vx, vy, p, and the eta and f slabs it copies in).
+ *
+ * Smoothers: the Jacobi variants and RAS (STOKES_RBGS is not batched and
+ * returns STOKES_ERR_ARG).  Every instance uses the same parameters, seed
+ * and shifts. */
+typedef struct stokes_batch stokes_batch; /* opaque, library-owned */
+
+/* Create a batch of `count` >= 1 instances (host arrays nx, ny, lx, ly of
+ * `count` entries; 2 <= nx, ny <= 65536; lx, ly > 0) computing in `dtype` on
+ * `cuda_stream`.  Allocates the library's slabs. */
+int stokes_batch_create(int count, const int *nx, const int *ny, const double *lx, const double *ly, int dtype,
+                        void *cuda_stream, stokes_batch **out);
+
+/* Instance `inst`: row pitch, offset of its first element in a slab, and its
+ * extent ((ny+1) x pitch).  inst = -1: *alloc_elems receives the size of a
+ * whole slab (elements), the others 0.  Outputs may be NULL. */
+int stokes_batch_get_layout(const stokes_batch *b, int inst, int *pitch_elems, size_t *offset_elems,
+                            size_t *alloc_elems);
+
+/* Viscosity and body force of every instance from device slabs (copied);
+ * the same rules as stokes_set_viscosity / stokes_set_rhs. */
+int stokes_batch_set_viscosity(stokes_batch *b, const void *eta_c, const void *eta_n);
+int stokes_batch_set_rhs(stokes_batch *b, const void *fx, const void *fy);
+
+/* stokes_smooth for every instance: smooth M v = f - G p in place on the vx,
+ * vy slabs (p slab may be NULL).  Asynchronous. */
+int stokes_batch_smooth(stokes_batch *b, void *vx, void *vy, const void *p, const stokes_smooth_params *params);
+
+/* Velocity energy sums of Sec. 6.4 for every instance, into the host array
+ * out[2 * count]: out[2i] = sum r_v^2 / (-diag M), out[2i+1] = sum f^2 /
+ * (-diag M), accumulated in FP64 in a fixed order.  Synchronises. */
+int stokes_batch_residual_energy(stokes_batch *b, const void *vx, const void *vy, const void *p, double *out);
+
+/* stokes_vcycle for every instance at once (the same parameters; the
+ * coarsest level of every instance must have at most 1024 unknowns).  An
+ * instance stops updating when it reaches tol, hits max_cycles or diverges.
+ * Host arrays of `count` entries (each may be NULL) receive each instance's
+ * final E_v, its number of V-cycles and its status (STOKES_OK,
+ * STOKES_ERR_NOT_CONVERGED or STOKES_ERR_DIVERGED).  Returns STOKES_OK when
+ * every instance converged, else STOKES_ERR_DIVERGED if any diverged, else
+ * STOKES_ERR_NOT_CONVERGED.  The batched V-cycle is captured once as a CUDA
+ * graph and replayed on a batch-owned stream.  Synchronises. */
+int stokes_batch_solve(stokes_batch *b, void *vx, void *vy, const void *p, const stokes_mg_params *params,
+                       double *final_rel_resid, int *cycles, int *status);
+
+/* Number of kernels the batch has launched so far (graph replays count
+ * every kernel node). */
+int stokes_batch_kernels(const stokes_batch *b, long long *kernels);
+
+/* Release every library-owned buffer of the batch.  NULL is accepted. */
+int stokes_batch_destroy(stokes_batch *b);
+
 /* Release every library-owned buffer of the context.  NULL is accepted. */
 int stokes_destroy(stokes_ctx *ctx);
 

@@ -78,6 +78,18 @@ _SIGS = {
     "stokes_profile_read": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(_D)]),
     "stokes_energy_norm_noalloc": (_I, [_I, _I, _D, _D, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "stokes_batch_create": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D),
+                                 _I, _VP, ctypes.POINTER(_VP)]),
+    "stokes_batch_get_layout": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t),
+                                     ctypes.POINTER(ctypes.c_size_t)]),
+    "stokes_batch_set_viscosity": (_I, [_VP, _VP, _VP]),
+    "stokes_batch_set_rhs": (_I, [_VP, _VP, _VP]),
+    "stokes_batch_smooth": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(stokes_smooth_params)]),
+    "stokes_batch_residual_energy": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(_D)]),
+    "stokes_batch_solve": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(stokes_mg_params), ctypes.POINTER(_D),
+                                ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "stokes_batch_kernels": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
+    "stokes_batch_destroy": (_I, [_VP]),
     "stokes_destroy": (_I, [_VP]),
     "stokes_strerror": (ctypes.c_char_p, [_I]),
     "stokes_last_cuda_error": (ctypes.c_char_p, []),
@@ -232,6 +244,63 @@ def stokes_destroy(ctx):
         _check(_lib().stokes_destroy(ctx), "stokes_destroy")
 
 
+def stokes_batch_create(nx, ny, lx, ly, dtype, cuda_stream=None):
+    n = len(nx)
+    out = ctypes.c_void_p()
+    stream = ctypes.c_void_p(cuda_stream) if cuda_stream else None
+    _check(_lib().stokes_batch_create(n, (_I * n)(*nx), (_I * n)(*ny), (_D * n)(*lx), (_D * n)(*ly), dtype, stream,
+                                      ctypes.byref(out)), "stokes_batch_create")
+    return out
+
+
+def stokes_batch_get_layout(b, inst):
+    """(pitch, offset, elements) of instance inst; inst = -1: (0, 0, slab size)."""
+    pitch, off, n = _I(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(_lib().stokes_batch_get_layout(b, inst, ctypes.byref(pitch), ctypes.byref(off), ctypes.byref(n)),
+           "stokes_batch_get_layout")
+    return pitch.value, off.value, n.value
+
+
+def stokes_batch_set_viscosity(b, eta_c, eta_n):
+    _check(_lib().stokes_batch_set_viscosity(b, _ptr(eta_c), _ptr(eta_n)), "stokes_batch_set_viscosity")
+
+
+def stokes_batch_set_rhs(b, fx, fy):
+    _check(_lib().stokes_batch_set_rhs(b, _ptr(fx), _ptr(fy)), "stokes_batch_set_rhs")
+
+
+def stokes_batch_smooth(b, vx, vy, p, params):
+    _check(_lib().stokes_batch_smooth(b, _ptr(vx), _ptr(vy), _ptr(p), ctypes.byref(params)), "stokes_batch_smooth")
+
+
+def stokes_batch_residual_energy(b, count, vx, vy, p=None):
+    out = (_D * (2 * count))()
+    _check(_lib().stokes_batch_residual_energy(b, _ptr(vx), _ptr(vy), _ptr(p), out), "stokes_batch_residual_energy")
+    return np.array(out[:], dtype=np.float64).reshape(count, 2)
+
+
+def stokes_batch_solve(b, count, vx, vy, p, params):
+    """Returns (status, E_v per instance, cycles per instance, status per
+    instance); raises on errors other than STOKES_ERR_NOT_CONVERGED and
+    STOKES_ERR_DIVERGED."""
+    fe, cy, ss = (_D * count)(), (_I * count)(), (_I * count)()
+    st = _lib().stokes_batch_solve(b, _ptr(vx), _ptr(vy), _ptr(p), ctypes.byref(params), fe, cy, ss)
+    if st not in (STOKES_OK, STOKES_ERR_NOT_CONVERGED, STOKES_ERR_DIVERGED):
+        raise StokesError(st, "stokes_batch_solve")
+    return st, np.array(fe[:]), np.array(cy[:], dtype=np.int64), np.array(ss[:], dtype=np.int64)
+
+
+def stokes_batch_kernels(b):
+    k = ctypes.c_longlong()
+    _check(_lib().stokes_batch_kernels(b, ctypes.byref(k)), "stokes_batch_kernels")
+    return k.value
+
+
+def stokes_batch_destroy(b):
+    if b is not None:
+        _check(_lib().stokes_batch_destroy(b), "stokes_batch_destroy")
+
+
 # --------------------------------------------------------------------------
 # convenience wrapper with torch tensors
 # --------------------------------------------------------------------------
@@ -331,3 +400,82 @@ class StokesContext:
     def profile(self):
         """{class: (kernel launches, timed groups, total ms)}"""
         return {name: stokes_profile_read(self.ctx, i) for i, name in enumerate(KERNEL_CLASSES)}
+
+
+class BatchContext:
+    """Owns a stokes_batch: instance i is an nx[i] x ny[i] grid; every field is
+    one slab tensor holding all instances (see stokes_batch_get_layout)."""
+
+    def __init__(self, nx, ny, lx=None, ly=None, dtype="f64", device="cuda", stream=None):
+        import torch
+        self.torch = torch
+        self.count = len(nx)
+        self.nx, self.ny = list(nx), list(ny)
+        self.lx = list(lx) if lx is not None else [1.0] * self.count
+        self.ly = list(ly) if ly is not None else [1.0] * self.count
+        self.dtype_code = STOKES_F64 if dtype in ("f64", "float64", torch.float64) else STOKES_F32
+        self.tdtype = torch.float64 if self.dtype_code == STOKES_F64 else torch.float32
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.b = stokes_batch_create(self.nx, self.ny, self.lx, self.ly, self.dtype_code, self.stream.cuda_stream)
+        self.total = stokes_batch_get_layout(self.b, -1)[2]
+        self.layout = [stokes_batch_get_layout(self.b, i) for i in range(self.count)]
+
+    def close(self):
+        if self.b is not None:
+            stokes_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def slab(self):
+        return self.torch.zeros(self.total, dtype=self.tdtype, device=self.device)
+
+    def view(self, slab, i):
+        """Instance i of a slab as its (ny+1) x pitch array."""
+        pitch, off, n = self.layout[i]
+        return slab[off:off + n].view(self.ny[i] + 1, pitch)
+
+    def _shape(self, name, i):
+        nx, ny = self.nx[i], self.ny[i]
+        return {"vx": (ny, nx + 1), "fx": (ny, nx + 1), "vy": (ny + 1, nx), "fy": (ny + 1, nx), "p": (ny, nx),
+                "eta_c": (ny, nx), "eta_n": (ny + 1, nx + 1)}[name]
+
+    def pack(self, arrs, name):
+        """List of natural-shape arrays (one per instance) -> slab tensor."""
+        host = self.torch.zeros(self.total, dtype=self.tdtype)
+        for i, a in enumerate(arrs):
+            r, c = self._shape(name, i)
+            a = np.asarray(a)
+            assert a.shape == (r, c), "%s[%d]: expected %s, got %s" % (name, i, (r, c), a.shape)
+            pitch, off, n = self.layout[i]
+            v = host[off:off + n].view(self.ny[i] + 1, pitch)
+            v[:r, :c] = self.torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(self.tdtype)
+        return host.to(self.device)
+
+    def unpack(self, slab, name, i):
+        r, c = self._shape(name, i)
+        return self.view(slab, i)[:r, :c].double().cpu().numpy()
+
+    def set_problems(self, probs):
+        stokes_batch_set_viscosity(self.b, self.pack([q.eta_c for q in probs], "eta_c"),
+                                   self.pack([q.eta_n for q in probs], "eta_n"))
+        stokes_batch_set_rhs(self.b, self.pack([q.fx for q in probs], "fx"), self.pack([q.fy for q in probs], "fy"))
+
+    def smooth(self, vx, vy, p=None, **kw):
+        stokes_batch_smooth(self.b, vx, vy, p, smooth_params(**kw))
+
+    def energy(self, vx, vy, p=None):
+        """(count, 2): sum r^2/(-diag M), sum f^2/(-diag M) per instance."""
+        return stokes_batch_residual_energy(self.b, self.count, vx, vy, p)
+
+    def solve(self, vx, vy, p=None, **kw):
+        """Returns (status, E_v[], cycles[], status[])."""
+        return stokes_batch_solve(self.b, self.count, vx, vy, p, mg_params(**kw))
+
+    def kernels(self):
+        return stokes_batch_kernels(self.b)

@@ -48,7 +48,18 @@ struct BOuter {
     T *vx, *vy, *rx, *ry, *zx, *zy, *px, *py, *qx, *qy;
 };
 
+// b = f - G p of one instance (p may be NULL)
+template <typename T>
+struct BRhs {
+    GridDesc<T> g;
+    const T *fx, *fy, *p;
+    T *bx, *by;
+};
+
 constexpr int BATCH_BX = 32, BATCH_BY = 8;
+
+template <typename T> // over (nx+1) x (ny+1) per instance
+cudaError_t batch_rhs(const BRhs<T> *tab, const BSeg *map, int nseg, int nblocks, cudaStream_t s);
 
 template <typename T>
 cudaError_t batch_residual(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, cudaStream_t s);

@@ -90,6 +90,27 @@ __global__ void k_seg_final(const BSeg *__restrict__ m, int n, const double *__r
     }
 }
 
+template <typename T>
+__global__ void kb_rhs(const BRhs<T> *__restrict__ tab, const BSeg *__restrict__ m, int n)
+{
+    const Pt p = point_of(m, n);
+    if (!p.valid) return;
+    const BRhs<T> &r = tab[p.inst];
+    const GridDesc<T> &g = r.g;
+    const int i = p.i, j = p.j;
+    const size_t P = (size_t)g.pitch, q = (size_t)j * P + i;
+    if (j < g.ny) {
+        T b = T(0);
+        if (vx_unknown(g, j, i)) b = r.p ? r_fma(r_sub(r.p[q], r.p[q - 1]), g.ihx, r.fx[q]) : r.fx[q];
+        r.bx[q] = b;
+    }
+    if (i < g.nx) {
+        T b = T(0);
+        if (vy_unknown(g, j, i)) b = r.p ? r_fma(r_sub(r.p[q], r.p[q - P]), g.ihy, r.fy[q]) : r.fy[q];
+        r.by[q] = b;
+    }
+}
+
 // ---- level operations ----------------------------------------------------------
 template <typename T>
 __global__ void kb_residual(const BLevel<T> *__restrict__ tab, const BSeg *__restrict__ m, int n)
@@ -414,6 +435,12 @@ inline unsigned nblk(int nb) { return (unsigned)(nb > 0 ? nb : 1); }
 #define BLOCK dim3(BATCH_BX, BATCH_BY)
 
 template <typename T>
+cudaError_t batch_rhs(const BRhs<T> *tab, const BSeg *map, int nseg, int nblocks, cudaStream_t s)
+{
+    if (nblocks > 0) kb_rhs<T><<<nblocks, BLOCK, 0, s>>>(tab, map, nseg);
+    return cudaGetLastError();
+}
+template <typename T>
 cudaError_t batch_residual(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, cudaStream_t s)
 {
     if (nblocks > 0) kb_residual<T><<<nblocks, BLOCK, 0, s>>>(tab, map, nseg);
@@ -521,6 +548,7 @@ cudaError_t batch_scalars(int count, const double *pq_pr, const double *zq, cons
 }
 
 #define INST(T)                                                                                                    \
+    template cudaError_t batch_rhs<T>(const BRhs<T> *, const BSeg *, int, int, cudaStream_t);                      \
     template cudaError_t batch_residual<T>(const BLevel<T> *, const BSeg *, int, int, cudaStream_t);               \
     template cudaError_t batch_restrict<T>(const BLevel<T> *, const BSeg *, int, int, cudaStream_t);               \
     template cudaError_t batch_prolong<T>(const BLevel<T> *, const BSeg *, int, int, cudaStream_t);                \

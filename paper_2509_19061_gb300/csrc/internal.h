@@ -131,6 +131,10 @@ cudaError_t launch_ras_batched(const BatchTiles<T> *tab, int count, int total, i
 size_t ras_batched_smem_bytes(int ti, int tj, int overlap, size_t elem);
 int ras_max_smem();
 
+// Record a failed CUDA call for stokes_last_cuda_error; returns
+// STOKES_ERR_OOM for an allocation failure, else STOKES_ERR_CUDA.
+int cuda_fail(cudaError_t e, const char *where);
+
 // SplitMix64 (Steele, Lea & Flood 2014): output c (from 0) of the generator
 // seeded with `seed`.
 uint64_t splitmix64(uint64_t seed, uint64_t c);

@@ -468,10 +468,8 @@ __global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_batched(const BatchTile
 // general kernel: every field of the window in shared memory
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(RAS_THREADS) k_ras(RasArgs<T> a)
+__device__ __forceinline__ void ras_smem_tile(const RasArgs<T> &a, int tile, T *sm)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *sm = reinterpret_cast<T *>(smem_raw);
     const int plane = a.plane, W = a.wp;
     T *Ax = sm, *Ay = sm + plane, *Bx = sm + 2 * plane, *By = sm + 3 * plane;
     T *Ec = sm + 4 * plane, *En = sm + 5 * plane, *Rx = sm + 6 * plane, *Ry = sm + 7 * plane;
@@ -479,7 +477,7 @@ __global__ void __launch_bounds__(RAS_THREADS) k_ras(RasArgs<T> a)
     const GridDesc<T> &g = a.g;
     const int nx = g.nx, ny = g.ny;
     const size_t P = (size_t)g.pitch;
-    const Window win = window_of(a, (int)blockIdx.x);
+    const Window win = window_of(a, tile);
     const int x0 = win.x0, x1 = win.x1, y0 = win.y0, y1 = win.y1, ox0 = win.ox0, oy0 = win.oy0;
     const int wx = win.WX, wy = win.WY;
 
@@ -559,6 +557,38 @@ __global__ void __launch_bounds__(RAS_THREADS) k_ras(RasArgs<T> a)
         if (gx >= 1 && gx <= nx - 1) a.ox[gq] = cx[q];
         if (gy >= 1 && gy <= ny - 1) a.oy[gq] = cy[q];
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RAS_THREADS) k_ras(RasArgs<T> a)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    ras_smem_tile(a, (int)blockIdx.x, reinterpret_cast<T *>(smem_raw));
+}
+
+// batched form of the general kernel: one CTA per tile of the launch's list
+template <typename T>
+__global__ void __launch_bounds__(RAS_THREADS) k_ras_batched_smem(const BatchTiles<T> *__restrict__ tab, int count,
+                                                                  RasArgs<T> shape)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int t = (int)blockIdx.x;
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab[mid].tile_begin <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchTiles<T> &e = tab[lo];
+    RasArgs<T> a = shape;
+    a.g = e.g;
+    a.c = e.c;
+    a.vx = e.vx;
+    a.vy = e.vy;
+    a.ox = e.ox;
+    a.oy = e.oy;
+    a.tg = e.tg;
+    ras_smem_tile(a, t - e.tile_begin, reinterpret_cast<T *>(smem_raw));
 }
 
 // which kernel a configuration uses, and its launch shape
@@ -708,17 +738,18 @@ cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const 
 
 size_t ras_batched_smem_bytes(int ti, int tj, int overlap, size_t elem)
 {
-    const RasPlan p = plan_ras(ti, tj, ti, tj, overlap, elem, false);
-    return p.kind == PLAN_SMEM ? (size_t)-1 : p.smem;
+    return plan_ras(ti, tj, ti, tj, overlap, elem, false).smem;
 }
 
 template <typename T>
 cudaError_t launch_ras_batched(const BatchTiles<T> *tab, int count, int total, int ti, int tj, int ksweeps,
                                int overlap, T omega, cudaStream_t s)
 {
-    // the register layout sized for a full window (instances at least one tile wide)
+    // launch shape sized for the largest window (tile ti x tj grown by the
+    // overlap): the register layout in a persistent launch where it fits,
+    // else the general kernel with one CTA per tile
     const RasPlan p = plan_ras(ti, tj, ti, tj, overlap, sizeof(T), false);
-    if (p.kind == PLAN_SMEM) return cudaErrorInvalidValue;
+    if (p.smem > (size_t)ras_max_smem()) return cudaErrorInvalidValue;
     RasArgs<T> a{};
     a.omega = omega;
     a.ks = ksweeps;
@@ -728,13 +759,21 @@ cudaError_t launch_ras_batched(const BatchTiles<T> *tab, int count, int total, i
     a.strips = p.strips;
     a.wp = p.wp;
     a.plane = p.plane;
+    if (total <= 0) return cudaSuccess;
+    if (p.kind == PLAN_SMEM) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_ras_batched_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+        if (e != cudaSuccess) return e;
+        k_ras_batched_smem<T><<<total, RAS_THREADS, p.smem, s>>>(tab, count, a);
+        return cudaGetLastError();
+    }
     cudaError_t e = cudaFuncSetAttribute(k_ras_batched<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ras_batched<T>, p.threads, p.smem);
     if (e != cudaSuccess) return e;
     const int grid = std::min(total, std::max(per_sm, 1) * sm_count());
-    if (grid > 0) k_ras_batched<T><<<grid, p.threads, p.smem, s>>>(tab, count, total, a);
+    k_ras_batched<T><<<grid, p.threads, p.smem, s>>>(tab, count, total, a);
     return cudaGetLastError();
 }
 

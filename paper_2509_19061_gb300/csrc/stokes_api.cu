@@ -16,14 +16,16 @@
 using namespace stokes;
 
 namespace {
-
 thread_local char g_cuda_err[256] = "";
+} // namespace
 
-int cuda_fail(cudaError_t e, const char *where)
+int stokes::cuda_fail(cudaError_t e, const char *where)
 {
     std::snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s", where, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? STOKES_ERR_OOM : STOKES_ERR_CUDA;
 }
+
+namespace {
 
 #define CK(call)                                                                                                   \
     do {                                                                                                           \

@@ -150,12 +150,14 @@ class BatchSpec:
 
 
 def batch_specs(seed=5, count=256):
-    """Instance table of the batched workload: side n = 16 round(2^U(6,10) / 16),
-    contrast c = 10^U(2,6), one sinker r ~ U[0.05, 0.2], centre ~ U[0.3, 0.7]^2."""
+    """Instance table of the batched workload: side n = 64 round(2^U(6,10) / 64)
+    (cells log-uniform between 64^2 and 1024^2; a multiple of 64, so that
+    halving reaches a coarsest level of at most 16 x 16 cells), contrast
+    c = 10^U(2,6), one sinker r ~ U[0.05, 0.2], centre ~ U[0.3, 0.7]^2."""
     rng = np.random.default_rng(seed)
     out: List[BatchSpec] = []
     for _ in range(count):
-        n = int(16 * round(2.0 ** rng.uniform(6.0, 10.0) / 16.0))
+        n = int(64 * round(2.0 ** rng.uniform(6.0, 10.0) / 64.0))
         c = 10.0 ** rng.uniform(2.0, 6.0)
         r = rng.uniform(0.05, 0.2)
         cx = rng.uniform(0.3, 0.7)

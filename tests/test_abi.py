@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -66,3 +67,39 @@ def test_product_path_has_no_oracle_dependency():
                     src = f.read()
                 assert "import oracle" not in src and "from oracle" not in src, fn
                 assert "stokes_oracle" not in src, fn
+
+
+def test_batch_argument_errors_without_device(lib):
+    from paper_2509_19061_gb300 import api
+    f = api._lib()
+    out = ctypes.c_void_p(123)
+    n2 = (ctypes.c_int * 2)(32, 1)
+    l2 = (ctypes.c_double * 2)(1.0, 1.0)
+    assert f.stokes_batch_create(2, n2, n2, l2, l2, 1, None, ctypes.byref(out)) == api.STOKES_ERR_ARG
+    assert out.value is None
+    assert f.stokes_batch_create(0, n2, n2, l2, l2, 1, None, ctypes.byref(out)) == api.STOKES_ERR_ARG
+    assert f.stokes_batch_get_layout(None, 0, None, None, None) == api.STOKES_ERR_ARG
+    assert f.stokes_batch_smooth(None, None, None, None, None) == api.STOKES_ERR_ARG
+    assert f.stokes_batch_solve(None, None, None, None, None, None, None, None) == api.STOKES_ERR_ARG
+    assert f.stokes_batch_destroy(None) == api.STOKES_OK
+
+
+def test_batched_workload_recipe():
+    """Sides are multiples of 64 between 64 and 1024 (so that halving reaches
+    a coarsest level of at most 16 x 16 cells), contrasts in [1e2, 1e6],
+    sinkers inside the box; the table is a pure function of the seed."""
+    from paper_2509_19061_gb300 import inputs
+    a = inputs.batch_specs(seed=5, count=256)
+    assert a == inputs.batch_specs(seed=5, count=256)
+    ns = [s.n for s in a]
+    assert all(n % 64 == 0 and 64 <= n <= 1024 for n in ns)
+    assert len(set(ns)) >= 12
+    for n in ns:
+        m = n
+        while m % 2 == 0 and m > 16:
+            m //= 2
+        assert 2 * m * (m - 1) <= 1024
+    assert all(1e2 <= s.contrast <= 1e6 for s in a)
+    assert all(s.radius + 0.3 > 0 and 0.05 <= s.radius <= 0.2 and 0.3 <= s.cx <= 0.7 for s in a)
+    cells = np.array([n * n for n in ns], dtype=np.float64)
+    assert 1.0e5 < cells.mean() < 3.0e5

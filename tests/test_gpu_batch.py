@@ -1,0 +1,199 @@
+"""GPU parity of the batched path (many instances of different sizes in one
+launch per step, the batched V-cycle as one CUDA graph) against one context
+per instance, through the C ABI.
+
+Every instance follows the schedule of its own context, so the smoothing
+results and the V-cycle / defect-correction iterates must agree bit for bit;
+the flexible-CG solve sums its inner products in another order and is
+compared to rounding.  The single-context path is itself pinned to the FP64
+oracle by the other GPU tests.
+"""
+import numpy as np
+import pytest
+
+from paper_2509_19061_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_19061_gb300 import api as a, build
+    build.build()
+    return a
+
+
+def problems(sizes, seed):
+    out = []
+    for q, (nx, ny) in enumerate(sizes):
+        ec, en = inputs.random_viscosity(nx, ny, seed + q, (-2.0, 2.0))
+        prob = inputs.sinker_problem(nx, ny, eta_in=1e3, lx=1.0, ly=ny / nx)
+        prob.eta_c, prob.eta_n = ec, en
+        out.append(prob)
+    return out
+
+
+def single_results(api, probs, dtype, v0, p, fn):
+    """Run fn(ctx, vx, vy, pt) on one context per instance; natural-shape v."""
+    import torch
+    res = []
+    for q, prob in enumerate(probs):
+        ctx = api.StokesContext(prob.nx, prob.ny, prob.lx, prob.ly, dtype)
+        ctx.set_problem(prob)
+        vx, vy = ctx.pack(v0[q][0], "vx"), ctx.pack(v0[q][1], "vy")
+        pt = None if p is None else ctx.pack(p[q], "p")
+        out = fn(ctx, vx, vy, pt)
+        torch.cuda.synchronize()
+        res.append((ctx.unpack(vx, "vx"), ctx.unpack(vy, "vy"), out))
+        ctx.close()
+    return res
+
+
+def batch_context(api, probs, dtype):
+    b = api.BatchContext([q.nx for q in probs], [q.ny for q in probs], [q.lx for q in probs],
+                         [q.ly for q in probs], dtype)
+    b.set_problems(probs)
+    return b
+
+
+SIZES = [(40, 24), (64, 64), (100, 70), (33, 50), (8, 12)]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("kw", [
+    dict(variant="ras", sweeps=9, tile=(32, 32), k=4, overlap=3, seed=5),
+    dict(variant="ras", sweeps=7, tile=(16, 12), k=3, overlap=1, seed=11),
+    dict(variant="ras", sweeps=6, tile=(8, 8), k=2, overlap=0, shifts=[[1, 2], [7, 0], [3, 3]]),
+    dict(variant="jacobi", sweeps=5),
+    dict(variant="fused", sweeps=6),
+    dict(variant="blocked", sweeps=3, tile=(16, 16)),
+])
+def test_batched_smoothing_is_bitwise_the_single_context(api, dtype, kw):
+    import torch
+    probs = problems(SIZES, 10)
+    v0 = [inputs.random_velocity(q.nx, q.ny, 100 + i) for i, q in enumerate(probs)]
+    p = [inputs.random_pressure(q.nx, q.ny, 200 + i, 0.5) for i, q in enumerate(probs)]
+    ref = single_results(api, probs, dtype, v0, p, lambda c, vx, vy, pt: c.smooth(vx, vy, pt, **kw))
+    b = batch_context(api, probs, dtype)
+    vx, vy = b.pack([v[0] for v in v0], "vx"), b.pack([v[1] for v in v0], "vy")
+    pt = b.pack(p, "p")
+    b.smooth(vx, vy, pt, **kw)
+    torch.cuda.synchronize()
+    for i in range(len(probs)):
+        assert np.array_equal(b.unpack(vx, "vx", i), ref[i][0]), (i, "vx")
+        assert np.array_equal(b.unpack(vy, "vy", i), ref[i][1]), (i, "vy")
+    # a second call reuses the cached plan and continues from the result
+    b.smooth(vx, vy, pt, **kw)
+    ref2 = single_results(api, probs, dtype, [(r[0], r[1]) for r in ref], p,
+                          lambda c, x, y, q: c.smooth(x, y, q, **kw))
+    torch.cuda.synchronize()
+    for i in range(len(probs)):
+        assert np.array_equal(b.unpack(vx, "vx", i), ref2[i][0])
+        assert np.array_equal(b.unpack(vy, "vy", i), ref2[i][1])
+    b.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_batched_energy_matches_the_single_context(api, dtype):
+    probs = problems(SIZES, 20)
+    v0 = [inputs.random_velocity(q.nx, q.ny, 300 + i) for i, q in enumerate(probs)]
+    p = [inputs.random_pressure(q.nx, q.ny, 400 + i, 0.5) for i, q in enumerate(probs)]
+    ref = single_results(api, probs, dtype, v0, p, lambda c, vx, vy, pt: c.energy(vx, vy, pt))
+    b = batch_context(api, probs, dtype)
+    vx, vy = b.pack([v[0] for v in v0], "vx"), b.pack([v[1] for v in v0], "vy")
+    e = b.energy(vx, vy, b.pack(p, "p"))
+    for i in range(len(probs)):
+        rv, _, ff = ref[i][2]
+        assert abs(e[i, 0] - rv) <= 1e-12 * rv and abs(e[i, 1] - ff) <= 1e-12 * ff
+    b.close()
+
+
+MG_SIZES = [(64, 64), (96, 64), (80, 48), (128, 128), (32, 32)]
+
+
+@pytest.mark.parametrize("dtype,inner", [("f64", "f64"), ("f64", "f32"), ("f32", "f32")])
+@pytest.mark.parametrize("sm", [
+    dict(variant="ras", tile=(32, 32), k=4, overlap=3, seed=1, nu_max=12),
+    dict(variant="ras", tile=(16, 8), k=2, overlap=0, seed=9, nu_max=10),
+    dict(variant="jacobi", nu_max=9),
+])
+def test_batched_defect_correction_is_bitwise_the_single_context(api, dtype, inner, sm):
+    """Three defect-correction cycles: every iterate is v += B(b - M v), with
+    no inner products on the path, so the batched V-cycle graph must
+    reproduce each instance's own context bit for bit."""
+    import torch
+    probs = [inputs.sinker_problem(nx, ny, eta_in=10.0 ** (1 + 0.5 * i), lx=1.0, ly=ny / nx)
+             for i, (nx, ny) in enumerate(MG_SIZES)]
+    v0 = [(np.zeros((q.ny, q.nx + 1)), np.zeros((q.ny + 1, q.nx))) for q in probs]
+    kw = dict(sm, inner=inner, krylov=False, tol=0.0, max_cycles=3)
+    ref = single_results(api, probs, dtype, v0, None, lambda c, vx, vy, pt: c.vcycle(vx, vy, pt, **kw))
+    b = batch_context(api, probs, dtype)
+    vx, vy = b.slab(), b.slab()
+    st, e, cyc, sts = b.solve(vx, vy, None, **kw)
+    torch.cuda.synchronize()
+    assert st == api.STOKES_ERR_NOT_CONVERGED and list(cyc) == [3] * len(probs)
+    for i in range(len(probs)):
+        assert np.array_equal(b.unpack(vx, "vx", i), ref[i][0]), i
+        assert np.array_equal(b.unpack(vy, "vy", i), ref[i][1]), i
+        assert abs(e[i] - ref[i][2][1]) <= 1e-12 * ref[i][2][1]
+    assert b.kernels() > 0
+    b.close()
+
+
+def test_batched_fcg_reaches_1e8_like_the_single_contexts(api):
+    """Flexible CG to E_v <= 1e-8 on sinkers of uneven sizes and contrasts
+    1e2..1e6 (the batched workload's recipe): every instance converges, in
+    the cycles its own context needs (rounding of the inner products aside),
+    to the same solution."""
+    import torch
+    specs = inputs.batch_specs(seed=5, count=6)
+    probs = [inputs.batch_problem(sp) for sp in specs]
+    kw = dict(variant="ras", tile=(32, 32), k=4, overlap=3, seed=1, nu_max=40, inner="f32", krylov=True,
+              tol=1e-8, max_cycles=200)
+    v0 = [(np.zeros((q.ny, q.nx + 1)), np.zeros((q.ny + 1, q.nx))) for q in probs]
+    ref = single_results(api, probs, "f64", v0, None, lambda c, vx, vy, pt: c.vcycle(vx, vy, pt, **kw))
+    b = batch_context(api, probs, "f64")
+    vx, vy = b.slab(), b.slab()
+    st, e, cyc, sts = b.solve(vx, vy, None, **kw)
+    torch.cuda.synchronize()
+    assert st == api.STOKES_OK and all(s == api.STOKES_OK for s in sts)
+    for i, q in enumerate(probs):
+        rst, re, rc = ref[i][2]
+        assert rst == api.STOKES_OK and e[i] <= 1e-8
+        assert abs(int(cyc[i]) - rc) <= 2, (i, cyc[i], rc)
+        dx = b.unpack(vx, "vx", i) - ref[i][0]
+        dy = b.unpack(vy, "vy", i) - ref[i][1]
+        num = np.sum(dx ** 2) + np.sum(dy ** 2)
+        den = np.sum(ref[i][0] ** 2) + np.sum(ref[i][1] ** 2)
+        assert np.sqrt(num / den) <= 1e-6, i
+    b.close()
+
+
+def test_batched_errors(api):
+    import torch
+    probs = problems([(32, 32), (40, 40)], 30)
+    b = batch_context(api, probs, "f64")
+    vx, vy = b.slab(), b.slab()
+    with pytest.raises(api.StokesError) as ex:
+        b.smooth(vx, vy, variant="rbgs", sweeps=2)
+    assert ex.value.status == api.STOKES_ERR_ARG
+    with pytest.raises(api.StokesError) as ex:
+        b.smooth(vx, vy, variant="ras", sweeps=2, k=0)
+    assert ex.value.status == api.STOKES_ERR_ARG
+    b.close()
+    # an instance whose coarsest level is too large for the dense solve
+    b = batch_context(api, problems([(32, 32), (126, 126)], 40), "f64")
+    with pytest.raises(api.StokesError) as ex:
+        b.solve(b.slab(), b.slab(), variant="ras", inner="f64")
+    assert ex.value.status == api.STOKES_ERR_ARG
+    b.close()
+    # solve before the problem is set
+    b = api.BatchContext([32], [32], dtype="f64")
+    with pytest.raises(api.StokesError) as ex:
+        b.solve(b.slab(), b.slab(), variant="ras")
+    assert ex.value.status == api.STOKES_ERR_STATE
+    b.close()
+    torch.cuda.synchronize()
