@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the variant table, e2e and CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--solve-n", type=int, default=4096, help="grid of the time-to-1e-8 solve")
+    ap.add_argument("--batch", type=int, default=256, help="instances of the batched workload (0: skip)")
     return ap.parse_args()
 
 
@@ -289,6 +290,8 @@ def run_ours(args):
         line["e2e"] = e2e_measure(args, ctx, prob, stream, world)
         line["variants"] = variant_table(args, api, prob)
         line["time_to_1e-8"] = solve_times(args, api)
+        if args.batch > 0:
+            line["batched"] = batch_leg(args, api)
         if world == 1:
             line["cpu_baseline"] = {kk: vv for kk, vv in cpu_sample(args, args.cpu_seconds).items()
                                     if kk != "seconds"}
@@ -370,6 +373,104 @@ def solve_times(args, api):
         out[inner + "_inner"] = {"seconds": dt, "cycles": cyc, "final_energy_residual": e, "status": st}
     out["speedup_f32_over_f64"] = out["f64_inner"]["seconds"] / out["f32_inner"]["seconds"]
     ctx.close()
+    return out
+
+
+def batch_leg(args, api):
+    """The batched workload: 256 seeded sinkers of uneven sizes (sides
+    64..1024, contrasts 1e2..1e6), all advanced together by the batched path
+    versus a loop over one context per instance.  Smoothing: FP32 RAS (32 x 32,
+    k = 4, overlap 3), 20 sweeps per call, aggregate Gcell-updates/s.  Solve:
+    FP64 flexible CG around the FP32 V-cycle to E_v <= 1e-8 for every
+    instance, wall time of the whole set (hierarchies and graphs built
+    beforehand)."""
+    import torch
+    from paper_2509_19061_gb300 import inputs
+    specs = inputs.batch_specs(seed=5, count=args.batch)
+    probs = [inputs.batch_problem(sp) for sp in specs]
+    cells = sum(q.nx * q.ny for q in probs)
+    out = {"workload": "batch_%d_sinkers_64to1024_seed5" % len(probs), "instances": len(probs),
+           "cells_total": cells}
+    sw = 20
+    smooth_kw = dict(variant="ras", sweeps=sw, tile=(32, 32), k=4, overlap=3, seed=1)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps / 1e3
+
+    # batched smoothing
+    b = api.BatchContext([q.nx for q in probs], [q.ny for q in probs], dtype="f32")
+    b.set_problems(probs)
+    vx, vy = b.slab(), b.slab()
+    k0 = b.kernels()
+    t_b = timed(lambda: b.smooth(vx, vy, None, **smooth_kw), 5)
+    launches_b = (b.kernels() - k0) // 6
+    # one context per instance
+    ctxs = []
+    for q in probs:
+        c = api.StokesContext(q.nx, q.ny, 1.0, 1.0, "f32")
+        c.set_problem(q)
+        ctxs.append((c, c.field(), c.field()))
+
+    def loop():
+        for c, x, y in ctxs:
+            c.smooth(x, y, None, **smooth_kw)
+    t_l = timed(loop, 2)
+    for c, _, _ in ctxs:
+        c.close()
+    b.close()
+    out["smooth"] = {"sweeps": sw, "schedule": "ras 32x32 k4 o3 f32",
+                     "batched_gcell_updates_per_s": cells * sw / t_b / 1e9, "batched_ms": 1e3 * t_b,
+                     "batched_launches": launches_b,
+                     "per_instance_gcell_updates_per_s": cells * sw / t_l / 1e9, "per_instance_ms": 1e3 * t_l,
+                     "speedup": t_l / t_b}
+    # time to E_v <= 1e-8 for every instance
+    kw = dict(variant="ras", tile=(32, 32), k=4, overlap=3, seed=1, nu_max=40, inner="f32", krylov=True,
+              tol=1e-8, max_cycles=300)
+    b = api.BatchContext([q.nx for q in probs], [q.ny for q in probs], dtype="f64")
+    b.set_problems(probs)
+    vx, vy = b.slab(), b.slab()
+    b.solve(vx, vy, None, **kw)  # hierarchy and graph
+    vx.zero_()
+    vy.zero_()
+    torch.cuda.synchronize()
+    k0 = b.kernels()
+    t0 = time.perf_counter()
+    st, e, cyc, sts = b.solve(vx, vy, None, **kw)
+    torch.cuda.synchronize()
+    t_bs = time.perf_counter() - t0
+    kb = b.kernels() - k0
+    b.close()
+    t_ls, worst, conv = 0.0, 0, 0
+    for q in probs:
+        c = api.StokesContext(q.nx, q.ny, 1.0, 1.0, "f64")
+        c.set_problem(q)
+        x, y = c.field(), c.field()
+        c.vcycle(x, y, None, **kw)
+        x.zero_()
+        y.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s1, e1, c1 = c.vcycle(x, y, None, **kw)
+        torch.cuda.synchronize()
+        t_ls += time.perf_counter() - t0
+        worst = max(worst, c1)
+        conv += s1 == api.STOKES_OK
+        c.close()
+    out["solve"] = {"tol": 1e-8, "outer": "f64 flexible CG", "inner": "f32 V-cycle, ras 32x32 k4 o3, nu cap 40",
+                    "batched_seconds": t_bs, "batched_status": int(st),
+                    "batched_converged": int(sum(1 for x in sts if x == api.STOKES_OK)),
+                    "batched_max_cycles": int(max(cyc)), "batched_kernels": int(kb),
+                    "per_instance_seconds": t_ls, "per_instance_converged": int(conv),
+                    "per_instance_max_cycles": int(worst), "speedup": t_ls / t_bs}
     return out
 
 

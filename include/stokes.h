@@ -348,6 +348,13 @@ int stokes_batch_residual_energy(stokes_batch *b, const void *vx, const void *vy
 int stokes_batch_solve(stokes_batch *b, void *vx, void *vy, const void *p, const stokes_mg_params *params,
                        double *final_rel_resid, int *cycles, int *status);
 
+/* Batch options: the stokes_option values of stokes_set_option, with the
+ * same meaning (STOKES_OPT_USE_TMA: 0 reads the windows of the batched tile
+ * kernel straight from global memory, same results).  A bounded wait that
+ * gives up is reported by the next stokes_batch_residual_energy or
+ * stokes_batch_solve as STOKES_ERR_TIMEOUT. */
+int stokes_batch_set_option(stokes_batch *b, int option, long long value);
+
 /* Number of kernels the batch has launched so far (graph replays count
  * every kernel node). */
 int stokes_batch_kernels(const stokes_batch *b, long long *kernels);

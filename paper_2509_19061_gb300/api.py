@@ -89,6 +89,7 @@ _SIGS = {
     "stokes_batch_solve": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(stokes_mg_params), ctypes.POINTER(_D),
                                 ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "stokes_batch_kernels": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
+    "stokes_batch_set_option": (_I, [_VP, _I, ctypes.c_longlong]),
     "stokes_batch_destroy": (_I, [_VP]),
     "stokes_destroy": (_I, [_VP]),
     "stokes_strerror": (ctypes.c_char_p, [_I]),
@@ -290,6 +291,10 @@ def stokes_batch_solve(b, count, vx, vy, p, params):
     return st, np.array(fe[:]), np.array(cy[:], dtype=np.int64), np.array(ss[:], dtype=np.int64)
 
 
+def stokes_batch_set_option(b, option, value):
+    _check(_lib().stokes_batch_set_option(b, option, int(value)), "stokes_batch_set_option")
+
+
 def stokes_batch_kernels(b):
     k = ctypes.c_longlong()
     _check(_lib().stokes_batch_kernels(b, ctypes.byref(k)), "stokes_batch_kernels")
@@ -479,3 +484,6 @@ class BatchContext:
 
     def kernels(self):
         return stokes_batch_kernels(self.b)
+
+    def set_option(self, option, value):
+        stokes_batch_set_option(self.b, option, value)

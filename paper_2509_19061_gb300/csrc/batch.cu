@@ -14,6 +14,8 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>
+
 #include "../../include/stokes.h"
 #include "batch.h"
 #include "internal.h"
@@ -135,6 +137,7 @@ struct RasForm {
 template <typename T>
 struct TileLaunch {
     const BatchTiles<T> *tab;
+    const void *maps; // per-instance tensor maps (TMA staging), or NULL
     int count, total, ti, tj, ks, overlap;
 };
 
@@ -159,7 +162,7 @@ struct Group {
 
 // the ping-pong of smooth_buffers for every instance of `gi` at once
 template <typename T>
-int plan_group(Owned &o, const std::vector<GInst<T>> &gi, const RasForm &f, bool walls, bool single,
+int plan_group(Owned &o, const std::vector<GInst<T>> &gi, const RasForm &f, bool walls, bool single, bool tma,
                const BLevel<T> *lev, Group<T> *out, cudaStream_t s)
 {
     *out = Group<T>();
@@ -203,6 +206,7 @@ int plan_group(Owned &o, const std::vector<GInst<T>> &gi, const RasForm &f, bool
             e.oy = by[q];
             e.tg = make_tiles(x.g.nx, x.g.ny, x.ti, x.tj, si, sj);
             e.tile_begin = total;
+            e.inst = x.inst;
             total += e.tg.ntx * e.tg.nty;
             shi = std::max(shi, std::min(x.ti, x.g.nx));
             shj = std::max(shj, std::min(x.tj, x.g.ny));
@@ -213,6 +217,14 @@ int plan_group(Owned &o, const std::vector<GInst<T>> &gi, const RasForm &f, bool
         if (ras_batched_smem_bytes(shi, shj, ov, sizeof(T)) > (size_t)ras_max_smem()) return STOKES_ERR_ARG;
         TileLaunch<T> L;
         ST(upload(o, tab, &L.tab, s));
+        L.maps = nullptr;
+        if (tma && ras_batched_tma(shi, shj, ov, sizeof(T))) {
+            std::vector<CUtensorMap> m(n * (ras_batched_maps_bytes() / sizeof(CUtensorMap)));
+            CK(ras_batched_encode<T>(tab.data(), (int)n, shi, shj, ov, m.data()));
+            const CUtensorMap *dm = nullptr;
+            ST(upload(o, m, &dm, s));
+            L.maps = dm;
+        }
         L.count = (int)n;
         L.total = total;
         L.ti = shi;
@@ -225,20 +237,22 @@ int plan_group(Owned &o, const std::vector<GInst<T>> &gi, const RasForm &f, bool
     return STOKES_OK;
 }
 
+// live (device, may be NULL): instances whose flag is 0 are skipped
 template <typename T>
-int run_group(const Group<T> &G, cudaStream_t s, long long *nk)
+int run_group(const Group<T> &G, const int *live, const RasRun &run, cudaStream_t s, long long *nk)
 {
     if (G.launches.empty()) return STOKES_OK;
     if (G.walls) {
-        CK(batch_copy<T>(G.lev, G.sub.map, G.sub.nseg, G.sub.nblocks, true, true, s));
+        CK(batch_copy<T>(G.lev, G.sub.map, G.sub.nseg, G.sub.nblocks, true, true, live, s));
         ++*nk;
     }
     for (const TileLaunch<T> &L : G.launches) {
-        CK(launch_ras_batched<T>(L.tab, L.count, L.total, L.ti, L.tj, L.ks, L.overlap, G.omega, s));
+        CK(launch_ras_batched<T>(L.tab, L.maps, L.count, L.total, L.ti, L.tj, L.ks, L.overlap, G.omega, live, run,
+                                 s));
         ++*nk;
     }
     if (G.back) {
-        CK(batch_copy<T>(G.lev, G.sub.map, G.sub.nseg, G.sub.nblocks, false, false, s));
+        CK(batch_copy<T>(G.lev, G.sub.map, G.sub.nseg, G.sub.nblocks, false, false, live, s));
         ++*nk;
     }
     return STOKES_OK;
@@ -312,6 +326,9 @@ struct stokes_batch {
     int *dactive = nullptr, *hactive = nullptr;
     double *hsum = nullptr;
     void *kw[8] = {};               // outer work r, z, p, q (x, y)
+    int *dstatus = nullptr, *hstatus = nullptr; // bounded-wait status word
+    bool use_tma = true;            // STOKES_OPT_USE_TMA
+    long long wait_limit = 2000000000LL;
     BHier *mg = nullptr;
     Owned base;                     // tables tied to the batch itself
     // smoothing plan cache
@@ -338,6 +355,15 @@ struct stokes_batch {
 };
 
 namespace {
+
+RasRun run_of(const stokes_batch *b)
+{
+    RasRun r;
+    r.allow_tma = b->use_tma;
+    r.status = b->dstatus;
+    r.wait_limit = b->wait_limit;
+    return r;
+}
 
 void free_hier(BHier *h)
 {
@@ -640,9 +666,9 @@ int plan_precond(stokes_batch *b, const stokes_mg_params *p, Precond<To, Ti> *P)
             f1.k = std::max(sweeps, 1);
             f1.overlap = 0;
             // zero-initialised walls of v and s at inner levels: no wall copies
-            ST(plan_group<Ti>(o, g1, f1, false, true, P->lev[l], &P->grp[l][ph][0], s));
-            ST(plan_group<Ti>(o, g2, ras_form(sm, sweeps, seed, STOKES_SHIFT_SPLITMIX), false, false, P->lev[l],
-                              &P->grp[l][ph][1], s));
+            ST(plan_group<Ti>(o, g1, f1, false, true, b->use_tma, P->lev[l], &P->grp[l][ph][0], s));
+            ST(plan_group<Ti>(o, g2, ras_form(sm, sweeps, seed, STOKES_SHIFT_SPLITMIX), false, false, b->use_tma,
+                              P->lev[l], &P->grp[l][ph][1], s));
         }
     }
     std::vector<BDense<Ti>> dt(n);
@@ -669,31 +695,35 @@ int plan_precond(stokes_batch *b, const stokes_mg_params *p, Precond<To, Ti> *P)
 
 // One application of z = B r for every instance (the order of the
 // single-problem V-cycle, instances in lockstep by level).
+// Instances whose live flag is 0 (converged, diverged or out of cycles) are
+// skipped: their z keeps its last value, which the outer iteration no
+// longer uses.
 template <typename To, typename Ti>
-int enqueue_precond(const Precond<To, Ti> &P, int Lmax, int count, cudaStream_t s, long long *nk)
+int enqueue_precond(const Precond<To, Ti> &P, int Lmax, int count, const int *live, const RasRun &run,
+                    cudaStream_t s, long long *nk)
 {
-    CK((batch_cast_in<To, Ti>(P.outer, P.lev[0], P.l0.map, P.l0.nseg, P.l0.nblocks, s)));
+    CK((batch_cast_in<To, Ti>(P.outer, P.lev[0], P.l0.map, P.l0.nseg, P.l0.nblocks, live, s)));
     ++*nk;
     for (int l = 0; l < Lmax - 1; ++l) {
-        CK(batch_zero_v<Ti>(P.lev[l], P.fine[l].map, P.fine[l].nseg, P.fine[l].nblocks, s));
+        CK(batch_zero_v<Ti>(P.lev[l], P.fine[l].map, P.fine[l].nseg, P.fine[l].nblocks, live, s));
         ++*nk;
     }
     for (int l = 0; l < Lmax - 1; ++l) {
-        ST(run_group<Ti>(P.grp[l][0][0], s, nk));
-        ST(run_group<Ti>(P.grp[l][0][1], s, nk));
-        CK(batch_residual<Ti>(P.lev[l], P.fine[l].map, P.fine[l].nseg, P.fine[l].nblocks, s));
-        CK(batch_restrict<Ti>(P.lev[l], P.coarse[l].map, P.coarse[l].nseg, P.coarse[l].nblocks, s));
+        ST(run_group<Ti>(P.grp[l][0][0], live, run, s, nk));
+        ST(run_group<Ti>(P.grp[l][0][1], live, run, s, nk));
+        CK(batch_residual<Ti>(P.lev[l], P.fine[l].map, P.fine[l].nseg, P.fine[l].nblocks, live, s));
+        CK(batch_restrict<Ti>(P.lev[l], P.coarse[l].map, P.coarse[l].nseg, P.coarse[l].nblocks, live, s));
         *nk += 2;
     }
-    CK(batch_dense<Ti>(P.dense, count, P.rows, s));
+    CK(batch_dense<Ti>(P.dense, count, P.rows, live, s));
     *nk += 3;
     for (int l = Lmax - 2; l >= 0; --l) {
-        CK(batch_prolong<Ti>(P.lev[l], P.fine[l].map, P.fine[l].nseg, P.fine[l].nblocks, s));
+        CK(batch_prolong<Ti>(P.lev[l], P.fine[l].map, P.fine[l].nseg, P.fine[l].nblocks, live, s));
         ++*nk;
-        ST(run_group<Ti>(P.grp[l][1][0], s, nk));
-        ST(run_group<Ti>(P.grp[l][1][1], s, nk));
+        ST(run_group<Ti>(P.grp[l][1][0], live, run, s, nk));
+        ST(run_group<Ti>(P.grp[l][1][1], live, run, s, nk));
     }
-    CK((batch_cast_out<To, Ti>(P.outer, P.lev[0], P.l0.map, P.l0.nseg, P.l0.nblocks, s)));
+    CK((batch_cast_out<To, Ti>(P.outer, P.lev[0], P.l0.map, P.l0.nseg, P.l0.nblocks, live, s)));
     ++*nk;
     return STOKES_OK;
 }
@@ -706,7 +736,7 @@ int capture(stokes_batch *b, const stokes_mg_params *p)
     long long nk = 0;
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(b->gstream, cudaStreamCaptureModeThreadLocal));
-    const int st = enqueue_precond<To, Ti>(P, b->mg->Lmax, b->count, b->gstream, &nk);
+    const int st = enqueue_precond<To, Ti>(P, b->mg->Lmax, b->count, b->dactive, run_of(b), b->gstream, &nk);
     const cudaError_t e = cudaStreamEndCapture(b->gstream, &graph);
     if (st != STOKES_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -798,11 +828,18 @@ int rhs(stokes_batch *b)
     return STOKES_OK;
 }
 
-// per-instance sums of the last reduction (2 doubles each), synchronising
+// per-instance sums of the last reduction (2 doubles each), synchronising;
+// reports (and clears) a bounded wait that gave up since the last check
 int read_sums(stokes_batch *b, const double *dev)
 {
     CK(cudaMemcpyAsync(b->hsum, dev, 2 * (size_t)b->count * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(b->hstatus, b->dstatus, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     CK(cudaStreamSynchronize(b->stream));
+    if (*b->hstatus) {
+        CK(cudaMemsetAsync(b->dstatus, 0, sizeof(int), b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+        return STOKES_ERR_TIMEOUT;
+    }
     return STOKES_OK;
 }
 
@@ -966,7 +1003,7 @@ int smooth_impl(stokes_batch *b, void *vx, void *vy, const void *p, const stokes
         RasForm ff = f;
         ff.shifts = shifts.empty() ? nullptr : shifts.data();
         ST(upload(b->sm_own, lev, &dlev, b->stream));
-        ST(plan_group<T>(b->sm_own, gi, ff, true, false, dlev, &G, b->stream));
+        ST(plan_group<T>(b->sm_own, gi, ff, true, false, b->use_tma, dlev, &G, b->stream));
         b->sm_key = key;
         b->sm_shifts = shifts;
         b->sm_v[0] = vx;
@@ -975,7 +1012,7 @@ int smooth_impl(stokes_batch *b, void *vx, void *vy, const void *p, const stokes
     }
     ST(rhs<T>(b));
     long long nk = 0;
-    const int st = run_group<T>(G, b->stream, &nk);
+    const int st = run_group<T>(G, nullptr, run_of(b), b->stream, &nk);
     b->kernels += nk;
     return st;
 }
@@ -1049,6 +1086,9 @@ int stokes_batch_create(int count, const int *nx, const int *ny, const double *l
         if (e == cudaSuccess) e = cudaMalloc(&b->dactive, (size_t)count * sizeof(int));
         if (e == cudaSuccess) e = cudaMallocHost(&b->hactive, (size_t)count * sizeof(int));
         if (e == cudaSuccess) e = cudaMallocHost(&b->hsum, 2 * (size_t)count * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&b->dstatus, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->dstatus, 0, sizeof(int), b->stream);
+        if (e == cudaSuccess) e = cudaMallocHost(&b->hstatus, sizeof(int));
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "stokes_batch_create");
     }
@@ -1167,6 +1207,28 @@ int stokes_batch_solve(stokes_batch *b, void *vx, void *vy, const void *p, const
     return solve_impl<float>(b, vx, vy, p, params, final_rel_resid, cycles, status);
 }
 
+int stokes_batch_set_option(stokes_batch *b, int option, long long value)
+{
+    if (!b) return STOKES_ERR_ARG;
+    switch (option) {
+    case STOKES_OPT_USE_TMA:
+    case STOKES_OPT_WAIT_LIMIT_CYCLES:
+        // plans and the captured graph embed both: rebuild them
+        CK(cudaStreamSynchronize(b->stream));
+        if (b->gexec) {
+            cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+        }
+        b->pc_own.release();
+        b->sm_own.release();
+        b->sm_valid = false;
+        if (option == STOKES_OPT_USE_TMA) b->use_tma = value != 0;
+        else b->wait_limit = value;
+        return STOKES_OK;
+    default: return STOKES_ERR_ARG;
+    }
+}
+
 int stokes_batch_kernels(const stokes_batch *b, long long *kernels)
 {
     if (!b || !kernels) return STOKES_ERR_ARG;
@@ -1195,11 +1257,12 @@ int stokes_batch_destroy(stokes_batch *b)
     for (void *w : b->kw)
         if (w) cudaFree(w);
     void *fs[] = {b->eta_c, b->eta_n, b->fx, b->fy, b->bx, b->by, b->sx, b->sy, b->ivx, b->ivy,
-                  b->partials, b->dsum, b->dpq, b->dzq, b->alpha, b->beta, b->dactive};
+                  b->partials, b->dsum, b->dpq, b->dzq, b->alpha, b->beta, b->dactive, b->dstatus};
     for (void *f : fs)
         if (f) cudaFree(f);
     if (b->hactive) cudaFreeHost(b->hactive);
     if (b->hsum) cudaFreeHost(b->hsum);
+    if (b->hstatus) cudaFreeHost(b->hstatus);
     delete b;
     return STOKES_OK;
 }

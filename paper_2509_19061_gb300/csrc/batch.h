@@ -58,33 +58,40 @@ struct BRhs {
 
 constexpr int BATCH_BX = 32, BATCH_BY = 8;
 
+// The multigrid level kernels take `active` (device, one flag per instance,
+// may be NULL): instances whose flag is 0 are skipped.
+
 template <typename T> // over (nx+1) x (ny+1) per instance
 cudaError_t batch_rhs(const BRhs<T> *tab, const BSeg *map, int nseg, int nblocks, cudaStream_t s);
 
 template <typename T>
-cudaError_t batch_residual(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, cudaStream_t s);
+cudaError_t batch_residual(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, const int *active,
+                           cudaStream_t s);
 template <typename T>
-cudaError_t batch_restrict(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, cudaStream_t s);
+cudaError_t batch_restrict(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, const int *active,
+                           cudaStream_t s);
 template <typename T>
-cudaError_t batch_prolong(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, cudaStream_t s);
+cudaError_t batch_prolong(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, const int *active,
+                          cudaStream_t s);
 // zero v of every listed level (map over pitch x (ny+1))
 template <typename T>
-cudaError_t batch_zero_v(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, cudaStream_t s);
+cudaError_t batch_zero_v(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, const int *active,
+                         cudaStream_t s);
 // copy the wall entries (copy_walls) or the in-extent entries (copy_all) of
 // (vx, vy) into (sx, sy) when to_scratch, else the other way
 template <typename T>
 cudaError_t batch_copy(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, bool walls_only, bool to_scratch,
-                       cudaStream_t s);
+                       const int *active, cudaStream_t s);
 // dense coarsest solves: `rows` unknowns in total over `count` instances
 template <typename T>
-cudaError_t batch_dense(const BDense<T> *tab, int count, int rows, cudaStream_t s);
+cudaError_t batch_dense(const BDense<T> *tab, int count, int rows, const int *active, cudaStream_t s);
 // level-0 inner b = (Ti) r and z = (To) level-0 inner v, over pitch x (ny+1)
 template <typename To, typename Ti>
 cudaError_t batch_cast_in(const BOuter<To> *out, const BLevel<Ti> *l0, const BSeg *map, int nseg, int nblocks,
-                          cudaStream_t s);
+                          const int *active, cudaStream_t s);
 template <typename To, typename Ti>
 cudaError_t batch_cast_out(const BOuter<To> *out, const BLevel<Ti> *l0, const BSeg *map, int nseg, int nblocks,
-                           cudaStream_t s);
+                           const int *active, cudaStream_t s);
 
 // ---- outer solve (per-instance sums into out[2 * inst + {0, 1}]) -------------
 // partials: 2 doubles per block of the launch

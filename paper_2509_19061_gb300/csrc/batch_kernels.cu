@@ -113,10 +113,11 @@ __global__ void kb_rhs(const BRhs<T> *__restrict__ tab, const BSeg *__restrict__
 
 // ---- level operations ----------------------------------------------------------
 template <typename T>
-__global__ void kb_residual(const BLevel<T> *__restrict__ tab, const BSeg *__restrict__ m, int n)
+__global__ void kb_residual(const BLevel<T> *__restrict__ tab, const BSeg *__restrict__ m, int n,
+                            const int *__restrict__ active)
 {
     const Pt p = point_of(m, n);
-    if (!p.valid) return;
+    if (!p.valid || (active && !active[p.inst])) return;
     const BLevel<T> &l = tab[p.inst];
     const GridDesc<T> &g = l.g;
     const int i = p.i, j = p.j;
@@ -141,30 +142,33 @@ __global__ void kb_residual(const BLevel<T> *__restrict__ tab, const BSeg *__res
 }
 
 template <typename T>
-__global__ void kb_restrict(const BLevel<T> *__restrict__ tab, const BSeg *__restrict__ m, int n)
+__global__ void kb_restrict(const BLevel<T> *__restrict__ tab, const BSeg *__restrict__ m, int n,
+                            const int *__restrict__ active)
 {
     const Pt p = point_of(m, n);
-    if (!p.valid) return;
+    if (!p.valid || (active && !active[p.inst])) return;
     const BLevel<T> &l = tab[p.inst];
     restrict_point(l.g.nx, l.g.ny, l.g.pitch, l.cnx, l.cny, l.cp, (const T *)l.rx, (const T *)l.ry, l.cbx, l.cby,
                    p.j, p.i);
 }
 
 template <typename T>
-__global__ void kb_prolong(const BLevel<T> *__restrict__ tab, const BSeg *__restrict__ m, int n)
+__global__ void kb_prolong(const BLevel<T> *__restrict__ tab, const BSeg *__restrict__ m, int n,
+                            const int *__restrict__ active)
 {
     const Pt p = point_of(m, n);
-    if (!p.valid) return;
+    if (!p.valid || (active && !active[p.inst])) return;
     const BLevel<T> &l = tab[p.inst];
     prolong_point(l.g.nx, l.g.ny, l.g.pitch, l.cnx, l.cny, l.cp, (const T *)l.cvx, (const T *)l.cvy, l.vx, l.vy,
                   p.j, p.i);
 }
 
 template <typename T>
-__global__ void kb_zero_v(const BLevel<T> *__restrict__ tab, const BSeg *__restrict__ m, int n)
+__global__ void kb_zero_v(const BLevel<T> *__restrict__ tab, const BSeg *__restrict__ m, int n,
+                            const int *__restrict__ active)
 {
     const Pt p = point_of(m, n);
-    if (!p.valid) return;
+    if (!p.valid || (active && !active[p.inst])) return;
     const BLevel<T> &l = tab[p.inst];
     const size_t q = (size_t)p.j * l.g.pitch + p.i;
     l.vx[q] = T(0);
@@ -173,10 +177,10 @@ __global__ void kb_zero_v(const BLevel<T> *__restrict__ tab, const BSeg *__restr
 
 template <typename T>
 __global__ void kb_copy(const BLevel<T> *__restrict__ tab, const BSeg *__restrict__ m, int n, bool walls_only,
-                        bool to_scratch)
+                        bool to_scratch, const int *__restrict__ active)
 {
     const Pt p = point_of(m, n);
-    if (!p.valid) return;
+    if (!p.valid || (active && !active[p.inst])) return;
     const BLevel<T> &l = tab[p.inst];
     const GridDesc<T> &g = l.g;
     const int i = p.i, j = p.j;
@@ -216,22 +220,28 @@ __device__ __forceinline__ void unk_pos(int u, int nx, int ny, int &comp, int &j
 }
 
 template <typename T>
-__global__ void kb_dense_pack(const BDense<T> *__restrict__ tab, int count, int rows)
+__global__ void kb_dense_pack(const BDense<T> *__restrict__ tab, int count, int rows,
+                                const int *__restrict__ active)
 {
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= rows) return;
-    const BDense<T> &d = tab[dense_of(tab, count, u)];
+    const int di = dense_of(tab, count, u);
+    if (active && !active[di]) return;
+    const BDense<T> &d = tab[di];
     int comp, j, i;
     unk_pos(u - d.unk_begin, d.nx, d.ny, comp, j, i);
     d.bvec[u - d.unk_begin] = (double)(comp == 0 ? d.bx : d.by)[(size_t)j * d.pitch + i];
 }
 
 template <typename T>
-__global__ void kb_dense_solve(const BDense<T> *__restrict__ tab, int count, int rows)
+__global__ void kb_dense_solve(const BDense<T> *__restrict__ tab, int count, int rows,
+                                const int *__restrict__ active)
 {
     const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
     if (row >= rows) return;
-    const BDense<T> &d = tab[dense_of(tab, count, row)];
+    const int di = dense_of(tab, count, row);
+    if (active && !active[di]) return;
+    const BDense<T> &d = tab[di];
     const int r = row - d.unk_begin;
     double s = 0.0;
     for (int c = lane; c < d.n; c += 32) s += d.Ainv[(size_t)r * d.n + c] * d.bvec[c];
@@ -240,11 +250,14 @@ __global__ void kb_dense_solve(const BDense<T> *__restrict__ tab, int count, int
 }
 
 template <typename T>
-__global__ void kb_dense_unpack(const BDense<T> *__restrict__ tab, int count, int rows)
+__global__ void kb_dense_unpack(const BDense<T> *__restrict__ tab, int count, int rows,
+                                const int *__restrict__ active)
 {
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= rows) return;
-    const BDense<T> &d = tab[dense_of(tab, count, u)];
+    const int di = dense_of(tab, count, u);
+    if (active && !active[di]) return;
+    const BDense<T> &d = tab[di];
     int comp, j, i;
     unk_pos(u - d.unk_begin, d.nx, d.ny, comp, j, i);
     (comp == 0 ? d.vx : d.vy)[(size_t)j * d.pitch + i] = (T)d.xvec[u - d.unk_begin];
@@ -252,10 +265,10 @@ __global__ void kb_dense_unpack(const BDense<T> *__restrict__ tab, int count, in
 
 template <typename To, typename Ti>
 __global__ void kb_cast_in(const BOuter<To> *__restrict__ out, const BLevel<Ti> *__restrict__ l0,
-                           const BSeg *__restrict__ m, int n)
+                           const BSeg *__restrict__ m, int n, const int *__restrict__ active)
 {
     const Pt p = point_of(m, n);
-    if (!p.valid) return;
+    if (!p.valid || (active && !active[p.inst])) return;
     const size_t q = (size_t)p.j * l0[p.inst].g.pitch + p.i;
     l0[p.inst].bx[q] = (Ti)out[p.inst].rx[q];
     l0[p.inst].by[q] = (Ti)out[p.inst].ry[q];
@@ -263,10 +276,10 @@ __global__ void kb_cast_in(const BOuter<To> *__restrict__ out, const BLevel<Ti> 
 
 template <typename To, typename Ti>
 __global__ void kb_cast_out(const BOuter<To> *__restrict__ out, const BLevel<Ti> *__restrict__ l0,
-                            const BSeg *__restrict__ m, int n)
+                            const BSeg *__restrict__ m, int n, const int *__restrict__ active)
 {
     const Pt p = point_of(m, n);
-    if (!p.valid) return;
+    if (!p.valid || (active && !active[p.inst])) return;
     const size_t q = (size_t)p.j * l0[p.inst].g.pitch + p.i;
     out[p.inst].zx[q] = (To)l0[p.inst].vx[q];
     out[p.inst].zy[q] = (To)l0[p.inst].vy[q];
@@ -441,57 +454,61 @@ cudaError_t batch_rhs(const BRhs<T> *tab, const BSeg *map, int nseg, int nblocks
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t batch_residual(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, cudaStream_t s)
+cudaError_t batch_residual(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, const int *active,
+                           cudaStream_t s)
 {
-    if (nblocks > 0) kb_residual<T><<<nblocks, BLOCK, 0, s>>>(tab, map, nseg);
+    if (nblocks > 0) kb_residual<T><<<nblocks, BLOCK, 0, s>>>(tab, map, nseg, active);
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t batch_restrict(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, cudaStream_t s)
+cudaError_t batch_restrict(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, const int *active,
+                           cudaStream_t s)
 {
-    if (nblocks > 0) kb_restrict<T><<<nblocks, BLOCK, 0, s>>>(tab, map, nseg);
+    if (nblocks > 0) kb_restrict<T><<<nblocks, BLOCK, 0, s>>>(tab, map, nseg, active);
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t batch_prolong(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, cudaStream_t s)
+cudaError_t batch_prolong(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, const int *active,
+                          cudaStream_t s)
 {
-    if (nblocks > 0) kb_prolong<T><<<nblocks, BLOCK, 0, s>>>(tab, map, nseg);
+    if (nblocks > 0) kb_prolong<T><<<nblocks, BLOCK, 0, s>>>(tab, map, nseg, active);
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t batch_zero_v(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, cudaStream_t s)
+cudaError_t batch_zero_v(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, const int *active,
+                         cudaStream_t s)
 {
-    if (nblocks > 0) kb_zero_v<T><<<nblocks, BLOCK, 0, s>>>(tab, map, nseg);
+    if (nblocks > 0) kb_zero_v<T><<<nblocks, BLOCK, 0, s>>>(tab, map, nseg, active);
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t batch_copy(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, bool walls_only, bool to_scratch,
-                       cudaStream_t s)
+                       const int *active, cudaStream_t s)
 {
-    if (nblocks > 0) kb_copy<T><<<nblocks, BLOCK, 0, s>>>(tab, map, nseg, walls_only, to_scratch);
+    if (nblocks > 0) kb_copy<T><<<nblocks, BLOCK, 0, s>>>(tab, map, nseg, walls_only, to_scratch, active);
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t batch_dense(const BDense<T> *tab, int count, int rows, cudaStream_t s)
+cudaError_t batch_dense(const BDense<T> *tab, int count, int rows, const int *active, cudaStream_t s)
 {
     if (count <= 0 || rows <= 0) return cudaSuccess;
-    kb_dense_pack<T><<<(rows + 255) / 256, 256, 0, s>>>(tab, count, rows);
-    kb_dense_solve<T><<<(rows + 7) / 8, 256, 0, s>>>(tab, count, rows);
-    kb_dense_unpack<T><<<(rows + 255) / 256, 256, 0, s>>>(tab, count, rows);
+    kb_dense_pack<T><<<(rows + 255) / 256, 256, 0, s>>>(tab, count, rows, active);
+    kb_dense_solve<T><<<(rows + 7) / 8, 256, 0, s>>>(tab, count, rows, active);
+    kb_dense_unpack<T><<<(rows + 255) / 256, 256, 0, s>>>(tab, count, rows, active);
     return cudaGetLastError();
 }
 template <typename To, typename Ti>
 cudaError_t batch_cast_in(const BOuter<To> *out, const BLevel<Ti> *l0, const BSeg *map, int nseg, int nblocks,
-                          cudaStream_t s)
+                          const int *active, cudaStream_t s)
 {
-    if (nblocks > 0) kb_cast_in<To, Ti><<<nblocks, BLOCK, 0, s>>>(out, l0, map, nseg);
+    if (nblocks > 0) kb_cast_in<To, Ti><<<nblocks, BLOCK, 0, s>>>(out, l0, map, nseg, active);
     return cudaGetLastError();
 }
 template <typename To, typename Ti>
 cudaError_t batch_cast_out(const BOuter<To> *out, const BLevel<Ti> *l0, const BSeg *map, int nseg, int nblocks,
-                           cudaStream_t s)
+                           const int *active, cudaStream_t s)
 {
-    if (nblocks > 0) kb_cast_out<To, Ti><<<nblocks, BLOCK, 0, s>>>(out, l0, map, nseg);
+    if (nblocks > 0) kb_cast_out<To, Ti><<<nblocks, BLOCK, 0, s>>>(out, l0, map, nseg, active);
     return cudaGetLastError();
 }
 
@@ -549,12 +566,13 @@ cudaError_t batch_scalars(int count, const double *pq_pr, const double *zq, cons
 
 #define INST(T)                                                                                                    \
     template cudaError_t batch_rhs<T>(const BRhs<T> *, const BSeg *, int, int, cudaStream_t);                      \
-    template cudaError_t batch_residual<T>(const BLevel<T> *, const BSeg *, int, int, cudaStream_t);               \
-    template cudaError_t batch_restrict<T>(const BLevel<T> *, const BSeg *, int, int, cudaStream_t);               \
-    template cudaError_t batch_prolong<T>(const BLevel<T> *, const BSeg *, int, int, cudaStream_t);                \
-    template cudaError_t batch_zero_v<T>(const BLevel<T> *, const BSeg *, int, int, cudaStream_t);                 \
-    template cudaError_t batch_copy<T>(const BLevel<T> *, const BSeg *, int, int, bool, bool, cudaStream_t);       \
-    template cudaError_t batch_dense<T>(const BDense<T> *, int, int, cudaStream_t);                                \
+    template cudaError_t batch_residual<T>(const BLevel<T> *, const BSeg *, int, int, const int *, cudaStream_t);  \
+    template cudaError_t batch_restrict<T>(const BLevel<T> *, const BSeg *, int, int, const int *, cudaStream_t);  \
+    template cudaError_t batch_prolong<T>(const BLevel<T> *, const BSeg *, int, int, const int *, cudaStream_t);   \
+    template cudaError_t batch_zero_v<T>(const BLevel<T> *, const BSeg *, int, int, const int *, cudaStream_t);    \
+    template cudaError_t batch_copy<T>(const BLevel<T> *, const BSeg *, int, int, bool, bool, const int *,         \
+                                       cudaStream_t);                                                              \
+    template cudaError_t batch_dense<T>(const BDense<T> *, int, int, const int *, cudaStream_t);                   \
     template cudaError_t batch_residual_energy<T>(const BOuter<T> *, const BSeg *, int, int, double *, double *,   \
                                                   cudaStream_t);                                                   \
     template cudaError_t batch_apply_dot<T>(const BOuter<T> *, const BSeg *, int, int, double *, double *,         \
@@ -569,21 +587,21 @@ cudaError_t batch_scalars(int count, const double *pq_pr, const double *zq, cons
 INST(float)
 INST(double)
 #undef INST
-template cudaError_t batch_cast_in<double, float>(const BOuter<double> *, const BLevel<float> *, const BSeg *, int,
-                                                  int, cudaStream_t);
-template cudaError_t batch_cast_in<double, double>(const BOuter<double> *, const BLevel<double> *, const BSeg *, int,
-                                                   int, cudaStream_t);
-template cudaError_t batch_cast_in<float, float>(const BOuter<float> *, const BLevel<float> *, const BSeg *, int,
-                                                 int, cudaStream_t);
-template cudaError_t batch_cast_in<float, double>(const BOuter<float> *, const BLevel<double> *, const BSeg *, int,
-                                                  int, cudaStream_t);
-template cudaError_t batch_cast_out<double, float>(const BOuter<double> *, const BLevel<float> *, const BSeg *, int,
-                                                   int, cudaStream_t);
+template cudaError_t batch_cast_in<double, float>(const BOuter<double> *, const BLevel<float> *, const BSeg *, int, int,
+                                                   const int *, cudaStream_t);
+template cudaError_t batch_cast_in<double, double>(const BOuter<double> *, const BLevel<double> *, const BSeg *, int, int,
+                                                   const int *, cudaStream_t);
+template cudaError_t batch_cast_in<float, float>(const BOuter<float> *, const BLevel<float> *, const BSeg *, int, int,
+                                                   const int *, cudaStream_t);
+template cudaError_t batch_cast_in<float, double>(const BOuter<float> *, const BLevel<double> *, const BSeg *, int, int,
+                                                   const int *, cudaStream_t);
+template cudaError_t batch_cast_out<double, float>(const BOuter<double> *, const BLevel<float> *, const BSeg *, int, int,
+                                                   const int *, cudaStream_t);
 template cudaError_t batch_cast_out<double, double>(const BOuter<double> *, const BLevel<double> *, const BSeg *,
-                                                    int, int, cudaStream_t);
-template cudaError_t batch_cast_out<float, float>(const BOuter<float> *, const BLevel<float> *, const BSeg *, int,
-                                                  int, cudaStream_t);
-template cudaError_t batch_cast_out<float, double>(const BOuter<float> *, const BLevel<double> *, const BSeg *, int,
-                                                   int, cudaStream_t);
+                                                    int, int, const int *, cudaStream_t);
+template cudaError_t batch_cast_out<float, float>(const BOuter<float> *, const BLevel<float> *, const BSeg *, int, int,
+                                                   const int *, cudaStream_t);
+template cudaError_t batch_cast_out<float, double>(const BOuter<float> *, const BLevel<double> *, const BSeg *, int, int,
+                                                   const int *, cudaStream_t);
 
 } // namespace stokes

@@ -120,15 +120,26 @@ struct BatchTiles {
     T *ox, *oy;
     TileGrid tg;
     int tile_begin;
+    int inst; // index into the launch's `live` flags
 };
 // One RAS outer iteration (ksweeps local sweeps) for every instance of the
 // device table `tab` (count entries, tiles numbered consecutively, `total`
 // tiles), all with tile size (ti, tj) and `overlap`: one persistent launch.
+// `maps` (device, may be NULL): the tensor maps of every instance, filled by
+// ras_batched_encode; with them the windows are staged by TMA.  `live`
+// (device, may be NULL): tiles of entries whose live[inst] is 0 are skipped.
 template <typename T>
-cudaError_t launch_ras_batched(const BatchTiles<T> *tab, int count, int total, int ti, int tj, int ksweeps,
-                               int overlap, T omega, cudaStream_t s);
+cudaError_t launch_ras_batched(const BatchTiles<T> *tab, const void *maps, int count, int total, int ti, int tj,
+                               int ksweeps, int overlap, T omega, const int *live, const RasRun &run, cudaStream_t s);
 // Shared memory one batched launch needs (tile size and overlap only).
 size_t ras_batched_smem_bytes(int ti, int tj, int overlap, size_t elem);
+// Whether a batched launch of this shape can stage windows by TMA, the bytes
+// of one instance's tensor maps, and their encoding for the host table `tab`
+// (count entries) into the host buffer `out` (count * ras_batched_maps_bytes()).
+bool ras_batched_tma(int ti, int tj, int overlap, size_t elem);
+size_t ras_batched_maps_bytes();
+template <typename T>
+cudaError_t ras_batched_encode(const BatchTiles<T> *tab, int count, int ti, int tj, int overlap, void *out);
 int ras_max_smem();
 
 // Record a failed CUDA call for stokes_last_cuda_error; returns

@@ -30,6 +30,7 @@
 //  k_ras      general kernel for windows too large for the register layout:
 //             every field of the window lives in shared memory.
 #include <algorithm>
+#include <cstring>
 
 #include "internal.h"
 #include "stencil.cuh"
@@ -422,7 +423,8 @@ __global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_reg(RasArgs<T> a)
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_batched(const BatchTiles<T> *__restrict__ tab, int count,
-                                                                 int total, RasArgs<T> shape)
+                                                                 int total, const int *__restrict__ live,
+                                                                 RasArgs<T> shape)
 {
     constexpr int R = KCfg<T>::R;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -440,6 +442,7 @@ __global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_batched(const BatchTile
             else hi = mid - 1;
         }
         const BatchTiles<T> &e = tab[lo];
+        if (live && !live[e.inst]) continue;
         RasArgs<T> a = shape;
         a.g = e.g;
         a.c = e.c;
@@ -461,6 +464,111 @@ __global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_batched(const BatchTile
         });
         __syncthreads();
         sweep_and_store<T, R>(a, w, c, col, strip, active, pl);
+    }
+}
+
+// batched persistent TMA-staged kernel: tile t of the launch belongs to the
+// last instance whose tile_begin <= t; instance e's windows are staged
+// through its own tensor maps maps[e] (global memory), the next tile's copy
+// overlapping the current tile's sweeps as in k_ras_tma
+template <typename T>
+__device__ __forceinline__ int batch_entry(const BatchTiles<T> *__restrict__ tab, int count, int t)
+{
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab[mid].tile_begin <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ RasArgs<T> batch_args(const RasArgs<T> &shape, const BatchTiles<T> &e)
+{
+    RasArgs<T> a = shape;
+    a.g = e.g;
+    a.c = e.c;
+    a.vx = e.vx;
+    a.vy = e.vy;
+    a.ox = e.ox;
+    a.oy = e.oy;
+    a.tg = e.tg;
+    return a;
+}
+
+template <typename T, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_ras_batched_tma(const BatchTiles<T> *__restrict__ tab,
+                                                                const TmaMaps *__restrict__ maps, int count,
+                                                                int total, const int *__restrict__ live,
+                                                                RasArgs<T> shape)
+{
+    constexpr int R = KCfg<T>::R;
+    constexpr int NF = KCfg<T>::INVD ? 8 : 6;
+    constexpr int ALIGN = 16 / (int)sizeof(T);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t off = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
+    T *const stage = reinterpret_cast<T *>(smem_raw + off);
+    const int BW = shape.bw, SP = shape.stage;
+    const Planes<T> pl(stage + NF * SP, shape.wp, shape.plane);
+    const int col = threadIdx.x % shape.wxm, strip = threadIdx.x / shape.wxm;
+    const bool active = (int)threadIdx.x < shape.wxm * shape.strips;
+    const uint32_t box_bytes = (uint32_t)(BW * shape.wym * (int)sizeof(T));
+
+    auto issue = [&](int t) {
+        const int e = batch_entry(tab, count, t);
+        const RasArgs<T> a = batch_args(shape, tab[e]);
+        const Window w = window_of(a, t - tab[e].tile_begin);
+        const int xs = w.ox0 & ~(ALIGN - 1);
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&bar, NF * box_bytes);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            fence_tensormap_acquire(&maps[e].m[f]);
+            tma_load_2d(stage + f * SP, &maps[e].m[f], xs, w.oy0, &bar);
+        }
+    };
+
+    // this CTA's next tile from t on (stride gridDim.x) whose instance is live
+    auto next_live = [&](int t) {
+        if (live)
+            while (t < total && !live[tab[batch_entry(tab, count, t)].inst]) t += (int)gridDim.x;
+        return t;
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_proxy_async();
+    }
+    zero_borders(shape, pl);
+    __syncthreads();
+    int tile = next_live((int)blockIdx.x);
+    if (threadIdx.x == 0 && tile < total) issue(tile);
+    uint32_t phase = 0;
+    while (tile < total) {
+        const bool ok = mbar_wait_bounded(&bar, phase, shape.wait_limit);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(shape.status, 1);
+                mbar_wait_bounded(&bar, phase, 4000000000LL);
+            }
+            __syncthreads();
+            return;
+        }
+        const int e = batch_entry(tab, count, tile);
+        const RasArgs<T> a = batch_args(shape, tab[e]);
+        const Window w = window_of(a, tile - tab[e].tile_begin);
+        const int dx = w.ox0 - (w.ox0 & ~(ALIGN - 1));
+        CellRegs<T, R> c;
+        setup_cells<T, R>(a, w, c, col, strip, active, pl,
+                          [&](int f, int wy, int wx) { return stage[f * SP + wy * BW + wx + dx]; });
+        __syncthreads();
+        const int next = next_live(tile + (int)gridDim.x);
+        if (threadIdx.x == 0 && next < total) issue(next);
+        phase ^= 1u;
+        sweep_and_store<T, R>(a, w, c, col, strip, active, pl);
+        tile = next;
     }
 }
 
@@ -569,7 +677,7 @@ __global__ void __launch_bounds__(RAS_THREADS) k_ras(RasArgs<T> a)
 // batched form of the general kernel: one CTA per tile of the launch's list
 template <typename T>
 __global__ void __launch_bounds__(RAS_THREADS) k_ras_batched_smem(const BatchTiles<T> *__restrict__ tab, int count,
-                                                                  RasArgs<T> shape)
+                                                                  const int *__restrict__ live, RasArgs<T> shape)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int t = (int)blockIdx.x;
@@ -580,6 +688,7 @@ __global__ void __launch_bounds__(RAS_THREADS) k_ras_batched_smem(const BatchTil
         else hi = mid - 1;
     }
     const BatchTiles<T> &e = tab[lo];
+    if (live && !live[e.inst]) return;
     RasArgs<T> a = shape;
     a.g = e.g;
     a.c = e.c;
@@ -741,15 +850,49 @@ size_t ras_batched_smem_bytes(int ti, int tj, int overlap, size_t elem)
     return plan_ras(ti, tj, ti, tj, overlap, elem, false).smem;
 }
 
+bool ras_batched_tma(int ti, int tj, int overlap, size_t elem)
+{
+    return plan_ras(ti, tj, ti, tj, overlap, elem, true).kind == PLAN_TMA;
+}
+
+size_t ras_batched_maps_bytes() { return sizeof(TmaMaps); }
+
 template <typename T>
-cudaError_t launch_ras_batched(const BatchTiles<T> *tab, int count, int total, int ti, int tj, int ksweeps,
-                               int overlap, T omega, cudaStream_t s)
+cudaError_t ras_batched_encode(const BatchTiles<T> *tab, int count, int ti, int tj, int overlap, void *out)
+{
+    constexpr int NF = KCfg<T>::INVD ? 8 : 6;
+    const RasPlan p = plan_ras(ti, tj, ti, tj, overlap, sizeof(T), true);
+    if (p.kind != PLAN_TMA) return cudaErrorInvalidValue;
+    TmaMaps *m = reinterpret_cast<TmaMaps *>(out);
+    const int es = (int)sizeof(T);
+    for (int i = 0; i < count; ++i) {
+        const BatchTiles<T> &e = tab[i];
+        const GridDesc<T> &g = e.g;
+        if (NF == 8 && (!e.c.inv_dx || !e.c.inv_dy)) return cudaErrorInvalidValue;
+        const void *ptrs[8] = {e.vx, e.vy, e.c.eta_c, e.c.eta_n, e.c.bx, e.c.by, e.c.inv_dx, e.c.inv_dy};
+        const int widths[8] = {g.nx + 1, g.nx, g.nx, g.nx + 1, g.nx + 1, g.nx, g.nx + 1, g.nx};
+        const int heights[8] = {g.ny, g.ny + 1, g.ny, g.ny + 1, g.ny, g.ny + 1, g.ny, g.ny + 1};
+        std::memset(&m[i], 0, sizeof(TmaMaps));
+        for (int f = 0; f < NF; ++f) {
+            const cudaError_t r =
+                make_tmap_2d(&m[i].m[f], ptrs[f], es, widths[f], heights[f], (long)g.pitch * es, p.bw, p.wym);
+            if (r != cudaSuccess) return r;
+        }
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_ras_batched(const BatchTiles<T> *tab, const void *maps, int count, int total, int ti, int tj,
+                               int ksweeps, int overlap, T omega, const int *live, const RasRun &run, cudaStream_t s)
 {
     // launch shape sized for the largest window (tile ti x tj grown by the
-    // overlap): the register layout in a persistent launch where it fits,
-    // else the general kernel with one CTA per tile
-    const RasPlan p = plan_ras(ti, tj, ti, tj, overlap, sizeof(T), false);
+    // overlap): TMA staging through per-instance tensor maps when `maps` is
+    // given, else the register layout reading global memory, else the
+    // general kernel with one CTA per tile
+    const RasPlan p = plan_ras(ti, tj, ti, tj, overlap, sizeof(T), maps != nullptr);
     if (p.smem > (size_t)ras_max_smem()) return cudaErrorInvalidValue;
+    if (maps && p.kind != PLAN_TMA) return cudaErrorInvalidValue;
     RasArgs<T> a{};
     a.omega = omega;
     a.ks = ksweeps;
@@ -759,28 +902,48 @@ cudaError_t launch_ras_batched(const BatchTiles<T> *tab, int count, int total, i
     a.strips = p.strips;
     a.wp = p.wp;
     a.plane = p.plane;
+    a.bw = p.bw;
+    a.stage = p.stage;
+    a.status = run.status;
+    a.wait_limit = run.wait_limit;
     if (total <= 0) return cudaSuccess;
-    if (p.kind == PLAN_SMEM) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_ras_batched_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    cudaError_t e;
+    if (p.kind == PLAN_TMA) {
+        void (*kern)(const BatchTiles<T> *, const TmaMaps *, int, int, const int *, RasArgs<T>) =
+            k_ras_batched_tma<T, REG_MAX_THREADS, 1>;
+        if constexpr (sizeof(T) == 4)
+            if (p.threads <= SMALL_THREADS) kern = k_ras_batched_tma<T, SMALL_THREADS, 2>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
         if (e != cudaSuccess) return e;
-        k_ras_batched_smem<T><<<total, RAS_THREADS, p.smem, s>>>(tab, count, a);
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, p.threads, p.smem);
+        if (e != cudaSuccess) return e;
+        const int grid = std::min(total, std::max(per_sm, 1) * sm_count());
+        kern<<<grid, p.threads, p.smem, s>>>(tab, reinterpret_cast<const TmaMaps *>(maps), count, total, live, a);
         return cudaGetLastError();
     }
-    cudaError_t e = cudaFuncSetAttribute(k_ras_batched<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (p.kind == PLAN_SMEM) {
+        e = cudaFuncSetAttribute(k_ras_batched_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+        if (e != cudaSuccess) return e;
+        k_ras_batched_smem<T><<<total, RAS_THREADS, p.smem, s>>>(tab, count, live, a);
+        return cudaGetLastError();
+    }
+    e = cudaFuncSetAttribute(k_ras_batched<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ras_batched<T>, p.threads, p.smem);
     if (e != cudaSuccess) return e;
     const int grid = std::min(total, std::max(per_sm, 1) * sm_count());
-    k_ras_batched<T><<<grid, p.threads, p.smem, s>>>(tab, count, total, a);
+    k_ras_batched<T><<<grid, p.threads, p.smem, s>>>(tab, count, total, live, a);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_ras_batched<float>(const BatchTiles<float> *, int, int, int, int, int, int, float,
-                                               cudaStream_t);
-template cudaError_t launch_ras_batched<double>(const BatchTiles<double> *, int, int, int, int, int, int, double,
-                                                cudaStream_t);
+template cudaError_t launch_ras_batched<float>(const BatchTiles<float> *, const void *, int, int, int, int, int,
+                                               int, float, const int *, const RasRun &, cudaStream_t);
+template cudaError_t launch_ras_batched<double>(const BatchTiles<double> *, const void *, int, int, int, int, int,
+                                                int, double, const int *, const RasRun &, cudaStream_t);
+template cudaError_t ras_batched_encode<float>(const BatchTiles<float> *, int, int, int, int, void *);
+template cudaError_t ras_batched_encode<double>(const BatchTiles<double> *, int, int, int, int, void *);
 
 template cudaError_t launch_ras<float>(const GridDesc<float> &, const Coeffs<float> &, float, const TileGrid &, int,
                                        int, const float *, const float *, float *, float *, const RasRun &,

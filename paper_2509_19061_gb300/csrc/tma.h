@@ -59,6 +59,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// Acquire a tensor map that lives in global memory (written before the
+// kernel started) for use by this thread's bulk tensor copies.
+__device__ __forceinline__ void fence_tensormap_acquire(const CUtensorMap *map)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+}
+
 // 2D tiled bulk tensor load of the box at element (x, y) into shared memory
 // (128-byte aligned), completing `bar`'s transaction count.  x * element
 // size must be a multiple of 16 bytes.

@@ -71,13 +71,15 @@ SIZES = [(40, 24), (64, 64), (100, 70), (33, 50), (8, 12)]
     dict(variant="fused", sweeps=6),
     dict(variant="blocked", sweeps=3, tile=(16, 16)),
 ])
-def test_batched_smoothing_is_bitwise_the_single_context(api, dtype, kw):
+@pytest.mark.parametrize("tma", [True, False])
+def test_batched_smoothing_is_bitwise_the_single_context(api, dtype, kw, tma):
     import torch
     probs = problems(SIZES, 10)
     v0 = [inputs.random_velocity(q.nx, q.ny, 100 + i) for i, q in enumerate(probs)]
     p = [inputs.random_pressure(q.nx, q.ny, 200 + i, 0.5) for i, q in enumerate(probs)]
     ref = single_results(api, probs, dtype, v0, p, lambda c, vx, vy, pt: c.smooth(vx, vy, pt, **kw))
     b = batch_context(api, probs, dtype)
+    b.set_option(api.STOKES_OPT_USE_TMA, 1 if tma else 0)
     vx, vy = b.pack([v[0] for v in v0], "vx"), b.pack([v[1] for v in v0], "vy")
     pt = b.pack(p, "p")
     b.smooth(vx, vy, pt, **kw)
@@ -197,3 +199,26 @@ def test_batched_errors(api):
     assert ex.value.status == api.STOKES_ERR_STATE
     b.close()
     torch.cuda.synchronize()
+
+
+def test_batched_wait_timeout_is_reported_and_recoverable(api):
+    """A bounded wait that gives up (limit below zero: at once) is recorded on
+    the device and reported by the next synchronising call; the batch keeps
+    working once the limit is restored."""
+    import torch
+    probs = problems([(64, 64), (40, 72)], 50)
+    b = batch_context(api, probs, "f32")
+    vx, vy = b.slab(), b.slab()
+    b.set_option(api.STOKES_OPT_WAIT_LIMIT_CYCLES, -1)
+    b.smooth(vx, vy, variant="ras", sweeps=4, tile=(32, 32), k=4, overlap=3)
+    with pytest.raises(api.StokesError) as ex:
+        b.energy(vx, vy)
+    assert ex.value.status == api.STOKES_ERR_TIMEOUT
+    b.set_option(api.STOKES_OPT_WAIT_LIMIT_CYCLES, 2000000000)
+    vx.zero_()
+    vy.zero_()
+    b.smooth(vx, vy, variant="ras", sweeps=4, tile=(32, 32), k=4, overlap=3)
+    e = b.energy(vx, vy)
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(e)) and np.all(e[:, 0] < e[:, 1])
+    b.close()
