@@ -292,6 +292,7 @@ def run_ours(args):
         line["time_to_1e-8"] = solve_times(args, api)
         if args.batch > 0:
             line["batched"] = batch_leg(args, api)
+        line["autotune"] = autotune_leg(args, api)
         if world == 1:
             line["cpu_baseline"] = {kk: vv for kk, vv in cpu_sample(args, args.cpu_seconds).items()
                                     if kk != "seconds"}
@@ -472,6 +473,21 @@ def batch_leg(args, api):
                     "per_instance_seconds": t_ls, "per_instance_converged": int(conv),
                     "per_instance_max_cycles": int(worst), "speedup": t_ls / t_bs}
     return out
+
+
+def autotune_leg(args, api):
+    """One tuning run of the RAS smoother (tile, k, overlap) by wall time of
+    the solve to E_v <= 1e-8: 1024^2 centred sinker, contrast 1e4, FP64 outer
+    flexible CG around the FP32 V-cycle, the tuner's default candidate list."""
+    from paper_2509_19061_gb300 import autotune, inputs
+    prob = inputs.sinker_problem(1024, eta_in=1e4)
+    win, table = autotune.tune(api, prob, dtype="f64", inner="f32")
+    dflt = [c for c in table if (c.tile_i, c.tile_j, c.k, c.overlap) == (32, 32, 4, 3)]
+    return {"workload": "sinker_1024x1024_contrast1e4", "objective": "seconds to E_v <= 1e-8",
+            "best": {"tile": [win.tile_i, win.tile_j], "k": win.k, "overlap": win.overlap,
+                     "seconds": win.seconds, "cycles": win.cycles},
+            "default_32x32_k4_o3_seconds": dflt[0].seconds if dflt else None,
+            "candidates": [[c.tile_i, c.tile_j, c.k, c.overlap, round(c.seconds, 5), c.cycles] for c in table]}
 
 
 def variant_table(args, api, prob):

@@ -1,0 +1,176 @@
+"""Autotuner for the RAS smoother inside the multigrid solve.
+
+The RAS tile shape (T_I, T_J), the local sweeps k and the overlap trade
+per-sweep throughput against convergence per sweep (Sec. 6.3): a larger k
+reads HBM less often but the tile-local Jacobi sweeps damp the global error
+less, and a zero overlap is cheapest per sweep but converges slowest.  The
+objective is therefore the wall time of the whole solve to E_v <= tol, not
+the speed of one sweep.
+
+Results are kept in a JSON cache keyed by (size bucket, dtype, contrast
+bucket): size bucket = round(log2(sqrt(nx * ny))), contrast bucket =
+round(log10(max eta / min eta)).  Tuning runs on the GPU through the
+library; lookups are plain Python.
+"""
+import json
+import math
+import os
+import time
+from dataclasses import asdict, dataclass
+
+DEFAULT_CANDIDATES = [(ti, tj, k, o) for (ti, tj) in ((16, 16), (32, 32), (64, 32))
+                      for k in (1, 2, 4, 8) for o in sorted({0, k - 1})]
+
+
+@dataclass
+class Choice:
+    tile_i: int
+    tile_j: int
+    k: int
+    overlap: int
+    seconds: float = float("nan")
+    cycles: int = -1
+
+    def smoother(self):
+        return dict(variant="ras", tile=(self.tile_i, self.tile_j), k=self.k, overlap=self.overlap)
+
+
+DEFAULT = Choice(32, 32, 4, 3)
+
+# cache shipped with the package, written on a GB300 by
+#   python -m paper_2509_19061_gb300.autotune --out paper_2509_19061_gb300/ras_tuning.json
+SHIPPED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "ras_tuning.json")
+
+
+def contrast_of(eta_c, eta_n):
+    lo = min(float(eta_c.min()), float(eta_n.min()))
+    hi = max(float(eta_c.max()), float(eta_n.max()))
+    return hi / lo
+
+
+def bucket(nx, ny, contrast, dtype):
+    size_b = int(round(math.log2(math.sqrt(nx * ny))))
+    con_b = int(round(math.log10(max(contrast, 1.0))))
+    return "n%d_%s_c%d" % (size_b, dtype, con_b)
+
+
+class Cache:
+    """JSON file of the best Choice per bucket."""
+
+    def __init__(self, path):
+        self.path = path
+        self.entries = {}
+        if path and os.path.exists(path):
+            with open(path) as f:
+                raw = json.load(f)
+            self.entries = {k: Choice(**v) for k, v in raw.get("entries", {}).items()}
+
+    def lookup(self, nx, ny, contrast, dtype):
+        """The cached Choice of the bucket, else the nearest cached size bucket
+        of the same dtype and contrast bucket, else the default."""
+        key = bucket(nx, ny, contrast, dtype)
+        if key in self.entries:
+            return self.entries[key]
+        size_b = int(key.split("_")[0][1:])
+        tail = key.split("_", 1)[1]
+        near = [(abs(int(k.split("_")[0][1:]) - size_b), k) for k in self.entries if k.split("_", 1)[1] == tail]
+        if near:
+            return self.entries[min(near)[1]]
+        return DEFAULT
+
+    def record(self, nx, ny, contrast, dtype, choice):
+        self.entries[bucket(nx, ny, contrast, dtype)] = choice
+
+    def save(self):
+        tmp = self.path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump({"objective": "wall seconds of the flexible-CG solve to E_v <= tol",
+                       "entries": {k: asdict(v) for k, v in sorted(self.entries.items())}}, f, indent=1)
+        os.replace(tmp, self.path)
+
+
+def tuned_smoother(nx, ny, eta_c, eta_n, dtype="f64", path=SHIPPED):
+    """Smoother keyword arguments (variant, tile, k, overlap) of the cached
+    choice for this grid, viscosity contrast and dtype."""
+    return Cache(path).lookup(nx, ny, contrast_of(eta_c, eta_n), dtype).smoother()
+
+
+def feasible(ti, tj, k, overlap, nx, ny):
+    """Tiles no larger than the grid; the overlap below the tile size."""
+    return ti <= nx and tj <= ny and 0 <= overlap < min(ti, tj) and k >= 1
+
+
+def tune(api, prob, dtype="f64", inner="f32", candidates=None, tol=1e-8, max_cycles=300, nu_max=40, seed=1,
+         reps=1):
+    """Time the solve of `prob` (an inputs.Problem) to E_v <= tol for every
+    candidate (tile_i, tile_j, k, overlap); returns (best Choice, list of all
+    Choices).  Each candidate is solved once untimed (hierarchy and graph
+    capture), then `reps` times from a zero guess; the minimum counts.
+    Candidates that do not converge get an infinite time."""
+    import torch
+    cands = [c for c in (candidates or DEFAULT_CANDIDATES) if feasible(*c, prob.nx, prob.ny)]
+    ctx = api.StokesContext(prob.nx, prob.ny, prob.lx, prob.ly, dtype)
+    ctx.set_problem(prob)
+    vx, vy = ctx.field(), ctx.field()
+    out = []
+    for ti, tj, k, o in cands:
+        kw = dict(variant="ras", tile=(ti, tj), k=k, overlap=o, seed=seed, nu_max=nu_max, inner=inner,
+                  krylov=True, tol=tol, max_cycles=max_cycles)
+        best, cyc = float("inf"), -1
+        try:
+            vx.zero_()
+            vy.zero_()
+            ctx.vcycle(vx, vy, None, **kw)
+            for _ in range(reps):
+                vx.zero_()
+                vy.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, e, c = ctx.vcycle(vx, vy, None, **kw)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                if st == api.STOKES_OK:
+                    best, cyc = min(best, dt), c
+        except api.StokesError:
+            best = float("inf")
+        out.append(Choice(ti, tj, k, o, best, cyc))
+    ctx.close()
+    win = min(out, key=lambda c: c.seconds) if out else DEFAULT
+    return win, out
+
+
+def tune_buckets(api, sizes=(256, 1024, 4096), contrasts=(1e2, 1e4, 1e6), dtype="f64", inner="f32", path=None,
+                 log=print):
+    """Tune one representative problem per (size, contrast) bucket: the
+    centred sinker of Sec. 6.1 with eta_in = contrast on an n x n grid.
+    Returns the cache (saved to `path` when given)."""
+    from . import inputs
+    cache = Cache(path) if path else Cache(None)
+    for n in sizes:
+        for c in contrasts:
+            prob = inputs.sinker_problem(n, eta_in=c)
+            win, table = tune(api, prob, dtype=dtype, inner=inner)
+            cache.record(n, n, contrast_of(prob.eta_c, prob.eta_n), dtype, win)
+            log("n=%d contrast=%.0e: best %s in %.4f s (%d cycles); default %s" % (
+                n, c, (win.tile_i, win.tile_j, win.k, win.overlap), win.seconds, win.cycles,
+                next(("%.4f s" % t.seconds for t in table
+                      if (t.tile_i, t.tile_j, t.k, t.overlap) == (32, 32, 4, 3)), "n/a")))
+    if path:
+        cache.save()
+    return cache
+
+
+if __name__ == "__main__":
+    import argparse
+
+    from . import api as _api
+    from . import build as _build
+    ap = argparse.ArgumentParser(description="tune the RAS smoother per size/contrast bucket")
+    ap.add_argument("--out", required=True, help="JSON cache to write")
+    ap.add_argument("--sizes", type=int, nargs="+", default=[256, 1024, 4096])
+    ap.add_argument("--contrasts", type=float, nargs="+", default=[1e2, 1e4, 1e6])
+    ap.add_argument("--dtype", default="f64")
+    ap.add_argument("--inner", default="f32")
+    a = ap.parse_args()
+    _build.build()
+    tune_buckets(_api, a.sizes, a.contrasts, a.dtype, a.inner, a.out)
