@@ -404,7 +404,6 @@ template <typename To, typename Ti>
 int build_hier(stokes_batch *b, BHier *h, int levels, int coarsest)
 {
     const size_t es = sizeof(Ti);
-    const bool inv = sizeof(Ti) == 8;
     const int n = b->count;
     cudaStream_t s = b->stream;
     h->L.assign(n, 1);
@@ -429,7 +428,6 @@ int build_hier(stokes_batch *b, BHier *h, int levels, int coarsest)
             }
         h->slab_elems[l] = place(h->d[l]);
         for (int f = 0; f < H_NF; ++f) {
-            if (!inv && (f == H_IVX || f == H_IVY)) continue;
             CK(cudaMalloc(&h->slab[l][f], h->slab_elems[l] * es));
             CK(cudaMemsetAsync(h->slab[l][f], 0, h->slab_elems[l] * es, s));
         }
@@ -440,14 +438,13 @@ int build_hier(stokes_batch *b, BHier *h, int levels, int coarsest)
     for (int l = 1; l < h->Lmax; ++l)
         for (int i = 0; i < n; ++i)
             if (l < h->L[i]) CK(mg_coarsen_eta<Ti>(level_view(h, l - 1, i, es), level_view(h, l, i, es), s));
-    if (inv)
-        for (int l = 0; l < h->Lmax; ++l)
-            for (int i = 0; i < n; ++i)
-                if (l < h->L[i]) {
-                    const MgLevel v = level_view(h, l, i, es);
-                    CK(launch_inv_diag<Ti>(make_grid<Ti>(v.nx, v.ny, v.pitch, v.hx, v.hy), (const Ti *)v.ec,
-                                           (const Ti *)v.en, (Ti *)v.ivx, (Ti *)v.ivy, s));
-                }
+    for (int l = 0; l < h->Lmax; ++l)
+        for (int i = 0; i < n; ++i)
+            if (l < h->L[i]) {
+                const MgLevel v = level_view(h, l, i, es);
+                CK(launch_inv_diag<Ti>(make_grid<Ti>(v.nx, v.ny, v.pitch, v.hx, v.hy), (const Ti *)v.ec,
+                                       (const Ti *)v.en, (Ti *)v.ivx, (Ti *)v.ivy, s));
+            }
     // dense inverses of -M on every coarsest level
     h->n.assign(n, 0);
     h->ubeg.assign(n, 0);

@@ -99,7 +99,7 @@ template <typename Ti>
 int build(MgHierarchy *h, const MgOuter &o, int levels, int coarsest, cudaStream_t s)
 {
     const size_t es = sizeof(Ti);
-    const bool inv = sizeof(Ti) == 8;
+    const bool inv = true; // 1/diag(M) on every level, read by the tile kernels
     // level sizes
     int nx = o.nx, ny = o.ny, L = 1;
     while (L < levels && L < MG_MAX_LEVELS && nx % 2 == 0 && ny % 2 == 0 && nx > coarsest && ny > coarsest) {

@@ -9,7 +9,7 @@
 namespace stokes {
 
 // One level of the hierarchy: every field is (ny+1) x pitch of the inner
-// precision.  ivx/ivy (1/diag) exist for FP64 hierarchies only.
+// precision, including ivx/ivy = 1/diag(M) at the unknowns.
 struct MgLevel {
     int nx, ny, pitch;
     size_t elems;

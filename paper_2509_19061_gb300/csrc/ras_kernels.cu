@@ -53,14 +53,15 @@ constexpr int REG_PLANES = 6;  // vx, vy, Txx, Sy, Tyy (strip ends), Sx (strip e
 //        non-unknown cells have weight 0), which costs more arithmetic but
 //        far fewer instructions: FP32 is issue-bound, FP64 is FP64-pipe-bound
 //  INVD  1/diag(M) is staged from the library's precomputed arrays instead
-//        of being computed per tile
+//        of being computed per tile (two more fields to read, but the
+//        per-tile reciprocals cost more issue slots than the bytes cost)
 template <typename T>
 struct KCfg;
 template <>
 struct KCfg<float> {
     static constexpr int R = 5;
     static constexpr bool TRAP = false;
-    static constexpr bool INVD = false;
+    static constexpr bool INVD = true;
 };
 template <>
 struct KCfg<double> {
@@ -90,6 +91,7 @@ struct RasArgs {
     int wxm, wym; // largest window extent (cells)
     int strips;   // strips per column (register kernels)
     int wp;       // shared-memory row pitch of the compute planes (elements)
+    int spad;     // extra elements between consecutive strips of a plane
     int plane;    // compute-plane size (elements)
     int bw;       // staging box width (elements); box height is wym
     int stage;    // staging-plane size (elements, 128-byte multiple)
@@ -132,12 +134,16 @@ struct CellRegs {
 
 // Compute planes: Vx, Vy, Fxx, Fsy, Fyy, Fsx, each (rows + 2) x WP with a
 // one-cell border; index (wy, wx), -1 <= wy <= rows, -1 <= wx <= wp - 2.
+// Element (wy, wx) sits at wy * WP + floor(wy / R) * SPAD + wx: the pad after
+// every strip of R rows makes the stride from one strip to the next congruent
+// to the window width modulo 32 banks, so a warp whose threads straddle two
+// strips (thread = strip * width + column) reads 32 consecutive banks.
 template <typename T>
 struct Planes {
     T *Vx, *Vy, *Fxx, *Fsy, *Fyy, *Fsx;
-    __device__ Planes(T *raw, int WP, int PL)
+    __device__ Planes(T *raw, int WP, int SPAD, int PL)
     {
-        T *b = raw + WP + 1;
+        T *b = raw + WP + SPAD + 1;
         Vx = b;
         Vy = b + PL;
         Fxx = b + 2 * PL;
@@ -152,7 +158,8 @@ struct Planes {
 template <typename T>
 __device__ __forceinline__ void zero_borders(const RasArgs<T> &a, const Planes<T> &pl)
 {
-    const int rows = a.strips * KCfg<T>::R, WP = a.wp, cols = a.wxm;
+    constexpr int R = KCfg<T>::R;
+    const int rows = a.strips * R, WP = a.wp, cols = a.wxm;
     const int n = 2 * (cols + 2) + 2 * rows;
     T *const ps[REG_PLANES] = {pl.Vx, pl.Vy, pl.Fxx, pl.Fsy, pl.Fyy, pl.Fsx};
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
@@ -167,8 +174,9 @@ __device__ __forceinline__ void zero_borders(const RasArgs<T> &a, const Planes<T
             wy = (t - 2 * (cols + 2)) >> 1;
             wx = (t & 1) ? cols : -1;
         }
+        const int q = wy * WP + (wy < 0 ? -1 : wy / R) * a.spad + wx;
 #pragma unroll
-        for (int f = 0; f < REG_PLANES; ++f) ps[f][wy * WP + wx] = T(0);
+        for (int f = 0; f < REG_PLANES; ++f) ps[f][q] = T(0);
     }
 }
 
@@ -211,8 +219,8 @@ __device__ __forceinline__ void setup_cells(const RasArgs<T> &a, const Window &w
             }
         }
         if (active) {
-            pl.Vx[wy * WP + col] = vxv;
-            pl.Vy[wy * WP + col] = vyv;
+            pl.Vx[wy * WP + strip * a.spad + col] = vxv;
+            pl.Vy[wy * WP + strip * a.spad + col] = vyv;
         }
         c.vx[r] = vxv;
         c.vy[r] = vyv;
@@ -227,12 +235,14 @@ __device__ __forceinline__ void setup_cells(const RasArgs<T> &a, const Window &w
 }
 
 // phase A for one cell: its fluxes into registers and the planes
+// (q: the cell's plane index; SW: the index step from the last row of a strip
+// to the first row of the next)
 template <typename T, int R>
 __device__ __forceinline__ void cell_fluxes(const GridDesc<T> &g, const CellRegs<T, R> &c, const Planes<T> &pl,
-                                            int r, int q, int WP, T *txx, T *tyy, T *sx, T *sy)
+                                            int r, int q, int SW, T *txx, T *tyy, T *sx, T *sy)
 {
-    const T vx_s = r > 0 ? c.vx[r - 1] : pl.Vx[q - WP];
-    const T vy_n = r < R - 1 ? c.vy[r + 1] : pl.Vy[q + WP];
+    const T vx_s = r > 0 ? c.vx[r - 1] : pl.Vx[q - SW];
+    const T vy_n = r < R - 1 ? c.vy[r + 1] : pl.Vy[q + SW];
     txx[r] = flux_n(c.ax[r], pl.Vx[q + 1], c.vx[r]);
     tyy[r] = flux_n(c.ay[r], vy_n, c.vy[r]);
     const T sh = shear(g, c.en[r], c.vx[r], vx_s, c.vy[r], pl.Vy[q - 1]);
@@ -251,7 +261,7 @@ __device__ __forceinline__ void sweep_and_store(const RasArgs<T> &a, const Windo
                                                 int strip, bool active, const Planes<T> &pl)
 {
     const GridDesc<T> &g = a.g;
-    const int WP = a.wp;
+    const int WP = a.wp, SW = a.wp + a.spad, q0 = strip * R * WP + strip * a.spad + col;
     T txx[R], tyy[R], sx[R], sy[R];
     for (int s = 1; s <= a.ks; ++s) {
         if (!KCfg<T>::TRAP) {
@@ -259,15 +269,15 @@ __device__ __forceinline__ void sweep_and_store(const RasArgs<T> &a, const Windo
             if (active) {
 #pragma unroll
                 for (int r = 0; r < R; ++r)
-                    cell_fluxes<T, R>(g, c, pl, r, (strip * R + r) * WP + col, WP, txx, tyy, sx, sy);
+                    cell_fluxes<T, R>(g, c, pl, r, q0 + r * WP, SW, txx, tyy, sx, sy);
             }
             __syncthreads();
             if (active) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const int q = (strip * R + r) * WP + col;
-                    const T sx_n = r < R - 1 ? sx[r + 1] : pl.Fsx[q + WP];
-                    const T tyy_s = r > 0 ? tyy[r - 1] : pl.Fyy[q - WP];
+                    const int q = q0 + r * WP;
+                    const T sx_n = r < R - 1 ? sx[r + 1] : pl.Fsx[q + SW];
+                    const T tyy_s = r > 0 ? tyy[r - 1] : pl.Fyy[q - SW];
                     c.vx[r] = jacobi_update(c.vx[r], c.bx[r], m_x(txx[r], pl.Fxx[q - 1], sx_n, sx[r]), c.wx[r]);
                     c.vy[r] = jacobi_update(c.vy[r], c.by[r], m_y(pl.Fsy[q + 1], sy[r], tyy[r], tyy_s), c.wy[r]);
                     pl.Vx[q] = c.vx[r];
@@ -286,21 +296,21 @@ __device__ __forceinline__ void sweep_and_store(const RasArgs<T> &a, const Windo
             for (int r = 0; r < R; ++r) {
                 const int wy = strip * R + r;
                 if (cx_flux && wy >= ry0 - 1 && wy <= ry1)
-                    cell_fluxes<T, R>(g, c, pl, r, wy * WP + col, WP, txx, tyy, sx, sy);
+                    cell_fluxes<T, R>(g, c, pl, r, q0 + r * WP, SW, txx, tyy, sx, sy);
             }
             __syncthreads();
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int wy = strip * R + r;
                 if (cx_in && wy >= ry0 && wy < ry1) {
-                    const int q = wy * WP + col;
+                    const int q = q0 + r * WP;
                     if (c.ux & (1u << r)) {
-                        const T sx_n = r < R - 1 ? sx[r + 1] : pl.Fsx[q + WP];
+                        const T sx_n = r < R - 1 ? sx[r + 1] : pl.Fsx[q + SW];
                         c.vx[r] = jacobi_update(c.vx[r], c.bx[r], m_x(txx[r], pl.Fxx[q - 1], sx_n, sx[r]), c.wx[r]);
                         pl.Vx[q] = c.vx[r];
                     }
                     if (c.uy & (1u << r)) {
-                        const T tyy_s = r > 0 ? tyy[r - 1] : pl.Fyy[q - WP];
+                        const T tyy_s = r > 0 ? tyy[r - 1] : pl.Fyy[q - SW];
                         c.vy[r] = jacobi_update(c.vy[r], c.by[r], m_y(pl.Fsy[q + 1], sy[r], tyy[r], tyy_s), c.wy[r]);
                         pl.Vy[q] = c.vy[r];
                     }
@@ -340,7 +350,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_ras_tma(const __grid_constant__ 
     const uint32_t off = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
     T *const stage = reinterpret_cast<T *>(smem_raw + off);
     const int BW = a.bw, SP = a.stage;
-    const Planes<T> pl(stage + NF * SP, a.wp, a.plane);
+    const Planes<T> pl(stage + NF * SP, a.wp, a.spad, a.plane);
 
     const int ntiles = a.tg.ntx * a.tg.nty;
     const int col = threadIdx.x % a.wxm, strip = threadIdx.x / a.wxm;
@@ -398,7 +408,7 @@ __global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_reg(RasArgs<T> a)
 {
     constexpr int R = KCfg<T>::R;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const Planes<T> pl(reinterpret_cast<T *>(smem_raw), a.wp, a.plane);
+    const Planes<T> pl(reinterpret_cast<T *>(smem_raw), a.wp, a.spad, a.plane);
     const GridDesc<T> &g = a.g;
     const Window w = window_of(a, (int)blockIdx.x);
     const int col = threadIdx.x % a.wxm, strip = threadIdx.x / a.wxm;
@@ -428,7 +438,7 @@ __global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_batched(const BatchTile
 {
     constexpr int R = KCfg<T>::R;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const Planes<T> pl(reinterpret_cast<T *>(smem_raw), shape.wp, shape.plane);
+    const Planes<T> pl(reinterpret_cast<T *>(smem_raw), shape.wp, shape.spad, shape.plane);
     const int col = threadIdx.x % shape.wxm, strip = threadIdx.x / shape.wxm;
     const bool active = (int)threadIdx.x < shape.wxm * shape.strips;
     zero_borders(shape, pl);
@@ -511,7 +521,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_ras_batched_tma(const BatchTiles
     const uint32_t off = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
     T *const stage = reinterpret_cast<T *>(smem_raw + off);
     const int BW = shape.bw, SP = shape.stage;
-    const Planes<T> pl(stage + NF * SP, shape.wp, shape.plane);
+    const Planes<T> pl(stage + NF * SP, shape.wp, shape.spad, shape.plane);
     const int col = threadIdx.x % shape.wxm, strip = threadIdx.x / shape.wxm;
     const bool active = (int)threadIdx.x < shape.wxm * shape.strips;
     const uint32_t box_bytes = (uint32_t)(BW * shape.wym * (int)sizeof(T));
@@ -704,7 +714,7 @@ __global__ void __launch_bounds__(RAS_THREADS) k_ras_batched_smem(const BatchTil
 enum { PLAN_TMA = 0, PLAN_REG = 1, PLAN_SMEM = 2 };
 struct RasPlan {
     int kind;
-    int wxm, wym, strips, wp, plane, threads, bw, stage;
+    int wxm, wym, strips, wp, spad, plane, threads, bw, stage;
     size_t smem;
 };
 
@@ -721,7 +731,9 @@ RasPlan plan_ras(int nx, int ny, int ti, int tj, int overlap, size_t elem, bool 
     const long threads = (long)p.wxm * p.strips;
     const size_t maxs = (size_t)ras_max_smem();
     p.wp = p.wxm + 2;
-    p.plane = p.wp * (p.strips * R + 2);
+    // strip stride congruent to the window width modulo 32 banks
+    p.spad = (((p.wxm - R * p.wp) % 32) + 32) % 32;
+    p.plane = p.wp * (p.strips * R + 2) + (p.strips + 1) * p.spad;
     const int align = 16 / (int)elem;
     p.bw = (p.wxm + align - 1 + align - 1) / align * align; // room for the alignment shift of x
     p.stage = (int)((((size_t)p.bw * p.wym * elem + 127) / 128 * 128) / elem);
@@ -737,6 +749,7 @@ RasPlan plan_ras(int nx, int ny, int ti, int tj, int overlap, size_t elem, bool 
     } else {
         p.kind = PLAN_SMEM;
         p.wp = p.wxm;
+        p.spad = 0;
         p.plane = p.wxm * p.wym;
         p.smem = (size_t)RAS_PLANES * (size_t)p.plane * elem;
         p.threads = RAS_THREADS;
@@ -802,6 +815,7 @@ cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const 
     a.wym = p.wym;
     a.strips = p.strips;
     a.wp = p.wp;
+    a.spad = p.spad;
     a.plane = p.plane;
     a.bw = p.bw;
     a.stage = p.stage;
@@ -901,6 +915,7 @@ cudaError_t launch_ras_batched(const BatchTiles<T> *tab, const void *maps, int c
     a.wym = p.wym;
     a.strips = p.strips;
     a.wp = p.wp;
+    a.spad = p.spad;
     a.plane = p.plane;
     a.bw = p.bw;
     a.stage = p.stage;

@@ -166,10 +166,9 @@ Coeffs<T> coeffs_of(const stokes_ctx *c)
     k.eta_n = (const T *)c->eta_n;
     k.bx = (const T *)c->bx;
     k.by = (const T *)c->by;
-    // FP64 kernels read 1/diag(M) (the FP64 pipe is their bottleneck); FP32
-    // kernels recompute it (HBM is theirs)
-    k.inv_dx = c->dtype == STOKES_F64 ? (const T *)c->ivx : nullptr;
-    k.inv_dy = c->dtype == STOKES_F64 ? (const T *)c->ivy : nullptr;
+    // the register tile kernels read 1/diag(M) instead of recomputing it
+    k.inv_dx = (const T *)c->ivx;
+    k.inv_dy = (const T *)c->ivy;
     return k;
 }
 
