@@ -4,8 +4,9 @@
 Workload (one "step"): the 8192 x 8192 layered sinker (10 seeded horizontal
 layers with log10 eta ~ U[-3, 3] plus a centred sinker, viscosity contrast up
 to 1e6, unit square, free-slip walls), FP32: form b = f - G p, run 100
-RAS-Jacobi sweeps (32 x 32 tiles, k = 4 local sweeps, overlap k-1, SplitMix64
-tile shifts), then evaluate the energy residual norm (FP64 accumulation, three
+RAS-Jacobi sweeps (56 x 32 tiles, k = 4 local sweeps, overlap k-1, SplitMix64
+tile shifts; with overlap k-1 the map is exactly Jacobi whatever the tile,
+and 56 x 32 is the fastest tile), then evaluate the energy residual norm (FP64 accumulation, three
 scalars back to the host).  One cell-update = vx and vy of one cell updated
 once; value = nx * ny * sweeps * steps / time.
 
@@ -45,7 +46,7 @@ def parse():
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--sweeps", type=int, default=100)
-    ap.add_argument("--tile", type=int, nargs=2, default=[32, 32])
+    ap.add_argument("--tile", type=int, nargs=2, default=[56, 32])
     ap.add_argument("--k", type=int, default=4)
     ap.add_argument("--overlap", type=int, default=None)
     ap.add_argument("--no-extras", action="store_true", help="skip the variant table, e2e and CPU baseline")
@@ -289,6 +290,7 @@ def run_ours(args):
     if not args.no_extras and rank == 0:
         line["e2e"] = e2e_measure(args, ctx, prob, stream, world)
         line["variants"] = variant_table(args, api, prob)
+        line["c2_f64_1024"] = c2_table(args, api)
         line["time_to_1e-8"] = solve_times(args, api)
         if args.batch > 0:
             line["batched"] = batch_leg(args, api)
@@ -349,19 +351,21 @@ def e2e_measure(args, ctx, prob, stream, world):
 def solve_times(args, api):
     """Time to a 1e-8 velocity energy residual on the 4096^2 multi-sinker
     (20 seeded inclusions, log10 eta ~ U[-3, 3]): FP64 outer flexible CG
-    around a V-cycle (RAS 32x32, k = 4, overlap 3, 5/5 sweeps x2.5 per level
-    capped at 40, dense FP64 coarsest) whose sweeps run in FP32 or FP64."""
+    around a V-cycle (5/5 sweeps x2.5 per level capped at 40, dense FP64
+    coarsest) whose sweeps run in FP32 or FP64; RAS schedule from the shipped
+    autotuner cache for this size and contrast."""
     import torch
-    from paper_2509_19061_gb300 import inputs
+    from paper_2509_19061_gb300 import autotune, inputs
     n = args.solve_n
     prob = inputs.multi_sinker(n, seed=3)
+    sm = autotune.tuned_smoother(n, n, prob.eta_c, prob.eta_n, "f64")
     ctx = api.StokesContext(n, n, 1.0, 1.0, "f64")
     ctx.set_problem(prob)
     out = {"workload": "multi_sinker_%dx%d_seed3" % (n, n), "tol": 1e-8, "outer": "f64 flexible CG",
-           "smoother": "ras 32x32 k4 o3", "nu": "5/5 x2.5 per level, cap 40"}
+           "smoother": "ras %dx%d k%d o%d (autotuned)" % (sm["tile"] + (sm["k"], sm["overlap"])),
+           "nu": "5/5 x2.5 per level, cap 40"}
     for inner in ("f32", "f64"):
-        kw = dict(variant="ras", tile=(32, 32), k=4, overlap=3, seed=1, nu_max=40, inner=inner, krylov=True,
-                  tol=1e-8, max_cycles=200)
+        kw = dict(sm, seed=1, nu_max=40, inner=inner, krylov=True, tol=1e-8, max_cycles=200)
         vx, vy = ctx.field(), ctx.field()
         ctx.vcycle(vx, vy, None, **kw)  # builds the hierarchy and the graph
         vx.zero_()
@@ -393,7 +397,12 @@ def batch_leg(args, api):
     out = {"workload": "batch_%d_sinkers_64to1024_seed5" % len(probs), "instances": len(probs),
            "cells_total": cells}
     sw = 20
-    smooth_kw = dict(variant="ras", sweeps=sw, tile=(32, 32), k=4, overlap=3, seed=1)
+    from paper_2509_19061_gb300 import autotune
+    tuned = autotune.Cache(autotune.SHIPPED).lookup(1024, 1024, 1e4, "f64")
+    sched = dict(variant="ras", tile=(tuned.tile_i, tuned.tile_j), k=tuned.k, overlap=tuned.overlap, seed=1)
+    label = "ras %dx%d k%d o%d (autotuned, 1024^2 contrast 1e4 bucket)" % (tuned.tile_i, tuned.tile_j, tuned.k,
+                                                                           tuned.overlap)
+    smooth_kw = dict(sched, sweeps=sw)
     stream = torch.cuda.current_stream()
 
     def timed(fn, reps):
@@ -428,14 +437,13 @@ def batch_leg(args, api):
     for c, _, _ in ctxs:
         c.close()
     b.close()
-    out["smooth"] = {"sweeps": sw, "schedule": "ras 32x32 k4 o3 f32",
+    out["smooth"] = {"sweeps": sw, "schedule": label + " f32",
                      "batched_gcell_updates_per_s": cells * sw / t_b / 1e9, "batched_ms": 1e3 * t_b,
                      "batched_launches": launches_b,
                      "per_instance_gcell_updates_per_s": cells * sw / t_l / 1e9, "per_instance_ms": 1e3 * t_l,
                      "speedup": t_l / t_b}
     # time to E_v <= 1e-8 for every instance
-    kw = dict(variant="ras", tile=(32, 32), k=4, overlap=3, seed=1, nu_max=40, inner="f32", krylov=True,
-              tol=1e-8, max_cycles=300)
+    kw = dict(sched, nu_max=40, inner="f32", krylov=True, tol=1e-8, max_cycles=300)
     b = api.BatchContext([q.nx for q in probs], [q.ny for q in probs], dtype="f64")
     b.set_problems(probs)
     vx, vy = b.slab(), b.slab()
@@ -466,7 +474,7 @@ def batch_leg(args, api):
         worst = max(worst, c1)
         conv += s1 == api.STOKES_OK
         c.close()
-    out["solve"] = {"tol": 1e-8, "outer": "f64 flexible CG", "inner": "f32 V-cycle, ras 32x32 k4 o3, nu cap 40",
+    out["solve"] = {"tol": 1e-8, "outer": "f64 flexible CG", "inner": "f32 V-cycle, %s, nu cap 40" % label,
                     "batched_seconds": t_bs, "batched_status": int(st),
                     "batched_converged": int(sum(1 for x in sts if x == api.STOKES_OK)),
                     "batched_max_cycles": int(max(cyc)), "batched_kernels": int(kb),
@@ -490,45 +498,96 @@ def autotune_leg(args, api):
             "candidates": [[c.tile_i, c.tile_j, c.k, c.overlap, round(c.seconds, 5), c.cycles] for c in table]}
 
 
-def variant_table(args, api, prob):
-    """Throughput of the other smoothers and RAS settings on the same grid
-    (Gcell-updates/s, device time of the smoothing call only)."""
+def _time_smooth(ctx, vx, vy, kw, reps=2):
     import torch
-    out = {}
+    stream = torch.cuda.current_stream()
+    ctx.smooth(vx, vy, None, **kw)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.smooth(vx, vy, None, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def variant_table(args, api, prob):
+    """The 8192^2 layered sinker (the throughput workload): FP32 and FP64
+    RAS-Jacobi with k in {1, 2, 4, 8} (overlap k-1, exact Jacobi, and
+    overlap 0, the paper's ring-only tile) and the other four smoothers.
+    Gcell-updates/s and effective GB/s (8 words per cell-sweep) over the
+    device time of the smoothing call; frac = effective GB/s over the
+    measured HBM copy bandwidth."""
     n = args.n
-    cases = [("f32", "jacobi", dict(sweeps=20)), ("f32", "fused", dict(sweeps=20)),
-             ("f32", "blocked", dict(sweeps=20, tile=(32, 32))), ("f32", "rbgs", dict(sweeps=20)),
-             ("f32", "ras", dict(sweeps=40, tile=(32, 32), k=1, overlap=0)),
-             ("f32", "ras", dict(sweeps=40, tile=(32, 32), k=2, overlap=1)),
-             ("f32", "ras", dict(sweeps=40, tile=(32, 32), k=8, overlap=7)),
-             ("f32", "ras", dict(sweeps=40, tile=(32, 32), k=4, overlap=0)),
-             ("f64", "ras", dict(sweeps=8, tile=(32, 32), k=4, overlap=3)),
-             ("f64", "fused", dict(sweeps=4))]
+    peak, _ = measured_peaks()
+    out = {}
+    cases = []
+    for k in (1, 2, 4, 8):
+        for o in sorted({k - 1, 0}):
+            cases.append(("f32", dict(variant="ras", sweeps=40, tile=(56, 32), k=k, overlap=o)))
+    cases += [("f32", dict(variant="ras", sweeps=40, tile=(32, 32), k=4, overlap=3)),
+              ("f32", dict(variant="jacobi", sweeps=20)), ("f32", dict(variant="fused", sweeps=20)),
+              ("f32", dict(variant="blocked", sweeps=20, tile=(56, 32))), ("f32", dict(variant="rbgs", sweeps=20))]
+    for k in (1, 2, 4, 8):
+        cases.append(("f64", dict(variant="ras", sweeps=8, tile=(32, 32), k=k, overlap=k - 1)))
+    cases += [("f64", dict(variant="ras", sweeps=8, tile=(32, 32), k=4, overlap=0)),
+              ("f64", dict(variant="fused", sweeps=4)), ("f64", dict(variant="rbgs", sweeps=4))]
     ctxs = {}
-    for dt_name, variant, kw in cases:
+    for dt_name, kw in cases:
         if dt_name not in ctxs:
             c = api.StokesContext(n, n, 1.0, 1.0, dt_name)
             c.set_problem(prob)
             ctxs[dt_name] = (c, c.field(), c.field())
         c, vx, vy = ctxs[dt_name]
-        stream = torch.cuda.current_stream()
-        c.smooth(vx, vy, None, variant=variant, **kw)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 2
-        e0.record(stream)
-        for _ in range(reps):
-            c.smooth(vx, vy, None, variant=variant, **kw)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        label = "%s_%s" % (dt_name, variant)
-        if variant == "ras":
+        ms = _time_smooth(c, vx, vy, kw)
+        label = "%s_%s" % (dt_name, kw["variant"])
+        if kw["variant"] in ("ras", "blocked"):
+            label += "_%dx%d" % kw["tile"]
+        if kw["variant"] == "ras":
             label += "_k%d_o%d" % (kw["k"], kw["overlap"])
-        out[label] = {"gcell_updates_per_s": n * n * kw["sweeps"] / (ms / 1e3) / 1e9, "sweeps": kw["sweeps"],
-                      "ms_per_call": ms}
+        cu = n * n * kw["sweeps"] / (ms / 1e3)
+        gbs = cu * WORDS_PER_CELL_SWEEP * (8 if dt_name == "f64" else 4) / 1e9
+        out[label] = {"gcell_updates_per_s": cu / 1e9, "effective_gbs": gbs, "frac": gbs / peak,
+                      "sweeps": kw["sweeps"], "ms_per_call": ms}
     for c, _, _ in ctxs.values():
         c.close()
     return out
+
+
+def c2_table(args, api):
+    """The 1024^2 sinker at contrast 1e4 in FP64: all five smoothers, 100
+    sweeps each, RAS with tiles 16^2, 32^2, 64 x 32 and k in {1, 2, 4, 8}
+    (overlap k-1).  The FP64 working set (8 fields x 8.4 MB) fits in the
+    129 MB L2, so these rates are L2-, not HBM-bound."""
+    from paper_2509_19061_gb300 import inputs
+    n = 1024
+    prob = inputs.sinker_problem(n, eta_in=1e4)
+    c = api.StokesContext(n, n, 1.0, 1.0, "f64")
+    c.set_problem(prob)
+    vx, vy = c.field(), c.field()
+    cases = [dict(variant=v, sweeps=100) for v in ("jacobi", "fused", "rbgs")]
+    cases.append(dict(variant="blocked", sweeps=100, tile=(32, 32)))
+    for tile in ((16, 16), (32, 32), (64, 32)):
+        for k in (1, 2, 4, 8):
+            cases.append(dict(variant="ras", sweeps=100, tile=tile, k=k, overlap=k - 1))
+    out = {}
+    for kw in cases:
+        label = kw["variant"]
+        if kw["variant"] in ("ras", "blocked"):
+            label += "_%dx%d" % kw["tile"]
+        if kw["variant"] == "ras":
+            label += "_k%d" % kw["k"]
+        try:
+            ms = _time_smooth(c, vx, vy, kw, reps=1)
+        except api.StokesError as ex:
+            # FP64 windows of large tiles and deep overlaps exceed shared memory
+            out[label] = {"error": str(ex)}
+            continue
+        cu = n * n * kw["sweeps"] / (ms / 1e3)
+        out[label] = {"gcell_updates_per_s": cu / 1e9, "effective_gbs": cu * WORDS_PER_CELL_SWEEP * 8 / 1e9,
+                      "ms_per_100_sweeps": ms}
+    c.close()
+    return {"workload": "sinker_1024x1024_contrast1e4_f64", "table": out}
 
 
 def main():

@@ -18,7 +18,7 @@ import os
 import time
 from dataclasses import asdict, dataclass
 
-DEFAULT_CANDIDATES = [(ti, tj, k, o) for (ti, tj) in ((16, 16), (32, 32), (64, 32))
+DEFAULT_CANDIDATES = [(ti, tj, k, o) for (ti, tj) in ((16, 16), (32, 32), (56, 32))
                       for k in (1, 2, 4, 8) for o in sorted({0, k - 1})]
 
 

@@ -153,13 +153,33 @@ struct Planes {
     }
 };
 
+// Plane geometry of a register-kernel launch.  For the window widths and
+// strip counts the launcher specialises (WXM > 0) every plane offset is a
+// compile-time constant, which lets shared-memory accesses use immediate
+// offsets; otherwise the values come from the launch arguments.  Both follow
+// the formulas of plan_ras.
+template <typename T, int WXM, int NS>
+struct Geo {
+    static constexpr int R = KCfg<T>::R;
+    static constexpr bool FIXED = WXM > 0;
+    static constexpr int WPC = WXM + 2;
+    static constexpr int SPC = (((WXM - R * WPC) % 32) + 32) % 32;
+    static constexpr int PLC = WPC * (NS * R + 2) + (NS + 1) * SPC;
+    int wxm, wp, spad, plane, strips;
+    __device__ __forceinline__ explicit Geo(const RasArgs<T> &a)
+        : wxm(FIXED ? WXM : a.wxm), wp(FIXED ? WPC : a.wp), spad(FIXED ? SPC : a.spad),
+          plane(FIXED ? PLC : a.plane), strips(FIXED ? NS : a.strips)
+    {
+    }
+};
+
 // Zero the one-cell border of every compute plane (it is never written
 // afterwards): the fluxes of window-edge cells then read finite values.
-template <typename T>
-__device__ __forceinline__ void zero_borders(const RasArgs<T> &a, const Planes<T> &pl)
+template <typename T, int WXM, int NS>
+__device__ __forceinline__ void zero_borders(const Geo<T, WXM, NS> &G, const Planes<T> &pl)
 {
     constexpr int R = KCfg<T>::R;
-    const int rows = a.strips * R, WP = a.wp, cols = a.wxm;
+    const int rows = G.strips * R, WP = G.wp, cols = G.wxm;
     const int n = 2 * (cols + 2) + 2 * rows;
     T *const ps[REG_PLANES] = {pl.Vx, pl.Vy, pl.Fxx, pl.Fsy, pl.Fyy, pl.Fsx};
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
@@ -174,7 +194,7 @@ __device__ __forceinline__ void zero_borders(const RasArgs<T> &a, const Planes<T
             wy = (t - 2 * (cols + 2)) >> 1;
             wx = (t & 1) ? cols : -1;
         }
-        const int q = wy * WP + (wy < 0 ? -1 : wy / R) * a.spad + wx;
+        const int q = wy * WP + (wy < 0 ? -1 : wy / R) * G.spad + wx;
 #pragma unroll
         for (int f = 0; f < REG_PLANES; ++f) ps[f][q] = T(0);
     }
@@ -184,12 +204,13 @@ __device__ __forceinline__ void zero_borders(const RasArgs<T> &a, const Planes<T
 // returns the window value of field 0..7 (vx, vy, eta_c, eta_n, bx, by,
 // 1/dx, 1/dy), zero outside the field's extent.  Cells outside the window get
 // zero state.
-template <typename T, int R, class LD>
-__device__ __forceinline__ void setup_cells(const RasArgs<T> &a, const Window &w, CellRegs<T, R> &c, int col,
-                                            int strip, bool active, const Planes<T> &pl, LD &&ld)
+template <typename T, int R, int WXM, int NS, class LD>
+__device__ __forceinline__ void setup_cells(const RasArgs<T> &a, const Geo<T, WXM, NS> &G, const Window &w,
+                                            CellRegs<T, R> &c, int col, int strip, bool active, const Planes<T> &pl,
+                                            LD &&ld)
 {
     const GridDesc<T> &g = a.g;
-    const int WP = a.wp;
+    const int WP = G.wp;
     const int gx = w.ox0 + col;
     c.ux = 0;
     c.uy = 0;
@@ -219,8 +240,8 @@ __device__ __forceinline__ void setup_cells(const RasArgs<T> &a, const Window &w
             }
         }
         if (active) {
-            pl.Vx[wy * WP + strip * a.spad + col] = vxv;
-            pl.Vy[wy * WP + strip * a.spad + col] = vyv;
+            pl.Vx[wy * WP + strip * G.spad + col] = vxv;
+            pl.Vy[wy * WP + strip * G.spad + col] = vyv;
         }
         c.vx[r] = vxv;
         c.vy[r] = vyv;
@@ -256,12 +277,13 @@ __device__ __forceinline__ void cell_fluxes(const GridDesc<T> &g, const CellRegs
 
 // ks local sweeps on the window (registers + shared planes), then write back
 // the unknowns of the tile's own cells.  Ends with a barrier.
-template <typename T, int R>
-__device__ __forceinline__ void sweep_and_store(const RasArgs<T> &a, const Window &w, CellRegs<T, R> &c, int col,
-                                                int strip, bool active, const Planes<T> &pl)
+template <typename T, int R, int WXM, int NS>
+__device__ __forceinline__ void sweep_and_store(const RasArgs<T> &a, const Geo<T, WXM, NS> &G, const Window &w,
+                                                CellRegs<T, R> &c, int col, int strip, bool active,
+                                                const Planes<T> &pl)
 {
     const GridDesc<T> &g = a.g;
-    const int WP = a.wp, SW = a.wp + a.spad, q0 = strip * R * WP + strip * a.spad + col;
+    const int WP = G.wp, SW = G.wp + G.spad, q0 = strip * (R * WP + G.spad) + col;
     T txx[R], tyy[R], sx[R], sy[R];
     for (int s = 1; s <= a.ks; ++s) {
         if (!KCfg<T>::TRAP) {
@@ -338,7 +360,7 @@ __device__ __forceinline__ void sweep_and_store(const RasArgs<T> &a, const Windo
 // ---------------------------------------------------------------------------
 // persistent TMA-staged kernel
 // ---------------------------------------------------------------------------
-template <typename T, int MAXT, int MINB>
+template <typename T, int MAXT, int MINB, int WXM, int NS>
 __global__ void __launch_bounds__(MAXT, MINB) k_ras_tma(const __grid_constant__ TmaMaps maps, RasArgs<T> a)
 {
     constexpr int R = KCfg<T>::R;
@@ -350,11 +372,12 @@ __global__ void __launch_bounds__(MAXT, MINB) k_ras_tma(const __grid_constant__ 
     const uint32_t off = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
     T *const stage = reinterpret_cast<T *>(smem_raw + off);
     const int BW = a.bw, SP = a.stage;
-    const Planes<T> pl(stage + NF * SP, a.wp, a.spad, a.plane);
+    const Geo<T, WXM, NS> G(a);
+    const Planes<T> pl(stage + NF * SP, G.wp, G.spad, G.plane);
 
     const int ntiles = a.tg.ntx * a.tg.nty;
-    const int col = threadIdx.x % a.wxm, strip = threadIdx.x / a.wxm;
-    const bool active = (int)threadIdx.x < a.wxm * a.strips;
+    const int col = (int)threadIdx.x % G.wxm, strip = (int)threadIdx.x / G.wxm;
+    const bool active = (int)threadIdx.x < G.wxm * G.strips;
     const uint32_t box_bytes = (uint32_t)(BW * a.wym * (int)sizeof(T));
 
     auto issue = [&](int tile) {
@@ -370,7 +393,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_ras_tma(const __grid_constant__ 
         mbar_init(&bar, 1);
         fence_proxy_async();
     }
-    zero_borders(a, pl);
+    zero_borders(G, pl);
     __syncthreads();
     int tile = blockIdx.x;
     if (threadIdx.x == 0 && tile < ntiles) issue(tile);
@@ -389,13 +412,13 @@ __global__ void __launch_bounds__(MAXT, MINB) k_ras_tma(const __grid_constant__ 
         const Window w = window_of(a, tile);
         const int dx = w.ox0 - (w.ox0 & ~(ALIGN - 1));
         CellRegs<T, R> c;
-        setup_cells<T, R>(a, w, c, col, strip, active, pl,
+        setup_cells<T, R>(a, G, w, c, col, strip, active, pl,
                           [&](int f, int wy, int wx) { return stage[f * SP + wy * BW + wx + dx]; });
         __syncthreads(); // staging consumed: refill it with the next tile
         const int next = tile + (int)gridDim.x;
         if (threadIdx.x == 0 && next < ntiles) issue(next);
         phase ^= 1u;
-        sweep_and_store<T, R>(a, w, c, col, strip, active, pl);
+        sweep_and_store<T, R>(a, G, w, c, col, strip, active, pl);
         tile = next;
     }
 }
@@ -408,16 +431,17 @@ __global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_reg(RasArgs<T> a)
 {
     constexpr int R = KCfg<T>::R;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const Planes<T> pl(reinterpret_cast<T *>(smem_raw), a.wp, a.spad, a.plane);
+    const Geo<T, 0, 0> G(a);
+    const Planes<T> pl(reinterpret_cast<T *>(smem_raw), G.wp, G.spad, G.plane);
     const GridDesc<T> &g = a.g;
     const Window w = window_of(a, (int)blockIdx.x);
     const int col = threadIdx.x % a.wxm, strip = threadIdx.x / a.wxm;
     const bool active = (int)threadIdx.x < a.wxm * a.strips;
     const size_t P = (size_t)g.pitch;
     const T *const src[8] = {a.vx, a.vy, a.c.eta_c, a.c.eta_n, a.c.bx, a.c.by, a.c.inv_dx, a.c.inv_dy};
-    zero_borders(a, pl);
+    zero_borders(G, pl);
     CellRegs<T, R> c;
-    setup_cells<T, R>(a, w, c, col, strip, active, pl, [&](int f, int wy, int wx) {
+    setup_cells<T, R>(a, G, w, c, col, strip, active, pl, [&](int f, int wy, int wx) {
         const int gy = w.oy0 + wy, gx = w.ox0 + wx;
         // extents: vx, bx, 1/dx ny x (nx+1); vy, by, 1/dy (ny+1) x nx; eta_c ny x nx; eta_n (ny+1) x (nx+1)
         const int ey = (f == 0 || f == 2 || f == 4 || f == 6) ? g.ny : g.ny + 1;
@@ -425,7 +449,7 @@ __global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_reg(RasArgs<T> a)
         return (gy >= 0 && gy < ey && gx >= 0 && gx < ex) ? src[f][(size_t)gy * P + (size_t)gx] : T(0);
     });
     __syncthreads();
-    sweep_and_store<T, R>(a, w, c, col, strip, active, pl);
+    sweep_and_store<T, R>(a, G, w, c, col, strip, active, pl);
 }
 
 // ---------------------------------------------------------------------------
@@ -438,10 +462,11 @@ __global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_batched(const BatchTile
 {
     constexpr int R = KCfg<T>::R;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const Planes<T> pl(reinterpret_cast<T *>(smem_raw), shape.wp, shape.spad, shape.plane);
+    const Geo<T, 0, 0> G(shape);
+    const Planes<T> pl(reinterpret_cast<T *>(smem_raw), G.wp, G.spad, G.plane);
     const int col = threadIdx.x % shape.wxm, strip = threadIdx.x / shape.wxm;
     const bool active = (int)threadIdx.x < shape.wxm * shape.strips;
-    zero_borders(shape, pl);
+    zero_borders(G, pl);
     __syncthreads();
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         // instance owning tile t: last entry with tile_begin <= t
@@ -466,14 +491,14 @@ __global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_batched(const BatchTile
         const size_t P = (size_t)g.pitch;
         const T *const src[8] = {a.vx, a.vy, a.c.eta_c, a.c.eta_n, a.c.bx, a.c.by, a.c.inv_dx, a.c.inv_dy};
         CellRegs<T, R> c;
-        setup_cells<T, R>(a, w, c, col, strip, active, pl, [&](int f, int wy, int wx) {
+        setup_cells<T, R>(a, G, w, c, col, strip, active, pl, [&](int f, int wy, int wx) {
             const int gy = w.oy0 + wy, gx = w.ox0 + wx;
             const int ey = (f == 0 || f == 2 || f == 4 || f == 6) ? g.ny : g.ny + 1;
             const int ex = (f == 1 || f == 2 || f == 5 || f == 7) ? g.nx : g.nx + 1;
             return (gy >= 0 && gy < ey && gx >= 0 && gx < ex) ? src[f][(size_t)gy * P + (size_t)gx] : T(0);
         });
         __syncthreads();
-        sweep_and_store<T, R>(a, w, c, col, strip, active, pl);
+        sweep_and_store<T, R>(a, G, w, c, col, strip, active, pl);
     }
 }
 
@@ -507,7 +532,7 @@ __device__ __forceinline__ RasArgs<T> batch_args(const RasArgs<T> &shape, const 
     return a;
 }
 
-template <typename T, int MAXT, int MINB>
+template <typename T, int MAXT, int MINB, int WXM, int NS>
 __global__ void __launch_bounds__(MAXT, MINB) k_ras_batched_tma(const BatchTiles<T> *__restrict__ tab,
                                                                 const TmaMaps *__restrict__ maps, int count,
                                                                 int total, const int *__restrict__ live,
@@ -521,9 +546,10 @@ __global__ void __launch_bounds__(MAXT, MINB) k_ras_batched_tma(const BatchTiles
     const uint32_t off = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
     T *const stage = reinterpret_cast<T *>(smem_raw + off);
     const int BW = shape.bw, SP = shape.stage;
-    const Planes<T> pl(stage + NF * SP, shape.wp, shape.spad, shape.plane);
-    const int col = threadIdx.x % shape.wxm, strip = threadIdx.x / shape.wxm;
-    const bool active = (int)threadIdx.x < shape.wxm * shape.strips;
+    const Geo<T, WXM, NS> G(shape);
+    const Planes<T> pl(stage + NF * SP, G.wp, G.spad, G.plane);
+    const int col = (int)threadIdx.x % G.wxm, strip = (int)threadIdx.x / G.wxm;
+    const bool active = (int)threadIdx.x < G.wxm * G.strips;
     const uint32_t box_bytes = (uint32_t)(BW * shape.wym * (int)sizeof(T));
 
     auto issue = [&](int t) {
@@ -551,7 +577,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_ras_batched_tma(const BatchTiles
         mbar_init(&bar, 1);
         fence_proxy_async();
     }
-    zero_borders(shape, pl);
+    zero_borders(G, pl);
     __syncthreads();
     int tile = next_live((int)blockIdx.x);
     if (threadIdx.x == 0 && tile < total) issue(tile);
@@ -571,13 +597,13 @@ __global__ void __launch_bounds__(MAXT, MINB) k_ras_batched_tma(const BatchTiles
         const Window w = window_of(a, tile - tab[e].tile_begin);
         const int dx = w.ox0 - (w.ox0 & ~(ALIGN - 1));
         CellRegs<T, R> c;
-        setup_cells<T, R>(a, w, c, col, strip, active, pl,
+        setup_cells<T, R>(a, G, w, c, col, strip, active, pl,
                           [&](int f, int wy, int wx) { return stage[f * SP + wy * BW + wx + dx]; });
         __syncthreads();
         const int next = next_live(tile + (int)gridDim.x);
         if (threadIdx.x == 0 && next < total) issue(next);
         phase ^= 1u;
-        sweep_and_store<T, R>(a, w, c, col, strip, active, pl);
+        sweep_and_store<T, R>(a, G, w, c, col, strip, active, pl);
         tile = next;
     }
 }
@@ -793,6 +819,48 @@ int ras_max_smem()
     return v;
 }
 
+// Kernel instance for a TMA plan.  FP32 windows of up to 320 threads cap
+// registers so that two CTAs share an SM (FP64 is bound by its FP64 pipe and
+// keeps 128 registers).  The window shapes of the common tiles (32 x 32 and
+// 56 x 32 with overlap 0 or 3 in FP32, 32 x 32 with overlap 3 in FP64) get
+// instances with compile-time plane geometry; the others use the generic one.
+template <int WXM, int NS, typename T>
+bool geo_matches(const RasPlan &p)
+{
+    using G = Geo<T, WXM, NS>;
+    return p.wxm == WXM && p.strips == NS && p.wp == G::WPC && p.spad == G::SPC && p.plane == G::PLC;
+}
+
+template <typename T>
+void (*pick_tma(const RasPlan &p))(TmaMaps, RasArgs<T>)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (geo_matches<64, 8, T>(p)) return k_ras_tma<T, REG_MAX_THREADS, 1, 64, 8>;
+        if (geo_matches<58, 7, T>(p)) return k_ras_tma<T, REG_MAX_THREADS, 1, 58, 7>;
+        if (geo_matches<40, 8, T>(p)) return k_ras_tma<T, SMALL_THREADS, 2, 40, 8>;
+        if (geo_matches<34, 7, T>(p)) return k_ras_tma<T, SMALL_THREADS, 2, 34, 7>;
+        if (p.threads <= SMALL_THREADS) return k_ras_tma<T, SMALL_THREADS, 2, 0, 0>;
+    } else {
+        if (geo_matches<40, 10, T>(p)) return k_ras_tma<T, REG_MAX_THREADS, 1, 40, 10>;
+    }
+    return k_ras_tma<T, REG_MAX_THREADS, 1, 0, 0>;
+}
+
+template <typename T>
+void (*pick_batched_tma(const RasPlan &p))(const BatchTiles<T> *, const TmaMaps *, int, int, const int *, RasArgs<T>)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (geo_matches<64, 8, T>(p)) return k_ras_batched_tma<T, REG_MAX_THREADS, 1, 64, 8>;
+        if (geo_matches<58, 7, T>(p)) return k_ras_batched_tma<T, REG_MAX_THREADS, 1, 58, 7>;
+        if (geo_matches<40, 8, T>(p)) return k_ras_batched_tma<T, SMALL_THREADS, 2, 40, 8>;
+        if (geo_matches<34, 7, T>(p)) return k_ras_batched_tma<T, SMALL_THREADS, 2, 34, 7>;
+        if (p.threads <= SMALL_THREADS) return k_ras_batched_tma<T, SMALL_THREADS, 2, 0, 0>;
+    } else {
+        if (geo_matches<40, 10, T>(p)) return k_ras_batched_tma<T, REG_MAX_THREADS, 1, 40, 10>;
+    }
+    return k_ras_batched_tma<T, REG_MAX_THREADS, 1, 0, 0>;
+}
+
 template <typename T>
 cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const TileGrid &tg, int ksweeps,
                        int overlap, const T *vx, const T *vy, T *ox, T *oy, const RasRun &run, cudaStream_t s)
@@ -835,11 +903,7 @@ cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const 
             e = make_tmap_2d(&m.m[f], ptrs[f], es, widths[f], heights[f], pb, p.bw, p.wym);
             if (e != cudaSuccess) return e;
         }
-        // FP32 windows of up to 320 threads: registers capped so that two CTAs
-        // share an SM (FP64 is bound by its FP64 pipe and keeps 128 registers)
-        void (*kern)(TmaMaps, RasArgs<T>) = k_ras_tma<T, REG_MAX_THREADS, 1>;
-        if constexpr (sizeof(T) == 4)
-            if (p.threads <= SMALL_THREADS) kern = k_ras_tma<T, SMALL_THREADS, 2>;
+        void (*kern)(TmaMaps, RasArgs<T>) = pick_tma<T>(p);
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
@@ -925,9 +989,7 @@ cudaError_t launch_ras_batched(const BatchTiles<T> *tab, const void *maps, int c
     cudaError_t e;
     if (p.kind == PLAN_TMA) {
         void (*kern)(const BatchTiles<T> *, const TmaMaps *, int, int, const int *, RasArgs<T>) =
-            k_ras_batched_tma<T, REG_MAX_THREADS, 1>;
-        if constexpr (sizeof(T) == 4)
-            if (p.threads <= SMALL_THREADS) kern = k_ras_batched_tma<T, SMALL_THREADS, 2>;
+            pick_batched_tma<T>(p);
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
