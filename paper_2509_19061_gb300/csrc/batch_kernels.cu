@@ -303,9 +303,8 @@ __global__ void kb_residual_energy(const BOuter<T> *__restrict__ tab, const BSeg
             if (vx_unknown(g, j, i)) {
                 op_x(g, o.ec, o.en, (const T *)o.vx, (const T *)o.vy, j, i, mm, d, vc);
                 r = r_sub(o.bx[q], mm);
-                const double w = -(double)o.ivx[q], f = (double)o.fx[q];
-                s0 = fma((double)r * (double)r, w, s0);
-                s1 = fma(f * f, w, s1);
+                s0 = acc_sq(s0, r, -o.ivx[q]);
+                s1 = acc_sq(s1, o.fx[q], -o.ivx[q]);
             }
             o.rx[q] = r;
         }
@@ -314,9 +313,8 @@ __global__ void kb_residual_energy(const BOuter<T> *__restrict__ tab, const BSeg
             if (vy_unknown(g, j, i)) {
                 op_y(g, o.ec, o.en, (const T *)o.vx, (const T *)o.vy, j, i, mm, d, vc);
                 r = r_sub(o.by[q], mm);
-                const double w = -(double)o.ivy[q], f = (double)o.fy[q];
-                s0 = fma((double)r * (double)r, w, s0);
-                s1 = fma(f * f, w, s1);
+                s0 = acc_sq(s0, r, -o.ivy[q]);
+                s1 = acc_sq(s1, o.fy[q], -o.ivy[q]);
             }
             o.ry[q] = r;
         }
@@ -376,13 +374,13 @@ __global__ void kb_update(const BOuter<T> *__restrict__ tab, const BSeg *__restr
             o.vx[q] = r_fma(a, o.px[q], o.vx[q]);
             const T rn = r_fma(-a, o.qx[q], o.rx[q]);
             o.rx[q] = rn;
-            s0 = fma((double)rn * (double)rn, -(double)o.ivx[q], s0);
+            s0 = acc_sq(s0, rn, -o.ivx[q]);
         }
         if (vy_unknown(g, j, i)) {
             o.vy[q] = r_fma(a, o.py[q], o.vy[q]);
             const T rn = r_fma(-a, o.qy[q], o.ry[q]);
             o.ry[q] = rn;
-            s0 = fma((double)rn * (double)rn, -(double)o.ivy[q], s0);
+            s0 = acc_sq(s0, rn, -o.ivy[q]);
         }
     }
     block_store2(s0, 0.0, partials);

@@ -77,10 +77,9 @@ __global__ void __launch_bounds__(RD_THREADS) k_energy_r(int nx, int ny, int pit
 {
     double s0 = 0.0, s1 = 0.0;
     for_unknowns(nx, ny, pitch, [&](size_t q, int comp) {
-        const double wgt = -(double)(comp ? iy[q] : ix[q]);
-        const double r = (double)(comp ? ry[q] : rx[q]), f = (double)(comp ? fy[q] : fx[q]);
-        s0 = fma(r * r, wgt, s0);
-        s1 = fma(f * f, wgt, s1);
+        const T wgt = -(comp ? iy[q] : ix[q]);
+        s0 = acc_sq(s0, comp ? ry[q] : rx[q], wgt);
+        s1 = acc_sq(s1, comp ? fy[q] : fx[q], wgt);
     });
     block_store2(s0, s1, partials);
 }
@@ -102,7 +101,7 @@ __global__ void __launch_bounds__(RD_THREADS) k_cg_update(int nx, int ny, int pi
         v[q] = r_fma(at, (comp ? py : px)[q], v[q]);
         const T rn = r_fma(-at, (comp ? qy : qx)[q], r[q]);
         r[q] = rn;
-        s0 = fma((double)rn * (double)rn, -(double)(comp ? iy[q] : ix[q]), s0);
+        s0 = acc_sq(s0, rn, -(comp ? iy[q] : ix[q]));
     });
     block_store2(s0, 0.0, partials);
 }

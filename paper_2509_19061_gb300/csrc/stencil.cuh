@@ -26,6 +26,13 @@ __device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b
 __device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
+
+// s + r^2 w, accumulated in FP64.  FP64 inputs: one FP64 fma.  FP32 inputs:
+// the product in FP32 (its rounding, 2^-23 relative, is below that of the
+// FP32 residual itself), then one FP64 add, a third of the FP64-pipe work
+// (the FP64 pipe of this GPU runs at 1/64 of the FP32 rate).
+__device__ __forceinline__ double acc_sq(double s, double r, double w) { return fma(r * r, w, s); }
+__device__ __forceinline__ double acc_sq(double s, float r, float w) { return s + (double)r_mul(r_mul(r, r), w); }
 __device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 // correctly rounded reciprocal (the same value as 1/x with IEEE division)

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(EN_THREADS) k_energy(GridDesc<T> g, const T *_
     // r_v = f - G p - M v with b = f - G p formed on the fly; the weights
     // 1/(-diag M) come from the context's 1/diag arrays when it has them
     double s_rv = 0.0, s_rp = 0.0, s_ff = 0.0;
-    const double ilap = 1.0 / g.lap;
+    const T ilap = (T)(1.0 / g.lap);
     const long w = (long)g.nx + 1, total = w * (long)(g.ny + 1);
     for (long t = (long)blockIdx.x * EN_THREADS + threadIdx.x; t < total; t += (long)gridDim.x * EN_THREADS) {
         const int j = (int)(t / w), i = (int)(t - (long)j * w);
@@ -199,23 +199,20 @@ __global__ void __launch_bounds__(EN_THREADS) k_energy(GridDesc<T> g, const T *_
         if (vx_unknown(g, j, i)) {
             op_x<T, MASK>(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
             const T b = p ? r_fma(r_sub(p[q], p[q - 1]), g.ihx, fx[q]) : fx[q];
-            const double r = (double)r_sub(b, m), f = (double)fx[q];
-            const double wi = -(double)(inv_dx ? inv_dx[q] : inv_diag(d));
-            s_rv = fma(r * r, wi, s_rv);
-            s_ff = fma(f * f, wi, s_ff);
+            const T wi = -(inv_dx ? inv_dx[q] : inv_diag(d));
+            s_rv = acc_sq(s_rv, r_sub(b, m), wi);
+            s_ff = acc_sq(s_ff, fx[q], wi);
         }
         if (vy_unknown(g, j, i)) {
             op_y<T, MASK>(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
             const T b = p ? r_fma(r_sub(p[q], p[q - g.pitch]), g.ihy, fy[q]) : fy[q];
-            const double r = (double)r_sub(b, m), f = (double)fy[q];
-            const double wi = -(double)(inv_dy ? inv_dy[q] : inv_diag(d));
-            s_rv = fma(r * r, wi, s_rv);
-            s_ff = fma(f * f, wi, s_ff);
+            const T wi = -(inv_dy ? inv_dy[q] : inv_diag(d));
+            s_rv = acc_sq(s_rv, r_sub(b, m), wi);
+            s_ff = acc_sq(s_ff, fy[q], wi);
         }
         if (i < g.nx && j < g.ny) {
             const T dv = r_fma(r_sub(vx[q + 1], vx[q]), g.ihx, r_mul(r_sub(vy[q + g.pitch], vy[q]), g.ihy));
-            const double r = (double)dv;
-            s_rp = fma(r * r, (double)eta_c[q] * ilap, s_rp);
+            s_rp = acc_sq(s_rp, dv, r_mul(eta_c[q], ilap));
         }
     }
     __shared__ double sh[3][EN_THREADS / 32];

@@ -112,6 +112,25 @@ def test_energy_norm_f64(api, with_p):
     assert again == got  # fixed summation order
 
 
+@pytest.mark.parametrize("with_p", [False, True])
+def test_energy_norm_f32(api, with_p):
+    """FP32 context: each term is formed in FP32 and summed in FP64.  Against
+    the oracle on the FP32-rounded inputs the sums agree to the FP32
+    rounding of the residual and the coefficients (1e-5 relative)."""
+    nx, ny = 77, 53
+    prob = rand_problem(nx, ny, 4)
+    vx, vy = inputs.random_velocity(nx, ny, 5, 1e-3)
+    p = inputs.random_pressure(nx, ny, 6) if with_p else None
+    r = Run(api, prob, "f32", (vx, vy), p)
+    got = r.ctx.energy(r.vx, r.vy, r.p)
+    f32 = lambda a: None if a is None else np.asarray(a, dtype=np.float32).astype(np.float64)
+    g32 = ora.Grid(nx, ny, prob.hx, prob.hy, f32(prob.eta_c), f32(prob.eta_n))
+    want = ora.energy(g32, f32(prob.fx), f32(prob.fy), f32(p), f32(vx), f32(vy))
+    for a, b in zip(got, want):
+        assert abs(a - b) <= 1e-5 * abs(b), (a, b)
+    assert r.ctx.energy(r.vx, r.vy, r.p) == got
+
+
 def test_energy_norm_is_one_at_zero_state(api):
     prob = inputs.sinker_problem(64)
     r = Run(api, prob, "f64")
