@@ -358,13 +358,14 @@ def solve_times(args, api):
     from paper_2509_19061_gb300 import autotune, inputs
     n = args.solve_n
     prob = inputs.multi_sinker(n, seed=3)
-    sm = autotune.tuned_smoother(n, n, prob.eta_c, prob.eta_n, "f64")
     ctx = api.StokesContext(n, n, 1.0, 1.0, "f64")
     ctx.set_problem(prob)
     out = {"workload": "multi_sinker_%dx%d_seed3" % (n, n), "tol": 1e-8, "outer": "f64 flexible CG",
-           "smoother": "ras %dx%d k%d o%d (autotuned)" % (sm["tile"] + (sm["k"], sm["overlap"])),
            "nu": "5/5 x2.5 per level, cap 40"}
     for inner in ("f32", "f64"):
+        # each precision with the schedule the autotuner chose for its sweeps
+        sm = autotune.tuned_smoother(n, n, prob.eta_c, prob.eta_n, inner)
+        out[inner + "_smoother"] = "ras %dx%d k%d o%d (autotuned)" % (sm["tile"] + (sm["k"], sm["overlap"]))
         kw = dict(sm, seed=1, nu_max=40, inner=inner, krylov=True, tol=1e-8, max_cycles=200)
         vx, vy = ctx.field(), ctx.field()
         ctx.vcycle(vx, vy, None, **kw)  # builds the hierarchy and the graph
@@ -398,10 +399,9 @@ def batch_leg(args, api):
            "cells_total": cells}
     sw = 20
     from paper_2509_19061_gb300 import autotune
-    tuned = autotune.Cache(autotune.SHIPPED).lookup(1024, 1024, 1e4, "f64")
+    tuned = autotune.Cache(autotune.SHIPPED).batch(autotune.BATCH_NAME if len(probs) == 256 else "")
     sched = dict(variant="ras", tile=(tuned.tile_i, tuned.tile_j), k=tuned.k, overlap=tuned.overlap, seed=1)
-    label = "ras %dx%d k%d o%d (autotuned, 1024^2 contrast 1e4 bucket)" % (tuned.tile_i, tuned.tile_j, tuned.k,
-                                                                           tuned.overlap)
+    label = "ras %dx%d k%d o%d (autotuned on this batch)" % (tuned.tile_i, tuned.tile_j, tuned.k, tuned.overlap)
     smooth_kw = dict(sched, sweeps=sw)
     stream = torch.cuda.current_stream()
 

@@ -8,8 +8,11 @@ objective is therefore the wall time of the whole solve to E_v <= tol, not
 the speed of one sweep.
 
 Results are kept in a JSON cache keyed by (size bucket, dtype, contrast
-bucket): size bucket = round(log2(sqrt(nx * ny))), contrast bucket =
-round(log10(max eta / min eta)).  Tuning runs on the GPU through the
+bucket): size bucket = round(log2(sqrt(nx * ny))), dtype = the precision
+the sweeps run in (the V-cycle's inner precision), contrast bucket =
+round(log10(max eta / min eta)).  A batch of instances shares one schedule,
+tuned on the batch itself (objective: the time until every instance has
+converged) and kept under its own name.  Tuning runs on the GPU through the
 library; lookups are plain Python.
 """
 import json
@@ -55,15 +58,21 @@ def bucket(nx, ny, contrast, dtype):
 
 
 class Cache:
-    """JSON file of the best Choice per bucket."""
+    """JSON file of the best Choice per bucket (and per named batch)."""
 
     def __init__(self, path):
         self.path = path
         self.entries = {}
+        self.batches = {}
         if path and os.path.exists(path):
             with open(path) as f:
                 raw = json.load(f)
             self.entries = {k: Choice(**v) for k, v in raw.get("entries", {}).items()}
+            self.batches = {k: Choice(**v) for k, v in raw.get("batches", {}).items()}
+
+    def batch(self, name):
+        """The Choice tuned for the named batch, else the default."""
+        return self.batches.get(name, DEFAULT)
 
     def lookup(self, nx, ny, contrast, dtype):
         """The cached Choice of the bucket, else the nearest cached size bucket
@@ -85,13 +94,14 @@ class Cache:
         tmp = self.path + ".tmp"
         with open(tmp, "w") as f:
             json.dump({"objective": "wall seconds of the flexible-CG solve to E_v <= tol",
-                       "entries": {k: asdict(v) for k, v in sorted(self.entries.items())}}, f, indent=1)
+                       "entries": {k: asdict(v) for k, v in sorted(self.entries.items())},
+                       "batches": {k: asdict(v) for k, v in sorted(self.batches.items())}}, f, indent=1)
         os.replace(tmp, self.path)
 
 
-def tuned_smoother(nx, ny, eta_c, eta_n, dtype="f64", path=SHIPPED):
+def tuned_smoother(nx, ny, eta_c, eta_n, dtype="f32", path=SHIPPED):
     """Smoother keyword arguments (variant, tile, k, overlap) of the cached
-    choice for this grid, viscosity contrast and dtype."""
+    choice for this grid, viscosity contrast and sweep precision."""
     return Cache(path).lookup(nx, ny, contrast_of(eta_c, eta_n), dtype).smoother()
 
 
@@ -140,17 +150,19 @@ def tune(api, prob, dtype="f64", inner="f32", candidates=None, tol=1e-8, max_cyc
 
 
 def tune_buckets(api, sizes=(256, 1024, 4096), contrasts=(1e2, 1e4, 1e6), dtype="f64", inner="f32", path=None,
-                 log=print):
+                 log=print, candidates=None, cache=None):
     """Tune one representative problem per (size, contrast) bucket: the
-    centred sinker of Sec. 6.1 with eta_in = contrast on an n x n grid.
-    Returns the cache (saved to `path` when given)."""
+    centred sinker of Sec. 6.1 with eta_in = contrast on an n x n grid, FP64
+    outer iteration, sweeps in `inner`.  Returns the cache (saved to `path`
+    when given)."""
     from . import inputs
-    cache = Cache(path) if path else Cache(None)
+    if cache is None:
+        cache = Cache(path) if path else Cache(None)
     for n in sizes:
         for c in contrasts:
             prob = inputs.sinker_problem(n, eta_in=c)
-            win, table = tune(api, prob, dtype=dtype, inner=inner)
-            cache.record(n, n, contrast_of(prob.eta_c, prob.eta_n), dtype, win)
+            win, table = tune(api, prob, dtype=dtype, inner=inner, candidates=candidates)
+            cache.record(n, n, contrast_of(prob.eta_c, prob.eta_n), inner, win)
             log("n=%d contrast=%.0e: best %s in %.4f s (%d cycles); default %s" % (
                 n, c, (win.tile_i, win.tile_j, win.k, win.overlap), win.seconds, win.cycles,
                 next(("%.4f s" % t.seconds for t in table
@@ -158,6 +170,48 @@ def tune_buckets(api, sizes=(256, 1024, 4096), contrasts=(1e2, 1e4, 1e6), dtype=
     if path:
         cache.save()
     return cache
+
+
+def tune_batch(api, probs, name, candidates=None, cache=None, tol=1e-8, max_cycles=300, nu_max=40, seed=1,
+               log=print):
+    """Tune one schedule for a batch (inputs.Problem list, solved together by
+    the batched path: FP64 outer flexible CG, FP32 sweeps) by the wall time
+    until every instance reaches E_v <= tol; schedules that leave an
+    instance unconverged get an infinite time.  Records the winner under
+    `name` in `cache` (when given) and returns (winner, table)."""
+    import torch
+    cands = candidates or [(32, 32, 4, 3), (56, 32, 4, 3), (32, 32, 8, 7), (32, 32, 4, 0), (56, 32, 4, 0),
+                           (32, 32, 8, 0), (56, 32, 8, 0), (32, 32, 2, 1), (16, 16, 4, 3)]
+    b = api.BatchContext([q.nx for q in probs], [q.ny for q in probs], [q.lx for q in probs],
+                         [q.ly for q in probs], "f64")
+    b.set_problems(probs)
+    vx, vy = b.slab(), b.slab()
+    out = []
+    for ti, tj, k, o in cands:
+        kw = dict(variant="ras", tile=(ti, tj), k=k, overlap=o, seed=seed, nu_max=nu_max, inner="f32", krylov=True,
+                  tol=tol, max_cycles=max_cycles)
+        vx.zero_()
+        vy.zero_()
+        b.solve(vx, vy, None, **kw)  # plans and graph
+        vx.zero_()
+        vy.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, e, cyc, sts = b.solve(vx, vy, None, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ok = st == api.STOKES_OK
+        out.append(Choice(ti, tj, k, o, dt if ok else float("inf"), int(max(cyc))))
+        log("batch %s: %s %.3f s, max %d cycles, %s" % (name, (ti, tj, k, o), dt, max(cyc),
+                                                       "converged" if ok else "not converged"))
+    b.close()
+    win = min(out, key=lambda c: c.seconds)
+    if cache is not None:
+        cache.batches[name] = win
+    return win, out
+
+
+BATCH_NAME = "batch256_seed5"
 
 
 if __name__ == "__main__":
@@ -171,6 +225,19 @@ if __name__ == "__main__":
     ap.add_argument("--contrasts", type=float, nargs="+", default=[1e2, 1e4, 1e6])
     ap.add_argument("--dtype", default="f64")
     ap.add_argument("--inner", default="f32")
+    ap.add_argument("--f64-sizes", type=int, nargs="*", default=[256, 1024],
+                    help="sizes also tuned with FP64 sweeps (tiles up to 32 x 32)")
+    ap.add_argument("--batch", type=int, default=256, help="instances of the tuned batch (0: none)")
     a = ap.parse_args()
     _build.build()
-    tune_buckets(_api, a.sizes, a.contrasts, a.dtype, a.inner, a.out)
+    cache = Cache(None)
+    cache.path = a.out
+    tune_buckets(_api, a.sizes, a.contrasts, a.dtype, "f32", cache=cache)
+    if a.f64_sizes:
+        f64c = [c for c in DEFAULT_CANDIDATES if c[0] <= 32]
+        tune_buckets(_api, a.f64_sizes, a.contrasts, a.dtype, "f64", candidates=f64c, cache=cache)
+    if a.batch > 0:
+        from . import inputs as _inputs
+        probs = [_inputs.batch_problem(sp) for sp in _inputs.batch_specs(seed=5, count=a.batch)]
+        tune_batch(_api, probs, BATCH_NAME, cache=cache)
+    cache.save()
