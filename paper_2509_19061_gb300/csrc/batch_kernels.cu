@@ -326,35 +326,15 @@ template <typename T>
 __global__ void kb_apply_dot(const BOuter<T> *__restrict__ tab, const BSeg *__restrict__ m, int n,
                              double *__restrict__ partials)
 {
-    const Pt p = point_of(m, n);
+    // the blocks of an instance are its 32 x 8 tiles (BATCH_BX x BATCH_BY)
+    __shared__ ApplyTile<T> sm;
+    const BSeg sg = m[seg_of(m, n, blockIdx.x)];
+    const int lb = blockIdx.x - sg.block_begin;
+    const BOuter<T> &o = tab[sg.inst];
     double s0 = 0.0, s1 = 0.0;
-    if (p.valid) {
-        const BOuter<T> &o = tab[p.inst];
-        const GridDesc<T> &g = o.g;
-        const int i = p.i, j = p.j;
-        const size_t q = (size_t)j * g.pitch + i;
-        T mm, d, vc;
-        if (j < g.ny) {
-            T r = T(0);
-            if (vx_unknown(g, j, i)) {
-                op_x(g, o.ec, o.en, (const T *)o.px, (const T *)o.py, j, i, mm, d, vc);
-                r = mm;
-                s0 = fma((double)vc, (double)mm, s0);
-                s1 = fma((double)vc, (double)o.rx[q], s1);
-            }
-            o.qx[q] = r;
-        }
-        if (i < g.nx) {
-            T r = T(0);
-            if (vy_unknown(g, j, i)) {
-                op_y(g, o.ec, o.en, (const T *)o.px, (const T *)o.py, j, i, mm, d, vc);
-                r = mm;
-                s0 = fma((double)vc, (double)mm, s0);
-                s1 = fma((double)vc, (double)o.ry[q], s1);
-            }
-            o.qy[q] = r;
-        }
-    }
+    static_assert(BATCH_BX == AT_X && BATCH_BY == AT_Y, "batched blocks are apply tiles");
+    apply_dot_tile<T>(o.g, o.ec, o.en, o.px, o.py, o.qx, o.qy, o.rx, o.ry, (lb % sg.bxb) * BATCH_BX,
+                      (lb / sg.bxb) * BATCH_BY, (int)(threadIdx.y * BATCH_BX + threadIdx.x), sm, s0, s1);
     block_store2(s0, s1, partials);
 }
 

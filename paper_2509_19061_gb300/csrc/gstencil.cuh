@@ -78,4 +78,92 @@ __device__ __forceinline__ bool vy_wall(const GridDesc<T> &g, int j, int i)
     return i < g.nx && (j == 0 || j == g.ny);
 }
 
+// ---- tiled operator apply with shared fluxes --------------------------------
+// q = M p on the 32 x 8 cell tile at (i0, j0), plus (<p, q>, <p, r>) over its
+// unknowns added to (s0, s1).  Every flux of the tile and a one-cell halo
+// (sigma'xx at cells, sigma'yy at cells, the shear at nodes) is computed once
+// into shared memory and M p assembled from them: about half the arithmetic
+// of evaluating the stencil per unknown, which computes each flux twice.  The
+// operands and helpers are those of op_x / op_y (library eta_n with zero
+// boundary nodes; rows and columns outside a field read as zero), so q is the
+// same bit for bit.  Called by all 256 threads of the block; tid is the
+// caller's linear thread index (0 .. 255).
+constexpr int AT_X = 32, AT_Y = 8;
+
+template <typename T>
+struct ApplyTile {
+    T txx[AT_Y][AT_X + 1];    // cells (j0 + a, i0 - 1 + b)
+    T tyy[AT_Y + 1][AT_X];    // cells (j0 - 1 + a, i0 + b)
+    T sh[AT_Y + 1][AT_X + 1]; // nodes (j0 + a, i0 + b)
+};
+
+template <typename T>
+__device__ __forceinline__ void apply_dot_tile(const GridDesc<T> &g, const T *__restrict__ ec,
+                                               const T *__restrict__ en, const T *__restrict__ px,
+                                               const T *__restrict__ py, T *__restrict__ qx, T *__restrict__ qy,
+                                               const T *__restrict__ rx, const T *__restrict__ ry, int i0, int j0,
+                                               int tid, ApplyTile<T> &sm, double &s0, double &s1)
+{
+    const size_t P = (size_t)g.pitch;
+    const int nt = AT_X * AT_Y, tx = tid % AT_X, ty = tid / AT_X;
+    for (int e = tid; e < AT_Y * (AT_X + 1); e += nt) {
+        const int a = e / (AT_X + 1), b = e % (AT_X + 1);
+        const int J = j0 + a, I = i0 - 1 + b;
+        T v = T(0);
+        if (J < g.ny && I >= 0 && I < g.nx) {
+            const size_t q = (size_t)J * P + I;
+            v = flux_n(coef_x(g, ec[q]), px[q + 1], px[q]);
+        }
+        sm.txx[a][b] = v;
+    }
+    for (int e = tid; e < (AT_Y + 1) * AT_X; e += nt) {
+        const int a = e / AT_X, b = e % AT_X;
+        const int J = j0 - 1 + a, I = i0 + b;
+        T v = T(0);
+        if (J >= 0 && J < g.ny && I < g.nx) {
+            const size_t q = (size_t)J * P + I;
+            v = flux_n(coef_y(g, ec[q]), py[q + P], py[q]);
+        }
+        sm.tyy[a][b] = v;
+    }
+    for (int e = tid; e < (AT_Y + 1) * (AT_X + 1); e += nt) {
+        const int a = e / (AT_X + 1), b = e % (AT_X + 1);
+        const int J = j0 + a, I = i0 + b;
+        T v = T(0);
+        if (J <= g.ny && I <= g.nx) {
+            const size_t q = (size_t)J * P + I;
+            const T vxa = J < g.ny ? px[q] : T(0), vxb = J > 0 ? px[q - P] : T(0);
+            const T vyr = I < g.nx ? py[q] : T(0), vyl = I > 0 ? py[q - 1] : T(0);
+            v = shear(g, en[q], vxa, vxb, vyr, vyl);
+        }
+        sm.sh[a][b] = v;
+    }
+    __syncthreads();
+    const int j = j0 + ty, i = i0 + tx;
+    if (j <= g.ny && i <= g.nx) {
+        const size_t q = (size_t)j * P + i;
+        if (j < g.ny) {
+            T m = T(0);
+            if (vx_unknown(g, j, i)) {
+                m = m_x(sm.txx[ty][tx + 1], sm.txx[ty][tx], r_mul(sm.sh[ty + 1][tx], g.ihy),
+                        r_mul(sm.sh[ty][tx], g.ihy));
+                s0 = fma((double)px[q], (double)m, s0);
+                s1 = fma((double)px[q], (double)rx[q], s1);
+            }
+            qx[q] = m;
+        }
+        if (i < g.nx) {
+            T m = T(0);
+            if (vy_unknown(g, j, i)) {
+                m = m_y(r_mul(sm.sh[ty][tx + 1], g.ihx), r_mul(sm.sh[ty][tx], g.ihx), sm.tyy[ty + 1][tx],
+                        sm.tyy[ty][tx]);
+                s0 = fma((double)py[q], (double)m, s0);
+                s1 = fma((double)py[q], (double)ry[q], s1);
+            }
+            qy[q] = m;
+        }
+    }
+    __syncthreads();
+}
+
 } // namespace stokes

@@ -4,6 +4,7 @@
 #include "../../include/stokes.h"
 #include "internal.h"
 #include "mg.h"
+#include "gstencil.cuh"
 #include "stencil.cuh"
 
 namespace stokes {
@@ -11,6 +12,7 @@ namespace stokes {
 namespace {
 
 constexpr int RD_THREADS = 256;
+static_assert(AT_X * AT_Y == RD_THREADS, "one thread per tile cell");
 constexpr int RD_BLOCKS = 152 * 4;
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -130,6 +132,25 @@ __global__ void __launch_bounds__(RD_THREADS) k_add(int nx, int ny, int pitch, c
     });
 }
 
+// q = M p and (<p, q>, <p, r>) over the unknowns, tile by tile (see
+// apply_dot_tile); each block walks the 32 x 8 cell tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ...
+template <typename T>
+__global__ void __launch_bounds__(RD_THREADS) k_apply_dot(GridDesc<T> g, const T *__restrict__ ec,
+                                                          const T *__restrict__ en, const T *__restrict__ px,
+                                                          const T *__restrict__ py, T *__restrict__ qx,
+                                                          T *__restrict__ qy, const T *__restrict__ rx,
+                                                          const T *__restrict__ ry, double *__restrict__ partials)
+{
+    __shared__ ApplyTile<T> sm;
+    const int ntx = (g.nx + 1 + AT_X - 1) / AT_X, nty = (g.ny + 1 + AT_Y - 1) / AT_Y;
+    double s0 = 0.0, s1 = 0.0;
+    for (int t = blockIdx.x; t < ntx * nty; t += gridDim.x)
+        apply_dot_tile<T>(g, ec, en, px, py, qx, qy, rx, ry, (t % ntx) * AT_X, (t / ntx) * AT_Y, (int)threadIdx.x,
+                          sm, s0, s1);
+    block_store2(s0, s1, partials);
+}
+
 __global__ void k_final2(const double *__restrict__ partials, int nblocks, double *__restrict__ out)
 {
     const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -148,6 +169,15 @@ cudaError_t kry_dot2(const KrylovView &k, const T *ax, const T *ay, const T *bx,
                      const T *cy, cudaStream_t s)
 {
     k_dot2<T><<<RD_BLOCKS, RD_THREADS, 0, s>>>(k.nx, k.ny, k.pitch, ax, ay, bx, by, cx, cy, k.partials);
+    k_final2<<<1, 64, 0, s>>>(k.partials, RD_BLOCKS, k.out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t kry_apply_dot(const KrylovView &k, const GridDesc<T> &g, const T *ec, const T *en, const T *px,
+                          const T *py, T *qx, T *qy, const T *rx, const T *ry, cudaStream_t s)
+{
+    k_apply_dot<T><<<RD_BLOCKS, RD_THREADS, 0, s>>>(g, ec, en, px, py, qx, qy, rx, ry, k.partials);
     k_final2<<<1, 64, 0, s>>>(k.partials, RD_BLOCKS, k.out);
     return cudaGetLastError();
 }
@@ -194,7 +224,9 @@ cudaError_t kry_add(const KrylovView &k, const T *zx, const T *zy, T *vx, T *vy,
                                        T *, T *, T *, T *, const T *, const T *, cudaStream_t);                    \
     template cudaError_t kry_direction<T>(const KrylovView &, double, const T *, const T *, T *, T *,             \
                                           cudaStream_t);                                                           \
-    template cudaError_t kry_add<T>(const KrylovView &, const T *, const T *, T *, T *, cudaStream_t);
+    template cudaError_t kry_add<T>(const KrylovView &, const T *, const T *, T *, T *, cudaStream_t);          \
+    template cudaError_t kry_apply_dot<T>(const KrylovView &, const GridDesc<T> &, const T *, const T *,        \
+                                          const T *, const T *, T *, T *, const T *, const T *, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -552,18 +552,22 @@ __global__ void __launch_bounds__(MAXT, MINB) k_ras_batched_tma(const BatchTiles
     const bool active = (int)threadIdx.x < G.wxm * G.strips;
     const uint32_t box_bytes = (uint32_t)(BW * shape.wym * (int)sizeof(T));
 
+    // tensor maps are acquired once per instance by the issuing thread
+    int acquired = -1;
     auto issue = [&](int t) {
         const int e = batch_entry(tab, count, t);
         const RasArgs<T> a = batch_args(shape, tab[e]);
         const Window w = window_of(a, t - tab[e].tile_begin);
         const int xs = w.ox0 & ~(ALIGN - 1);
+        if (e != acquired) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) fence_tensormap_acquire(&maps[e].m[f]);
+            acquired = e;
+        }
         fence_proxy_async();
         mbar_arrive_expect_tx(&bar, NF * box_bytes);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            fence_tensormap_acquire(&maps[e].m[f]);
-            tma_load_2d(stage + f * SP, &maps[e].m[f], xs, w.oy0, &bar);
-        }
+        for (int f = 0; f < NF; ++f) tma_load_2d(stage + f * SP, &maps[e].m[f], xs, w.oy0, &bar);
     };
 
     // this CTA's next tile from t on (stride gridDim.x) whose instance is live

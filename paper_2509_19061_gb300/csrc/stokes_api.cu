@@ -429,9 +429,9 @@ int vcycle_impl(stokes_ctx *c, T *vx, T *vy, const T *p, const stokes_mg_params 
         CK(cudaMemcpyAsync(px, zx, c->elems * c->esize, cudaMemcpyDeviceToDevice, c->stream));
         CK(cudaMemcpyAsync(py, zy, c->elems * c->esize, cudaMemcpyDeviceToDevice, c->stream));
         for (;;) {
-            RUN(STOKES_K_APPLY, 1,
-                launch_apply<T>(g, (const T *)c->eta_c, (const T *)c->eta_n, px, py, nullptr, qx, qy, c->stream));
-            RUN(STOKES_K_MG, 2, kry_dot2<T>(kv, px, py, qx, qy, rx, ry, c->stream));
+            RUN(STOKES_K_APPLY, 2,
+                kry_apply_dot<T>(kv, g, (const T *)c->eta_c, (const T *)c->eta_n, px, py, qx, qy, rx, ry,
+                                 c->stream));
             double pq = 0.0, pr = 0.0;
             if ((st = read2(c, &pq, &pr)) != STOKES_OK) return st;
             const double a = pr / pq;
