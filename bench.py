@@ -489,7 +489,11 @@ def batch_leg(args, api):
     b = api.BatchContext([q.nx for q in probs], [q.ny for q in probs], dtype="f64")
     b.set_problems(probs)
     vx, vy = b.slab(), b.slab()
-    b.solve(vx, vy, None, **kw)  # hierarchy and graph
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.solve(vx, vy, None, **kw)  # hierarchy, dense coarsest inverses, plans, graph, and one solve
+    torch.cuda.synchronize()
+    t_first = time.perf_counter() - t0
     vx.zero_()
     vy.zero_()
     torch.cuda.synchronize()
@@ -517,7 +521,7 @@ def batch_leg(args, api):
         conv += s1 == api.STOKES_OK
         c.close()
     out["solve"] = {"tol": 1e-8, "outer": "f64 flexible CG", "inner": "f32 V-cycle, %s, nu cap 40" % label,
-                    "batched_seconds": t_bs, "batched_status": int(st),
+                    "batched_seconds": t_bs, "batched_first_call_seconds": t_first, "batched_status": int(st),
                     "batched_converged": int(sum(1 for x in sts if x == api.STOKES_OK)),
                     "batched_max_cycles": int(max(cyc)), "batched_kernels": int(kb),
                     "per_instance_seconds": t_ls, "per_instance_converged": int(conv),

@@ -463,15 +463,44 @@ int build_hier(stokes_batch *b, BHier *h, int levels, int coarsest)
     CK(cudaMalloc(&h->Ainv, asz * 8));
     CK(cudaMalloc(&h->bvec, (size_t)h->rows * 8));
     CK(cudaMalloc(&h->xvec, (size_t)h->rows * 8));
+    // all factorisations in chunks whose work matrices fit in 1 GB: one
+    // launch per kernel and chunk, one CTA (or column block) per instance
     double *A = nullptr, *W = nullptr;
     int *dst = nullptr;
+    DenseJob *djobs = nullptr;
     int st = STOKES_OK;
-    cudaError_t e = cudaMalloc(&A, nmax * nmax * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&W, nmax * nmax * 8);
+    const size_t budget = (size_t)1 << 30;
+    const size_t per = std::max(nmax * nmax * 16, (size_t)16);
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)n, budget / per));
+    cudaError_t e = cudaMalloc(&A, (size_t)chunk * nmax * nmax * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&W, (size_t)chunk * nmax * nmax * 8);
     if (e == cudaSuccess) e = cudaMalloc(&dst, (size_t)n * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&djobs, (size_t)chunk * sizeof(DenseJob));
     if (e == cudaSuccess) e = cudaMemsetAsync(dst, 0, (size_t)n * sizeof(int), s);
-    for (int i = 0; i < n && e == cudaSuccess; ++i)
-        e = mg_dense_setup<Ti>(level_view(h, h->L[i] - 1, i, es), h->n[i], A, W, h->Ainv + h->aoff[i], dst + i, s);
+    std::vector<DenseJob> jobs(chunk);
+    for (int i0 = 0; i0 < n && e == cudaSuccess; i0 += chunk) {
+        const int c = std::min(chunk, n - i0);
+        for (int q = 0; q < c; ++q) {
+            const int i = i0 + q;
+            const MgLevel v = level_view(h, h->L[i] - 1, i, es);
+            DenseJob &jb = jobs[q];
+            jb.nx = v.nx;
+            jb.ny = v.ny;
+            jb.pitch = v.pitch;
+            jb.n = h->n[i];
+            jb.ihx = 1.0 / v.hx;
+            jb.ihy = 1.0 / v.hy;
+            jb.ec = v.ec;
+            jb.en = v.en;
+            jb.A = A + (size_t)q * nmax * nmax;
+            jb.W = W + (size_t)q * nmax * nmax;
+            jb.Ainv = h->Ainv + h->aoff[i];
+            jb.status = dst + i;
+        }
+        e = cudaMemcpyAsync(djobs, jobs.data(), (size_t)c * sizeof(DenseJob), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = mg_dense_setup_many<Ti>(djobs, c, (int)nmax, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s); // the host table is rewritten next
+    }
     std::vector<int> bad(n, 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(bad.data(), dst, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -479,6 +508,7 @@ int build_hier(stokes_batch *b, BHier *h, int levels, int coarsest)
     cudaFree(A);
     cudaFree(W);
     cudaFree(dst);
+    cudaFree(djobs);
     if (st != STOKES_OK) return st;
     for (int i = 0; i < n; ++i)
         if (bad[i]) return STOKES_ERR_DIVERGED;

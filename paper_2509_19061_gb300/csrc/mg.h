@@ -91,6 +91,19 @@ cudaError_t mg_prolong_add(const MgLevel &f, const MgLevel &c, cudaStream_t s);
 template <typename T>
 cudaError_t mg_dense_setup(const MgLevel &l, int n, double *A, double *W, double *Ainv, int *status,
                            cudaStream_t s);
+// One dense coarsest factorisation: the level's grid and viscosity (inner
+// precision), its n unknowns, n x n FP64 work matrices A and W, the inverse
+// Ainv and a status word (set to 1 if -M is not positive definite).
+struct DenseJob {
+    int nx, ny, pitch, n;
+    double ihx, ihy;
+    const void *ec, *en;
+    double *A, *W, *Ainv;
+    int *status;
+};
+// `count` factorisations at once (device table `jobs`, n <= nmax each).
+template <typename T>
+cudaError_t mg_dense_setup_many(const DenseJob *jobs, int count, int nmax, cudaStream_t s);
 template <typename T>
 cudaError_t mg_dense_solve(const MgLevel &l, int n, const double *Ainv, double *bvec, double *xvec, cudaStream_t s);
 

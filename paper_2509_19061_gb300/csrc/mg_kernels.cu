@@ -119,10 +119,16 @@ __device__ __forceinline__ void unknown_pos(int u, int nx, int ny, int &comp, in
 
 // A[r][c] = -(M e_c)_r in FP64 from the level's viscosity (boundary nodes of
 // eta_n hold zero)
+// (one job per blockIdx.y)
 template <typename T>
-__global__ void k_assemble(int nx, int ny, int pitch, double ihx, double ihy, const T *__restrict__ ec,
-                           const T *__restrict__ en, int n, double *__restrict__ A)
+__global__ void k_assemble(const DenseJob *__restrict__ jobs)
 {
+    const DenseJob &jb = jobs[blockIdx.y];
+    const int nx = jb.nx, ny = jb.ny, pitch = jb.pitch, n = jb.n;
+    const double ihx = jb.ihx, ihy = jb.ihy;
+    const T *__restrict__ ec = (const T *)jb.ec;
+    const T *__restrict__ en = (const T *)jb.en;
+    double *__restrict__ A = jb.A;
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long)n * n) return;
     const int r = (int)(t / n), c = (int)(t - (long)r * n);
@@ -153,10 +159,14 @@ __global__ void k_assemble(int nx, int ny, int pitch, double ihx, double ihy, co
     A[(size_t)r * n + c] = -m;
 }
 
-// In-place Cholesky A = L L^T (lower triangle) by one CTA; status = 1 if a
-// pivot is not positive.
-__global__ void k_cholesky(int n, double *__restrict__ A, int *__restrict__ status)
+// In-place Cholesky A = L L^T (lower triangle) by one CTA per job
+// (blockIdx.x); status = 1 if a pivot is not positive.  Every entry is
+// updated in the order k = 0, 1, ..., whatever the thread layout.
+__global__ void k_cholesky(const DenseJob *__restrict__ jobs)
 {
+    const DenseJob &jb = jobs[blockIdx.x];
+    const int n = jb.n;
+    double *__restrict__ A = jb.A;
     __shared__ double piv;
     __shared__ int bad;
     if (threadIdx.x == 0) bad = 0;
@@ -171,19 +181,26 @@ __global__ void k_cholesky(int n, double *__restrict__ A, int *__restrict__ stat
         __syncthreads();
         for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[(size_t)i * n + k] /= piv;
         __syncthreads();
-        const int m = n - k - 1; // trailing lower triangle, rows/cols k+1..n-1
-        for (long t = threadIdx.x; t < (long)m * m; t += blockDim.x) {
-            const int i = k + 1 + (int)(t / m), j = k + 1 + (int)(t % m);
-            if (j <= i) A[(size_t)i * n + j] -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
+        // trailing lower triangle, rows/cols k+1..n-1: warp w takes rows
+        // k+1+w, k+1+w+nw, ..., its lanes the columns of a row
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int i = k + 1 + w; i < n; i += nw) {
+            const double lik = A[(size_t)i * n + k];
+            for (int j = k + 1 + lane; j <= i; j += 32) A[(size_t)i * n + j] -= lik * A[(size_t)j * n + k];
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0 && bad) *status = 1;
+    if (threadIdx.x == 0 && bad) *jb.status = 1;
 }
 
-// W = L^{-1}, column c by thread c (forward substitution), lower triangle
-__global__ void k_tri_inverse(int n, const double *__restrict__ L, double *__restrict__ W)
+// W = L^{-1}, column c by thread c (forward substitution), lower triangle;
+// one job per blockIdx.y
+__global__ void k_tri_inverse(const DenseJob *__restrict__ jobs)
 {
+    const DenseJob &jb = jobs[blockIdx.y];
+    const int n = jb.n;
+    const double *__restrict__ L = jb.A;
+    double *__restrict__ W = jb.W;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
     for (int i = 0; i < c; ++i) W[(size_t)i * n + c] = 0.0;
@@ -195,9 +212,13 @@ __global__ void k_tri_inverse(int n, const double *__restrict__ L, double *__res
     }
 }
 
-// Ainv = W^T W
-__global__ void k_gram(int n, const double *__restrict__ W, double *__restrict__ Ainv)
+// Ainv = W^T W; one job per blockIdx.y
+__global__ void k_gram(const DenseJob *__restrict__ jobs)
 {
+    const DenseJob &jb = jobs[blockIdx.y];
+    const int n = jb.n;
+    const double *__restrict__ W = jb.W;
+    double *__restrict__ Ainv = jb.Ainv;
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long)n * n) return;
     const int i = (int)(t / n), j = (int)(t - (long)i * n);
@@ -291,16 +312,46 @@ cudaError_t mg_prolong_add(const MgLevel &f, const MgLevel &c, cudaStream_t s)
 }
 
 template <typename T>
+cudaError_t mg_dense_setup_many(const DenseJob *jobs, int count, int nmax, cudaStream_t s)
+{
+    const long nn = (long)nmax * nmax;
+    for (int j0 = 0; j0 < count; j0 += 65535) {
+        const int c = count - j0 < 65535 ? count - j0 : 65535;
+        const DenseJob *jb = jobs + j0;
+        k_assemble<T><<<dim3((unsigned)((nn + 255) / 256), c), 256, 0, s>>>(jb);
+        k_cholesky<<<c, 1024, 0, s>>>(jb);
+        k_tri_inverse<<<dim3((nmax + 127) / 128, c), 128, 0, s>>>(jb);
+        k_gram<<<dim3((unsigned)((nn + 255) / 256), c), 256, 0, s>>>(jb);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t mg_dense_setup(const MgLevel &l, int n, double *A, double *W, double *Ainv, int *status,
                            cudaStream_t s)
 {
-    const long nn = (long)n * n;
-    k_assemble<T><<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(l.nx, l.ny, l.pitch, 1.0 / l.hx, 1.0 / l.hy,
-                                                               (const T *)l.ec, (const T *)l.en, n, A);
-    k_cholesky<<<1, 1024, 0, s>>>(n, A, status);
-    k_tri_inverse<<<(n + 127) / 128, 128, 0, s>>>(n, A, W);
-    k_gram<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(n, W, Ainv);
-    return cudaGetLastError();
+    DenseJob h;
+    h.nx = l.nx;
+    h.ny = l.ny;
+    h.pitch = l.pitch;
+    h.n = n;
+    h.ihx = 1.0 / l.hx;
+    h.ihy = 1.0 / l.hy;
+    h.ec = l.ec;
+    h.en = l.en;
+    h.A = A;
+    h.W = W;
+    h.Ainv = Ainv;
+    h.status = status;
+    // a one-entry job table in stream-ordered memory, freed after the kernels
+    DenseJob *d = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&d, sizeof(DenseJob), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(d, &h, sizeof(DenseJob), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = mg_dense_setup_many<T>(d, 1, n, s);
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaFreeAsync(d, s);
+    return e != cudaSuccess ? e : e2;
 }
 
 template <typename T>
@@ -319,6 +370,7 @@ cudaError_t mg_dense_solve(const MgLevel &l, int n, const double *Ainv, double *
     template cudaError_t mg_prolong_add<T>(const MgLevel &, const MgLevel &, cudaStream_t);                        \
     template cudaError_t mg_dense_setup<T>(const MgLevel &, int, double *, double *, double *, int *,              \
                                            cudaStream_t);                                                          \
+    template cudaError_t mg_dense_setup_many<T>(const DenseJob *, int, int, cudaStream_t);                         \
     template cudaError_t mg_dense_solve<T>(const MgLevel &, int, const double *, double *, double *, cudaStream_t);
 INST(float)
 INST(double)
