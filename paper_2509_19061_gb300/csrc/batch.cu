@@ -137,6 +137,7 @@ struct RasForm {
 template <typename T>
 struct TileLaunch {
     const BatchTiles<T> *tab;
+    const int *tmap;  // table entry of every tile
     const void *maps; // per-instance tensor maps (TMA staging), or NULL
     int count, total, ti, tj, ks, overlap;
 };
@@ -217,6 +218,12 @@ int plan_group(Owned &o, const std::vector<GInst<T>> &gi, const RasForm &f, bool
         if (ras_batched_smem_bytes(shi, shj, ov, sizeof(T)) > (size_t)ras_max_smem()) return STOKES_ERR_ARG;
         TileLaunch<T> L;
         ST(upload(o, tab, &L.tab, s));
+        {
+            std::vector<int> tm((size_t)total);
+            for (size_t q = 0; q < n; ++q)
+                for (int u = 0; u < tab[q].tg.ntx * tab[q].tg.nty; ++u) tm[(size_t)tab[q].tile_begin + u] = (int)q;
+            ST(upload(o, tm, &L.tmap, s));
+        }
         L.maps = nullptr;
         if (tma && ras_batched_tma(shi, shj, ov, sizeof(T))) {
             std::vector<CUtensorMap> m(n * (ras_batched_maps_bytes() / sizeof(CUtensorMap)));
@@ -247,8 +254,8 @@ int run_group(const Group<T> &G, const int *live, const RasRun &run, cudaStream_
         ++*nk;
     }
     for (const TileLaunch<T> &L : G.launches) {
-        CK(launch_ras_batched<T>(L.tab, L.maps, L.count, L.total, L.ti, L.tj, L.ks, L.overlap, G.omega, live, run,
-                                 s));
+        CK(launch_ras_batched<T>(L.tab, L.tmap, L.maps, L.count, L.total, L.ti, L.tj, L.ks, L.overlap, G.omega, live,
+                                 run, s));
         ++*nk;
     }
     if (G.back) {

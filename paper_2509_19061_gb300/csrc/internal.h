@@ -125,12 +125,15 @@ struct BatchTiles {
 // One RAS outer iteration (ksweeps local sweeps) for every instance of the
 // device table `tab` (count entries, tiles numbered consecutively, `total`
 // tiles), all with tile size (ti, tj) and `overlap`: one persistent launch.
-// `maps` (device, may be NULL): the tensor maps of every instance, filled by
-// ras_batched_encode; with them the windows are staged by TMA.  `live`
-// (device, may be NULL): tiles of entries whose live[inst] is 0 are skipped.
+// `tmap` (device, may be NULL): the table entry of every tile of the launch
+// (else found by binary search on tile_begin).  `maps` (device, may be
+// NULL): the tensor maps of every instance, filled by ras_batched_encode;
+// with them the windows are staged by TMA.  `live` (device, may be NULL):
+// tiles of entries whose live[inst] is 0 are skipped.
 template <typename T>
-cudaError_t launch_ras_batched(const BatchTiles<T> *tab, const void *maps, int count, int total, int ti, int tj,
-                               int ksweeps, int overlap, T omega, const int *live, const RasRun &run, cudaStream_t s);
+cudaError_t launch_ras_batched(const BatchTiles<T> *tab, const int *tmap, const void *maps, int count, int total,
+                               int ti, int tj, int ksweeps, int overlap, T omega, const int *live, const RasRun &run,
+                               cudaStream_t s);
 // Shared memory one batched launch needs (tile size and overlap only).
 size_t ras_batched_smem_bytes(int ti, int tj, int overlap, size_t elem);
 // Whether a batched launch of this shape can stage windows by TMA, the bytes

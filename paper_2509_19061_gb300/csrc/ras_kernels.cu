@@ -452,11 +452,28 @@ __global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_reg(RasArgs<T> a)
     sweep_and_store<T, R>(a, G, w, c, col, strip, active, pl);
 }
 
+// entry of the launch's table that owns tile t: from the per-tile map when
+// the launch has one, else by binary search on tile_begin
+template <typename T>
+__device__ __forceinline__ int batch_entry(const BatchTiles<T> *__restrict__ tab, const int *__restrict__ tmap,
+                                           int count, int t)
+{
+    if (tmap) return tmap[t];
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab[mid].tile_begin <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // ---------------------------------------------------------------------------
 // batched persistent kernel: the tiles of many instances in one launch
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_batched(const BatchTiles<T> *__restrict__ tab, int count,
+__global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_batched(const BatchTiles<T> *__restrict__ tab,
+                                                                 const int *__restrict__ tmap, int count,
                                                                  int total, const int *__restrict__ live,
                                                                  RasArgs<T> shape)
 {
@@ -469,14 +486,7 @@ __global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_batched(const BatchTile
     zero_borders(G, pl);
     __syncthreads();
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
-        // instance owning tile t: last entry with tile_begin <= t
-        int lo = 0, hi = count - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tab[mid].tile_begin <= t) lo = mid;
-            else hi = mid - 1;
-        }
-        const BatchTiles<T> &e = tab[lo];
+        const BatchTiles<T> &e = tab[batch_entry(tab, tmap, count, t)];
         if (live && !live[e.inst]) continue;
         RasArgs<T> a = shape;
         a.g = e.g;
@@ -506,17 +516,6 @@ __global__ void __launch_bounds__(REG_MAX_THREADS) k_ras_batched(const BatchTile
 // last instance whose tile_begin <= t; instance e's windows are staged
 // through its own tensor maps maps[e] (global memory), the next tile's copy
 // overlapping the current tile's sweeps as in k_ras_tma
-template <typename T>
-__device__ __forceinline__ int batch_entry(const BatchTiles<T> *__restrict__ tab, int count, int t)
-{
-    int lo = 0, hi = count - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (tab[mid].tile_begin <= t) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
 
 template <typename T>
 __device__ __forceinline__ RasArgs<T> batch_args(const RasArgs<T> &shape, const BatchTiles<T> &e)
@@ -534,6 +533,7 @@ __device__ __forceinline__ RasArgs<T> batch_args(const RasArgs<T> &shape, const 
 
 template <typename T, int MAXT, int MINB, int WXM, int NS>
 __global__ void __launch_bounds__(MAXT, MINB) k_ras_batched_tma(const BatchTiles<T> *__restrict__ tab,
+                                                                const int *__restrict__ tmap,
                                                                 const TmaMaps *__restrict__ maps, int count,
                                                                 int total, const int *__restrict__ live,
                                                                 RasArgs<T> shape)
@@ -552,12 +552,52 @@ __global__ void __launch_bounds__(MAXT, MINB) k_ras_batched_tma(const BatchTiles
     const bool active = (int)threadIdx.x < G.wxm * G.strips;
     const uint32_t box_bytes = (uint32_t)(BW * shape.wym * (int)sizeof(T));
 
+    // Each CTA takes chunks of CH consecutive tiles, chunk c, c + gridDim.x,
+    // ...: consecutive tiles mostly belong to one instance, so the cursor
+    // (e, tb, te) = (entry, its first tile, one past its last) usually just
+    // steps on and the instance's arguments are reloaded only when it
+    // changes, while the round-robin over chunks keeps the CTAs balanced when
+    // finished instances drop out.
+    constexpr int CH = 8;
+    const int stride = (int)gridDim.x * CH;
+    auto end_of = [&](int e) { return tab[e].tile_begin + tab[e].tg.ntx * tab[e].tg.nty; };
+    int e = 0, tb = 0, te = 0;
+    auto seek = [&](int t) {
+        if (t < tb || t >= te) {
+            e = batch_entry(tab, tmap, count, t);
+            tb = tab[e].tile_begin;
+            te = end_of(e);
+        }
+    };
+    // this CTA's position after t in its sequence of chunks
+    auto step = [&](int t) { return (t + 1) % CH ? t + 1 : t + 1 - CH + stride; };
+    // first position >= t (in this CTA's sequence) whose instance is live
+    auto advance = [&](int t) {
+        while (t < total) {
+            seek(t);
+            if (live && !live[tab[e].inst]) {
+                // skip the rest of this instance within the chunk
+                const int cend = (t / CH + 1) * CH;
+                t = te < cend ? te : cend - CH + stride;
+                continue;
+            }
+            break;
+        }
+        return t;
+    };
+
+    int ea = -1; // entry whose arguments `a` holds
+    RasArgs<T> a = shape;
     // tensor maps are acquired once per instance by the issuing thread
     int acquired = -1;
-    auto issue = [&](int t) {
-        const int e = batch_entry(tab, count, t);
-        const RasArgs<T> a = batch_args(shape, tab[e]);
-        const Window w = window_of(a, t - tab[e].tile_begin);
+    auto issue = [&](int t, int e, int tb) {
+        Window w;
+        if (e == ea) {
+            w = window_of(a, t - tb);
+        } else {
+            const RasArgs<T> b = batch_args(shape, tab[e]);
+            w = window_of(b, t - tb);
+        }
         const int xs = w.ox0 & ~(ALIGN - 1);
         if (e != acquired) {
 #pragma unroll
@@ -570,21 +610,14 @@ __global__ void __launch_bounds__(MAXT, MINB) k_ras_batched_tma(const BatchTiles
         for (int f = 0; f < NF; ++f) tma_load_2d(stage + f * SP, &maps[e].m[f], xs, w.oy0, &bar);
     };
 
-    // this CTA's next tile from t on (stride gridDim.x) whose instance is live
-    auto next_live = [&](int t) {
-        if (live)
-            while (t < total && !live[tab[batch_entry(tab, count, t)].inst]) t += (int)gridDim.x;
-        return t;
-    };
-
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_proxy_async();
     }
     zero_borders(G, pl);
     __syncthreads();
-    int tile = next_live((int)blockIdx.x);
-    if (threadIdx.x == 0 && tile < total) issue(tile);
+    int tile = advance((int)blockIdx.x * CH);
+    if (threadIdx.x == 0 && tile < total) issue(tile, e, tb);
     uint32_t phase = 0;
     while (tile < total) {
         const bool ok = mbar_wait_bounded(&bar, phase, shape.wait_limit);
@@ -596,16 +629,18 @@ __global__ void __launch_bounds__(MAXT, MINB) k_ras_batched_tma(const BatchTiles
             __syncthreads();
             return;
         }
-        const int e = batch_entry(tab, count, tile);
-        const RasArgs<T> a = batch_args(shape, tab[e]);
-        const Window w = window_of(a, tile - tab[e].tile_begin);
+        if (e != ea) {
+            a = batch_args(shape, tab[e]);
+            ea = e;
+        }
+        const Window w = window_of(a, tile - tb);
         const int dx = w.ox0 - (w.ox0 & ~(ALIGN - 1));
         CellRegs<T, R> c;
         setup_cells<T, R>(a, G, w, c, col, strip, active, pl,
                           [&](int f, int wy, int wx) { return stage[f * SP + wy * BW + wx + dx]; });
         __syncthreads();
-        const int next = next_live(tile + (int)gridDim.x);
-        if (threadIdx.x == 0 && next < total) issue(next);
+        const int next = advance(step(tile));
+        if (threadIdx.x == 0 && next < total) issue(next, e, tb);
         phase ^= 1u;
         sweep_and_store<T, R>(a, G, w, c, col, strip, active, pl);
         tile = next;
@@ -716,18 +751,13 @@ __global__ void __launch_bounds__(RAS_THREADS) k_ras(RasArgs<T> a)
 
 // batched form of the general kernel: one CTA per tile of the launch's list
 template <typename T>
-__global__ void __launch_bounds__(RAS_THREADS) k_ras_batched_smem(const BatchTiles<T> *__restrict__ tab, int count,
+__global__ void __launch_bounds__(RAS_THREADS) k_ras_batched_smem(const BatchTiles<T> *__restrict__ tab,
+                                                                  const int *__restrict__ tmap, int count,
                                                                   const int *__restrict__ live, RasArgs<T> shape)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int t = (int)blockIdx.x;
-    int lo = 0, hi = count - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (tab[mid].tile_begin <= t) lo = mid;
-        else hi = mid - 1;
-    }
-    const BatchTiles<T> &e = tab[lo];
+    const BatchTiles<T> &e = tab[batch_entry(tab, tmap, count, t)];
     if (live && !live[e.inst]) return;
     RasArgs<T> a = shape;
     a.g = e.g;
@@ -851,7 +881,8 @@ void (*pick_tma(const RasPlan &p))(TmaMaps, RasArgs<T>)
 }
 
 template <typename T>
-void (*pick_batched_tma(const RasPlan &p))(const BatchTiles<T> *, const TmaMaps *, int, int, const int *, RasArgs<T>)
+void (*pick_batched_tma(const RasPlan &p))(const BatchTiles<T> *, const int *, const TmaMaps *, int, int, const int *,
+                                           RasArgs<T>)
 {
     if constexpr (sizeof(T) == 4) {
         if (geo_matches<64, 8, T>(p)) return k_ras_batched_tma<T, REG_MAX_THREADS, 1, 64, 8>;
@@ -965,8 +996,9 @@ cudaError_t ras_batched_encode(const BatchTiles<T> *tab, int count, int ti, int 
 }
 
 template <typename T>
-cudaError_t launch_ras_batched(const BatchTiles<T> *tab, const void *maps, int count, int total, int ti, int tj,
-                               int ksweeps, int overlap, T omega, const int *live, const RasRun &run, cudaStream_t s)
+cudaError_t launch_ras_batched(const BatchTiles<T> *tab, const int *tmap, const void *maps, int count, int total,
+                               int ti, int tj, int ksweeps, int overlap, T omega, const int *live, const RasRun &run,
+                               cudaStream_t s)
 {
     // launch shape sized for the largest window (tile ti x tj grown by the
     // overlap): TMA staging through per-instance tensor maps when `maps` is
@@ -992,7 +1024,7 @@ cudaError_t launch_ras_batched(const BatchTiles<T> *tab, const void *maps, int c
     if (total <= 0) return cudaSuccess;
     cudaError_t e;
     if (p.kind == PLAN_TMA) {
-        void (*kern)(const BatchTiles<T> *, const TmaMaps *, int, int, const int *, RasArgs<T>) =
+        void (*kern)(const BatchTiles<T> *, const int *, const TmaMaps *, int, int, const int *, RasArgs<T>) =
             pick_batched_tma<T>(p);
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
         if (e != cudaSuccess) return e;
@@ -1000,13 +1032,14 @@ cudaError_t launch_ras_batched(const BatchTiles<T> *tab, const void *maps, int c
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, p.threads, p.smem);
         if (e != cudaSuccess) return e;
         const int grid = std::min(total, std::max(per_sm, 1) * sm_count());
-        kern<<<grid, p.threads, p.smem, s>>>(tab, reinterpret_cast<const TmaMaps *>(maps), count, total, live, a);
+        kern<<<grid, p.threads, p.smem, s>>>(tab, tmap, reinterpret_cast<const TmaMaps *>(maps), count, total, live,
+                                             a);
         return cudaGetLastError();
     }
     if (p.kind == PLAN_SMEM) {
         e = cudaFuncSetAttribute(k_ras_batched_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
         if (e != cudaSuccess) return e;
-        k_ras_batched_smem<T><<<total, RAS_THREADS, p.smem, s>>>(tab, count, live, a);
+        k_ras_batched_smem<T><<<total, RAS_THREADS, p.smem, s>>>(tab, tmap, count, live, a);
         return cudaGetLastError();
     }
     e = cudaFuncSetAttribute(k_ras_batched<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
@@ -1015,14 +1048,14 @@ cudaError_t launch_ras_batched(const BatchTiles<T> *tab, const void *maps, int c
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ras_batched<T>, p.threads, p.smem);
     if (e != cudaSuccess) return e;
     const int grid = std::min(total, std::max(per_sm, 1) * sm_count());
-    k_ras_batched<T><<<grid, p.threads, p.smem, s>>>(tab, count, total, live, a);
+    k_ras_batched<T><<<grid, p.threads, p.smem, s>>>(tab, tmap, count, total, live, a);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_ras_batched<float>(const BatchTiles<float> *, const void *, int, int, int, int, int,
-                                               int, float, const int *, const RasRun &, cudaStream_t);
-template cudaError_t launch_ras_batched<double>(const BatchTiles<double> *, const void *, int, int, int, int, int,
-                                                int, double, const int *, const RasRun &, cudaStream_t);
+template cudaError_t launch_ras_batched<float>(const BatchTiles<float> *, const int *, const void *, int, int, int,
+                                               int, int, int, float, const int *, const RasRun &, cudaStream_t);
+template cudaError_t launch_ras_batched<double>(const BatchTiles<double> *, const int *, const void *, int, int, int,
+                                                int, int, int, double, const int *, const RasRun &, cudaStream_t);
 template cudaError_t ras_batched_encode<float>(const BatchTiles<float> *, int, int, int, int, void *);
 template cudaError_t ras_batched_encode<double>(const BatchTiles<double> *, int, int, int, int, void *);
 
