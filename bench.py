@@ -207,6 +207,25 @@ def workload_config(args):
             "step": "b = f - G p, %d RAS sweeps, energy norm" % args.sweeps}
 
 
+def max_over_ranks(x, world, device):
+    """The largest x over all ranks, returned on every rank (x itself when
+    world == 1).  NCCL on the GPU machine; the CPU tests use gloo."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, cells, sweeps, steps, ms_total):
+    """Whole-job Gcell-updates/s: every rank smooths its own replica of the
+    workload, so the job processes world x cells x sweeps x steps updates in
+    the slowest rank's time."""
+    return world * cells * sweeps * steps / (ms_total / 1e3) / 1e9
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -255,16 +274,12 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
     barrier()
-    ms_total = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     prof = ctx.profile()
     launches = sum(v[0] for v in prof.values())
     ras_launches, ras_groups, ras_ms = prof["ras"]
     ms_step = ms_total / args.steps
-    value = world * cells * args.sweeps * args.steps / (ms_total / 1e3) / 1e9
+    value = job_value(world, cells, args.sweeps, args.steps, ms_total)
 
     # roofline of the dominant kernel (the RAS tile kernel): algorithmic bytes
     # = 8 words per cell per sweep, k sweeps per launch
@@ -289,17 +304,22 @@ def run_ours(args):
             "gpu_launches": launches, "roofline": roofline, "clocks": clk.summary(),
             "energy_residual_after_step": (energy[0] / energy[2]) ** 0.5}
 
-    if not args.no_extras and rank == 0:
-        line["e2e"] = e2e_measure(args, ctx, prob, stream, world)
+    if not args.no_extras:
+        # every rank runs the end-to-end step (slowest rank's time counts)
+        e2e = e2e_measure(args, ctx, prob, stream, world, barrier)
+        if rank == 0:
+            line["e2e"] = e2e
+    # the single-GPU tables (variants, solves, batched workload, tuning, CPU
+    # baseline) run at N = 1 only: at N > 1 they would hold every GPU while
+    # rank 0 alone works
+    if not args.no_extras and world == 1:
         line["variants"] = variant_table(args, api, prob)
         line["c2_f64_1024"] = c2_table(args, api)
         line["time_to_1e-8"] = solve_times(args, api)
         if args.batch > 0:
             line["batched"] = batch_leg(args, api)
         line["autotune"] = autotune_leg(args, api)
-        if world == 1:
-            line["cpu_baseline"] = {kk: vv for kk, vv in cpu_sample(args, args.cpu_seconds).items()
-                                    if kk != "seconds"}
+        line["cpu_baseline"] = {kk: vv for kk, vv in cpu_sample(args, args.cpu_seconds).items() if kk != "seconds"}
     ctx.close()
     if rank == 0:
         print(json.dumps(line))
@@ -308,7 +328,7 @@ def run_ours(args):
     return 0
 
 
-def e2e_measure(args, ctx, prob, stream, world):
+def e2e_measure(args, ctx, prob, stream, world, barrier=lambda: None):
     """Same step through the public API with host buffers: every step copies
     all of its inputs (eta_c, eta_n, fx, fy, initial vx, vy) from pinned host
     memory to the device, runs set_viscosity, set_rhs, smooth and the energy
@@ -367,9 +387,10 @@ def e2e_measure(args, ctx, prob, stream, world):
         torch.cuda.synchronize()
 
     run(2)
+    barrier()
     t0 = time.perf_counter()
     run(steps)
-    dt = time.perf_counter() - t0
+    dt = max_over_ranks(time.perf_counter() - t0, world, "cuda")
     h2d_bytes = sum(t.numel() * t.element_size() for t in host.values())
     d2h_bytes = outs[0][0].numel() * outs[0][0].element_size() * 2 + 24
     return {"value": world * args.n * args.n * args.sweeps * steps / dt / 1e9, "unit": UNIT,
