@@ -34,6 +34,11 @@ METRIC = "RAS-Jacobi Gcell-updates/s + % HBM peak; time to 1e-8 residual FP32 vs
 UNIT = "Gcell-updates/s"
 WORDS_PER_CELL_SWEEP = 8  # read vx, vy, eta_c, eta_n, bx, by; write vx, vy
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0
+# FP32 tile-kernel arithmetic per cell-sweep (an FMA counts 2): fluxes
+# sigma'xx, sigma'yy (2 + 2), the node shear (6) scaled twice (2), M v in x
+# and y (3 + 3), the two damped updates (3 + 3)
+FLOPS_PER_CELL_SWEEP = 24
 RAS_SOURCES = ["paper_2509_19061_gb300/csrc/ras_kernels.cu", "paper_2509_19061_gb300/csrc/stencil.cuh"]
 
 
@@ -53,6 +58,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--solve-n", type=int, default=4096, help="grid of the time-to-1e-8 solve")
     ap.add_argument("--batch", type=int, default=256, help="instances of the batched workload (0: skip)")
+    ap.add_argument("--c2-sweeps", type=int, default=100, help="sweeps per smoother in the 1024^2 FP64 table")
     ap.add_argument("--only", choices=["solve", "batch", "autotune", "c2"],
                     help="run one extra leg alone and print its JSON (for profiling it)")
     return ap.parse_args()
@@ -148,6 +154,20 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle sample (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
+def host_cpu():
+    """CPU model and core count of this host (lscpu / nproc equivalents)."""
+    model = "unknown"
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"model": model, "nproc": os.cpu_count()}
+
+
 def cpu_sample(args, target_s):
     """Time the FP64 oracle's RAS-Jacobi on the same workload generator at
     1024^2 (same tiles, k, overlap, shifts) for about target_s seconds."""
@@ -168,6 +188,7 @@ def cpu_sample(args, target_s):
     ora.ras(g, bx, by, 0.3, sweeps, args.tile[0], args.tile[1], k, o, shift_mode=1, seed=1)
     dt = time.perf_counter() - t0
     return {"value": n * n * sweeps / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "host": host_cpu(),
             "sample": "FP64 C oracle, single thread, layered sinker %dx%d (same generator, seed 4), RAS %dx%d "
                       "tiles k=%d overlap=%d, %d sweeps in %.1f s" % (n, n, args.tile[0], args.tile[1], k, o,
                                                                       sweeps, dt),
@@ -294,6 +315,10 @@ def run_ours(args):
                 peak_kind == "measured" else "fallback 6800 GB/s",
                 "kernel": "k_ras", "kernel_avg_ms": avg_ms, "kernel_share": ras_ms / ms_total,
                 "algorithmic_bytes_per_launch": per_launch_bytes,
+                "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
+                "dram_bytes_per_cell_sweep": None if traffic is None else traffic / (cells * k),
+                "flops_per_cell_update": FLOPS_PER_CELL_SWEEP,
+                "achieved_tflops": FLOPS_PER_CELL_SWEEP * cells * k / (avg_ms / 1e3) / 1e12,
                 "note": "effective bytes: 8 words/cell/sweep x k sweeps per launch; with k > 1 the tile is "
                         "read from HBM once per k sweeps, so frac may exceed 1 (temporal blocking)"}
 
@@ -623,7 +648,7 @@ def variant_table(args, api, prob):
 
 def c2_table(args, api):
     """The 1024^2 sinker at contrast 1e4 in FP64: all five smoothers, 100
-    sweeps each, RAS with tiles 16^2, 32^2, 64 x 32 and k in {1, 2, 4, 8}
+    sweeps each (--c2-sweeps), RAS with tiles 16^2, 32^2, 64 x 32 and k in {1, 2, 4, 8}
     (overlap k-1).  The FP64 working set (8 fields x 8.4 MB) fits in the
     129 MB L2, so these rates are L2-, not HBM-bound."""
     from paper_2509_19061_gb300 import inputs
@@ -632,11 +657,12 @@ def c2_table(args, api):
     c = api.StokesContext(n, n, 1.0, 1.0, "f64")
     c.set_problem(prob)
     vx, vy = c.field(), c.field()
-    cases = [dict(variant=v, sweeps=100) for v in ("jacobi", "fused", "rbgs")]
-    cases.append(dict(variant="blocked", sweeps=100, tile=(32, 32)))
+    sw = args.c2_sweeps
+    cases = [dict(variant=v, sweeps=sw) for v in ("jacobi", "fused", "rbgs")]
+    cases.append(dict(variant="blocked", sweeps=sw, tile=(32, 32)))
     for tile in ((16, 16), (32, 32), (64, 32)):
         for k in (1, 2, 4, 8):
-            cases.append(dict(variant="ras", sweeps=100, tile=tile, k=k, overlap=k - 1))
+            cases.append(dict(variant="ras", sweeps=sw, tile=tile, k=k, overlap=k - 1))
     out = {}
     for kw in cases:
         label = kw["variant"]
@@ -652,7 +678,7 @@ def c2_table(args, api):
             continue
         cu = n * n * kw["sweeps"] / (ms / 1e3)
         out[label] = {"gcell_updates_per_s": cu / 1e9, "effective_gbs": cu * WORDS_PER_CELL_SWEEP * 8 / 1e9,
-                      "ms_per_100_sweeps": ms}
+                      "ms_per_call": ms, "sweeps": sw}
     c.close()
     return {"workload": "sinker_1024x1024_contrast1e4_f64", "table": out}
 
