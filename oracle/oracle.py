@@ -285,3 +285,77 @@ def mg_fcg(g: Grid, fx, fy, p, mg: MG, tol, max_its, vx=None, vy=None):
     if c < 0:
         raise ValueError("ora_mg_fcg failed")
     return vx, vy, c, fe.value, hist[:c + 1].copy()
+
+
+# ---------------------------------------------------------------------------
+# inexact Uzawa iteration around the multigrid velocity solve (Sec. 3.1-3.2;
+# solver configuration of Sec. 6.2)
+# ---------------------------------------------------------------------------
+def eta_min(eta_c, eta_n):
+    """Smallest viscosity of the domain (Sec. 6.2): over the cells and the
+    interior nodes (boundary nodes carry no shear stress and are ignored by
+    the operator)."""
+    return float(min(np.min(eta_c), np.min(np.asarray(eta_n)[1:-1, 1:-1])))
+
+
+def blend_eta(eta_c, eta_n, theta, emin):
+    """Viscosity continuation of Sec. 6.2: eta_comp = (1 - theta) eta_min +
+    theta eta, at the cells and at the nodes."""
+    return (1.0 - theta) * emin + theta * _f64(eta_c), (1.0 - theta) * emin + theta * _f64(eta_n)
+
+
+def continuation_theta(cycle, interval, stages):
+    """theta of Uzawa cycle `cycle` (from 0): 0, 1/(stages-1), ..., 1, one
+    stage per `interval` cycles (Sec. 6.2: 0, 0.25, ..., 1 every 25 cycles);
+    interval 0 means no continuation (theta = 1)."""
+    if interval <= 0 or stages <= 1:
+        return 1.0
+    return min(cycle // interval, stages - 1) / (stages - 1)
+
+
+def lithostatic(g: Grid, fy):
+    """Initial pressure of Sec. 6.2, p = integral of rho g_y dy from the bottom,
+    written discretely at the cell centres as p[0][i] = 0 and
+    p[j][i] = p[j-1][i] + hy rho g_y at the vy face between them, with
+    rho g_y = -f_y (reading: so that G p balances f_y exactly at every interior
+    vy face), then shifted to zero mean."""
+    fy = _f64(fy)
+    p = np.zeros((g.ny, g.nx))
+    for j in range(1, g.ny):
+        p[j] = p[j - 1] - g.hy * fy[j]
+    return p - p.mean()
+
+
+def uzawa(g: Grid, fx, fy, mg: MG, cycles, omega_p=0.6, theta_interval=25, theta_stages=5, krylov=True, vel_its=1,
+          p=None, vx=None, vy=None):
+    """Inexact Uzawa iteration (Sec. 3.1-3.2, configuration of Sec. 6.2).
+
+    Each cycle: the momentum solve M_theta v = f - G p from the current v
+    (viscosity eta_theta of the continuation stage), with `vel_its`
+    applications of the V-cycle: flexible-CG iterations preconditioned by it
+    (krylov, the default: its first step is preconditioned steepest descent,
+    which stays stable where the V-cycle is not a convergent splitting at
+    high contrast) or defect-correction cycles (the paper's "single
+    multigrid iteration" taken literally); the pressure update
+    p <- p - omega_p eta_c,theta D v
+    (reading: the paper's p + alpha eta D v with D taken with the sign that
+    makes D M^-1 G positive, M being negative definite in the sign
+    convention of Eq. (1)-(3); here D is the divergence); the pressure is
+    shifted to zero mean (Sec. 6.2).  After every cycle the relative energy
+    residual of Sec. 6.4 (velocity and pressure parts, true viscosity) is
+    recorded.  Returns (vx, vy, p, history)."""
+    vx = g.zeros_vx() if vx is None else _f64(vx).copy()
+    vy = g.zeros_vy() if vy is None else _f64(vy).copy()
+    p = lithostatic(g, fy) if p is None else _f64(p).copy()
+    emin = eta_min(g.eta_c, g.eta_n)
+    hist = []
+    for c in range(cycles):
+        theta = continuation_theta(c, theta_interval, theta_stages)
+        ec, en = blend_eta(g.eta_c, g.eta_n, theta, emin)
+        gc = Grid(g.nx, g.ny, g.hx, g.hy, ec, en)
+        vx, vy, _, _, _ = (mg_fcg if krylov else mg_solve)(gc, fx, fy, p, mg, 0.0, vel_its, vx, vy)
+        p = p - omega_p * ec * apply_D(g, vx, vy)
+        p = p - p.mean()
+        rv, rp, ff = energy(g, fx, fy, p, vx, vy)
+        hist.append(float(np.sqrt((rv + rp) / ff)))
+    return vx, vy, p, np.array(hist)

@@ -564,3 +564,126 @@ def test_flexible_cg_reaches_1e8_and_the_dense_solution(ora):
     # the dense factorisation itself carries cond(M) * eps ~ 1e-8 of error here
     np.testing.assert_allclose(vx, dx, atol=1e-7 * np.abs(dx).max())
     np.testing.assert_allclose(vy, dy, atol=1e-7 * np.abs(dy).max())
+
+
+# ---------------------------------------------------------------------------
+# inexact Uzawa iteration (Sec. 3.1-3.2, configuration of Sec. 6.2)
+# ---------------------------------------------------------------------------
+def saddle_point_solution(ora, g, fx, fy):
+    """Direct solution of [M G; D 0] [v; p] = [f; 0] with zero-mean p, from the
+    dense matrices of the oracle's M, G and D (columns by unit vectors) and
+    a least-squares solve of the system augmented by the mean constraint."""
+    mx, my = unknown_masks(g.nx, g.ny)
+    ux = [(j, i) for j in range(g.ny) for i in range(g.nx + 1) if mx[j, i]]
+    uy = [(j, i) for j in range(g.ny + 1) for i in range(g.nx) if my[j, i]]
+    cells = [(j, i) for j in range(g.ny) for i in range(g.nx)]
+    nu, nc = len(ux) + len(uy), len(cells)
+
+    def vec_of(vx, vy):
+        return np.concatenate([[vx[a] for a in ux], [vy[a] for a in uy]])
+
+    K = np.zeros((nu + nc + 1, nu + nc))
+    for c in range(nu):
+        vx, vy = g.zeros_vx(), g.zeros_vy()
+        if c < len(ux):
+            vx[ux[c]] = 1.0
+        else:
+            vy[uy[c - len(ux)]] = 1.0
+        K[:nu, c] = vec_of(*ora.apply_M(g, vx, vy))
+        K[nu:nu + nc, c] = ora.apply_D(g, vx, vy).ravel()
+    for c in range(nc):
+        p = np.zeros((g.ny, g.nx))
+        p[cells[c]] = 1.0
+        K[:nu, nu + c] = vec_of(*ora.apply_G(g, p))
+    K[nu + nc, nu:] = 1.0
+    rhs = np.concatenate([vec_of(fx, fy), np.zeros(nc + 1)])
+    sol = np.linalg.lstsq(K, rhs, rcond=None)[0]
+    vx, vy = g.zeros_vx(), g.zeros_vy()
+    for c, a in enumerate(ux):
+        vx[a] = sol[c]
+    for c, a in enumerate(uy):
+        vy[a] = sol[len(ux) + c]
+    return vx, vy, sol[nu:].reshape(g.ny, g.nx)
+
+
+def test_lithostatic_pressure_balances_gravity(ora):
+    """G p_litho = f_y at every interior vy face for any f_y, and zero mean."""
+    g = rand_grid(ora, 11, 9, 21)
+    fy = np.random.default_rng(3).standard_normal((10, 11))
+    p = ora.lithostatic(g, fy)
+    assert abs(p.mean()) <= 1e-14
+    gx, gy = ora.apply_G(g, p)
+    np.testing.assert_allclose(gy[1:-1, :], fy[1:-1, :], rtol=1e-12, atol=1e-12)
+
+
+def test_uzawa_hydrostatic_state_is_a_fixed_point(ora):
+    """Uniform density: v = 0 with the lithostatic pressure solves the Stokes
+    system exactly, whatever the viscosity, so Uzawa stays there."""
+    g = rand_grid(ora, 32, 32, 22)
+    fx = np.zeros((32, 33))
+    fy = np.ones((33, 32))  # rho g_y = -1 everywhere
+    vx, vy, p, hist = ora.uzawa(g, fx, fy, ora.MG(variant=4, ti=8, tj=8, k=2, overlap=1), 3, theta_interval=0)
+    assert np.all(vx == 0.0) and np.all(vy == 0.0)
+    np.testing.assert_allclose(p, ora.lithostatic(g, fy), rtol=0, atol=1e-13)
+    assert np.all(hist <= 1e-12)
+
+
+def test_uzawa_converges_to_the_saddle_point_solution(ora):
+    """With an exact velocity solve (one level: the dense solve) the Uzawa
+    fixed point is the solution of the full discrete Stokes system."""
+    nx, ny = 12, 10
+    ec, en = inputs.random_viscosity(nx, ny, 23, (0.0, 1.0))
+    g = ora.Grid(nx, ny, 1.0 / nx, 1.0 / ny, ec, en)
+    prob = inputs.sinker_problem(nx, ny, eta_in=10.0, ly=1.0)
+    fx, fy = prob.fx, prob.fy
+    vx, vy, p, hist = ora.uzawa(g, fx, fy, ora.MG(max_levels=1, variant=1), 600, theta_interval=0)
+    sx, sy, sp = saddle_point_solution(ora, g, fx, fy)
+    scale = max(np.abs(sx).max(), np.abs(sy).max())
+    np.testing.assert_allclose(vx, sx, atol=1e-8 * scale)
+    np.testing.assert_allclose(vy, sy, atol=1e-8 * scale)
+    np.testing.assert_allclose(p, sp, atol=1e-8 * np.abs(sp).max())
+    assert hist[-1] <= 1e-8
+
+
+def test_uzawa_pressure_sign_reading(ora):
+    """The update p <- p - omega_p eta D v contracts; the opposite sign (planted
+    here as a negative omega_p) makes the same iteration diverge."""
+    nx, ny = 12, 10
+    g = rand_grid(ora, nx, ny, 24, rng=(0.0, 1.0))
+    prob = inputs.sinker_problem(nx, ny, eta_in=10.0, ly=1.0)
+    mg = ora.MG(max_levels=1, variant=1)
+    good = ora.uzawa(g, prob.fx, prob.fy, mg, 40, theta_interval=0)[3]
+    bad = ora.uzawa(g, prob.fx, prob.fy, mg, 40, omega_p=-0.6, theta_interval=0)[3]
+    assert good[-1] < 1e-2 * good[0]
+    assert bad[-1] > 10.0 * bad[0]
+
+
+def test_continuation_schedule_and_blend(ora):
+    th = [ora.continuation_theta(c, 25, 5) for c in (0, 24, 25, 49, 50, 75, 99, 100, 400)]
+    assert th == [0.0, 0.0, 0.25, 0.25, 0.5, 0.75, 0.75, 1.0, 1.0]
+    assert ora.continuation_theta(3, 0, 5) == 1.0
+    ec, en = inputs.random_viscosity(6, 5, 25, (-3.0, 3.0))
+    emin = ora.eta_min(ec, en)
+    assert emin == min(ec.min(), en[1:-1, 1:-1].min())
+    c0, n0 = ora.blend_eta(ec, en, 0.0, emin)
+    assert np.all(c0 == emin) and np.all(n0 == emin)
+    c1, n1 = ora.blend_eta(ec, en, 1.0, emin)
+    assert np.array_equal(c1, ec) and np.array_equal(n1, en)
+
+
+def test_uzawa_with_vcycles_and_continuation_on_the_sinker(ora):
+    """The configuration of Sec. 6.2 (one V-cycle per Uzawa cycle, RAS 8 x 8
+    smoother, continuation in five stages) drives the full energy residual
+    of the 1e4-contrast sinker down by orders of magnitude when the V-cycle
+    preconditions a CG step; used as a defect-correction cycle, the same
+    V-cycle is not a convergent splitting at this contrast (rediscretised
+    coarse levels) and the iteration diverges, which is why CG is the
+    default velocity step."""
+    prob = inputs.sinker_problem(32, eta_in=1e4)
+    g = grid_from(ora, prob)
+    mg = ora.MG(variant=4, ti=8, tj=8, k=4, overlap=3, seed=1)
+    vx, vy, p, hist = ora.uzawa(g, prob.fx, prob.fy, mg, 150, theta_interval=10)
+    assert hist[-1] <= 1e-3 * hist[:20].max()
+    assert abs(p.mean()) <= 1e-12 * np.abs(p).max()
+    vx2, vy2, p2, hist2 = ora.uzawa(g, prob.fx, prob.fy, mg, 40, theta_interval=0, krylov=False)
+    assert hist2[-1] > 1e3 * hist2[0]
