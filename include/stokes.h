@@ -211,6 +211,51 @@ int stokes_residual_energy_norm(stokes_ctx *ctx, const void *vx, const void *vy,
 int stokes_vcycle(stokes_ctx *ctx, void *vx, void *vy, const void *p, const stokes_mg_params *params,
                   double *final_rel_resid, int *cycles);
 
+/* Parameters of the inexact Uzawa iteration (Sec. 3.1-3.2; solver
+ * configuration of Sec. 6.2).
+ * mg              the velocity step of every Uzawa cycle: mg.max_cycles (>= 1)
+ *                 applications of the V-cycle, as flexible-CG iterations
+ *                 (mg.krylov = 1, which stays stable where the V-cycle is not a
+ *                 convergent splitting at high viscosity contrast) or as
+ *                 defect-correction cycles (mg.krylov = 0, the paper's "one
+ *                 multigrid iteration per Uzawa cycle" taken literally);
+ *                 mg.tol is ignored.
+ * omega_p         pressure relaxation (0.6 in Sec. 6.3): p <- p - omega_p eta_c D v,
+ *                 with the cell viscosity as the approximate inverse Schur
+ *                 complement and D the divergence; p is then shifted to zero mean.
+ * cycles          maximum number of Uzawa cycles.
+ * theta_interval, theta_stages   viscosity continuation (Sec. 6.2): cycle n uses
+ *                 eta_theta = (1 - theta) eta_min + theta eta with
+ *                 theta = min(n / theta_interval, theta_stages - 1) / (theta_stages - 1)
+ *                 (25 and 5 in the paper); theta_interval = 0 turns it off.
+ *                 eta_min is the smallest viscosity over the cells and the
+ *                 interior nodes.  The context's viscosity is restored on return.
+ * tol             stop once the relative energy residual (velocity and pressure
+ *                 parts of Sec. 6.4, the caller's viscosity) is <= tol; 0 runs
+ *                 every cycle.
+ * lithostatic_init  1: start from the lithostatic pressure of f (p[0][i] = 0,
+ *                 p[j][i] = p[j-1][i] - hy fy[j][i], zero mean), overwriting p;
+ *                 0: start from the caller's p. */
+typedef struct {
+    stokes_mg_params mg;
+    double omega_p;
+    int cycles;
+    int theta_interval, theta_stages;
+    double tol;
+    int lithostatic_init;
+} stokes_uzawa_params;
+
+/* Solve the Stokes system M v + G p = f, D v = 0 (Eq. (6) and Eq. (4)) by the
+ * inexact Uzawa iteration of `params`, improving (vx, vy, p) in place (device
+ * buffers in the context's layout; p must hold an initial pressure unless
+ * lithostatic_init).  history (host, may be NULL) receives the relative energy
+ * residual after every cycle (params->cycles entries at most); *cycles the
+ * number of cycles run and *final_rel_resid the last residual (either may be
+ * NULL).  Returns STOKES_ERR_NOT_CONVERGED when tol > 0 was not reached,
+ * STOKES_ERR_DIVERGED on NaN/Inf.  Synchronises after every cycle. */
+int stokes_uzawa(stokes_ctx *ctx, void *vx, void *vy, void *p, const stokes_uzawa_params *params, double *history,
+                 int *cycles, double *final_rel_resid);
+
 /* Context options (stokes_set_option). */
 typedef enum {
     STOKES_OPT_USE_TMA = 0,          /* 1 (default): the tile smoothers stage windows with TMA bulk

@@ -60,6 +60,12 @@ class stokes_mg_params(ctypes.Structure):
                 ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int)]
 
 
+class stokes_uzawa_params(ctypes.Structure):
+    _fields_ = [("mg", stokes_mg_params), ("omega_p", ctypes.c_double), ("cycles", ctypes.c_int),
+                ("theta_interval", ctypes.c_int), ("theta_stages", ctypes.c_int), ("tol", ctypes.c_double),
+                ("lithostatic_init", ctypes.c_int)]
+
+
 _VP, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
 _SIGS = {
     "stokes_create": (_I, [_I, _I, _D, _D, _I, _VP, ctypes.POINTER(_VP)]),
@@ -72,6 +78,8 @@ _SIGS = {
     "stokes_residual_energy_norm": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(_D)]),
     "stokes_vcycle": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(stokes_mg_params), ctypes.POINTER(_D),
                            ctypes.POINTER(_I)]),
+    "stokes_uzawa": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(stokes_uzawa_params), ctypes.POINTER(_D),
+                          ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "stokes_set_option": (_I, [_VP, _I, ctypes.c_longlong]),
     "stokes_synchronize": (_I, [_VP]),
     "stokes_profile_reset": (_I, [_VP, _I]),
@@ -208,6 +216,26 @@ def stokes_vcycle(ctx, vx, vy, p, params):
     if st not in (STOKES_OK, STOKES_ERR_NOT_CONVERGED):
         raise StokesError(st, "stokes_vcycle")
     return st, fr.value, cy.value
+
+
+def uzawa_params(cycles=100, omega_p=0.6, theta_interval=25, theta_stages=5, tol=0.0, lithostatic_init=True,
+                 vel_its=1, **mg):
+    """Build a stokes_uzawa_params (Sec. 6.2 defaults: omega_p 0.6, continuation
+    in 5 stages of 25 cycles); vel_its V-cycles (CG iterations) per cycle."""
+    m = mg_params(max_cycles=vel_its, **mg)
+    return stokes_uzawa_params(m, omega_p, cycles, theta_interval, theta_stages, tol, 1 if lithostatic_init else 0)
+
+
+def stokes_uzawa(ctx, vx, vy, p, params):
+    """Returns (status, history, cycles, final E); raises on errors other than
+    STOKES_ERR_NOT_CONVERGED."""
+    hist = (_D * max(params.cycles, 1))()
+    cy, fe = _I(0), _D(0.0)
+    st = _lib().stokes_uzawa(ctx, _ptr(vx), _ptr(vy), _ptr(p), ctypes.byref(params), hist, ctypes.byref(cy),
+                             ctypes.byref(fe))
+    if st not in (STOKES_OK, STOKES_ERR_NOT_CONVERGED):
+        raise StokesError(st, "stokes_uzawa")
+    return st, np.array(hist[:cy.value]), cy.value, fe.value
 
 
 def stokes_set_option(ctx, option, value):
@@ -398,6 +426,10 @@ class StokesContext:
     def vcycle(self, vx, vy, p=None, **kw):
         """Defect-correction multigrid solve; returns (status, E_v, cycles)."""
         return stokes_vcycle(self.ctx, vx, vy, p, mg_params(**kw))
+
+    def uzawa(self, vx, vy, p, **kw):
+        """Inexact Uzawa solve; returns (status, history, cycles, final E)."""
+        return stokes_uzawa(self.ctx, vx, vy, p, uzawa_params(**kw))
 
     def profile_reset(self, timing=False):
         stokes_profile_reset(self.ctx, timing)

@@ -153,6 +153,21 @@ int cuda_fail(cudaError_t e, const char *where);
 // seeded with `seed`.
 uint64_t splitmix64(uint64_t seed, uint64_t c);
 
+// ---- inexact Uzawa iteration (uzawa.cu) ------------------------------------
+// `partials` holds uzawa_partials() doubles; results land in device doubles.
+int uzawa_partials();
+template <typename T> // *out = min over cells and interior nodes
+cudaError_t uz_eta_min(const GridDesc<T> &g, const T *ec, const T *en, double *partials, double *out, cudaStream_t s);
+template <typename T> // continuation blend from the base viscosity (boundary nodes of on stay 0)
+cudaError_t uz_blend(const GridDesc<T> &g, double theta, const double *emin, const T *bc, const T *bn, T *oc, T *on,
+                     cudaStream_t s);
+template <typename T> // p <- p - omega_p eta_c D v, then zero mean (*sum: the sum before the shift)
+cudaError_t uz_pressure_update(const GridDesc<T> &g, double omega_p, const T *ec, const T *vx, const T *vy, T *p,
+                               double *partials, double *sum, cudaStream_t s);
+template <typename T> // lithostatic pressure of f_y, zero mean
+cudaError_t uz_lithostatic(const GridDesc<T> &g, double hy, const T *fy, T *p, double *partials, double *sum,
+                           cudaStream_t s);
+
 // ---- smoother schedules (smooth.cu) ---------------------------------------
 // Where kernel launches go: counts (and, for a context with timing on, times)
 // each launch group of `nk` kernels of class `kind` (stokes_kernel_class).

@@ -3,6 +3,7 @@
 // outer iterations with their tile shifts, ping-pong buffers) and the energy
 // norm.  Every arithmetic step runs in the kernels of stencil_kernels.cu and
 // ras_kernels.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -66,7 +67,9 @@ struct stokes_ctx {
     cudaStream_t stream;
     void *eta_c = nullptr, *eta_n = nullptr, *fx = nullptr, *fy = nullptr;
     void *bx = nullptr, *by = nullptr, *sx = nullptr, *sy = nullptr;
-    void *ivx = nullptr, *ivy = nullptr; // 1/diag(M) (FP64 contexts: the FP64 pipe is the bottleneck)
+    void *ivx = nullptr, *ivy = nullptr; // 1/diag(M), read by the tile kernels and the energy sums
+    void *eta_c0 = nullptr, *eta_n0 = nullptr; // the caller's viscosity during a continuation
+    double *uz_partials = nullptr, *uz_scal = nullptr; // Uzawa reductions; uz_scal: [eta_min, sum]
     double *partials = nullptr, *dsum = nullptr, *hsum = nullptr;
     bool have_eta = false, have_f = false;
     int *dstatus = nullptr;              // device status word of the bounded waits
@@ -463,6 +466,109 @@ int vcycle_impl(stokes_ctx *c, T *vx, T *vy, const T *p, const stokes_mg_params 
     return verdict < 0 ? verdict : STOKES_OK;
 }
 
+// swap in the viscosity of continuation stage theta (from the saved base)
+template <typename T>
+int set_stage(stokes_ctx *c, double theta)
+{
+    const GridDesc<T> g = grid_of<T>(c);
+    RUN(STOKES_K_COPY, 1,
+        uz_blend<T>(g, theta, c->uz_scal, (const T *)c->eta_c0, (const T *)c->eta_n0, (T *)c->eta_c, (T *)c->eta_n,
+                    c->stream));
+    RUN(STOKES_K_COPY, 1,
+        launch_inv_diag<T>(g, (const T *)c->eta_c, (const T *)c->eta_n, (T *)c->ivx, (T *)c->ivy, c->stream));
+    mg_invalidate(c->mg);
+    if (c->gexec) { // the graph holds the old hierarchy's buffers
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return STOKES_OK;
+}
+
+// Inexact Uzawa iteration (Sec. 3.1-3.2, configuration of Sec. 6.2).
+template <typename T>
+int uzawa_impl(stokes_ctx *c, T *vx, T *vy, T *p, const stokes_uzawa_params *u, double *hist, int *cycles,
+               double *final_e)
+{
+    const GridDesc<T> g = grid_of<T>(c);
+    if (!c->uz_partials) {
+        CK(cudaMalloc(&c->uz_partials, (size_t)uzawa_partials() * sizeof(double)));
+        CK(cudaMalloc(&c->uz_scal, 2 * sizeof(double)));
+    }
+    if (u->lithostatic_init)
+        RUN(STOKES_K_RHS, 4,
+            uz_lithostatic<T>(g, c->hy, (const T *)c->fy, p, c->uz_partials, c->uz_scal + 1, c->stream));
+    const bool cont = u->theta_interval > 0 && u->theta_stages > 1;
+    if (cont) {
+        if (!c->eta_c0) {
+            int st = alloc_field(c, &c->eta_c0);
+            if (st == STOKES_OK) st = alloc_field(c, &c->eta_n0);
+            if (st != STOKES_OK) return st;
+        }
+        CK(cudaMemcpyAsync(c->eta_c0, c->eta_c, c->elems * c->esize, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->eta_n0, c->eta_n, c->elems * c->esize, cudaMemcpyDeviceToDevice, c->stream));
+        RUN(STOKES_K_COPY, 2,
+            uz_eta_min<T>(g, (const T *)c->eta_c, (const T *)c->eta_n, c->uz_partials, c->uz_scal, c->stream));
+    }
+    stokes_mg_params mp = u->mg;
+    mp.tol = 0.0; // the velocity step always runs its mg.max_cycles V-cycles (unless the residual is 0)
+    int stage = -1, st = STOKES_OK, n = 0;
+    double e = 0.0;
+    for (; n < u->cycles; ++n) {
+        double theta = 1.0;
+        if (cont) {
+            const int sg = std::min(n / u->theta_interval, u->theta_stages - 1);
+            theta = (double)sg / (double)(u->theta_stages - 1);
+            if (sg != stage) {
+                if ((st = set_stage<T>(c, theta)) != STOKES_OK) break;
+                stage = sg;
+            }
+        }
+        // velocity step: M_theta v = f - G p from the current v
+        st = vcycle_impl<T>(c, vx, vy, p, &mp, nullptr, nullptr);
+        if (st == STOKES_ERR_NOT_CONVERGED) st = STOKES_OK;
+        if (st != STOKES_OK) break;
+        // pressure step and zero mean
+        RUN(STOKES_K_MG, 3,
+            uz_pressure_update<T>(g, u->omega_p, (const T *)c->eta_c, vx, vy, p, c->uz_partials, c->uz_scal + 1,
+                                  c->stream));
+        // relative energy residual (Sec. 6.4) with the caller's viscosity
+        const bool base = cont && theta != 1.0;
+        RUN(STOKES_K_ENERGY, 2,
+            launch_energy<T>(g, (const T *)(base ? c->eta_c0 : c->eta_c), (const T *)(base ? c->eta_n0 : c->eta_n),
+                             base ? nullptr : (const T *)c->ivx, base ? nullptr : (const T *)c->ivy,
+                             (const T *)c->fx, (const T *)c->fy, p, vx, vy, c->partials, c->dsum, c->stream));
+        CK(cudaMemcpyAsync(c->hsum, c->dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if ((st = device_status(c)) != STOKES_OK) break;
+        e = std::sqrt((c->hsum[0] + c->hsum[1]) / c->hsum[2]);
+        if (hist) hist[n] = e;
+        if (!std::isfinite(e)) {
+            st = STOKES_ERR_DIVERGED;
+            ++n;
+            break;
+        }
+        if (e <= u->tol) {
+            ++n;
+            break;
+        }
+    }
+    // leave the context with the caller's viscosity
+    if (cont && stage != u->theta_stages - 1 && stage >= 0) {
+        CK(cudaMemcpyAsync(c->eta_c, c->eta_c0, c->elems * c->esize, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->eta_n, c->eta_n0, c->elems * c->esize, cudaMemcpyDeviceToDevice, c->stream));
+        RUN(STOKES_K_COPY, 1,
+            launch_inv_diag<T>(g, (const T *)c->eta_c, (const T *)c->eta_n, (T *)c->ivx, (T *)c->ivy, c->stream));
+        mg_invalidate(c->mg);
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+    }
+    if (cycles) *cycles = n;
+    if (final_e) *final_e = e;
+    if (st != STOKES_OK) return st;
+    return (u->tol > 0.0 && !(e <= u->tol)) ? STOKES_ERR_NOT_CONVERGED : STOKES_OK;
+}
+
 } // namespace
 
 // ---------------------------------------------------------------------------
@@ -549,7 +655,7 @@ int stokes_destroy(stokes_ctx *c)
     prof_flush(c);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
     void *fields[] = {c->eta_c, c->eta_n, c->fx, c->fy, c->bx, c->by, c->sx, c->sy, c->ivx, c->ivy, c->partials,
-                      c->dsum, c->dstatus};
+                      c->dsum, c->dstatus, c->eta_c0, c->eta_n0, c->uz_partials, c->uz_scal};
     for (void *f : fields)
         if (f) cudaFree(f);
     if (c->hsum) cudaFreeHost(c->hsum);
@@ -661,6 +767,23 @@ int stokes_vcycle(stokes_ctx *c, void *vx, void *vy, const void *p, const stokes
     if (c->dtype == STOKES_F64)
         return vcycle_impl<double>(c, (double *)vx, (double *)vy, (const double *)p, params, final_rel_resid, cycles);
     return vcycle_impl<float>(c, (float *)vx, (float *)vy, (const float *)p, params, final_rel_resid, cycles);
+}
+
+int stokes_uzawa(stokes_ctx *c, void *vx, void *vy, void *p, const stokes_uzawa_params *params, double *history,
+                 int *cycles, double *final_rel_resid)
+{
+    if (!c || !vx || !vy || !p || !params) return STOKES_ERR_ARG;
+    const stokes_uzawa_params &u = *params;
+    if (u.cycles < 0 || !(u.omega_p > 0.0) || !std::isfinite(u.omega_p) || u.theta_interval < 0 ||
+        u.theta_stages < 0 || !(u.tol >= 0.0) || u.mg.max_cycles < 1)
+        return STOKES_ERR_ARG;
+    int st = check_mg_params(c, &u.mg);
+    if (st != STOKES_OK) return st;
+    if (!c->have_eta || !c->have_f) return STOKES_ERR_STATE;
+    if (c->dtype == STOKES_F64)
+        return uzawa_impl<double>(c, (double *)vx, (double *)vy, (double *)p, params, history, cycles,
+                                  final_rel_resid);
+    return uzawa_impl<float>(c, (float *)vx, (float *)vy, (float *)p, params, history, cycles, final_rel_resid);
 }
 
 int stokes_set_option(stokes_ctx *c, int option, long long value)
