@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--solve-n", type=int, default=4096, help="grid of the time-to-1e-8 solve")
     ap.add_argument("--batch", type=int, default=256, help="instances of the batched workload (0: skip)")
     ap.add_argument("--c2-sweeps", type=int, default=100, help="sweeps per smoother in the 1024^2 FP64 table")
-    ap.add_argument("--only", choices=["solve", "batch", "autotune", "c2"],
+    ap.add_argument("--uzawa-n", type=int, default=1024, help="grid of the Uzawa Stokes solve")
+    ap.add_argument("--only", choices=["solve", "batch", "autotune", "c2", "uzawa"],
                     help="run one extra leg alone and print its JSON (for profiling it)")
     return ap.parse_args()
 
@@ -344,6 +345,7 @@ def run_ours(args):
         if args.batch > 0:
             line["batched"] = batch_leg(args, api)
         line["autotune"] = autotune_leg(args, api)
+        line["uzawa_stokes"] = uzawa_leg(args, api)
         line["cpu_baseline"] = {kk: vv for kk, vv in cpu_sample(args, args.cpu_seconds).items() if kk != "seconds"}
     ctx.close()
     if rank == 0:
@@ -575,6 +577,44 @@ def batch_leg(args, api):
     return out
 
 
+def uzawa_leg(args, api):
+    """The full Stokes solve of Sec. 6.2 on the centred sinker (1024^2,
+    contrast 1e6): inexact Uzawa with a velocity step of four CG iterations,
+    each preconditioned by one V-cycle (RAS 32 x 32, k = 4, overlap 3; one
+    step per cycle stalls at this size), omega_p = 0.6, lithostatic start,
+    continuation in five stages of 25 cycles; wall time until the full
+    relative energy residual (velocity and pressure) reaches 1e-8, with the
+    V-cycle in FP32 or FP64 (outer iteration FP64)."""
+    import torch
+    from paper_2509_19061_gb300 import inputs
+    n = args.uzawa_n
+    prob = inputs.sinker_problem(n, eta_in=1e6)
+    out = {"workload": "sinker_%dx%d_contrast1e6" % (n, n), "tol": 1e-8, "omega_p": 0.6,
+           "continuation": "theta 0, 1/4, .., 1 every 25 cycles",
+           "velocity_step": "4 CG iterations, each one V-cycle (ras 32x32 k4 o3)"}
+    for inner in ("f32", "f64"):
+        ctx = api.StokesContext(n, n, 1.0, 1.0, "f64")
+        ctx.set_problem(prob)
+        vx, vy, p = ctx.field(), ctx.field(), ctx.field()
+        kw = dict(cycles=600, theta_interval=25, tol=1e-8, inner=inner, variant="ras", tile=(32, 32), k=4,
+                  overlap=3, seed=1, nu_max=40, vel_its=4)
+        ctx.uzawa(vx, vy, p, **dict(kw, cycles=2))  # hierarchy and graph
+        vx.zero_()
+        vy.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, hist, cyc, e = ctx.uzawa(vx, vy, p, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[inner + "_inner"] = {"seconds": dt, "cycles": cyc, "final_energy_residual": e, "status": st,
+                                 "ms_per_cycle": 1e3 * dt / max(cyc, 1),
+                                 "residual_at": {str(c): float(hist[c - 1]) for c in (25, 50, 100, 200, 400)
+                                                 if c <= len(hist)}}
+        ctx.close()
+    out["speedup_f32_over_f64"] = out["f64_inner"]["seconds"] / out["f32_inner"]["seconds"]
+    return out
+
+
 def autotune_leg(args, api):
     """One tuning run of the RAS smoother (tile, k, overlap) by wall time of
     the solve to E_v <= 1e-8: 1024^2 centred sinker, contrast 1e4, FP64 outer
@@ -687,7 +727,8 @@ def run_only(args):
     import torch
     from paper_2509_19061_gb300 import api
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    leg = {"solve": solve_times, "batch": batch_leg, "autotune": autotune_leg, "c2": c2_table}[args.only]
+    leg = {"solve": solve_times, "batch": batch_leg, "autotune": autotune_leg, "c2": c2_table,
+           "uzawa": uzawa_leg}[args.only]
     print(json.dumps({"leg": args.only, "result": leg(args, api)}))
     return 0
 
