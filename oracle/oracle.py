@@ -359,3 +359,64 @@ def uzawa(g: Grid, fx, fy, mg: MG, cycles, omega_p=0.6, theta_interval=25, theta
         rv, rp, ff = energy(g, fx, fy, p, vx, vy)
         hist.append(float(np.sqrt((rv + rp) / ff)))
     return vx, vy, p, np.array(hist)
+
+
+# ---------------------------------------------------------------------------
+# Anderson acceleration of the inexact Uzawa iteration (Algorithm 1, Sec. 3.3)
+# ---------------------------------------------------------------------------
+def anderson_coefficients(R, reg=1e-14):
+    """alpha = argmin ||R alpha||_2 subject to sum(alpha) = 1 for the columns of
+    R (Algorithm 1), from the normal equations of the constrained problem:
+    H y = 1 with H = R^T R (plus reg * max diag H on the diagonal, reading:
+    keeps H invertible when residuals are nearly dependent), alpha = y / sum y."""
+    R = np.asarray(R, dtype=np.float64)
+    H = R.T @ R
+    H = H + reg * max(float(np.max(np.diag(H))), 1e-300) * np.eye(H.shape[0])
+    y = np.linalg.solve(H, np.ones(H.shape[0]))
+    return y / y.sum()
+
+
+def uzawa_map(g: Grid, fx, fy, mg: MG, vx, vy, p, theta, emin, omega_p=0.6, krylov=True, vel_its=1):
+    """F(x) of Algorithm 1: one inexact Uzawa cycle (see uzawa) from
+    x = (vx, vy, p) at continuation parameter theta."""
+    ec, en = blend_eta(g.eta_c, g.eta_n, theta, emin)
+    gc = Grid(g.nx, g.ny, g.hx, g.hy, ec, en)
+    vx, vy, _, _, _ = (mg_fcg if krylov else mg_solve)(gc, fx, fy, p, mg, 0.0, vel_its, vx, vy)
+    p = p - omega_p * ec * apply_D(g, vx, vy)
+    return vx, vy, p - p.mean()
+
+
+def anderson_uzawa(g: Grid, fx, fy, mg: MG, cycles, depth=5, omega_p=0.6, theta_interval=25, theta_stages=5,
+                   krylov=True, vel_its=1, p=None, vx=None, vy=None, reg=1e-14):
+    """Algorithm 1 on the inexact Uzawa map F over x = [v, p]: x1 = F(x0);
+    then r_k = F(x_k) - x_k over the last min(depth, k) + 1 iterates,
+    alpha = argmin ||R alpha||_2 with sum(alpha) = 1, and
+    x_{k+1} = sum_i alpha_i F(x_i).  The 2-norm runs over every entry of vx,
+    vy and p (walls and their residuals are zero).  Reading: F changes with
+    the continuation stage, so the history restarts when theta changes.
+    depth 0 is the plain iteration.  Returns (vx, vy, p, history of the
+    relative energy residual after every cycle)."""
+    vx = g.zeros_vx() if vx is None else _f64(vx).copy()
+    vy = g.zeros_vy() if vy is None else _f64(vy).copy()
+    p = lithostatic(g, fy) if p is None else _f64(p).copy()
+    emin = eta_min(g.eta_c, g.eta_n)
+    Fs, Rs, hist, stage = [], [], [], None
+    for c in range(cycles):
+        theta = continuation_theta(c, theta_interval, theta_stages)
+        if theta != stage:
+            Fs, Rs, stage = [], [], theta
+        F = uzawa_map(g, fx, fy, mg, vx, vy, p, theta, emin, omega_p, krylov, vel_its)
+        x = (vx, vy, p)
+        Fs.append(F)
+        Rs.append(np.concatenate([(a - b).ravel() for a, b in zip(F, x)]))
+        Fs, Rs = Fs[-(depth + 1):], Rs[-(depth + 1):]
+        if len(Rs) == 1 or depth == 0:
+            vx, vy, p = F
+        else:
+            alpha = anderson_coefficients(np.stack(Rs, axis=1), reg)
+            vx = sum(a * f[0] for a, f in zip(alpha, Fs))
+            vy = sum(a * f[1] for a, f in zip(alpha, Fs))
+            p = sum(a * f[2] for a, f in zip(alpha, Fs))
+        rv, rp, ff = energy(g, fx, fy, p, vx, vy)
+        hist.append(float(np.sqrt((rv + rp) / ff)))
+    return vx, vy, p, np.array(hist)

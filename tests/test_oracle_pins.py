@@ -687,3 +687,71 @@ def test_uzawa_with_vcycles_and_continuation_on_the_sinker(ora):
     assert abs(p.mean()) <= 1e-12 * np.abs(p).max()
     vx2, vy2, p2, hist2 = ora.uzawa(g, prob.fx, prob.fy, mg, 40, theta_interval=0, krylov=False)
     assert hist2[-1] > 1e3 * hist2[0]
+
+
+# ---------------------------------------------------------------------------
+# Anderson acceleration (Algorithm 1)
+# ---------------------------------------------------------------------------
+def test_anderson_coefficients_solve_the_constrained_least_squares(ora):
+    """KKT conditions of min ||R a|| s.t. sum a = 1: the coefficients sum to
+    one and R^T R a is a multiple of the all-ones vector; and no other
+    feasible direction lowers the objective."""
+    rng = np.random.default_rng(7)
+    R = rng.standard_normal((50, 4))
+    a = ora.anderson_coefficients(R, reg=0.0)
+    assert abs(a.sum() - 1.0) <= 1e-14
+    g = R.T @ (R @ a)
+    np.testing.assert_allclose(g, np.full(4, g.mean()), rtol=1e-10)
+    f0 = np.linalg.norm(R @ a)
+    for _ in range(20):
+        d = rng.standard_normal(4)
+        d -= d.mean()
+        assert np.linalg.norm(R @ (a + 1e-3 * d)) >= f0
+
+
+def test_anderson_terminates_on_a_linear_map(ora):
+    """On an affine fixed-point map of dimension n, Anderson with depth >= n
+    is GMRES in disguise: it reaches the fixed point in at most n + 1 steps
+    (here checked through the coefficient routine, as Algorithm 1 uses it)."""
+    rng = np.random.default_rng(8)
+    n = 4
+    A = 0.5 * rng.standard_normal((n, n)) / np.sqrt(n)
+    b = rng.standard_normal(n)
+    xs = np.linalg.solve(np.eye(n) - A, b)
+    x = np.zeros(n)
+    Fs, Rs = [], []
+    for k in range(n + 2):
+        F = A @ x + b
+        Fs.append(F)
+        Rs.append(F - x)
+        if len(Rs) == 1:
+            x = F
+        else:
+            a = ora.anderson_coefficients(np.stack(Rs, axis=1), reg=0.0)
+            x = sum(ai * fi for ai, fi in zip(a, Fs))
+    np.testing.assert_allclose(x, xs, rtol=1e-9, atol=1e-9)
+
+
+def test_anderson_depth_zero_is_the_plain_iteration(ora):
+    prob = inputs.sinker_problem(32, eta_in=1e2)
+    g = grid_from(ora, prob)
+    mg = ora.MG(variant=4, ti=8, tj=8, k=2, overlap=1, seed=2)
+    a = ora.anderson_uzawa(g, prob.fx, prob.fy, mg, 12, depth=0, theta_interval=5)
+    b = ora.uzawa(g, prob.fx, prob.fy, mg, 12, theta_interval=5)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_anderson_accelerates_uzawa(ora):
+    """With exact velocity solves, Anderson (depth 5) reaches a 1e-8 energy
+    residual in far fewer cycles than the plain Uzawa iteration."""
+    nx, ny = 12, 10
+    ec, en = inputs.random_viscosity(nx, ny, 23, (0.0, 1.0))
+    g = ora.Grid(nx, ny, 1.0 / nx, 1.0 / ny, ec, en)
+    prob = inputs.sinker_problem(nx, ny, eta_in=10.0, ly=1.0)
+    mg = ora.MG(max_levels=1, variant=1)
+    plain = ora.uzawa(g, prob.fx, prob.fy, mg, 200, theta_interval=0)[3]
+    acc = ora.anderson_uzawa(g, prob.fx, prob.fy, mg, 200, depth=5, theta_interval=0)[3]
+    n_plain = int(np.argmax(plain <= 1e-8)) if np.any(plain <= 1e-8) else 10 ** 6
+    n_acc = int(np.argmax(acc <= 1e-8))
+    assert acc[n_acc] <= 1e-8 and 2 * n_acc < n_plain
