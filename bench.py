@@ -592,12 +592,12 @@ def uzawa_leg(args, api):
     out = {"workload": "sinker_%dx%d_contrast1e6" % (n, n), "tol": 1e-8, "omega_p": 0.6,
            "continuation": "theta 0, 1/4, .., 1 every 25 cycles",
            "velocity_step": "4 CG iterations, each one V-cycle (ras 32x32 k4 o3)"}
-    for inner in ("f32", "f64"):
+    for inner, label, aa in (("f32", "f32_inner", 0), ("f64", "f64_inner", 0), ("f32", "f32_inner_anderson5", 5)):
         ctx = api.StokesContext(n, n, 1.0, 1.0, "f64")
         ctx.set_problem(prob)
         vx, vy, p = ctx.field(), ctx.field(), ctx.field()
         kw = dict(cycles=600, theta_interval=25, tol=1e-8, inner=inner, variant="ras", tile=(32, 32), k=4,
-                  overlap=3, seed=1, nu_max=40, vel_its=4)
+                  overlap=3, seed=1, nu_max=40, vel_its=4, anderson=aa)
         ctx.uzawa(vx, vy, p, **dict(kw, cycles=2))  # hierarchy and graph
         vx.zero_()
         vy.zero_()
@@ -606,7 +606,7 @@ def uzawa_leg(args, api):
         st, hist, cyc, e = ctx.uzawa(vx, vy, p, **kw)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        out[inner + "_inner"] = {"seconds": dt, "cycles": cyc, "final_energy_residual": e, "status": st,
+        out[label] = {"seconds": dt, "cycles": cyc, "final_energy_residual": e, "status": st,
                                  "ms_per_cycle": 1e3 * dt / max(cyc, 1),
                                  "residual_at": {str(c): float(hist[c - 1]) for c in (25, 50, 100, 200, 400)
                                                  if c <= len(hist)}}

@@ -235,7 +235,15 @@ int stokes_vcycle(stokes_ctx *ctx, void *vx, void *vy, const void *p, const stok
  *                 every cycle.
  * lithostatic_init  1: start from the lithostatic pressure of f (p[0][i] = 0,
  *                 p[j][i] = p[j-1][i] - hy fy[j][i], zero mean), overwriting p;
- *                 0: start from the caller's p. */
+ *                 0: start from the caller's p.
+ * anderson_depth  Anderson acceleration of the Uzawa map over x = [v, p]
+ *                 (Algorithm 1) with depth m = anderson_depth (0 <= m < 16; 0 off):
+ *                 x_{k+1} = sum_i alpha_i F(x_i) over the last min(m, k) + 1
+ *                 iterates, alpha minimising || sum_i alpha_i (F(x_i) - x_i) ||_2
+ *                 (2-norm over every entry of vx, vy, p) subject to sum alpha = 1,
+ *                 solved on the host from FP64 inner products with a relative
+ *                 diagonal shift of 1e-14; the history restarts at every
+ *                 continuation stage.  Needs 6 (m + 1) + 3 extra device fields. */
 typedef struct {
     stokes_mg_params mg;
     double omega_p;
@@ -243,6 +251,7 @@ typedef struct {
     int theta_interval, theta_stages;
     double tol;
     int lithostatic_init;
+    int anderson_depth;
 } stokes_uzawa_params;
 
 /* Solve the Stokes system M v + G p = f, D v = 0 (Eq. (6) and Eq. (4)) by the

@@ -63,7 +63,7 @@ class stokes_mg_params(ctypes.Structure):
 class stokes_uzawa_params(ctypes.Structure):
     _fields_ = [("mg", stokes_mg_params), ("omega_p", ctypes.c_double), ("cycles", ctypes.c_int),
                 ("theta_interval", ctypes.c_int), ("theta_stages", ctypes.c_int), ("tol", ctypes.c_double),
-                ("lithostatic_init", ctypes.c_int)]
+                ("lithostatic_init", ctypes.c_int), ("anderson_depth", ctypes.c_int)]
 
 
 _VP, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
@@ -219,11 +219,13 @@ def stokes_vcycle(ctx, vx, vy, p, params):
 
 
 def uzawa_params(cycles=100, omega_p=0.6, theta_interval=25, theta_stages=5, tol=0.0, lithostatic_init=True,
-                 vel_its=1, **mg):
+                 vel_its=1, anderson=0, **mg):
     """Build a stokes_uzawa_params (Sec. 6.2 defaults: omega_p 0.6, continuation
-    in 5 stages of 25 cycles); vel_its V-cycles (CG iterations) per cycle."""
+    in 5 stages of 25 cycles); vel_its V-cycles (CG iterations) per cycle;
+    anderson = depth of the Anderson acceleration (0 off)."""
     m = mg_params(max_cycles=vel_its, **mg)
-    return stokes_uzawa_params(m, omega_p, cycles, theta_interval, theta_stages, tol, 1 if lithostatic_init else 0)
+    return stokes_uzawa_params(m, omega_p, cycles, theta_interval, theta_stages, tol, 1 if lithostatic_init else 0,
+                               anderson)
 
 
 def stokes_uzawa(ctx, vx, vy, p, params):

@@ -168,6 +168,25 @@ template <typename T> // lithostatic pressure of f_y, zero mean
 cudaError_t uz_lithostatic(const GridDesc<T> &g, double hy, const T *fy, T *p, double *partials, double *sum,
                            cudaStream_t s);
 
+// Anderson acceleration over x = (vx, vy, p): up to AA_MAX stored vectors.
+constexpr int AA_MAX = 16;
+template <typename T>
+struct AndersonSet {
+    const T *x[AA_MAX], *y[AA_MAX], *p[AA_MAX];
+    int n;
+};
+struct AndersonAlpha {
+    double a[AA_MAX];
+};
+// aa_multidot: `uzawa_partials() * AA_MAX` partials; out[j] = <a_0, hs_j> (three fields)
+template <typename T>
+cudaError_t aa_diff(size_t n, const T *f, const T *x, T *r, cudaStream_t s);
+template <typename T>
+cudaError_t aa_multidot(size_t n, const AndersonSet<T> &a, const AndersonSet<T> &hs, double *partials, double *out,
+                        cudaStream_t s);
+template <typename T>
+cudaError_t aa_combine(size_t n, const AndersonSet<T> &F, const AndersonAlpha &al, T *x, T *y, T *p, cudaStream_t s);
+
 // ---- smoother schedules (smooth.cu) ---------------------------------------
 // Where kernel launches go: counts (and, for a context with timing on, times)
 // each launch group of `nk` kernels of class `kind` (stokes_kernel_class).

@@ -70,6 +70,8 @@ struct stokes_ctx {
     void *ivx = nullptr, *ivy = nullptr; // 1/diag(M), read by the tile kernels and the energy sums
     void *eta_c0 = nullptr, *eta_n0 = nullptr; // the caller's viscosity during a continuation
     double *uz_partials = nullptr, *uz_scal = nullptr; // Uzawa reductions; uz_scal: [eta_min, sum]
+    std::vector<void *> aa;              // Anderson history: (depth+1) x (F, r) x 3 fields, then x_old (3)
+    double *aa_partials = nullptr, *aa_out = nullptr, *aa_hout = nullptr;
     double *partials = nullptr, *dsum = nullptr, *hsum = nullptr;
     bool have_eta = false, have_f = false;
     int *dstatus = nullptr;              // device status word of the bounded waits
@@ -466,6 +468,33 @@ int vcycle_impl(stokes_ctx *c, T *vx, T *vy, const T *p, const stokes_mg_params 
     return verdict < 0 ? verdict : STOKES_OK;
 }
 
+// Solve H y = b (n x n, row-major, n <= AA_MAX) by Gaussian elimination with
+// partial pivoting; false if singular.
+bool small_solve(int n, double *H, double *b)
+{
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < n; ++i)
+            if (std::fabs(H[i * n + k]) > std::fabs(H[piv * n + k])) piv = i;
+        if (!(std::fabs(H[piv * n + k]) > 0.0)) return false;
+        if (piv != k) {
+            for (int j = 0; j < n; ++j) std::swap(H[k * n + j], H[piv * n + j]);
+            std::swap(b[k], b[piv]);
+        }
+        for (int i = k + 1; i < n; ++i) {
+            const double f = H[i * n + k] / H[k * n + k];
+            for (int j = k; j < n; ++j) H[i * n + j] -= f * H[k * n + j];
+            b[i] -= f * b[k];
+        }
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        double v = b[k];
+        for (int j = k + 1; j < n; ++j) v -= H[k * n + j] * b[j];
+        b[k] = v / H[k * n + k];
+    }
+    return true;
+}
+
 // swap in the viscosity of continuation stage theta (from the saved base)
 template <typename T>
 int set_stage(stokes_ctx *c, double theta)
@@ -511,6 +540,28 @@ int uzawa_impl(stokes_ctx *c, T *vx, T *vy, T *p, const stokes_uzawa_params *u, 
     }
     stokes_mg_params mp = u->mg;
     mp.tol = 0.0; // the velocity step always runs its mg.max_cycles V-cycles (unless the residual is 0)
+    // Anderson acceleration (Algorithm 1): history of F(x_i) and r_i = F(x_i) - x_i
+    const int depth = u->anderson_depth, slots = depth + 1;
+    const size_t fbytes = c->elems * c->esize;
+    if (depth > 0 && (int)c->aa.size() < 6 * slots + 3) {
+        while ((int)c->aa.size() < 6 * slots + 3) {
+            void *f = nullptr;
+            const int st0 = alloc_field(c, &f);
+            if (st0 != STOKES_OK) return st0;
+            c->aa.push_back(f);
+        }
+        if (!c->aa_partials) {
+            CK(cudaMalloc(&c->aa_partials, (size_t)uzawa_partials() * AA_MAX * sizeof(double)));
+            CK(cudaMalloc(&c->aa_out, AA_MAX * sizeof(double)));
+            CK(cudaMallocHost(&c->aa_hout, AA_MAX * sizeof(double)));
+        }
+    }
+    auto fld = [&](int slot, int kind, int comp) { return (T *)c->aa[(size_t)(slot * 6 + kind * 3 + comp)]; };
+    T *const xo[3] = {depth > 0 ? (T *)c->aa[6 * slots] : nullptr, depth > 0 ? (T *)c->aa[6 * slots + 1] : nullptr,
+                      depth > 0 ? (T *)c->aa[6 * slots + 2] : nullptr};
+    T *const xs[3] = {vx, vy, p};
+    std::vector<int> order;                 // slots, oldest first
+    std::vector<double> H((size_t)slots * slots, 0.0); // <r_s, r_t> by slot
     int stage = -1, st = STOKES_OK, n = 0;
     double e = 0.0;
     for (; n < u->cycles; ++n) {
@@ -521,8 +572,11 @@ int uzawa_impl(stokes_ctx *c, T *vx, T *vy, T *p, const stokes_uzawa_params *u, 
             if (sg != stage) {
                 if ((st = set_stage<T>(c, theta)) != STOKES_OK) break;
                 stage = sg;
+                order.clear(); // the map F changes with theta: restart the history
             }
         }
+        if (depth > 0)
+            for (int q = 0; q < 3; ++q) CK(cudaMemcpyAsync(xo[q], xs[q], fbytes, cudaMemcpyDeviceToDevice, c->stream));
         // velocity step: M_theta v = f - G p from the current v
         st = vcycle_impl<T>(c, vx, vy, p, &mp, nullptr, nullptr);
         if (st == STOKES_ERR_NOT_CONVERGED) st = STOKES_OK;
@@ -531,6 +585,67 @@ int uzawa_impl(stokes_ctx *c, T *vx, T *vy, T *p, const stokes_uzawa_params *u, 
         RUN(STOKES_K_MG, 3,
             uz_pressure_update<T>(g, u->omega_p, (const T *)c->eta_c, vx, vy, p, c->uz_partials, c->uz_scal + 1,
                                   c->stream));
+        if (depth > 0) {
+            // store F(x) and r = F(x) - x in a free slot, newest last
+            int slot = 0;
+            if ((int)order.size() == slots) {
+                slot = order.front();
+                order.erase(order.begin());
+            } else {
+                std::vector<bool> used(slots, false);
+                for (int o : order) used[o] = true;
+                while (used[slot]) ++slot;
+            }
+            for (int q = 0; q < 3; ++q) {
+                CK(cudaMemcpyAsync(fld(slot, 0, q), xs[q], fbytes, cudaMemcpyDeviceToDevice, c->stream));
+                RUN(STOKES_K_MG, 1, aa_diff<T>(c->elems, xs[q], xo[q], fld(slot, 1, q), c->stream));
+            }
+            order.push_back(slot);
+            // <r_new, r_j> for every stored slot
+            AndersonSet<T> a{}, hs{};
+            a.x[0] = fld(slot, 1, 0);
+            a.y[0] = fld(slot, 1, 1);
+            a.p[0] = fld(slot, 1, 2);
+            a.n = 1;
+            hs.n = (int)order.size();
+            for (int j = 0; j < hs.n; ++j) {
+                hs.x[j] = fld(order[j], 1, 0);
+                hs.y[j] = fld(order[j], 1, 1);
+                hs.p[j] = fld(order[j], 1, 2);
+            }
+            RUN(STOKES_K_MG, 2, aa_multidot<T>(c->elems, a, hs, c->aa_partials, c->aa_out, c->stream));
+            CK(cudaMemcpyAsync(c->aa_hout, c->aa_out, AA_MAX * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            if ((st = device_status(c)) != STOKES_OK) break;
+            for (int j = 0; j < hs.n; ++j) {
+                H[(size_t)slot * slots + order[j]] = c->aa_hout[j];
+                H[(size_t)order[j] * slots + slot] = c->aa_hout[j];
+            }
+            if (hs.n > 1) {
+                // alpha = argmin ||R alpha|| with sum alpha = 1: H y = 1, alpha = y / sum y
+                const int m = hs.n;
+                double Hm[AA_MAX * AA_MAX], y[AA_MAX], dmax = 0.0;
+                for (int i = 0; i < m; ++i) {
+                    for (int j = 0; j < m; ++j) Hm[i * m + j] = H[(size_t)order[i] * slots + order[j]];
+                    dmax = std::max(dmax, Hm[i * m + i]);
+                    y[i] = 1.0;
+                }
+                for (int i = 0; i < m; ++i) Hm[i * m + i] += 1e-14 * std::max(dmax, 1e-300);
+                if (small_solve(m, Hm, y)) {
+                    double sy = 0.0;
+                    for (int i = 0; i < m; ++i) sy += y[i];
+                    AndersonAlpha al{};
+                    AndersonSet<T> F{};
+                    F.n = m;
+                    for (int i = 0; i < m; ++i) {
+                        al.a[i] = y[i] / sy;
+                        F.x[i] = fld(order[i], 0, 0);
+                        F.y[i] = fld(order[i], 0, 1);
+                        F.p[i] = fld(order[i], 0, 2);
+                    }
+                    RUN(STOKES_K_MG, 1, aa_combine<T>(c->elems, F, al, vx, vy, p, c->stream));
+                }
+            }
+        }
         // relative energy residual (Sec. 6.4) with the caller's viscosity
         const bool base = cont && theta != 1.0;
         RUN(STOKES_K_ENERGY, 2,
@@ -660,6 +775,10 @@ int stokes_destroy(stokes_ctx *c)
         if (f) cudaFree(f);
     if (c->hsum) cudaFreeHost(c->hsum);
     if (c->hstatus) cudaFreeHost(c->hstatus);
+    for (void *f : c->aa) cudaFree(f);
+    if (c->aa_partials) cudaFree(c->aa_partials);
+    if (c->aa_out) cudaFree(c->aa_out);
+    if (c->aa_hout) cudaFreeHost(c->aa_hout);
     delete c;
     return STOKES_OK;
 }
@@ -775,7 +894,8 @@ int stokes_uzawa(stokes_ctx *c, void *vx, void *vy, void *p, const stokes_uzawa_
     if (!c || !vx || !vy || !p || !params) return STOKES_ERR_ARG;
     const stokes_uzawa_params &u = *params;
     if (u.cycles < 0 || !(u.omega_p > 0.0) || !std::isfinite(u.omega_p) || u.theta_interval < 0 ||
-        u.theta_stages < 0 || !(u.tol >= 0.0) || u.mg.max_cycles < 1)
+        u.theta_stages < 0 || !(u.tol >= 0.0) || u.mg.max_cycles < 1 || u.anderson_depth < 0 ||
+        u.anderson_depth >= AA_MAX)
         return STOKES_ERR_ARG;
     int st = check_mg_params(c, &u.mg);
     if (st != STOKES_OK) return st;

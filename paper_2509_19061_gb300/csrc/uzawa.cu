@@ -146,9 +146,103 @@ __global__ void k_litho(GridDesc<T> g, T hy, const T *__restrict__ fy, T *__rest
     }
 }
 
+// ---- Anderson acceleration (Algorithm 1) -----------------------------------
+// r = F - x over whole arrays (walls and padding are zero in both)
+template <typename T>
+__global__ void k_diff(size_t n, const T *__restrict__ f, const T *__restrict__ x, T *__restrict__ r)
+{
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        r[t] = r_sub(f[t], x[t]);
+}
+
+// <a, h_j> for j < hs.n, summed over the three fields; partials[blk * AA_MAX + j]
+template <typename T>
+__global__ void __launch_bounds__(UZ_THREADS) k_multidot(size_t n, AndersonSet<T> a, AndersonSet<T> hs,
+                                                         double *__restrict__ partials)
+{
+    __shared__ double sh[UZ_THREADS / 32][AA_MAX];
+    double s[AA_MAX];
+#pragma unroll
+    for (int j = 0; j < AA_MAX; ++j) s[j] = 0.0;
+    for (size_t t = (size_t)blockIdx.x * UZ_THREADS + threadIdx.x; t < n; t += (size_t)gridDim.x * UZ_THREADS) {
+        const double ax = (double)a.x[0][t], ay = (double)a.y[0][t], ap = (double)a.p[0][t];
+#pragma unroll
+        for (int j = 0; j < AA_MAX; ++j)
+            if (j < hs.n) {
+                s[j] = fma(ax, (double)hs.x[j][t], s[j]);
+                s[j] = fma(ay, (double)hs.y[j][t], s[j]);
+                s[j] = fma(ap, (double)hs.p[j][t], s[j]);
+            }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < AA_MAX; ++j) {
+        const double v = warp_sum(s[j]);
+        if (lane == 0) sh[wid][j] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < AA_MAX) {
+        double v = 0.0;
+        for (int q = 0; q < UZ_THREADS / 32; ++q) v += sh[q][threadIdx.x];
+        partials[(size_t)blockIdx.x * AA_MAX + threadIdx.x] = v;
+    }
+}
+
+// out[j] = sum over blocks of partials[b * AA_MAX + j], one warp per j
+__global__ void k_final_multi(const double *__restrict__ partials, int nblocks, double *__restrict__ out)
+{
+    const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int b = lane; b < nblocks; b += 32) s += partials[(size_t)b * AA_MAX + j];
+    s = warp_sum(s);
+    if (lane == 0) out[j] = s;
+}
+
+// x = sum_j alpha_j F_j, accumulated in the order j = 0, 1, ...
+template <typename T>
+__global__ void k_combine(size_t n, AndersonSet<T> F, AndersonAlpha al, T *__restrict__ x, T *__restrict__ y,
+                          T *__restrict__ p)
+{
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        T sx = r_mul((T)al.a[0], F.x[0][t]), sy = r_mul((T)al.a[0], F.y[0][t]), sp = r_mul((T)al.a[0], F.p[0][t]);
+        for (int j = 1; j < F.n; ++j) {
+            const T aj = (T)al.a[j];
+            sx = r_add(sx, r_mul(aj, F.x[j][t]));
+            sy = r_add(sy, r_mul(aj, F.y[j][t]));
+            sp = r_add(sp, r_mul(aj, F.p[j][t]));
+        }
+        x[t] = sx;
+        y[t] = sy;
+        p[t] = sp;
+    }
+}
+
 } // namespace
 
 int uzawa_partials() { return UZ_BLOCKS; }
+
+template <typename T>
+cudaError_t aa_diff(size_t n, const T *f, const T *x, T *r, cudaStream_t s)
+{
+    k_diff<T><<<UZ_BLOCKS, UZ_THREADS, 0, s>>>(n, f, x, r);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t aa_multidot(size_t n, const AndersonSet<T> &a, const AndersonSet<T> &hs, double *partials, double *out,
+                        cudaStream_t s)
+{
+    k_multidot<T><<<UZ_BLOCKS, UZ_THREADS, 0, s>>>(n, a, hs, partials);
+    k_final_multi<<<1, 32 * AA_MAX, 0, s>>>(partials, UZ_BLOCKS, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t aa_combine(size_t n, const AndersonSet<T> &F, const AndersonAlpha &al, T *x, T *y, T *p, cudaStream_t s)
+{
+    k_combine<T><<<UZ_BLOCKS, UZ_THREADS, 0, s>>>(n, F, al, x, y, p);
+    return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t uz_eta_min(const GridDesc<T> &g, const T *ec, const T *en, double *partials, double *out, cudaStream_t s)
@@ -188,6 +282,11 @@ cudaError_t uz_lithostatic(const GridDesc<T> &g, double hy, const T *fy, T *p, d
 }
 
 #define INST(T)                                                                                                    \
+    template cudaError_t aa_diff<T>(size_t, const T *, const T *, T *, cudaStream_t);                             \
+    template cudaError_t aa_multidot<T>(size_t, const AndersonSet<T> &, const AndersonSet<T> &, double *,        \
+                                        double *, cudaStream_t);                                                  \
+    template cudaError_t aa_combine<T>(size_t, const AndersonSet<T> &, const AndersonAlpha &, T *, T *, T *,       \
+                                       cudaStream_t);                                                              \
     template cudaError_t uz_eta_min<T>(const GridDesc<T> &, const T *, const T *, double *, double *,             \
                                        cudaStream_t);                                                              \
     template cudaError_t uz_blend<T>(const GridDesc<T> &, double, const double *, const T *, const T *, T *, T *,  \

@@ -129,3 +129,29 @@ def test_uzawa_errors(api):
         ctx.uzawa(vx, vy, p, cycles=3, variant="fused")
     assert ex.value.status == api.STOKES_ERR_STATE
     ctx.close()
+
+
+@pytest.mark.parametrize("depth", [2, 5])
+def test_anderson_uzawa_f64_matches_the_oracle(api, depth):
+    """Algorithm 1 over the Uzawa map with an FP64 V-cycle: v, p and the
+    residual history follow the oracle (the least-squares weights come from
+    inner products summed in another order, hence the looser bound)."""
+    prob = inputs.sinker_problem(64, 48, eta_in=1e2, ly=48 / 64)
+    sm = dict(variant="ras", tile=(8, 8), k=2, overlap=1, seed=5, nu_max=12)
+    st, hist, cyc, e, v = gpu_uzawa(api, prob, cycles=30, theta_interval=8, inner="f64", anderson=depth, **sm)
+    rx, ry, rp, rh = ora.anderson_uzawa(ogrid(prob), prob.fx, prob.fy, oracle_mg(sm), 30, depth=depth,
+                                        theta_interval=8)
+    assert rel(v[:2], (rx, ry)) <= 1e-7
+    assert rel((v[2],), (rp,)) <= 1e-7
+    np.testing.assert_allclose(hist, rh, rtol=1e-6)
+
+
+def test_anderson_needs_fewer_uzawa_cycles(api):
+    prob = inputs.sinker_problem(128, eta_in=1e6)
+    kw = dict(cycles=300, theta_interval=25, tol=1e-8, inner="f32", variant="ras", tile=(32, 32), k=4, overlap=3,
+              seed=1, nu_max=40)
+    st0, h0, c0, e0, _ = gpu_uzawa(api, prob, **kw)
+    st1, h1, c1, e1, _ = gpu_uzawa(api, prob, anderson=5, **kw)
+    print("plain %d cycles, Anderson(5) %d cycles" % (c0, c1))
+    assert st1 == api.STOKES_OK and e1 <= 1e-8
+    assert c1 < c0
