@@ -764,7 +764,9 @@ int ora_dense_solve(int nx, int ny, double hx, double hy, const double *eta_c, c
 }
 
 /* smoother codes shared with the C interface's enumeration */
-enum { ORA_JACOBI = 0, ORA_JACOBI_FUSED = 1, ORA_JACOBI_BLOCKED = 2, ORA_RBGS = 3, ORA_RAS = 4 };
+/* ORA_MIXED (V-cycle only): the "mixed" smoother of Sec. 6.3, Jacobi on the
+ * finest level and RAS on every coarser level. */
+enum { ORA_JACOBI = 0, ORA_JACOBI_FUSED = 1, ORA_JACOBI_BLOCKED = 2, ORA_RBGS = 3, ORA_RAS = 4, ORA_MIXED = 5 };
 
 typedef struct {
     int variant, ti, tj, k, overlap;
@@ -773,13 +775,15 @@ typedef struct {
     int nu_max;
 } smoother_t;
 
-static void run_smoother(const level_t *lv, const smoother_t *sm, const double *bx, const double *by, int sweeps,
-                         uint64_t call_index, double *vx, double *vy)
+static void run_smoother(const level_t *lv, int level, const smoother_t *sm, const double *bx, const double *by,
+                         int sweeps, uint64_t call_index, double *vx, double *vy)
 {
     if (sweeps <= 0) return;
-    if (sm->variant == ORA_RBGS)
+    int variant = sm->variant;
+    if (variant == ORA_MIXED) variant = level == 0 ? ORA_JACOBI : ORA_RAS;
+    if (variant == ORA_RBGS)
         ora_rbgs(lv->nx, lv->ny, lv->hx, lv->hy, lv->eta_c, lv->eta_n, bx, by, sm->omega, sweeps, vx, vy);
-    else if (sm->variant == ORA_RAS)
+    else if (variant == ORA_RAS)
         ora_ras(lv->nx, lv->ny, lv->hx, lv->hy, lv->eta_c, lv->eta_n, bx, by, sm->omega, sweeps, sm->ti, sm->tj,
                 sm->k, sm->overlap, 1, ora_splitmix64(sm->seed, call_index), NULL, 0, vx, vy, NULL);
     else
@@ -821,7 +825,7 @@ static int vcycle_rec(level_t *lv, int L, int l, const smoother_t *sm, int nu_pr
         return st;
     }
     uint64_t base = (uint64_t)l * 2u;
-    run_smoother(F, sm, bx, by, ora_mg_sweeps(nu_pre, growth, l, sm->nu_max), base, vx, vy);
+    run_smoother(F, l, sm, bx, by, ora_mg_sweeps(nu_pre, growth, l, sm->nu_max), base, vx, vy);
     level_t *C = &lv[l + 1];
     size_t fnx = (size_t)F->ny * (F->nx + 1), fny = (size_t)(F->ny + 1) * F->nx;
     size_t cnx = (size_t)C->ny * (C->nx + 1), cny = (size_t)(C->ny + 1) * C->nx;
@@ -832,7 +836,7 @@ static int vcycle_rec(level_t *lv, int L, int l, const smoother_t *sm, int nu_pr
     mg_restrict(F, C, rx, ry, cbx, cby);
     int st = vcycle_rec(lv, L, l + 1, sm, nu_pre, nu_post, growth, cbx, cby, cvx, cvy);
     mg_prolong_add(F, C, cvx, cvy, vx, vy);
-    run_smoother(F, sm, bx, by, ora_mg_sweeps(nu_post, growth, l, sm->nu_max), base + 1u, vx, vy);
+    run_smoother(F, l, sm, bx, by, ora_mg_sweeps(nu_post, growth, l, sm->nu_max), base + 1u, vx, vy);
     free(rx); free(ry); free(cbx); free(cby); free(cvx); free(cvy);
     return st;
 }

@@ -755,3 +755,28 @@ def test_anderson_accelerates_uzawa(ora):
     n_plain = int(np.argmax(plain <= 1e-8)) if np.any(plain <= 1e-8) else 10 ** 6
     n_acc = int(np.argmax(acc <= 1e-8))
     assert acc[n_acc] <= 1e-8 and 2 * n_acc < n_plain
+
+
+def test_mixed_smoother_is_jacobi_fine_and_ras_coarse(ora):
+    """The "mixed" V-cycle (Sec. 6.3) equals a V-cycle whose finest level is
+    smoothed by Jacobi and whose coarser levels by RAS: on two levels (the
+    coarse one solved exactly) it is the Jacobi V-cycle, on three levels it
+    differs from both pure cycles, and it converges."""
+    prob = inputs.sinker_problem(32, eta_in=1e2)
+    g = grid_from(ora, prob)
+    bx, by = ora.rhs(g, prob.fx, prob.fy)
+    two = dict(max_levels=2, ti=8, tj=8, k=4, overlap=0, seed=3)
+    mixed = ora.vcycle(g, bx, by, ora.MG(variant=5, **two))
+    jac = ora.vcycle(g, bx, by, ora.MG(variant=0, **two))
+    for a, b in zip(mixed, jac):
+        np.testing.assert_array_equal(a, b)
+    prob = inputs.sinker_problem(64, eta_in=1e2)
+    g = grid_from(ora, prob)
+    bx, by = ora.rhs(g, prob.fx, prob.fy)
+    three = dict(max_levels=3, ti=8, tj=8, k=4, overlap=0, seed=3)
+    m3 = ora.vcycle(g, bx, by, ora.MG(variant=5, **three))
+    j3 = ora.vcycle(g, bx, by, ora.MG(variant=0, **three))
+    r3 = ora.vcycle(g, bx, by, ora.MG(variant=4, **three))
+    assert not np.array_equal(m3[0], j3[0]) and not np.array_equal(m3[0], r3[0])
+    vx, vy, c, fe, hist = ora.mg_solve(g, prob.fx, prob.fy, None, ora.MG(variant=5, **three), 1e-8, 60)
+    assert fe <= 1e-8
