@@ -70,7 +70,10 @@ typedef enum {
     STOKES_JACOBI_FUSED = 1,   /* (iii) the same map, vx and vy in one pass */
     STOKES_JACOBI_BLOCKED = 2, /* (iv)  the same map, one pass over shared-memory tiles */
     STOKES_RBGS = 3,           /* (i)   red-black Gauss-Seidel: vx red, vx black, vy red, vy black */
-    STOKES_RAS = 4             /* (v)   RAS-type temporally blocked Jacobi, Sec. 4.3 / Algorithm 2 */
+    STOKES_RAS = 4,            /* (v)   RAS-type temporally blocked Jacobi, Sec. 4.3 / Algorithm 2 */
+    STOKES_MIXED = 5           /* V-cycle smoother only (stokes_mg_params): Jacobi on the finest level,
+                                  RAS (with the smoother's tiles, k, overlap) on every coarser level,
+                                  the "mixed" configuration of Sec. 6.3 */
 } stokes_variant;
 
 typedef enum {

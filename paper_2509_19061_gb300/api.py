@@ -27,14 +27,14 @@ STOKES_ERR_NOT_CONVERGED = -6
 STOKES_ERR_STATE = -7
 
 STOKES_F32, STOKES_F64 = 0, 1
-STOKES_JACOBI, STOKES_JACOBI_FUSED, STOKES_JACOBI_BLOCKED, STOKES_RBGS, STOKES_RAS = 0, 1, 2, 3, 4
+STOKES_JACOBI, STOKES_JACOBI_FUSED, STOKES_JACOBI_BLOCKED, STOKES_RBGS, STOKES_RAS, STOKES_MIXED = 0, 1, 2, 3, 4, 5
 STOKES_FIELD_VX, STOKES_FIELD_VY, STOKES_FIELD_P, STOKES_FIELD_ETA_C, STOKES_FIELD_ETA_N = 0, 1, 2, 3, 4
 STOKES_SHIFT_NONE, STOKES_SHIFT_SPLITMIX, STOKES_SHIFT_LIST = 0, 1, 2
 STOKES_OPT_USE_TMA, STOKES_OPT_WAIT_LIMIT_CYCLES = 0, 1
 KERNEL_CLASSES = ["ras", "jacobi", "rbgs", "rhs", "energy", "copy", "apply", "mg"]
 
 VARIANTS = {"jacobi": STOKES_JACOBI, "fused": STOKES_JACOBI_FUSED, "blocked": STOKES_JACOBI_BLOCKED,
-            "rbgs": STOKES_RBGS, "ras": STOKES_RAS}
+            "rbgs": STOKES_RBGS, "ras": STOKES_RAS, "mixed": STOKES_MIXED}
 
 
 class StokesError(RuntimeError):

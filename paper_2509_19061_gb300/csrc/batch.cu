@@ -659,7 +659,7 @@ int plan_precond(stokes_batch *b, const stokes_mg_params *p, Precond<To, Ti> *P)
         // smoothing groups of this level: whole-level single tiles (Jacobi-like
         // smoothers on levels up to 64^2) and tiled instances
         if (l == h->Lmax - 1) continue;
-        const stokes_smooth_params &sm = p->smoother;
+        const stokes_smooth_params sm = level_smoother(p->smoother, l);
         for (int ph = 0; ph < 2; ++ph) {
             const int sweeps = mg_sweeps(ph == 0 ? p->nu_pre : p->nu_post, p->nu_growth, l, p->nu_max);
             const uint64_t seed = splitmix64(sm.seed, 2u * (uint64_t)l + (uint64_t)ph);
@@ -1228,9 +1228,9 @@ int stokes_batch_solve(stokes_batch *b, void *vx, void *vy, const void *p, const
     sm.shift_mode = STOKES_SHIFT_SPLITMIX;
     sm.shifts = nullptr;
     const int es_in = q.inner_dtype == STOKES_F64 ? 8 : 4;
-    if (sm.variant < STOKES_JACOBI || sm.variant > STOKES_RAS || sm.variant == STOKES_RBGS || !(sm.omega > 0.0))
+    if (sm.variant < STOKES_JACOBI || sm.variant > STOKES_MIXED || sm.variant == STOKES_RBGS || !(sm.omega > 0.0))
         return STOKES_ERR_ARG;
-    if (sm.variant == STOKES_RAS) {
+    if (sm.variant == STOKES_RAS || sm.variant == STOKES_MIXED) {
         if (sm.k < 1 || sm.overlap < 0 || sm.tile_i < 0 || sm.tile_j < 0) return STOKES_ERR_ARG;
         const int ti = sm.tile_i > 0 ? sm.tile_i : 32, tj = sm.tile_j > 0 ? sm.tile_j : 32;
         if (ras_batched_smem_bytes(ti, tj, sm.overlap, es_in) > (size_t)ras_max_smem()) return STOKES_ERR_ARG;

@@ -158,7 +158,7 @@ int build(MgHierarchy *h, const MgOuter &o, int levels, int coarsest, cudaStream
 // smoothing spec of level l and phase ph
 SmoothSpec level_spec(const stokes_mg_params *p, const MgLevel &l, int lvl, int ph, size_t es)
 {
-    const stokes_smooth_params &sm = p->smoother;
+    const stokes_smooth_params sm = level_smoother(p->smoother, lvl);
     SmoothSpec s;
     s.variant = sm.variant;
     s.sweeps = mg_sweeps(ph == 0 ? p->nu_pre : p->nu_post, p->nu_growth, lvl, p->nu_max);
@@ -232,6 +232,13 @@ int enqueue_precond(MgHierarchy *h, const Tc *rx, const Tc *ry, Tc *zx, Tc *zy, 
 }
 
 } // namespace
+
+stokes_smooth_params level_smoother(const stokes_smooth_params &sm, int level)
+{
+    stokes_smooth_params s = sm;
+    if (s.variant == STOKES_MIXED) s.variant = level == 0 ? STOKES_JACOBI : STOKES_RAS;
+    return s;
+}
 
 int mg_sweeps(int nu0, double growth, int l, int nu_max)
 {

@@ -74,6 +74,9 @@ cudaError_t kry_direction(const KrylovView &k, double beta, const T *zx, const T
 template <typename T> // v += z
 cudaError_t kry_add(const KrylovView &k, const T *zx, const T *zy, T *vx, T *vy, cudaStream_t s);
 
+// The smoother of level l (STOKES_MIXED: Jacobi on level 0, RAS below).
+stokes_smooth_params level_smoother(const stokes_smooth_params &sm, int level);
+
 // Sweeps of level l: ceil(nu0 growth^l), capped at nu_max when nu_max > 0.
 int mg_sweeps(int nu0, double growth, int l, int nu_max);
 

@@ -289,6 +289,7 @@ int check_mg_params(const stokes_ctx *c, const stokes_mg_params *p)
     sm.sweeps = 0;
     sm.shift_mode = STOKES_SHIFT_SPLITMIX;
     sm.shifts = nullptr;
+    if (sm.variant == STOKES_MIXED) sm.variant = STOKES_RAS; // its coarse levels use the RAS parameters
     int ti, tj;
     // the window must fit on the finest level in the inner precision
     return check_smooth_params(c->nx, c->ny, p->inner_dtype == STOKES_F64 ? 8 : 4, &sm, &ti, &tj);

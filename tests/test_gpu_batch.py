@@ -121,6 +121,7 @@ MG_SIZES = [(64, 64), (96, 64), (80, 48), (128, 128), (32, 32)]
     dict(variant="ras", tile=(32, 32), k=4, overlap=3, seed=1, nu_max=12),
     dict(variant="ras", tile=(16, 8), k=2, overlap=0, seed=9, nu_max=10),
     dict(variant="jacobi", nu_max=9),
+    dict(variant="mixed", tile=(16, 16), k=4, overlap=0, seed=6, nu_max=10),
 ])
 def test_batched_defect_correction_is_bitwise_the_single_context(api, dtype, inner, sm):
     """Three defect-correction cycles: every iterate is v += B(b - M v), with

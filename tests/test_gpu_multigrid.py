@@ -35,7 +35,7 @@ def rel(a, b):
     return float(np.sqrt(num / den))
 
 
-VARIANT_CODE = {"jacobi": 0, "fused": 1, "blocked": 2, "rbgs": 3, "ras": 4}
+VARIANT_CODE = {"jacobi": 0, "fused": 1, "blocked": 2, "rbgs": 3, "ras": 4, "mixed": 5}
 
 
 def run_solve(api, prob, dtype, cycles, tol=0.0, p=None, **mg):
@@ -74,6 +74,7 @@ def oracle_solve(prob, cycles, tol=0.0, p=None, krylov=False, **mg):
     dict(n=(96, 64), variant="ras", tile=(16, 12), k=3, overlap=1, seed=9, nu_max=20),
     dict(n=(64, 64), variant="rbgs", nu_max=10),
     dict(n=(48, 40), variant="blocked", tile=(16, 16)),
+    dict(n=(128, 96), variant="mixed", tile=(16, 16), k=4, overlap=0, seed=4, nu_max=16),
 ])
 @pytest.mark.parametrize("krylov", [False, True])
 def test_vcycle_f64_matches_oracle(api, case, krylov):

@@ -10,7 +10,7 @@ from paper_2509_19061_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-VARIANT_CODE = {"jacobi": 0, "fused": 1, "blocked": 2, "rbgs": 3, "ras": 4}
+VARIANT_CODE = {"jacobi": 0, "fused": 1, "blocked": 2, "rbgs": 3, "ras": 4, "mixed": 5}
 
 
 @pytest.fixture(scope="module")
@@ -85,6 +85,8 @@ def test_hydrostatic_state_is_a_fixed_point(api):
                                                                         seed=5, nu_max=12)),
     dict(n=(64, 64), krylov=True, vel_its=2, theta_interval=0, sm=dict(variant="jacobi", nu_max=10)),
     dict(n=(48, 40), krylov=False, vel_its=1, theta_interval=5, sm=dict(variant="fused", nu_max=10)),
+    dict(n=(96, 64), krylov=True, vel_its=1, theta_interval=6, sm=dict(variant="mixed", tile=(16, 16), k=4,
+                                                                        overlap=0, seed=2, nu_max=16)),
 ])
 def test_uzawa_f64_matches_the_oracle(api, case):
     """Thirty Uzawa cycles with an FP64 V-cycle: velocity, pressure and the
