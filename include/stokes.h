@@ -157,7 +157,8 @@ typedef struct {
 
 /* Create a context for an nx x ny grid on [0, lx] x [0, ly] computing in `dtype`
  * on `cuda_stream` (a cudaStream_t, NULL for the legacy default stream) of the
- * current device.  nx, ny >= 2; lx, ly > 0.  *out is set on success, NULL
+ * current device.  2 <= nx, ny <= 262144 (larger sides are rejected with
+ * STOKES_ERR_ARG); lx, ly > 0.  *out is set on success, NULL
  * otherwise.  Allocates the library's per-grid buffers.  (Sec. 2.1.) */
 int stokes_create(int nx, int ny, double lx, double ly, int dtype, void *cuda_stream, stokes_ctx **out);
 

@@ -711,7 +711,7 @@ int stokes_create(int nx, int ny, double lx, double ly, int dtype, void *cuda_st
 {
     if (!out) return STOKES_ERR_ARG;
     *out = nullptr;
-    if (nx < 2 || ny < 2 || nx > (1 << 20) || ny > (1 << 20) || !(lx > 0.0) || !(ly > 0.0)) return STOKES_ERR_ARG;
+    if (nx < 2 || ny < 2 || nx > (1 << 18) || ny > (1 << 18) || !(lx > 0.0) || !(ly > 0.0)) return STOKES_ERR_ARG;
     if (dtype != STOKES_F32 && dtype != STOKES_F64) return STOKES_ERR_ARG;
     stokes_ctx *c = new (std::nothrow) stokes_ctx();
     if (!c) return STOKES_ERR_OOM;

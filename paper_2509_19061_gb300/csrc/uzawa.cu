@@ -79,7 +79,7 @@ template <typename T>
 __global__ void k_blend(GridDesc<T> g, T theta, const double *__restrict__ emin, const T *__restrict__ bc,
                         const T *__restrict__ bn, T *__restrict__ oc, T *__restrict__ on)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i > g.nx || j > g.ny) return;
     const size_t q = (size_t)j * g.pitch + i;
     const T base = r_mul(T(1) - theta, (T)emin[0]);
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(UZ_THREADS) k_p_sum(GridDesc<T> g, const T *__
 template <typename T>
 __global__ void k_p_shift(GridDesc<T> g, const double *__restrict__ sum, T *__restrict__ p)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= g.nx || j >= g.ny) return;
     const T mean = (T)(sum[0] / ((double)g.nx * (double)g.ny));
     const size_t q = (size_t)j * g.pitch + i;
@@ -221,6 +221,10 @@ __global__ void k_combine(size_t n, AndersonSet<T> F, AndersonAlpha al, T *__res
 
 int uzawa_partials() { return UZ_BLOCKS; }
 
+namespace {
+inline dim3 grid2(int w, int h) { return dim3((unsigned)((w + 31) / 32), (unsigned)((h + 7) / 8)); }
+} // namespace
+
 template <typename T>
 cudaError_t aa_diff(size_t n, const T *f, const T *x, T *r, cudaStream_t s)
 {
@@ -256,7 +260,7 @@ template <typename T>
 cudaError_t uz_blend(const GridDesc<T> &g, double theta, const double *emin, const T *bc, const T *bn, T *oc, T *on,
                      cudaStream_t s)
 {
-    k_blend<T><<<dim3((g.nx + 1 + 255) / 256, g.ny + 1), 256, 0, s>>>(g, (T)theta, emin, bc, bn, oc, on);
+    k_blend<T><<<grid2(g.nx + 1, g.ny + 1), dim3(32, 8), 0, s>>>(g, (T)theta, emin, bc, bn, oc, on);
     return cudaGetLastError();
 }
 
@@ -266,7 +270,7 @@ cudaError_t uz_pressure_update(const GridDesc<T> &g, double omega_p, const T *ec
 {
     k_p_update<T><<<UZ_BLOCKS, UZ_THREADS, 0, s>>>(g, (T)omega_p, ec, vx, vy, p, partials);
     k_final1<false><<<1, 32, 0, s>>>(partials, UZ_BLOCKS, sum);
-    k_p_shift<T><<<dim3((g.nx + 255) / 256, g.ny), 256, 0, s>>>(g, sum, p);
+    k_p_shift<T><<<grid2(g.nx, g.ny), dim3(32, 8), 0, s>>>(g, sum, p);
     return cudaGetLastError();
 }
 
@@ -277,7 +281,7 @@ cudaError_t uz_lithostatic(const GridDesc<T> &g, double hy, const T *fy, T *p, d
     k_litho<T><<<(g.nx + 127) / 128, 128, 0, s>>>(g, (T)hy, fy, p);
     k_p_sum<T><<<UZ_BLOCKS, UZ_THREADS, 0, s>>>(g, p, partials);
     k_final1<false><<<1, 32, 0, s>>>(partials, UZ_BLOCKS, sum);
-    k_p_shift<T><<<dim3((g.nx + 255) / 256, g.ny), 256, 0, s>>>(g, sum, p);
+    k_p_shift<T><<<grid2(g.nx, g.ny), dim3(32, 8), 0, s>>>(g, sum, p);
     return cudaGetLastError();
 }
 

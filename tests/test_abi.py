@@ -51,6 +51,8 @@ def test_argument_errors_without_device(lib):
     assert out.value is None
     assert f.stokes_create(8, 8, 0.0, 1.0, 1, None, ctypes.byref(out)) == api.STOKES_ERR_ARG
     assert f.stokes_create(8, 8, 1.0, 1.0, 7, None, ctypes.byref(out)) == api.STOKES_ERR_ARG
+    assert f.stokes_create((1 << 18) + 1, 8, 1.0, 1.0, 1, None, ctypes.byref(out)) == api.STOKES_ERR_ARG
+    assert f.stokes_create(8, (1 << 18) + 1, 1.0, 1.0, 1, None, ctypes.byref(out)) == api.STOKES_ERR_ARG
     assert f.stokes_get_layout(None, 0, None, None, None, None) == api.STOKES_ERR_ARG
     assert f.stokes_smooth(None, None, None, None, None) == api.STOKES_ERR_ARG
     assert f.stokes_destroy(None) == api.STOKES_OK

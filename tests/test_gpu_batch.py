@@ -223,3 +223,28 @@ def test_batched_wait_timeout_is_reported_and_recoverable(api):
     torch.cuda.synchronize()
     assert np.all(np.isfinite(e)) and np.all(e[:, 0] < e[:, 1])
     b.close()
+
+
+def test_full_batched_workload_samples_match_single_contexts(api):
+    """The batched workload at full size (256 seeded instances, sides 64 to
+    1024, 4.85e7 cells) in the benchmark's launch configuration (FP32 RAS
+    32 x 32, k = 4, overlap 3, TMA staging): eight sweeps; sampled instances
+    (the smallest, the largest and two others) equal their own contexts bit
+    for bit."""
+    import torch
+    specs = inputs.batch_specs(seed=5, count=256)
+    probs = [inputs.batch_problem(sp) for sp in specs]
+    kw = dict(variant="ras", sweeps=8, tile=(32, 32), k=4, overlap=3, seed=1)
+    b = batch_context(api, probs, "f32")
+    vx, vy = b.slab(), b.slab()
+    b.smooth(vx, vy, None, **kw)
+    torch.cuda.synchronize()
+    sizes = [q.nx for q in probs]
+    sample = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 17, 200})
+    v0 = [(np.zeros((probs[i].ny, probs[i].nx + 1)), np.zeros((probs[i].ny + 1, probs[i].nx))) for i in sample]
+    ref = single_results(api, [probs[i] for i in sample], "f32", v0, None,
+                         lambda c, x, y, pt: c.smooth(x, y, pt, **kw))
+    for r, i in zip(ref, sample):
+        assert np.array_equal(b.unpack(vx, "vx", i), r[0]), i
+        assert np.array_equal(b.unpack(vy, "vy", i), r[1]), i
+    b.close()
