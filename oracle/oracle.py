@@ -420,3 +420,35 @@ def anderson_uzawa(g: Grid, fx, fy, mg: MG, cycles, depth=5, omega_p=0.6, theta_
         rv, rp, ff = energy(g, fx, fy, p, vx, vy)
         hist.append(float(np.sqrt((rv + rp) / ff)))
     return vx, vy, p, np.array(hist)
+
+
+def mg_refine(g: Grid, fx, fy, p, mg: MG, tol, max_cycles, inner_its, vx=None, vy=None):
+    """Defect correction around inner flexible-CG solves (the outer loop of
+    the precision pattern of Sec. 3.2 with FP32 sweeps): r = f - G p - M v;
+    stop when E_v <= tol or max_cycles V-cycles were applied; else solve
+    M e = r approximately by `inner_its` flexible-CG iterations from e = 0,
+    each preconditioned by one V-cycle, and set v += e.  All FP64 here; the
+    library runs the inner iterations in the V-cycle's precision.  Returns
+    (vx, vy, V-cycles, final E_v, history of E_v per outer step)."""
+    vx = g.zeros_vx() if vx is None else _f64(vx).copy()
+    vy = g.zeros_vy() if vy is None else _f64(vy).copy()
+    bx, by = rhs(g, fx, fy, p)
+    dx, dy = diag_M(g)
+    mx = np.zeros_like(dx, dtype=bool)
+    mx[:, 1:g.nx] = True
+    my = np.zeros_like(dy, dtype=bool)
+    my[1:g.ny, :] = True
+    den = np.sum(_f64(fx)[mx] ** 2 / -dx[mx]) + np.sum(_f64(fy)[my] ** 2 / -dy[my])
+    hist, cycles = [], 0
+    while True:
+        ax, ay = apply_M(g, vx, vy)
+        rx = np.where(mx, bx - ax, 0.0)
+        ry = np.where(my, by - ay, 0.0)
+        e = float(np.sqrt((np.sum(rx[mx] ** 2 / -dx[mx]) + np.sum(ry[my] ** 2 / -dy[my])) / den))
+        hist.append(e)
+        if e <= tol or cycles >= max_cycles:
+            return vx, vy, cycles, e, np.array(hist)
+        ex, ey, _, _, _ = mg_fcg(g, rx, ry, None, mg, 0.0, inner_its)
+        vx = vx + ex
+        vy = vy + ey
+        cycles += inner_its

@@ -780,3 +780,21 @@ def test_mixed_smoother_is_jacobi_fine_and_ras_coarse(ora):
     assert not np.array_equal(m3[0], j3[0]) and not np.array_equal(m3[0], r3[0])
     vx, vy, c, fe, hist = ora.mg_solve(g, prob.fx, prob.fy, None, ora.MG(variant=5, **three), 1e-8, 60)
     assert fe <= 1e-8
+
+
+def test_refinement_around_inner_cg_reaches_the_dense_solution(ora):
+    """Defect correction whose correction is a few flexible-CG iterations
+    reaches E_v <= 1e-9 and the dense direct solution; with one inner
+    iteration per outer step it is the flexible CG's first step repeated."""
+    prob = inputs.sinker_problem(32, eta_in=1e3)
+    g = grid_from(ora, prob)
+    mg = ora.MG(variant=4, ti=8, tj=8, k=4, overlap=3, seed=1)
+    vx, vy, c, fe, hist = ora.mg_refine(g, prob.fx, prob.fy, None, mg, 1e-9, 200, 6)
+    assert fe <= 1e-9 and c % 6 == 0
+    dx, dy = ora.dense_solve(g, prob.fx, prob.fy)
+    np.testing.assert_allclose(vx, dx, atol=1e-7 * np.abs(dx).max())
+    np.testing.assert_allclose(vy, dy, atol=1e-7 * np.abs(dy).max())
+    # one outer step with inner_its iterations equals that many FCG iterations
+    a = ora.mg_refine(g, prob.fx, prob.fy, None, mg, 0.0, 6, 6)
+    b = ora.mg_fcg(g, prob.fx, prob.fy, None, mg, 0.0, 6)
+    np.testing.assert_allclose(a[0], b[0], rtol=0, atol=1e-12 * np.abs(b[0]).max())
