@@ -140,8 +140,15 @@ typedef struct {
  *             conjugate gradients (one-term recurrence) with B as the
  *             preconditioner, which keeps converging at high viscosity
  *             contrast where defect correction stagnates.  B is one V-cycle.
+ *             2: defect correction in the context's precision whose correction
+ *             is `inner_its` flexible-CG iterations run entirely in inner_dtype
+ *             (operator, inner products accumulated in FP64, updates), each
+ *             preconditioned by B: the outer residual is formed in the
+ *             context's precision once per `inner_its` V-cycles only.
  * tol         stop when the relative velocity energy residual E_v <= tol.
- * max_cycles  at most this many V-cycles (applications of B). */
+ * max_cycles  at most this many V-cycles (applications of B).
+ * inner_its   flexible-CG iterations per outer step when krylov = 2 (>= 1);
+ *             ignored otherwise.  Not supported by stokes_batch_solve. */
 typedef struct {
     int levels;
     int coarsest;
@@ -153,6 +160,7 @@ typedef struct {
     int krylov;
     double tol;
     int max_cycles;
+    int inner_its;
 } stokes_mg_params;
 
 /* Create a context for an nx x ny grid on [0, lx] x [0, ly] computing in `dtype`

@@ -57,7 +57,7 @@ class stokes_mg_params(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("coarsest", ctypes.c_int), ("nu_pre", ctypes.c_int),
                 ("nu_post", ctypes.c_int), ("nu_growth", ctypes.c_double), ("nu_max", ctypes.c_int),
                 ("inner_dtype", ctypes.c_int), ("smoother", stokes_smooth_params), ("krylov", ctypes.c_int),
-                ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int)]
+                ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int), ("inner_its", ctypes.c_int)]
 
 
 class stokes_uzawa_params(ctypes.Structure):
@@ -188,13 +188,16 @@ def smooth_params(variant="ras", sweeps=1, tile=(32, 32), k=4, overlap=None, ome
 
 
 def mg_params(levels=16, coarsest=16, nu_pre=5, nu_post=5, nu_growth=2.5, nu_max=0, inner="f32", krylov=True,
-              tol=1e-8, max_cycles=100, **smoother):
-    """Build a stokes_mg_params (Sec. 6.2 defaults: 5/5 sweeps, growth 2.5)."""
+              tol=1e-8, max_cycles=100, inner_its=0, **smoother):
+    """Build a stokes_mg_params (Sec. 6.2 defaults: 5/5 sweeps, growth 2.5).
+    krylov: False / True (0 / 1) or 2 (defect correction around inner_its
+    flexible-CG iterations in the inner precision)."""
     smoother.setdefault("variant", "ras")
     sm = smooth_params(**smoother)
     inner_code = STOKES_F64 if inner in ("f64", "float64") else STOKES_F32
-    return stokes_mg_params(levels, coarsest, nu_pre, nu_post, nu_growth, nu_max, inner_code, sm,
-                            1 if krylov else 0, tol, max_cycles)
+    kr = int(krylov) if not isinstance(krylov, bool) else (1 if krylov else 0)
+    return stokes_mg_params(levels, coarsest, nu_pre, nu_post, nu_growth, nu_max, inner_code, sm, kr, tol,
+                            max_cycles, inner_its)
 
 
 def stokes_smooth(ctx, vx, vy, p, params):

@@ -151,6 +151,18 @@ __global__ void __launch_bounds__(RD_THREADS) k_apply_dot(GridDesc<T> g, const T
     block_store2(s0, s1, partials);
 }
 
+// v += (To) e at the unknowns
+template <typename To, typename Ti>
+__global__ void __launch_bounds__(RD_THREADS) k_add_cast(int nx, int ny, int pitch, const Ti *__restrict__ ex,
+                                                         const Ti *__restrict__ ey, To *__restrict__ vx,
+                                                         To *__restrict__ vy)
+{
+    for_unknowns(nx, ny, pitch, [&](size_t q, int comp) {
+        To *v = comp ? vy : vx;
+        v[q] = r_add(v[q], (To)(comp ? ey : ex)[q]);
+    });
+}
+
 __global__ void k_final2(const double *__restrict__ partials, int nblocks, double *__restrict__ out)
 {
     const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -214,6 +226,21 @@ cudaError_t kry_add(const KrylovView &k, const T *zx, const T *zy, T *vx, T *vy,
     k_add<T><<<RD_BLOCKS, RD_THREADS, 0, s>>>(k.nx, k.ny, k.pitch, zx, zy, vx, vy);
     return cudaGetLastError();
 }
+
+template <typename To, typename Ti>
+cudaError_t kry_add_cast(const KrylovView &k, const Ti *ex, const Ti *ey, To *vx, To *vy, cudaStream_t s)
+{
+    k_add_cast<To, Ti><<<RD_BLOCKS, RD_THREADS, 0, s>>>(k.nx, k.ny, k.pitch, ex, ey, vx, vy);
+    return cudaGetLastError();
+}
+template cudaError_t kry_add_cast<double, float>(const KrylovView &, const float *, const float *, double *, double *,
+                                                 cudaStream_t);
+template cudaError_t kry_add_cast<double, double>(const KrylovView &, const double *, const double *, double *,
+                                                  double *, cudaStream_t);
+template cudaError_t kry_add_cast<float, float>(const KrylovView &, const float *, const float *, float *, float *,
+                                                cudaStream_t);
+template cudaError_t kry_add_cast<float, double>(const KrylovView &, const double *, const double *, float *,
+                                                 float *, cudaStream_t);
 
 #define INST(T)                                                                                                    \
     template cudaError_t kry_dot2<T>(const KrylovView &, const T *, const T *, const T *, const T *, const T *,    \

@@ -262,6 +262,8 @@ void mg_destroy(MgHierarchy *h)
 
 int mg_levels(const MgHierarchy *h) { return h ? h->L : 0; }
 
+const MgLevel &mg_level(const MgHierarchy *h, int l) { return h->lv[l]; }
+
 int mg_ensure(MgHierarchy **hp, const MgOuter &o, const stokes_mg_params *p, cudaStream_t s)
 {
     if (!*hp) {

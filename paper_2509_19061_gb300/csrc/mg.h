@@ -38,8 +38,9 @@ void mg_destroy(MgHierarchy *h);
 // dense solve, STOKES_ERR_DIVERGED if its matrix is not positive definite).
 int mg_ensure(MgHierarchy **h, const MgOuter &o, const stokes_mg_params *params, cudaStream_t s);
 
-// Number of levels of a built hierarchy.
+// Number of levels of a built hierarchy, and level l of it.
 int mg_levels(const MgHierarchy *h);
+const MgLevel &mg_level(const MgHierarchy *h, int l);
 
 // Enqueue one application of the preconditioner z = B r on `s`: r (outer
 // precision `outer_dtype`, zero off the unknowns) is cast to the inner
@@ -73,6 +74,8 @@ template <typename T> // p = z + beta p
 cudaError_t kry_direction(const KrylovView &k, double beta, const T *zx, const T *zy, T *px, T *py, cudaStream_t s);
 template <typename T> // v += z
 cudaError_t kry_add(const KrylovView &k, const T *zx, const T *zy, T *vx, T *vy, cudaStream_t s);
+template <typename To, typename Ti> // v += (To) e at the unknowns
+cudaError_t kry_add_cast(const KrylovView &k, const Ti *ex, const Ti *ey, To *vx, To *vy, cudaStream_t s);
 
 // The smoother of level l (STOKES_MIXED: Jacobi on level 0, RAS below).
 stokes_smooth_params level_smoother(const stokes_smooth_params &sm, int level);

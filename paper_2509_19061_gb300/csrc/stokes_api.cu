@@ -83,6 +83,8 @@ struct stokes_ctx {
     // outer solve: work vectors r, z, p, q (x and y each), reduction buffers,
     // and the preconditioner z = B r as a CUDA graph replayed on gstream
     void *kw[8] = {};
+    void *iw[10] = {};                   // inner-precision r, z, p, q, e (x, y) of the refinement mode
+    int iw_dtype = -1;
     double *kpartials = nullptr, *kout = nullptr, *hout = nullptr;
     cudaStream_t gstream = nullptr;
     cudaEvent_t gev[2] = {nullptr, nullptr};
@@ -284,7 +286,8 @@ int check_mg_params(const stokes_ctx *c, const stokes_mg_params *p)
         p->nu_max < 0 || p->max_cycles < 0 || !(p->tol >= 0.0))
         return STOKES_ERR_ARG;
     if (p->inner_dtype != STOKES_F32 && p->inner_dtype != STOKES_F64) return STOKES_ERR_ARG;
-    if (p->krylov != 0 && p->krylov != 1) return STOKES_ERR_ARG;
+    if (p->krylov < 0 || p->krylov > 2) return STOKES_ERR_ARG;
+    if (p->krylov == 2 && p->inner_its < 1) return STOKES_ERR_ARG;
     stokes_smooth_params sm = p->smoother;
     sm.sweeps = 0;
     sm.shift_mode = STOKES_SHIFT_SPLITMIX;
@@ -325,10 +328,34 @@ int ensure_work(stokes_ctx *c)
     return STOKES_OK;
 }
 
-// (Re)capture the preconditioner z = B r (fixed work buffers) for these parameters.
+// Inner-precision work vectors of the refinement mode (krylov = 2).
+int ensure_inner_work(stokes_ctx *c, int dtype)
+{
+    if (c->iw[0] && c->iw_dtype == dtype) return STOKES_OK;
+    for (void *&w : c->iw)
+        if (w) {
+            cudaFree(w);
+            w = nullptr;
+        }
+    const size_t es = dtype == STOKES_F64 ? 8 : 4;
+    for (void *&w : c->iw) {
+        CK(cudaMalloc(&w, c->elems * es));
+        CK(cudaMemsetAsync(w, 0, c->elems * es, c->stream));
+    }
+    c->iw_dtype = dtype;
+    return STOKES_OK;
+}
+
+// (Re)capture the preconditioner z = B r (fixed work buffers) for these
+// parameters: on the outer work vectors, or on the inner-precision ones in
+// the refinement mode.
 int ensure_graph(stokes_ctx *c, const stokes_mg_params *p)
 {
     if (c->gexec && std::memcmp(p, c->gkey, sizeof *p) == 0) return STOKES_OK;
+    if (p->krylov == 2) {
+        const int st = ensure_inner_work(c, p->inner_dtype);
+        if (st != STOKES_OK) return st;
+    }
     if (c->gexec) {
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
@@ -341,8 +368,10 @@ int ensure_graph(stokes_ctx *c, const stokes_mg_params *p)
     CountHook hook;
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
-    const int st = mg_enqueue_precond(c->mg, c->dtype, c->kw[0], c->kw[1], c->kw[2], c->kw[3], p, run_opts(c),
-                                      c->gstream, hook);
+    const bool inner = p->krylov == 2;
+    const int st = mg_enqueue_precond(c->mg, inner ? p->inner_dtype : c->dtype, inner ? c->iw[0] : c->kw[0],
+                                      inner ? c->iw[1] : c->kw[1], inner ? c->iw[2] : c->kw[2],
+                                      inner ? c->iw[3] : c->kw[3], p, run_opts(c), c->gstream, hook);
     const cudaError_t e = cudaStreamEndCapture(c->gstream, &graph);
     if (st != STOKES_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -429,7 +458,57 @@ int vcycle_impl(stokes_ctx *c, T *vx, T *vy, const T *p, const stokes_mg_params 
         return 0;
     };
     int verdict = check();
-    if (params->krylov && verdict == 0) {
+    if (params->krylov == 2) {
+        // defect correction around inner-precision flexible CG
+        auto refine = [&](auto tag) -> int {
+            using Ti = decltype(tag);
+            Ti *w[10];
+            for (int q = 0; q < 10; ++q) w[q] = (Ti *)c->iw[q];
+            Ti *rix = w[0], *riy = w[1], *zix = w[2], *ziy = w[3], *pix = w[4], *piy = w[5], *qix = w[6],
+               *qiy = w[7], *eix = w[8], *eiy = w[9];
+            const MgLevel &l0 = mg_level(c->mg, 0);
+            const GridDesc<Ti> gi = make_grid<Ti>(l0.nx, l0.ny, l0.pitch, l0.hx, l0.hy);
+            const Ti *ixi = (const Ti *)l0.ivx, *iyi = (const Ti *)l0.ivy;
+            const size_t ib = c->elems * sizeof(Ti);
+            while (verdict == 0) {
+                RUN(STOKES_K_MG, 1, (mg_cast<T, Ti>(c->elems, rx, rix, c->stream)));
+                RUN(STOKES_K_MG, 1, (mg_cast<T, Ti>(c->elems, ry, riy, c->stream)));
+                CK(cudaMemsetAsync(eix, 0, ib, c->stream));
+                CK(cudaMemsetAsync(eiy, 0, ib, c->stream));
+                int st2 = replay_graph(c);
+                if (st2 != STOKES_OK) return st2;
+                CK(cudaMemcpyAsync(pix, zix, ib, cudaMemcpyDeviceToDevice, c->stream));
+                CK(cudaMemcpyAsync(piy, ziy, ib, cudaMemcpyDeviceToDevice, c->stream));
+                for (int k = 0; k < params->inner_its; ++k) {
+                    RUN(STOKES_K_APPLY, 2,
+                        kry_apply_dot<Ti>(kv, gi, (const Ti *)l0.ec, (const Ti *)l0.en, pix, piy, qix, qiy, rix, riy,
+                                          c->stream));
+                    double pq = 0.0, pr = 0.0;
+                    if ((st2 = read2(c, &pq, &pr)) != STOKES_OK) return st2;
+                    RUN(STOKES_K_MG, 2,
+                        kry_update<Ti>(kv, pr / pq, pix, piy, qix, qiy, eix, eiy, rix, riy, ixi, iyi, c->stream));
+                    if (k == params->inner_its - 1) break;
+                    if ((st2 = replay_graph(c)) != STOKES_OK) return st2;
+                    RUN(STOKES_K_MG, 2,
+                        kry_dot2<Ti>(kv, zix, ziy, qix, qiy, (const Ti *)nullptr, (const Ti *)nullptr, c->stream));
+                    double zq = 0.0;
+                    if ((st2 = read2(c, &zq, nullptr)) != STOKES_OK) return st2;
+                    RUN(STOKES_K_MG, 1, kry_direction<Ti>(kv, -zq / pq, zix, ziy, pix, piy, c->stream));
+                }
+                RUN(STOKES_K_MG, 1, (kry_add_cast<T, Ti>(kv, eix, eiy, vx, vy, c->stream)));
+                it += params->inner_its;
+                RUN(STOKES_K_MG, 1, mg_residual<T>(top, c->stream));
+                RUN(STOKES_K_ENERGY, 2,
+                    kry_energy<T>(kv, rx, ry, (const T *)c->fx, (const T *)c->fy, ix, iy, c->stream));
+                if ((st2 = read2(c, &num, nullptr)) != STOKES_OK) return st2;
+                e = std::sqrt(num / den);
+                verdict = check();
+            }
+            return STOKES_OK;
+        };
+        st = params->inner_dtype == STOKES_F64 ? refine(double{}) : refine(float{});
+        if (st != STOKES_OK) return st;
+    } else if (params->krylov && verdict == 0) {
         st = replay_graph(c);
         if (st != STOKES_OK) return st;
         CK(cudaMemcpyAsync(px, zx, c->elems * c->esize, cudaMemcpyDeviceToDevice, c->stream));
@@ -760,6 +839,8 @@ int stokes_destroy(stokes_ctx *c)
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->gstream) cudaStreamSynchronize(c->gstream);
     for (void *w : c->kw)
+        if (w) cudaFree(w);
+    for (void *w : c->iw)
         if (w) cudaFree(w);
     if (c->kpartials) cudaFree(c->kpartials);
     if (c->kout) cudaFree(c->kout);

@@ -131,3 +131,34 @@ def test_multigrid_errors(api):
         ctx.vcycle(vx, vy, variant="fused")
     assert ex.value.status == api.STOKES_ERR_STATE
     ctx.close()
+
+
+def test_refinement_f64_matches_the_oracle(api):
+    """krylov = 2 with an FP64 inner precision: two outer defect-correction
+    steps, each three flexible-CG iterations preconditioned by the V-cycle,
+    match the oracle's refinement loop."""
+    prob = inputs.sinker_problem(96, 64, eta_in=1e3, lx=1.0, ly=64 / 96)
+    kw = dict(variant="ras", tile=(16, 16), k=4, overlap=3, seed=3, nu_max=20)
+    st, e, c, v = run_solve(api, prob, "f64", 6, inner="f64", krylov=2, inner_its=3, **kw)
+    assert st == api.STOKES_ERR_NOT_CONVERGED and c == 6
+    m = ora.MG(variant=4, ti=16, tj=16, k=4, overlap=3, seed=3, nu_max=20)
+    rx, ry, rc, re, rh = ora.mg_refine(ogrid(prob), prob.fx, prob.fy, None, m, 0.0, 6, 3)
+    assert rel(v, (rx, ry)) <= 1e-10
+    assert abs(e - re) <= 1e-8 * re
+
+
+def test_refinement_fp32_inner_reaches_1e8(api):
+    """FP32 inner flexible CG (operator, updates and the V-cycle in FP32)
+    inside FP64 defect correction reaches E_v <= 1e-8 on the 1e6-contrast
+    multi-sinker and lands on the oracle's converged solution."""
+    prob = inputs.multi_sinker(128, seed=3)
+    kw = dict(variant="ras", tile=(32, 32), k=4, overlap=3, nu_max=40, seed=1)
+    st, e, c, v = run_solve(api, prob, "f64", 120, tol=1e-8, inner="f32", krylov=2, inner_its=8, **kw)
+    assert st == api.STOKES_OK and e <= 1e-8, (st, e, c)
+    ref = oracle_solve(prob, 120, tol=1e-10, krylov=True, **kw)
+    g = ogrid(prob)
+    dx, dy = ora.diag_M(g)
+    num = np.sum(-dx * (v[0] - ref[0]) ** 2) + np.sum(-dy * (v[1] - ref[1]) ** 2)
+    den = np.sum(-dx * ref[0] ** 2) + np.sum(-dy * ref[1] ** 2)
+    print("refinement, fp32 inner: %d V-cycles, E_v %.2e, energy error %.2e" % (c, e, np.sqrt(num / den)))
+    assert np.sqrt(num / den) <= 1e-6
