@@ -283,11 +283,18 @@ typedef enum {
                                         tensor copies in a persistent kernel when the window fits;
                                         0: they read windows straight from global memory.  The
                                         results are identical either way. */
-    STOKES_OPT_WAIT_LIMIT_CYCLES = 1 /* SM clock cycles a device-side wait for a staged window may
+    STOKES_OPT_WAIT_LIMIT_CYCLES = 1, /* SM clock cycles a device-side wait for a staged window may
                                         take before the kernel gives up, records STOKES_ERR_TIMEOUT
                                         and exits (default 2e9, about one second; 0 = one try;
                                         negative = give up at once, which tests use to exercise the
                                         timeout path). */
+    STOKES_OPT_PAIRED = 2            /* 1 (default): FP32 tile windows of 49 to 64 columns run the
+                                        packed-pair kernel (two columns per thread, paired FP32
+                                        instructions); 2: every FP32 window of at most 64 columns
+                                        does; 0: never (one column per thread).  Needs
+                                        STOKES_OPT_USE_TMA; the results are identical either way
+                                        (up to the sign of exact zeros).  Other values:
+                                        STOKES_ERR_ARG. */
 } stokes_option;
 
 int stokes_set_option(stokes_ctx *ctx, int option, long long value);
@@ -321,6 +328,23 @@ typedef enum {
  * NULL). */
 int stokes_profile_reset(stokes_ctx *ctx, int enable_timing);
 int stokes_profile_read(stokes_ctx *ctx, int kind, long long *kernels, long long *groups, double *total_ms);
+
+/* Which tile kernel a RAS / blocked-Jacobi launch of this grid, tile and
+ * overlap uses (Sec. 4.3: the window is the tile grown by overlap + 1), with
+ * the given STOKES_OPT_USE_TMA (0/1) and STOKES_OPT_PAIRED (0/1/2) values: *kernel gets a
+ * stokes_tile_kernel value, *threads the CTA size, *smem_bytes the dynamic
+ * shared memory (outputs may be NULL).  Diagnostic only; reads the current
+ * device's shared-memory limit.  STOKES_ERR_ARG on sizes < 1, overlap < 0, a
+ * bad dtype or pair mode; STOKES_ERR_CUDA without a device. */
+typedef enum {
+    STOKES_TILE_TMA = 0,    /* persistent, TMA-staged window, one column per thread */
+    STOKES_TILE_GLOBAL = 1, /* one CTA per tile, window read from global memory */
+    STOKES_TILE_SHARED = 2, /* general kernel, every field of the window in shared memory */
+    STOKES_TILE_PAIR = 3    /* persistent, TMA-staged, two columns per thread, paired FP32 instructions */
+} stokes_tile_kernel;
+
+int stokes_tile_kernel_plan(int nx, int ny, int ti, int tj, int overlap, int dtype, int use_tma, int pair_mode,
+                            int *kernel, int *threads, size_t *smem_bytes);
 
 /* Energy residual sums without allocating.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc, for instance

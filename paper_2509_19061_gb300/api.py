@@ -30,7 +30,7 @@ STOKES_F32, STOKES_F64 = 0, 1
 STOKES_JACOBI, STOKES_JACOBI_FUSED, STOKES_JACOBI_BLOCKED, STOKES_RBGS, STOKES_RAS, STOKES_MIXED = 0, 1, 2, 3, 4, 5
 STOKES_FIELD_VX, STOKES_FIELD_VY, STOKES_FIELD_P, STOKES_FIELD_ETA_C, STOKES_FIELD_ETA_N = 0, 1, 2, 3, 4
 STOKES_SHIFT_NONE, STOKES_SHIFT_SPLITMIX, STOKES_SHIFT_LIST = 0, 1, 2
-STOKES_OPT_USE_TMA, STOKES_OPT_WAIT_LIMIT_CYCLES = 0, 1
+STOKES_OPT_USE_TMA, STOKES_OPT_WAIT_LIMIT_CYCLES, STOKES_OPT_PAIRED = 0, 1, 2
 KERNEL_CLASSES = ["ras", "jacobi", "rbgs", "rhs", "energy", "copy", "apply", "mg"]
 
 VARIANTS = {"jacobi": STOKES_JACOBI, "fused": STOKES_JACOBI_FUSED, "blocked": STOKES_JACOBI_BLOCKED,
@@ -82,6 +82,8 @@ _SIGS = {
                           ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "stokes_set_option": (_I, [_VP, _I, ctypes.c_longlong]),
     "stokes_synchronize": (_I, [_VP]),
+    "stokes_tile_kernel_plan": (_I, [_I, _I, _I, _I, _I, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                     ctypes.POINTER(ctypes.c_size_t)]),
     "stokes_profile_reset": (_I, [_VP, _I]),
     "stokes_profile_read": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(_D)]),
@@ -249,6 +251,19 @@ def stokes_set_option(ctx, option, value):
 
 def stokes_synchronize(ctx):
     _check(_lib().stokes_synchronize(ctx), "stokes_synchronize")
+
+
+TILE_KERNELS = {0: "tma", 1: "global", 2: "shared", 3: "pair"}
+
+
+def stokes_tile_kernel_plan(nx, ny, tile, overlap, dtype="f32", use_tma=True, pair_mode=1):
+    """(kernel name, CTA threads, dynamic shared bytes) of a tile-smoother launch."""
+    kern, thr, smem = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+    code = STOKES_F64 if dtype in ("f64", "float64") else STOKES_F32
+    _check(_lib().stokes_tile_kernel_plan(nx, ny, tile[0], tile[1], overlap, code, 1 if use_tma else 0,
+                                          int(pair_mode), ctypes.byref(kern), ctypes.byref(thr),
+                                          ctypes.byref(smem)), "stokes_tile_kernel_plan")
+    return TILE_KERNELS[kern.value], thr.value, smem.value
 
 
 def stokes_profile_reset(ctx, enable_timing):

@@ -335,6 +335,7 @@ struct stokes_batch {
     void *kw[8] = {};               // outer work r, z, p, q (x, y)
     int *dstatus = nullptr, *hstatus = nullptr; // bounded-wait status word
     bool use_tma = true;            // STOKES_OPT_USE_TMA
+    int pair_mode = 1;              // STOKES_OPT_PAIRED
     long long wait_limit = 2000000000LL;
     BHier *mg = nullptr;
     Owned base;                     // tables tied to the batch itself
@@ -367,6 +368,7 @@ RasRun run_of(const stokes_batch *b)
 {
     RasRun r;
     r.allow_tma = b->use_tma;
+    r.pair_mode = b->pair_mode;
     r.status = b->dstatus;
     r.wait_limit = b->wait_limit;
     return r;
@@ -1247,7 +1249,9 @@ int stokes_batch_set_option(stokes_batch *b, int option, long long value)
     switch (option) {
     case STOKES_OPT_USE_TMA:
     case STOKES_OPT_WAIT_LIMIT_CYCLES:
-        // plans and the captured graph embed both: rebuild them
+    case STOKES_OPT_PAIRED:
+        if (option == STOKES_OPT_PAIRED && (value < 0 || value > 2)) return STOKES_ERR_ARG;
+        // plans and the captured graph embed these: rebuild them
         CK(cudaStreamSynchronize(b->stream));
         if (b->gexec) {
             cudaGraphExecDestroy(b->gexec);
@@ -1257,6 +1261,7 @@ int stokes_batch_set_option(stokes_batch *b, int option, long long value)
         b->sm_own.release();
         b->sm_valid = false;
         if (option == STOKES_OPT_USE_TMA) b->use_tma = value != 0;
+        else if (option == STOKES_OPT_PAIRED) b->pair_mode = (int)value;
         else b->wait_limit = value;
         return STOKES_OK;
     default: return STOKES_ERR_ARG;

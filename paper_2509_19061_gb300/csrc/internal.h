@@ -98,6 +98,7 @@ TileGrid make_tiles(int nx, int ny, int ti, int tj, int si, int sj);
 // Per-launch options of the tile kernels.
 struct RasRun {
     bool allow_tma;        // use the persistent TMA-staged kernel when the window fits
+    int pair_mode = 1;     // FP32 packed-pair TMA kernel: 0 never, 1 windows of 49-64 columns, 2 any window <= 64
     int *status;           // device word set to 1 when a bounded wait gives up
     long long wait_limit;  // SM cycles a wait may take
 };
@@ -108,6 +109,9 @@ cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const 
                        int overlap, const T *vx, const T *vy, T *ox, T *oy, const RasRun &run, cudaStream_t s);
 // shared memory a RAS launch needs for this grid, tile and overlap
 size_t ras_smem_bytes(int nx, int ny, int ti, int tj, int overlap, size_t elem);
+// the tile kernel (stokes_tile_kernel value), CTA size and dynamic shared memory of a launch
+void ras_kernel_plan(int nx, int ny, int ti, int tj, int overlap, size_t elem, bool allow_tma, int pair_mode,
+                     int *kind, int *threads, size_t *smem);
 
 // One instance's share of a batched tile launch: its grid, coefficients,
 // snapshot (vx, vy) -> output (ox, oy), tiling, and the index of its first

@@ -424,6 +424,311 @@ __global__ void __launch_bounds__(MAXT, MINB) k_ras_tma(const __grid_constant__ 
 }
 
 // ---------------------------------------------------------------------------
+// packed-pair FP32 kernel
+// ---------------------------------------------------------------------------
+// sm_100-class GPUs execute two FP32 additions, multiplications or fused
+// multiply-adds of one thread as one instruction on a 64-bit register pair
+// (add/sub/mul/fma.rn.f32x2).  Each lane of this kernel owns two adjacent
+// window columns (c0 = 2 lane, c1 = c0 + 1) of PR rows, so every stencil
+// operation of stencil.cuh runs once per column pair, lane for lane the same
+// rounded operation: the results are those of the scalar kernels, bit for bit
+// up to the sign of exact zeros.
+// One warp spans a whole window row strip (up to 64 columns): horizontal
+// neighbours come from the neighbouring lane by shuffles, and the only
+// shared-memory traffic of a sweep is the first and last row of each strip.
+// A strip computes the two neighbour fluxes it needs (Tyy of the row above
+// it, the shear of the row below it) from those rows itself, so a sweep
+// needs one barrier, with the edge rows double-buffered by sweep parity.
+// Window columns 64 and -1 do not exist: the shuffles of lanes 31 and 0 then
+// return the lane's own value, which only reaches the fluxes of the window's
+// ring cells (never updated: weight 0) and stays finite.
+struct f2 {
+    unsigned long long u;
+};
+__device__ __forceinline__ f2 pk(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.u) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float f2lo(f2 a)
+{
+    float x, y;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.u));
+    return x;
+}
+__device__ __forceinline__ float f2hi(f2 a)
+{
+    float x, y;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.u));
+    return y;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.u) : "l"(a.u), "l"(b.u));
+    return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.u) : "l"(a.u), "l"(b.u));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.u) : "l"(a.u), "l"(b.u));
+    return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.u) : "l"(a.u), "l"(b.u), "l"(c.u));
+    return r;
+}
+// a * b rounded once and never fused into a following addition: the code
+// generator contracts mul.rn.f32x2 followed by add/sub.rn.f32x2 into one
+// fused multiply-add despite the rounding modifier (measured: a packed
+// product minus a nearly equal value differs from the scalar rounded
+// sequence in almost every case), so the product is formed as
+// fma(a, b, +0), which rounds a * b once and is not contracted.  Its only
+// difference from a plain product is the sign of an exact zero (+0 for -0).
+__device__ __forceinline__ f2 mul2r(f2 a, f2 b)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.u) : "l"(a.u), "l"(b.u), "l"(0ull));
+    return r;
+}
+// (x(c0 - 1), x(c0)) and (x(c1), x(c1 + 1)) of a pair (x(c0), x(c1))
+__device__ __forceinline__ f2 west_pair(f2 a) { return pk(__shfl_up_sync(0xffffffffu, f2hi(a), 1), f2lo(a)); }
+__device__ __forceinline__ f2 east_pair(f2 a) { return pk(f2hi(a), __shfl_down_sync(0xffffffffu, f2lo(a), 1)); }
+
+constexpr int PR = 4;          // rows per lane
+constexpr int PAIR_COLS = 64;  // window columns of one warp
+constexpr int PAIR_EDGE_KINDS = 4; // first-row vx, first-row vy, last-row vx, last-row vy
+
+struct PairCells {
+    f2 vx[PR], vy[PR], ax[PR], ay[PR], en[PR], bx[PR], by[PR], wx[PR], wy[PR];
+    f2 en_below, ay_above; // eta_n of the next strip's first row, ay of the previous strip's last row
+    unsigned ux, uy;       // bit 2 r + h: cell (row r, column c0 + h) is a vx / vy unknown inside the ring
+};
+
+// fluxes of one row pair
+struct PairFlux {
+    f2 txx, tyy, sx, sy;
+};
+
+// Cell fields of one window cell from the staged boxes (zero outside the
+// window), in the form setup_cells uses.
+struct PairCell {
+    float vx, vy, ec, en, bx, by, wx, wy;
+    bool ux, uy;
+};
+
+template <class LD>
+__device__ __forceinline__ PairCell pair_cell(const RasArgs<float> &a, const Window &w, int wy, int col, LD &&ld)
+{
+    const GridDesc<float> &g = a.g;
+    PairCell p = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, false, false};
+    if (wy < 0 || wy >= w.WY || col >= w.WX) return p;
+    const int gx = w.ox0 + col, gy = w.oy0 + wy;
+    p.vx = ld(0, wy, col);
+    p.vy = ld(1, wy, col);
+    p.ec = ld(2, wy, col);
+    p.en = ld(3, wy, col);
+    p.bx = ld(4, wy, col);
+    p.by = ld(5, wy, col);
+    const bool inner = col >= 1 && col < w.WX - 1 && wy >= 1 && wy < w.WY - 1;
+    if (inner && gy >= 0 && gy < g.ny && gx >= 1 && gx <= g.nx - 1) {
+        p.ux = true;
+        p.wx = jacobi_weight(a.omega, ld(6, wy, col));
+    }
+    if (inner && gx >= 0 && gx < g.nx && gy >= 1 && gy <= g.ny - 1) {
+        p.uy = true;
+        p.wy = jacobi_weight(a.omega, ld(7, wy, col));
+    }
+    return p;
+}
+
+template <class LD>
+__device__ __forceinline__ void pair_setup(const RasArgs<float> &a, const Window &w, PairCells &c, int lane, int strip,
+                                           LD &&ld)
+{
+    const GridDesc<float> &g = a.g;
+    const int c0 = 2 * lane;
+    c.ux = 0;
+    c.uy = 0;
+#pragma unroll
+    for (int r = 0; r < PR; ++r) {
+        const int wy = strip * PR + r;
+        const PairCell p0 = pair_cell(a, w, wy, c0, ld), p1 = pair_cell(a, w, wy, c0 + 1, ld);
+        c.vx[r] = pk(p0.vx, p1.vx);
+        c.vy[r] = pk(p0.vy, p1.vy);
+        c.ax[r] = pk(coef_x(g, p0.ec), coef_x(g, p1.ec));
+        c.ay[r] = pk(coef_y(g, p0.ec), coef_y(g, p1.ec));
+        c.en[r] = pk(p0.en, p1.en);
+        c.bx[r] = pk(p0.bx, p1.bx);
+        c.by[r] = pk(p0.by, p1.by);
+        c.wx[r] = pk(p0.wx, p1.wx);
+        c.wy[r] = pk(p0.wy, p1.wy);
+        c.ux |= (p0.ux ? 1u : 0u) << (2 * r) | (p1.ux ? 1u : 0u) << (2 * r + 1);
+        c.uy |= (p0.uy ? 1u : 0u) << (2 * r) | (p1.uy ? 1u : 0u) << (2 * r + 1);
+    }
+    // eta_c of the row above the strip and eta_n of the row below it
+    const int above = strip * PR - 1, below = strip * PR + PR;
+    float ea[2], nb[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const bool col_in = c0 + h < w.WX;
+        ea[h] = col_in && above >= 0 ? ld(2, above, c0 + h) : 0.f;
+        nb[h] = col_in && below < w.WY ? ld(3, below, c0 + h) : 0.f;
+    }
+    c.ay_above = pk(coef_y(g, ea[0]), coef_y(g, ea[1]));
+    c.en_below = pk(nb[0], nb[1]);
+}
+
+// fluxes of row r: Txx, Tyy, Sx, Sy (vy_n: the vy pair of the row below r,
+// vx_s: the vx pair of the row above it, both before this sweep)
+__device__ __forceinline__ PairFlux pair_flux(f2 ax, f2 ay, f2 en, f2 vx, f2 vy, f2 vy_n, f2 vx_s, f2 ihx, f2 ihy)
+{
+    PairFlux F;
+    F.txx = mul2r(ax, sub2(east_pair(vx), vx));
+    F.tyy = mul2r(ay, sub2(vy_n, vy));
+    const f2 sh = mul2(en, fma2(sub2(vx, vx_s), ihy, mul2(sub2(vy, west_pair(vy)), ihx)));
+    F.sx = mul2r(sh, ihy);
+    F.sy = mul2r(sh, ihx);
+    return F;
+}
+
+// ks local sweeps of the window in registers, then the write-back of the
+// tile's own unknowns.  Ends with a barrier.  edge: [buffer][kind][strip + 1]
+// [lane] pairs, strips -1 and ns all zero.
+__device__ __forceinline__ void pair_sweeps(const RasArgs<float> &a, const Window &w, PairCells &c, int lane, int strip,
+                                            f2 *edge, int es)
+{
+    const GridDesc<float> &g = a.g;
+    const f2 ihx = pk(g.ihx, g.ihx), ihy = pk(g.ihy, g.ihy);
+    auto E = [&](int buf, int kind, int s) -> f2 & {
+        return edge[((buf * PAIR_EDGE_KINDS + kind) * es + s + 1) * 32 + lane];
+    };
+    for (int s = 1; s <= a.ks; ++s) {
+        const int rb = (s - 1) & 1, wb = rb ^ 1;
+        const f2 vx_above = E(rb, 2, strip - 1), vy_above = E(rb, 3, strip - 1);
+        const f2 vx_below = E(rb, 0, strip + 1), vy_below = E(rb, 1, strip + 1);
+        // Tyy of the row above the strip and Sx of the row below it
+        const f2 tyy_above = mul2r(c.ay_above, sub2(c.vy[0], vy_above));
+        const f2 sh_below = mul2(c.en_below, fma2(sub2(vx_below, c.vx[PR - 1]), ihy,
+                                                  mul2(sub2(vy_below, west_pair(vy_below)), ihx)));
+        const f2 sx_below = mul2r(sh_below, ihy);
+        PairFlux F0 = pair_flux(c.ax[0], c.ay[0], c.en[0], c.vx[0], c.vy[0], PR > 1 ? c.vy[1] : vy_below, vx_above,
+                                ihx, ihy);
+        f2 tyy_s = tyy_above;
+#pragma unroll
+        for (int r = 0; r < PR; ++r) {
+            // fluxes of row r + 1 read the old vx of row r: form them before row r moves
+            PairFlux F1 = F0;
+            if (r + 1 < PR)
+                F1 = pair_flux(c.ax[r + 1], c.ay[r + 1], c.en[r + 1], c.vx[r + 1], c.vy[r + 1],
+                               r + 2 < PR ? c.vy[r + 2] : vy_below, c.vx[r], ihx, ihy);
+            const f2 sx_n = r + 1 < PR ? F1.sx : sx_below;
+            const f2 mx = add2(sub2(F0.txx, west_pair(F0.txx)), sub2(sx_n, F0.sx));
+            const f2 my = add2(sub2(east_pair(F0.sy), F0.sy), sub2(F0.tyy, tyy_s));
+            c.vx[r] = fma2(sub2(c.bx[r], mx), c.wx[r], c.vx[r]);
+            c.vy[r] = fma2(sub2(c.by[r], my), c.wy[r], c.vy[r]);
+            tyy_s = F0.tyy;
+            F0 = F1;
+        }
+        E(wb, 0, strip) = c.vx[0];
+        E(wb, 1, strip) = c.vy[0];
+        E(wb, 2, strip) = c.vx[PR - 1];
+        E(wb, 3, strip) = c.vy[PR - 1];
+        __syncthreads();
+    }
+    // ---- write back the unknowns of the tile's own cells
+    const size_t P = (size_t)g.pitch;
+#pragma unroll
+    for (int r = 0; r < PR; ++r) {
+        const int gy = w.oy0 + strip * PR + r;
+        if (gy < w.y0 || gy >= w.y1) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int gx = w.ox0 + 2 * lane + h;
+            if (gx < w.x0 || gx >= w.x1) continue;
+            const size_t q = (size_t)gy * P + (size_t)gx;
+            const unsigned bit = 1u << (2 * r + h);
+            if (c.ux & bit) a.ox[q] = h ? f2hi(c.vx[r]) : f2lo(c.vx[r]);
+            if (c.uy & bit) a.oy[q] = h ? f2hi(c.vy[r]) : f2lo(c.vy[r]);
+        }
+    }
+}
+
+// Persistent TMA-staged kernel of the pair layout: one warp per strip of PR
+// window rows, a.strips warps; the staging and the timeout handling are
+// those of k_ras_tma.
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_ras_pair(const __grid_constant__ TmaMaps maps, RasArgs<float> a)
+{
+    constexpr int NF = 8;
+    constexpr int ALIGN = 4; // TMA x coordinates are multiples of 16 bytes
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t off = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
+    float *const stage = reinterpret_cast<float *>(smem_raw + off);
+    const int BW = a.bw, SP = a.stage;
+    const int es = a.strips + 2;
+    f2 *const edge = reinterpret_cast<f2 *>(stage + NF * SP);
+    const int ntiles = a.tg.ntx * a.tg.nty;
+    const int lane = (int)threadIdx.x & 31, strip = (int)threadIdx.x >> 5;
+    const uint32_t box_bytes = (uint32_t)(BW * a.wym * (int)sizeof(float));
+
+    auto issue = [&](int tile) {
+        const Window w = window_of(a, tile);
+        const int xs = w.ox0 & ~(ALIGN - 1);
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&bar, NF * box_bytes);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) tma_load_2d(stage + f * SP, &maps.m[f], xs, w.oy0, &bar);
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_proxy_async();
+    }
+    // edge rows of the missing strips -1 and ns stay zero (the window's zero border)
+    for (int t = (int)threadIdx.x; t < 2 * PAIR_EDGE_KINDS * es * 32; t += (int)blockDim.x) edge[t].u = 0ull;
+    __syncthreads();
+    int tile = blockIdx.x;
+    if (threadIdx.x == 0 && tile < ntiles) issue(tile);
+    uint32_t phase = 0;
+    while (tile < ntiles) {
+        const bool ok = mbar_wait_bounded(&bar, phase, a.wait_limit);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(a.status, 1);
+                mbar_wait_bounded(&bar, phase, 4000000000LL);
+            }
+            __syncthreads();
+            return;
+        }
+        const Window w = window_of(a, tile);
+        const int dx = w.ox0 - (w.ox0 & ~(ALIGN - 1));
+        PairCells c;
+        pair_setup(a, w, c, lane, strip, [&](int f, int wy, int wx) { return stage[f * SP + wy * BW + wx + dx]; });
+        edge[((0 * PAIR_EDGE_KINDS + 0) * es + strip + 1) * 32 + lane] = c.vx[0];
+        edge[((0 * PAIR_EDGE_KINDS + 1) * es + strip + 1) * 32 + lane] = c.vy[0];
+        edge[((0 * PAIR_EDGE_KINDS + 2) * es + strip + 1) * 32 + lane] = c.vx[PR - 1];
+        edge[((0 * PAIR_EDGE_KINDS + 3) * es + strip + 1) * 32 + lane] = c.vy[PR - 1];
+        __syncthreads(); // staging consumed, edge rows visible
+        const int next = tile + (int)gridDim.x;
+        if (threadIdx.x == 0 && next < ntiles) issue(next);
+        phase ^= 1u;
+        pair_sweeps(a, w, c, lane, strip, edge, es);
+        tile = next;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // register-resident kernel reading the window from global memory
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -771,14 +1076,22 @@ __global__ void __launch_bounds__(RAS_THREADS) k_ras_batched_smem(const BatchTil
 }
 
 // which kernel a configuration uses, and its launch shape
-enum { PLAN_TMA = 0, PLAN_REG = 1, PLAN_SMEM = 2 };
+enum { PLAN_TMA = 0, PLAN_REG = 1, PLAN_SMEM = 2, PLAN_PAIR = 3 };
 struct RasPlan {
     int kind;
     int wxm, wym, strips, wp, spad, plane, threads, bw, stage;
     size_t smem;
 };
 
-RasPlan plan_ras(int nx, int ny, int ti, int tj, int overlap, size_t elem, bool allow_tma)
+constexpr int PAIR_MAX_THREADS = 640;
+// Narrower windows leave lanes idle; up to this width the one-column kernel is
+// as fast or faster (measured at 8192^2: 40 columns 264 vs 177 Gcell/s, 48
+// columns equal)
+constexpr int PAIR_MIN_COLS = 48;
+
+// pair_mode: 0 never the pair kernel, 1 for windows of PAIR_MIN_COLS + 1 to
+// PAIR_COLS columns, 2 for any window of at most PAIR_COLS columns
+RasPlan plan_ras(int nx, int ny, int ti, int tj, int overlap, size_t elem, bool allow_tma, int pair_mode = 0)
 {
     RasPlan p;
     const int h = overlap + 1;
@@ -800,6 +1113,20 @@ RasPlan plan_ras(int nx, int ny, int ti, int tj, int overlap, size_t elem, bool 
     const size_t reg_smem = (size_t)REG_PLANES * (size_t)p.plane * elem;
     const size_t tma_smem = (size_t)nf * (size_t)p.stage * elem + reg_smem + 128;
     p.threads = (int)((threads + 31) / 32 * 32);
+    if (elem == 4 && allow_tma && pair_mode > 0 && p.wxm <= PAIR_COLS && (pair_mode > 1 || p.wxm > PAIR_MIN_COLS) &&
+        p.bw <= 256 && p.wym <= 256) {
+        // packed-pair layout: one warp per strip of PR rows, edge rows double-buffered
+        const int strips = (p.wym + PR - 1) / PR;
+        const size_t edge = (size_t)2 * PAIR_EDGE_KINDS * (strips + 2) * 32 * sizeof(f2);
+        const size_t smem = (size_t)nf * (size_t)p.stage * elem + edge + 128;
+        if (32 * strips <= PAIR_MAX_THREADS && smem <= maxs) {
+            p.kind = PLAN_PAIR;
+            p.strips = strips;
+            p.threads = 32 * strips;
+            p.smem = smem;
+            return p;
+        }
+    }
     if (threads <= REG_MAX_THREADS && allow_tma && p.bw <= 256 && p.wym <= 256 && tma_smem <= maxs) {
         p.kind = PLAN_TMA;
         p.smem = tma_smem;
@@ -838,6 +1165,15 @@ TileGrid make_tiles(int nx, int ny, int ti, int tj, int si, int sj)
     t.ntx = fx >= nx ? 1 : 1 + (nx - fx + ti - 1) / ti;
     t.nty = fy >= ny ? 1 : 1 + (ny - fy + tj - 1) / tj;
     return t;
+}
+
+void ras_kernel_plan(int nx, int ny, int ti, int tj, int overlap, size_t elem, bool allow_tma, int pair_mode,
+                     int *kind, int *threads, size_t *smem)
+{
+    const RasPlan p = plan_ras(nx, ny, ti, tj, overlap, elem, allow_tma, pair_mode);
+    *kind = p.kind;
+    *threads = p.threads;
+    *smem = p.smem;
 }
 
 size_t ras_smem_bytes(int nx, int ny, int ti, int tj, int overlap, size_t elem)
@@ -902,7 +1238,7 @@ cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const 
 {
     constexpr int NF = KCfg<T>::INVD ? 8 : 6;
     const bool have_inv = c.inv_dx && c.inv_dy;
-    const RasPlan p = plan_ras(g.nx, g.ny, tg.ti, tg.tj, overlap, sizeof(T), run.allow_tma);
+    const RasPlan p = plan_ras(g.nx, g.ny, tg.ti, tg.tj, overlap, sizeof(T), run.allow_tma, run.pair_mode);
     RasArgs<T> a;
     a.g = g;
     a.c = c;
@@ -927,7 +1263,7 @@ cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const 
     const int ntiles = tg.ntx * tg.nty;
     cudaError_t e;
     if (KCfg<T>::INVD && !have_inv && p.kind != PLAN_SMEM) return cudaErrorInvalidValue;
-    if (p.kind == PLAN_TMA) {
+    if (p.kind == PLAN_TMA || p.kind == PLAN_PAIR) {
         TmaMaps m;
         const int es = (int)sizeof(T);
         const long pb = (long)g.pitch * es;
@@ -939,6 +1275,9 @@ cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const 
             if (e != cudaSuccess) return e;
         }
         void (*kern)(TmaMaps, RasArgs<T>) = pick_tma<T>(p);
+        if constexpr (sizeof(T) == 4) {
+            if (p.kind == PLAN_PAIR) kern = p.threads <= 384 ? k_ras_pair<384> : k_ras_pair<PAIR_MAX_THREADS>;
+        }
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;

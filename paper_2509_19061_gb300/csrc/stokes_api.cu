@@ -77,6 +77,7 @@ struct stokes_ctx {
     int *dstatus = nullptr;              // device status word of the bounded waits
     int *hstatus = nullptr;              // pinned host copy
     bool use_tma = true;                 // STOKES_OPT_USE_TMA
+    int pair_mode = 1;                   // STOKES_OPT_PAIRED
     long long wait_limit = 2000000000LL; // STOKES_OPT_WAIT_LIMIT_CYCLES (about 1 s)
     MgHierarchy *mg = nullptr;
     Profiler prof;
@@ -202,6 +203,7 @@ RasRun run_opts(const stokes_ctx *c)
 {
     RasRun r;
     r.allow_tma = c->use_tma;
+    r.pair_mode = c->pair_mode;
     r.status = c->dstatus;
     r.wait_limit = c->wait_limit;
     return r;
@@ -994,8 +996,32 @@ int stokes_set_option(stokes_ctx *c, int option, long long value)
     switch (option) {
     case STOKES_OPT_USE_TMA: c->use_tma = value != 0; return STOKES_OK;
     case STOKES_OPT_WAIT_LIMIT_CYCLES: c->wait_limit = value; return STOKES_OK;
+    case STOKES_OPT_PAIRED:
+        if (value < 0 || value > 2) return STOKES_ERR_ARG;
+        c->pair_mode = (int)value;
+        return STOKES_OK;
     default: return STOKES_ERR_ARG;
     }
+}
+
+int stokes_tile_kernel_plan(int nx, int ny, int ti, int tj, int overlap, int dtype, int use_tma, int pair_mode,
+                            int *kernel, int *threads, size_t *smem_bytes)
+{
+    if (nx < 1 || ny < 1 || ti < 1 || tj < 1 || overlap < 0 || (dtype != STOKES_F32 && dtype != STOKES_F64) ||
+        pair_mode < 0 || pair_mode > 2)
+        return STOKES_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return STOKES_ERR_CUDA;
+    }
+    int kind = 0, thr = 0;
+    size_t smem = 0;
+    ras_kernel_plan(nx, ny, ti, tj, overlap, dtype == STOKES_F64 ? 8 : 4, use_tma != 0, pair_mode, &kind, &thr, &smem);
+    if (kernel) *kernel = kind;
+    if (threads) *threads = thr;
+    if (smem_bytes) *smem_bytes = smem;
+    return STOKES_OK;
 }
 
 int stokes_synchronize(stokes_ctx *c)

@@ -57,6 +57,10 @@ def test_argument_errors_without_device(lib):
     assert f.stokes_smooth(None, None, None, None, None) == api.STOKES_ERR_ARG
     assert f.stokes_destroy(None) == api.STOKES_OK
     assert f.stokes_strerror(api.STOKES_ERR_DIVERGED).decode().startswith("diverged")
+    assert f.stokes_set_option(None, api.STOKES_OPT_PAIRED, 1) == api.STOKES_ERR_ARG
+    for bad in [(0, 8, 8, 8, 1, 0, 1, 1), (8, 8, 8, 8, -1, 0, 1, 1), (8, 8, 8, 8, 1, 2, 1, 1),
+                (8, 8, 8, 8, 1, 0, 1, 3), (8, 8, 0, 8, 1, 0, 1, 1)]:
+        assert f.stokes_tile_kernel_plan(*bad, None, None, None) == api.STOKES_ERR_ARG, bad
 
 
 def test_product_path_has_no_oracle_dependency():

@@ -404,3 +404,72 @@ def test_staging_wait_timeout_is_reported_and_context_recovers(api):
     assert rel(r2.v(), ref) <= F64_TOL
     r.smooth(variant="ras", sweeps=4, tile=(32, 32), k=4, overlap=3, seed=1)
     r.ctx.synchronize()
+
+
+# ---------------------------------------------------------------------------
+# the packed-pair FP32 kernel (two columns per thread) gives the bits of the
+# one-column-per-thread kernel
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("nx,ny,tile,k,o", [
+    (301, 207, (56, 32), 4, 3),   # 64-column window, the benchmark's shape
+    (301, 207, (32, 32), 4, 3),   # 40-column window: idle lanes
+    (301, 207, (60, 20), 2, 1),
+    (301, 207, (62, 64), 1, 0),   # 66 window rows: 17 strips
+    (301, 207, (48, 40), 8, 7),
+    (301, 207, (13, 7), 2, 5),
+    (70, 45, (56, 32), 4, 0),     # ragged last tiles, overlap 0
+    (5, 3, (56, 32), 3, 2),       # grid smaller than the tile
+    (2, 2, (8, 8), 2, 1),
+])
+def test_pair_kernel_matches_the_column_kernel(api, nx, ny, tile, k, o):
+    """Mode 2 sends every window of at most 64 columns to the pair kernel;
+    its fields equal those of the one-column kernel (and, for o >= k - 1, of
+    global fused Jacobi) value for value."""
+    name, threads, smem = api.stokes_tile_kernel_plan(nx, ny, tile, o, "f32", pair_mode=2)
+    assert name == "pair", (name, threads)
+    assert api.stokes_tile_kernel_plan(nx, ny, tile, o, "f32", pair_mode=0)[0] != "pair"
+    prob = rand_problem(nx, ny, 43)
+    v0 = inputs.random_velocity(nx, ny, 44, 0.1)
+    outs = []
+    for pair in (2, 0):
+        r = Run(api, prob, "f32", v0)
+        r.ctx.set_option(api.STOKES_OPT_PAIRED, pair)
+        r.smooth(variant="ras", sweeps=9, tile=tile, k=k, overlap=o, seed=78)
+        outs.append(r.v())
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    if o >= k - 1:
+        r = Run(api, prob, "f32", v0)
+        r.smooth(variant="fused", sweeps=9)
+        jac = r.v()
+        assert np.array_equal(outs[0][0], jac[0]) and np.array_equal(outs[0][1], jac[1])
+
+
+def test_pair_kernel_selection(api):
+    plan = api.stokes_tile_kernel_plan
+    assert plan(1024, 1024, (56, 32), 3, "f32")[0] == "pair"       # 64-column window: default mode
+    assert plan(1024, 1024, (62, 32), 0, "f32")[0] == "pair"
+    assert plan(1024, 1024, (40, 32), 3, "f32")[0] != "pair"       # 48 columns: one-column kernel
+    assert plan(1024, 1024, (40, 32), 3, "f32", pair_mode=2)[0] == "pair"
+    assert plan(1024, 1024, (64, 32), 3, "f32", pair_mode=2)[0] != "pair"  # 72 columns
+    assert plan(1024, 1024, (56, 32), 3, "f64")[0] != "pair"
+    assert plan(1024, 1024, (56, 32), 3, "f32", use_tma=False)[0] != "pair"
+    with pytest.raises(api.StokesError):
+        plan(1024, 1024, (56, 32), 3, "f32", pair_mode=3)
+    ctx = api.StokesContext(16, 16, 1.0, 1.0, "f32")
+    with pytest.raises(api.StokesError):
+        ctx.set_option(api.STOKES_OPT_PAIRED, 5)
+    ctx.close()
+
+
+def test_pair_kernel_wait_timeout_is_reported(api):
+    nx, ny = 128, 96
+    prob = rand_problem(nx, ny, 45)
+    r = Run(api, prob, "f32")
+    r.ctx.set_option(api.STOKES_OPT_WAIT_LIMIT_CYCLES, -1)
+    r.smooth(variant="ras", sweeps=4, tile=(56, 32), k=4, overlap=3, seed=1)
+    with pytest.raises(api.StokesError) as e:
+        r.ctx.synchronize()
+    assert e.value.status == api.STOKES_ERR_TIMEOUT
+    r.ctx.set_option(api.STOKES_OPT_WAIT_LIMIT_CYCLES, 2_000_000_000)
+    r.smooth(variant="ras", sweeps=4, tile=(56, 32), k=4, overlap=3, seed=1)
+    r.ctx.synchronize()
