@@ -664,53 +664,69 @@ __device__ __forceinline__ void pair_sweeps(const RasArgs<float> &a, const Windo
 }
 
 // Persistent TMA-staged kernel of the pair layout: one warp per strip of PR
-// window rows, a.strips warps; the staging and the timeout handling are
-// those of k_ras_tma.
-template <int MAXT>
+// window rows, a.strips warps.  NST staging buffers: with two, the windows of
+// the next two tiles are in flight while a tile is swept (one tile of
+// prefetch leaves short sweeps waiting on HBM latency).  The timeout
+// handling is that of k_ras_tma, waiting for every copy in flight.
+template <int MAXT, int NST>
 __global__ void __launch_bounds__(MAXT, 1) k_ras_pair(const __grid_constant__ TmaMaps maps, RasArgs<float> a)
 {
     constexpr int NF = 8;
     constexpr int ALIGN = 4; // TMA x coordinates are multiples of 16 bytes
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar[NST];
     const uint32_t off = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
-    float *const stage = reinterpret_cast<float *>(smem_raw + off);
+    float *const stage0 = reinterpret_cast<float *>(smem_raw + off);
     const int BW = a.bw, SP = a.stage;
     const int es = a.strips + 2;
-    f2 *const edge = reinterpret_cast<f2 *>(stage + NF * SP);
+    f2 *const edge = reinterpret_cast<f2 *>(stage0 + NST * NF * SP);
     const int ntiles = a.tg.ntx * a.tg.nty;
+    const int grid = (int)gridDim.x;
     const int lane = (int)threadIdx.x & 31, strip = (int)threadIdx.x >> 5;
     const uint32_t box_bytes = (uint32_t)(BW * a.wym * (int)sizeof(float));
 
-    auto issue = [&](int tile) {
+    auto issue = [&](int tile, int j) {
         const Window w = window_of(a, tile);
         const int xs = w.ox0 & ~(ALIGN - 1);
+        float *const st = stage0 + j * NF * SP;
         fence_proxy_async();
-        mbar_arrive_expect_tx(&bar, NF * box_bytes);
+        mbar_arrive_expect_tx(&bar[j], NF * box_bytes);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) tma_load_2d(stage + f * SP, &maps.m[f], xs, w.oy0, &bar);
+        for (int f = 0; f < NF; ++f) tma_load_2d(st + f * SP, &maps.m[f], xs, w.oy0, &bar[j]);
     };
 
     if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
+#pragma unroll
+        for (int j = 0; j < NST; ++j) mbar_init(&bar[j], 1);
         fence_proxy_async();
     }
     // edge rows of the missing strips -1 and ns stay zero (the window's zero border)
     for (int t = (int)threadIdx.x; t < 2 * PAIR_EDGE_KINDS * es * 32; t += (int)blockDim.x) edge[t].u = 0ull;
     __syncthreads();
     int tile = blockIdx.x;
-    if (threadIdx.x == 0 && tile < ntiles) issue(tile);
-    uint32_t phase = 0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < NST; ++j)
+            if (tile + j * grid < ntiles) issue(tile + j * grid, j);
+    }
+    uint32_t phases = 0; // bit j: parity of the next completion of bar[j]
+    int j = 0;           // staging buffer of `tile`
     while (tile < ntiles) {
-        const bool ok = mbar_wait_bounded(&bar, phase, a.wait_limit);
+        const bool ok = mbar_wait_bounded(&bar[j], (phases >> j) & 1u, a.wait_limit);
         if (!__syncthreads_and(ok)) {
+            // give up: record the timeout, let every copy in flight land, leave
             if (threadIdx.x == 0) {
                 atomicExch(a.status, 1);
-                mbar_wait_bounded(&bar, phase, 4000000000LL);
+#pragma unroll
+                for (int d = 0; d < NST; ++d) {
+                    const int jj = (j + d) % NST;
+                    if (tile + d * grid < ntiles) mbar_wait_bounded(&bar[jj], (phases >> jj) & 1u, 4000000000LL);
+                }
             }
             __syncthreads();
             return;
         }
+        const float *const stage = stage0 + j * NF * SP;
         const Window w = window_of(a, tile);
         const int dx = w.ox0 - (w.ox0 & ~(ALIGN - 1));
         PairCells c;
@@ -719,12 +735,13 @@ __global__ void __launch_bounds__(MAXT, 1) k_ras_pair(const __grid_constant__ Tm
         edge[((0 * PAIR_EDGE_KINDS + 1) * es + strip + 1) * 32 + lane] = c.vy[0];
         edge[((0 * PAIR_EDGE_KINDS + 2) * es + strip + 1) * 32 + lane] = c.vx[PR - 1];
         edge[((0 * PAIR_EDGE_KINDS + 3) * es + strip + 1) * 32 + lane] = c.vy[PR - 1];
-        __syncthreads(); // staging consumed, edge rows visible
-        const int next = tile + (int)gridDim.x;
-        if (threadIdx.x == 0 && next < ntiles) issue(next);
-        phase ^= 1u;
+        __syncthreads(); // staging buffer j consumed, edge rows visible
+        const int refill = tile + NST * grid;
+        if (threadIdx.x == 0 && refill < ntiles) issue(refill, j);
+        phases ^= 1u << j;
         pair_sweeps(a, w, c, lane, strip, edge, es);
-        tile = next;
+        tile += grid;
+        j = NST > 1 ? (j + 1) % NST : 0;
     }
 }
 
@@ -1080,6 +1097,7 @@ enum { PLAN_TMA = 0, PLAN_REG = 1, PLAN_SMEM = 2, PLAN_PAIR = 3 };
 struct RasPlan {
     int kind;
     int wxm, wym, strips, wp, spad, plane, threads, bw, stage;
+    int nstage = 1; // staging buffers (pair kernel)
     size_t smem;
 };
 
@@ -1115,15 +1133,17 @@ RasPlan plan_ras(int nx, int ny, int ti, int tj, int overlap, size_t elem, bool 
     p.threads = (int)((threads + 31) / 32 * 32);
     if (elem == 4 && allow_tma && pair_mode > 0 && p.wxm <= PAIR_COLS && (pair_mode > 1 || p.wxm > PAIR_MIN_COLS) &&
         p.bw <= 256 && p.wym <= 256) {
-        // packed-pair layout: one warp per strip of PR rows, edge rows double-buffered
+        // packed-pair layout: one warp per strip of PR rows, edge rows double-buffered,
+        // two staging buffers when they fit
         const int strips = (p.wym + PR - 1) / PR;
         const size_t edge = (size_t)2 * PAIR_EDGE_KINDS * (strips + 2) * 32 * sizeof(f2);
-        const size_t smem = (size_t)nf * (size_t)p.stage * elem + edge + 128;
-        if (32 * strips <= PAIR_MAX_THREADS && smem <= maxs) {
+        const size_t one = (size_t)nf * (size_t)p.stage * elem;
+        if (32 * strips <= PAIR_MAX_THREADS && one + edge + 128 <= maxs) {
             p.kind = PLAN_PAIR;
             p.strips = strips;
             p.threads = 32 * strips;
-            p.smem = smem;
+            p.nstage = 2 * one + edge + 128 <= maxs ? 2 : 1;
+            p.smem = p.nstage * one + edge + 128;
             return p;
         }
     }
@@ -1276,7 +1296,10 @@ cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const 
         }
         void (*kern)(TmaMaps, RasArgs<T>) = pick_tma<T>(p);
         if constexpr (sizeof(T) == 4) {
-            if (p.kind == PLAN_PAIR) kern = p.threads <= 384 ? k_ras_pair<384> : k_ras_pair<PAIR_MAX_THREADS>;
+            if (p.kind == PLAN_PAIR) {
+                if (p.nstage == 2) kern = p.threads <= 384 ? k_ras_pair<384, 2> : k_ras_pair<PAIR_MAX_THREADS, 2>;
+                else kern = p.threads <= 384 ? k_ras_pair<384, 1> : k_ras_pair<PAIR_MAX_THREADS, 1>;
+            }
         }
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
         if (e != cudaSuccess) return e;
