@@ -19,6 +19,7 @@ sample of the same workload (see cpu_sample below).
 import argparse
 import hashlib
 import json
+import math
 import os
 import shutil
 import statistics
@@ -232,6 +233,26 @@ def workload_config(args):
             "step": "b = f - G p, %d RAS sweeps, energy norm" % args.sweeps}
 
 
+TILE_KERNEL_NAMES = {"pair": "k_ras_pair", "tma": "k_ras_tma", "global": "k_ras_reg", "shared": "k_ras"}
+
+
+def tile_kernel_name(api, n, tile, overlap, dt_name):
+    """Name of the tile kernel the library picks for this launch shape."""
+    return TILE_KERNEL_NAMES[api.stokes_tile_kernel_plan(n, n, tuple(tile), overlap, dt_name)[0]]
+
+
+def median_ci(xs):
+    """Median of the per-step times with its distribution-free 95% confidence
+    interval (order statistics n/2 -+ 0.98 sqrt(n), 1-based)."""
+    v = sorted(xs)
+    n = len(v)
+    if n == 0:
+        return None
+    lo = max(int(math.floor(n / 2 - 0.98 * math.sqrt(n))), 1)
+    hi = min(int(math.ceil(n / 2 + 1 + 0.98 * math.sqrt(n))), n)
+    return {"median": statistics.median(v), "ci95": [v[lo - 1], v[hi - 1]], "n": n, "unit": "ms"}
+
+
 def max_over_ranks(x, world, device):
     """The largest x over all ranks, returned on every rank (x itself when
     world == 1).  NCCL on the GPU machine; the CPU tests use gloo."""
@@ -291,14 +312,16 @@ def run_ours(args):
     ctx.profile_reset(timing=True)
     barrier()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    e0, e1 = evs[0], evs[-1]
     with ClockSampler(local) as clk:
         e0.record(stream)
         for it in range(args.steps):
             energy = step(args.sweeps, it)
-        e1.record(stream)
+            evs[it + 1].record(stream)
         torch.cuda.synchronize()
     barrier()
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
     ms_total = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     prof = ctx.profile()
     launches = sum(v[0] for v in prof.values())
@@ -317,7 +340,8 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if
                 peak_kind == "measured" else "fallback 6800 GB/s",
-                "kernel": "k_ras", "kernel_avg_ms": avg_ms, "kernel_share": ras_ms / ms_total,
+                "kernel": tile_kernel_name(api, n, args.tile, o, dt_name), "kernel_avg_ms": avg_ms,
+                "kernel_share": ras_ms / ms_total,
                 "algorithmic_bytes_per_launch": per_launch_bytes,
                 "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
                 "dram_bytes_per_cell_sweep": None if traffic is None else traffic / (cells * k),
@@ -331,6 +355,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": dt_name, "data": "synthetic (seeded layered sinker, no dataset)",
             "config": dict(workload_config(args), parallelism="replicas%d" % world if world > 1 else "single"),
             "gpu_launches": launches, "roofline": roofline, "clocks": clk.summary(),
+            "step_ms": median_ci(step_ms),
             "energy_residual_after_step": (energy[0] / energy[2]) ** 0.5}
 
     if not args.no_extras:
@@ -727,7 +752,9 @@ def variant_table(args, api, prob):
     for k in (1, 2, 4, 8):
         for o in sorted({k - 1, 0}):
             cases.append(("f32", dict(variant="ras", sweeps=40, tile=(56, 32), k=k, overlap=o)))
-    cases += [("f32", dict(variant="ras", sweeps=40, tile=(32, 32), k=4, overlap=3)),
+    cases += [("f32", dict(variant="ras", sweeps=40, tile=(48, 32), k=8, overlap=7)),
+              ("f32", dict(variant="ras", sweeps=40, tile=(62, 32), k=8, overlap=0)),
+              ("f32", dict(variant="ras", sweeps=40, tile=(32, 32), k=4, overlap=3)),
               ("f32", dict(variant="jacobi", sweeps=20)), ("f32", dict(variant="fused", sweeps=20)),
               ("f32", dict(variant="blocked", sweeps=20, tile=(56, 32))), ("f32", dict(variant="rbgs", sweeps=20))]
     for k in (1, 2, 4, 8):
@@ -751,6 +778,8 @@ def variant_table(args, api, prob):
         gbs = cu * WORDS_PER_CELL_SWEEP * (8 if dt_name == "f64" else 4) / 1e9
         out[label] = {"gcell_updates_per_s": cu / 1e9, "effective_gbs": gbs, "frac": gbs / peak,
                       "sweeps": kw["sweeps"], "ms_per_call": ms}
+        if kw["variant"] in ("ras", "blocked"):
+            out[label]["kernel"] = tile_kernel_name(api, n, kw["tile"], kw.get("overlap", 0), dt_name)
     for c, _, _ in ctxs.values():
         c.close()
     return out
