@@ -298,13 +298,14 @@ __global__ void kb_residual_energy(const BOuter<T> *__restrict__ tab, const BSeg
         const int i = p.i, j = p.j;
         const size_t q = (size_t)j * g.pitch + i;
         T mm, d, vc;
+        CellSq<T> c0(s0), c1(s1); // the cell's vx and vy terms
         if (j < g.ny) {
             T r = T(0);
             if (vx_unknown(g, j, i)) {
                 op_x(g, o.ec, o.en, (const T *)o.vx, (const T *)o.vy, j, i, mm, d, vc);
                 r = r_sub(o.bx[q], mm);
-                s0 = acc_sq(s0, r, -o.ivx[q]);
-                s1 = acc_sq(s1, o.fx[q], -o.ivx[q]);
+                c0.add(r, -o.ivx[q]);
+                c1.add(o.fx[q], -o.ivx[q]);
             }
             o.rx[q] = r;
         }
@@ -313,11 +314,13 @@ __global__ void kb_residual_energy(const BOuter<T> *__restrict__ tab, const BSeg
             if (vy_unknown(g, j, i)) {
                 op_y(g, o.ec, o.en, (const T *)o.vx, (const T *)o.vy, j, i, mm, d, vc);
                 r = r_sub(o.by[q], mm);
-                s0 = acc_sq(s0, r, -o.ivy[q]);
-                s1 = acc_sq(s1, o.fy[q], -o.ivy[q]);
+                c0.add(r, -o.ivy[q]);
+                c1.add(o.fy[q], -o.ivy[q]);
             }
             o.ry[q] = r;
         }
+        c0.done();
+        c1.done();
     }
     block_store2(s0, s1, partials);
 }

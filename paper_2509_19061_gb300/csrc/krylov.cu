@@ -41,17 +41,24 @@ __device__ __forceinline__ void block_store2(double s0, double s1, double *parti
     }
 }
 
-// Visit every velocity unknown once: f(q, component) with q the element offset.
+// Visit every cell once: f(q, vx is an unknown, vy is an unknown) with q the
+// element offset; for_unknowns visits every velocity unknown once: f(q, component).
+template <class F>
+__device__ __forceinline__ void for_cells(int nx, int ny, int pitch, F &&f)
+{
+    // rows round-robin over the blocks, columns over the threads
+    for (int j = blockIdx.x; j <= ny; j += gridDim.x)
+        for (int i = threadIdx.x; i <= nx; i += RD_THREADS)
+            f((size_t)j * pitch + i, j < ny && i >= 1 && i <= nx - 1, i < nx && j >= 1 && j <= ny - 1);
+}
+
 template <class F>
 __device__ __forceinline__ void for_unknowns(int nx, int ny, int pitch, F &&f)
 {
-    const long w = (long)nx + 1, total = w * (long)(ny + 1);
-    for (long t = (long)blockIdx.x * RD_THREADS + threadIdx.x; t < total; t += (long)gridDim.x * RD_THREADS) {
-        const int j = (int)(t / w), i = (int)(t - (long)j * w);
-        const size_t q = (size_t)j * pitch + i;
-        if (j < ny && i >= 1 && i <= nx - 1) f(q, 0);
-        if (i < nx && j >= 1 && j <= ny - 1) f(q, 1);
-    }
+    for_cells(nx, ny, pitch, [&](size_t q, bool ux, bool uy) {
+        if (ux) f(q, 0);
+        if (uy) f(q, 1);
+    });
 }
 
 // (<a, b>, <a, c>)
@@ -78,10 +85,20 @@ __global__ void __launch_bounds__(RD_THREADS) k_energy_r(int nx, int ny, int pit
                                                          const T *__restrict__ iy, double *__restrict__ partials)
 {
     double s0 = 0.0, s1 = 0.0;
-    for_unknowns(nx, ny, pitch, [&](size_t q, int comp) {
-        const T wgt = -(comp ? iy[q] : ix[q]);
-        s0 = acc_sq(s0, comp ? ry[q] : rx[q], wgt);
-        s1 = acc_sq(s1, comp ? fy[q] : fx[q], wgt);
+    for_cells(nx, ny, pitch, [&](size_t q, bool ux, bool uy) {
+        CellSq<T> c0(s0), c1(s1); // the cell's vx and vy terms
+        if (ux) {
+            const T wgt = -ix[q];
+            c0.add(rx[q], wgt);
+            c1.add(fx[q], wgt);
+        }
+        if (uy) {
+            const T wgt = -iy[q];
+            c0.add(ry[q], wgt);
+            c1.add(fy[q], wgt);
+        }
+        c0.done();
+        c1.done();
     });
     block_store2(s0, s1, partials);
 }

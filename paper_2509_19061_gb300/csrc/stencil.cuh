@@ -35,6 +35,40 @@ __device__ __forceinline__ double acc_sq(double s, double r, double w) { return 
 __device__ __forceinline__ double acc_sq(double s, float r, float w) { return s + (double)r_mul(r_mul(r, r), w); }
 __device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+// The squared residual terms r^2 w of one cell (its vx and its vy unknown),
+// added to an FP64 sum `s`.  FP64: each term with one FP64 fma, as acc_sq.
+// FP32: the cell's two terms are added in FP32 (one more rounding, 2^-24
+// relative, on a sum of two positive terms) and the cell enters the FP64 sum
+// once, which halves the FP64-pipe operations of the energy reductions.
+// Every energy kernel forms a cell's value this way, so the single-context
+// and the batched reductions differ only in the order of their FP64 sums.
+template <typename T>
+struct CellSq;
+template <>
+struct CellSq<double> {
+    double &s;
+    __device__ __forceinline__ explicit CellSq(double &sum) : s(sum) {}
+    __device__ __forceinline__ void add(double r, double w) { s = fma(r * r, w, s); }
+    __device__ __forceinline__ void done() {}
+};
+template <>
+struct CellSq<float> {
+    double &s;
+    float t = 0.f;
+    bool any = false;
+    __device__ __forceinline__ explicit CellSq(double &sum) : s(sum) {}
+    __device__ __forceinline__ void add(float r, float w)
+    {
+        const float v = __fmul_rn(__fmul_rn(r, r), w);
+        t = any ? __fadd_rn(t, v) : v;
+        any = true;
+    }
+    __device__ __forceinline__ void done()
+    {
+        if (any) s += (double)t;
+    }
+};
+
 // correctly rounded reciprocal (the same value as 1/x with IEEE division)
 __device__ __forceinline__ float r_rcp(float a) { return __frcp_rn(a); }
 __device__ __forceinline__ double r_rcp(double a) { return __drcp_rn(a); }

@@ -191,25 +191,28 @@ __global__ void __launch_bounds__(EN_THREADS) k_energy(GridDesc<T> g, const T *_
     // 1/(-diag M) come from the context's 1/diag arrays when it has them
     double s_rv = 0.0, s_rp = 0.0, s_ff = 0.0;
     const T ilap = (T)(1.0 / g.lap);
-    const long w = (long)g.nx + 1, total = w * (long)(g.ny + 1);
-    for (long t = (long)blockIdx.x * EN_THREADS + threadIdx.x; t < total; t += (long)gridDim.x * EN_THREADS) {
-        const int j = (int)(t / w), i = (int)(t - (long)j * w);
+    // rows round-robin over the blocks, columns over the threads (no index division)
+    for (int j = blockIdx.x; j <= g.ny; j += gridDim.x)
+    for (int i = threadIdx.x; i <= g.nx; i += EN_THREADS) {
         const size_t q = (size_t)j * g.pitch + i;
         T m, d, vc;
+        CellSq<T> rv(s_rv), ff(s_ff); // the cell's vx and vy terms
         if (vx_unknown(g, j, i)) {
             op_x<T, MASK>(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
             const T b = p ? r_fma(r_sub(p[q], p[q - 1]), g.ihx, fx[q]) : fx[q];
             const T wi = -(inv_dx ? inv_dx[q] : inv_diag(d));
-            s_rv = acc_sq(s_rv, r_sub(b, m), wi);
-            s_ff = acc_sq(s_ff, fx[q], wi);
+            rv.add(r_sub(b, m), wi);
+            ff.add(fx[q], wi);
         }
         if (vy_unknown(g, j, i)) {
             op_y<T, MASK>(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
             const T b = p ? r_fma(r_sub(p[q], p[q - g.pitch]), g.ihy, fy[q]) : fy[q];
             const T wi = -(inv_dy ? inv_dy[q] : inv_diag(d));
-            s_rv = acc_sq(s_rv, r_sub(b, m), wi);
-            s_ff = acc_sq(s_ff, fy[q], wi);
+            rv.add(r_sub(b, m), wi);
+            ff.add(fy[q], wi);
         }
+        rv.done();
+        ff.done();
         if (i < g.nx && j < g.ny) {
             const T dv = r_fma(r_sub(vx[q + 1], vx[q]), g.ihx, r_mul(r_sub(vy[q + g.pitch], vy[q]), g.ihy));
             s_rp = acc_sq(s_rp, dv, r_mul(eta_c[q], ilap));
