@@ -184,7 +184,8 @@ int stokes_get_layout(const stokes_ctx *ctx, int field, int *rows, int *cols, in
 int stokes_set_viscosity(stokes_ctx *ctx, const void *eta_c, const void *eta_n);
 
 /* Set the body force f of Eq. (6) (fx like vx, fy like vy; f_y = -rho g_y for
- * Eq. (2) with gravity g_y).  Device pointers, copied. */
+ * Eq. (2) with gravity g_y).  Device pointers, copied at the unknowns (the
+ * wall and padding entries are not read). */
 int stokes_set_rhs(stokes_ctx *ctx, const void *fx, const void *fy);
 
 /* out = M v + G p at every unknown (Eq. (6) left-hand side), zero on walls and

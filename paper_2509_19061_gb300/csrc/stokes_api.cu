@@ -249,12 +249,18 @@ SmoothSpec spec_of(const stokes_smooth_params *p, int ti, int tj)
 }
 
 // Runs the smoother of `p` on (vx, vy) with b already formed.
+// without a pressure b = f: the smoothers read f directly (no b = f - G p pass)
 template <typename T>
-int smooth_impl(stokes_ctx *c, T *vx, T *vy, const stokes_smooth_params *p, int ti, int tj)
+int smooth_impl(stokes_ctx *c, T *vx, T *vy, const stokes_smooth_params *p, int ti, int tj, bool b_is_f)
 {
     CtxHook hook(c);
-    return smooth_buffers<T>(grid_of<T>(c), coeffs_of<T>(c), vx, vy, (T *)c->sx, (T *)c->sy, spec_of(p, ti, tj),
-                             run_opts(c), c->stream, hook);
+    Coeffs<T> k = coeffs_of<T>(c);
+    if (b_is_f) {
+        k.bx = (const T *)c->fx;
+        k.by = (const T *)c->fy;
+    }
+    return smooth_buffers<T>(grid_of<T>(c), k, vx, vy, (T *)c->sx, (T *)c->sy, spec_of(p, ti, tj), run_opts(c),
+                             c->stream, hook);
 }
 
 template <typename T>
@@ -914,9 +920,13 @@ int stokes_set_viscosity(stokes_ctx *c, const void *eta_c, const void *eta_n)
 int stokes_set_rhs(stokes_ctx *c, const void *fx, const void *fy)
 {
     if (!c || !fx || !fy) return STOKES_ERR_ARG;
-    const size_t bytes = c->elems * c->esize;
-    CK(cudaMemcpyAsync(c->fx, fx, bytes, cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->fy, fy, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    // f at the unknowns, zero on walls and padding: f is then b = f - G p for p = 0
+    if (c->dtype == STOKES_F64)
+        RUN(STOKES_K_RHS, 1, launch_rhs<double>(grid_of<double>(c), (const double *)fx, (const double *)fy, nullptr,
+                                                (double *)c->fx, (double *)c->fy, c->stream));
+    else
+        RUN(STOKES_K_RHS, 1, launch_rhs<float>(grid_of<float>(c), (const float *)fx, (const float *)fy, nullptr,
+                                               (float *)c->fx, (float *)c->fy, c->stream));
     c->have_f = true;
     return STOKES_OK;
 }
@@ -942,14 +952,17 @@ int stokes_smooth(stokes_ctx *c, void *vx, void *vy, const void *p, const stokes
     int ti, tj, st = check_smooth_params(c->nx, c->ny, c->esize, params, &ti, &tj);
     if (st != STOKES_OK) return st;
     if (!c->have_eta || !c->have_f) return STOKES_ERR_STATE;
+    const bool b_is_f = p == nullptr;
     if (c->dtype == STOKES_F64) {
-        RUN(STOKES_K_RHS, 1, launch_rhs<double>(grid_of<double>(c), (const double *)c->fx, (const double *)c->fy, (const double *)p,
-                              (double *)c->bx, (double *)c->by, c->stream));
-        return smooth_impl<double>(c, (double *)vx, (double *)vy, params, ti, tj);
+        if (!b_is_f)
+            RUN(STOKES_K_RHS, 1, launch_rhs<double>(grid_of<double>(c), (const double *)c->fx, (const double *)c->fy,
+                                                    (const double *)p, (double *)c->bx, (double *)c->by, c->stream));
+        return smooth_impl<double>(c, (double *)vx, (double *)vy, params, ti, tj, b_is_f);
     }
-    RUN(STOKES_K_RHS, 1, launch_rhs<float>(grid_of<float>(c), (const float *)c->fx, (const float *)c->fy, (const float *)p,
-                         (float *)c->bx, (float *)c->by, c->stream));
-    return smooth_impl<float>(c, (float *)vx, (float *)vy, params, ti, tj);
+    if (!b_is_f)
+        RUN(STOKES_K_RHS, 1, launch_rhs<float>(grid_of<float>(c), (const float *)c->fx, (const float *)c->fy,
+                                               (const float *)p, (float *)c->bx, (float *)c->by, c->stream));
+    return smooth_impl<float>(c, (float *)vx, (float *)vy, params, ti, tj, b_is_f);
 }
 
 int stokes_residual_energy_norm(stokes_ctx *c, const void *vx, const void *vy, const void *p, double out[3])
