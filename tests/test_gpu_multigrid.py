@@ -162,3 +162,18 @@ def test_refinement_fp32_inner_reaches_1e8(api):
     den = np.sum(-dx * ref[0] ** 2) + np.sum(-dy * ref[1] ** 2)
     print("refinement, fp32 inner: %d V-cycles, E_v %.2e, energy error %.2e" % (c, e, np.sqrt(num / den)))
     assert np.sqrt(num / den) <= 1e-6
+
+
+def test_nan_viscosity_is_reported_as_diverged(api):
+    """A NaN planted in eta on the host reaches the residual: the solve stops
+    with STOKES_ERR_DIVERGED instead of running on."""
+    prob = inputs.sinker_problem(64, eta_in=1e3)
+    prob.eta_c = prob.eta_c.copy()
+    prob.eta_c[20, 30] = np.nan
+    ctx = api.StokesContext(64, 64, 1.0, 1.0, "f64")
+    ctx.set_problem(prob)
+    vx, vy = ctx.field(), ctx.field()
+    with pytest.raises(api.StokesError) as e:
+        ctx.vcycle(vx, vy, None, variant="ras", tile=(32, 32), k=4, overlap=3, inner="f32", tol=1e-8, max_cycles=20)
+    assert e.value.status == api.STOKES_ERR_DIVERGED
+    ctx.close()

@@ -473,3 +473,48 @@ def test_pair_kernel_wait_timeout_is_reported(api):
     r.ctx.set_option(api.STOKES_OPT_WAIT_LIMIT_CYCLES, 2_000_000_000)
     r.smooth(variant="ras", sweeps=4, tile=(56, 32), k=4, overlap=3, seed=1)
     r.ctx.synchronize()
+
+
+# ---------------------------------------------------------------------------
+# padding canaries: no smoother reads or writes the layout's padding
+# ---------------------------------------------------------------------------
+def _with_canaries(api, ctx, t, name):
+    """Copy of a packed field with NaN in every padding entry of the layout."""
+    import torch
+    r, c = ctx.shape[name]
+    out = t.clone()
+    out[r:, :] = float("nan")
+    out[:, c:] = float("nan")
+    return out
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("kw", [
+    dict(variant="jacobi", sweeps=3), dict(variant="fused", sweeps=3), dict(variant="rbgs", sweeps=2),
+    dict(variant="blocked", sweeps=2, tile=(24, 16)),
+    dict(variant="ras", sweeps=6, tile=(56, 32), k=4, overlap=3, seed=3),
+    dict(variant="ras", sweeps=6, tile=(62, 32), k=2, overlap=0, seed=4),
+    dict(variant="ras", sweeps=6, tile=(16, 8), k=3, overlap=1, seed=5),
+    dict(variant="ras", sweeps=4, tile=(72, 40), k=2, overlap=1, seed=6),
+])
+def test_smoothers_ignore_layout_padding(api, dtype, kw):
+    """NaN in every padding entry of vx and vy (rows and columns beyond each
+    field's extent) changes no unknown and is not overwritten."""
+    import torch
+    nx, ny = 150, 97
+    prob = rand_problem(nx, ny, 46)
+    v0 = inputs.random_velocity(nx, ny, 47, 0.1)
+    a = Run(api, prob, dtype, v0)
+    a.smooth(**kw)
+    want = a.v()
+    b = Run(api, prob, dtype, v0)
+    b.vx = _with_canaries(api, b.ctx, b.vx, "vx")
+    b.vy = _with_canaries(api, b.ctx, b.vy, "vy")
+    b.smooth(**kw)
+    got = b.v()
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+    torch.cuda.synchronize()
+    for t, name in ((b.vx, "vx"), (b.vy, "vy")):
+        r, c = b.ctx.shape[name]
+        h = t.double().cpu().numpy()
+        assert np.isnan(h[r:, :]).all() and np.isnan(h[:, c:]).all(), name
