@@ -682,10 +682,7 @@ int plan_precond(stokes_batch *b, const stokes_mg_params *p, Precond<To, Ti> *P)
                 x.vy = e.vy;
                 x.sx = e.sx;
                 x.sy = e.sy;
-                const bool single = jacobi_like(sm) && sweeps > 0 &&
-                                    ras_smem_bytes(e.g.nx, e.g.ny, e.g.nx, e.g.ny, 0, es) <=
-                                        (size_t)ras_max_smem() &&
-                                    e.g.nx <= 64 && e.g.ny <= 64;
+                const bool single = jacobi_like(sm) && sweeps > 0 && ras_whole_level_tile(e.g.nx, e.g.ny, es);
                 if (single) {
                     x.ti = e.g.nx;
                     x.tj = e.g.ny;

@@ -109,6 +109,10 @@ cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const 
                        int overlap, const T *vx, const T *vy, T *ox, T *oy, const RasRun &run, cudaStream_t s);
 // shared memory a RAS launch needs for this grid, tile and overlap
 size_t ras_smem_bytes(int nx, int ny, int ti, int tj, int overlap, size_t elem);
+// Whether a Jacobi-equivalent smoothing of an nx x ny level runs all its sweeps
+// as one launch with the whole level as one tile (its window fits a register
+// layout); the single-context and the batched V-cycle take the same decision.
+bool ras_whole_level_tile(int nx, int ny, size_t elem);
 // the tile kernel (stokes_tile_kernel value), CTA size and dynamic shared memory of a launch
 void ras_kernel_plan(int nx, int ny, int ti, int tj, int overlap, size_t elem, bool allow_tma, int pair_mode,
                      int *kind, int *threads, size_t *smem);

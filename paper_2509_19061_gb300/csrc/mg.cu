@@ -171,12 +171,12 @@ SmoothSpec level_spec(const stokes_mg_params *p, const MgLevel &l, int lvl, int 
     s.shift_mode = STOKES_SHIFT_SPLITMIX;
     s.shifts = nullptr;
     // Jacobi in any schedule (and RAS with overlap >= k-1, which is Jacobi)
-    // on a level that fits one tile-kernel window: all sweeps in one launch
+    // on a level whose whole-level window fits a register tile kernel: all
+    // sweeps in one launch (the same map, so the same values)
     const bool jacobi = sm.variant == STOKES_JACOBI || sm.variant == STOKES_JACOBI_FUSED ||
                         sm.variant == STOKES_JACOBI_BLOCKED ||
                         (sm.variant == STOKES_RAS && sm.overlap >= sm.k - 1);
-    if (jacobi && s.sweeps > 0 && ras_smem_bytes(l.nx, l.ny, l.nx, l.ny, 0, es) <= (size_t)ras_max_smem() &&
-        l.nx <= 64 && l.ny <= 64) {
+    if (jacobi && s.sweeps > 0 && ras_whole_level_tile(l.nx, l.ny, es)) {
         s.variant = STOKES_RAS;
         s.ti = l.nx;
         s.tj = l.ny;

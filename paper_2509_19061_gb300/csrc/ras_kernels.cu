@@ -1196,6 +1196,14 @@ void ras_kernel_plan(int nx, int ny, int ti, int tj, int overlap, size_t elem, b
     *smem = p.smem;
 }
 
+bool ras_whole_level_tile(int nx, int ny, size_t elem)
+{
+    // one tile of the whole level, overlap 0: worth it when the window fits a
+    // register layout (a single CTA of the general kernel is slower than the
+    // level's regular tiling)
+    return nx <= 64 && ny <= 64 && plan_ras(nx, ny, nx, ny, 0, elem, true, 0).kind != PLAN_SMEM;
+}
+
 size_t ras_smem_bytes(int nx, int ny, int ti, int tj, int overlap, size_t elem)
 {
     return plan_ras(nx, ny, ti, tj, overlap, elem, false).smem;
