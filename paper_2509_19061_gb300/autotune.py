@@ -24,7 +24,7 @@ from dataclasses import asdict, dataclass
 DEFAULT_CANDIDATES = [(ti, tj, k, o) for (ti, tj) in ((16, 16), (32, 32), (56, 32))
                       for k in (1, 2, 4, 8) for o in sorted({0, k - 1})]
 # 64-column windows, which the FP32 packed-pair kernel sweeps: exact Jacobi at k = 8 and ring-only tiles
-DEFAULT_CANDIDATES += [(48, 32, 8, 7), (62, 32, 4, 0), (62, 32, 8, 0)]
+DEFAULT_CANDIDATES += [(48, 32, 8, 7), (62, 32, 4, 0), (62, 32, 8, 0), (48, 64, 8, 7), (62, 56, 8, 0)]
 
 
 @dataclass

@@ -328,7 +328,9 @@ def test_argument_and_state_errors(api):
 # full size: 8192^2 layered sinker (contrast 1e6), the benchmark's launch
 # configuration; sampled tiles of one outer iteration against the oracle
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("dtype,tile,k,o", [("f32", (32, 32), 4, 3), ("f64", (32, 32), 4, 3),
+@pytest.mark.parametrize("dtype,tile,k,o", [("f32", (48, 64), 8, 7),   # the benchmark's schedule
+                                            ("f32", (62, 56), 8, 0),   # ring-only tiles, pair kernel
+                                            ("f32", (32, 32), 4, 3), ("f64", (32, 32), 4, 3),
                                             ("f32", (32, 32), 4, 0)])
 def test_full_size_sampled_tiles(api, dtype, tile, k, o):
     n = 8192
@@ -416,6 +418,7 @@ def test_staging_wait_timeout_is_reported_and_context_recovers(api):
     (301, 207, (60, 20), 2, 1),
     (301, 207, (62, 64), 1, 0),   # 66 window rows: 17 strips
     (301, 207, (48, 40), 8, 7),
+    (301, 207, (48, 64), 8, 7),   # 80 window rows: 20 strips, the largest CTA
     (301, 207, (13, 7), 2, 5),
     (70, 45, (56, 32), 4, 0),     # ragged last tiles, overlap 0
     (5, 3, (56, 32), 3, 2),       # grid smaller than the tile
