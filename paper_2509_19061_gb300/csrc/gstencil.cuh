@@ -81,25 +81,29 @@ __device__ __forceinline__ bool vy_wall(const GridDesc<T> &g, int j, int i)
 // ---- tiled operator apply with shared fluxes --------------------------------
 // q = M p on the 32 x 8 cell tile at (i0, j0), plus (<p, q>, <p, r>) over its
 // unknowns added to (s0, s1).  Every flux of the tile and a one-cell halo
-// (sigma'xx at cells, sigma'yy at cells, the shear at nodes) is computed once
-// into shared memory and M p assembled from them: about half the arithmetic
-// of evaluating the stencil per unknown, which computes each flux twice.  The
-// operands and helpers are those of op_x / op_y (library eta_n with zero
-// boundary nodes; rows and columns outside a field read as zero), so q is the
-// same bit for bit.  Called by all 256 threads of the block; tid is the
-// caller's linear thread index (0 .. 255).
+// (sigma'xx / hx at cells, sigma'yy / hy at cells, the shear at nodes scaled
+// by 1/hy and by 1/hx) is computed once into shared memory and M p assembled
+// from them: about half the arithmetic of evaluating the stencil per unknown,
+// which computes each flux twice.  ax, ay (nullable): the cell coefficients
+// 2 eta_c / hx^2 and 2 eta_c / hy^2 precomputed by coef_x / coef_y, which
+// saves their evaluation per flux.  The operands and helpers are those of
+// op_x / op_y (library eta_n with zero boundary nodes; rows and columns
+// outside a field read as zero), so q is the same bit for bit.  Called by all
+// 256 threads of the block; tid is the caller's linear thread index (0 .. 255).
 constexpr int AT_X = 32, AT_Y = 8;
 
 template <typename T>
 struct ApplyTile {
-    T txx[AT_Y][AT_X + 1];    // cells (j0 + a, i0 - 1 + b)
-    T tyy[AT_Y + 1][AT_X];    // cells (j0 - 1 + a, i0 + b)
-    T sh[AT_Y + 1][AT_X + 1]; // nodes (j0 + a, i0 + b)
+    T txx[AT_Y][AT_X + 1];     // cells (j0 + a, i0 - 1 + b)
+    T tyy[AT_Y + 1][AT_X];     // cells (j0 - 1 + a, i0 + b)
+    T sx[AT_Y + 1][AT_X + 1];  // nodes (j0 + a, i0 + b): shear / hy
+    T sy[AT_Y + 1][AT_X + 1];  // the same nodes: shear / hx
 };
 
 template <typename T>
 __device__ __forceinline__ void apply_dot_tile(const GridDesc<T> &g, const T *__restrict__ ec,
-                                               const T *__restrict__ en, const T *__restrict__ px,
+                                               const T *__restrict__ en, const T *__restrict__ ax,
+                                               const T *__restrict__ ay, const T *__restrict__ px,
                                                const T *__restrict__ py, T *__restrict__ qx, T *__restrict__ qy,
                                                const T *__restrict__ rx, const T *__restrict__ ry, int i0, int j0,
                                                int tid, ApplyTile<T> &sm, double &s0, double &s1)
@@ -112,7 +116,7 @@ __device__ __forceinline__ void apply_dot_tile(const GridDesc<T> &g, const T *__
         T v = T(0);
         if (J < g.ny && I >= 0 && I < g.nx) {
             const size_t q = (size_t)J * P + I;
-            v = flux_n(coef_x(g, ec[q]), px[q + 1], px[q]);
+            v = flux_n(ax ? ax[q] : coef_x(g, ec[q]), px[q + 1], px[q]);
         }
         sm.txx[a][b] = v;
     }
@@ -122,7 +126,7 @@ __device__ __forceinline__ void apply_dot_tile(const GridDesc<T> &g, const T *__
         T v = T(0);
         if (J >= 0 && J < g.ny && I < g.nx) {
             const size_t q = (size_t)J * P + I;
-            v = flux_n(coef_y(g, ec[q]), py[q + P], py[q]);
+            v = flux_n(ay ? ay[q] : coef_y(g, ec[q]), py[q + P], py[q]);
         }
         sm.tyy[a][b] = v;
     }
@@ -136,7 +140,8 @@ __device__ __forceinline__ void apply_dot_tile(const GridDesc<T> &g, const T *__
             const T vyr = I < g.nx ? py[q] : T(0), vyl = I > 0 ? py[q - 1] : T(0);
             v = shear(g, en[q], vxa, vxb, vyr, vyl);
         }
-        sm.sh[a][b] = v;
+        sm.sx[a][b] = r_mul(v, g.ihy);
+        sm.sy[a][b] = r_mul(v, g.ihx);
     }
     __syncthreads();
     const int j = j0 + ty, i = i0 + tx;
@@ -145,8 +150,7 @@ __device__ __forceinline__ void apply_dot_tile(const GridDesc<T> &g, const T *__
         if (j < g.ny) {
             T m = T(0);
             if (vx_unknown(g, j, i)) {
-                m = m_x(sm.txx[ty][tx + 1], sm.txx[ty][tx], r_mul(sm.sh[ty + 1][tx], g.ihy),
-                        r_mul(sm.sh[ty][tx], g.ihy));
+                m = m_x(sm.txx[ty][tx + 1], sm.txx[ty][tx], sm.sx[ty + 1][tx], sm.sx[ty][tx]);
                 s0 = fma((double)px[q], (double)m, s0);
                 s1 = fma((double)px[q], (double)rx[q], s1);
             }
@@ -155,8 +159,7 @@ __device__ __forceinline__ void apply_dot_tile(const GridDesc<T> &g, const T *__
         if (i < g.nx) {
             T m = T(0);
             if (vy_unknown(g, j, i)) {
-                m = m_y(r_mul(sm.sh[ty][tx + 1], g.ihx), r_mul(sm.sh[ty][tx], g.ihx), sm.tyy[ty + 1][tx],
-                        sm.tyy[ty][tx]);
+                m = m_y(sm.sy[ty][tx + 1], sm.sy[ty][tx], sm.tyy[ty + 1][tx], sm.tyy[ty][tx]);
                 s0 = fma((double)py[q], (double)m, s0);
                 s1 = fma((double)py[q], (double)ry[q], s1);
             }

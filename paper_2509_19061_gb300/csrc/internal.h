@@ -213,8 +213,11 @@ struct SmoothSpec {
 
 // Smooth M v = b in place on (vx, vy) with the coefficients `k` (b included),
 // ping-ponging through the scratch pair (sx, sy).  Returns a stokes_status.
+// With `swapped` non-null, a result that ends in (sx, sy) after an odd number
+// of passes is left there (*swapped = true) instead of being copied back; the
+// caller then treats (sx, sy) as the velocity and (vx, vy) as the scratch.
 template <typename T>
 int smooth_buffers(const GridDesc<T> &g, const Coeffs<T> &k, T *vx, T *vy, T *sx, T *sy, const SmoothSpec &p,
-                   const RasRun &run, cudaStream_t s, LaunchHook &hook);
+                   const RasRun &run, cudaStream_t s, LaunchHook &hook, bool *swapped = nullptr);
 
 } // namespace stokes

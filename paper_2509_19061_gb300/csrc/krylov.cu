@@ -154,7 +154,8 @@ __global__ void __launch_bounds__(RD_THREADS) k_add(int nx, int ny, int pitch, c
 // blockIdx.x + gridDim.x, ...
 template <typename T>
 __global__ void __launch_bounds__(RD_THREADS) k_apply_dot(GridDesc<T> g, const T *__restrict__ ec,
-                                                          const T *__restrict__ en, const T *__restrict__ px,
+                                                          const T *__restrict__ en, const T *__restrict__ ax,
+                                                          const T *__restrict__ ay, const T *__restrict__ px,
                                                           const T *__restrict__ py, T *__restrict__ qx,
                                                           T *__restrict__ qy, const T *__restrict__ rx,
                                                           const T *__restrict__ ry, double *__restrict__ partials)
@@ -163,9 +164,24 @@ __global__ void __launch_bounds__(RD_THREADS) k_apply_dot(GridDesc<T> g, const T
     const int ntx = (g.nx + 1 + AT_X - 1) / AT_X, nty = (g.ny + 1 + AT_Y - 1) / AT_Y;
     double s0 = 0.0, s1 = 0.0;
     for (int t = blockIdx.x; t < ntx * nty; t += gridDim.x)
-        apply_dot_tile<T>(g, ec, en, px, py, qx, qy, rx, ry, (t % ntx) * AT_X, (t / ntx) * AT_Y, (int)threadIdx.x,
+        apply_dot_tile<T>(g, ec, en, ax, ay, px, py, qx, qy, rx, ry, (t % ntx) * AT_X, (t / ntx) * AT_Y, (int)threadIdx.x,
                           sm, s0, s1);
     block_store2(s0, s1, partials);
+}
+
+// the flux coefficients of every cell: ax = coef_x(eta_c), ay = coef_y(eta_c)
+template <typename T>
+__global__ void __launch_bounds__(RD_THREADS) k_coef(GridDesc<T> g, int nx, int ny, int pitch,
+                                                     const T *__restrict__ ec, T *__restrict__ ax,
+                                                     T *__restrict__ ay)
+{
+    for (int j = blockIdx.x; j < ny; j += gridDim.x)
+        for (int i = threadIdx.x; i < nx; i += RD_THREADS) {
+            const size_t q = (size_t)j * pitch + i;
+            const T e = ec[q];
+            ax[q] = coef_x(g, e);
+            ay[q] = coef_y(g, e);
+        }
 }
 
 // v += (To) e at the unknowns
@@ -203,11 +219,19 @@ cudaError_t kry_dot2(const KrylovView &k, const T *ax, const T *ay, const T *bx,
 }
 
 template <typename T>
-cudaError_t kry_apply_dot(const KrylovView &k, const GridDesc<T> &g, const T *ec, const T *en, const T *px,
-                          const T *py, T *qx, T *qy, const T *rx, const T *ry, cudaStream_t s)
+cudaError_t kry_apply_dot(const KrylovView &k, const GridDesc<T> &g, const T *ec, const T *en, const T *ax,
+                          const T *ay, const T *px, const T *py, T *qx, T *qy, const T *rx, const T *ry,
+                          cudaStream_t s)
 {
-    k_apply_dot<T><<<RD_BLOCKS, RD_THREADS, 0, s>>>(g, ec, en, px, py, qx, qy, rx, ry, k.partials);
+    k_apply_dot<T><<<RD_BLOCKS, RD_THREADS, 0, s>>>(g, ec, en, ax, ay, px, py, qx, qy, rx, ry, k.partials);
     k_final2<<<1, 64, 0, s>>>(k.partials, RD_BLOCKS, k.out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t kry_coef(const KrylovView &k, const GridDesc<T> &g, const T *ec, T *ax, T *ay, cudaStream_t s)
+{
+    k_coef<T><<<RD_BLOCKS, RD_THREADS, 0, s>>>(g, k.nx, k.ny, k.pitch, ec, ax, ay);
     return cudaGetLastError();
 }
 
@@ -270,7 +294,9 @@ template cudaError_t kry_add_cast<float, double>(const KrylovView &, const doubl
                                           cudaStream_t);                                                           \
     template cudaError_t kry_add<T>(const KrylovView &, const T *, const T *, T *, T *, cudaStream_t);          \
     template cudaError_t kry_apply_dot<T>(const KrylovView &, const GridDesc<T> &, const T *, const T *,        \
-                                          const T *, const T *, T *, T *, const T *, const T *, cudaStream_t);
+                                          const T *, const T *, const T *, const T *, T *, T *, const T *,      \
+                                          const T *, cudaStream_t);                                             \
+    template cudaError_t kry_coef<T>(const KrylovView &, const GridDesc<T> &, const T *, T *, T *, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -9,6 +9,7 @@
 // The cycle is used as the preconditioner z = B r of the outer solve.
 #include <cmath>
 #include <new>
+#include <utility>
 
 #include "../../include/stokes.h"
 #include "internal.h"
@@ -199,6 +200,42 @@ int enqueue_precond(MgHierarchy *h, const Tc *rx, const Tc *ry, Tc *zx, Tc *zy, 
     } while (0)
     const int L = h->L;
     MgLevel &l0 = h->lv[0];
+    // A smoothing that ends in a level's scratch pair leaves its result there
+    // and the level's (vx, vy) and (sx, sy) pointers trade places for the rest
+    // of this enqueue (the launches record the addresses they were given); the
+    // guard puts the host-side pointers back when the enqueue ends.
+    struct Restore {
+        MgHierarchy *h;
+        void *p[MG_MAX_LEVELS][4];
+        explicit Restore(MgHierarchy *hh) : h(hh)
+        {
+            for (int l = 0; l < h->L; ++l) {
+                p[l][0] = h->lv[l].vx;
+                p[l][1] = h->lv[l].vy;
+                p[l][2] = h->lv[l].sx;
+                p[l][3] = h->lv[l].sy;
+            }
+        }
+        ~Restore()
+        {
+            for (int l = 0; l < h->L; ++l) {
+                h->lv[l].vx = p[l][0];
+                h->lv[l].vy = p[l][1];
+                h->lv[l].sx = p[l][2];
+                h->lv[l].sy = p[l][3];
+            }
+        }
+    } restore(h);
+    auto smooth_level = [&](MgLevel &f, int l, int phase) -> int {
+        bool swapped = false;
+        const int r = smooth_buffers<Ti>(level_grid<Ti>(f), level_coeffs<Ti>(f), (Ti *)f.vx, (Ti *)f.vy, (Ti *)f.sx,
+                                         (Ti *)f.sy, level_spec(p, f, l, phase, sizeof(Ti)), run, s, hook, &swapped);
+        if (swapped) {
+            std::swap(f.vx, f.sx);
+            std::swap(f.vy, f.sy);
+        }
+        return r;
+    };
     LAUNCH(STOKES_K_MG, 1, (mg_cast<Tc, Ti>(l0.elems, rx, l0.bx, s)));
     LAUNCH(STOKES_K_MG, 1, (mg_cast<Tc, Ti>(l0.elems, ry, l0.by, s)));
     for (int l = 0; l < L; ++l) {
@@ -209,8 +246,7 @@ int enqueue_precond(MgHierarchy *h, const Tc *rx, const Tc *ry, Tc *zx, Tc *zy, 
     // down: smooth, residual, restrict
     for (int l = 0; l < L - 1; ++l) {
         MgLevel &f = h->lv[l];
-        st = smooth_buffers<Ti>(level_grid<Ti>(f), level_coeffs<Ti>(f), (Ti *)f.vx, (Ti *)f.vy, (Ti *)f.sx,
-                                (Ti *)f.sy, level_spec(p, f, l, 0, sizeof(Ti)), run, s, hook);
+        st = smooth_level(f, l, 0);
         if (st != STOKES_OK) return st;
         LAUNCH(STOKES_K_MG, 1, mg_residual<Ti>(f, s));
         LAUNCH(STOKES_K_MG, 1, mg_restrict<Ti>(f, h->lv[l + 1], s));
@@ -221,8 +257,7 @@ int enqueue_precond(MgHierarchy *h, const Tc *rx, const Tc *ry, Tc *zx, Tc *zy, 
     for (int l = L - 2; l >= 0; --l) {
         MgLevel &f = h->lv[l];
         LAUNCH(STOKES_K_MG, 1, mg_prolong_add<Ti>(f, h->lv[l + 1], s));
-        st = smooth_buffers<Ti>(level_grid<Ti>(f), level_coeffs<Ti>(f), (Ti *)f.vx, (Ti *)f.vy, (Ti *)f.sx,
-                                (Ti *)f.sy, level_spec(p, f, l, 1, sizeof(Ti)), run, s, hook);
+        st = smooth_level(f, l, 1);
         if (st != STOKES_OK) return st;
     }
     LAUNCH(STOKES_K_MG, 1, (mg_cast<Ti, Tc>(l0.elems, l0.vx, zx, s)));

@@ -61,9 +61,13 @@ int krylov_partials();
 template <typename T> // (<a, b>, <a, c>); c may be NULL
 cudaError_t kry_dot2(const KrylovView &k, const T *ax, const T *ay, const T *bx, const T *by, const T *cx,
                      const T *cy, cudaStream_t s);
-template <typename T> // q = M p (library eta_n: boundary nodes zero); out = (<p, q>, <p, r>)
-cudaError_t kry_apply_dot(const KrylovView &k, const GridDesc<T> &g, const T *ec, const T *en, const T *px,
-                          const T *py, T *qx, T *qy, const T *rx, const T *ry, cudaStream_t s);
+template <typename T> // q = M p (library eta_n: boundary nodes zero); out = (<p, q>, <p, r>);
+                      // ax, ay: coefficients from kry_coef, or NULL to form them per flux
+cudaError_t kry_apply_dot(const KrylovView &k, const GridDesc<T> &g, const T *ec, const T *en, const T *ax,
+                          const T *ay, const T *px, const T *py, T *qx, T *qy, const T *rx, const T *ry,
+                          cudaStream_t s);
+template <typename T> // ax = 2 eta_c / hx^2, ay = 2 eta_c / hy^2 at every cell (coef_x / coef_y)
+cudaError_t kry_coef(const KrylovView &k, const GridDesc<T> &g, const T *ec, T *ax, T *ay, cudaStream_t s);
 template <typename T> // (sum r^2 w, sum f^2 w), w = -1/diag(M) from ix, iy
 cudaError_t kry_energy(const KrylovView &k, const T *rx, const T *ry, const T *fx, const T *fy, const T *ix,
                        const T *iy, cudaStream_t s);

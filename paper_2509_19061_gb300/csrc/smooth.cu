@@ -8,8 +8,9 @@ namespace stokes {
 
 template <typename T>
 int smooth_buffers(const GridDesc<T> &g, const Coeffs<T> &k, T *vx, T *vy, T *sx, T *sy, const SmoothSpec &p,
-                   const RasRun &run, cudaStream_t s, LaunchHook &hook)
+                   const RasRun &run, cudaStream_t s, LaunchHook &hook, bool *swapped)
 {
+    if (swapped) *swapped = false;
     const T omega = (T)p.omega;
     int st = STOKES_OK;
 #define LAUNCH(kind, nk, expr)                                                                                     \
@@ -60,14 +61,19 @@ int smooth_buffers(const GridDesc<T> &g, const Coeffs<T> &k, T *vx, T *vy, T *sx
             ++passes;
         }
     }
-    if (passes & 1) LAUNCH(STOKES_K_COPY, 1, launch_copy_velocity<T>(g, ax, ay, vx, vy, s));
+    if (passes & 1) {
+        if (swapped)
+            *swapped = true; // the result stays in (sx, sy); the caller swaps its pointers
+        else
+            LAUNCH(STOKES_K_COPY, 1, launch_copy_velocity<T>(g, ax, ay, vx, vy, s));
+    }
 #undef LAUNCH
     return STOKES_OK;
 }
 
 template int smooth_buffers<float>(const GridDesc<float> &, const Coeffs<float> &, float *, float *, float *,
-                                   float *, const SmoothSpec &, const RasRun &, cudaStream_t, LaunchHook &);
+                                   float *, const SmoothSpec &, const RasRun &, cudaStream_t, LaunchHook &, bool *);
 template int smooth_buffers<double>(const GridDesc<double> &, const Coeffs<double> &, double *, double *, double *,
-                                    double *, const SmoothSpec &, const RasRun &, cudaStream_t, LaunchHook &);
+                                    double *, const SmoothSpec &, const RasRun &, cudaStream_t, LaunchHook &, bool *);
 
 } // namespace stokes

@@ -68,6 +68,11 @@ struct stokes_ctx {
     void *eta_c = nullptr, *eta_n = nullptr, *fx = nullptr, *fy = nullptr;
     void *bx = nullptr, *by = nullptr, *sx = nullptr, *sy = nullptr;
     void *ivx = nullptr, *ivy = nullptr; // 1/diag(M), read by the tile kernels and the energy sums
+    // flux coefficients 2 eta_c / hx^2, 2 eta_c / hy^2 of the outer operator
+    // apply, formed for viscosity version coef_version (eta_version counts the
+    // viscosity changes)
+    void *cax = nullptr, *cay = nullptr;
+    long long eta_version = 0, coef_version = -1;
     void *eta_c0 = nullptr, *eta_n0 = nullptr; // the caller's viscosity during a continuation
     double *uz_partials = nullptr, *uz_scal = nullptr; // Uzawa reductions; uz_scal: [eta_min, sum]
     std::vector<void *> aa;              // Anderson history: (depth+1) x (F, r) x 3 fields, then x_old (3)
@@ -323,6 +328,23 @@ MgOuter outer_of(const stokes_ctx *c)
 }
 
 // work vectors of the outer solve, allocated on first use
+// The flux coefficients of the current viscosity (allocated on first use).
+template <typename T>
+int ensure_coef(stokes_ctx *c, const KrylovView &kv)
+{
+    if (!c->cax) {
+        int st = alloc_field(c, &c->cax);
+        if (st == STOKES_OK) st = alloc_field(c, &c->cay);
+        if (st != STOKES_OK) return st;
+        c->coef_version = -1;
+    }
+    if (c->coef_version != c->eta_version) {
+        RUN(STOKES_K_COPY, 1, kry_coef<T>(kv, grid_of<T>(c), (const T *)c->eta_c, (T *)c->cax, (T *)c->cay, c->stream));
+        c->coef_version = c->eta_version;
+    }
+    return STOKES_OK;
+}
+
 int ensure_work(stokes_ctx *c)
 {
     if (c->kw[0]) return STOKES_OK;
@@ -489,7 +511,8 @@ int vcycle_impl(stokes_ctx *c, T *vx, T *vy, const T *p, const stokes_mg_params 
                 CK(cudaMemcpyAsync(piy, ziy, ib, cudaMemcpyDeviceToDevice, c->stream));
                 for (int k = 0; k < params->inner_its; ++k) {
                     RUN(STOKES_K_APPLY, 2,
-                        kry_apply_dot<Ti>(kv, gi, (const Ti *)l0.ec, (const Ti *)l0.en, pix, piy, qix, qiy, rix, riy,
+                        kry_apply_dot<Ti>(kv, gi, (const Ti *)l0.ec, (const Ti *)l0.en, (const Ti *)nullptr,
+                                          (const Ti *)nullptr, pix, piy, qix, qiy, rix, riy,
                                           c->stream));
                     double pq = 0.0, pr = 0.0;
                     if ((st2 = read2(c, &pq, &pr)) != STOKES_OK) return st2;
@@ -517,13 +540,15 @@ int vcycle_impl(stokes_ctx *c, T *vx, T *vy, const T *p, const stokes_mg_params 
         st = params->inner_dtype == STOKES_F64 ? refine(double{}) : refine(float{});
         if (st != STOKES_OK) return st;
     } else if (params->krylov && verdict == 0) {
+        if ((st = ensure_coef<T>(c, kv)) != STOKES_OK) return st;
         st = replay_graph(c);
         if (st != STOKES_OK) return st;
         CK(cudaMemcpyAsync(px, zx, c->elems * c->esize, cudaMemcpyDeviceToDevice, c->stream));
         CK(cudaMemcpyAsync(py, zy, c->elems * c->esize, cudaMemcpyDeviceToDevice, c->stream));
         for (;;) {
             RUN(STOKES_K_APPLY, 2,
-                kry_apply_dot<T>(kv, g, (const T *)c->eta_c, (const T *)c->eta_n, px, py, qx, qy, rx, ry,
+                kry_apply_dot<T>(kv, g, (const T *)c->eta_c, (const T *)c->eta_n, (const T *)c->cax,
+                                 (const T *)c->cay, px, py, qx, qy, rx, ry,
                                  c->stream));
             double pq = 0.0, pr = 0.0;
             if ((st = read2(c, &pq, &pr)) != STOKES_OK) return st;
@@ -594,6 +619,7 @@ int set_stage(stokes_ctx *c, double theta)
     RUN(STOKES_K_COPY, 1,
         launch_inv_diag<T>(g, (const T *)c->eta_c, (const T *)c->eta_n, (T *)c->ivx, (T *)c->ivy, c->stream));
     mg_invalidate(c->mg);
+    ++c->eta_version;
     if (c->gexec) { // the graph holds the old hierarchy's buffers
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
@@ -761,6 +787,7 @@ int uzawa_impl(stokes_ctx *c, T *vx, T *vy, T *p, const stokes_uzawa_params *u, 
         RUN(STOKES_K_COPY, 1,
             launch_inv_diag<T>(g, (const T *)c->eta_c, (const T *)c->eta_n, (T *)c->ivx, (T *)c->ivy, c->stream));
         mg_invalidate(c->mg);
+        ++c->eta_version;
         if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);
             c->gexec = nullptr;
@@ -859,7 +886,8 @@ int stokes_destroy(stokes_ctx *c)
     mg_destroy(c->mg);
     prof_flush(c);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
-    void *fields[] = {c->eta_c, c->eta_n, c->fx, c->fy, c->bx, c->by, c->sx, c->sy, c->ivx, c->ivy, c->partials,
+    void *fields[] = {c->eta_c, c->eta_n, c->fx, c->fy, c->bx, c->by, c->sx, c->sy, c->ivx, c->ivy, c->cax, c->cay,
+                      c->partials,
                       c->dsum, c->dstatus, c->eta_c0, c->eta_n0, c->uz_partials, c->uz_scal};
     for (void *f : fields)
         if (f) cudaFree(f);
@@ -910,6 +938,7 @@ int stokes_set_viscosity(stokes_ctx *c, const void *eta_c, const void *eta_n)
     }
     c->have_eta = true;
     mg_invalidate(c->mg);
+    ++c->eta_version;
     if (c->gexec) { // the graph holds the old hierarchy's buffers
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
