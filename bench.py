@@ -421,7 +421,7 @@ def e2e_measure(args, ctx, prob, stream, world, barrier=lambda: None):
     drained = [torch.cuda.Event() for _ in range(2)]
     k = args.k
     o = args.overlap if args.overlap is not None else k - 1
-    steps = max(2, args.steps // 2)
+    steps = max(2, args.steps)
 
     def h2d(i):
         b = dev[i % 2]

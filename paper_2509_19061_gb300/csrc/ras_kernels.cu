@@ -551,7 +551,10 @@ __device__ __forceinline__ PairCell pair_cell(const RasArgs<float> &a, const Win
     return p;
 }
 
-template <class LD>
+// SQ: square cells (1/hx = 1/hy and 1/hx^2 = 1/hy^2 bit for bit), where the
+// coefficient of Tyy equals that of Txx and Sy equals Sx: the kernel keeps
+// one of each (fewer registers, one packed multiply less per row).
+template <bool SQ, class LD>
 __device__ __forceinline__ void pair_setup(const RasArgs<float> &a, const Window &w, PairCells &c, int lane, int strip,
                                            LD &&ld)
 {
@@ -566,7 +569,7 @@ __device__ __forceinline__ void pair_setup(const RasArgs<float> &a, const Window
         c.vx[r] = pk(p0.vx, p1.vx);
         c.vy[r] = pk(p0.vy, p1.vy);
         c.ax[r] = pk(coef_x(g, p0.ec), coef_x(g, p1.ec));
-        c.ay[r] = pk(coef_y(g, p0.ec), coef_y(g, p1.ec));
+        c.ay[r] = SQ ? c.ax[r] : pk(coef_y(g, p0.ec), coef_y(g, p1.ec));
         c.en[r] = pk(p0.en, p1.en);
         c.bx[r] = pk(p0.bx, p1.bx);
         c.by[r] = pk(p0.by, p1.by);
@@ -590,20 +593,22 @@ __device__ __forceinline__ void pair_setup(const RasArgs<float> &a, const Window
 
 // fluxes of row r: Txx, Tyy, Sx, Sy (vy_n: the vy pair of the row below r,
 // vx_s: the vx pair of the row above it, both before this sweep)
+template <bool SQ>
 __device__ __forceinline__ PairFlux pair_flux(f2 ax, f2 ay, f2 en, f2 vx, f2 vy, f2 vy_n, f2 vx_s, f2 ihx, f2 ihy)
 {
     PairFlux F;
     F.txx = mul2r(ax, sub2(east_pair(vx), vx));
-    F.tyy = mul2r(ay, sub2(vy_n, vy));
+    F.tyy = mul2r(SQ ? ax : ay, sub2(vy_n, vy));
     const f2 sh = mul2(en, fma2(sub2(vx, vx_s), ihy, mul2(sub2(vy, west_pair(vy)), ihx)));
     F.sx = mul2r(sh, ihy);
-    F.sy = mul2r(sh, ihx);
+    F.sy = SQ ? F.sx : mul2r(sh, ihx);
     return F;
 }
 
 // ks local sweeps of the window in registers, then the write-back of the
 // tile's own unknowns.  Ends with a barrier.  edge: [buffer][kind][strip + 1]
 // [lane] pairs, strips -1 and ns all zero.
+template <bool SQ>
 __device__ __forceinline__ void pair_sweeps(const RasArgs<float> &a, const Window &w, PairCells &c, int lane, int strip,
                                             f2 *edge, int es)
 {
@@ -621,7 +626,7 @@ __device__ __forceinline__ void pair_sweeps(const RasArgs<float> &a, const Windo
         const f2 sh_below = mul2(c.en_below, fma2(sub2(vx_below, c.vx[PR - 1]), ihy,
                                                   mul2(sub2(vy_below, west_pair(vy_below)), ihx)));
         const f2 sx_below = mul2r(sh_below, ihy);
-        PairFlux F0 = pair_flux(c.ax[0], c.ay[0], c.en[0], c.vx[0], c.vy[0], PR > 1 ? c.vy[1] : vy_below, vx_above,
+        PairFlux F0 = pair_flux<SQ>(c.ax[0], c.ay[0], c.en[0], c.vx[0], c.vy[0], PR > 1 ? c.vy[1] : vy_below, vx_above,
                                 ihx, ihy);
         f2 tyy_s = tyy_above;
 #pragma unroll
@@ -629,7 +634,7 @@ __device__ __forceinline__ void pair_sweeps(const RasArgs<float> &a, const Windo
             // fluxes of row r + 1 read the old vx of row r: form them before row r moves
             PairFlux F1 = F0;
             if (r + 1 < PR)
-                F1 = pair_flux(c.ax[r + 1], c.ay[r + 1], c.en[r + 1], c.vx[r + 1], c.vy[r + 1],
+                F1 = pair_flux<SQ>(c.ax[r + 1], c.ay[r + 1], c.en[r + 1], c.vx[r + 1], c.vy[r + 1],
                                r + 2 < PR ? c.vy[r + 2] : vy_below, c.vx[r], ihx, ihy);
             const f2 sx_n = r + 1 < PR ? F1.sx : sx_below;
             const f2 mx = add2(sub2(F0.txx, west_pair(F0.txx)), sub2(sx_n, F0.sx));
@@ -668,7 +673,7 @@ __device__ __forceinline__ void pair_sweeps(const RasArgs<float> &a, const Windo
 // the next two tiles are in flight while a tile is swept (one tile of
 // prefetch leaves short sweeps waiting on HBM latency).  The timeout
 // handling is that of k_ras_tma, waiting for every copy in flight.
-template <int MAXT, int NST>
+template <int MAXT, int NST, bool SQ>
 __global__ void __launch_bounds__(MAXT, 1) k_ras_pair(const __grid_constant__ TmaMaps maps, RasArgs<float> a)
 {
     constexpr int NF = 8;
@@ -730,7 +735,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_ras_pair(const __grid_constant__ Tm
         const Window w = window_of(a, tile);
         const int dx = w.ox0 - (w.ox0 & ~(ALIGN - 1));
         PairCells c;
-        pair_setup(a, w, c, lane, strip, [&](int f, int wy, int wx) { return stage[f * SP + wy * BW + wx + dx]; });
+        pair_setup<SQ>(a, w, c, lane, strip, [&](int f, int wy, int wx) { return stage[f * SP + wy * BW + wx + dx]; });
         edge[((0 * PAIR_EDGE_KINDS + 0) * es + strip + 1) * 32 + lane] = c.vx[0];
         edge[((0 * PAIR_EDGE_KINDS + 1) * es + strip + 1) * 32 + lane] = c.vy[0];
         edge[((0 * PAIR_EDGE_KINDS + 2) * es + strip + 1) * 32 + lane] = c.vx[PR - 1];
@@ -739,7 +744,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_ras_pair(const __grid_constant__ Tm
         const int refill = tile + NST * grid;
         if (threadIdx.x == 0 && refill < ntiles) issue(refill, j);
         phases ^= 1u << j;
-        pair_sweeps(a, w, c, lane, strip, edge, es);
+        pair_sweeps<SQ>(a, w, c, lane, strip, edge, es);
         tile += grid;
         j = NST > 1 ? (j + 1) % NST : 0;
     }
@@ -1305,8 +1310,18 @@ cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const 
         void (*kern)(TmaMaps, RasArgs<T>) = pick_tma<T>(p);
         if constexpr (sizeof(T) == 4) {
             if (p.kind == PLAN_PAIR) {
-                if (p.nstage == 2) kern = p.threads <= 384 ? k_ras_pair<384, 2> : k_ras_pair<PAIR_MAX_THREADS, 2>;
-                else kern = p.threads <= 384 ? k_ras_pair<384, 1> : k_ras_pair<PAIR_MAX_THREADS, 1>;
+                const bool sq = g.ihx == g.ihy && g.ihx2 == g.ihy2;
+                if (sq) {
+                    if (p.nstage == 2)
+                        kern = p.threads <= 384 ? k_ras_pair<384, 2, true> : k_ras_pair<PAIR_MAX_THREADS, 2, true>;
+                    else
+                        kern = p.threads <= 384 ? k_ras_pair<384, 1, true> : k_ras_pair<PAIR_MAX_THREADS, 1, true>;
+                } else {
+                    if (p.nstage == 2)
+                        kern = p.threads <= 384 ? k_ras_pair<384, 2, false> : k_ras_pair<PAIR_MAX_THREADS, 2, false>;
+                    else
+                        kern = p.threads <= 384 ? k_ras_pair<384, 1, false> : k_ras_pair<PAIR_MAX_THREADS, 1, false>;
+                }
             }
         }
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);

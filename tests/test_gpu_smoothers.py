@@ -447,6 +447,30 @@ def test_pair_kernel_matches_the_column_kernel(api, nx, ny, tile, k, o):
         assert np.array_equal(outs[0][0], jac[0]) and np.array_equal(outs[0][1], jac[1])
 
 
+@pytest.mark.parametrize("tile,k,o", [((48, 64), 8, 7), ((56, 32), 4, 3), ((62, 56), 8, 0), ((48, 32), 3, 2)])
+def test_pair_kernel_square_cells(api, tile, k, o):
+    """Square cells (hx = hy bit for bit: 300 x 200 cells on 1.5 x 1.0) take
+    the pair kernel's square-cell form, which keeps one coefficient for Txx
+    and Tyy and one scaled shear; its fields equal those of the one-column
+    kernel value for value, and those of global fused Jacobi for o >= k - 1."""
+    nx, ny = 300, 200
+    prob = rand_problem(nx, ny, 47, lx=1.5, ly=1.0)
+    assert prob.lx / nx == prob.ly / ny
+    v0 = inputs.random_velocity(nx, ny, 48, 0.1)
+    outs = []
+    for pair in (1, 0):
+        r = Run(api, prob, "f32", v0)
+        r.ctx.set_option(api.STOKES_OPT_PAIRED, pair)
+        r.smooth(variant="ras", sweeps=11, tile=tile, k=k, overlap=o, seed=79)
+        outs.append(r.v())
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    if o >= k - 1:
+        r = Run(api, prob, "f32", v0)
+        r.smooth(variant="fused", sweeps=11)
+        jac = r.v()
+        assert np.array_equal(outs[0][0], jac[0]) and np.array_equal(outs[0][1], jac[1])
+
+
 def test_pair_kernel_selection(api):
     plan = api.stokes_tile_kernel_plan
     assert plan(1024, 1024, (56, 32), 3, "f32")[0] == "pair"       # 64-column window: default mode
