@@ -216,8 +216,13 @@ struct SmoothSpec {
 // With `swapped` non-null, a result that ends in (sx, sy) after an odd number
 // of passes is left there (*swapped = true) instead of being copied back; the
 // caller then treats (sx, sy) as the velocity and (vx, vy) as the scratch.
+// With a second scratch pair (tx, ty) (and no `swapped`), an odd number of
+// passes ends in (vx, vy) by alternating between the two scratch pairs.
 template <typename T>
 int smooth_buffers(const GridDesc<T> &g, const Coeffs<T> &k, T *vx, T *vy, T *sx, T *sy, const SmoothSpec &p,
-                   const RasRun &run, cudaStream_t s, LaunchHook &hook, bool *swapped = nullptr);
+                   const RasRun &run, cudaStream_t s, LaunchHook &hook, bool *swapped = nullptr, T *tx = nullptr,
+                   T *ty = nullptr);
+// ping-pong passes of one smoothing call (0 for RBGS, which works in place)
+int smooth_passes(const SmoothSpec &p);
 
 } // namespace stokes

@@ -125,6 +125,58 @@ __global__ void __launch_bounds__(RD_THREADS) k_cg_update(int nx, int ny, int pi
     block_store2(s0, 0.0, partials);
 }
 
+// <z, b> with z in its own precision (the V-cycle's result): (double) z is exact
+template <typename T, typename Tz>
+__global__ void __launch_bounds__(RD_THREADS) k_dot_z(int nx, int ny, int pitch, const Tz *__restrict__ zx,
+                                                      const Tz *__restrict__ zy, const T *__restrict__ bx,
+                                                      const T *__restrict__ by, double *__restrict__ partials)
+{
+    double s0 = 0.0;
+    for_unknowns(nx, ny, pitch, [&](size_t q, int comp) {
+        s0 = fma((double)(comp ? zy[q] : zx[q]), (double)(comp ? by[q] : bx[q]), s0);
+    });
+    block_store2(s0, 0.0, partials);
+}
+
+// p = (T) z + beta p at the unknowns, z in its own precision; FIRST: p = (T) z
+template <typename T, typename Tz, bool FIRST>
+__global__ void __launch_bounds__(RD_THREADS) k_direction_z(int nx, int ny, int pitch, double beta,
+                                                            const Tz *__restrict__ zx, const Tz *__restrict__ zy,
+                                                            T *__restrict__ px, T *__restrict__ py)
+{
+    const T bt = (T)beta;
+    for_unknowns(nx, ny, pitch, [&](size_t q, int comp) {
+        T *p = comp ? py : px;
+        const T z = (T)(comp ? zy : zx)[q];
+        p[q] = FIRST ? z : r_fma(bt, p[q], z);
+    });
+}
+
+// v += a p, r -= a q, bi = (Ti) r; returns (sum r_new^2 w, 0)
+template <typename T, typename Ti>
+__global__ void __launch_bounds__(RD_THREADS) k_cg_update_cast(int nx, int ny, int pitch, double a,
+                                                               const T *__restrict__ px, const T *__restrict__ py,
+                                                               const T *__restrict__ qx, const T *__restrict__ qy,
+                                                               T *__restrict__ vx, T *__restrict__ vy,
+                                                               T *__restrict__ rx, T *__restrict__ ry,
+                                                               const T *__restrict__ ix, const T *__restrict__ iy,
+                                                               Ti *__restrict__ bix, Ti *__restrict__ biy,
+                                                               double *__restrict__ partials)
+{
+    const T at = (T)a;
+    double s0 = 0.0;
+    for_unknowns(nx, ny, pitch, [&](size_t q, int comp) {
+        T *v = comp ? vy : vx;
+        T *r = comp ? ry : rx;
+        v[q] = r_fma(at, (comp ? py : px)[q], v[q]);
+        const T rn = r_fma(-at, (comp ? qy : qx)[q], r[q]);
+        r[q] = rn;
+        (comp ? biy : bix)[q] = (Ti)rn;
+        s0 = acc_sq(s0, rn, -(comp ? iy[q] : ix[q]));
+    });
+    block_store2(s0, 0.0, partials);
+}
+
 // p = z + beta p at the unknowns
 template <typename T>
 __global__ void __launch_bounds__(RD_THREADS) k_cg_direction(int nx, int ny, int pitch, double beta,
@@ -253,6 +305,49 @@ cudaError_t kry_update(const KrylovView &k, double a, const T *px, const T *py, 
     k_final2<<<1, 64, 0, s>>>(k.partials, RD_BLOCKS, k.out);
     return cudaGetLastError();
 }
+
+template <typename T, typename Tz>
+cudaError_t kry_dot_z(const KrylovView &k, const Tz *zx, const Tz *zy, const T *bx, const T *by, cudaStream_t s)
+{
+    k_dot_z<T, Tz><<<RD_BLOCKS, RD_THREADS, 0, s>>>(k.nx, k.ny, k.pitch, zx, zy, bx, by, k.partials);
+    k_final2<<<1, 64, 0, s>>>(k.partials, RD_BLOCKS, k.out);
+    return cudaGetLastError();
+}
+
+template <typename T, typename Tz>
+cudaError_t kry_direction_z(const KrylovView &k, double beta, const Tz *zx, const Tz *zy, T *px, T *py,
+                            cudaStream_t s)
+{
+    if (beta == 0.0)
+        k_direction_z<T, Tz, true><<<RD_BLOCKS, RD_THREADS, 0, s>>>(k.nx, k.ny, k.pitch, beta, zx, zy, px, py);
+    else
+        k_direction_z<T, Tz, false><<<RD_BLOCKS, RD_THREADS, 0, s>>>(k.nx, k.ny, k.pitch, beta, zx, zy, px, py);
+    return cudaGetLastError();
+}
+
+template <typename T, typename Ti>
+cudaError_t kry_update_cast(const KrylovView &k, double a, const T *px, const T *py, const T *qx, const T *qy, T *vx,
+                            T *vy, T *rx, T *ry, const T *ix, const T *iy, Ti *bix, Ti *biy, cudaStream_t s)
+{
+    k_cg_update_cast<T, Ti><<<RD_BLOCKS, RD_THREADS, 0, s>>>(k.nx, k.ny, k.pitch, a, px, py, qx, qy, vx, vy, rx, ry,
+                                                             ix, iy, bix, biy, k.partials);
+    k_final2<<<1, 64, 0, s>>>(k.partials, RD_BLOCKS, k.out);
+    return cudaGetLastError();
+}
+
+#define INST_Z(T, Tz)                                                                                              \
+    template cudaError_t kry_dot_z<T, Tz>(const KrylovView &, const Tz *, const Tz *, const T *, const T *,       \
+                                          cudaStream_t);                                                           \
+    template cudaError_t kry_direction_z<T, Tz>(const KrylovView &, double, const Tz *, const Tz *, T *, T *,     \
+                                                cudaStream_t);                                                     \
+    template cudaError_t kry_update_cast<T, Tz>(const KrylovView &, double, const T *, const T *, const T *,       \
+                                                const T *, T *, T *, T *, T *, const T *, const T *, Tz *, Tz *,  \
+                                                cudaStream_t);
+INST_Z(double, float)
+INST_Z(double, double)
+INST_Z(float, float)
+INST_Z(float, double)
+#undef INST_Z
 
 template <typename T>
 cudaError_t kry_direction(const KrylovView &k, double beta, const T *zx, const T *zy, T *px, T *py, cudaStream_t s)

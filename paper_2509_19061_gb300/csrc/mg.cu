@@ -28,6 +28,7 @@ struct MgHierarchy {
     int n = 0; // coarsest unknowns
     double *A = nullptr, *W = nullptr, *Ainv = nullptr, *bvec = nullptr, *xvec = nullptr;
     int *dstatus = nullptr;
+    const void *zx = nullptr, *zy = nullptr; // finest-level result of the last enqueued application
 };
 
 namespace {
@@ -236,8 +237,10 @@ int enqueue_precond(MgHierarchy *h, const Tc *rx, const Tc *ry, Tc *zx, Tc *zy, 
         }
         return r;
     };
-    LAUNCH(STOKES_K_MG, 1, (mg_cast<Tc, Ti>(l0.elems, rx, l0.bx, s)));
-    LAUNCH(STOKES_K_MG, 1, (mg_cast<Tc, Ti>(l0.elems, ry, l0.by, s)));
+    if (rx) {
+        LAUNCH(STOKES_K_MG, 1, (mg_cast<Tc, Ti>(l0.elems, rx, l0.bx, s)));
+        LAUNCH(STOKES_K_MG, 1, (mg_cast<Tc, Ti>(l0.elems, ry, l0.by, s)));
+    }
     for (int l = 0; l < L; ++l) {
         MgLevel &v = h->lv[l];
         LAUNCH(STOKES_K_COPY, 0, cudaMemsetAsync(v.vx, 0, v.elems * sizeof(Ti), s));
@@ -260,8 +263,12 @@ int enqueue_precond(MgHierarchy *h, const Tc *rx, const Tc *ry, Tc *zx, Tc *zy, 
         st = smooth_level(f, l, 1);
         if (st != STOKES_OK) return st;
     }
-    LAUNCH(STOKES_K_MG, 1, (mg_cast<Ti, Tc>(l0.elems, l0.vx, zx, s)));
-    LAUNCH(STOKES_K_MG, 1, (mg_cast<Ti, Tc>(l0.elems, l0.vy, zy, s)));
+    h->zx = l0.vx;
+    h->zy = l0.vy;
+    if (zx) {
+        LAUNCH(STOKES_K_MG, 1, (mg_cast<Ti, Tc>(l0.elems, l0.vx, zx, s)));
+        LAUNCH(STOKES_K_MG, 1, (mg_cast<Ti, Tc>(l0.elems, l0.vy, zy, s)));
+    }
 #undef LAUNCH
     return STOKES_OK;
 }
@@ -296,6 +303,14 @@ void mg_destroy(MgHierarchy *h)
 }
 
 int mg_levels(const MgHierarchy *h) { return h ? h->L : 0; }
+
+int mg_dtype(const MgHierarchy *h) { return h ? h->dtype : -1; }
+
+void mg_result(const MgHierarchy *h, const void **zx, const void **zy)
+{
+    *zx = h->zx;
+    *zy = h->zy;
+}
 
 const MgLevel &mg_level(const MgHierarchy *h, int l) { return h->lv[l]; }
 

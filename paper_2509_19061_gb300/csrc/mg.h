@@ -46,8 +46,17 @@ const MgLevel &mg_level(const MgHierarchy *h, int l);
 // precision `outer_dtype`, zero off the unknowns) is cast to the inner
 // precision, one V-cycle runs from a zero initial guess, and its result is
 // cast back into z.  Every buffer is (ny+1) x pitch of the finest level.
+// rx = NULL: no input cast (the caller has written r, in the inner precision,
+// to the finest level's right-hand side, mg_level(h, 0).bx / .by, beforehand);
+// zx = NULL: no output cast (z stays in the inner precision, in the buffers
+// mg_result reports after the enqueue).
 int mg_enqueue_precond(MgHierarchy *h, int outer_dtype, const void *rx, const void *ry, void *zx, void *zy,
                        const stokes_mg_params *params, const RasRun &run, cudaStream_t s, LaunchHook &hook);
+// The finest-level buffers that hold the V-cycle's result (inner precision)
+// at the end of the last enqueued application.
+void mg_result(const MgHierarchy *h, const void **zx, const void **zy);
+// Inner precision of a built hierarchy (STOKES_F32 / STOKES_F64).
+int mg_dtype(const MgHierarchy *h);
 
 // ---- outer-solve vector kernels (krylov.cu) ---------------------------------
 // Sums over the velocity unknowns, accumulated in FP64 in a fixed order; the
@@ -61,6 +70,14 @@ int krylov_partials();
 template <typename T> // (<a, b>, <a, c>); c may be NULL
 cudaError_t kry_dot2(const KrylovView &k, const T *ax, const T *ay, const T *bx, const T *by, const T *cx,
                      const T *cy, cudaStream_t s);
+template <typename T, typename Tz> // (<z, b>, 0) with z in its own precision
+cudaError_t kry_dot_z(const KrylovView &k, const Tz *zx, const Tz *zy, const T *bx, const T *by, cudaStream_t s);
+template <typename T, typename Tz> // p = (T) z + beta p (beta = 0: p = (T) z)
+cudaError_t kry_direction_z(const KrylovView &k, double beta, const Tz *zx, const Tz *zy, T *px, T *py,
+                            cudaStream_t s);
+template <typename T, typename Ti> // kry_update, and bi = (Ti) r_new at the unknowns
+cudaError_t kry_update_cast(const KrylovView &k, double a, const T *px, const T *py, const T *qx, const T *qy, T *vx,
+                            T *vy, T *rx, T *ry, const T *ix, const T *iy, Ti *bix, Ti *biy, cudaStream_t s);
 template <typename T> // q = M p (library eta_n: boundary nodes zero); out = (<p, q>, <p, r>);
                       // ax, ay: coefficients from kry_coef, or NULL to form them per flux
 cudaError_t kry_apply_dot(const KrylovView &k, const GridDesc<T> &g, const T *ec, const T *en, const T *ax,

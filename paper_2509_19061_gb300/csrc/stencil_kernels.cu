@@ -179,6 +179,80 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// Compensated FP32 sum (Knuth's TwoSum: the rounding error of every addition
+// is carried in lo), for the FP32 terms of one row of cells; added to an FP64
+// sum once per row, which keeps the FP64 pipe (1/64 of the FP32 rate on this
+// GPU) out of the per-cell work.  The error of hi + lo is of the order of
+// 2^-44 of the row sum, far below the 2^-24 rounding of each FP32 term.
+struct CompF {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float t)
+    {
+        const float s = __fadd_rn(hi, t);
+        const float bb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(t, bb));
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ void flush(double &S)
+    {
+        S += (double)hi + (double)lo;
+        hi = lo = 0.f;
+    }
+};
+
+// The FP32 energy sums: per cell the terms of CellSq<float> (a cell's vx and vy
+// terms added in FP32), per row a compensated FP32 sum, per thread an FP64 sum.
+template <bool MASK>
+__device__ __forceinline__ void energy_rows_f32(const GridDesc<float> &g, const float *__restrict__ eta_c,
+                                                const float *__restrict__ eta_n, const float *__restrict__ inv_dx,
+                                                const float *__restrict__ inv_dy, const float *__restrict__ fx,
+                                                const float *__restrict__ fy, const float *__restrict__ p,
+                                                const float *__restrict__ vx, const float *__restrict__ vy,
+                                                double &s_rv, double &s_rp, double &s_ff)
+{
+    const float ilap = (float)(1.0 / g.lap);
+    for (int j = blockIdx.x; j <= g.ny; j += gridDim.x) {
+        CompF rv, rp, ff;
+        for (int i = threadIdx.x; i <= g.nx; i += EN_THREADS) {
+            const size_t q = (size_t)j * g.pitch + i;
+            float m, d, vc;
+            float trv = 0.f, tff = 0.f;
+            bool any = false;
+            if (vx_unknown(g, j, i)) {
+                op_x<float, MASK>(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
+                const float b = p ? r_fma(r_sub(p[q], p[q - 1]), g.ihx, fx[q]) : fx[q];
+                const float wi = -(inv_dx ? inv_dx[q] : inv_diag(d));
+                const float r = r_sub(b, m);
+                trv = r_mul(r_mul(r, r), wi);
+                tff = r_mul(r_mul(fx[q], fx[q]), wi);
+                any = true;
+            }
+            if (vy_unknown(g, j, i)) {
+                op_y<float, MASK>(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
+                const float b = p ? r_fma(r_sub(p[q], p[q - g.pitch]), g.ihy, fy[q]) : fy[q];
+                const float wi = -(inv_dy ? inv_dy[q] : inv_diag(d));
+                const float r = r_sub(b, m);
+                const float a = r_mul(r_mul(r, r), wi), c = r_mul(r_mul(fy[q], fy[q]), wi);
+                trv = any ? r_add(trv, a) : a;
+                tff = any ? r_add(tff, c) : c;
+                any = true;
+            }
+            if (any) {
+                rv.add(trv);
+                ff.add(tff);
+            }
+            if (i < g.nx && j < g.ny) {
+                const float dv = r_fma(r_sub(vx[q + 1], vx[q]), g.ihx, r_mul(r_sub(vy[q + g.pitch], vy[q]), g.ihy));
+                rp.add(r_mul(r_mul(dv, dv), r_mul(eta_c[q], ilap)));
+            }
+        }
+        rv.flush(s_rv);
+        rp.flush(s_rp);
+        ff.flush(s_ff);
+    }
+}
+
 template <typename T, bool MASK = false>
 __global__ void __launch_bounds__(EN_THREADS) k_energy(GridDesc<T> g, const T *__restrict__ eta_c,
                                                        const T *__restrict__ eta_n, const T *__restrict__ inv_dx,
@@ -192,6 +266,9 @@ __global__ void __launch_bounds__(EN_THREADS) k_energy(GridDesc<T> g, const T *_
     double s_rv = 0.0, s_rp = 0.0, s_ff = 0.0;
     const T ilap = (T)(1.0 / g.lap);
     // rows round-robin over the blocks, columns over the threads (no index division)
+    if constexpr (sizeof(T) == 4)
+        energy_rows_f32<MASK>(g, eta_c, eta_n, inv_dx, inv_dy, fx, fy, p, vx, vy, s_rv, s_rp, s_ff);
+    else
     for (int j = blockIdx.x; j <= g.ny; j += gridDim.x)
     for (int i = threadIdx.x; i <= g.nx; i += EN_THREADS) {
         const size_t q = (size_t)j * g.pitch + i;

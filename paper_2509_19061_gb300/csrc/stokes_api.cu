@@ -67,6 +67,7 @@ struct stokes_ctx {
     cudaStream_t stream;
     void *eta_c = nullptr, *eta_n = nullptr, *fx = nullptr, *fy = nullptr;
     void *bx = nullptr, *by = nullptr, *sx = nullptr, *sy = nullptr;
+    void *sx2 = nullptr, *sy2 = nullptr; // second scratch pair (allocated by the first odd-pass smoothing)
     void *ivx = nullptr, *ivy = nullptr; // 1/diag(M), read by the tile kernels and the energy sums
     // flux coefficients 2 eta_c / hx^2, 2 eta_c / hy^2 of the outer operator
     // apply, formed for viscosity version coef_version (eta_version counts the
@@ -95,6 +96,7 @@ struct stokes_ctx {
     cudaStream_t gstream = nullptr;
     cudaEvent_t gev[2] = {nullptr, nullptr};
     cudaGraphExec_t gexec = nullptr;
+    const void *gz[2] = {nullptr, nullptr}; // where the captured V-cycle leaves z (inner precision, krylov = 1)
     unsigned char gkey[sizeof(stokes_mg_params)] = {};
     long long gkernels[STOKES_K_COUNT] = {};
 };
@@ -264,8 +266,15 @@ int smooth_impl(stokes_ctx *c, T *vx, T *vy, const stokes_smooth_params *p, int 
         k.bx = (const T *)c->fx;
         k.by = (const T *)c->fy;
     }
-    return smooth_buffers<T>(grid_of<T>(c), k, vx, vy, (T *)c->sx, (T *)c->sy, spec_of(p, ti, tj), run_opts(c),
-                             c->stream, hook);
+    const SmoothSpec spec = spec_of(p, ti, tj);
+    const int n_pass = smooth_passes(spec);
+    if (n_pass >= 3 && (n_pass & 1) && !c->sx2) { // second scratch pair: odd pass counts end in place
+        int st = alloc_field(c, &c->sx2);
+        if (st == STOKES_OK) st = alloc_field(c, &c->sy2);
+        if (st != STOKES_OK) return st;
+    }
+    return smooth_buffers<T>(grid_of<T>(c), k, vx, vy, (T *)c->sx, (T *)c->sy, spec, run_opts(c), c->stream, hook,
+                             nullptr, (T *)c->sx2, (T *)c->sy2);
 }
 
 template <typename T>
@@ -399,10 +408,16 @@ int ensure_graph(stokes_ctx *c, const stokes_mg_params *p)
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
     const bool inner = p->krylov == 2;
-    const int st = mg_enqueue_precond(c->mg, inner ? p->inner_dtype : c->dtype, inner ? c->iw[0] : c->kw[0],
-                                      inner ? c->iw[1] : c->kw[1], inner ? c->iw[2] : c->kw[2],
-                                      inner ? c->iw[3] : c->kw[3], p, run_opts(c), c->gstream, hook);
+    // flexible CG (krylov = 1) writes r in the inner precision itself and
+    // reads z where the V-cycle leaves it: no casts in the graph
+    const bool direct = p->krylov == 1;
+    const int st = direct ? mg_enqueue_precond(c->mg, c->dtype, nullptr, nullptr, nullptr, nullptr, p, run_opts(c),
+                                               c->gstream, hook)
+                          : mg_enqueue_precond(c->mg, inner ? p->inner_dtype : c->dtype, inner ? c->iw[0] : c->kw[0],
+                                               inner ? c->iw[1] : c->kw[1], inner ? c->iw[2] : c->kw[2],
+                                               inner ? c->iw[3] : c->kw[3], p, run_opts(c), c->gstream, hook);
     const cudaError_t e = cudaStreamEndCapture(c->gstream, &graph);
+    if (st == STOKES_OK && direct) mg_result(c->mg, &c->gz[0], &c->gz[1]);
     if (st != STOKES_OK) {
         if (graph) cudaGraphDestroy(graph);
         return st;
@@ -540,30 +555,43 @@ int vcycle_impl(stokes_ctx *c, T *vx, T *vy, const T *p, const stokes_mg_params 
         st = params->inner_dtype == STOKES_F64 ? refine(double{}) : refine(float{});
         if (st != STOKES_OK) return st;
     } else if (params->krylov && verdict == 0) {
+        // flexible CG: the V-cycle reads r from the finest level's right-hand
+        // side in the inner precision (written by the update kernel) and
+        // leaves z in the inner precision, read as such by <z, q> and p = z + beta p
         if ((st = ensure_coef<T>(c, kv)) != STOKES_OK) return st;
-        st = replay_graph(c);
+        auto fcg = [&](auto tag) -> int {
+            using Ti = decltype(tag);
+            const MgLevel &l0 = mg_level(c->mg, 0);
+            Ti *bix = (Ti *)l0.bx, *biy = (Ti *)l0.by;
+            const Ti *zix = (const Ti *)c->gz[0], *ziy = (const Ti *)c->gz[1];
+            RUN(STOKES_K_MG, 1, (mg_cast<T, Ti>(c->elems, rx, bix, c->stream)));
+            RUN(STOKES_K_MG, 1, (mg_cast<T, Ti>(c->elems, ry, biy, c->stream)));
+            int s2 = replay_graph(c);
+            if (s2 != STOKES_OK) return s2;
+            RUN(STOKES_K_MG, 1, (kry_direction_z<T, Ti>(kv, 0.0, zix, ziy, px, py, c->stream)));
+            for (;;) {
+                RUN(STOKES_K_APPLY, 2,
+                    kry_apply_dot<T>(kv, g, (const T *)c->eta_c, (const T *)c->eta_n, (const T *)c->cax,
+                                     (const T *)c->cay, px, py, qx, qy, rx, ry, c->stream));
+                double pq = 0.0, pr = 0.0;
+                if ((s2 = read2(c, &pq, &pr)) != STOKES_OK) return s2;
+                const double a = pr / pq;
+                RUN(STOKES_K_MG, 2,
+                    (kry_update_cast<T, Ti>(kv, a, px, py, qx, qy, vx, vy, rx, ry, ix, iy, bix, biy, c->stream)));
+                if ((s2 = read2(c, &num, nullptr)) != STOKES_OK) return s2;
+                ++it;
+                e = std::sqrt(num / den);
+                if ((verdict = check()) != 0) break;
+                if ((s2 = replay_graph(c)) != STOKES_OK) return s2;
+                RUN(STOKES_K_MG, 2, (kry_dot_z<T, Ti>(kv, zix, ziy, qx, qy, c->stream)));
+                double zq = 0.0;
+                if ((s2 = read2(c, &zq, nullptr)) != STOKES_OK) return s2;
+                RUN(STOKES_K_MG, 1, (kry_direction_z<T, Ti>(kv, -zq / pq, zix, ziy, px, py, c->stream)));
+            }
+            return STOKES_OK;
+        };
+        st = mg_dtype(c->mg) == STOKES_F64 ? fcg(double{}) : fcg(float{});
         if (st != STOKES_OK) return st;
-        CK(cudaMemcpyAsync(px, zx, c->elems * c->esize, cudaMemcpyDeviceToDevice, c->stream));
-        CK(cudaMemcpyAsync(py, zy, c->elems * c->esize, cudaMemcpyDeviceToDevice, c->stream));
-        for (;;) {
-            RUN(STOKES_K_APPLY, 2,
-                kry_apply_dot<T>(kv, g, (const T *)c->eta_c, (const T *)c->eta_n, (const T *)c->cax,
-                                 (const T *)c->cay, px, py, qx, qy, rx, ry,
-                                 c->stream));
-            double pq = 0.0, pr = 0.0;
-            if ((st = read2(c, &pq, &pr)) != STOKES_OK) return st;
-            const double a = pr / pq;
-            RUN(STOKES_K_MG, 2, kry_update<T>(kv, a, px, py, qx, qy, vx, vy, rx, ry, ix, iy, c->stream));
-            if ((st = read2(c, &num, nullptr)) != STOKES_OK) return st;
-            ++it;
-            e = std::sqrt(num / den);
-            if ((verdict = check()) != 0) break;
-            if ((st = replay_graph(c)) != STOKES_OK) return st;
-            RUN(STOKES_K_MG, 2, kry_dot2<T>(kv, zx, zy, qx, qy, (const T *)nullptr, (const T *)nullptr, c->stream));
-            double zq = 0.0;
-            if ((st = read2(c, &zq, nullptr)) != STOKES_OK) return st;
-            RUN(STOKES_K_MG, 1, kry_direction<T>(kv, -zq / pq, zx, zy, px, py, c->stream));
-        }
     } else {
         while (verdict == 0) {
             if ((st = replay_graph(c)) != STOKES_OK) return st;
@@ -886,7 +914,7 @@ int stokes_destroy(stokes_ctx *c)
     mg_destroy(c->mg);
     prof_flush(c);
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
-    void *fields[] = {c->eta_c, c->eta_n, c->fx, c->fy, c->bx, c->by, c->sx, c->sy, c->ivx, c->ivy, c->cax, c->cay,
+    void *fields[] = {c->eta_c, c->eta_n, c->fx, c->fy, c->bx, c->by, c->sx, c->sy, c->ivx, c->ivy, c->cax, c->cay, c->sx2, c->sy2,
                       c->partials,
                       c->dsum, c->dstatus, c->eta_c0, c->eta_n0, c->uz_partials, c->uz_scal};
     for (void *f : fields)
