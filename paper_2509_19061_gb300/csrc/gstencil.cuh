@@ -100,16 +100,16 @@ struct ApplyTile {
     T sy[AT_Y + 1][AT_X + 1];  // the same nodes: shear / hx
 };
 
+// The fluxes of the tile at (i0, j0) and its one-cell halo from the velocity
+// (px, py) into shared memory, ending with a barrier.
 template <typename T>
-__device__ __forceinline__ void apply_dot_tile(const GridDesc<T> &g, const T *__restrict__ ec,
-                                               const T *__restrict__ en, const T *__restrict__ ax,
-                                               const T *__restrict__ ay, const T *__restrict__ px,
-                                               const T *__restrict__ py, T *__restrict__ qx, T *__restrict__ qy,
-                                               const T *__restrict__ rx, const T *__restrict__ ry, int i0, int j0,
-                                               int tid, ApplyTile<T> &sm, double &s0, double &s1)
+__device__ __forceinline__ void flux_tile_stage(const GridDesc<T> &g, const T *__restrict__ ec,
+                                                const T *__restrict__ en, const T *__restrict__ ax,
+                                                const T *__restrict__ ay, const T *__restrict__ px,
+                                                const T *__restrict__ py, int i0, int j0, int tid, ApplyTile<T> &sm)
 {
     const size_t P = (size_t)g.pitch;
-    const int nt = AT_X * AT_Y, tx = tid % AT_X, ty = tid / AT_X;
+    const int nt = AT_X * AT_Y;
     for (int e = tid; e < AT_Y * (AT_X + 1); e += nt) {
         const int a = e / (AT_X + 1), b = e % (AT_X + 1);
         const int J = j0 + a, I = i0 - 1 + b;
@@ -144,6 +144,19 @@ __device__ __forceinline__ void apply_dot_tile(const GridDesc<T> &g, const T *__
         sm.sy[a][b] = r_mul(v, g.ihx);
     }
     __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void apply_dot_tile(const GridDesc<T> &g, const T *__restrict__ ec,
+                                               const T *__restrict__ en, const T *__restrict__ ax,
+                                               const T *__restrict__ ay, const T *__restrict__ px,
+                                               const T *__restrict__ py, T *__restrict__ qx, T *__restrict__ qy,
+                                               const T *__restrict__ rx, const T *__restrict__ ry, int i0, int j0,
+                                               int tid, ApplyTile<T> &sm, double &s0, double &s1)
+{
+    const size_t P = (size_t)g.pitch;
+    const int tx = tid % AT_X, ty = tid / AT_X;
+    flux_tile_stage<T>(g, ec, en, ax, ay, px, py, i0, j0, tid, sm);
     const int j = j0 + ty, i = i0 + tx;
     if (j <= g.ny && i <= g.nx) {
         const size_t q = (size_t)j * P + i;
