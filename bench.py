@@ -544,8 +544,9 @@ def solve_times(args, api):
 def batch_leg(args, api):
     """The batched workload: 256 seeded sinkers of uneven sizes (sides
     64..1024, contrasts 1e2..1e6), all advanced together by the batched path
-    versus a loop over one context per instance.  Smoothing: FP32 RAS (32 x 32,
-    k = 4, overlap 3), 20 sweeps per call, aggregate Gcell-updates/s.  Solve:
+    versus a loop over one context per instance.  Smoothing: FP32 RAS in the
+    schedule the autotuner picked for this batch, 20 sweeps per call,
+    aggregate Gcell-updates/s.  Solve:
     FP64 flexible CG around the FP32 V-cycle to E_v <= 1e-8 for every
     instance, wall time of the whole set (hierarchies and graphs built
     beforehand)."""

@@ -183,7 +183,8 @@ def tune_batch(api, probs, name, candidates=None, cache=None, tol=1e-8, max_cycl
     `name` in `cache` (when given) and returns (winner, table)."""
     import torch
     cands = candidates or [(32, 32, 4, 3), (56, 32, 4, 3), (32, 32, 8, 7), (32, 32, 4, 0), (56, 32, 4, 0),
-                           (32, 32, 8, 0), (56, 32, 8, 0), (32, 32, 2, 1), (16, 16, 4, 3)]
+                           (32, 32, 8, 0), (56, 32, 8, 0), (32, 32, 2, 1), (16, 16, 4, 3),
+                           (48, 32, 8, 7), (48, 64, 8, 7), (62, 56, 8, 0)]
     b = api.BatchContext([q.nx for q in probs], [q.ny for q in probs], [q.lx for q in probs],
                          [q.ly for q in probs], "f64")
     b.set_problems(probs)
@@ -223,7 +224,7 @@ if __name__ == "__main__":
     from . import build as _build
     ap = argparse.ArgumentParser(description="tune the RAS smoother per size/contrast bucket")
     ap.add_argument("--out", required=True, help="JSON cache to write")
-    ap.add_argument("--sizes", type=int, nargs="+", default=[256, 1024, 4096])
+    ap.add_argument("--sizes", type=int, nargs="*", default=[256, 1024, 4096])
     ap.add_argument("--contrasts", type=float, nargs="+", default=[1e2, 1e4, 1e6])
     ap.add_argument("--dtype", default="f64")
     ap.add_argument("--inner", default="f32")
@@ -234,7 +235,8 @@ if __name__ == "__main__":
     _build.build()
     cache = Cache(None)
     cache.path = a.out
-    tune_buckets(_api, a.sizes, a.contrasts, a.dtype, "f32", cache=cache)
+    if a.sizes:
+        tune_buckets(_api, a.sizes, a.contrasts, a.dtype, "f32", cache=cache)
     if a.f64_sizes:
         f64c = [c for c in DEFAULT_CANDIDATES if c[0] <= 32]
         tune_buckets(_api, a.f64_sizes, a.contrasts, a.dtype, "f64", candidates=f64c, cache=cache)

@@ -140,6 +140,7 @@ struct TileLaunch {
     const int *tmap;  // table entry of every tile
     const void *maps; // per-instance tensor maps (TMA staging), or NULL
     int count, total, ti, tj, ks, overlap;
+    bool square;      // every instance has square cells
 };
 
 // one instance of a group: level grid and coefficients, velocity and scratch
@@ -164,7 +165,7 @@ struct Group {
 // the ping-pong of smooth_buffers for every instance of `gi` at once
 template <typename T>
 int plan_group(Owned &o, const std::vector<GInst<T>> &gi, const RasForm &f, bool walls, bool single, bool tma,
-               const BLevel<T> *lev, Group<T> *out, cudaStream_t s)
+               int pair_mode, const BLevel<T> *lev, Group<T> *out, cudaStream_t s)
 {
     *out = Group<T>();
     if (gi.empty() || f.sweeps == 0) return STOKES_OK;
@@ -215,7 +216,9 @@ int plan_group(Owned &o, const std::vector<GInst<T>> &gi, const RasForm &f, bool
             std::swap(ay[q], by[q]);
         }
         const int ov = single ? 0 : f.overlap;
-        if (ras_batched_smem_bytes(shi, shj, ov, sizeof(T)) > (size_t)ras_max_smem()) return STOKES_ERR_ARG;
+        // a TMA-staged shape (one-column or pair layout) fits by construction
+        const bool staged = tma && ras_batched_tma(shi, shj, ov, sizeof(T), pair_mode);
+        if (!staged && ras_batched_smem_bytes(shi, shj, ov, sizeof(T)) > (size_t)ras_max_smem()) return STOKES_ERR_ARG;
         TileLaunch<T> L;
         ST(upload(o, tab, &L.tab, s));
         {
@@ -225,9 +228,12 @@ int plan_group(Owned &o, const std::vector<GInst<T>> &gi, const RasForm &f, bool
             ST(upload(o, tm, &L.tmap, s));
         }
         L.maps = nullptr;
-        if (tma && ras_batched_tma(shi, shj, ov, sizeof(T))) {
+        L.square = true;
+        for (size_t q = 0; q < n; ++q)
+            L.square = L.square && tab[q].g.ihx == tab[q].g.ihy && tab[q].g.ihx2 == tab[q].g.ihy2;
+        if (staged) {
             std::vector<CUtensorMap> m(n * (ras_batched_maps_bytes() / sizeof(CUtensorMap)));
-            CK(ras_batched_encode<T>(tab.data(), (int)n, shi, shj, ov, m.data()));
+            CK(ras_batched_encode<T>(tab.data(), (int)n, shi, shj, ov, pair_mode, m.data()));
             const CUtensorMap *dm = nullptr;
             ST(upload(o, m, &dm, s));
             L.maps = dm;
@@ -255,7 +261,7 @@ int run_group(const Group<T> &G, const int *live, const RasRun &run, cudaStream_
     }
     for (const TileLaunch<T> &L : G.launches) {
         CK(launch_ras_batched<T>(L.tab, L.tmap, L.maps, L.count, L.total, L.ti, L.tj, L.ks, L.overlap, G.omega, live,
-                                 run, s));
+                                 run, L.square, s));
         ++*nk;
     }
     if (G.back) {
@@ -699,9 +705,9 @@ int plan_precond(stokes_batch *b, const stokes_mg_params *p, Precond<To, Ti> *P)
             f1.k = std::max(sweeps, 1);
             f1.overlap = 0;
             // zero-initialised walls of v and s at inner levels: no wall copies
-            ST(plan_group<Ti>(o, g1, f1, false, true, b->use_tma, P->lev[l], &P->grp[l][ph][0], s));
+            ST(plan_group<Ti>(o, g1, f1, false, true, b->use_tma, b->pair_mode, P->lev[l], &P->grp[l][ph][0], s));
             ST(plan_group<Ti>(o, g2, ras_form(sm, sweeps, seed, STOKES_SHIFT_SPLITMIX), false, false, b->use_tma,
-                              P->lev[l], &P->grp[l][ph][1], s));
+                              b->pair_mode, P->lev[l], &P->grp[l][ph][1], s));
         }
     }
     std::vector<BDense<Ti>> dt(n);
@@ -1036,7 +1042,7 @@ int smooth_impl(stokes_batch *b, void *vx, void *vy, const void *p, const stokes
         RasForm ff = f;
         ff.shifts = shifts.empty() ? nullptr : shifts.data();
         ST(upload(b->sm_own, lev, &dlev, b->stream));
-        ST(plan_group<T>(b->sm_own, gi, ff, true, false, b->use_tma, dlev, &G, b->stream));
+        ST(plan_group<T>(b->sm_own, gi, ff, true, false, b->use_tma, b->pair_mode, dlev, &G, b->stream));
         b->sm_key = key;
         b->sm_shifts = shifts;
         b->sm_v[0] = vx;

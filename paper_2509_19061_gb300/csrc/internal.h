@@ -137,20 +137,24 @@ struct BatchTiles {
 // (else found by binary search on tile_begin).  `maps` (device, may be
 // NULL): the tensor maps of every instance, filled by ras_batched_encode;
 // with them the windows are staged by TMA.  `live` (device, may be NULL):
-// tiles of entries whose live[inst] is 0 are skipped.
+// tiles of entries whose live[inst] is 0 are skipped.  `square`: every
+// instance has square cells (1/hx = 1/hy bit for bit), which lets an FP32
+// launch of the pair layout use its square-cell form.
 template <typename T>
 cudaError_t launch_ras_batched(const BatchTiles<T> *tab, const int *tmap, const void *maps, int count, int total,
                                int ti, int tj, int ksweeps, int overlap, T omega, const int *live, const RasRun &run,
-                               cudaStream_t s);
+                               bool square, cudaStream_t s);
 // Shared memory one batched launch needs (tile size and overlap only).
 size_t ras_batched_smem_bytes(int ti, int tj, int overlap, size_t elem);
-// Whether a batched launch of this shape can stage windows by TMA, the bytes
-// of one instance's tensor maps, and their encoding for the host table `tab`
-// (count entries) into the host buffer `out` (count * ras_batched_maps_bytes()).
-bool ras_batched_tma(int ti, int tj, int overlap, size_t elem);
+// Whether a batched launch of this shape can stage windows by TMA (in the
+// one-column or, with pair_mode as STOKES_OPT_PAIRED, the pair layout), the
+// bytes of one instance's tensor maps, and their encoding for the host table
+// `tab` (count entries) into the host buffer `out` (count * ras_batched_maps_bytes()).
+bool ras_batched_tma(int ti, int tj, int overlap, size_t elem, int pair_mode);
 size_t ras_batched_maps_bytes();
 template <typename T>
-cudaError_t ras_batched_encode(const BatchTiles<T> *tab, int count, int ti, int tj, int overlap, void *out);
+cudaError_t ras_batched_encode(const BatchTiles<T> *tab, int count, int ti, int tj, int overlap, int pair_mode,
+                               void *out);
 int ras_max_smem();
 
 // Record a failed CUDA call for stokes_last_cuda_error; returns

@@ -974,6 +974,117 @@ __global__ void __launch_bounds__(MAXT, MINB) k_ras_batched_tma(const BatchTiles
     }
 }
 
+// Batched form of the packed-pair FP32 kernel: the tile walk, per-instance
+// tensor maps and live-instance skipping of k_ras_batched_tma, the window
+// setup and sweeps of k_ras_pair (one staging buffer: the next tile's copy is
+// issued once the current window is in registers and lands while it is swept).
+template <int MAXT, bool SQ>
+__global__ void __launch_bounds__(MAXT, 1) k_ras_batched_pair(const BatchTiles<float> *__restrict__ tab,
+                                                              const int *__restrict__ tmap,
+                                                              const TmaMaps *__restrict__ maps, int count, int total,
+                                                              const int *__restrict__ live, RasArgs<float> shape)
+{
+    constexpr int NF = 8;
+    constexpr int ALIGN = 4; // TMA x coordinates are multiples of 16 bytes
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t off = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
+    float *const stage = reinterpret_cast<float *>(smem_raw + off);
+    const int BW = shape.bw, SP = shape.stage;
+    const int es = shape.strips + 2;
+    f2 *const edge = reinterpret_cast<f2 *>(stage + NF * SP);
+    const int lane = (int)threadIdx.x & 31, strip = (int)threadIdx.x >> 5;
+    const uint32_t box_bytes = (uint32_t)(BW * shape.wym * (int)sizeof(float));
+
+    constexpr int CH = 8; // chunks of consecutive tiles per CTA, as in k_ras_batched_tma
+    const int stride = (int)gridDim.x * CH;
+    auto end_of = [&](int e) { return tab[e].tile_begin + tab[e].tg.ntx * tab[e].tg.nty; };
+    int e = 0, tb = 0, te = 0;
+    auto seek = [&](int t) {
+        if (t < tb || t >= te) {
+            e = batch_entry(tab, tmap, count, t);
+            tb = tab[e].tile_begin;
+            te = end_of(e);
+        }
+    };
+    auto step = [&](int t) { return (t + 1) % CH ? t + 1 : t + 1 - CH + stride; };
+    auto advance = [&](int t) {
+        while (t < total) {
+            seek(t);
+            if (live && !live[tab[e].inst]) {
+                const int cend = (t / CH + 1) * CH;
+                t = te < cend ? te : cend - CH + stride;
+                continue;
+            }
+            break;
+        }
+        return t;
+    };
+
+    int ea = -1;
+    RasArgs<float> a = shape;
+    int acquired = -1;
+    auto issue = [&](int t, int e, int tb) {
+        Window w;
+        if (e == ea) {
+            w = window_of(a, t - tb);
+        } else {
+            const RasArgs<float> b = batch_args(shape, tab[e]);
+            w = window_of(b, t - tb);
+        }
+        const int xs = w.ox0 & ~(ALIGN - 1);
+        if (e != acquired) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) fence_tensormap_acquire(&maps[e].m[f]);
+            acquired = e;
+        }
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&bar, NF * box_bytes);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) tma_load_2d(stage + f * SP, &maps[e].m[f], xs, w.oy0, &bar);
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_proxy_async();
+    }
+    // edge rows of the missing strips -1 and ns stay zero (the window's zero border)
+    for (int t = (int)threadIdx.x; t < 2 * PAIR_EDGE_KINDS * es * 32; t += (int)blockDim.x) edge[t].u = 0ull;
+    __syncthreads();
+    int tile = advance((int)blockIdx.x * CH);
+    if (threadIdx.x == 0 && tile < total) issue(tile, e, tb);
+    uint32_t phase = 0;
+    while (tile < total) {
+        const bool ok = mbar_wait_bounded(&bar, phase, shape.wait_limit);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(shape.status, 1);
+                mbar_wait_bounded(&bar, phase, 4000000000LL);
+            }
+            __syncthreads();
+            return;
+        }
+        if (e != ea) {
+            a = batch_args(shape, tab[e]);
+            ea = e;
+        }
+        const Window w = window_of(a, tile - tb);
+        const int dx = w.ox0 - (w.ox0 & ~(ALIGN - 1));
+        PairCells c;
+        pair_setup<SQ>(a, w, c, lane, strip, [&](int f, int wy, int wx) { return stage[f * SP + wy * BW + wx + dx]; });
+        edge[((0 * PAIR_EDGE_KINDS + 0) * es + strip + 1) * 32 + lane] = c.vx[0];
+        edge[((0 * PAIR_EDGE_KINDS + 1) * es + strip + 1) * 32 + lane] = c.vy[0];
+        edge[((0 * PAIR_EDGE_KINDS + 2) * es + strip + 1) * 32 + lane] = c.vx[PR - 1];
+        edge[((0 * PAIR_EDGE_KINDS + 3) * es + strip + 1) * 32 + lane] = c.vy[PR - 1];
+        __syncthreads(); // staging buffer consumed, edge rows visible
+        const int next = advance(step(tile));
+        if (threadIdx.x == 0 && next < total) issue(next, e, tb);
+        phase ^= 1u;
+        pair_sweeps<SQ>(a, w, c, lane, strip, edge, es);
+        tile = next;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // general kernel: every field of the window in shared memory
 // ---------------------------------------------------------------------------
@@ -1348,19 +1459,22 @@ size_t ras_batched_smem_bytes(int ti, int tj, int overlap, size_t elem)
     return plan_ras(ti, tj, ti, tj, overlap, elem, false).smem;
 }
 
-bool ras_batched_tma(int ti, int tj, int overlap, size_t elem)
+bool ras_batched_tma(int ti, int tj, int overlap, size_t elem, int pair_mode)
 {
-    return plan_ras(ti, tj, ti, tj, overlap, elem, true).kind == PLAN_TMA;
+    const int kind = plan_ras(ti, tj, ti, tj, overlap, elem, true, pair_mode).kind;
+    return kind == PLAN_TMA || kind == PLAN_PAIR;
 }
 
 size_t ras_batched_maps_bytes() { return sizeof(TmaMaps); }
 
 template <typename T>
-cudaError_t ras_batched_encode(const BatchTiles<T> *tab, int count, int ti, int tj, int overlap, void *out)
+cudaError_t ras_batched_encode(const BatchTiles<T> *tab, int count, int ti, int tj, int overlap, int pair_mode,
+                               void *out)
 {
     constexpr int NF = KCfg<T>::INVD ? 8 : 6;
-    const RasPlan p = plan_ras(ti, tj, ti, tj, overlap, sizeof(T), true);
-    if (p.kind != PLAN_TMA) return cudaErrorInvalidValue;
+    // the pair and the one-column plans stage the same boxes
+    const RasPlan p = plan_ras(ti, tj, ti, tj, overlap, sizeof(T), true, pair_mode);
+    if (p.kind != PLAN_TMA && p.kind != PLAN_PAIR) return cudaErrorInvalidValue;
     TmaMaps *m = reinterpret_cast<TmaMaps *>(out);
     const int es = (int)sizeof(T);
     for (int i = 0; i < count; ++i) {
@@ -1383,15 +1497,16 @@ cudaError_t ras_batched_encode(const BatchTiles<T> *tab, int count, int ti, int 
 template <typename T>
 cudaError_t launch_ras_batched(const BatchTiles<T> *tab, const int *tmap, const void *maps, int count, int total,
                                int ti, int tj, int ksweeps, int overlap, T omega, const int *live, const RasRun &run,
-                               cudaStream_t s)
+                               bool square, cudaStream_t s)
 {
     // launch shape sized for the largest window (tile ti x tj grown by the
     // overlap): TMA staging through per-instance tensor maps when `maps` is
-    // given, else the register layout reading global memory, else the
-    // general kernel with one CTA per tile
-    const RasPlan p = plan_ras(ti, tj, ti, tj, overlap, sizeof(T), maps != nullptr);
+    // given (the FP32 pair layout for windows it takes, in its square-cell
+    // form when every instance has square cells), else the register layout
+    // reading global memory, else the general kernel with one CTA per tile
+    const RasPlan p = plan_ras(ti, tj, ti, tj, overlap, sizeof(T), maps != nullptr, maps ? run.pair_mode : 0);
     if (p.smem > (size_t)ras_max_smem()) return cudaErrorInvalidValue;
-    if (maps && p.kind != PLAN_TMA) return cudaErrorInvalidValue;
+    if (maps && p.kind != PLAN_TMA && p.kind != PLAN_PAIR) return cudaErrorInvalidValue;
     RasArgs<T> a{};
     a.omega = omega;
     a.ks = ksweeps;
@@ -1408,6 +1523,23 @@ cudaError_t launch_ras_batched(const BatchTiles<T> *tab, const int *tmap, const 
     a.wait_limit = run.wait_limit;
     if (total <= 0) return cudaSuccess;
     cudaError_t e;
+    if constexpr (sizeof(T) == 4) {
+        if (p.kind == PLAN_PAIR) {
+            // one staging buffer beside the edge rows
+            const size_t one = (size_t)8 * (size_t)p.stage * sizeof(float);
+            const size_t smem = one + (size_t)2 * PAIR_EDGE_KINDS * (p.strips + 2) * 32 * sizeof(f2) + 128;
+            void (*kern)(const BatchTiles<float> *, const int *, const TmaMaps *, int, int, const int *,
+                         RasArgs<float>);
+            if (square) kern = p.threads <= 384 ? k_ras_batched_pair<384, true> : k_ras_batched_pair<PAIR_MAX_THREADS, true>;
+            else kern = p.threads <= 384 ? k_ras_batched_pair<384, false> : k_ras_batched_pair<PAIR_MAX_THREADS, false>;
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            const int grid = std::min(total, sm_count());
+            kern<<<grid, p.threads, smem, s>>>(tab, tmap, reinterpret_cast<const TmaMaps *>(maps), count, total, live,
+                                               a);
+            return cudaGetLastError();
+        }
+    }
     if (p.kind == PLAN_TMA) {
         void (*kern)(const BatchTiles<T> *, const int *, const TmaMaps *, int, int, const int *, RasArgs<T>) =
             pick_batched_tma<T>(p);
@@ -1438,11 +1570,12 @@ cudaError_t launch_ras_batched(const BatchTiles<T> *tab, const int *tmap, const 
 }
 
 template cudaError_t launch_ras_batched<float>(const BatchTiles<float> *, const int *, const void *, int, int, int,
-                                               int, int, int, float, const int *, const RasRun &, cudaStream_t);
+                                               int, int, int, float, const int *, const RasRun &, bool, cudaStream_t);
 template cudaError_t launch_ras_batched<double>(const BatchTiles<double> *, const int *, const void *, int, int, int,
-                                                int, int, int, double, const int *, const RasRun &, cudaStream_t);
-template cudaError_t ras_batched_encode<float>(const BatchTiles<float> *, int, int, int, int, void *);
-template cudaError_t ras_batched_encode<double>(const BatchTiles<double> *, int, int, int, int, void *);
+                                                int, int, int, double, const int *, const RasRun &, bool,
+                                                cudaStream_t);
+template cudaError_t ras_batched_encode<float>(const BatchTiles<float> *, int, int, int, int, int, void *);
+template cudaError_t ras_batched_encode<double>(const BatchTiles<double> *, int, int, int, int, int, void *);
 
 template cudaError_t launch_ras<float>(const GridDesc<float> &, const Coeffs<float> &, float, const TileGrid &, int,
                                        int, const float *, const float *, float *, float *, const RasRun &,

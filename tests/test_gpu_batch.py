@@ -70,10 +70,14 @@ SIZES = [(40, 24), (64, 64), (100, 70), (33, 50), (8, 12)]
     dict(variant="jacobi", sweeps=5),
     dict(variant="fused", sweeps=6),
     dict(variant="blocked", sweeps=3, tile=(16, 16)),
+    dict(variant="ras", sweeps=9, tile=(56, 32), k=4, overlap=3, seed=5),    # 64-column windows: FP32 pair layout
+    dict(variant="ras", sweeps=17, tile=(48, 64), k=8, overlap=7, seed=3),   # 64 x 80 windows, 20 warps
 ])
 @pytest.mark.parametrize("tma", [True, False])
 def test_batched_smoothing_is_bitwise_the_single_context(api, dtype, kw, tma):
     import torch
+    if dtype == "f64" and kw.get("tile") == (48, 64):
+        pytest.skip("an FP64 64 x 80 window exceeds shared memory (STOKES_ERR_ARG in every path)")
     probs = problems(SIZES, 10)
     v0 = [inputs.random_velocity(q.nx, q.ny, 100 + i) for i, q in enumerate(probs)]
     p = [inputs.random_pressure(q.nx, q.ny, 200 + i, 0.5) for i, q in enumerate(probs)]
@@ -113,6 +117,62 @@ def test_batched_energy_matches_the_single_context(api, dtype):
     b.close()
 
 
+SQUARE_SIZES = [(64, 64), (100, 100), (48, 48), (130, 130), (7, 7)]
+
+
+@pytest.mark.parametrize("kw", [
+    dict(variant="ras", sweeps=9, tile=(56, 32), k=4, overlap=3, seed=5),
+    dict(variant="ras", sweeps=17, tile=(48, 64), k=8, overlap=7, seed=3),
+    dict(variant="ras", sweeps=10, tile=(62, 56), k=8, overlap=0, seed=8),
+])
+def test_batched_pair_layout_square_cells(api, kw):
+    """A batch whose instances all have square cells runs the pair layout in
+    its square-cell form; every instance equals its own context (which takes
+    the same form) value for value, and the exact-Jacobi schedules equal
+    global fused Jacobi."""
+    import torch
+    probs = problems(SQUARE_SIZES, 60)
+    assert all(q.lx / q.nx == q.ly / q.ny for q in probs)
+    v0 = [inputs.random_velocity(q.nx, q.ny, 600 + i) for i, q in enumerate(probs)]
+    ref = single_results(api, probs, "f32", v0, None, lambda c, vx, vy, pt: c.smooth(vx, vy, pt, **kw))
+    b = batch_context(api, probs, "f32")
+    vx, vy = b.pack([v[0] for v in v0], "vx"), b.pack([v[1] for v in v0], "vy")
+    b.smooth(vx, vy, None, **kw)
+    torch.cuda.synchronize()
+    for i in range(len(probs)):
+        assert np.array_equal(b.unpack(vx, "vx", i), ref[i][0]), (i, "vx")
+        assert np.array_equal(b.unpack(vy, "vy", i), ref[i][1]), (i, "vy")
+    if kw["overlap"] >= kw["k"] - 1:
+        jac = single_results(api, probs, "f32", v0, None,
+                             lambda c, vx, vy, pt: c.smooth(vx, vy, pt, variant="fused", sweeps=kw["sweeps"]))
+        for i in range(len(probs)):
+            assert np.array_equal(b.unpack(vx, "vx", i), jac[i][0]), (i, "vx")
+            assert np.array_equal(b.unpack(vy, "vy", i), jac[i][1]), (i, "vy")
+    b.close()
+
+
+def test_batched_pair_wait_timeout_is_reported(api):
+    """The batched pair kernel's bounded staging wait: a limit below zero
+    gives up at once, the timeout is reported, and the batch recovers."""
+    import torch
+    probs = problems([(64, 64), (100, 100)], 70)
+    b = batch_context(api, probs, "f32")
+    vx, vy = b.slab(), b.slab()
+    b.set_option(api.STOKES_OPT_WAIT_LIMIT_CYCLES, -1)
+    b.smooth(vx, vy, variant="ras", sweeps=4, tile=(56, 32), k=4, overlap=3)
+    with pytest.raises(api.StokesError) as ex:
+        b.energy(vx, vy)
+    assert ex.value.status == api.STOKES_ERR_TIMEOUT
+    b.set_option(api.STOKES_OPT_WAIT_LIMIT_CYCLES, 2000000000)
+    vx.zero_()
+    vy.zero_()
+    b.smooth(vx, vy, variant="ras", sweeps=4, tile=(56, 32), k=4, overlap=3)
+    e = b.energy(vx, vy)
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(e)) and np.all(e[:, 0] < e[:, 1])
+    b.close()
+
+
 MG_SIZES = [(64, 64), (96, 64), (80, 48), (128, 128), (32, 32)]
 
 
@@ -122,6 +182,7 @@ MG_SIZES = [(64, 64), (96, 64), (80, 48), (128, 128), (32, 32)]
     dict(variant="ras", tile=(16, 8), k=2, overlap=0, seed=9, nu_max=10),
     dict(variant="jacobi", nu_max=9),
     dict(variant="mixed", tile=(16, 16), k=4, overlap=0, seed=6, nu_max=10),
+    dict(variant="ras", tile=(56, 32), k=4, overlap=3, seed=2, nu_max=12),   # pair layout on the 64+ levels
 ])
 def test_batched_defect_correction_is_bitwise_the_single_context(api, dtype, inner, sm):
     """Three defect-correction cycles: every iterate is v += B(b - M v), with
@@ -225,16 +286,19 @@ def test_batched_wait_timeout_is_reported_and_recoverable(api):
     b.close()
 
 
-def test_full_batched_workload_samples_match_single_contexts(api):
+@pytest.mark.parametrize("tile,k,o", [((48, 32), 8, 7),   # the benchmark's (autotuned) schedule: pair layout
+                                      ((32, 32), 4, 3)])  # one-column TMA layout
+def test_full_batched_workload_samples_match_single_contexts(api, tile, k, o):
     """The batched workload at full size (256 seeded instances, sides 64 to
-    1024, 4.85e7 cells) in the benchmark's launch configuration (FP32 RAS
-    32 x 32, k = 4, overlap 3, TMA staging): eight sweeps; sampled instances
-    (the smallest, the largest and two others) equal their own contexts bit
-    for bit."""
+    1024, 4.85e7 cells) in the benchmark's launch configuration (FP32 RAS,
+    the autotuned 48 x 32, k = 8, overlap 7 on the pair layout, TMA staging)
+    and in the one-column layout: eight sweeps; sampled instances (the
+    smallest, the largest and two others) equal their own contexts bit for
+    bit."""
     import torch
     specs = inputs.batch_specs(seed=5, count=256)
     probs = [inputs.batch_problem(sp) for sp in specs]
-    kw = dict(variant="ras", sweeps=8, tile=(32, 32), k=4, overlap=3, seed=1)
+    kw = dict(variant="ras", sweeps=8, tile=tile, k=k, overlap=o, seed=1)
     b = batch_context(api, probs, "f32")
     vx, vy = b.slab(), b.slab()
     b.smooth(vx, vy, None, **kw)
