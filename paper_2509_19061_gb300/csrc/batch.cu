@@ -332,6 +332,7 @@ struct stokes_batch {
     std::vector<double> lx, ly;
     void *eta_c = nullptr, *eta_n = nullptr, *fx = nullptr, *fy = nullptr, *bx = nullptr, *by = nullptr;
     void *sx = nullptr, *sy = nullptr, *ivx = nullptr, *ivy = nullptr;
+    void *cax = nullptr, *cay = nullptr; // flux coefficients of the outer operator apply
     bool have_eta = false, have_f = false;
     Sub all;                        // every instance over (nx+1) x (ny+1)
     double *partials = nullptr;     // 2 per block of `all`
@@ -602,6 +603,8 @@ std::vector<BOuter<To>> outer_table(const stokes_batch *b, const void *vx, const
         o.en = (const To *)at(b->eta_n, d.off, es);
         o.ivx = (const To *)at(b->ivx, d.off, es);
         o.ivy = (const To *)at(b->ivy, d.off, es);
+        o.ax = (const To *)at(b->cax, d.off, es);
+        o.ay = (const To *)at(b->cay, d.off, es);
         o.fx = (const To *)at(b->fx, d.off, es);
         o.fy = (const To *)at(b->fy, d.off, es);
         o.bx = (const To *)at(b->bx, d.off, es);
@@ -1106,7 +1109,8 @@ int stokes_batch_create(int count, const int *nx, const int *ny, const double *l
     for (int i = 0; i < count; ++i) b->d[i] = dims_of(nx[i], ny[i], lx[i] / nx[i], ly[i] / ny[i]);
     b->total = place(b->d);
     int st = STOKES_OK;
-    void **fields[] = {&b->eta_c, &b->eta_n, &b->fx, &b->fy, &b->bx, &b->by, &b->sx, &b->sy, &b->ivx, &b->ivy};
+    void **fields[] = {&b->eta_c, &b->eta_n, &b->fx, &b->fy, &b->bx, &b->by, &b->sx, &b->sy, &b->ivx, &b->ivy,
+                       &b->cax, &b->cay};
     for (void **f : fields)
         if ((st = alloc_slab(b, f)) != STOKES_OK) break;
     if (st == STOKES_OK) {
@@ -1172,6 +1176,10 @@ int stokes_batch_set_viscosity(stokes_batch *b, const void *eta_c, const void *e
                 e = launch_inv_diag<double>(g, (const double *)at(b->eta_c, d.off, es),
                                             (const double *)at(b->eta_n, d.off, es), (double *)at(b->ivx, d.off, es),
                                             (double *)at(b->ivy, d.off, es), b->stream);
+            if (e == cudaSuccess)
+                e = kry_coef<double>(KrylovView{d.nx, d.ny, d.pitch, nullptr, nullptr}, g,
+                                     (const double *)at(b->eta_c, d.off, es), (double *)at(b->cax, d.off, es),
+                                     (double *)at(b->cay, d.off, es), b->stream);
             st = e == cudaSuccess ? STOKES_OK : cuda_fail(e, "stokes_batch_set_viscosity");
         } else {
             const GridDesc<float> g = make_grid<float>(d.nx, d.ny, d.pitch, d.hx, d.hy);
@@ -1183,10 +1191,14 @@ int stokes_batch_set_viscosity(stokes_batch *b, const void *eta_c, const void *e
                 e = launch_inv_diag<float>(g, (const float *)at(b->eta_c, d.off, es),
                                            (const float *)at(b->eta_n, d.off, es), (float *)at(b->ivx, d.off, es),
                                            (float *)at(b->ivy, d.off, es), b->stream);
+            if (e == cudaSuccess)
+                e = kry_coef<float>(KrylovView{d.nx, d.ny, d.pitch, nullptr, nullptr}, g,
+                                    (const float *)at(b->eta_c, d.off, es), (float *)at(b->cax, d.off, es),
+                                    (float *)at(b->cay, d.off, es), b->stream);
             st = e == cudaSuccess ? STOKES_OK : cuda_fail(e, "stokes_batch_set_viscosity");
         }
         if (st != STOKES_OK) return st;
-        b->kernels += 2;
+        b->kernels += 3;
     }
     b->have_eta = true;
     if (b->mg) b->mg->stale = true;
@@ -1298,7 +1310,7 @@ int stokes_batch_destroy(stokes_batch *b)
     b->pc_own.release();
     for (void *w : b->kw)
         if (w) cudaFree(w);
-    void *fs[] = {b->eta_c, b->eta_n, b->fx, b->fy, b->bx, b->by, b->sx, b->sy, b->ivx, b->ivy,
+    void *fs[] = {b->eta_c, b->eta_n, b->fx, b->fy, b->bx, b->by, b->sx, b->sy, b->ivx, b->ivy, b->cax, b->cay,
                   b->partials, b->dsum, b->dpq, b->dzq, b->alpha, b->beta, b->dactive, b->dstatus};
     for (void *f : fs)
         if (f) cudaFree(f);

@@ -45,6 +45,7 @@ template <typename T>
 struct BOuter {
     GridDesc<T> g;
     const T *ec, *en, *ivx, *ivy, *fx, *fy, *bx, *by;
+    const T *ax, *ay; // flux coefficients 2 eta_c / hx^2, 2 eta_c / hy^2
     T *vx, *vy, *rx, *ry, *zx, *zy, *px, *py, *qx, *qy;
 };
 

@@ -336,7 +336,7 @@ __global__ void kb_apply_dot(const BOuter<T> *__restrict__ tab, const BSeg *__re
     const BOuter<T> &o = tab[sg.inst];
     double s0 = 0.0, s1 = 0.0;
     static_assert(BATCH_BX == AT_X && BATCH_BY == AT_Y, "batched blocks are apply tiles");
-    apply_dot_tile<T>(o.g, o.ec, o.en, nullptr, nullptr, o.px, o.py, o.qx, o.qy, o.rx, o.ry, (lb % sg.bxb) * BATCH_BX,
+    apply_dot_tile<T>(o.g, o.ec, o.en, o.ax, o.ay, o.px, o.py, o.qx, o.qy, o.rx, o.ry, (lb % sg.bxb) * BATCH_BX,
                       (lb / sg.bxb) * BATCH_BY, (int)(threadIdx.y * BATCH_BX + threadIdx.x), sm, s0, s1);
     block_store2(s0, s1, partials);
 }
