@@ -288,6 +288,9 @@ def run_ours(args):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    # all work on a created stream: kernels on the legacy default stream would
+    # wait for the copies the end-to-end leg runs on its own streams
+    torch.cuda.set_stream(torch.cuda.Stream())
     if world > 1:
         dist.init_process_group("nccl")
 
