@@ -427,24 +427,14 @@ def e2e_measure(args, ctx, prob, stream, world, barrier=lambda: None):
     steps = max(2, args.steps)
 
     def h2d(i):
+        # buffer set i % 2 is free once step i - 2's result has left it
         b = dev[i % 2]
         with torch.cuda.stream(cs):
             if i >= 2:
-                cs.wait_event(drained[i % 2])  # step i-2's result has left this buffer set
+                cs.wait_event(drained[i % 2])
             for name, t in host.items():
                 b[name].copy_(t, non_blocking=True)
             copied[i % 2].record(cs)
-
-    def compute(i):
-        b = dev[i % 2]
-        stream.wait_event(copied[i % 2])
-        ctx.set_viscosity_dev(b["eta_c"], b["eta_n"])
-        ctx.set_rhs_dev(b["fx"], b["fy"])
-        ctx.smooth(b["vx"], b["vy"], None, variant="ras", sweeps=args.sweeps, tile=tuple(args.tile), k=k,
-                   overlap=o, seed=i)
-        e = ctx.energy(b["vx"], b["vy"])  # synchronises the context's stream
-        computed[i % 2].record(stream)
-        return e
 
     def d2h(i):
         b, (ox, oy) = dev[i % 2], outs[i % 2]
@@ -455,12 +445,25 @@ def e2e_measure(args, ctx, prob, stream, world, barrier=lambda: None):
             drained[i % 2].record(co)
 
     def run(n):
+        # step i: its kernels are enqueued first, then step i-1's result
+        # copy-out and step i+1's inputs copy-in (both overlap step i's
+        # kernels; a copy enqueued ahead of a step's kernels held them back
+        # until it finished), then step i's energy norm, which synchronises
         h2d(0)
         for i in range(n):
+            b = dev[i % 2]
+            stream.wait_event(copied[i % 2])
+            ctx.set_viscosity_dev(b["eta_c"], b["eta_n"])
+            ctx.set_rhs_dev(b["fx"], b["fy"])
+            ctx.smooth(b["vx"], b["vy"], None, variant="ras", sweeps=args.sweeps, tile=tuple(args.tile), k=k,
+                       overlap=o, seed=i)
+            computed[i % 2].record(stream)
+            if i >= 1:
+                d2h(i - 1)
             if i + 1 < n:
                 h2d(i + 1)
-            compute(i)
-            d2h(i)
+            ctx.energy(b["vx"], b["vy"])  # synchronises the context's stream
+        d2h(n - 1)
         torch.cuda.synchronize()
 
     run(2)
@@ -473,8 +476,8 @@ def e2e_measure(args, ctx, prob, stream, world, barrier=lambda: None):
     return {"value": world * args.n * args.n * args.sweeps * steps / dt / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes, "steps": steps,
             "ms_per_step": 1000.0 * dt / steps,
-            "pipelining": "inputs of step i+1 copied on one stream and step i-1's result on another while step i "
-                          "computes"}
+            "pipelining": "step i's kernels enqueued first, then step i-1's result copied out on one stream and "
+                          "step i+1's inputs copied in on another while step i computes"}
 
 
 def solve_times(args, api):
