@@ -194,7 +194,13 @@ int stokes_apply_operator(stokes_ctx *ctx, const void *vx, const void *vy, const
 
 /* Smooth M v = f - G p in place on (vx, vy) with the smoother of `params`
  * (Sec. 5).  p may be NULL (p = 0).  Requires stokes_set_viscosity and
- * stokes_set_rhs.  Asynchronous. */
+ * stokes_set_rhs.  Asynchronous.  The passes ping-pong between (vx, vy) and
+ * context-owned scratch fields; the first call whose pass count is odd and at
+ * least 3 (RAS: ceil(sweeps / k) outer iterations; Jacobi variants: one pass
+ * per sweep) allocates a second scratch pair (two fields) so that the result
+ * ends in (vx, vy) without a copy: make that call once before capturing
+ * stokes_smooth into a CUDA graph.  Returns STOKES_ERR_OOM if that allocation
+ * fails. */
 int stokes_smooth(stokes_ctx *ctx, void *vx, void *vy, const void *p, const stokes_smooth_params *params);
 
 /* Energy residual sums of Sec. 6.4, accumulated in FP64:
