@@ -583,7 +583,12 @@ template <typename To, typename Ti>
 struct Precond {
     Sub l0;
     const BOuter<To> *outer = nullptr;
-    const BLevel<Ti> *lev[B_MAX_LEVELS] = {};
+    const BLevel<Ti> *lev[B_MAX_LEVELS] = {}; // zero-initial velocity buffers
+    // velocity buffers after the pre-smoothing (and, as the prolongation
+    // source, the next coarser level's after its post-smoothing): a smoothing
+    // with an odd number of passes leaves its result in the level's scratch pair
+    const BLevel<Ti> *mid[B_MAX_LEVELS] = {};
+    const BLevel<Ti> *fin0 = nullptr; // level 0 after its post-smoothing (z)
     Sub fine[B_MAX_LEVELS], coarse[B_MAX_LEVELS];
     Group<Ti> grp[B_MAX_LEVELS][2][2]; // [level][phase][single-tile, tiled]
     const BDense<Ti> *dense = nullptr;
@@ -630,8 +635,16 @@ int plan_precond(stokes_batch *b, const stokes_mg_params *p, Precond<To, Ti> *P)
         const std::vector<BOuter<To>> t = outer_table<To>(b, nullptr, nullptr);
         ST(upload(o, t, &P->outer, s));
     }
+    // host copies of the level tables, and where each instance's velocity
+    // lives after the pre- and the post-smoothing of each level
+    struct VBuf {
+        Ti *vx, *vy, *sx, *sy;
+    };
+    std::vector<std::vector<BLevel<Ti>>> tabs(h->Lmax);
+    std::vector<std::vector<VBuf>> after_pre(h->Lmax, std::vector<VBuf>(n)), after_post(h->Lmax, std::vector<VBuf>(n));
     for (int l = 0; l < h->Lmax; ++l) {
-        std::vector<BLevel<Ti>> t(n);
+        std::vector<BLevel<Ti>> &t = tabs[l];
+        t.resize(n);
         std::memset((void *)t.data(), 0, t.size() * sizeof(BLevel<Ti>));
         std::vector<Rect> rf, rc;
         for (int i = 0; i < n; ++i) {
@@ -667,9 +680,15 @@ int plan_precond(stokes_batch *b, const stokes_mg_params *p, Precond<To, Ti> *P)
         ST(upload(o, t, &P->lev[l], s));
         ST(make_sub(o, rf, &P->fine[l], s));
         ST(make_sub(o, rc, &P->coarse[l], s));
+        std::vector<VBuf> cur(n);
+        for (int i = 0; i < n; ++i) cur[i] = {t[i].vx, t[i].vy, t[i].sx, t[i].sy};
         // smoothing groups of this level: whole-level single tiles (Jacobi-like
         // smoothers on levels up to 64^2) and tiled instances
-        if (l == h->Lmax - 1) continue;
+        if (l == h->Lmax - 1) {
+            after_pre[l] = cur;
+            after_post[l] = cur;
+            continue;
+        }
         const stokes_smooth_params sm = level_smoother(p->smoother, l);
         for (int ph = 0; ph < 2; ++ph) {
             const int sweeps = mg_sweeps(ph == 0 ? p->nu_pre : p->nu_post, p->nu_growth, l, p->nu_max);
@@ -687,10 +706,10 @@ int plan_precond(stokes_batch *b, const stokes_mg_params *p, Precond<To, Ti> *P)
                 x.c.by = e.by;
                 x.c.inv_dx = e.ivx;
                 x.c.inv_dy = e.ivy;
-                x.vx = e.vx;
-                x.vy = e.vy;
-                x.sx = e.sx;
-                x.sy = e.sy;
+                x.vx = cur[i].vx;
+                x.vy = cur[i].vy;
+                x.sx = cur[i].sx;
+                x.sy = cur[i].sy;
                 const bool single = jacobi_like(sm) && sweeps > 0 && ras_whole_level_tile(e.g.nx, e.g.ny, es);
                 if (single) {
                     x.ti = e.g.nx;
@@ -711,7 +730,44 @@ int plan_precond(stokes_batch *b, const stokes_mg_params *p, Precond<To, Ti> *P)
             ST(plan_group<Ti>(o, g1, f1, false, true, b->use_tma, b->pair_mode, P->lev[l], &P->grp[l][ph][0], s));
             ST(plan_group<Ti>(o, g2, ras_form(sm, sweeps, seed, STOKES_SHIFT_SPLITMIX), false, false, b->use_tma,
                               b->pair_mode, P->lev[l], &P->grp[l][ph][1], s));
+            // an odd number of passes leaves the result in the scratch pair:
+            // no copy back, the two pairs trade roles from here on
+            const std::vector<GInst<Ti>> *gs[2] = {&g1, &g2};
+            for (int q = 0; q < 2; ++q) {
+                Group<Ti> &G = P->grp[l][ph][q];
+                if (!G.back) continue;
+                G.back = false;
+                for (const GInst<Ti> &x : *gs[q]) {
+                    std::swap(cur[x.inst].vx, cur[x.inst].sx);
+                    std::swap(cur[x.inst].vy, cur[x.inst].sy);
+                }
+            }
+            if (ph == 0) after_pre[l] = cur;
         }
+        after_post[l] = cur;
+    }
+    // tables of the residual, restriction and prolongation (fine velocity after
+    // the pre-smoothing, coarse velocity after its post-smoothing) and of z
+    for (int l = 0; l + 1 < h->Lmax; ++l) {
+        std::vector<BLevel<Ti>> t = tabs[l];
+        for (int i = 0; i < n; ++i) {
+            if (l >= h->L[i] - 1) continue;
+            t[i].vx = after_pre[l][i].vx;
+            t[i].vy = after_pre[l][i].vy;
+            t[i].sx = after_pre[l][i].sx;
+            t[i].sy = after_pre[l][i].sy;
+            t[i].cvx = after_post[l + 1][i].vx;
+            t[i].cvy = after_post[l + 1][i].vy;
+        }
+        ST(upload(o, t, &P->mid[l], s));
+    }
+    {
+        std::vector<BLevel<Ti>> t = tabs[0];
+        for (int i = 0; i < n; ++i) {
+            t[i].vx = after_post[0][i].vx;
+            t[i].vy = after_post[0][i].vy;
+        }
+        ST(upload(o, t, &P->fin0, s));
     }
     std::vector<BDense<Ti>> dt(n);
     for (int i = 0; i < n; ++i) {
@@ -753,19 +809,19 @@ int enqueue_precond(const Precond<To, Ti> &P, int Lmax, int count, const int *li
     for (int l = 0; l < Lmax - 1; ++l) {
         ST(run_group<Ti>(P.grp[l][0][0], live, run, s, nk));
         ST(run_group<Ti>(P.grp[l][0][1], live, run, s, nk));
-        CK(batch_residual<Ti>(P.lev[l], P.fine[l].map, P.fine[l].nseg, P.fine[l].nblocks, live, s));
-        CK(batch_restrict<Ti>(P.lev[l], P.coarse[l].map, P.coarse[l].nseg, P.coarse[l].nblocks, live, s));
+        CK(batch_residual<Ti>(P.mid[l], P.fine[l].map, P.fine[l].nseg, P.fine[l].nblocks, live, s));
+        CK(batch_restrict<Ti>(P.mid[l], P.coarse[l].map, P.coarse[l].nseg, P.coarse[l].nblocks, live, s));
         *nk += 2;
     }
     CK(batch_dense<Ti>(P.dense, count, P.rows, live, s));
     *nk += 3;
     for (int l = Lmax - 2; l >= 0; --l) {
-        CK(batch_prolong<Ti>(P.lev[l], P.fine[l].map, P.fine[l].nseg, P.fine[l].nblocks, live, s));
+        CK(batch_prolong<Ti>(P.mid[l], P.fine[l].map, P.fine[l].nseg, P.fine[l].nblocks, live, s));
         ++*nk;
         ST(run_group<Ti>(P.grp[l][1][0], live, run, s, nk));
         ST(run_group<Ti>(P.grp[l][1][1], live, run, s, nk));
     }
-    CK((batch_cast_out<To, Ti>(P.outer, P.lev[0], P.l0.map, P.l0.nseg, P.l0.nblocks, live, s)));
+    CK((batch_cast_out<To, Ti>(P.outer, P.fin0, P.l0.map, P.l0.nseg, P.l0.nblocks, live, s)));
     ++*nk;
     return STOKES_OK;
 }
