@@ -366,6 +366,12 @@ struct stokes_batch {
     cudaGraphExec_t gexec = nullptr;
     unsigned char gkey[sizeof(stokes_mg_params)] = {};
     long long gkernels = 0;
+    // flexible CG: the graph has no casts; the finest level's right-hand side
+    // (table g_l0) is written by the CG update and z read from table g_fin,
+    // both in the inner precision g_inner
+    bool g_direct = false;
+    int g_inner = -1;
+    const void *g_l0 = nullptr, *g_fin = nullptr;
     long long kernels = 0;          // kernels launched so far
 };
 
@@ -798,10 +804,12 @@ int plan_precond(stokes_batch *b, const stokes_mg_params *p, Precond<To, Ti> *P)
 // longer uses.
 template <typename To, typename Ti>
 int enqueue_precond(const Precond<To, Ti> &P, int Lmax, int count, const int *live, const RasRun &run,
-                    cudaStream_t s, long long *nk)
+                    cudaStream_t s, long long *nk, bool casts)
 {
-    CK((batch_cast_in<To, Ti>(P.outer, P.lev[0], P.l0.map, P.l0.nseg, P.l0.nblocks, live, s)));
-    ++*nk;
+    if (casts) {
+        CK((batch_cast_in<To, Ti>(P.outer, P.lev[0], P.l0.map, P.l0.nseg, P.l0.nblocks, live, s)));
+        ++*nk;
+    }
     for (int l = 0; l < Lmax - 1; ++l) {
         CK(batch_zero_v<Ti>(P.lev[l], P.fine[l].map, P.fine[l].nseg, P.fine[l].nblocks, live, s));
         ++*nk;
@@ -821,8 +829,10 @@ int enqueue_precond(const Precond<To, Ti> &P, int Lmax, int count, const int *li
         ST(run_group<Ti>(P.grp[l][1][0], live, run, s, nk));
         ST(run_group<Ti>(P.grp[l][1][1], live, run, s, nk));
     }
-    CK((batch_cast_out<To, Ti>(P.outer, P.fin0, P.l0.map, P.l0.nseg, P.l0.nblocks, live, s)));
-    ++*nk;
+    if (casts) {
+        CK((batch_cast_out<To, Ti>(P.outer, P.fin0, P.l0.map, P.l0.nseg, P.l0.nblocks, live, s)));
+        ++*nk;
+    }
     return STOKES_OK;
 }
 
@@ -834,7 +844,9 @@ int capture(stokes_batch *b, const stokes_mg_params *p)
     long long nk = 0;
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(b->gstream, cudaStreamCaptureModeThreadLocal));
-    const int st = enqueue_precond<To, Ti>(P, b->mg->Lmax, b->count, b->dactive, run_of(b), b->gstream, &nk);
+    const bool direct = p->krylov != 0;
+    const int st = enqueue_precond<To, Ti>(P, b->mg->Lmax, b->count, b->dactive, run_of(b), b->gstream, &nk,
+                                           !direct);
     const cudaError_t e = cudaStreamEndCapture(b->gstream, &graph);
     if (st != STOKES_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -848,6 +860,10 @@ int capture(stokes_batch *b, const stokes_mg_params *p)
         return cuda_fail(ei, "cudaGraphInstantiate");
     }
     b->gkernels = nk;
+    b->g_direct = direct;
+    b->g_inner = p->inner_dtype == STOKES_F64 ? STOKES_F64 : STOKES_F32;
+    b->g_l0 = P.lev[0];
+    b->g_fin = P.fin0;
     return STOKES_OK;
 }
 
@@ -986,7 +1002,33 @@ int solve_impl(stokes_batch *b, void *vx, void *vy, const void *p, const stokes_
         }
     };
     if (live > 0) CK(cudaMemcpyAsync(b->dactive, b->hactive, n * sizeof(int), cudaMemcpyHostToDevice, s));
-    if (prm->krylov && live > 0) {
+    auto fcg_direct = [&](auto tag) -> int {
+        using Ti = decltype(tag);
+        const BLevel<Ti> *l0 = (const BLevel<Ti> *)b->g_l0, *fin = (const BLevel<Ti> *)b->g_fin;
+        CK((batch_cast_in<T, Ti>(ot, l0, A.map, A.nseg, A.nblocks, nullptr, s)));
+        ST(replay(b));
+        CK((batch_direction_in<T, Ti>(ot, fin, A.map, A.nseg, A.nblocks, nullptr, s)));
+        b->kernels += 2;
+        for (;;) {
+            CK(batch_apply_dot<T>(ot, A.map, A.nseg, A.nblocks, b->partials, b->dpq, s));
+            CK(batch_scalars(n, b->dpq, nullptr, b->dactive, b->alpha, nullptr, s));
+            CK((batch_update_cast<T, Ti>(ot, l0, A.map, A.nseg, A.nblocks, b->alpha, b->partials, b->dsum, s)));
+            b->kernels += 5;
+            ST(read_sums(b, b->dsum));
+            advance();
+            if (live == 0) break;
+            CK(cudaMemcpyAsync(b->dactive, b->hactive, n * sizeof(int), cudaMemcpyHostToDevice, s));
+            ST(replay(b));
+            CK((batch_dot_zq_in<T, Ti>(ot, fin, A.map, A.nseg, A.nblocks, b->partials, b->dzq, s)));
+            CK(batch_scalars(n, b->dpq, b->dzq, b->dactive, nullptr, b->beta, s));
+            CK((batch_direction_in<T, Ti>(ot, fin, A.map, A.nseg, A.nblocks, b->beta, s)));
+            b->kernels += 4;
+        }
+        return STOKES_OK;
+    };
+    if (prm->krylov && live > 0 && b->g_direct) {
+        ST(b->g_inner == STOKES_F64 ? fcg_direct(double{}) : fcg_direct(float{}));
+    } else if (prm->krylov && live > 0) {
         ST(replay(b));
         CK(batch_direction<T>(ot, A.map, A.nseg, A.nblocks, nullptr, s));
         ++b->kernels;

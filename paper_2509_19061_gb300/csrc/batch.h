@@ -111,6 +111,19 @@ cudaError_t batch_dot_zq(const BOuter<T> *tab, const BSeg *map, int nseg, int nb
 template <typename T> // p = z + beta[inst] p  (beta NULL: p = z)
 cudaError_t batch_direction(const BOuter<T> *tab, const BSeg *map, int nseg, int nblocks, const double *beta,
                             cudaStream_t s);
+// Flexible CG with z and the V-cycle's right-hand side in the inner precision
+// (no casts around the V-cycle): the update also writes (Ti) r_new into the
+// finest level's b (table l0); <z, q> and p = z + beta p read z from the
+// finest level's velocity buffers where the V-cycle leaves it (table fin).
+template <typename To, typename Ti>
+cudaError_t batch_update_cast(const BOuter<To> *tab, const BLevel<Ti> *l0, const BSeg *map, int nseg, int nblocks,
+                              const double *alpha, double *partials, double *out, cudaStream_t s);
+template <typename To, typename Ti>
+cudaError_t batch_dot_zq_in(const BOuter<To> *tab, const BLevel<Ti> *fin, const BSeg *map, int nseg, int nblocks,
+                            double *partials, double *out, cudaStream_t s);
+template <typename To, typename Ti>
+cudaError_t batch_direction_in(const BOuter<To> *tab, const BLevel<Ti> *fin, const BSeg *map, int nseg, int nblocks,
+                               const double *beta, cudaStream_t s);
 template <typename T> // v += z on instances whose active flag is set
 cudaError_t batch_add(const BOuter<T> *tab, const BSeg *map, int nseg, int nblocks, const int *active, cudaStream_t s);
 // alpha[i] = active[i] ? s[2i+1] / s[2i] : 0      (FCG step length)

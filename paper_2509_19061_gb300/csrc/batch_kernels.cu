@@ -399,6 +399,78 @@ __global__ void kb_direction(const BOuter<T> *__restrict__ tab, const BSeg *__re
     if (vy_unknown(g, p.j, p.i)) o.py[q] = beta ? r_fma(b, o.py[q], o.zy[q]) : o.zy[q];
 }
 
+// Flexible CG without casts around the V-cycle: the update also writes r in
+// the inner precision into the finest level's right-hand side (l0), and
+// <z, q> and p = z + beta p read z in the inner precision where the V-cycle
+// leaves it (fin); (To) of an inner value is exact, so the iterates are those
+// of the casting form.
+template <typename To, typename Ti>
+__global__ void kb_update_cast(const BOuter<To> *__restrict__ tab, const BLevel<Ti> *__restrict__ l0,
+                               const BSeg *__restrict__ m, int n, const double *__restrict__ alpha,
+                               double *__restrict__ partials)
+{
+    const Pt p = point_of(m, n);
+    double s0 = 0.0;
+    if (p.valid) {
+        const BOuter<To> &o = tab[p.inst];
+        const GridDesc<To> &g = o.g;
+        const To a = (To)alpha[p.inst];
+        const int i = p.i, j = p.j;
+        const size_t q = (size_t)j * g.pitch + i;
+        if (vx_unknown(g, j, i)) {
+            o.vx[q] = r_fma(a, o.px[q], o.vx[q]);
+            const To rn = r_fma(-a, o.qx[q], o.rx[q]);
+            o.rx[q] = rn;
+            l0[p.inst].bx[q] = (Ti)rn;
+            s0 = acc_sq(s0, rn, -o.ivx[q]);
+        }
+        if (vy_unknown(g, j, i)) {
+            o.vy[q] = r_fma(a, o.py[q], o.vy[q]);
+            const To rn = r_fma(-a, o.qy[q], o.ry[q]);
+            o.ry[q] = rn;
+            l0[p.inst].by[q] = (Ti)rn;
+            s0 = acc_sq(s0, rn, -o.ivy[q]);
+        }
+    }
+    block_store2(s0, 0.0, partials);
+}
+
+template <typename To, typename Ti>
+__global__ void kb_dot_zq_in(const BOuter<To> *__restrict__ tab, const BLevel<Ti> *__restrict__ fin,
+                             const BSeg *__restrict__ m, int n, double *__restrict__ partials)
+{
+    const Pt p = point_of(m, n);
+    double s0 = 0.0;
+    if (p.valid) {
+        const BOuter<To> &o = tab[p.inst];
+        const GridDesc<To> &g = o.g;
+        const size_t q = (size_t)p.j * g.pitch + p.i;
+        if (vx_unknown(g, p.j, p.i)) s0 = fma((double)fin[p.inst].vx[q], (double)o.qx[q], s0);
+        if (vy_unknown(g, p.j, p.i)) s0 = fma((double)fin[p.inst].vy[q], (double)o.qy[q], s0);
+    }
+    block_store2(s0, 0.0, partials);
+}
+
+template <typename To, typename Ti>
+__global__ void kb_direction_in(const BOuter<To> *__restrict__ tab, const BLevel<Ti> *__restrict__ fin,
+                                const BSeg *__restrict__ m, int n, const double *__restrict__ beta)
+{
+    const Pt p = point_of(m, n);
+    if (!p.valid) return;
+    const BOuter<To> &o = tab[p.inst];
+    const GridDesc<To> &g = o.g;
+    const size_t q = (size_t)p.j * g.pitch + p.i;
+    const To b = beta ? (To)beta[p.inst] : To(0);
+    if (vx_unknown(g, p.j, p.i)) {
+        const To z = (To)fin[p.inst].vx[q];
+        o.px[q] = beta ? r_fma(b, o.px[q], z) : z;
+    }
+    if (vy_unknown(g, p.j, p.i)) {
+        const To z = (To)fin[p.inst].vy[q];
+        o.py[q] = beta ? r_fma(b, o.py[q], z) : z;
+    }
+}
+
 template <typename T>
 __global__ void kb_add(const BOuter<T> *__restrict__ tab, const BSeg *__restrict__ m, int n,
                        const int *__restrict__ active)
@@ -532,6 +604,42 @@ cudaError_t batch_direction(const BOuter<T> *tab, const BSeg *map, int nseg, int
     if (nblocks > 0) kb_direction<T><<<nblocks, BLOCK, 0, s>>>(tab, map, nseg, beta);
     return cudaGetLastError();
 }
+template <typename To, typename Ti>
+cudaError_t batch_update_cast(const BOuter<To> *tab, const BLevel<Ti> *l0, const BSeg *map, int nseg, int nblocks,
+                              const double *alpha, double *partials, double *out, cudaStream_t s)
+{
+    kb_update_cast<To, Ti><<<nblk(nblocks), BLOCK, 0, s>>>(tab, l0, map, nseg, alpha, partials);
+    k_seg_final<<<(nseg + 7) / 8, 256, 0, s>>>(map, nseg, partials, out);
+    return cudaGetLastError();
+}
+template <typename To, typename Ti>
+cudaError_t batch_dot_zq_in(const BOuter<To> *tab, const BLevel<Ti> *fin, const BSeg *map, int nseg, int nblocks,
+                            double *partials, double *out, cudaStream_t s)
+{
+    kb_dot_zq_in<To, Ti><<<nblk(nblocks), BLOCK, 0, s>>>(tab, fin, map, nseg, partials);
+    k_seg_final<<<(nseg + 7) / 8, 256, 0, s>>>(map, nseg, partials, out);
+    return cudaGetLastError();
+}
+template <typename To, typename Ti>
+cudaError_t batch_direction_in(const BOuter<To> *tab, const BLevel<Ti> *fin, const BSeg *map, int nseg, int nblocks,
+                               const double *beta, cudaStream_t s)
+{
+    if (nblocks > 0) kb_direction_in<To, Ti><<<nblocks, BLOCK, 0, s>>>(tab, fin, map, nseg, beta);
+    return cudaGetLastError();
+}
+#define INST_IN(To, Ti)                                                                                            \
+    template cudaError_t batch_update_cast<To, Ti>(const BOuter<To> *, const BLevel<Ti> *, const BSeg *, int, int, \
+                                                   const double *, double *, double *, cudaStream_t);              \
+    template cudaError_t batch_dot_zq_in<To, Ti>(const BOuter<To> *, const BLevel<Ti> *, const BSeg *, int, int,   \
+                                                 double *, double *, cudaStream_t);                                \
+    template cudaError_t batch_direction_in<To, Ti>(const BOuter<To> *, const BLevel<Ti> *, const BSeg *, int,     \
+                                                    int, const double *, cudaStream_t);
+INST_IN(double, float)
+INST_IN(double, double)
+INST_IN(float, float)
+INST_IN(float, double)
+#undef INST_IN
+
 template <typename T>
 cudaError_t batch_add(const BOuter<T> *tab, const BSeg *map, int nseg, int nblocks, const int *active, cudaStream_t s)
 {
