@@ -172,6 +172,34 @@ def test_sinker_64_ras_every_sweep_f64(api):
 
 
 # ---------------------------------------------------------------------------
+# the 1024^2 sinker at contrast 1e4 in FP64, 100 sweeps per smoother: the
+# benchmark's smoother table (every smoother, RAS tiles of 16^2 to 64 x 32)
+# against the oracle on the whole field
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kw", [
+    dict(variant="jacobi"), dict(variant="fused"), dict(variant="rbgs"),
+    dict(variant="blocked", tile=(32, 32)),
+    dict(variant="ras", tile=(32, 32), k=2, overlap=1),
+    dict(variant="ras", tile=(16, 16), k=4, overlap=3),
+    dict(variant="ras", tile=(64, 32), k=4, overlap=3),
+])
+def test_sinker_1024_contrast1e4_100_sweeps_f64(api, kw):
+    n, sweeps = 1024, 100
+    prob = inputs.sinker_problem(n, eta_in=1e4)
+    g = ogrid(prob)
+    bx, by = ora.rhs(g, prob.fx, prob.fy, None)
+    r = Run(api, prob, "f64")
+    r.smooth(sweeps=sweeps, seed=1, **kw)
+    if kw["variant"] == "ras":
+        ref = ora.ras(g, bx, by, 0.3, sweeps, kw["tile"][0], kw["tile"][1], kw["k"], kw["overlap"], shift_mode=1,
+                      seed=1)
+    else:
+        fn = ora.rbgs if kw["variant"] == "rbgs" else ora.jacobi
+        ref = fn(g, bx, by, 0.3, sweeps, g.zeros_vx(), g.zeros_vy())
+    assert rel(r.v(), ref) <= F64_TOL
+
+
+# ---------------------------------------------------------------------------
 # ragged grids, several tiles, hx != hy, non-zero pressure
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("variant", ["jacobi", "fused", "blocked", "rbgs"])
