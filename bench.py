@@ -91,15 +91,25 @@ def source_hash(paths):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(key, src_hash):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
+def ncu_entry(key, src_hash):
+    """The committed ncu summary entry of this launch shape, if it was taken
     on the current kernel source; None otherwise."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         e = d[key]
-        return float(e["dram_bytes_per_launch"]) if e.get("source_hash") == src_hash else None
+        return e if e.get("source_hash") == src_hash else None
+    except Exception:
+        return None
+
+
+def ncu_traffic(key, src_hash):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; None otherwise."""
+    e = ncu_entry(key, src_hash)
+    try:
+        return None if e is None else float(e["dram_bytes_per_launch"])
     except Exception:
         return None
 
@@ -346,6 +356,7 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     key = "ras_%s_%d_t%dx%d_k%d_o%d" % (dt_name, n, args.tile[0], args.tile[1], k, o)
     traffic = ncu_traffic(key, source_hash(RAS_SOURCES))
+    limiter = (ncu_entry(key, source_hash(RAS_SOURCES)) or {}).get("limiter")
     tflops = FLOPS_PER_CELL_SWEEP * cells * sweeps_per_launch / (avg_ms / 1e3) / 1e12
     alu_peak = NOMINAL_FP32_TFLOPS if dt_name == "f32" else NOMINAL_FP64_TFLOPS
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -363,6 +374,7 @@ def run_ours(args):
                         "note": "algorithmic flops of the owned cells; the window overlap and the kernel's "
                                 "other instructions are not counted"},
                 "sweeps_per_launch": sweeps_per_launch,
+                "limiter": limiter,
                 "note": "effective bytes: 8 words/cell/sweep x sweeps per launch; with k > 1 the tile is "
                         "read from HBM once per k sweeps, so frac may exceed 1 (temporal blocking)"}
 
