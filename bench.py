@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--c2-sweeps", type=int, default=100, help="sweeps per smoother in the 1024^2 FP64 table")
     ap.add_argument("--uzawa-n", type=int, default=1024, help="grid of the Uzawa Stokes solve")
     ap.add_argument("--robust-n", type=int, default=256, help="grid of the smoother robustness comparison")
-    ap.add_argument("--only", choices=["solve", "batch", "autotune", "c2", "uzawa", "robustness"],
+    ap.add_argument("--only", choices=["solve", "batch", "autotune", "c2", "uzawa", "robustness", "fp32err"],
                     help="run one extra leg alone and print its JSON (for profiling it)")
     return ap.parse_args()
 
@@ -395,6 +395,7 @@ def run_ours(args):
     # baseline) run at N = 1 only: at N > 1 they would hold every GPU while
     # rank 0 alone works
     if not args.no_extras and world == 1:
+        line["fp32_vs_fp64"] = fp32_error_leg(args, api, prob)
         line["variants"] = variant_table(args, api, prob)
         line["c2_f64_1024"] = c2_table(args, api)
         line["time_to_1e-8"] = solve_times(args, api)
@@ -775,6 +776,53 @@ def _time_smooth(ctx, vx, vy, kw, reps=2):
     return e0.elapsed_time(e1) / reps
 
 
+def energy_weights(prob):
+    """-diag(M) at the velocity unknowns (zero elsewhere) in the natural
+    layouts, from the viscosities of an inputs.Problem (eta_n zero on the
+    boundary nodes: free slip)."""
+    import numpy as np
+    ec = np.asarray(prob.eta_c, dtype=np.float64)
+    en = np.array(prob.eta_n, dtype=np.float64)
+    en[0, :] = en[-1, :] = en[:, 0] = en[:, -1] = 0.0
+    ihx2, ihy2 = 1.0 / prob.hx ** 2, 1.0 / prob.hy ** 2
+    ny, nx = ec.shape
+    wx = np.zeros((ny, nx + 1))
+    wx[:, 1:nx] = 2.0 * (ec[:, 1:] + ec[:, :-1]) * ihx2 + (en[1:, 1:nx] + en[:-1, 1:nx]) * ihy2
+    wy = np.zeros((ny + 1, nx))
+    wy[1:ny, :] = 2.0 * (ec[1:, :] + ec[:-1, :]) * ihy2 + (en[1:ny, 1:] + en[1:ny, :-1]) * ihx2
+    return wx, wy
+
+
+def fp32_error_leg(args, api, prob):
+    """The FP32 result of the benchmark's smoothing (100 sweeps from zero,
+    the benchmark's schedule) against the FP64 GPU result of the same map
+    (RAS with overlap k - 1 is exact Jacobi whatever the tiles; the FP64 path
+    matches the FP64 oracle to 1e-12 in the tests), in the diag(-M)-weighted
+    energy norm, relative."""
+    import numpy as np
+    n = args.n
+    k = args.k
+    o = args.overlap if args.overlap is not None else k - 1
+    if o < k - 1:
+        return {"skipped": "the schedule is not exact Jacobi"}
+    res = {}
+    for dt_name, kw in (("f32", dict(tile=tuple(args.tile), k=k, overlap=o)),
+                        ("f64", dict(tile=(32, 32), k=4, overlap=3))):
+        c = api.StokesContext(n, n, 1.0, 1.0, dt_name)
+        c.set_problem(prob)
+        vx, vy = c.field(), c.field()
+        c.smooth(vx, vy, None, variant="ras", sweeps=args.sweeps, seed=7, **kw)
+        res[dt_name] = (c.unpack(vx, "vx"), c.unpack(vy, "vy"))
+        c.close()
+    wx, wy = energy_weights(prob)
+    (ax, ay), (bx, by) = res["f32"], res["f64"]
+    num = np.sum(wx * (ax - bx) ** 2) + np.sum(wy * (ay - by) ** 2)
+    den = np.sum(wx * bx ** 2) + np.sum(wy * by ** 2)
+    return {"energy_norm_rel_error": float(np.sqrt(num / den)), "sweeps": args.sweeps,
+            "fp32": "ras %dx%d k%d o%d" % (args.tile[0], args.tile[1], k, o),
+            "fp64": "ras 32x32 k4 o3 (the same map: exact Jacobi)"}
+
+
 def variant_table(args, api, prob):
     """The 8192^2 layered sinker (the throughput workload): FP32 and FP64
     RAS-Jacobi with k in {1, 2, 4, 8} (overlap k-1, exact Jacobi, and
@@ -865,6 +913,10 @@ def run_only(args):
     import torch
     from paper_2509_19061_gb300 import api
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if args.only == "fp32err":
+        from paper_2509_19061_gb300 import inputs
+        print(json.dumps({"leg": args.only, "result": fp32_error_leg(args, api, inputs.layered_sinker(args.n, seed=4))}))
+        return 0
     leg = {"solve": solve_times, "batch": batch_leg, "autotune": autotune_leg, "c2": c2_table,
            "uzawa": uzawa_leg, "robustness": robustness_leg}[args.only]
     print(json.dumps({"leg": args.only, "result": leg(args, api)}))
