@@ -417,6 +417,78 @@ def test_energy_norm_pressure_weight(ora):
     assert rp == pytest.approx(want, rel=1e-13)
 
 
+def hand_minus_diag(g, nx, ny):
+    """-diag(M) written out from the stress fluxes of Eq. (3): a vx unknown
+    enters sigma'xx of its two neighbouring cells with 2 eta_c / hx^2 each and
+    sigma'xy of its two neighbouring nodes with eta_n / hy^2 each; boundary
+    nodes carry no shear stress (free slip)."""
+    en = np.array(g.eta_n, dtype=np.float64)
+    en[0, :] = en[ny, :] = 0.0
+    en[:, 0] = en[:, nx] = 0.0
+    wx = np.zeros((ny, nx + 1))
+    wy = np.zeros((ny + 1, nx))
+    for j in range(ny):
+        for i in range(1, nx):
+            wx[j, i] = 2 * (g.eta_c[j, i] + g.eta_c[j, i - 1]) / g.hx**2 + (en[j + 1, i] + en[j, i]) / g.hy**2
+    for j in range(1, ny):
+        for i in range(nx):
+            wy[j, i] = 2 * (g.eta_c[j, i] + g.eta_c[j - 1, i]) / g.hy**2 + (en[j, i + 1] + en[j, i]) / g.hx**2
+    return wx, wy
+
+
+@pytest.mark.parametrize("at_wall", [False, True])
+def test_energy_norm_velocity_weight(ora, at_wall):
+    """The velocity part of the energy norm weights r_v^2 by 1 / (-diag M)
+    (Sec. 6.4).  With v = 0, p = 0 and f a unit vector at one vx unknown, the
+    sum is 1 / (-M_ii); likewise at one vy unknown.  The weight is written out
+    by hand from the viscosities (boundary nodes without shear) and also read
+    off as -(M e_i)_i by a unit-vector apply of the operator, so a weight of
+    -d^2, 1/d or +d, or a swapped hx / hy, fails.  at_wall puts the unknowns
+    next to a wall, where one shear node is a boundary node."""
+    nx, ny, lx, ly = 9, 7, 1.0, 0.6
+    g = rand_grid(ora, nx, ny, 41, lx, ly)
+    wx, wy = hand_minus_diag(g, nx, ny)
+    (jx, ix), (jy, iy) = ((0, 4), (3, 0)) if at_wall else ((3, 5), (4, 2))
+    fx, fy = g.zeros_vx(), g.zeros_vy()
+    fx[jx, ix] = 1.0
+    rv, rp, ff = ora.energy(g, fx, g.zeros_vy(), None, g.zeros_vx(), g.zeros_vy())
+    assert rp == 0.0
+    assert rv == pytest.approx(1.0 / wx[jx, ix], rel=1e-13) and ff == pytest.approx(1.0 / wx[jx, ix], rel=1e-13)
+    ex = g.zeros_vx()
+    ex[jx, ix] = 1.0
+    mx, _ = ora.apply_M(g, ex, g.zeros_vy())
+    assert rv == pytest.approx(-1.0 / mx[jx, ix], rel=1e-13)
+    fy[jy, iy] = 1.0
+    rv, rp, ff = ora.energy(g, g.zeros_vx(), fy, None, g.zeros_vx(), g.zeros_vy())
+    assert rv == pytest.approx(1.0 / wy[jy, iy], rel=1e-13) and ff == pytest.approx(1.0 / wy[jy, iy], rel=1e-13)
+    ey = g.zeros_vy()
+    ey[jy, iy] = 1.0
+    _, my = ora.apply_M(g, g.zeros_vx(), ey)
+    assert rv == pytest.approx(-1.0 / my[jy, iy], rel=1e-13)
+
+
+def test_energy_norm_velocity_weight_on_a_residual(ora):
+    """A non-zero state: with f = 0 and v a unit vector e at one vx unknown,
+    r_v = -M e is non-zero at the unknown and its stencil neighbours (vx and
+    vy), so the velocity sum is sum_u (M e)_u^2 / (-M_uu) with the hand-written
+    weights, summed over unknowns of both components with different weights."""
+    nx, ny, lx, ly = 8, 6, 1.2, 0.5
+    g = rand_grid(ora, nx, ny, 43, lx, ly)
+    wx, wy = hand_minus_diag(g, nx, ny)
+    mxm, mym = unknown_masks(nx, ny)
+    ex = g.zeros_vx()
+    ex[2, 3] = 1.0
+    mx, my = ora.apply_M(g, ex, g.zeros_vy())
+    assert np.count_nonzero(mx[mxm]) >= 3 and np.count_nonzero(my[mym]) >= 4
+    want = np.sum(mx[mxm] ** 2 / wx[mxm]) + np.sum(my[mym] ** 2 / wy[mym])
+    rv, rp, ff = ora.energy(g, g.zeros_vx(), g.zeros_vy(), None, ex, g.zeros_vy())
+    assert ff == 0.0
+    assert rv == pytest.approx(want, rel=1e-13)
+    # the pressure part of the same state: D e is +-1/hx in the two cells beside the face
+    lap = 2 / g.hx**2 + 2 / g.hy**2
+    assert rp == pytest.approx((g.eta_c[2, 2] + g.eta_c[2, 3]) / g.hx**2 / lap, rel=1e-13)
+
+
 # --------------------------------------------------------------------------
 # multigrid (Sec. 3.2, Sec. 6.2)
 # --------------------------------------------------------------------------
