@@ -376,11 +376,16 @@ int stokes_tile_kernel_plan(int nx, int ny, int ti, int tj, int overlap, int dty
  * calls whose work overlaps on the GPU (on different streams, or from
  * different host threads) race and return wrong sums.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.
+ * device current; make that first call before any stream capture.  The
+ * address is looked up again if the device's context was replaced since (after
+ * cudaDeviceReset), so that call, too, must come before any stream capture.
  *
  * Limits: 2 <= nx, ny <= 46340, pitch >= nx + 1 and (ny + 1) * pitch < 2^31;
  * anything else returns STOKES_ERR_ARG, as do NULL inputs or a bad dtype.
- * CUDA failures return STOKES_ERR_CUDA. */
+ * The reduction writes one triple of partial sums per block: if the library's
+ * energy reduction ran more than the array's 608 blocks, the call would
+ * return STOKES_ERR_ARG (this build runs exactly 608).  CUDA failures return
+ * STOKES_ERR_CUDA. */
 int stokes_energy_norm_noalloc(int nx, int ny, double lx, double ly, int dtype, int pitch, const void *eta_c,
                                const void *eta_n, const void *fx, const void *fy, const void *p, const void *vx,
                                const void *vy, double *out_dev, void *cuda_stream);

@@ -11,6 +11,8 @@
 // (one partial sum per block) lives in the file-scope device array below.
 #include <mutex>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/stokes.h"
 #include "internal.h"
 
@@ -29,9 +31,36 @@ constexpr int NOALLOC_MAX_SIDE = 46340;
 constexpr int MAX_DEVICES = 128;
 std::mutex g_mu;
 double *g_addr[MAX_DEVICES] = {};
+unsigned long long g_ctx_id[MAX_DEVICES] = {};
 
-// Device address of the scratch array on the current device, looked up
-// once per device (with that device current).
+// Unique id of the calling thread's current CUDA context (0 if none is
+// current yet), through the driver entry points the runtime hands out.
+unsigned long long current_context_id()
+{
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+            cudaGetLastError();
+            return 0;
+        }
+        get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f1);
+        get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f2);
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the scratch array on the current device, looked up once
+// per device (with that device current) and again only if the device's
+// context was replaced since (cudaDeviceReset ends the context the address
+// belonged to; the module, and with it the array, is then loaded anew).
 int scratch_on_current_device(double **out)
 {
     int dev = 0;
@@ -39,11 +68,13 @@ int scratch_on_current_device(double **out)
     if (e != cudaSuccess) return STOKES_ERR_CUDA;
     if (dev < 0 || dev >= MAX_DEVICES) return STOKES_ERR_ARG;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    const unsigned long long id = current_context_id();
+    if (!g_addr[dev] || id == 0 || id != g_ctx_id[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_partials);
         if (e != cudaSuccess || !p) return STOKES_ERR_CUDA;
         g_addr[dev] = static_cast<double *>(p);
+        g_ctx_id[dev] = current_context_id(); // the lookup makes the primary context current
     }
     *out = g_addr[dev];
     return STOKES_OK;

@@ -53,6 +53,33 @@ def test_noalloc_matches_context_energy_norm_twice(api, dtype):
     ctx.close()
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_noalloc_without_pressure_matches_context(api, dtype):
+    """p = NULL means p = 0: the sums equal the context's without a pressure."""
+    import torch
+    nx, ny, lx, ly = 97, 64, 1.0, 0.8
+    prob = inputs.sinker_problem(nx, ny, lx=lx, ly=ly, eta_in=1e4)
+    ctx = api.StokesContext(nx, ny, lx, ly, dtype)
+    ec, en = ctx.pack(prob.eta_c, "eta_c"), ctx.pack(prob.eta_n, "eta_n")
+    fx, fy = ctx.pack(prob.fx, "fx"), ctx.pack(prob.fy, "fy")
+    ctx.set_viscosity_dev(ec, en)
+    ctx.set_rhs_dev(fx, fy)
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    for seed in (8, 9):
+        v = inputs.random_velocity(nx, ny, seed, 0.01)
+        vx, vy = ctx.pack(v[0], "vx"), ctx.pack(v[1], "vy")
+        want = ctx.energy(vx, vy, None)
+        assert want[1] > 0.0
+        api.stokes_energy_norm_noalloc(nx, ny, lx, ly, ctx.dtype_code, ctx.pitch, ec, en, fx, fy, None, vx, vy, out,
+                                       stream)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        for a, b in zip(got, want):
+            assert abs(a - b) <= REL_TOL * abs(b), (got, want)
+    ctx.close()
+
+
 def test_noalloc_rejects_grids_beyond_its_limits(api):
     import torch
     t = torch.zeros(8, device="cuda")
