@@ -68,7 +68,8 @@ def parse():
     ap.add_argument("--c2-sweeps", type=int, default=100, help="sweeps per smoother in the 1024^2 FP64 table")
     ap.add_argument("--uzawa-n", type=int, default=1024, help="grid of the Uzawa Stokes solve")
     ap.add_argument("--robust-n", type=int, default=256, help="grid of the smoother robustness comparison")
-    ap.add_argument("--only", choices=["solve", "batch", "autotune", "c2", "uzawa", "robustness", "fp32err"],
+    ap.add_argument("--only", choices=["solve", "batch", "autotune", "c2", "uzawa", "robustness", "fp32err",
+                                       "smoothers"],
                     help="run one extra leg alone and print its JSON (for profiling it)")
     return ap.parse_args()
 
@@ -892,6 +893,33 @@ def variant_table(args, api, prob):
     return out
 
 
+def smoothers_leg(args, api):
+    """The global-memory smoothers (Jacobi as separate vx / vy passes, fused
+    Jacobi, red-black Gauss-Seidel) on the layered sinker at --n, FP32 and
+    FP64: one warm-up call and three timed calls of `sweeps` sweeps each
+    (few launches, so that an ncu capture of the same command stays small).
+    Gcell-updates/s and effective GB/s (8 words per cell-sweep) over the
+    measured HBM copy bandwidth."""
+    from paper_2509_19061_gb300 import inputs
+    n = args.n
+    peak, _ = measured_peaks()
+    prob = inputs.layered_sinker(n, seed=4)
+    out = {}
+    for dt_name, sweeps in (("f32", 4), ("f64", 2)):
+        c = api.StokesContext(n, n, 1.0, 1.0, dt_name)
+        c.set_problem(prob)
+        vx, vy = c.field(), c.field()
+        for v in ("jacobi", "fused", "rbgs"):
+            kw = dict(variant=v, sweeps=sweeps)
+            ms = _time_smooth(c, vx, vy, kw, reps=3)
+            cu = n * n * sweeps / (ms / 1e3)
+            gbs = cu * WORDS_PER_CELL_SWEEP * (8 if dt_name == "f64" else 4) / 1e9
+            out["%s_%s" % (dt_name, v)] = {"gcell_updates_per_s": cu / 1e9, "effective_gbs": gbs,
+                                            "frac": gbs / peak, "sweeps": sweeps, "ms_per_call": ms}
+        c.close()
+    return out
+
+
 def c2_table(args, api):
     """The 1024^2 sinker at contrast 1e4 in FP64: all five smoothers, 100
     sweeps each (--c2-sweeps), RAS with tiles 16^2, 32^2, 64 x 32 and k in {1, 2, 4, 8}
@@ -938,7 +966,7 @@ def run_only(args):
         print(json.dumps({"leg": args.only, "result": fp32_error_leg(args, api, inputs.layered_sinker(args.n, seed=4))}))
         return 0
     leg = {"solve": solve_times, "batch": batch_leg, "autotune": autotune_leg, "c2": c2_table,
-           "uzawa": uzawa_leg, "robustness": robustness_leg}[args.only]
+           "uzawa": uzawa_leg, "robustness": robustness_leg, "smoothers": smoothers_leg}[args.only]
     print(json.dumps({"leg": args.only, "result": leg(args, api)}))
     return 0
 

@@ -13,8 +13,11 @@
  * Every field buffer the caller passes is one pitched 2D array of
  * (ny+1) rows x `pitch` elements of the context's dtype (row j starts at
  * element j*pitch), whatever the field; stokes_get_layout returns the pitch
- * and each field's own extent.  Entries outside a field's extent are padding:
- * they are never read, and output buffers get zeros there.  The unknowns are
+ * and each field's own extent.  Every field buffer starts on a 16-byte
+ * boundary (any cudaMalloc or torch allocation does; the smoothing entry
+ * points return STOKES_ERR_ARG otherwise).  Entries outside a field's extent
+ * are padding: their values are never used (the kernels may read the bytes,
+ * which lie inside the buffer), and output buffers get zeros there.  The unknowns are
  * vx with 1 <= i <= nx-1 and vy with 1 <= j <= ny-1; the wall entries
  * vx[.][0], vx[.][nx], vy[0][.], vy[ny][.] are Dirichlet data (zero for the
  * impermeable walls of Sec. 6.1), read but never written.  The shear stress is

@@ -65,8 +65,11 @@ cudaError_t launch_apply(const GridDesc<T> &g, const T *eta_c, const T *eta_n, c
 template <typename T>
 cudaError_t launch_jacobi(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const T *vx, const T *vy, T *ox, T *oy,
                           int fused, cudaStream_t s);
+// One red-black Gauss-Seidel sweep (vx red, vx black, vy red, vy black):
+// reads (vx, vy), writes the unknowns of (ox, oy).
 template <typename T>
-cudaError_t launch_rbgs_sweep(const GridDesc<T> &g, const Coeffs<T> &c, T omega, T *vx, T *vy, cudaStream_t s);
+cudaError_t launch_rbgs_sweep(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const T *vx, const T *vy, T *ox,
+                              T *oy, cudaStream_t s);
 // copy the in-extent entries (unknowns and walls) of vx, vy
 template <typename T>
 cudaError_t launch_copy_velocity(const GridDesc<T> &g, const T *vx, const T *vy, T *ox, T *oy, cudaStream_t s);

@@ -6,10 +6,11 @@
 
 namespace stokes {
 
-// number of ping-pong passes of a smoothing (RBGS works in place: 0)
+// number of ping-pong passes of a smoothing (one per sweep; one per outer
+// iteration of RAS)
 int smooth_passes(const SmoothSpec &p)
 {
-    if (p.sweeps <= 0 || p.variant == STOKES_RBGS) return 0;
+    if (p.sweeps <= 0) return 0;
     if (p.variant == STOKES_RAS) return (p.sweeps + p.k - 1) / p.k;
     return p.sweeps;
 }
@@ -27,10 +28,6 @@ int smooth_buffers(const GridDesc<T> &g, const Coeffs<T> &k, T *vx, T *vy, T *sx
         if (st != STOKES_OK) return st;                                                                            \
     } while (0)
     if (p.sweeps == 0) return STOKES_OK;
-    if (p.variant == STOKES_RBGS) {
-        for (int it = 0; it < p.sweeps; ++it) LAUNCH(STOKES_K_RBGS, 4, launch_rbgs_sweep<T>(g, k, omega, vx, vy, s));
-        return STOKES_OK;
-    }
     // ping-pong between (vx, vy) and the scratch pair; the scratch walls take
     // the Dirichlet values of (vx, vy).  With a second scratch pair (tx, ty)
     // and an odd number n >= 3 of passes, pass 1 goes from (vx, vy) to (sx, sy),
@@ -78,7 +75,9 @@ int smooth_buffers(const GridDesc<T> &g, const Coeffs<T> &k, T *vx, T *vy, T *sx
         }
     } else {
         for (int it = 0; it < p.sweeps; ++it) {
-            if (p.variant == STOKES_JACOBI_BLOCKED) {
+            if (p.variant == STOKES_RBGS) {
+                LAUNCH(STOKES_K_RBGS, 1, launch_rbgs_sweep<T>(g, k, omega, ax, ay, bx, by, s));
+            } else if (p.variant == STOKES_JACOBI_BLOCKED) {
                 const TileGrid tg = make_tiles(g.nx, g.ny, p.ti, p.tj, 0, 0);
                 LAUNCH(STOKES_K_RAS, 1, launch_ras<T>(g, k, omega, tg, 1, 0, ax, ay, bx, by, run, s));
             } else {

@@ -1,6 +1,6 @@
 // stencil_kernels.cu -- global-memory kernels of libstokes: copies, right-hand
-// side, operator apply, Jacobi (separate and fused passes), red-black
-// Gauss-Seidel and the energy residual norm.
+// side, operator apply and the energy residual norm (the Jacobi and
+// Gauss-Seidel sweeps are in sweep_kernels.cu).
 //
 // The operator is the flux form of Eq. (1)-(3) of arXiv 2509.19061 on the
 // fully staggered grid of Sec. 2.1: deviatoric stresses at cell centres
@@ -86,58 +86,6 @@ __global__ void k_apply(GridDesc<T> g, const T *__restrict__ eta_c, const T *__r
     }
     ox[q] = rx;
     oy[q] = ry;
-}
-
-// One damped Jacobi pass.  DO_X / DO_Y select the component(s); every update
-// reads the old (vx, vy); walls are copied so the output is a complete field.
-template <typename T, bool DO_X, bool DO_Y>
-__global__ void k_jacobi(GridDesc<T> g, Coeffs<T> c, T omega, const T *__restrict__ vx, const T *__restrict__ vy,
-                         T *__restrict__ ox, T *__restrict__ oy)
-{
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    if (i > g.nx || j > g.ny) return;
-    const size_t q = (size_t)j * g.pitch + i;
-    T m, d, vc;
-    if (DO_X) {
-        if (vx_unknown(g, j, i)) {
-            op_x(g, c.eta_c, c.eta_n, vx, vy, j, i, m, d, vc);
-            const T inv = c.inv_dx ? c.inv_dx[q] : inv_diag(d);
-            ox[q] = jacobi_update(vc, c.bx[q], m, jacobi_weight(omega, inv));
-        } else if (vx_wall(g, j, i)) {
-            ox[q] = vx[q];
-        }
-    }
-    if (DO_Y) {
-        if (vy_unknown(g, j, i)) {
-            op_y(g, c.eta_c, c.eta_n, vx, vy, j, i, m, d, vc);
-            const T inv = c.inv_dy ? c.inv_dy[q] : inv_diag(d);
-            oy[q] = jacobi_update(vc, c.by[q], m, jacobi_weight(omega, inv));
-        } else if (vy_wall(g, j, i)) {
-            oy[q] = vy[q];
-        }
-    }
-}
-
-// One colour of one component of red-black Gauss-Seidel, in place.  Thread t
-// of row j takes the t-th point of that colour in the row.
-template <typename T, bool X>
-__global__ void k_rbgs(GridDesc<T> g, Coeffs<T> c, T omega, int colour, T *__restrict__ vx, T *__restrict__ vy)
-{
-    const int t = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    const int i = 2 * t + ((j + colour) & 1);
-    const size_t q = (size_t)j * g.pitch + i;
-    T m, d, vc;
-    if (X) {
-        if (!vx_unknown(g, j, i)) return;
-        op_x(g, c.eta_c, c.eta_n, vx, vy, j, i, m, d, vc);
-        const T inv = c.inv_dx ? c.inv_dx[q] : inv_diag(d);
-        vx[q] = jacobi_update(vc, c.bx[q], m, jacobi_weight(omega, inv));
-    } else {
-        if (!vy_unknown(g, j, i)) return;
-        op_y(g, c.eta_c, c.eta_n, vx, vy, j, i, m, d, vc);
-        const T inv = c.inv_dy ? c.inv_dy[q] : inv_diag(d);
-        vy[q] = jacobi_update(vc, c.by[q], m, jacobi_weight(omega, inv));
-    }
 }
 
 template <typename T>
@@ -469,31 +417,6 @@ cudaError_t launch_apply(const GridDesc<T> &g, const T *eta_c, const T *eta_n, c
 }
 
 template <typename T>
-cudaError_t launch_jacobi(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const T *vx, const T *vy, T *ox, T *oy,
-                          int fused, cudaStream_t s)
-{
-    const dim3 grid = grid2d(g.nx + 1, g.ny + 1), block(BX, BY);
-    if (fused) {
-        k_jacobi<T, true, true><<<grid, block, 0, s>>>(g, c, omega, vx, vy, ox, oy);
-    } else {
-        k_jacobi<T, true, false><<<grid, block, 0, s>>>(g, c, omega, vx, vy, ox, oy);
-        k_jacobi<T, false, true><<<grid, block, 0, s>>>(g, c, omega, vx, vy, ox, oy);
-    }
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_rbgs_sweep(const GridDesc<T> &g, const Coeffs<T> &c, T omega, T *vx, T *vy, cudaStream_t s)
-{
-    const dim3 grid = grid2d((g.nx + 2) / 2, g.ny + 1), block(BX, BY);
-    k_rbgs<T, true><<<grid, block, 0, s>>>(g, c, omega, 0, vx, vy);
-    k_rbgs<T, true><<<grid, block, 0, s>>>(g, c, omega, 1, vx, vy);
-    k_rbgs<T, false><<<grid, block, 0, s>>>(g, c, omega, 0, vx, vy);
-    k_rbgs<T, false><<<grid, block, 0, s>>>(g, c, omega, 1, vx, vy);
-    return cudaGetLastError();
-}
-
-template <typename T>
 cudaError_t launch_copy_velocity(const GridDesc<T> &g, const T *vx, const T *vy, T *ox, T *oy, cudaStream_t s)
 {
     k_copy_velocity<T><<<grid2d(g.nx + 1, g.ny + 1), dim3(BX, BY), 0, s>>>(g, vx, vy, ox, oy);
@@ -544,9 +467,6 @@ cudaError_t launch_energy_raw(const GridDesc<T> &g, const T *eta_c, const T *eta
                                        cudaStream_t);                                                              \
     template cudaError_t launch_apply<T>(const GridDesc<T> &, const T *, const T *, const T *, const T *,          \
                                          const T *, T *, T *, cudaStream_t);                                       \
-    template cudaError_t launch_jacobi<T>(const GridDesc<T> &, const Coeffs<T> &, T, const T *, const T *, T *,    \
-                                          T *, int, cudaStream_t);                                                 \
-    template cudaError_t launch_rbgs_sweep<T>(const GridDesc<T> &, const Coeffs<T> &, T, T *, T *, cudaStream_t); \
     template cudaError_t launch_copy_velocity<T>(const GridDesc<T> &, const T *, const T *, T *, T *,              \
                                                  cudaStream_t);                                                    \
     template cudaError_t launch_copy_walls<T>(const GridDesc<T> &, const T *, const T *, T *, T *, cudaStream_t);  \

@@ -1003,9 +1003,14 @@ int stokes_apply_operator(stokes_ctx *c, const void *vx, const void *vy, const v
     return STOKES_OK;
 }
 
+// field buffers start on a 16-byte boundary (the sweep kernels read and write
+// 16-byte vectors; TMA copies need the same)
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
 int stokes_smooth(stokes_ctx *c, void *vx, void *vy, const void *p, const stokes_smooth_params *params)
 {
     if (!c || !vx || !vy) return STOKES_ERR_ARG;
+    if (!aligned16(vx) || !aligned16(vy) || !aligned16(p)) return STOKES_ERR_ARG;
     int ti, tj, st = check_smooth_params(c->nx, c->ny, c->esize, params, &ti, &tj);
     if (st != STOKES_OK) return st;
     if (!c->have_eta || !c->have_f) return STOKES_ERR_STATE;
@@ -1034,6 +1039,7 @@ int stokes_vcycle(stokes_ctx *c, void *vx, void *vy, const void *p, const stokes
                   double *final_rel_resid, int *cycles)
 {
     if (!c || !vx || !vy || !params) return STOKES_ERR_ARG;
+    if (!aligned16(vx) || !aligned16(vy) || !aligned16(p)) return STOKES_ERR_ARG;
     const int st = check_mg_params(c, params);
     if (st != STOKES_OK) return st;
     if (!c->have_eta || !c->have_f) return STOKES_ERR_STATE;
@@ -1046,6 +1052,7 @@ int stokes_uzawa(stokes_ctx *c, void *vx, void *vy, void *p, const stokes_uzawa_
                  int *cycles, double *final_rel_resid)
 {
     if (!c || !vx || !vy || !p || !params) return STOKES_ERR_ARG;
+    if (!aligned16(vx) || !aligned16(vy) || !aligned16(p)) return STOKES_ERR_ARG;
     const stokes_uzawa_params &u = *params;
     if (u.cycles < 0 || !(u.omega_p > 0.0) || !std::isfinite(u.omega_p) || u.theta_interval < 0 ||
         u.theta_stages < 0 || !(u.tol >= 0.0) || u.mg.max_cycles < 1 || u.anderson_depth < 0 ||
