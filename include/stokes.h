@@ -467,6 +467,58 @@ int stokes_batch_kernels(const stokes_batch *b, long long *kernels);
 /* Release every library-owned buffer of the batch.  NULL is accepted. */
 int stokes_batch_destroy(stokes_batch *b);
 
+/* ---- Slab decomposition: RAS as a domain decomposition ---------------------
+ * RAS-Jacobi (Sec. 4.3, Algorithm 2) is a domain decomposition: each tile
+ * solves its local problem on an overlapping subdomain and writes only the
+ * unknowns it owns.  A slab set splits the grid into `nslabs` horizontal
+ * slabs, the layout of a multi-GPU run with one slab per GPU: slab s owns the
+ * cell rows [r0, r1) of a balanced split and keeps its own copy of the
+ * viscosity, the right-hand side and the velocity on the rows [R0, R1) =
+ * [r0 - H, r1 + H) clipped to the grid, H = tile_j + overlap + 1.  Each outer
+ * iteration runs the tile kernel on every slab's storage (the global shifted
+ * tiling of Algorithm 2, so every tile that meets a slab's own rows is
+ * computed there exactly as on the whole grid) and then copies to every slab
+ * the rows it stores but does not own from the neighbour that owns them
+ * (one device-to-device copy per field and side).  The result equals
+ * stokes_smooth's with the same parameters, bit for bit.  All slabs live on
+ * the device and stream of the set; every slab must own at least H + 1 rows.
+ * Layouts are those of a single context (stokes_get_layout of a context of
+ * the same nx, ny, dtype). */
+typedef struct stokes_slabs stokes_slabs; /* opaque, library-owned */
+
+/* Own rows [out[0], out[1]) and stored rows [out[2], out[3]) of slab `slab`
+ * of an ny-row grid split into nslabs slabs, for tiles of tile_j rows and
+ * `overlap`; a host computation (no device).  STOKES_ERR_ARG if a slab would
+ * own fewer than tile_j + overlap + 2 rows. */
+int stokes_slab_plan(int ny, int nslabs, int tile_j, int overlap, int slab, int out[4]);
+
+/* Create a set of nslabs (1 <= nslabs <= ny/2) slabs of an nx x ny grid on
+ * [0, lx] x [0, ly] in `dtype` on `cuda_stream`; the same limits as
+ * stokes_create.  Allocates the global copies; the slab storage is allocated
+ * by the first smoothing (and again when tile_j + overlap changes). */
+int stokes_slabs_create(int nx, int ny, double lx, double ly, int dtype, int nslabs, void *cuda_stream,
+                        stokes_slabs **out);
+
+/* Viscosity and body force of the whole grid (device buffers in the
+ * single-context layout, copied), as stokes_set_viscosity / stokes_set_rhs. */
+int stokes_slabs_set_viscosity(stokes_slabs *s, const void *eta_c, const void *eta_n);
+int stokes_slabs_set_rhs(stokes_slabs *s, const void *fx, const void *fy);
+
+/* RAS-Jacobi smoothing of the whole grid's (vx, vy) in place (p may be NULL)
+ * through the slabs: `params` as for stokes_smooth with variant STOKES_RAS
+ * (anything else is STOKES_ERR_ARG).  Scatters (vx, vy) and p into the
+ * slabs, runs the outer iterations with their halo exchanges, gathers the
+ * own rows back and synchronises the stream (STOKES_ERR_TIMEOUT if a bounded
+ * wait of the tile kernel gave up).  STOKES_ERR_STATE before the viscosity
+ * and the right-hand side are set. */
+int stokes_slabs_smooth(stokes_slabs *s, void *vx, void *vy, const void *p, const stokes_smooth_params *params);
+
+/* Halo copies made so far and their bytes. */
+int stokes_slabs_exchanges(const stokes_slabs *s, long long *copies, long long *bytes);
+
+/* Release the set.  NULL returns STOKES_ERR_ARG. */
+int stokes_slabs_destroy(stokes_slabs *s);
+
 /* Release every library-owned buffer of the context.  NULL is accepted. */
 int stokes_destroy(stokes_ctx *ctx);
 

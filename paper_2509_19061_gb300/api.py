@@ -101,6 +101,13 @@ _SIGS = {
     "stokes_batch_kernels": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
     "stokes_batch_set_option": (_I, [_VP, _I, ctypes.c_longlong]),
     "stokes_batch_destroy": (_I, [_VP]),
+    "stokes_slab_plan": (_I, [_I, _I, _I, _I, _I, ctypes.POINTER(_I)]),
+    "stokes_slabs_create": (_I, [_I, _I, _D, _D, _I, _I, _VP, ctypes.POINTER(_VP)]),
+    "stokes_slabs_set_viscosity": (_I, [_VP, _VP, _VP]),
+    "stokes_slabs_set_rhs": (_I, [_VP, _VP, _VP]),
+    "stokes_slabs_smooth": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(stokes_smooth_params)]),
+    "stokes_slabs_exchanges": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+    "stokes_slabs_destroy": (_I, [_VP]),
     "stokes_destroy": (_I, [_VP]),
     "stokes_strerror": (ctypes.c_char_p, [_I]),
     "stokes_last_cuda_error": (ctypes.c_char_p, []),
@@ -354,6 +361,44 @@ def stokes_batch_destroy(b):
         _check(_lib().stokes_batch_destroy(b), "stokes_batch_destroy")
 
 
+def stokes_slab_plan(ny, nslabs, tile_j, overlap, slab):
+    """(r0, r1, R0, R1): own and stored cell rows of one slab (host only)."""
+    out = (_I * 4)()
+    _check(_lib().stokes_slab_plan(ny, nslabs, tile_j, overlap, slab, out), "stokes_slab_plan")
+    return tuple(out)
+
+
+def stokes_slabs_create(nx, ny, lx, ly, dtype, nslabs, cuda_stream=None):
+    out = ctypes.c_void_p()
+    stream = ctypes.c_void_p(cuda_stream) if cuda_stream else None
+    _check(_lib().stokes_slabs_create(nx, ny, lx, ly, dtype, nslabs, stream, ctypes.byref(out)),
+           "stokes_slabs_create")
+    return out
+
+
+def stokes_slabs_set_viscosity(s, eta_c, eta_n):
+    _check(_lib().stokes_slabs_set_viscosity(s, _ptr(eta_c), _ptr(eta_n)), "stokes_slabs_set_viscosity")
+
+
+def stokes_slabs_set_rhs(s, fx, fy):
+    _check(_lib().stokes_slabs_set_rhs(s, _ptr(fx), _ptr(fy)), "stokes_slabs_set_rhs")
+
+
+def stokes_slabs_smooth(s, vx, vy, p, params):
+    _check(_lib().stokes_slabs_smooth(s, _ptr(vx), _ptr(vy), _ptr(p), ctypes.byref(params)), "stokes_slabs_smooth")
+
+
+def stokes_slabs_exchanges(s):
+    c, b = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(_lib().stokes_slabs_exchanges(s, ctypes.byref(c), ctypes.byref(b)), "stokes_slabs_exchanges")
+    return c.value, b.value
+
+
+def stokes_slabs_destroy(s):
+    if s is not None:
+        _check(_lib().stokes_slabs_destroy(s), "stokes_slabs_destroy")
+
+
 # --------------------------------------------------------------------------
 # convenience wrapper with torch tensors
 # --------------------------------------------------------------------------
@@ -539,3 +584,40 @@ class BatchContext:
 
     def set_option(self, option, value):
         stokes_batch_set_option(self.b, option, value)
+
+
+class SlabContext:
+    """Owns a stokes_slabs set; field tensors use the single-context layout
+    (StokesContext.pack / unpack of the same grid)."""
+
+    def __init__(self, nx, ny, lx=1.0, ly=1.0, dtype="f64", nslabs=2, device="cuda", stream=None):
+        import torch
+        self.torch = torch
+        self.nx, self.ny, self.nslabs = nx, ny, nslabs
+        self.dtype_code = STOKES_F64 if dtype in ("f64", "float64", torch.float64) else STOKES_F32
+        self.stream = stream if stream is not None else torch.cuda.current_stream(torch.device(device))
+        self.s = stokes_slabs_create(nx, ny, lx, ly, self.dtype_code, nslabs, self.stream.cuda_stream)
+
+    def close(self):
+        if self.s is not None:
+            stokes_slabs_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_viscosity_dev(self, eta_c, eta_n):
+        stokes_slabs_set_viscosity(self.s, eta_c, eta_n)
+
+    def set_rhs_dev(self, fx, fy):
+        stokes_slabs_set_rhs(self.s, fx, fy)
+
+    def smooth(self, vx, vy, p=None, **kw):
+        kw.setdefault("variant", "ras")
+        stokes_slabs_smooth(self.s, vx, vy, p, smooth_params(**kw))
+
+    def exchanges(self):
+        return stokes_slabs_exchanges(self.s)
