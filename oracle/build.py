@@ -1,4 +1,4 @@
-"""Build the C oracle into oracle/libstokes_oracle.so (plain gcc, FP64).
+"""Build the C oracle (2D and 3D) into oracle/libstokes_oracle.so (plain gcc, FP64).
 
 Test infrastructure only: the oracle is loaded by the tests, the smoke check
 and the CPU-baseline leg of the benchmark, never by the product path.
@@ -9,6 +9,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "stokes_oracle.c")
+SRCS = [SRC, os.path.join(HERE, "stokes3d_oracle.c")]
 LIB = os.path.join(HERE, "libstokes_oracle.so")
 
 # -ffp-contract=off: every product and sum is rounded exactly where it is written.
@@ -17,9 +18,9 @@ CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-Wall", "
 
 def build_oracle(force: bool = False) -> str:
     """Compile the oracle if the library is missing or older than its source."""
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(s) for s in SRCS):
         tmp = LIB + ".tmp.%d" % os.getpid()
-        subprocess.run(["gcc", *CFLAGS, "-o", tmp, SRC, "-lm"], check=True)
+        subprocess.run(["gcc", *CFLAGS, "-o", tmp, *SRCS, "-lm"], check=True)
         os.replace(tmp, LIB)
     return LIB
 

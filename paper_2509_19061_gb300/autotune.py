@@ -25,6 +25,20 @@ DEFAULT_CANDIDATES = [(ti, tj, k, o) for (ti, tj) in ((16, 16), (32, 32), (56, 3
                       for k in (1, 2, 4, 8) for o in sorted({0, k - 1})]
 # 64-column windows, which the FP32 packed-pair kernel sweeps: exact Jacobi at k = 8 and ring-only tiles
 DEFAULT_CANDIDATES += [(48, 32, 8, 7), (62, 32, 4, 0), (62, 32, 8, 0), (48, 64, 8, 7), (62, 56, 8, 0)]
+# FP64 exact Jacobi at k = 8 on a window that fits the register layout (40 x 40)
+DEFAULT_CANDIDATES += [(24, 24, 8, 7)]
+
+
+def fast_layout(api, nx, ny, ti, tj, overlap, dtype):
+    """Whether a launch shape runs a register-resident tile kernel.  Windows
+    that fit none (an FP32 window wider than 64 columns at overlap 7, an FP64
+    window of more than 512 cells per strip column set) fall to the general
+    all-shared-memory kernel, 3 to 5 times slower per sweep, so the tuner
+    does not consider them."""
+    try:
+        return api.stokes_tile_kernel_plan(nx, ny, (ti, tj), overlap, dtype)[0] != "shared"
+    except api.StokesError:
+        return False
 
 
 @dataclass
@@ -120,7 +134,8 @@ def tune(api, prob, dtype="f64", inner="f32", candidates=None, tol=1e-8, max_cyc
     capture), then `reps` times from a zero guess; the minimum counts.
     Candidates that do not converge get an infinite time."""
     import torch
-    cands = [c for c in (candidates or DEFAULT_CANDIDATES) if feasible(*c, prob.nx, prob.ny)]
+    cands = [c for c in (candidates or DEFAULT_CANDIDATES) if feasible(*c, prob.nx, prob.ny)
+             and fast_layout(api, prob.nx, prob.ny, c[0], c[1], c[3], inner)]
     ctx = api.StokesContext(prob.nx, prob.ny, prob.lx, prob.ly, dtype)
     ctx.set_problem(prob)
     vx, vy = ctx.field(), ctx.field()
@@ -185,6 +200,8 @@ def tune_batch(api, probs, name, candidates=None, cache=None, tol=1e-8, max_cycl
     cands = candidates or [(32, 32, 4, 3), (56, 32, 4, 3), (32, 32, 8, 7), (32, 32, 4, 0), (56, 32, 4, 0),
                            (32, 32, 8, 0), (56, 32, 8, 0), (32, 32, 2, 1), (16, 16, 4, 3),
                            (48, 32, 8, 7), (48, 64, 8, 7), (62, 56, 8, 0)]
+    n_max = max(max(q.nx, q.ny) for q in probs)
+    cands = [c for c in cands if fast_layout(api, n_max, n_max, c[0], c[1], c[3], "f32")]
     b = api.BatchContext([q.nx for q in probs], [q.ny for q in probs], [q.lx for q in probs],
                          [q.ly for q in probs], "f64")
     b.set_problems(probs)

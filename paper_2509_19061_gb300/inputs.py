@@ -202,3 +202,119 @@ def random_shifts(n_outer, ti, tj, seed):
     s[:, 0] = rng.integers(0, ti, size=n_outer)
     s[:, 1] = rng.integers(0, tj, size=n_outer)
     return s
+
+
+# ---------------------------------------------------------------------------
+# 3D staggered grid: nx x ny x nz cells, arrays indexed [k][j][i]
+#   vx-like nz x ny x (nx+1), vy-like nz x (ny+1) x nx, vz-like (nz+1) x ny x nx,
+#   cells nz x ny x nx, x-y edges nz x (ny+1) x (nx+1), x-z edges
+#   (nz+1) x ny x (nx+1), y-z edges (nz+1) x (ny+1) x nx.
+# Density sits with vz (gravity along -z); the body force is f_z = -rho g_z.
+# ---------------------------------------------------------------------------
+@dataclass
+class Problem3:
+    nx: int
+    ny: int
+    nz: int
+    lx: float
+    ly: float
+    lz: float
+    eta_c: np.ndarray
+    eta_xy: np.ndarray
+    eta_xz: np.ndarray
+    eta_yz: np.ndarray
+    rho: np.ndarray  # at vz points
+    fx: np.ndarray
+    fy: np.ndarray
+    fz: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def hx(self):
+        return self.lx / self.nx
+
+    @property
+    def hy(self):
+        return self.ly / self.ny
+
+    @property
+    def hz(self):
+        return self.lz / self.nz
+
+
+def _axes3(nx, ny, nz, lx, ly, lz):
+    hx, hy, hz = lx / nx, ly / ny, lz / nz
+    c = [(np.arange(n) + 0.5) * h for n, h in ((nx, hx), (ny, hy), (nz, hz))]
+    e = [np.arange(n + 1) * h for n, h in ((nx, hx), (ny, hy), (nz, hz))]
+    return c, e
+
+
+def _ball(xs, ys, zs, cx, cy, cz, r):
+    """Mask [k][j][i] of the points (xs[i], ys[j], zs[k]) strictly inside the ball."""
+    return ((xs[None, None, :] - cx) ** 2 + (ys[None, :, None] - cy) ** 2 + (zs[:, None, None] - cz) ** 2) < r * r
+
+
+def sinker3d_problem(nx, ny=None, nz=None, eta_in=1e3, eta_out=1.0, rho_in=2.0, rho_out=1.0, radius=0.1,
+                     center=(0.5, 0.5, 0.5), lx=1.0, ly=1.0, lz=1.0, g_z=-1.0):
+    """A spherical sinker in a box (the 3D counterpart of the Sec. 6.1
+    sinker): every material property point-sampled at its own location."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    (xc, yc, zc), (xn, yn, zn) = _axes3(nx, ny, nz, lx, ly, lz)
+    cx, cy, cz = center[0] * lx, center[1] * ly, center[2] * lz
+    r = radius * min(lx, ly, lz)
+    eta_c = np.where(_ball(xc, yc, zc, cx, cy, cz, r), eta_in, eta_out).astype(np.float64)
+    eta_xy = np.where(_ball(xn, yn, zc, cx, cy, cz, r), eta_in, eta_out).astype(np.float64)
+    eta_xz = np.where(_ball(xn, yc, zn, cx, cy, cz, r), eta_in, eta_out).astype(np.float64)
+    eta_yz = np.where(_ball(xc, yn, zn, cx, cy, cz, r), eta_in, eta_out).astype(np.float64)
+    rho = np.where(_ball(xc, yc, zn, cx, cy, cz, r), rho_in, rho_out).astype(np.float64)
+    fx = np.zeros((nz, ny, nx + 1))
+    fy = np.zeros((nz, ny + 1, nx))
+    fz = -rho * g_z
+    fz[0] = 0.0
+    fz[nz] = 0.0
+    return Problem3(nx, ny, nz, lx, ly, lz, eta_c, eta_xy, eta_xz, eta_yz, rho, fx, fy, fz,
+                    dict(kind="sinker3d", eta_in=eta_in))
+
+
+def layered3d_problem(n, seed=6, layers=10, eta_range=(-3.0, 3.0), sinker_eta=1e3, sinker_rho=2.0, radius=0.1):
+    """The 3D counterpart of the layered sinker: `layers` horizontal layers
+    (along z, drawn bottom to top) with log10 eta ~ U[eta_range] plus a
+    centred spherical sinker, on the unit cube."""
+    rng = np.random.default_rng(seed)
+    prob = sinker3d_problem(n, eta_in=sinker_eta, eta_out=1.0, rho_in=sinker_rho, radius=radius)
+    (xc, yc, zc), (xn, yn, zn) = _axes3(n, n, n, 1.0, 1.0, 1.0)
+    etas = 10.0 ** rng.uniform(*eta_range, size=layers)
+    lay_c = np.minimum((zc * layers).astype(int), layers - 1)
+    lay_n = np.minimum((zn * layers).astype(int), layers - 1)
+    r = radius
+    for arr, zs, xs, ys in ((prob.eta_c, lay_c, xc, yc), (prob.eta_xy, lay_c, xn, yn),
+                            (prob.eta_xz, lay_n, xn, yc), (prob.eta_yz, lay_n, xc, yn)):
+        zz = zc if zs is lay_c else zn
+        inside = _ball(xs, ys, zz, 0.5, 0.5, 0.5, r)
+        arr[...] = np.where(inside, sinker_eta, etas[zs][:, None, None])
+    prob.meta = dict(kind="layered3d", seed=seed, layer_eta=etas.tolist())
+    return prob
+
+
+def random_viscosity3d(nx, ny, nz, seed, log10_range=(-2.0, 2.0)):
+    """Seeded log-uniform viscosity at the cells and the three edge sets."""
+    rng = np.random.default_rng(seed)
+    u = lambda shape: 10.0 ** rng.uniform(*log10_range, size=shape)
+    return (u((nz, ny, nx)), u((nz, ny + 1, nx + 1)), u((nz + 1, ny, nx + 1)), u((nz + 1, ny + 1, nx)))
+
+
+def random_velocity3d(nx, ny, nz, seed, scale=1.0):
+    """Seeded random velocity with zero wall entries."""
+    rng = np.random.default_rng(seed)
+    vx = rng.standard_normal((nz, ny, nx + 1)) * scale
+    vy = rng.standard_normal((nz, ny + 1, nx)) * scale
+    vz = rng.standard_normal((nz + 1, ny, nx)) * scale
+    vx[:, :, 0] = vx[:, :, nx] = 0.0
+    vy[:, 0, :] = vy[:, ny, :] = 0.0
+    vz[0] = vz[nz] = 0.0
+    return vx, vy, vz
+
+
+def random_pressure3d(nx, ny, nz, seed, scale=1.0):
+    return np.random.default_rng(seed).standard_normal((nz, ny, nx)) * scale

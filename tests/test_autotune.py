@@ -79,3 +79,24 @@ def test_shipped_cache_covers_the_tuned_buckets():
         assert autotune.feasible(ch.tile_i, ch.tile_j, ch.k, ch.overlap, 256, 256)
     kw = autotune.tuned_smoother(1024, 1024, np.ones((2, 2)), np.full((3, 3), 1e4))
     assert kw["variant"] == "ras" and kw["k"] >= 1
+
+
+@pytest.mark.gpu
+def test_tuner_keeps_only_register_layout_shapes():
+    """Launch shapes whose window fits no register layout run the general
+    shared-memory tile kernel (3 to 5 times slower per sweep); the tuner
+    leaves them out, so no tuned schedule falls off that cliff."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_19061_gb300 import api, build
+    build.build()
+    assert not autotune.fast_layout(api, 4096, 4096, 56, 32, 7, "f32")   # 72-column window
+    assert autotune.fast_layout(api, 4096, 4096, 48, 64, 7, "f32")       # 64 x 80: pair layout
+    assert not autotune.fast_layout(api, 1024, 1024, 32, 32, 7, "f64")   # 48 x 48: 576 threads
+    assert autotune.fast_layout(api, 1024, 1024, 24, 24, 7, "f64")       # 40 x 40
+    for dtype, n in (("f32", 4096), ("f64", 1024)):
+        kept = [c for c in autotune.DEFAULT_CANDIDATES if autotune.fast_layout(api, n, n, c[0], c[1], c[3], dtype)]
+        assert len(kept) >= 12
+        for ti, tj, k, o in kept:
+            assert api.stokes_tile_kernel_plan(n, n, (ti, tj), o, dtype)[0] in ("tma", "pair", "global")
