@@ -68,8 +68,9 @@ def parse():
     ap.add_argument("--c2-sweeps", type=int, default=100, help="sweeps per smoother in the 1024^2 FP64 table")
     ap.add_argument("--uzawa-n", type=int, default=1024, help="grid of the Uzawa Stokes solve")
     ap.add_argument("--robust-n", type=int, default=256, help="grid of the smoother robustness comparison")
+    ap.add_argument("--n3d", type=int, default=384, help="cells per side of the 3D smoothing leg")
     ap.add_argument("--only", choices=["solve", "batch", "autotune", "c2", "uzawa", "robustness", "fp32err",
-                                       "smoothers"],
+                                       "smoothers", "smooth3d"],
                     help="run one extra leg alone and print its JSON (for profiling it)")
     return ap.parse_args()
 
@@ -425,6 +426,8 @@ def run_ours(args):
         line["autotune"] = autotune_leg(args, api)
         line["uzawa_stokes"] = uzawa_leg(args, api)
         line["smoother_robustness"] = robustness_leg(args, api)
+        line["smooth3d"] = smooth3d_leg(args, api)
+        line["global_smoothers"] = smoothers_leg(args, api)
         line["cpu_baseline"] = {kk: vv for kk, vv in cpu_sample(args, args.cpu_seconds).items() if kk != "seconds"}
     ctx.close()
     if rank == 0:
@@ -926,6 +929,52 @@ def smoothers_leg(args, api):
     return out
 
 
+WORDS_PER_CELL_SWEEP_3D = 13  # read vx, vy, vz, eta_c, eta_xy, eta_xz, eta_yz, bx, by, bz; write vx, vy, vz
+
+
+def smooth3d_leg(args, api):
+    """The 3D operator (the 3D extension of Sec. 9): the layered 3D sinker at
+    --n3d cells per side (fields of 4 or 8 bytes x (n+1)^2 x pitch, far above
+    L2), FP32 and FP64: fused Jacobi and RAS-Jacobi on 3D tiles (space and
+    time blocked together), one warm-up call, then three timed calls.
+    Gcell-updates/s (one cell-update: its vx, vy and vz once) and effective
+    GB/s at 13 words per cell-sweep over the measured HBM copy bandwidth."""
+    from paper_2509_19061_gb300 import inputs
+    peak, _ = measured_peaks()
+    out = {}
+    for dt_name, n in (("f32", args.n3d), ("f64", max(64, args.n3d // 2))):
+        prob = inputs.layered3d_problem(n, seed=6)
+        ctx = api.Stokes3DContext(n, n, n, 1.0, 1.0, 1.0, dt_name)
+        ctx.set_problem(prob)
+        v = [ctx.field() for _ in range(3)]
+        cases = [dict(variant="fused", sweeps=4), dict(variant="ras", sweeps=4, tile=(8, 8, 8), k=2, overlap=1),
+                 dict(variant="ras", sweeps=4, tile=(8, 8, 8), k=4, overlap=0)]
+        if dt_name == "f32":
+            cases.append(dict(variant="ras", sweeps=4, tile=(16, 8, 8), k=2, overlap=1))
+        import torch
+        stream = torch.cuda.current_stream()
+        for kw in cases:
+            ctx.smooth(*v, None, **kw)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                ctx.smooth(*v, None, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 3
+            cu = n ** 3 * kw["sweeps"] / (ms / 1e3)
+            gbs = cu * WORDS_PER_CELL_SWEEP_3D * (8 if dt_name == "f64" else 4) / 1e9
+            label = "%s_%d_%s" % (dt_name, n, kw["variant"])
+            if kw["variant"] == "ras":
+                label += "_%dx%dx%d_k%d_o%d" % (kw["tile"] + (kw["k"], kw["overlap"]))
+            out[label] = {"gcell_updates_per_s": cu / 1e9, "effective_gbs": gbs, "frac": gbs / peak,
+                          "ms_per_call": ms, "sweeps": kw["sweeps"]}
+        e = ctx.energy(*v)
+        out["%s_%d_energy_after" % (dt_name, n)] = (e[0] / e[2]) ** 0.5
+        ctx.close()
+    return out
+
+
 def c2_table(args, api):
     """The 1024^2 sinker at contrast 1e4 in FP64: all five smoothers, 100
     sweeps each (--c2-sweeps), RAS with tiles 16^2, 32^2, 64 x 32 and k in {1, 2, 4, 8}
@@ -979,7 +1028,8 @@ def run_only(args):
         print(json.dumps({"leg": args.only, "result": fp32_error_leg(args, api, inputs.layered_sinker(args.n, seed=4))}))
         return 0
     leg = {"solve": solve_times, "batch": batch_leg, "autotune": autotune_leg, "c2": c2_table,
-           "uzawa": uzawa_leg, "robustness": robustness_leg, "smoothers": smoothers_leg}[args.only]
+           "uzawa": uzawa_leg, "robustness": robustness_leg, "smoothers": smoothers_leg,
+           "smooth3d": smooth3d_leg}[args.only]
     print(json.dumps({"leg": args.only, "result": leg(args, api)}))
     return 0
 

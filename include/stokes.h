@@ -519,6 +519,83 @@ int stokes_slabs_exchanges(const stokes_slabs *s, long long *copies, long long *
 /* Release the set.  NULL returns STOKES_ERR_ARG. */
 int stokes_slabs_destroy(stokes_slabs *s);
 
+/* ---- 3D: the staggered operator in three dimensions -------------------------
+ * The paper develops the method in 2D and names the 3D extension (space-time
+ * "4D" blocking) as future work (Sec. 9).  A 3D context carries the same
+ * operator, readings and smoothers over to an nx x ny x nz grid on
+ * [0, lx] x [0, ly] x [0, lz]:
+ *   vx[k][j][i] at (i hx, (j+1/2) hy, (k+1/2) hz),  k < nz, j < ny, i <= nx
+ *   vy[k][j][i] at ((i+1/2) hx, j hy, (k+1/2) hz),  k < nz, j <= ny, i < nx
+ *   vz[k][j][i] at ((i+1/2) hx, (j+1/2) hy, k hz),  k <= nz, j < ny, i < nx
+ *   p, eta_c at cell centres (k < nz, j < ny, i < nx)
+ *   eta_xy at x-y edges (i hx, j hy, (k+1/2) hz), the viscosity of sigma'_xy
+ *   eta_xz at x-z edges (i hx, (j+1/2) hy, k hz), of sigma'_xz
+ *   eta_yz at y-z edges ((i+1/2) hx, j hy, k hz), of sigma'_yz
+ * sigma'_ii = 2 eta_c dv_i/dx_i at the cells, sigma'_ij = eta_ij (dv_i/dx_j +
+ * dv_j/dx_i) at the edges, zero on an edge in a wall it is tangential to (free
+ * slip); the unknowns are the interior faces of each component.  Every field
+ * buffer is one array of (nz+1) planes x (ny+1) rows x pitch elements of the
+ * context's dtype, entry (k, j, i) at (k (ny+1) + j) pitch + i, starting on a
+ * 16-byte boundary (stokes3d_get_layout gives pitch and size).  Ownership,
+ * streams and errors as for the 2D context. */
+typedef struct stokes3d_ctx stokes3d_ctx; /* opaque, library-owned */
+
+/* Smoothing parameters in 3D: variant STOKES_JACOBI_FUSED or STOKES_RAS;
+ * RAS tiles of tile_i x tile_j x tile_k cells (all >= 1) cut at s + m T in
+ * each direction, `k` local sweeps on the tile grown by `overlap`; shifts as
+ * in 2D with three values per outer iteration (SplitMix64 draws 3t, 3t+1,
+ * 3t+2 of `seed` taken mod the tile sizes, or the list shifts[3t .. 3t+2]). */
+typedef struct {
+    int variant;
+    int sweeps;
+    int tile_i, tile_j, tile_k;
+    int k;
+    int overlap;
+    double omega;
+    uint64_t seed;
+    int shift_mode;
+    const int32_t *shifts;
+} stokes3d_smooth_params;
+
+/* Create a 3D context: 2 <= nx, ny, nz <= 4096, lengths > 0, dtype
+ * STOKES_F32 or STOKES_F64, work on `cuda_stream`.  Allocates its buffers. */
+int stokes3d_create(int nx, int ny, int nz, double lx, double ly, double lz, int dtype, void *cuda_stream,
+                    stokes3d_ctx **out);
+
+/* Row pitch (elements), rows per plane (ny + 1) and elements of one field buffer. */
+int stokes3d_get_layout(const stokes3d_ctx *ctx, int *pitch_elems, int *plane_rows, size_t *alloc_elems);
+
+/* Viscosity at cells and edges (device buffers, copied; the edges in walls
+ * they are tangential to are ignored). */
+int stokes3d_set_viscosity(stokes3d_ctx *ctx, const void *eta_c, const void *eta_xy, const void *eta_xz,
+                           const void *eta_yz);
+
+/* Body force (fx like vx, fy like vy, fz like vz; copied). */
+int stokes3d_set_rhs(stokes3d_ctx *ctx, const void *fx, const void *fy, const void *fz);
+
+/* out = M v + G p at the unknowns (p may be NULL), zero elsewhere in each
+ * field's extent.  STOKES_ERR_STATE before the viscosity is set. */
+int stokes3d_apply_operator(stokes3d_ctx *ctx, const void *vx, const void *vy, const void *vz, const void *p,
+                            void *out_x, void *out_y, void *out_z);
+
+/* Smooth M v = f - G p in place on (vx, vy, vz) (p may be NULL).  Fused
+ * Jacobi, or RAS-Jacobi on 3D tiles with the window of each tile in shared
+ * memory: STOKES_ERR_ARG when that window does not fit. */
+int stokes3d_smooth(stokes3d_ctx *ctx, void *vx, void *vy, void *vz, const void *p,
+                    const stokes3d_smooth_params *params);
+
+/* The three energy sums of stokes_residual_energy_norm in 3D: sum r_v^2 /
+ * (-diag M), sum (D v)^2 eta_c / (2/hx^2 + 2/hy^2 + 2/hz^2), sum f^2 /
+ * (-diag M), accumulated in FP64 in a fixed order; synchronises. */
+int stokes3d_residual_energy_norm(stokes3d_ctx *ctx, const void *vx, const void *vy, const void *vz, const void *p,
+                                  double out[3]);
+
+/* Kernels launched by the context so far. */
+int stokes3d_kernels(const stokes3d_ctx *ctx, long long *kernels);
+
+/* Release the context.  NULL is accepted. */
+int stokes3d_destroy(stokes3d_ctx *ctx);
+
 /* Release every library-owned buffer of the context.  NULL is accepted. */
 int stokes_destroy(stokes_ctx *ctx);
 

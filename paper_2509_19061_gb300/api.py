@@ -66,6 +66,13 @@ class stokes_uzawa_params(ctypes.Structure):
                 ("lithostatic_init", ctypes.c_int), ("anderson_depth", ctypes.c_int)]
 
 
+class stokes3d_smooth_params(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("sweeps", ctypes.c_int), ("tile_i", ctypes.c_int),
+                ("tile_j", ctypes.c_int), ("tile_k", ctypes.c_int), ("k", ctypes.c_int), ("overlap", ctypes.c_int),
+                ("omega", ctypes.c_double), ("seed", ctypes.c_uint64), ("shift_mode", ctypes.c_int),
+                ("shifts", ctypes.POINTER(ctypes.c_int32))]
+
+
 _VP, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
 _SIGS = {
     "stokes_create": (_I, [_I, _I, _D, _D, _I, _VP, ctypes.POINTER(_VP)]),
@@ -108,6 +115,15 @@ _SIGS = {
     "stokes_slabs_smooth": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(stokes_smooth_params)]),
     "stokes_slabs_exchanges": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
     "stokes_slabs_destroy": (_I, [_VP]),
+    "stokes3d_create": (_I, [_I, _I, _I, _D, _D, _D, _I, _VP, ctypes.POINTER(_VP)]),
+    "stokes3d_get_layout": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t)]),
+    "stokes3d_set_viscosity": (_I, [_VP, _VP, _VP, _VP, _VP]),
+    "stokes3d_set_rhs": (_I, [_VP, _VP, _VP, _VP]),
+    "stokes3d_apply_operator": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "stokes3d_smooth": (_I, [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(stokes3d_smooth_params)]),
+    "stokes3d_residual_energy_norm": (_I, [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(_D)]),
+    "stokes3d_kernels": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
+    "stokes3d_destroy": (_I, [_VP]),
     "stokes_destroy": (_I, [_VP]),
     "stokes_strerror": (ctypes.c_char_p, [_I]),
     "stokes_last_cuda_error": (ctypes.c_char_p, []),
@@ -399,6 +415,74 @@ def stokes_slabs_destroy(s):
         _check(_lib().stokes_slabs_destroy(s), "stokes_slabs_destroy")
 
 
+def stokes3d_create(nx, ny, nz, lx, ly, lz, dtype, cuda_stream=None):
+    out = ctypes.c_void_p()
+    stream = ctypes.c_void_p(cuda_stream) if cuda_stream else None
+    _check(_lib().stokes3d_create(nx, ny, nz, lx, ly, lz, dtype, stream, ctypes.byref(out)), "stokes3d_create")
+    return out
+
+
+def stokes3d_get_layout(ctx):
+    """(pitch, rows per plane, elements of one field buffer)."""
+    p, r, n = _I(), _I(), ctypes.c_size_t()
+    _check(_lib().stokes3d_get_layout(ctx, ctypes.byref(p), ctypes.byref(r), ctypes.byref(n)), "stokes3d_get_layout")
+    return p.value, r.value, n.value
+
+
+def stokes3d_set_viscosity(ctx, eta_c, eta_xy, eta_xz, eta_yz):
+    _check(_lib().stokes3d_set_viscosity(ctx, _ptr(eta_c), _ptr(eta_xy), _ptr(eta_xz), _ptr(eta_yz)),
+           "stokes3d_set_viscosity")
+
+
+def stokes3d_set_rhs(ctx, fx, fy, fz):
+    _check(_lib().stokes3d_set_rhs(ctx, _ptr(fx), _ptr(fy), _ptr(fz)), "stokes3d_set_rhs")
+
+
+def stokes3d_apply_operator(ctx, vx, vy, vz, p, ox, oy, oz):
+    _check(_lib().stokes3d_apply_operator(ctx, _ptr(vx), _ptr(vy), _ptr(vz), _ptr(p), _ptr(ox), _ptr(oy), _ptr(oz)),
+           "stokes3d_apply_operator")
+
+
+def smooth3d_params(variant="ras", sweeps=1, tile=(8, 8, 8), k=2, overlap=None, omega=0.3, seed=0, shift_mode=None,
+                    shifts=None):
+    """Build a stokes3d_smooth_params (overlap=None means k-1)."""
+    v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    if overlap is None:
+        overlap = max(k - 1, 0)
+    if shift_mode is None:
+        shift_mode = STOKES_SHIFT_LIST if shifts is not None else STOKES_SHIFT_SPLITMIX
+    prm = stokes3d_smooth_params(v, sweeps, tile[0], tile[1], tile[2], k, overlap, omega, seed & (2**64 - 1),
+                                 shift_mode, None)
+    if shifts is not None:
+        arr = np.ascontiguousarray(np.asarray(shifts, dtype=np.int32).reshape(-1))
+        prm._shifts_keepalive = arr
+        prm.shifts = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    return prm
+
+
+def stokes3d_smooth(ctx, vx, vy, vz, p, params):
+    _check(_lib().stokes3d_smooth(ctx, _ptr(vx), _ptr(vy), _ptr(vz), _ptr(p), ctypes.byref(params)),
+           "stokes3d_smooth")
+
+
+def stokes3d_residual_energy_norm(ctx, vx, vy, vz, p=None):
+    out = (ctypes.c_double * 3)()
+    _check(_lib().stokes3d_residual_energy_norm(ctx, _ptr(vx), _ptr(vy), _ptr(vz), _ptr(p), out),
+           "stokes3d_residual_energy_norm")
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def stokes3d_kernels(ctx):
+    k = ctypes.c_longlong()
+    _check(_lib().stokes3d_kernels(ctx, ctypes.byref(k)), "stokes3d_kernels")
+    return k.value
+
+
+def stokes3d_destroy(ctx):
+    if ctx is not None:
+        _check(_lib().stokes3d_destroy(ctx), "stokes3d_destroy")
+
+
 # --------------------------------------------------------------------------
 # convenience wrapper with torch tensors
 # --------------------------------------------------------------------------
@@ -621,3 +705,75 @@ class SlabContext:
 
     def exchanges(self):
         return stokes_slabs_exchanges(self.s)
+
+
+class Stokes3DContext:
+    """Owns a stokes3d_ctx; allocates field tensors in the library layout
+    ((nz+1) x (ny+1) x pitch) and converts from and to the natural [k][j][i]
+    staggered shapes."""
+
+    def __init__(self, nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, dtype="f64", device="cuda", stream=None):
+        import torch
+        self.torch = torch
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.lx, self.ly, self.lz = lx, ly, lz
+        self.dtype_code = STOKES_F64 if dtype in ("f64", "float64", torch.float64) else STOKES_F32
+        self.tdtype = torch.float64 if self.dtype_code == STOKES_F64 else torch.float32
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.ctx = stokes3d_create(nx, ny, nz, lx, ly, lz, self.dtype_code, self.stream.cuda_stream)
+        self.pitch, _, self.alloc = stokes3d_get_layout(self.ctx)
+        self.shape = {"vx": (nz, ny, nx + 1), "vy": (nz, ny + 1, nx), "vz": (nz + 1, ny, nx), "p": (nz, ny, nx),
+                      "eta_c": (nz, ny, nx), "eta_xy": (nz, ny + 1, nx + 1), "eta_xz": (nz + 1, ny, nx + 1),
+                      "eta_yz": (nz + 1, ny + 1, nx)}
+        for a, b in (("fx", "vx"), ("fy", "vy"), ("fz", "vz")):
+            self.shape[a] = self.shape[b]
+
+    def close(self):
+        if self.ctx is not None:
+            stokes3d_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def field(self):
+        return self.torch.zeros((self.nz + 1, self.ny + 1, self.pitch), dtype=self.tdtype, device=self.device)
+
+    def pack(self, arr, name):
+        r = self.shape[name]
+        a = np.asarray(arr)
+        assert a.shape == r, "%s: expected %s, got %s" % (name, r, a.shape)
+        host = self.torch.zeros((self.nz + 1, self.ny + 1, self.pitch), dtype=self.tdtype)
+        host[:r[0], :r[1], :r[2]] = self.torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(self.tdtype)
+        return host.to(self.device)
+
+    def unpack(self, t, name):
+        r = self.shape[name]
+        return t[:r[0], :r[1], :r[2]].double().cpu().numpy()
+
+    def set_problem(self, prob):
+        stokes3d_set_viscosity(self.ctx, self.pack(prob.eta_c, "eta_c"), self.pack(prob.eta_xy, "eta_xy"),
+                               self.pack(prob.eta_xz, "eta_xz"), self.pack(prob.eta_yz, "eta_yz"))
+        stokes3d_set_rhs(self.ctx, self.pack(prob.fx, "fx"), self.pack(prob.fy, "fy"), self.pack(prob.fz, "fz"))
+
+    def set_viscosity(self, eta_c, eta_xy, eta_xz, eta_yz):
+        stokes3d_set_viscosity(self.ctx, self.pack(eta_c, "eta_c"), self.pack(eta_xy, "eta_xy"),
+                               self.pack(eta_xz, "eta_xz"), self.pack(eta_yz, "eta_yz"))
+
+    def apply(self, vx, vy, vz, p=None):
+        out = (self.field(), self.field(), self.field())
+        stokes3d_apply_operator(self.ctx, vx, vy, vz, p, *out)
+        return out
+
+    def smooth(self, vx, vy, vz, p=None, **kw):
+        stokes3d_smooth(self.ctx, vx, vy, vz, p, smooth3d_params(**kw))
+
+    def energy(self, vx, vy, vz, p=None):
+        return stokes3d_residual_energy_norm(self.ctx, vx, vy, vz, p)
+
+    def kernels(self):
+        return stokes3d_kernels(self.ctx)
