@@ -216,6 +216,36 @@ def cpu_sample(args, target_s):
             "seconds": dt}
 
 
+def cpu_sample_all_cores(args, target_s, reps=5):
+    """The OpenMP build of the same oracle source (the tiles of an outer
+    iteration in parallel) on every host core: the same RAS sample as
+    cpu_sample, `reps` repetitions of about target_s / reps seconds each;
+    median and the range of the repetitions."""
+    import oracle as ora
+    from paper_2509_19061_gb300 import inputs
+    n = 1024
+    prob = inputs.layered_sinker(n, seed=4)
+    g = ora.Grid(n, n, prob.hx, prob.hy, prob.eta_c, prob.eta_n)
+    bx, by = ora.rhs(g, prob.fx, prob.fy, None)
+    k = args.k
+    o = args.overlap if args.overlap is not None else k - 1
+    t0 = time.perf_counter()
+    ora.ras_all_cores(g, bx, by, 0.3, k, args.tile[0], args.tile[1], k, o, shift_mode=1, seed=1)
+    t_one = max(time.perf_counter() - t0, 1e-3)
+    sweeps = max(1, int(target_s / reps / t_one)) * k
+    vals = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        ora.ras_all_cores(g, bx, by, 0.3, sweeps, args.tile[0], args.tile[1], k, o, shift_mode=1, seed=1)
+        vals.append(n * n * sweeps / (time.perf_counter() - t0) / 1e9)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": statistics.median(vals), "unit": UNIT, "cores": cores, "kind": "oracle (OpenMP build)",
+            "range": [min(vals), max(vals)], "reps": reps,
+            "sample": "FP64 C oracle built with OpenMP, %d threads, layered sinker %dx%d, RAS %dx%d tiles k=%d "
+                      "overlap=%d, %d sweeps per repetition" % (cores, n, n, args.tile[0], args.tile[1], k, o,
+                                                                sweeps)}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -429,6 +459,7 @@ def run_ours(args):
         line["smooth3d"] = smooth3d_leg(args, api)
         line["global_smoothers"] = smoothers_leg(args, api)
         line["cpu_baseline"] = {kk: vv for kk, vv in cpu_sample(args, args.cpu_seconds).items() if kk != "seconds"}
+        line["cpu_baseline"]["all_cores"] = cpu_sample_all_cores(args, args.cpu_seconds / 2)
     ctx.close()
     if rank == 0:
         print(json.dumps(line))

@@ -16,6 +16,19 @@ LIB = os.path.join(HERE, "libstokes_oracle.so")
 CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-Wall", "-Wextra"]
 
 
+LIB_OMP = os.path.join(HERE, "libstokes_oracle_omp.so")
+
+
+def build_oracle_omp(force: bool = False) -> str:
+    """The same sources built with OpenMP (the RAS tiles of one outer
+    iteration run in parallel); used only for the all-cores CPU baseline."""
+    if force or not os.path.exists(LIB_OMP) or os.path.getmtime(LIB_OMP) < max(os.path.getmtime(s) for s in SRCS):
+        tmp = LIB_OMP + ".tmp.%d" % os.getpid()
+        subprocess.run(["gcc", *CFLAGS, "-fopenmp", "-o", tmp, *SRCS, "-lm"], check=True)
+        os.replace(tmp, LIB_OMP)
+    return LIB_OMP
+
+
 def build_oracle(force: bool = False) -> str:
     """Compile the oracle if the library is missing or older than its source."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(s) for s in SRCS):

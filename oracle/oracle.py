@@ -46,17 +46,23 @@ _SIGS = {
 }
 
 
+def _bind(h):
+    for name, (res, args) in _SIGS.items():
+        f = getattr(h, name)
+        f.restype = res
+        f.argtypes = args
+    return h
+
+
 def lib():
     """Load (building first if needed) the oracle shared library."""
     global _lib
     if _lib is None:
-        h = ctypes.CDLL(build_oracle())
-        for name, (res, args) in _SIGS.items():
-            f = getattr(h, name)
-            f.restype = res
-            f.argtypes = args
-        _lib = h
+        _lib = _bind(ctypes.CDLL(build_oracle()))
     return _lib
+
+
+
 
 
 def _p(a):
@@ -452,3 +458,22 @@ def mg_refine(g: Grid, fx, fy, p, mg: MG, tol, max_cycles, inner_its, vx=None, v
         vx = vx + ex
         vy = vy + ey
         cycles += inner_its
+
+
+_lib_omp = None
+
+
+def ras_all_cores(g: Grid, bx, by, omega, sweeps, ti, tj, k, overlap, shift_mode=1, seed=0):
+    """ras() from the OpenMP build of the same source (the tiles of an outer
+    iteration in parallel on every core the OpenMP runtime is given); the
+    same result as ras().  For the all-cores CPU baseline only."""
+    global _lib_omp
+    if _lib_omp is None:
+        from .build import build_oracle_omp
+        _lib_omp = _bind(ctypes.CDLL(build_oracle_omp()))
+    vx, vy = g.zeros_vx(), g.zeros_vy()
+    st = _lib_omp.ora_ras(*g.head, _p(_f64(bx)), _p(_f64(by)), omega, sweeps, ti, tj, k, overlap, shift_mode,
+                          seed & (2**64 - 1), None, 0, _p(vx), _p(vy), None)
+    if st != 0:
+        raise ValueError("ora_ras: bad arguments")
+    return vx, vy

@@ -349,56 +349,66 @@ static int ras_outer(const grid_t *g, const double *bx, const double *by, double
             int tmp = order[t]; order[t] = order[r]; order[r] = tmp;
         }
 
-    double *wx = malloc(nvx(g) * sizeof(double)), *wy = malloc(nvy(g) * sizeof(double));
-    double *tx = malloc(nvx(g) * sizeof(double)), *ty = malloc(nvy(g) * sizeof(double));
-    memcpy(wx, sx, nvx(g) * sizeof(double));
-    memcpy(wy, sy, nvy(g) * sizeof(double));
-    memcpy(tx, sx, nvx(g) * sizeof(double));
-    memcpy(ty, sy, nvy(g) * sizeof(double));
-
-    for (int q = 0; q < ntiles; ++q) {
-        int tid = order[q];
-        int bxi = tid % ntx, byj = tid / ntx;
-        int x0 = cx[bxi], x1 = cx[bxi + 1], y0 = cy[byj], y1 = cy[byj + 1];
-        /* local problem: cells of the tile grown by `overlap`, clipped */
-        int lx0 = x0 - overlap < 0 ? 0 : x0 - overlap;
-        int lx1 = x1 + overlap > nx ? nx : x1 + overlap;
-        int ly0 = y0 - overlap < 0 ? 0 : y0 - overlap;
-        int ly1 = y1 + overlap > ny ? ny : y1 + overlap;
-        /* k local Jacobi sweeps; w holds the local iterate, everything outside
-         * the local problem stays at the snapshot (Dirichlet) */
-        for (int s = 0; s < ksweeps; ++s) {
-            for (int j = ly0; j < ly1; ++j)
-                for (int i = lx0; i < lx1; ++i) {
-                    if (is_vx_unknown(g, j, i)) VX(tx, j, i) = jacobi_x(g, wx, wy, bx, omega, j, i);
-                    if (is_vy_unknown(g, j, i)) VY(ty, j, i) = jacobi_y(g, wx, wy, by, omega, j, i);
+    /* The tiles are independent (each reads the snapshot and writes only the
+     * unknowns it owns), so an OpenMP build runs them in parallel, each
+     * thread with its own work copies; the plain build runs them in order. */
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+    {
+        double *wx = malloc(nvx(g) * sizeof(double)), *wy = malloc(nvy(g) * sizeof(double));
+        double *tx = malloc(nvx(g) * sizeof(double)), *ty = malloc(nvy(g) * sizeof(double));
+        memcpy(wx, sx, nvx(g) * sizeof(double));
+        memcpy(wy, sy, nvy(g) * sizeof(double));
+        memcpy(tx, sx, nvx(g) * sizeof(double));
+        memcpy(ty, sy, nvy(g) * sizeof(double));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int q = 0; q < ntiles; ++q) {
+            int tid = order[q];
+            int bxi = tid % ntx, byj = tid / ntx;
+            int x0 = cx[bxi], x1 = cx[bxi + 1], y0 = cy[byj], y1 = cy[byj + 1];
+            /* local problem: cells of the tile grown by `overlap`, clipped */
+            int lx0 = x0 - overlap < 0 ? 0 : x0 - overlap;
+            int lx1 = x1 + overlap > nx ? nx : x1 + overlap;
+            int ly0 = y0 - overlap < 0 ? 0 : y0 - overlap;
+            int ly1 = y1 + overlap > ny ? ny : y1 + overlap;
+            /* k local Jacobi sweeps; w holds the local iterate, everything
+             * outside the local problem stays at the snapshot (Dirichlet) */
+            for (int s = 0; s < ksweeps; ++s) {
+                for (int j = ly0; j < ly1; ++j)
+                    for (int i = lx0; i < lx1; ++i) {
+                        if (is_vx_unknown(g, j, i)) VX(tx, j, i) = jacobi_x(g, wx, wy, bx, omega, j, i);
+                        if (is_vy_unknown(g, j, i)) VY(ty, j, i) = jacobi_y(g, wx, wy, by, omega, j, i);
+                    }
+                for (int j = ly0; j < ly1; ++j)
+                    for (int i = lx0; i < lx1; ++i) {
+                        if (is_vx_unknown(g, j, i)) VX(wx, j, i) = VX(tx, j, i);
+                        if (is_vy_unknown(g, j, i)) VY(wy, j, i) = VY(ty, j, i);
+                    }
+            }
+            /* keep only the unknowns owned by the tile's own cells */
+            for (int j = y0; j < y1; ++j)
+                for (int i = x0; i < x1; ++i) {
+                    if (is_vx_unknown(g, j, i)) {
+                        VX(ox, j, i) = VX(wx, j, i);
+                        if (count_x) VX(count_x, j, i) += 1;
+                    }
+                    if (is_vy_unknown(g, j, i)) {
+                        VY(oy, j, i) = VY(wy, j, i);
+                        if (count_y) VY(count_y, j, i) += 1;
+                    }
                 }
+            /* restore the snapshot in the local region */
             for (int j = ly0; j < ly1; ++j)
                 for (int i = lx0; i < lx1; ++i) {
-                    if (is_vx_unknown(g, j, i)) VX(wx, j, i) = VX(tx, j, i);
-                    if (is_vy_unknown(g, j, i)) VY(wy, j, i) = VY(ty, j, i);
+                    if (is_vx_unknown(g, j, i)) VX(wx, j, i) = VX(tx, j, i) = VX(sx, j, i);
+                    if (is_vy_unknown(g, j, i)) VY(wy, j, i) = VY(ty, j, i) = VY(sy, j, i);
                 }
         }
-        /* keep only the unknowns owned by the tile's own cells */
-        for (int j = y0; j < y1; ++j)
-            for (int i = x0; i < x1; ++i) {
-                if (is_vx_unknown(g, j, i)) {
-                    VX(ox, j, i) = VX(wx, j, i);
-                    if (count_x) VX(count_x, j, i) += 1;
-                }
-                if (is_vy_unknown(g, j, i)) {
-                    VY(oy, j, i) = VY(wy, j, i);
-                    if (count_y) VY(count_y, j, i) += 1;
-                }
-            }
-        /* restore the snapshot in the local region */
-        for (int j = ly0; j < ly1; ++j)
-            for (int i = lx0; i < lx1; ++i) {
-                if (is_vx_unknown(g, j, i)) VX(wx, j, i) = VX(tx, j, i) = VX(sx, j, i);
-                if (is_vy_unknown(g, j, i)) VY(wy, j, i) = VY(ty, j, i) = VY(sy, j, i);
-            }
+        free(wx); free(wy); free(tx); free(ty);
     }
-    free(wx); free(wy); free(tx); free(ty);
     free(order); free(cx); free(cy);
     return 0;
 }

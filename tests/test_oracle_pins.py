@@ -870,3 +870,15 @@ def test_refinement_around_inner_cg_reaches_the_dense_solution(ora):
     a = ora.mg_refine(g, prob.fx, prob.fy, None, mg, 0.0, 6, 6)
     b = ora.mg_fcg(g, prob.fx, prob.fy, None, mg, 0.0, 6)
     np.testing.assert_allclose(a[0], b[0], rtol=0, atol=1e-12 * np.abs(b[0]).max())
+
+
+def test_ras_openmp_build_equals_the_plain_oracle(ora):
+    """The OpenMP build of the oracle (tiles of an outer iteration in
+    parallel, each thread with its own work copies) gives the plain oracle's
+    result bit for bit."""
+    prob = inputs.sinker_problem(70, 50, eta_in=1e3, lx=1.0, ly=0.7)
+    g = grid_from(ora, prob)
+    bx, by = ora.rhs(g, prob.fx, prob.fy, None)
+    a = ora.ras(g, bx, by, 0.3, 9, 12, 8, 4, 1, shift_mode=1, seed=5)
+    b = ora.ras_all_cores(g, bx, by, 0.3, 9, 12, 8, 4, 1, shift_mode=1, seed=5)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
