@@ -30,6 +30,7 @@
 //  k_ras      general kernel for windows too large for the register layout:
 //             every field of the window lives in shared memory.
 #include <algorithm>
+#include <type_traits>
 #include <cstring>
 
 #include "internal.h"
@@ -507,11 +508,13 @@ __device__ __forceinline__ f2 east_pair(f2 a) { return pk(f2hi(a), __shfl_down_s
 constexpr int PR = 4;          // rows per lane
 constexpr int PAIR_COLS = 64;  // window columns of one warp
 constexpr int PAIR_EDGE_KINDS = 4; // first-row vx, first-row vy, last-row vx, last-row vy
+// edge rows per kind and buffer of a kernel of at most maxt threads: its
+// strips plus the two zero strips -1 and ns
+__host__ __device__ constexpr int pair_edge_stride(int maxt) { return maxt / 32 + 2; }
 
 struct PairCells {
     f2 vx[PR], vy[PR], ax[PR], ay[PR], en[PR], bx[PR], by[PR], wx[PR], wy[PR];
     f2 en_below, ay_above; // eta_n of the next strip's first row, ay of the previous strip's last row
-    unsigned ux, uy;       // bit 2 r + h: cell (row r, column c0 + h) is a vx / vy unknown inside the ring
 };
 
 // fluxes of one row pair
@@ -560,35 +563,41 @@ __device__ __forceinline__ void pair_setup(const RasArgs<float> &a, const Window
 {
     const GridDesc<float> &g = a.g;
     const int c0 = 2 * lane;
-    c.ux = 0;
-    c.uy = 0;
+    // Columns inside the window (the others read as zero) and inside its
+    // ring (updated).  Row tests are the same for the whole warp.  A cell
+    // inside the ring that is not an unknown (a wall, or outside the domain)
+    // gets the weight omega x 0 = 0 from its staged 1/diag, which is zero
+    // there (written so on the walls, zero-filled outside each array), so
+    // no per-cell unknown test is needed.
+    const bool in0 = c0 < w.WX, in1 = c0 + 1 < w.WX;
+    const bool up0 = c0 >= 1 && c0 < w.WX - 1, up1 = c0 + 1 < w.WX - 1;
 #pragma unroll
     for (int r = 0; r < PR; ++r) {
         const int wy = strip * PR + r;
-        const PairCell p0 = pair_cell(a, w, wy, c0, ld), p1 = pair_cell(a, w, wy, c0 + 1, ld);
-        c.vx[r] = pk(p0.vx, p1.vx);
-        c.vy[r] = pk(p0.vy, p1.vy);
-        c.ax[r] = pk(coef_x(g, p0.ec), coef_x(g, p1.ec));
-        c.ay[r] = SQ ? c.ax[r] : pk(coef_y(g, p0.ec), coef_y(g, p1.ec));
-        c.en[r] = pk(p0.en, p1.en);
-        c.bx[r] = pk(p0.bx, p1.bx);
-        c.by[r] = pk(p0.by, p1.by);
-        c.wx[r] = pk(p0.wx, p1.wx);
-        c.wy[r] = pk(p0.wy, p1.wy);
-        c.ux |= (p0.ux ? 1u : 0u) << (2 * r) | (p1.ux ? 1u : 0u) << (2 * r + 1);
-        c.uy |= (p0.uy ? 1u : 0u) << (2 * r) | (p1.uy ? 1u : 0u) << (2 * r + 1);
+        const bool row_in = wy < w.WY, row_up = wy >= 1 && wy < w.WY - 1;
+        float v0[8], v1[8];
+#pragma unroll
+        for (int f = 0; f < 8; ++f) {
+            v0[f] = row_in && in0 ? ld(f, wy, c0) : 0.f;
+            v1[f] = row_in && in1 ? ld(f, wy, c0 + 1) : 0.f;
+        }
+        c.vx[r] = pk(v0[0], v1[0]);
+        c.vy[r] = pk(v0[1], v1[1]);
+        c.ax[r] = pk(coef_x(g, v0[2]), coef_x(g, v1[2]));
+        c.ay[r] = SQ ? c.ax[r] : pk(coef_y(g, v0[2]), coef_y(g, v1[2]));
+        c.en[r] = pk(v0[3], v1[3]);
+        c.bx[r] = pk(v0[4], v1[4]);
+        c.by[r] = pk(v0[5], v1[5]);
+        c.wx[r] = pk(row_up && up0 ? jacobi_weight(a.omega, v0[6]) : 0.f,
+                     row_up && up1 ? jacobi_weight(a.omega, v1[6]) : 0.f);
+        c.wy[r] = pk(row_up && up0 ? jacobi_weight(a.omega, v0[7]) : 0.f,
+                     row_up && up1 ? jacobi_weight(a.omega, v1[7]) : 0.f);
     }
     // eta_c of the row above the strip and eta_n of the row below it
     const int above = strip * PR - 1, below = strip * PR + PR;
-    float ea[2], nb[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const bool col_in = c0 + h < w.WX;
-        ea[h] = col_in && above >= 0 ? ld(2, above, c0 + h) : 0.f;
-        nb[h] = col_in && below < w.WY ? ld(3, below, c0 + h) : 0.f;
-    }
-    c.ay_above = pk(coef_y(g, ea[0]), coef_y(g, ea[1]));
-    c.en_below = pk(nb[0], nb[1]);
+    const bool ab = above >= 0, be = below < w.WY;
+    c.ay_above = pk(coef_y(g, ab && in0 ? ld(2, above, c0) : 0.f), coef_y(g, ab && in1 ? ld(2, above, c0 + 1) : 0.f));
+    c.en_below = pk(be && in0 ? ld(3, below, c0) : 0.f, be && in1 ? ld(3, below, c0 + 1) : 0.f);
 }
 
 // fluxes of row r: Txx, Tyy, Sx, Sy (vy_n: the vy pair of the row below r,
@@ -606,28 +615,30 @@ __device__ __forceinline__ PairFlux pair_flux(f2 ax, f2 ay, f2 en, f2 vx, f2 vy,
 }
 
 // ks local sweeps of the window in registers, then the write-back of the
-// tile's own unknowns.  Ends with a barrier.  edge: [buffer][kind][strip + 1]
-// [lane] pairs, strips -1 and ns all zero.
-template <bool SQ>
+// tile's own cells.  Ends with a barrier.  Edge rows: own = this lane's entry
+// of its strip in buffer 0, kind 0; kind k of buffer b sits (4 b + k) ES 32
+// pairs further and the strips above and below 32 pairs before and after
+// (strips -1 and ns all zero).  ES is the kernel's maximum strips + 2, so
+// every edge address is the lane's pointer plus a constant.
+template <bool SQ, int ES>
 __device__ __forceinline__ void pair_sweeps(const RasArgs<float> &a, const Window &w, PairCells &c, int lane, int strip,
-                                            f2 *edge, int es)
+                                            f2 *own)
 {
     const GridDesc<float> &g = a.g;
     const f2 ihx = pk(g.ihx, g.ihx), ihy = pk(g.ihy, g.ihy);
-    auto E = [&](int buf, int kind, int s) -> f2 & {
-        return edge[((buf * PAIR_EDGE_KINDS + kind) * es + s + 1) * 32 + lane];
-    };
-    for (int s = 1; s <= a.ks; ++s) {
-        const int rb = (s - 1) & 1, wb = rb ^ 1;
-        const f2 vx_above = E(rb, 2, strip - 1), vy_above = E(rb, 3, strip - 1);
-        const f2 vx_below = E(rb, 0, strip + 1), vy_below = E(rb, 1, strip + 1);
+    constexpr int KS = ES * 32;
+    // one sweep reading edge buffer RB and writing the other one
+    auto sweep = [&](auto rbc) {
+        constexpr int RB = decltype(rbc)::value, WB = RB ^ 1;
+        const f2 vx_above = own[(RB * PAIR_EDGE_KINDS + 2) * KS - 32], vy_above = own[(RB * PAIR_EDGE_KINDS + 3) * KS - 32];
+        const f2 vx_below = own[(RB * PAIR_EDGE_KINDS + 0) * KS + 32], vy_below = own[(RB * PAIR_EDGE_KINDS + 1) * KS + 32];
         // Tyy of the row above the strip and Sx of the row below it
         const f2 tyy_above = mul2r(c.ay_above, sub2(c.vy[0], vy_above));
         const f2 sh_below = mul2(c.en_below, fma2(sub2(vx_below, c.vx[PR - 1]), ihy,
                                                   mul2(sub2(vy_below, west_pair(vy_below)), ihx)));
         const f2 sx_below = mul2r(sh_below, ihy);
         PairFlux F0 = pair_flux<SQ>(c.ax[0], c.ay[0], c.en[0], c.vx[0], c.vy[0], PR > 1 ? c.vy[1] : vy_below, vx_above,
-                                ihx, ihy);
+                                    ihx, ihy);
         f2 tyy_s = tyy_above;
 #pragma unroll
         for (int r = 0; r < PR; ++r) {
@@ -635,7 +646,7 @@ __device__ __forceinline__ void pair_sweeps(const RasArgs<float> &a, const Windo
             PairFlux F1 = F0;
             if (r + 1 < PR)
                 F1 = pair_flux<SQ>(c.ax[r + 1], c.ay[r + 1], c.en[r + 1], c.vx[r + 1], c.vy[r + 1],
-                               r + 2 < PR ? c.vy[r + 2] : vy_below, c.vx[r], ihx, ihy);
+                                   r + 2 < PR ? c.vy[r + 2] : vy_below, c.vx[r], ihx, ihy);
             const f2 sx_n = r + 1 < PR ? F1.sx : sx_below;
             const f2 mx = add2(sub2(F0.txx, west_pair(F0.txx)), sub2(sx_n, F0.sx));
             const f2 my = add2(sub2(east_pair(F0.sy), F0.sy), sub2(F0.tyy, tyy_s));
@@ -644,26 +655,39 @@ __device__ __forceinline__ void pair_sweeps(const RasArgs<float> &a, const Windo
             tyy_s = F0.tyy;
             F0 = F1;
         }
-        E(wb, 0, strip) = c.vx[0];
-        E(wb, 1, strip) = c.vy[0];
-        E(wb, 2, strip) = c.vx[PR - 1];
-        E(wb, 3, strip) = c.vy[PR - 1];
+        own[(WB * PAIR_EDGE_KINDS + 0) * KS] = c.vx[0];
+        own[(WB * PAIR_EDGE_KINDS + 1) * KS] = c.vy[0];
+        own[(WB * PAIR_EDGE_KINDS + 2) * KS] = c.vx[PR - 1];
+        own[(WB * PAIR_EDGE_KINDS + 3) * KS] = c.vy[PR - 1];
         __syncthreads();
+    };
+    // sweep s (from 1) reads buffer (s - 1) mod 2
+    int s = 0;
+    for (; s + 2 <= a.ks; s += 2) {
+        sweep(std::integral_constant<int, 0>());
+        sweep(std::integral_constant<int, 1>());
     }
-    // ---- write back the unknowns of the tile's own cells
-    const size_t P = (size_t)g.pitch;
+    if (s < a.ks) sweep(std::integral_constant<int, 0>());
+    // ---- write back the tile's own cells.  Both components of every owned
+    // cell are stored: the cells a sweep does not update (walls) keep their
+    // staged value, which is the value already there (the walls of both
+    // buffers of a ping-pong pair are the same), and an owned cell lies
+    // inside both arrays' extents.
+    const long long P = (long long)g.pitch;
+    const int gx0 = w.ox0 + 2 * lane;
+    const bool own0 = gx0 >= w.x0 && gx0 < w.x1, own1 = gx0 + 1 >= w.x0 && gx0 + 1 < w.x1;
 #pragma unroll
     for (int r = 0; r < PR; ++r) {
         const int gy = w.oy0 + strip * PR + r;
         if (gy < w.y0 || gy >= w.y1) continue;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int gx = w.ox0 + 2 * lane + h;
-            if (gx < w.x0 || gx >= w.x1) continue;
-            const size_t q = (size_t)gy * P + (size_t)gx;
-            const unsigned bit = 1u << (2 * r + h);
-            if (c.ux & bit) a.ox[q] = h ? f2hi(c.vx[r]) : f2lo(c.vx[r]);
-            if (c.uy & bit) a.oy[q] = h ? f2hi(c.vy[r]) : f2lo(c.vy[r]);
+        const long long q = (long long)gy * P + gx0;
+        if (own0) {
+            a.ox[q] = f2lo(c.vx[r]);
+            a.oy[q] = f2lo(c.vy[r]);
+        }
+        if (own1) {
+            a.ox[q + 1] = f2hi(c.vx[r]);
+            a.oy[q + 1] = f2hi(c.vy[r]);
         }
     }
 }
@@ -683,12 +707,13 @@ __global__ void __launch_bounds__(MAXT, 1) k_ras_pair(const __grid_constant__ Tm
     const uint32_t off = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
     float *const stage0 = reinterpret_cast<float *>(smem_raw + off);
     const int BW = a.bw, SP = a.stage;
-    const int es = a.strips + 2;
+    constexpr int ES = pair_edge_stride(MAXT);
     f2 *const edge = reinterpret_cast<f2 *>(stage0 + NST * NF * SP);
     const int ntiles = a.tg.ntx * a.tg.nty;
     const int grid = (int)gridDim.x;
     const int lane = (int)threadIdx.x & 31, strip = (int)threadIdx.x >> 5;
     const uint32_t box_bytes = (uint32_t)(BW * a.wym * (int)sizeof(float));
+    f2 *const own = edge + (strip + 1) * 32 + lane;
 
     auto issue = [&](int tile, int j) {
         const Window w = window_of(a, tile);
@@ -706,7 +731,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_ras_pair(const __grid_constant__ Tm
         fence_proxy_async();
     }
     // edge rows of the missing strips -1 and ns stay zero (the window's zero border)
-    for (int t = (int)threadIdx.x; t < 2 * PAIR_EDGE_KINDS * es * 32; t += (int)blockDim.x) edge[t].u = 0ull;
+    for (int t = (int)threadIdx.x; t < 2 * PAIR_EDGE_KINDS * ES * 32; t += (int)blockDim.x) edge[t].u = 0ull;
     __syncthreads();
     int tile = blockIdx.x;
     if (threadIdx.x == 0) {
@@ -717,8 +742,23 @@ __global__ void __launch_bounds__(MAXT, 1) k_ras_pair(const __grid_constant__ Tm
     uint32_t phases = 0; // bit j: parity of the next completion of bar[j]
     int j = 0;           // staging buffer of `tile`
     while (tile < ntiles) {
+        // Each thread waits for the window itself and goes on to its setup: a
+        // warp that finished the previous tile's write-back early overlaps its
+        // staged reads with the other warps' stores.  The edge rows it writes
+        // are no longer read (the last sweep ended with a barrier).  The
+        // threads agree on a timeout at the barrier after the setup; values
+        // read from a window whose copy had not landed are then discarded.
         const bool ok = mbar_wait_bounded(&bar[j], (phases >> j) & 1u, a.wait_limit);
-        if (!__syncthreads_and(ok)) {
+        const float *const stage = stage0 + j * NF * SP;
+        const Window w = window_of(a, tile);
+        const int dx = w.ox0 - (w.ox0 & ~(ALIGN - 1));
+        PairCells c;
+        pair_setup<SQ>(a, w, c, lane, strip, [&](int f, int wy, int wx) { return stage[f * SP + wy * BW + wx + dx]; });
+        own[0 * ES * 32] = c.vx[0];
+        own[1 * ES * 32] = c.vy[0];
+        own[2 * ES * 32] = c.vx[PR - 1];
+        own[3 * ES * 32] = c.vy[PR - 1];
+        if (!__syncthreads_and(ok)) { // staging buffer j consumed, edge rows visible
             // give up: record the timeout, let every copy in flight land, leave
             if (threadIdx.x == 0) {
                 atomicExch(a.status, 1);
@@ -731,20 +771,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_ras_pair(const __grid_constant__ Tm
             __syncthreads();
             return;
         }
-        const float *const stage = stage0 + j * NF * SP;
-        const Window w = window_of(a, tile);
-        const int dx = w.ox0 - (w.ox0 & ~(ALIGN - 1));
-        PairCells c;
-        pair_setup<SQ>(a, w, c, lane, strip, [&](int f, int wy, int wx) { return stage[f * SP + wy * BW + wx + dx]; });
-        edge[((0 * PAIR_EDGE_KINDS + 0) * es + strip + 1) * 32 + lane] = c.vx[0];
-        edge[((0 * PAIR_EDGE_KINDS + 1) * es + strip + 1) * 32 + lane] = c.vy[0];
-        edge[((0 * PAIR_EDGE_KINDS + 2) * es + strip + 1) * 32 + lane] = c.vx[PR - 1];
-        edge[((0 * PAIR_EDGE_KINDS + 3) * es + strip + 1) * 32 + lane] = c.vy[PR - 1];
-        __syncthreads(); // staging buffer j consumed, edge rows visible
         const int refill = tile + NST * grid;
         if (threadIdx.x == 0 && refill < ntiles) issue(refill, j);
         phases ^= 1u << j;
-        pair_sweeps<SQ>(a, w, c, lane, strip, edge, es);
+        pair_sweeps<SQ, ES>(a, w, c, lane, strip, own);
         tile += grid;
         j = NST > 1 ? (j + 1) % NST : 0;
     }
@@ -991,10 +1021,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_ras_batched_pair(const BatchTiles<f
     const uint32_t off = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
     float *const stage = reinterpret_cast<float *>(smem_raw + off);
     const int BW = shape.bw, SP = shape.stage;
-    const int es = shape.strips + 2;
+    constexpr int ES = pair_edge_stride(MAXT);
     f2 *const edge = reinterpret_cast<f2 *>(stage + NF * SP);
     const int lane = (int)threadIdx.x & 31, strip = (int)threadIdx.x >> 5;
     const uint32_t box_bytes = (uint32_t)(BW * shape.wym * (int)sizeof(float));
+    f2 *const own = edge + (strip + 1) * 32 + lane;
 
     constexpr int CH = 8; // chunks of consecutive tiles per CTA, as in k_ras_batched_tma
     const int stride = (int)gridDim.x * CH;
@@ -1049,21 +1080,15 @@ __global__ void __launch_bounds__(MAXT, 1) k_ras_batched_pair(const BatchTiles<f
         fence_proxy_async();
     }
     // edge rows of the missing strips -1 and ns stay zero (the window's zero border)
-    for (int t = (int)threadIdx.x; t < 2 * PAIR_EDGE_KINDS * es * 32; t += (int)blockDim.x) edge[t].u = 0ull;
+    for (int t = (int)threadIdx.x; t < 2 * PAIR_EDGE_KINDS * ES * 32; t += (int)blockDim.x) edge[t].u = 0ull;
     __syncthreads();
     int tile = advance((int)blockIdx.x * CH);
     if (threadIdx.x == 0 && tile < total) issue(tile, e, tb);
     uint32_t phase = 0;
     while (tile < total) {
+        // as in k_ras_pair: no barrier before the setup, the timeout agreed on
+        // at the barrier after it
         const bool ok = mbar_wait_bounded(&bar, phase, shape.wait_limit);
-        if (!__syncthreads_and(ok)) {
-            if (threadIdx.x == 0) {
-                atomicExch(shape.status, 1);
-                mbar_wait_bounded(&bar, phase, 4000000000LL);
-            }
-            __syncthreads();
-            return;
-        }
         if (e != ea) {
             a = batch_args(shape, tab[e]);
             ea = e;
@@ -1072,15 +1097,22 @@ __global__ void __launch_bounds__(MAXT, 1) k_ras_batched_pair(const BatchTiles<f
         const int dx = w.ox0 - (w.ox0 & ~(ALIGN - 1));
         PairCells c;
         pair_setup<SQ>(a, w, c, lane, strip, [&](int f, int wy, int wx) { return stage[f * SP + wy * BW + wx + dx]; });
-        edge[((0 * PAIR_EDGE_KINDS + 0) * es + strip + 1) * 32 + lane] = c.vx[0];
-        edge[((0 * PAIR_EDGE_KINDS + 1) * es + strip + 1) * 32 + lane] = c.vy[0];
-        edge[((0 * PAIR_EDGE_KINDS + 2) * es + strip + 1) * 32 + lane] = c.vx[PR - 1];
-        edge[((0 * PAIR_EDGE_KINDS + 3) * es + strip + 1) * 32 + lane] = c.vy[PR - 1];
-        __syncthreads(); // staging buffer consumed, edge rows visible
+        own[0 * ES * 32] = c.vx[0];
+        own[1 * ES * 32] = c.vy[0];
+        own[2 * ES * 32] = c.vx[PR - 1];
+        own[3 * ES * 32] = c.vy[PR - 1];
+        if (!__syncthreads_and(ok)) { // staging buffer consumed, edge rows visible
+            if (threadIdx.x == 0) {
+                atomicExch(shape.status, 1);
+                mbar_wait_bounded(&bar, phase, 4000000000LL);
+            }
+            __syncthreads();
+            return;
+        }
         const int next = advance(step(tile));
         if (threadIdx.x == 0 && next < total) issue(next, e, tb);
         phase ^= 1u;
-        pair_sweeps<SQ>(a, w, c, lane, strip, edge, es);
+        pair_sweeps<SQ, ES>(a, w, c, lane, strip, own);
         tile = next;
     }
 }
@@ -1252,7 +1284,8 @@ RasPlan plan_ras(int nx, int ny, int ti, int tj, int overlap, size_t elem, bool 
         // packed-pair layout: one warp per strip of PR rows, edge rows double-buffered,
         // two staging buffers when they fit
         const int strips = (p.wym + PR - 1) / PR;
-        const size_t edge = (size_t)2 * PAIR_EDGE_KINDS * (strips + 2) * 32 * sizeof(f2);
+        const int maxt = 32 * strips <= 384 ? 384 : PAIR_MAX_THREADS; // the kernel instance that runs it
+        const size_t edge = (size_t)2 * PAIR_EDGE_KINDS * pair_edge_stride(maxt) * 32 * sizeof(f2);
         const size_t one = (size_t)nf * (size_t)p.stage * elem;
         if (32 * strips <= PAIR_MAX_THREADS && one + edge + 128 <= maxs) {
             p.kind = PLAN_PAIR;
@@ -1527,7 +1560,8 @@ cudaError_t launch_ras_batched(const BatchTiles<T> *tab, const int *tmap, const 
         if (p.kind == PLAN_PAIR) {
             // one staging buffer beside the edge rows
             const size_t one = (size_t)8 * (size_t)p.stage * sizeof(float);
-            const size_t smem = one + (size_t)2 * PAIR_EDGE_KINDS * (p.strips + 2) * 32 * sizeof(f2) + 128;
+            const size_t smem =
+                one + (size_t)2 * PAIR_EDGE_KINDS * pair_edge_stride(p.threads <= 384 ? 384 : PAIR_MAX_THREADS) * 32 * sizeof(f2) + 128;
             void (*kern)(const BatchTiles<float> *, const int *, const TmaMaps *, int, int, const int *,
                          RasArgs<float>);
             if (square) kern = p.threads <= 384 ? k_ras_batched_pair<384, true> : k_ras_batched_pair<PAIR_MAX_THREADS, true>;
