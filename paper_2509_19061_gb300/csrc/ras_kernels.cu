@@ -505,7 +505,7 @@ __device__ __forceinline__ f2 mul2r(f2 a, f2 b)
 __device__ __forceinline__ f2 west_pair(f2 a) { return pk(__shfl_up_sync(0xffffffffu, f2hi(a), 1), f2lo(a)); }
 __device__ __forceinline__ f2 east_pair(f2 a) { return pk(f2hi(a), __shfl_down_sync(0xffffffffu, f2lo(a), 1)); }
 
-constexpr int PR = 4;          // rows per lane
+constexpr int PR = 5;          // rows per lane
 constexpr int PAIR_COLS = 64;  // window columns of one warp
 constexpr int PAIR_EDGE_KINDS = 4; // first-row vx, first-row vy, last-row vx, last-row vy
 // edge rows per kind and buffer of a kernel of at most maxt threads: its
@@ -557,9 +557,17 @@ __device__ __forceinline__ PairCell pair_cell(const RasArgs<float> &a, const Win
 // SQ: square cells (1/hx = 1/hy and 1/hx^2 = 1/hy^2 bit for bit), where the
 // coefficient of Tyy equals that of Txx and Sy equals Sx: the kernel keeps
 // one of each (fewer registers, one packed multiply less per row).
-template <bool SQ, class LD>
+// Staging row width of the pair kernels (elements): a 64-column window plus
+// room for the alignment shift of its first column, for every pair window,
+// so that every staged read is the lane's pointer plus a constant.
+constexpr int PAIR_BW = 68;
+
+// Registers of one strip from the staged window.  lp points at field 0, the
+// strip's first row and column 2 lane of the window; field f starts SP
+// elements after field f - 1.
+template <bool SQ>
 __device__ __forceinline__ void pair_setup(const RasArgs<float> &a, const Window &w, PairCells &c, int lane, int strip,
-                                           LD &&ld)
+                                           const float *lp, int SP)
 {
     const GridDesc<float> &g = a.g;
     const int c0 = 2 * lane;
@@ -571,33 +579,35 @@ __device__ __forceinline__ void pair_setup(const RasArgs<float> &a, const Window
     // no per-cell unknown test is needed.
     const bool in0 = c0 < w.WX, in1 = c0 + 1 < w.WX;
     const bool up0 = c0 >= 1 && c0 < w.WX - 1, up1 = c0 + 1 < w.WX - 1;
+    const f2 om = pk(a.omega, a.omega), cx = pk(g.ihx2, g.ihx2), cy = pk(g.ihy2, g.ihy2);
+    auto ld2 = [&](bool row, int f, int r) {
+        const float *p = lp + f * SP + r * PAIR_BW;
+        return pk(row && in0 ? p[0] : 0.f, row && in1 ? p[1] : 0.f);
+    };
 #pragma unroll
     for (int r = 0; r < PR; ++r) {
         const int wy = strip * PR + r;
         const bool row_in = wy < w.WY, row_up = wy >= 1 && wy < w.WY - 1;
-        float v0[8], v1[8];
+        f2 v[8];
 #pragma unroll
-        for (int f = 0; f < 8; ++f) {
-            v0[f] = row_in && in0 ? ld(f, wy, c0) : 0.f;
-            v1[f] = row_in && in1 ? ld(f, wy, c0 + 1) : 0.f;
-        }
-        c.vx[r] = pk(v0[0], v1[0]);
-        c.vy[r] = pk(v0[1], v1[1]);
-        c.ax[r] = pk(coef_x(g, v0[2]), coef_x(g, v1[2]));
-        c.ay[r] = SQ ? c.ax[r] : pk(coef_y(g, v0[2]), coef_y(g, v1[2]));
-        c.en[r] = pk(v0[3], v1[3]);
-        c.bx[r] = pk(v0[4], v1[4]);
-        c.by[r] = pk(v0[5], v1[5]);
-        c.wx[r] = pk(row_up && up0 ? jacobi_weight(a.omega, v0[6]) : 0.f,
-                     row_up && up1 ? jacobi_weight(a.omega, v1[6]) : 0.f);
-        c.wy[r] = pk(row_up && up0 ? jacobi_weight(a.omega, v0[7]) : 0.f,
-                     row_up && up1 ? jacobi_weight(a.omega, v1[7]) : 0.f);
+        for (int f = 0; f < 8; ++f) v[f] = ld2(row_in, f, r);
+        c.vx[r] = v[0];
+        c.vy[r] = v[1];
+        // coef_x, coef_y and jacobi_weight of stencil.cuh, lane for lane
+        const f2 e2 = add2(v[2], v[2]);
+        c.ax[r] = mul2(e2, cx);
+        c.ay[r] = SQ ? c.ax[r] : mul2(e2, cy);
+        c.en[r] = v[3];
+        c.bx[r] = v[4];
+        c.by[r] = v[5];
+        const f2 wx = mul2(om, v[6]), wy2 = mul2(om, v[7]);
+        c.wx[r] = pk(row_up && up0 ? f2lo(wx) : 0.f, row_up && up1 ? f2hi(wx) : 0.f);
+        c.wy[r] = pk(row_up && up0 ? f2lo(wy2) : 0.f, row_up && up1 ? f2hi(wy2) : 0.f);
     }
     // eta_c of the row above the strip and eta_n of the row below it
-    const int above = strip * PR - 1, below = strip * PR + PR;
-    const bool ab = above >= 0, be = below < w.WY;
-    c.ay_above = pk(coef_y(g, ab && in0 ? ld(2, above, c0) : 0.f), coef_y(g, ab && in1 ? ld(2, above, c0 + 1) : 0.f));
-    c.en_below = pk(be && in0 ? ld(3, below, c0) : 0.f, be && in1 ? ld(3, below, c0 + 1) : 0.f);
+    const f2 ea = ld2(strip > 0, 2, -1);
+    c.ay_above = mul2(add2(ea, ea), cy);
+    c.en_below = ld2(strip * PR + PR < w.WY, 3, PR);
 }
 
 // fluxes of row r: Txx, Tyy, Sx, Sy (vy_n: the vy pair of the row below r,
@@ -674,13 +684,12 @@ __device__ __forceinline__ void pair_sweeps(const RasArgs<float> &a, const Windo
     // buffers of a ping-pong pair are the same), and an owned cell lies
     // inside both arrays' extents.
     const long long P = (long long)g.pitch;
-    const int gx0 = w.ox0 + 2 * lane;
+    const int gx0 = w.ox0 + 2 * lane, gy0 = w.oy0 + strip * PR;
     const bool own0 = gx0 >= w.x0 && gx0 < w.x1, own1 = gx0 + 1 >= w.x0 && gx0 + 1 < w.x1;
+    long long q = (long long)gy0 * P + gx0;
 #pragma unroll
-    for (int r = 0; r < PR; ++r) {
-        const int gy = w.oy0 + strip * PR + r;
-        if (gy < w.y0 || gy >= w.y1) continue;
-        const long long q = (long long)gy * P + gx0;
+    for (int r = 0; r < PR; ++r, q += P) {
+        if (gy0 + r < w.y0 || gy0 + r >= w.y1) continue;
         if (own0) {
             a.ox[q] = f2lo(c.vx[r]);
             a.oy[q] = f2lo(c.vy[r]);
@@ -704,19 +713,21 @@ __global__ void __launch_bounds__(MAXT, 1) k_ras_pair(const __grid_constant__ Tm
     constexpr int ALIGN = 4; // TMA x coordinates are multiples of 16 bytes
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[NST];
+    __shared__ Window win[NST]; // window of the tile staged in buffer j, written by the thread that issues it
     const uint32_t off = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
     float *const stage0 = reinterpret_cast<float *>(smem_raw + off);
-    const int BW = a.bw, SP = a.stage;
+    const int SP = a.stage;
     constexpr int ES = pair_edge_stride(MAXT);
     f2 *const edge = reinterpret_cast<f2 *>(stage0 + NST * NF * SP);
     const int ntiles = a.tg.ntx * a.tg.nty;
     const int grid = (int)gridDim.x;
     const int lane = (int)threadIdx.x & 31, strip = (int)threadIdx.x >> 5;
-    const uint32_t box_bytes = (uint32_t)(BW * a.wym * (int)sizeof(float));
+    const uint32_t box_bytes = (uint32_t)(PAIR_BW * a.wym * (int)sizeof(float));
     f2 *const own = edge + (strip + 1) * 32 + lane;
 
     auto issue = [&](int tile, int j) {
         const Window w = window_of(a, tile);
+        win[j] = w;
         const int xs = w.ox0 & ~(ALIGN - 1);
         float *const st = stage0 + j * NF * SP;
         fence_proxy_async();
@@ -739,6 +750,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_ras_pair(const __grid_constant__ Tm
         for (int j = 0; j < NST; ++j)
             if (tile + j * grid < ntiles) issue(tile + j * grid, j);
     }
+    __syncthreads(); // the first windows are visible
     uint32_t phases = 0; // bit j: parity of the next completion of bar[j]
     int j = 0;           // staging buffer of `tile`
     while (tile < ntiles) {
@@ -750,10 +762,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_ras_pair(const __grid_constant__ Tm
         // read from a window whose copy had not landed are then discarded.
         const bool ok = mbar_wait_bounded(&bar[j], (phases >> j) & 1u, a.wait_limit);
         const float *const stage = stage0 + j * NF * SP;
-        const Window w = window_of(a, tile);
+        const Window w = win[j];
         const int dx = w.ox0 - (w.ox0 & ~(ALIGN - 1));
         PairCells c;
-        pair_setup<SQ>(a, w, c, lane, strip, [&](int f, int wy, int wx) { return stage[f * SP + wy * BW + wx + dx]; });
+        pair_setup<SQ>(a, w, c, lane, strip, stage + strip * PR * PAIR_BW + 2 * lane + dx, SP);
         own[0 * ES * 32] = c.vx[0];
         own[1 * ES * 32] = c.vy[0];
         own[2 * ES * 32] = c.vx[PR - 1];
@@ -1020,11 +1032,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_ras_batched_pair(const BatchTiles<f
     __shared__ __align__(8) uint64_t bar;
     const uint32_t off = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
     float *const stage = reinterpret_cast<float *>(smem_raw + off);
-    const int BW = shape.bw, SP = shape.stage;
+    const int SP = shape.stage;
     constexpr int ES = pair_edge_stride(MAXT);
     f2 *const edge = reinterpret_cast<f2 *>(stage + NF * SP);
     const int lane = (int)threadIdx.x & 31, strip = (int)threadIdx.x >> 5;
-    const uint32_t box_bytes = (uint32_t)(BW * shape.wym * (int)sizeof(float));
+    const uint32_t box_bytes = (uint32_t)(PAIR_BW * shape.wym * (int)sizeof(float));
     f2 *const own = edge + (strip + 1) * 32 + lane;
 
     constexpr int CH = 8; // chunks of consecutive tiles per CTA, as in k_ras_batched_tma
@@ -1096,7 +1108,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_ras_batched_pair(const BatchTiles<f
         const Window w = window_of(a, tile - tb);
         const int dx = w.ox0 - (w.ox0 & ~(ALIGN - 1));
         PairCells c;
-        pair_setup<SQ>(a, w, c, lane, strip, [&](int f, int wy, int wx) { return stage[f * SP + wy * BW + wx + dx]; });
+        pair_setup<SQ>(a, w, c, lane, strip, stage + strip * PR * PAIR_BW + 2 * lane + dx, SP);
         own[0 * ES * 32] = c.vx[0];
         own[1 * ES * 32] = c.vy[0];
         own[2 * ES * 32] = c.vx[PR - 1];
@@ -1249,7 +1261,8 @@ struct RasPlan {
     size_t smem;
 };
 
-constexpr int PAIR_MAX_THREADS = 640;
+constexpr int PAIR_MAX_THREADS = 512;
+constexpr int PAIR_SMALL_THREADS = 384; // the smaller pair kernel instance
 // Narrower windows leave lanes idle; up to this width the one-column kernel is
 // as fast or faster (measured at 8192^2: 40 columns 264 vs 177 Gcell/s, 48
 // columns equal)
@@ -1284,11 +1297,14 @@ RasPlan plan_ras(int nx, int ny, int ti, int tj, int overlap, size_t elem, bool 
         // packed-pair layout: one warp per strip of PR rows, edge rows double-buffered,
         // two staging buffers when they fit
         const int strips = (p.wym + PR - 1) / PR;
-        const int maxt = 32 * strips <= 384 ? 384 : PAIR_MAX_THREADS; // the kernel instance that runs it
+        const int maxt = 32 * strips <= PAIR_SMALL_THREADS ? PAIR_SMALL_THREADS : PAIR_MAX_THREADS; // the kernel instance that runs it
         const size_t edge = (size_t)2 * PAIR_EDGE_KINDS * pair_edge_stride(maxt) * 32 * sizeof(f2);
-        const size_t one = (size_t)nf * (size_t)p.stage * elem;
+        const int bw = PAIR_BW, stage = (int)((((size_t)bw * p.wym * elem + 127) / 128 * 128) / elem);
+        const size_t one = (size_t)nf * (size_t)stage * elem;
         if (32 * strips <= PAIR_MAX_THREADS && one + edge + 128 <= maxs) {
             p.kind = PLAN_PAIR;
+            p.bw = bw;
+            p.stage = stage;
             p.strips = strips;
             p.threads = 32 * strips;
             p.nstage = 2 * one + edge + 128 <= maxs ? 2 : 1;
@@ -1457,14 +1473,14 @@ cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const 
                 const bool sq = g.ihx == g.ihy && g.ihx2 == g.ihy2;
                 if (sq) {
                     if (p.nstage == 2)
-                        kern = p.threads <= 384 ? k_ras_pair<384, 2, true> : k_ras_pair<PAIR_MAX_THREADS, 2, true>;
+                        kern = p.threads <= PAIR_SMALL_THREADS ? k_ras_pair<PAIR_SMALL_THREADS, 2, true> : k_ras_pair<PAIR_MAX_THREADS, 2, true>;
                     else
-                        kern = p.threads <= 384 ? k_ras_pair<384, 1, true> : k_ras_pair<PAIR_MAX_THREADS, 1, true>;
+                        kern = p.threads <= PAIR_SMALL_THREADS ? k_ras_pair<PAIR_SMALL_THREADS, 1, true> : k_ras_pair<PAIR_MAX_THREADS, 1, true>;
                 } else {
                     if (p.nstage == 2)
-                        kern = p.threads <= 384 ? k_ras_pair<384, 2, false> : k_ras_pair<PAIR_MAX_THREADS, 2, false>;
+                        kern = p.threads <= PAIR_SMALL_THREADS ? k_ras_pair<PAIR_SMALL_THREADS, 2, false> : k_ras_pair<PAIR_MAX_THREADS, 2, false>;
                     else
-                        kern = p.threads <= 384 ? k_ras_pair<384, 1, false> : k_ras_pair<PAIR_MAX_THREADS, 1, false>;
+                        kern = p.threads <= PAIR_SMALL_THREADS ? k_ras_pair<PAIR_SMALL_THREADS, 1, false> : k_ras_pair<PAIR_MAX_THREADS, 1, false>;
                 }
             }
         }
@@ -1561,11 +1577,11 @@ cudaError_t launch_ras_batched(const BatchTiles<T> *tab, const int *tmap, const 
             // one staging buffer beside the edge rows
             const size_t one = (size_t)8 * (size_t)p.stage * sizeof(float);
             const size_t smem =
-                one + (size_t)2 * PAIR_EDGE_KINDS * pair_edge_stride(p.threads <= 384 ? 384 : PAIR_MAX_THREADS) * 32 * sizeof(f2) + 128;
+                one + (size_t)2 * PAIR_EDGE_KINDS * pair_edge_stride(p.threads <= PAIR_SMALL_THREADS ? PAIR_SMALL_THREADS : PAIR_MAX_THREADS) * 32 * sizeof(f2) + 128;
             void (*kern)(const BatchTiles<float> *, const int *, const TmaMaps *, int, int, const int *,
                          RasArgs<float>);
-            if (square) kern = p.threads <= 384 ? k_ras_batched_pair<384, true> : k_ras_batched_pair<PAIR_MAX_THREADS, true>;
-            else kern = p.threads <= 384 ? k_ras_batched_pair<384, false> : k_ras_batched_pair<PAIR_MAX_THREADS, false>;
+            if (square) kern = p.threads <= PAIR_SMALL_THREADS ? k_ras_batched_pair<PAIR_SMALL_THREADS, true> : k_ras_batched_pair<PAIR_MAX_THREADS, true>;
+            else kern = p.threads <= PAIR_SMALL_THREADS ? k_ras_batched_pair<PAIR_SMALL_THREADS, false> : k_ras_batched_pair<PAIR_MAX_THREADS, false>;
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             const int grid = std::min(total, sm_count());
