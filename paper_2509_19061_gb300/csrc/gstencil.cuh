@@ -12,7 +12,7 @@ namespace stokes {
 // eta_n and are read as zero.
 // MASK: eta_n is the caller's raw array, so boundary nodes are zeroed here
 // (the library's own copy already holds zeros there).
-template <typename T, bool MASK = false>
+template <typename T, bool MASK = false, int SQM = 2>
 __device__ __forceinline__ void op_x(const GridDesc<T> &g, const T *__restrict__ eta_c, const T *__restrict__ eta_n,
                                      const T *__restrict__ vx, const T *__restrict__ vy, int j, int i, T &m, T &d,
                                      T &vc)
@@ -28,14 +28,14 @@ __device__ __forceinline__ void op_x(const GridDesc<T> &g, const T *__restrict__
     const T enS = (MASK && j == 0) ? T(0) : eta_n[q];
     const T txx_c = flux_n(coef_x(g, ecC), vE, vc);
     const T txx_w = flux_n(coef_x(g, ecW), vc, vW);
-    const T sx_n = r_mul(shear(g, enN, vN, vc, vy[q + P], vy[q + P - 1]), g.ihy);
-    const T sx_c = r_mul(shear(g, enS, vc, vS, vy[q], vy[q - 1]), g.ihy);
+    const T sx_n = shear_x<SQM>(g, enN, vN, vc, vy[q + P], vy[q + P - 1]);
+    const T sx_c = shear_x<SQM>(g, enS, vc, vS, vy[q], vy[q - 1]);
     m = m_x(txx_c, txx_w, sx_n, sx_c);
     d = diag_x(g, ecC, ecW, enN, enS);
 }
 
 // (M v)_y and diag(M)_y at vy unknown (j, i), 1 <= j <= ny-1, 0 <= i < nx.
-template <typename T, bool MASK = false>
+template <typename T, bool MASK = false, int SQM = 2>
 __device__ __forceinline__ void op_y(const GridDesc<T> &g, const T *__restrict__ eta_c, const T *__restrict__ eta_n,
                                      const T *__restrict__ vx, const T *__restrict__ vy, int j, int i, T &m, T &d,
                                      T &vc)
@@ -51,8 +51,8 @@ __device__ __forceinline__ void op_y(const GridDesc<T> &g, const T *__restrict__
     const T enW = (MASK && i == 0) ? T(0) : eta_n[q];
     const T tyy_c = flux_n(coef_y(g, ecC), vN, vc);
     const T tyy_s = flux_n(coef_y(g, ecS), vc, vS);
-    const T sy_e = r_mul(shear(g, enE, vx[q + 1], vx[q + 1 - P], vE, vc), g.ihx);
-    const T sy_c = r_mul(shear(g, enW, vx[q], vx[q - P], vc, vW), g.ihx);
+    const T sy_e = shear_y<SQM>(g, enE, vx[q + 1], vx[q + 1 - P], vE, vc);
+    const T sy_c = shear_y<SQM>(g, enW, vx[q], vx[q - P], vc, vW);
     m = m_y(sy_e, sy_c, tyy_c, tyy_s);
     d = diag_y(g, ecC, ecS, enE, enW);
 }
@@ -133,15 +133,15 @@ __device__ __forceinline__ void flux_tile_stage(const GridDesc<T> &g, const T *_
     for (int e = tid; e < (AT_Y + 1) * (AT_X + 1); e += nt) {
         const int a = e / (AT_X + 1), b = e % (AT_X + 1);
         const int J = j0 + a, I = i0 + b;
-        T v = T(0);
+        T sx = T(0), sy = T(0);
         if (J <= g.ny && I <= g.nx) {
             const size_t q = (size_t)J * P + I;
             const T vxa = J < g.ny ? px[q] : T(0), vxb = J > 0 ? px[q - P] : T(0);
             const T vyr = I < g.nx ? py[q] : T(0), vyl = I > 0 ? py[q - 1] : T(0);
-            v = shear(g, en[q], vxa, vxb, vyr, vyl);
+            shear_xy(g, en[q], vxa, vxb, vyr, vyl, sx, sy);
         }
-        sm.sx[a][b] = r_mul(v, g.ihy);
-        sm.sy[a][b] = r_mul(v, g.ihx);
+        sm.sx[a][b] = sx;
+        sm.sy[a][b] = sy;
     }
     __syncthreads();
 }

@@ -18,6 +18,7 @@ struct GridDesc {
     T ihx2, ihy2; // 1/hx^2, 1/hy^2
     T two_ihx2, two_ihy2; // 2/hx^2, 2/hy^2
     double lap;   // 2/hx^2 + 2/hy^2 (pressure weight of the energy norm)
+    int square;   // 1/hx = 1/hy and 1/hx^2 = 1/hy^2 in T: the square-cell form of the shear fluxes
 };
 
 template <typename T>
@@ -34,6 +35,7 @@ GridDesc<T> make_grid(int nx, int ny, int pitch, double hx, double hy)
     g.two_ihx2 = g.ihx2 + g.ihx2;
     g.two_ihy2 = g.ihy2 + g.ihy2;
     g.lap = 2.0 / (hx * hx) + 2.0 / (hy * hy);
+    g.square = g.ihx == g.ihy && g.ihx2 == g.ihy2 ? 1 : 0;
     return g;
 }
 

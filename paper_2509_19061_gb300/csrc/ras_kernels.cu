@@ -267,9 +267,7 @@ __device__ __forceinline__ void cell_fluxes(const GridDesc<T> &g, const CellRegs
     const T vy_n = r < R - 1 ? c.vy[r + 1] : pl.Vy[q + SW];
     txx[r] = flux_n(c.ax[r], pl.Vx[q + 1], c.vx[r]);
     tyy[r] = flux_n(c.ay[r], vy_n, c.vy[r]);
-    const T sh = shear(g, c.en[r], c.vx[r], vx_s, c.vy[r], pl.Vy[q - 1]);
-    sx[r] = r_mul(sh, g.ihy);
-    sy[r] = r_mul(sh, g.ihx);
+    shear_xy(g, c.en[r], c.vx[r], vx_s, c.vy[r], pl.Vy[q - 1], sx[r], sy[r]);
     pl.Fxx[q] = txx[r];
     pl.Fsy[q] = sy[r];
     if (r == R - 1) pl.Fyy[q] = tyy[r];
@@ -580,6 +578,7 @@ __device__ __forceinline__ void pair_setup(const RasArgs<float> &a, const Window
     const bool in0 = c0 < w.WX, in1 = c0 + 1 < w.WX;
     const bool up0 = c0 >= 1 && c0 < w.WX - 1, up1 = c0 + 1 < w.WX - 1;
     const f2 om = pk(a.omega, a.omega), cx = pk(g.ihx2, g.ihx2), cy = pk(g.ihy2, g.ihy2);
+    const bool sqc = SQ || g.square; // the square-cell shear (per grid, also in the general form)
     auto ld2 = [&](bool row, int f, int r) {
         const float *p = lp + f * SP + r * PAIR_BW;
         return pk(row && in0 ? p[0] : 0.f, row && in1 ? p[1] : 0.f);
@@ -597,7 +596,7 @@ __device__ __forceinline__ void pair_setup(const RasArgs<float> &a, const Window
         const f2 e2 = add2(v[2], v[2]);
         c.ax[r] = mul2(e2, cx);
         c.ay[r] = SQ ? c.ax[r] : mul2(e2, cy);
-        c.en[r] = v[3];
+        c.en[r] = sqc ? mul2(v[3], cx) : v[3]; // square cells: eta_n / h^2 (shear_sq)
         c.bx[r] = v[4];
         c.by[r] = v[5];
         const f2 wx = mul2(om, v[6]), wy2 = mul2(om, v[7]);
@@ -607,20 +606,28 @@ __device__ __forceinline__ void pair_setup(const RasArgs<float> &a, const Window
     // eta_c of the row above the strip and eta_n of the row below it
     const f2 ea = ld2(strip > 0, 2, -1);
     c.ay_above = mul2(add2(ea, ea), cy);
-    c.en_below = ld2(strip * PR + PR < w.WY, 3, PR);
+    const f2 eb = ld2(strip * PR + PR < w.WY, 3, PR);
+    c.en_below = sqc ? mul2(eb, cx) : eb;
 }
 
 // fluxes of row r: Txx, Tyy, Sx, Sy (vy_n: the vy pair of the row below r,
 // vx_s: the vx pair of the row above it, both before this sweep)
 template <bool SQ>
-__device__ __forceinline__ PairFlux pair_flux(f2 ax, f2 ay, f2 en, f2 vx, f2 vy, f2 vy_n, f2 vx_s, f2 ihx, f2 ihy)
+__device__ __forceinline__ PairFlux pair_flux(f2 ax, f2 ay, f2 en, f2 vx, f2 vy, f2 vy_n, f2 vx_s, f2 ihx, f2 ihy,
+                                              bool sqc)
 {
     PairFlux F;
     F.txx = mul2r(ax, sub2(east_pair(vx), vx));
     F.tyy = mul2r(SQ ? ax : ay, sub2(vy_n, vy));
-    const f2 sh = mul2(en, fma2(sub2(vx, vx_s), ihy, mul2(sub2(vy, west_pair(vy)), ihx)));
-    F.sx = mul2r(sh, ihy);
-    F.sy = SQ ? F.sx : mul2r(sh, ihx);
+    if (SQ || sqc) {
+        // shear_sq of stencil.cuh; en holds eta_n / h^2
+        F.sx = mul2r(en, add2(sub2(vx, vx_s), sub2(vy, west_pair(vy))));
+        F.sy = F.sx;
+    } else {
+        const f2 sh = mul2(en, fma2(sub2(vx, vx_s), ihy, mul2(sub2(vy, west_pair(vy)), ihx)));
+        F.sx = mul2r(sh, ihy);
+        F.sy = mul2r(sh, ihx);
+    }
     return F;
 }
 
@@ -636,6 +643,7 @@ __device__ __forceinline__ void pair_sweeps(const RasArgs<float> &a, const Windo
 {
     const GridDesc<float> &g = a.g;
     const f2 ihx = pk(g.ihx, g.ihx), ihy = pk(g.ihy, g.ihy);
+    const bool sqc = SQ || g.square;
     constexpr int KS = ES * 32;
     // one sweep reading edge buffer RB and writing the other one
     auto sweep = [&](auto rbc) {
@@ -644,11 +652,16 @@ __device__ __forceinline__ void pair_sweeps(const RasArgs<float> &a, const Windo
         const f2 vx_below = own[(RB * PAIR_EDGE_KINDS + 0) * KS + 32], vy_below = own[(RB * PAIR_EDGE_KINDS + 1) * KS + 32];
         // Tyy of the row above the strip and Sx of the row below it
         const f2 tyy_above = mul2r(c.ay_above, sub2(c.vy[0], vy_above));
-        const f2 sh_below = mul2(c.en_below, fma2(sub2(vx_below, c.vx[PR - 1]), ihy,
-                                                  mul2(sub2(vy_below, west_pair(vy_below)), ihx)));
-        const f2 sx_below = mul2r(sh_below, ihy);
+        f2 sx_below;
+        if (sqc) {
+            sx_below = mul2r(c.en_below, add2(sub2(vx_below, c.vx[PR - 1]), sub2(vy_below, west_pair(vy_below))));
+        } else {
+            const f2 sh_below = mul2(c.en_below, fma2(sub2(vx_below, c.vx[PR - 1]), ihy,
+                                                      mul2(sub2(vy_below, west_pair(vy_below)), ihx)));
+            sx_below = mul2r(sh_below, ihy);
+        }
         PairFlux F0 = pair_flux<SQ>(c.ax[0], c.ay[0], c.en[0], c.vx[0], c.vy[0], PR > 1 ? c.vy[1] : vy_below, vx_above,
-                                    ihx, ihy);
+                                    ihx, ihy, sqc);
         f2 tyy_s = tyy_above;
 #pragma unroll
         for (int r = 0; r < PR; ++r) {
@@ -656,7 +669,7 @@ __device__ __forceinline__ void pair_sweeps(const RasArgs<float> &a, const Windo
             PairFlux F1 = F0;
             if (r + 1 < PR)
                 F1 = pair_flux<SQ>(c.ax[r + 1], c.ay[r + 1], c.en[r + 1], c.vx[r + 1], c.vy[r + 1],
-                                   r + 2 < PR ? c.vy[r + 2] : vy_below, c.vx[r], ihx, ihy);
+                                   r + 2 < PR ? c.vy[r + 2] : vy_below, c.vx[r], ihx, ihy, sqc);
             const f2 sx_n = r + 1 < PR ? F1.sx : sx_below;
             const f2 mx = add2(sub2(F0.txx, west_pair(F0.txx)), sub2(sx_n, F0.sx));
             const f2 my = add2(sub2(east_pair(F0.sy), F0.sy), sub2(F0.tyy, tyy_s));
@@ -1189,8 +1202,8 @@ __device__ __forceinline__ void ras_smem_tile(const RasArgs<T> &a, int tile, T *
                 const T vc = cx[q];
                 const T txx_c = flux_n(coef_x(g, Ec[q]), cx[q + 1], vc);
                 const T txx_w = flux_n(coef_x(g, Ec[q - 1]), vc, cx[q - 1]);
-                const T sx_n = r_mul(shear(g, En[q + W], cx[q + W], vc, cy[q + W], cy[q + W - 1]), g.ihy);
-                const T sx_c = r_mul(shear(g, En[q], vc, cx[q - W], cy[q], cy[q - 1]), g.ihy);
+                const T sx_n = shear_x(g, En[q + W], cx[q + W], vc, cy[q + W], cy[q + W - 1]);
+                const T sx_c = shear_x(g, En[q], vc, cx[q - W], cy[q], cy[q - 1]);
                 const T d = diag_x(g, Ec[q], Ec[q - 1], En[q + W], En[q]);
                 nxv[q] = jacobi_update(vc, Rx[q], m_x(txx_c, txx_w, sx_n, sx_c), jacobi_weight(a.omega, inv_diag(d)));
             }
@@ -1198,8 +1211,8 @@ __device__ __forceinline__ void ras_smem_tile(const RasArgs<T> &a, int tile, T *
                 const T vc = cy[q];
                 const T tyy_c = flux_n(coef_y(g, Ec[q]), cy[q + W], vc);
                 const T tyy_s = flux_n(coef_y(g, Ec[q - W]), vc, cy[q - W]);
-                const T sy_e = r_mul(shear(g, En[q + 1], cx[q + 1], cx[q + 1 - W], cy[q + 1], vc), g.ihx);
-                const T sy_c = r_mul(shear(g, En[q], cx[q], cx[q - W], vc, cy[q - 1]), g.ihx);
+                const T sy_e = shear_y(g, En[q + 1], cx[q + 1], cx[q + 1 - W], cy[q + 1], vc);
+                const T sy_c = shear_y(g, En[q], cx[q], cx[q - W], vc, cy[q - 1]);
                 const T d = diag_y(g, Ec[q], Ec[q - W], En[q + 1], En[q]);
                 nyv[q] = jacobi_update(vc, Ry[q], m_y(sy_e, sy_c, tyy_c, tyy_s), jacobi_weight(a.omega, inv_diag(d)));
             }
@@ -1470,7 +1483,7 @@ cudaError_t launch_ras(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const 
         void (*kern)(TmaMaps, RasArgs<T>) = pick_tma<T>(p);
         if constexpr (sizeof(T) == 4) {
             if (p.kind == PLAN_PAIR) {
-                const bool sq = g.ihx == g.ihy && g.ihx2 == g.ihy2;
+                const bool sq = g.square != 0;
                 if (sq) {
                     if (p.nstage == 2)
                         kern = p.threads <= PAIR_SMALL_THREADS ? k_ras_pair<PAIR_SMALL_THREADS, 2, true> : k_ras_pair<PAIR_MAX_THREADS, 2, true>;

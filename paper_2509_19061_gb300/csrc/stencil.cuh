@@ -99,6 +99,48 @@ __device__ __forceinline__ T shear(const GridDesc<T> &g, T en, T vx_c, T vx_s, T
     return r_mul(en, r_fma(r_sub(vx_c, vx_s), g.ihy, r_mul(r_sub(vy_c, vy_w), g.ihx)));
 }
 
+// Scaled shear fluxes Sx = sigma'_xy / hy and Sy = sigma'_xy / hx at node
+// (i, j).  General cells: the shear above times 1/hy and 1/hx.  Square cells
+// (g.square): Sx = Sy = (eta_n / h^2) ((vx_c - vx_s) + (vy_c - vy_w)), the
+// same quantity in four operations instead of six.  Every kernel takes the
+// form of its grid, so the schedules of one map still agree bit for bit.
+template <typename T>
+__device__ __forceinline__ T shear_sq(T en_h2, T vx_c, T vx_s, T vy_c, T vy_w)
+{
+    return r_mul(en_h2, r_add(r_sub(vx_c, vx_s), r_sub(vy_c, vy_w)));
+}
+// SQM: 0 the general form, 1 the square-cell form, 2 the form of the grid
+// (g.square); kernels that know the form at launch take 0 or 1
+template <int SQM = 2, typename T>
+__device__ __forceinline__ bool square_form(const GridDesc<T> &g)
+{
+    return SQM == 2 ? g.square != 0 : SQM == 1;
+}
+template <int SQM = 2, typename T>
+__device__ __forceinline__ T shear_x(const GridDesc<T> &g, T en, T vx_c, T vx_s, T vy_c, T vy_w)
+{
+    return square_form<SQM>(g) ? shear_sq(r_mul(en, g.ihx2), vx_c, vx_s, vy_c, vy_w)
+                               : r_mul(shear(g, en, vx_c, vx_s, vy_c, vy_w), g.ihy);
+}
+template <int SQM = 2, typename T>
+__device__ __forceinline__ T shear_y(const GridDesc<T> &g, T en, T vx_c, T vx_s, T vy_c, T vy_w)
+{
+    return square_form<SQM>(g) ? shear_sq(r_mul(en, g.ihx2), vx_c, vx_s, vy_c, vy_w)
+                               : r_mul(shear(g, en, vx_c, vx_s, vy_c, vy_w), g.ihx);
+}
+// both at one node
+template <int SQM = 2, typename T>
+__device__ __forceinline__ void shear_xy(const GridDesc<T> &g, T en, T vx_c, T vx_s, T vy_c, T vy_w, T &sx, T &sy)
+{
+    if (square_form<SQM>(g)) {
+        sx = sy = shear_sq(r_mul(en, g.ihx2), vx_c, vx_s, vy_c, vy_w);
+    } else {
+        const T sh = shear(g, en, vx_c, vx_s, vy_c, vy_w);
+        sx = r_mul(sh, g.ihy);
+        sy = r_mul(sh, g.ihx);
+    }
+}
+
 // (M v)_x from Txx(j,i), Txx(j,i-1), Sx(j+1,i), Sx(j,i)
 template <typename T>
 __device__ __forceinline__ T m_x(T txx_c, T txx_w, T sx_n, T sx_c)

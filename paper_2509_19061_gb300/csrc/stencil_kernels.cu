@@ -151,7 +151,7 @@ struct CompF {
 
 // The FP32 energy sums: per cell the terms of CellSq<float> (a cell's vx and vy
 // terms added in FP32), per row a compensated FP32 sum, per thread an FP64 sum.
-template <bool MASK>
+template <bool MASK, int SQM>
 __device__ __forceinline__ void energy_rows_f32(const GridDesc<float> &g, const float *__restrict__ eta_c,
                                                 const float *__restrict__ eta_n, const float *__restrict__ inv_dx,
                                                 const float *__restrict__ inv_dy, const float *__restrict__ fx,
@@ -168,7 +168,7 @@ __device__ __forceinline__ void energy_rows_f32(const GridDesc<float> &g, const 
             float trv = 0.f, tff = 0.f;
             bool any = false;
             if (vx_unknown(g, j, i)) {
-                op_x<float, MASK>(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
+                op_x<float, MASK, SQM>(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
                 const float b = p ? r_fma(r_sub(p[q], p[q - 1]), g.ihx, fx[q]) : fx[q];
                 const float wi = -(inv_dx ? inv_dx[q] : inv_diag(d));
                 const float r = r_sub(b, m);
@@ -177,7 +177,7 @@ __device__ __forceinline__ void energy_rows_f32(const GridDesc<float> &g, const 
                 any = true;
             }
             if (vy_unknown(g, j, i)) {
-                op_y<float, MASK>(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
+                op_y<float, MASK, SQM>(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
                 const float b = p ? r_fma(r_sub(p[q], p[q - g.pitch]), g.ihy, fy[q]) : fy[q];
                 const float wi = -(inv_dy ? inv_dy[q] : inv_diag(d));
                 const float r = r_sub(b, m);
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(EN_THREADS) k_energy_tile(GridDesc<T> g, const
     }
 }
 
-template <typename T, bool MASK = false>
+template <typename T, bool MASK = false, int SQM = 2>
 __global__ void __launch_bounds__(EN_THREADS) k_energy(GridDesc<T> g, const T *__restrict__ eta_c,
                                                        const T *__restrict__ eta_n, const T *__restrict__ inv_dx,
                                                        const T *__restrict__ inv_dy, const T *__restrict__ fx,
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(EN_THREADS) k_energy(GridDesc<T> g, const T *_
     const T ilap = (T)(1.0 / g.lap);
     // rows round-robin over the blocks, columns over the threads (no index division)
     if constexpr (sizeof(T) == 4)
-        energy_rows_f32<MASK>(g, eta_c, eta_n, inv_dx, inv_dy, fx, fy, p, vx, vy, s_rv, s_rp, s_ff);
+        energy_rows_f32<MASK, SQM>(g, eta_c, eta_n, inv_dx, inv_dy, fx, fy, p, vx, vy, s_rv, s_rp, s_ff);
     else
     for (int j = blockIdx.x; j <= g.ny; j += gridDim.x)
     for (int i = threadIdx.x; i <= g.nx; i += EN_THREADS) {
@@ -333,14 +333,14 @@ __global__ void __launch_bounds__(EN_THREADS) k_energy(GridDesc<T> g, const T *_
         T m, d, vc;
         CellSq<T> rv(s_rv), ff(s_ff); // the cell's vx and vy terms
         if (vx_unknown(g, j, i)) {
-            op_x<T, MASK>(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
+            op_x<T, MASK, SQM>(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
             const T b = p ? r_fma(r_sub(p[q], p[q - 1]), g.ihx, fx[q]) : fx[q];
             const T wi = -(inv_dx ? inv_dx[q] : inv_diag(d));
             rv.add(r_sub(b, m), wi);
             ff.add(fx[q], wi);
         }
         if (vy_unknown(g, j, i)) {
-            op_y<T, MASK>(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
+            op_y<T, MASK, SQM>(g, eta_c, eta_n, vx, vy, j, i, m, d, vc);
             const T b = p ? r_fma(r_sub(p[q], p[q - g.pitch]), g.ihy, fy[q]) : fy[q];
             const T wi = -(inv_dy ? inv_dy[q] : inv_diag(d));
             rv.add(r_sub(b, m), wi);
@@ -444,8 +444,12 @@ cudaError_t launch_energy(const GridDesc<T> &g, const T *eta_c, const T *eta_n, 
     if constexpr (sizeof(T) == 8)
         k_energy_tile<T><<<EN_BLOCKS, EN_THREADS, 0, s>>>(g, eta_c, eta_n, inv_dx, inv_dy, fx, fy, p, vx, vy,
                                                           partials);
+    else if (g.square)
+        k_energy<T, false, 1><<<EN_BLOCKS, EN_THREADS, 0, s>>>(g, eta_c, eta_n, inv_dx, inv_dy, fx, fy, p, vx, vy,
+                                                               partials);
     else
-        k_energy<T><<<EN_BLOCKS, EN_THREADS, 0, s>>>(g, eta_c, eta_n, inv_dx, inv_dy, fx, fy, p, vx, vy, partials);
+        k_energy<T, false, 0><<<EN_BLOCKS, EN_THREADS, 0, s>>>(g, eta_c, eta_n, inv_dx, inv_dy, fx, fy, p, vx, vy,
+                                                               partials);
     k_energy_final<<<1, 96, 0, s>>>(partials, EN_BLOCKS, out);
     return cudaGetLastError();
 }
@@ -454,8 +458,12 @@ template <typename T>
 cudaError_t launch_energy_raw(const GridDesc<T> &g, const T *eta_c, const T *eta_n, const T *fx, const T *fy,
                               const T *p, const T *vx, const T *vy, double *partials, double *out, cudaStream_t s)
 {
-    k_energy<T, true><<<EN_BLOCKS, EN_THREADS, 0, s>>>(g, eta_c, eta_n, nullptr, nullptr, fx, fy, p, vx, vy,
-                                                       partials);
+    if (g.square)
+        k_energy<T, true, 1><<<EN_BLOCKS, EN_THREADS, 0, s>>>(g, eta_c, eta_n, nullptr, nullptr, fx, fy, p, vx, vy,
+                                                              partials);
+    else
+        k_energy<T, true, 0><<<EN_BLOCKS, EN_THREADS, 0, s>>>(g, eta_c, eta_n, nullptr, nullptr, fx, fy, p, vx, vy,
+                                                              partials);
     k_energy_final<<<1, 96, 0, s>>>(partials, EN_BLOCKS, out);
     return cudaGetLastError();
 }

@@ -215,9 +215,7 @@ __device__ __forceinline__ void jacobi_rows(const GridDesc<T> &g, const Coeffs<T
 #pragma unroll
         for (int k = 0; k < VW; ++k) {
             tyyS[k] = flux_n(coef_y(g, ecS[k]), vyC[k], vyS[k]);
-            const T sh = shear(g, enC[k], vxC[k], vxS[k], vyC[k], k ? vyC[k - 1] : vyw);
-            sxC[k] = r_mul(sh, g.ihy);
-            syC[k] = r_mul(sh, g.ihx);
+            shear_xy(g, enC[k], vxC[k], vxS[k], vyC[k], k ? vyC[k - 1] : vyw, sxC[k], syC[k]);
         }
     }
     for (int j = j0; j < j1; ++j) {
@@ -239,9 +237,7 @@ __device__ __forceinline__ void jacobi_rows(const GridDesc<T> &g, const Coeffs<T
             const T vyw = shfl_up1(vyN[VW - 1]);
 #pragma unroll
             for (int k = 0; k < VW; ++k) {
-                const T sh = shear(g, enN[k], vxN[k], vxC[k], vyN[k], k ? vyN[k - 1] : vyw);
-                sxN[k] = r_mul(sh, g.ihy);
-                syN[k] = r_mul(sh, g.ihx);
+                shear_xy(g, enN[k], vxN[k], vxC[k], vyN[k], k ? vyN[k - 1] : vyw, sxN[k], syN[k]);
             }
         }
         T tyy[VW];
@@ -391,8 +387,8 @@ __device__ __forceinline__ void gs_half(const GridDesc<T> &g, GsSmem<T, INV> &w,
             const T ecC = w.ec[a][b], ecW = w.ec[a][b - 1], enN = w.en[a + 1][b], enS = w.en[a][b];
             const T txx_c = flux_n(coef_x(g, ecC), w.vx[a][b + 1], vc);
             const T txx_w = flux_n(coef_x(g, ecW), vc, w.vx[a][b - 1]);
-            const T sx_n = r_mul(shear(g, enN, w.vx[a + 1][b], vc, w.vy[a + 1][b], w.vy[a + 1][b - 1]), g.ihy);
-            const T sx_c = r_mul(shear(g, enS, vc, w.vx[a - 1][b], w.vy[a][b], w.vy[a][b - 1]), g.ihy);
+            const T sx_n = shear_x(g, enN, w.vx[a + 1][b], vc, w.vy[a + 1][b], w.vy[a + 1][b - 1]);
+            const T sx_c = shear_x(g, enS, vc, w.vx[a - 1][b], w.vy[a][b], w.vy[a][b - 1]);
             const T m = m_x(txx_c, txx_w, sx_n, sx_c);
             T inv;
             if constexpr (INV) inv = w.ix[a][b];
@@ -404,8 +400,8 @@ __device__ __forceinline__ void gs_half(const GridDesc<T> &g, GsSmem<T, INV> &w,
             const T ecC = w.ec[a][b], ecS = w.ec[a - 1][b], enE = w.en[a][b + 1], enW = w.en[a][b];
             const T tyy_c = flux_n(coef_y(g, ecC), w.vy[a + 1][b], vc);
             const T tyy_s = flux_n(coef_y(g, ecS), vc, w.vy[a - 1][b]);
-            const T sy_e = r_mul(shear(g, enE, w.vx[a][b + 1], w.vx[a - 1][b + 1], w.vy[a][b + 1], vc), g.ihx);
-            const T sy_c = r_mul(shear(g, enW, w.vx[a][b], w.vx[a - 1][b], vc, w.vy[a][b - 1]), g.ihx);
+            const T sy_e = shear_y(g, enE, w.vx[a][b + 1], w.vx[a - 1][b + 1], w.vy[a][b + 1], vc);
+            const T sy_c = shear_y(g, enW, w.vx[a][b], w.vx[a - 1][b], vc, w.vy[a][b - 1]);
             const T m = m_y(sy_e, sy_c, tyy_c, tyy_s);
             T inv;
             if constexpr (INV) inv = w.iy[a][b];
