@@ -444,10 +444,7 @@ cudaError_t launch_energy(const GridDesc<T> &g, const T *eta_c, const T *eta_n, 
     if constexpr (sizeof(T) == 8)
         k_energy_tile<T><<<EN_BLOCKS, EN_THREADS, 0, s>>>(g, eta_c, eta_n, inv_dx, inv_dy, fx, fy, p, vx, vy,
                                                           partials);
-    else if (g.square)
-        k_energy<T, false, 1><<<EN_BLOCKS, EN_THREADS, 0, s>>>(g, eta_c, eta_n, inv_dx, inv_dy, fx, fy, p, vx, vy,
-                                                               partials);
-    else
+    else // the general shear form on every grid: the square-cell form measured slower here (0.88 against 0.73 ms)
         k_energy<T, false, 0><<<EN_BLOCKS, EN_THREADS, 0, s>>>(g, eta_c, eta_n, inv_dx, inv_dy, fx, fy, p, vx, vy,
                                                                partials);
     k_energy_final<<<1, 96, 0, s>>>(partials, EN_BLOCKS, out);
@@ -458,12 +455,8 @@ template <typename T>
 cudaError_t launch_energy_raw(const GridDesc<T> &g, const T *eta_c, const T *eta_n, const T *fx, const T *fy,
                               const T *p, const T *vx, const T *vy, double *partials, double *out, cudaStream_t s)
 {
-    if (g.square)
-        k_energy<T, true, 1><<<EN_BLOCKS, EN_THREADS, 0, s>>>(g, eta_c, eta_n, nullptr, nullptr, fx, fy, p, vx, vy,
-                                                              partials);
-    else
-        k_energy<T, true, 0><<<EN_BLOCKS, EN_THREADS, 0, s>>>(g, eta_c, eta_n, nullptr, nullptr, fx, fy, p, vx, vy,
-                                                              partials);
+    k_energy<T, true, 0><<<EN_BLOCKS, EN_THREADS, 0, s>>>(g, eta_c, eta_n, nullptr, nullptr, fx, fy, p, vx, vy,
+                                                          partials);
     k_energy_final<<<1, 96, 0, s>>>(partials, EN_BLOCKS, out);
     return cudaGetLastError();
 }

@@ -133,7 +133,7 @@ constexpr int JR_PD = 3;
 // unknowns and walls of (ox, oy), nothing else.  The row loads of iterations
 // j + 1 .. j + JR_PD - 1 are in flight (cp.async into the warp's `stage`)
 // while iteration j computes.
-template <typename T, int VW, bool DX, bool DY, bool INV>
+template <typename T, int VW, bool DX, bool DY, bool INV, int SQM>
 __device__ __forceinline__ void jacobi_rows(const GridDesc<T> &g, const Coeffs<T> &c, T omega,
                                             const T *__restrict__ vx, const T *__restrict__ vy, T *__restrict__ ox,
                                             T *__restrict__ oy, int rows, int strip, T *stage)
@@ -215,7 +215,7 @@ __device__ __forceinline__ void jacobi_rows(const GridDesc<T> &g, const Coeffs<T
 #pragma unroll
         for (int k = 0; k < VW; ++k) {
             tyyS[k] = flux_n(coef_y(g, ecS[k]), vyC[k], vyS[k]);
-            shear_xy(g, enC[k], vxC[k], vxS[k], vyC[k], k ? vyC[k - 1] : vyw, sxC[k], syC[k]);
+            shear_xy<SQM>(g, enC[k], vxC[k], vxS[k], vyC[k], k ? vyC[k - 1] : vyw, sxC[k], syC[k]);
         }
     }
     for (int j = j0; j < j1; ++j) {
@@ -237,7 +237,7 @@ __device__ __forceinline__ void jacobi_rows(const GridDesc<T> &g, const Coeffs<T
             const T vyw = shfl_up1(vyN[VW - 1]);
 #pragma unroll
             for (int k = 0; k < VW; ++k) {
-                shear_xy(g, enN[k], vxN[k], vxC[k], vyN[k], k ? vyN[k - 1] : vyw, sxN[k], syN[k]);
+                shear_xy<SQM>(g, enN[k], vxN[k], vxC[k], vyN[k], k ? vyN[k - 1] : vyw, sxN[k], syN[k]);
             }
         }
         T tyy[VW];
@@ -293,7 +293,7 @@ __device__ __forceinline__ void jacobi_rows(const GridDesc<T> &g, const Coeffs<T
 template <typename T, bool DX, bool DY, bool INV>
 constexpr size_t jr_stage_bytes() { return (size_t)JR_PD * JrFields<DX, DY, INV>::N * 32 * 16; }
 
-template <typename T, int VW, bool DX, bool DY, bool INV>
+template <typename T, int VW, bool DX, bool DY, bool INV, int SQM>
 __global__ void __launch_bounds__(JR_WARPS * 32) k_jacobi_rows(GridDesc<T> g, Coeffs<T> c, T omega,
                                                                const T *__restrict__ vx, const T *__restrict__ vy,
                                                                T *__restrict__ ox, T *__restrict__ oy, int rows)
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(JR_WARPS * 32) k_jacobi_rows(GridDesc<T> g, Co
     const int w = (int)threadIdx.x >> 5;
     const int strip = (int)blockIdx.x * JR_WARPS + w;
     T *stage = reinterpret_cast<T *>(jr_smem + (size_t)w * jr_stage_bytes<T, DX, DY, INV>());
-    jacobi_rows<T, VW, DX, DY, INV>(g, c, omega, vx, vy, ox, oy, rows, strip, stage);
+    jacobi_rows<T, VW, DX, DY, INV, SQM>(g, c, omega, vx, vy, ox, oy, rows, strip, stage);
 }
 
 // values per lane: one 16-byte vector
@@ -330,13 +330,17 @@ cudaError_t jacobi_pass(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const
     const dim3 grid((unsigned)((strips + JR_WARPS - 1) / JR_WARPS), (unsigned)((g.ny + rows) / rows));
     // FP32 forms 1/diag on the fly; FP64 reads it when the arrays exist
     const bool inv = sizeof(T) == 8 && c.inv_dx && c.inv_dy;
-    if (inv) {
-        const size_t smem = JR_WARPS * jr_stage_bytes<T, DX, DY, true>();
-        k_jacobi_rows<T, VW, DX, DY, true><<<grid, JR_WARPS * 32, smem, s>>>(g, c, omega, vx, vy, ox, oy, rows);
-    } else {
-        const size_t smem = JR_WARPS * jr_stage_bytes<T, DX, DY, false>();
-        k_jacobi_rows<T, VW, DX, DY, false><<<grid, JR_WARPS * 32, smem, s>>>(g, c, omega, vx, vy, ox, oy, rows);
-    }
+    // the shear form is fixed per launch (square cells or not)
+    const size_t smem_t = JR_WARPS * jr_stage_bytes<T, DX, DY, true>();
+    const size_t smem_f = JR_WARPS * jr_stage_bytes<T, DX, DY, false>();
+    if (inv && g.square)
+        k_jacobi_rows<T, VW, DX, DY, true, 1><<<grid, JR_WARPS * 32, smem_t, s>>>(g, c, omega, vx, vy, ox, oy, rows);
+    else if (inv)
+        k_jacobi_rows<T, VW, DX, DY, true, 0><<<grid, JR_WARPS * 32, smem_t, s>>>(g, c, omega, vx, vy, ox, oy, rows);
+    else if (g.square)
+        k_jacobi_rows<T, VW, DX, DY, false, 1><<<grid, JR_WARPS * 32, smem_f, s>>>(g, c, omega, vx, vy, ox, oy, rows);
+    else
+        k_jacobi_rows<T, VW, DX, DY, false, 0><<<grid, JR_WARPS * 32, smem_f, s>>>(g, c, omega, vx, vy, ox, oy, rows);
     return cudaGetLastError();
 }
 
@@ -367,7 +371,7 @@ static_assert(GS_TX % 32 == 0 && GS_H == 4 && (GS_WX * 4) % 16 == 0, "RBGS windo
 // memory: a point of one colour reads only points of the other colour of its
 // own component (and the other component, which this half-sweep does not
 // change).
-template <typename T, bool INV, bool X>
+template <typename T, bool INV, bool X, int SQM>
 __device__ __forceinline__ void gs_half(const GridDesc<T> &g, GsSmem<T, INV> &w, T omega, int ox0, int oy0, int colour,
                                         int ring, int tid)
 {
@@ -387,8 +391,8 @@ __device__ __forceinline__ void gs_half(const GridDesc<T> &g, GsSmem<T, INV> &w,
             const T ecC = w.ec[a][b], ecW = w.ec[a][b - 1], enN = w.en[a + 1][b], enS = w.en[a][b];
             const T txx_c = flux_n(coef_x(g, ecC), w.vx[a][b + 1], vc);
             const T txx_w = flux_n(coef_x(g, ecW), vc, w.vx[a][b - 1]);
-            const T sx_n = shear_x(g, enN, w.vx[a + 1][b], vc, w.vy[a + 1][b], w.vy[a + 1][b - 1]);
-            const T sx_c = shear_x(g, enS, vc, w.vx[a - 1][b], w.vy[a][b], w.vy[a][b - 1]);
+            const T sx_n = shear_x<SQM>(g, enN, w.vx[a + 1][b], vc, w.vy[a + 1][b], w.vy[a + 1][b - 1]);
+            const T sx_c = shear_x<SQM>(g, enS, vc, w.vx[a - 1][b], w.vy[a][b], w.vy[a][b - 1]);
             const T m = m_x(txx_c, txx_w, sx_n, sx_c);
             T inv;
             if constexpr (INV) inv = w.ix[a][b];
@@ -400,8 +404,8 @@ __device__ __forceinline__ void gs_half(const GridDesc<T> &g, GsSmem<T, INV> &w,
             const T ecC = w.ec[a][b], ecS = w.ec[a - 1][b], enE = w.en[a][b + 1], enW = w.en[a][b];
             const T tyy_c = flux_n(coef_y(g, ecC), w.vy[a + 1][b], vc);
             const T tyy_s = flux_n(coef_y(g, ecS), vc, w.vy[a - 1][b]);
-            const T sy_e = shear_y(g, enE, w.vx[a][b + 1], w.vx[a - 1][b + 1], w.vy[a][b + 1], vc);
-            const T sy_c = shear_y(g, enW, w.vx[a][b], w.vx[a - 1][b], vc, w.vy[a][b - 1]);
+            const T sy_e = shear_y<SQM>(g, enE, w.vx[a][b + 1], w.vx[a - 1][b + 1], w.vy[a][b + 1], vc);
+            const T sy_c = shear_y<SQM>(g, enW, w.vx[a][b], w.vx[a - 1][b], vc, w.vy[a][b - 1]);
             const T m = m_y(sy_e, sy_c, tyy_c, tyy_s);
             T inv;
             if constexpr (INV) inv = w.iy[a][b];
@@ -413,7 +417,7 @@ __device__ __forceinline__ void gs_half(const GridDesc<T> &g, GsSmem<T, INV> &w,
 }
 
 // One RBGS sweep of tile (blockIdx.x, blockIdx.y) from (vx, vy) into (ox, oy).
-template <typename T, bool INV>
+template <typename T, bool INV, int SQM>
 __global__ void __launch_bounds__(GS_THREADS) k_rbgs_tile(GridDesc<T> g, Coeffs<T> c, T omega,
                                                           const T *__restrict__ vx, const T *__restrict__ vy,
                                                           T *__restrict__ ox, T *__restrict__ oy)
@@ -458,10 +462,10 @@ __global__ void __launch_bounds__(GS_THREADS) k_rbgs_tile(GridDesc<T> g, Coeffs<
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    gs_half<T, INV, true>(g, w, omega, ox0, oy0, 0, 1, tid);  // vx red on the tile + 3
-    gs_half<T, INV, true>(g, w, omega, ox0, oy0, 1, 2, tid);  // vx black on the tile + 2
-    gs_half<T, INV, false>(g, w, omega, ox0, oy0, 0, 3, tid); // vy red on the tile + 1
-    gs_half<T, INV, false>(g, w, omega, ox0, oy0, 1, 4, tid); // vy black on the tile
+    gs_half<T, INV, true, SQM>(g, w, omega, ox0, oy0, 0, 1, tid);  // vx red on the tile + 3
+    gs_half<T, INV, true, SQM>(g, w, omega, ox0, oy0, 1, 2, tid);  // vx black on the tile + 2
+    gs_half<T, INV, false, SQM>(g, w, omega, ox0, oy0, 0, 3, tid); // vy red on the tile + 1
+    gs_half<T, INV, false, SQM>(g, w, omega, ox0, oy0, 1, 4, tid); // vy black on the tile
     // the unknowns of the tile's own cells
     for (int e = tid; e < GS_TY * GS_TX; e += GS_THREADS) {
         const int a = GS_H + e / GS_TX, b = GS_H + e % GS_TX;
@@ -490,18 +494,19 @@ cudaError_t launch_rbgs_sweep(const GridDesc<T> &g, const Coeffs<T> &c, T omega,
 {
     const dim3 grid((unsigned)((g.nx + GS_TX - 1) / GS_TX), (unsigned)((g.ny + GS_TY - 1) / GS_TY));
     // FP64 reads 1/diag (FP64 reciprocals are slow); FP32 forms it
+    auto run = [&](auto kern, size_t smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) kern<<<grid, GS_THREADS, smem, s>>>(g, c, omega, vx, vy, ox, oy);
+        return e;
+    };
     cudaError_t e;
-    if (sizeof(T) == 8 && c.inv_dx && c.inv_dy) {
-        const size_t smem = sizeof(GsSmem<T, true>);
-        e = cudaFuncSetAttribute(k_rbgs_tile<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_rbgs_tile<T, true><<<grid, GS_THREADS, smem, s>>>(g, c, omega, vx, vy, ox, oy);
-    } else {
-        const size_t smem = sizeof(GsSmem<T, false>);
-        e = cudaFuncSetAttribute(k_rbgs_tile<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_rbgs_tile<T, false><<<grid, GS_THREADS, smem, s>>>(g, c, omega, vx, vy, ox, oy);
-    }
+    if (sizeof(T) == 8 && c.inv_dx && c.inv_dy)
+        e = g.square ? run(k_rbgs_tile<T, true, 1>, sizeof(GsSmem<T, true>))
+                     : run(k_rbgs_tile<T, true, 0>, sizeof(GsSmem<T, true>));
+    else
+        e = g.square ? run(k_rbgs_tile<T, false, 1>, sizeof(GsSmem<T, false>))
+                     : run(k_rbgs_tile<T, false, 0>, sizeof(GsSmem<T, false>));
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
