@@ -425,7 +425,7 @@ def energy_sums_fsum(g, fx, fy, vx, vy):
 
 
 @pytest.mark.parametrize("dtype,tile,k,o,kernel", [
-    ("f32", (48, 64), 8, 7, "pair"),    # the benchmark's schedule (square-cell pair form, 640 threads)
+    ("f32", (48, 64), 8, 7, "pair"),    # the benchmark's schedule (square-cell pair form, 512 threads)
     ("f32", (62, 56), 8, 0, "pair"),    # ring-only tiles, pair layout
     ("f32", (32, 32), 4, 3, "tma"),     # one-column layout, 25 passes
     ("f64", (32, 32), 4, 3, "tma"),     # FP64, 25 passes
