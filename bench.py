@@ -40,7 +40,9 @@ FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0
 # FP32 tile-kernel arithmetic per cell-sweep (an FMA counts 2): fluxes
 # sigma'xx, sigma'yy (2 + 2), the node shear (6) scaled twice (2), M v in x
-# and y (3 + 3), the two damped updates (3 + 3)
+# and y (3 + 3), the two damped updates (3 + 3); the general form's count,
+# kept as the algorithmic figure on square cells too, where the kernel forms
+# the scaled shear in 4
 FLOPS_PER_CELL_SWEEP = 24
 # nominal arithmetic peaks of the GB300 (152 SMs at 2.07 GHz): FP32 128 lanes
 # per SM, an FMA counting 2 flops; FP64 at its nominal 1.25 TFLOP/s
