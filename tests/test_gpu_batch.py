@@ -286,15 +286,16 @@ def test_batched_wait_timeout_is_reported_and_recoverable(api):
     b.close()
 
 
-@pytest.mark.parametrize("tile,k,o", [((48, 32), 8, 7),   # the benchmark's (autotuned) schedule: pair layout
+@pytest.mark.parametrize("tile,k,o", [((48, 64), 8, 7),   # the benchmark's (autotuned) schedule: pair layout
+                                      ((48, 32), 8, 7),   # the smaller pair-kernel instance
                                       ((32, 32), 4, 3)])  # one-column TMA layout
 def test_full_batched_workload_samples_match_single_contexts(api, tile, k, o):
     """The batched workload at full size (256 seeded instances, sides 64 to
     1024, 4.85e7 cells) in the benchmark's launch configuration (FP32 RAS,
-    the autotuned 48 x 32, k = 8, overlap 7 on the pair layout, TMA staging)
-    and in the one-column layout: eight sweeps; sampled instances (the
-    smallest, the largest and two others) equal their own contexts bit for
-    bit."""
+    the autotuned 48 x 64, k = 8, overlap 7 on the pair layout, TMA staging),
+    with 48 x 32 tiles and in the one-column layout: eight sweeps; sampled
+    instances (the smallest, the largest and two others) equal their own
+    contexts bit for bit."""
     import torch
     specs = inputs.batch_specs(seed=5, count=256)
     probs = [inputs.batch_problem(sp) for sp in specs]
