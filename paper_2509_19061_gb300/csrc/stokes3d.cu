@@ -315,13 +315,44 @@ __global__ void k3_apply(G3<T> g, GAcc<T> a, const T *__restrict__ p, T *__restr
                                   : T(0);
 }
 
+// accessor without extent tests, for points whose neighbours all lie inside
+// every field's extent (the same values as GAcc there)
+template <typename T>
+struct UAcc {
+    G3<T> g;
+    const T *__restrict__ x, *__restrict__ y, *__restrict__ z;
+    const T *__restrict__ c, *__restrict__ xy, *__restrict__ xz, *__restrict__ yz;
+    __device__ __forceinline__ T vx(int k, int j, int i) const { return x[g.at(k, j, i)]; }
+    __device__ __forceinline__ T vy(int k, int j, int i) const { return y[g.at(k, j, i)]; }
+    __device__ __forceinline__ T vz(int k, int j, int i) const { return z[g.at(k, j, i)]; }
+    __device__ __forceinline__ T ec(int k, int j, int i) const { return c[g.at(k, j, i)]; }
+    __device__ __forceinline__ T exy(int k, int j, int i) const { return xy[g.at(k, j, i)]; }
+    __device__ __forceinline__ T exz(int k, int j, int i) const { return xz[g.at(k, j, i)]; }
+    __device__ __forceinline__ T eyz(int k, int j, int i) const { return yz[g.at(k, j, i)]; }
+};
+
 // ---- fused damped Jacobi -------------------------------------------------------
 // Every unknown from the old (vx, vy, vz); walls copied, padding untouched.
+// A block whose points and their neighbours (one cell each way) lie inside
+// the cells 1 .. n - 2 of every axis has only unknowns and reads only inside
+// every extent: it takes the same arithmetic without extent or unknown tests.
 template <typename T>
 __global__ void k3_jacobi(G3<T> g, GAcc<T> a, C3<T> c, T omega, T *__restrict__ ox, T *__restrict__ oy,
                           T *__restrict__ oz)
 {
-    const int i = blockIdx.x * B3X + threadIdx.x, j = blockIdx.y * B3Y + threadIdx.y, k = blockIdx.z * B3Z + threadIdx.z;
+    const int i0 = blockIdx.x * B3X, j0 = blockIdx.y * B3Y, k0 = blockIdx.z * B3Z;
+    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y, k = k0 + threadIdx.z;
+    if (i0 >= 1 && i0 + B3X <= g.nx - 1 && j0 >= 1 && j0 + B3Y <= g.ny - 1 && k0 >= 1 && k0 + B3Z <= g.nz - 1) {
+        UAcc<T> u;
+        u.g = g;
+        u.x = a.x; u.y = a.y; u.z = a.z;
+        u.c = a.c; u.xy = a.xy; u.xz = a.xz; u.yz = a.yz;
+        const size_t q = g.at(k, j, i);
+        ox[q] = jacobi_update(a.x[q], c.bx[q], op3_x(g, u, k, j, i), jacobi_weight(omega, c.ix[q]));
+        oy[q] = jacobi_update(a.y[q], c.by[q], op3_y(g, u, k, j, i), jacobi_weight(omega, c.iy[q]));
+        oz[q] = jacobi_update(a.z[q], c.bz[q], op3_z(g, u, k, j, i), jacobi_weight(omega, c.iz[q]));
+        return;
+    }
     if (i > g.nx || j > g.ny || k > g.nz) return;
     const size_t q = g.at(k, j, i);
     if (in_vx(g, k, j, i)) {

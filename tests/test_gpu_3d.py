@@ -119,6 +119,31 @@ def test_jacobi3d_every_sweep_f64(api, o3):
         assert rel(r.get(), want) <= F64_TOL, (s, rel(r.get(), want))
 
 
+@pytest.mark.parametrize("n", [(70, 13, 9), (97, 18, 12)])
+def test_jacobi3d_interior_blocks_f64(api, o3, n):
+    """Grids large enough that the fused Jacobi has blocks whose points and
+    neighbours all lie inside every extent (taken without extent tests) next
+    to boundary blocks: every sweep count matches the oracle, and RAS with
+    overlap k - 1 equals it bit for bit in FP64 and FP32."""
+    prob = problem(*n, 17)
+    v0 = inputs.random_velocity3d(*n, 18, 0.1)
+    p = inputs.random_pressure3d(*n, 19, 0.2)
+    g = ogrid(o3, prob)
+    b = o3.rhs(g, prob.fx, prob.fy, prob.fz, p)
+    for s in (1, 3):
+        r = Run3(api, prob, "f64", v0, p)
+        r.smooth(variant="fused", sweeps=s)
+        want = o3.jacobi(g, b, 0.3, s, v0)
+        assert rel(r.get(), want) <= F64_TOL, (s, rel(r.get(), want))
+    for dtype in ("f64", "f32"):
+        a = Run3(api, prob, dtype, v0, p)
+        a.smooth(variant="ras", sweeps=4, tile=(8, 8, 8), k=2, overlap=1, seed=4)
+        f = Run3(api, prob, dtype, v0, p)
+        f.smooth(variant="fused", sweeps=4)
+        for x, y in zip(a.get(), f.get()):
+            assert np.array_equal(x, y), dtype
+
+
 @pytest.mark.parametrize("n,tile,k,o", [((12, 10, 9), (4, 4, 4), 2, 1), ((12, 10, 9), (5, 3, 4), 3, 0),
                                          ((12, 10, 9), (4, 5, 3), 3, 2), ((20, 20, 20), (8, 8, 8), 2, 1),
                                          ((9, 7, 5), (16, 16, 16), 2, 0), ((17, 6, 11), (4, 4, 4), 4, 3),
