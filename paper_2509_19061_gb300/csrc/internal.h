@@ -86,6 +86,13 @@ cudaError_t launch_energy(const GridDesc<T> &g, const T *eta_c, const T *eta_n, 
                           const T *fx, const T *fy, const T *p, const T *vx, const T *vy, double *partials,
                           double *out, cudaStream_t s);
 
+// The FP32 sums by row-marching warps (the library's viscosity copies; 1/diag
+// from inv_dx / inv_dy, or formed from the viscosity when they are NULL);
+// writes `*nblocks` <= energy_partials() partial triples.
+cudaError_t launch_energy_rows(const GridDesc<float> &g, const float *eta_c, const float *eta_n, const float *fx,
+                               const float *fy, const float *inv_dx, const float *inv_dy, const float *p,
+                               const float *vx, const float *vy, double *partials, int *nblocks, cudaStream_t s);
+
 // The same sums from the caller's raw viscosity (boundary nodes of eta_n
 // zeroed on the fly, 1/diag computed in the kernel); `partials` holds
 // energy_partials() * 3 doubles.

@@ -439,15 +439,17 @@ cudaError_t launch_energy(const GridDesc<T> &g, const T *eta_c, const T *eta_n, 
                           double *out, cudaStream_t s)
 {
     // FP64: the FP64 pipe is the bound, and the tiled kernel forms every flux
-    // once (6.1 instead of 9.7 ms at 8192^2); FP32: the row kernel, whose
-    // loads run faster than the tile's staging (0.74 against 1.9 ms)
-    if constexpr (sizeof(T) == 8)
+    // once (6.1 instead of 9.7 ms at 8192^2); FP32: row-marching warps that
+    // read every field once (`sweep_kernels.cu`)
+    int nb = EN_BLOCKS;
+    if constexpr (sizeof(T) == 8) {
         k_energy_tile<T><<<EN_BLOCKS, EN_THREADS, 0, s>>>(g, eta_c, eta_n, inv_dx, inv_dy, fx, fy, p, vx, vy,
                                                           partials);
-    else // the general shear form on every grid: the square-cell form measured slower here (0.88 against 0.73 ms)
-        k_energy<T, false, 0><<<EN_BLOCKS, EN_THREADS, 0, s>>>(g, eta_c, eta_n, inv_dx, inv_dy, fx, fy, p, vx, vy,
-                                                               partials);
-    k_energy_final<<<1, 96, 0, s>>>(partials, EN_BLOCKS, out);
+    } else {
+        const cudaError_t e = launch_energy_rows(g, eta_c, eta_n, fx, fy, inv_dx, inv_dy, p, vx, vy, partials, &nb, s);
+        if (e != cudaSuccess) return e;
+    }
+    k_energy_final<<<1, 96, 0, s>>>(partials, nb, out);
     return cudaGetLastError();
 }
 

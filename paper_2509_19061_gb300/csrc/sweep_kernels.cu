@@ -476,7 +476,291 @@ __global__ void __launch_bounds__(GS_THREADS) k_rbgs_tile(GridDesc<T> g, Coeffs<
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 energy sums (Sec. 6.4) by row-marching warps
+// ---------------------------------------------------------------------------
+// The warp layout and row staging of jacobi_rows; per position the terms of
+// the other FP32 energy kernels: r = b - M v (b = f - G p formed on the fly),
+// r^2 / (-diag M) and f^2 / (-diag M) of the vx and the vy unknown (a cell's
+// two terms added in FP32), (D v)^2 eta_c / (2/hx^2 + 2/hy^2) of the cell;
+// 1/diag from the viscosity, as k_inv_diag forms it.  Per lane the terms go
+// into compensated FP32 sums over a band of rows, flushed into FP64 sums.
+struct CompSum {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float t)
+    {
+        const float s = __fadd_rn(hi, t);
+        const float bb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(t, bb));
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ void flush(double &S)
+    {
+        S += (double)hi + (double)lo;
+        hi = lo = 0.f;
+    }
+};
+
+// row fields of iteration j: vx, vy, eta_n of row j + 1; eta_c, fx, fy, (with
+// INV) 1/diag at vx and vy, (with HASP) p of row j
+template <bool INV, bool HASP>
+struct ErFields {
+    static constexpr int IX = 6, IY = 7, P = INV ? 8 : 6;
+    static constexpr int N = P + (HASP ? 1 : 0);
+};
+
+template <int SQM, bool INV, bool HASP>
+__device__ __forceinline__ void energy_band(const GridDesc<float> &g, const float *__restrict__ ec,
+                                            const float *__restrict__ en, const float *__restrict__ fx,
+                                            const float *__restrict__ fy, const float *__restrict__ ix,
+                                            const float *__restrict__ iy, const float *__restrict__ p,
+                                            const float *__restrict__ vx, const float *__restrict__ vy, int j0,
+                                            int j1, int strip, float *stage, double &s_rv, double &s_rp,
+                                            double &s_ff)
+{
+    using EF = ErFields<INV, HASP>;
+    constexpr int VW = 4, OWN = 30 * VW, N = EF::N;
+    using V = float4;
+    const int lane = (int)threadIdx.x & 31;
+    const int w0 = strip * OWN;
+    if (w0 > g.nx) return;
+    const int c0 = w0 - VW + lane * VW;
+    const bool own = lane >= 1 && lane <= 30;
+    const int nx = g.nx, ny = g.ny;
+    const int cx = nx + 1, cy = nx;
+    const bool col_ok = c0 >= 0 && c0 < g.pitch;
+    const float ilap = (float)(1.0 / g.lap);
+    V *const st = reinterpret_cast<V *>(stage);
+    auto src = [&](int f, int j, int &row, int &nrows) -> const float * {
+        switch (f) {
+        case 0: row = j + 1; nrows = ny; return vx;
+        case 1: row = j + 1; nrows = ny + 1; return vy;
+        case 2: row = j + 1; nrows = ny + 1; return en;
+        case 3: row = j; nrows = ny; return ec;
+        case 4: row = j; nrows = ny; return fx;
+        case 5: row = j; nrows = ny + 1; return fy;
+        default: break;
+        }
+        row = j;
+        if (INV && f == EF::IX) { nrows = ny; return ix; }
+        if (INV && f == EF::IY) { nrows = ny + 1; return iy; }
+        nrows = ny;
+        return p;
+    };
+    auto issue = [&](int j) {
+        if (j < j1 && col_ok) {
+            V *const slot = st + (j % JR_PD) * N * 32 + lane;
+#pragma unroll
+            for (int f = 0; f < N; ++f) {
+                int row, nrows;
+                const float *q = src(f, j, row, nrows);
+                if (row >= 0 && row < nrows) cp_async16(slot + f * 32, q + (size_t)row * g.pitch + c0);
+            }
+        }
+        cp_async_commit();
+    };
+    auto take = [&](int f, int j, int cols, float(&a)[VW]) {
+        int row, nrows;
+        (void)src(f, j, row, nrows);
+        if (col_ok && row >= 0 && row < nrows) {
+            const V v = st[(j % JR_PD) * N * 32 + f * 32 + lane];
+            const float *e = reinterpret_cast<const float *>(&v);
+#pragma unroll
+            for (int k = 0; k < VW; ++k) a[k] = (c0 + k < cols) ? e[k] : 0.f;
+        } else {
+#pragma unroll
+            for (int k = 0; k < VW; ++k) a[k] = 0.f;
+        }
+    };
+#pragma unroll
+    for (int d = 0; d < JR_PD - 1; ++d) issue(j0 + d);
+
+    float vxC[VW], vyC[VW], enC[VW], ecS[VW], tyyS[VW], sxC[VW], syC[VW], pS[VW];
+    {
+        float vxS[VW], vyS[VW];
+        ld_row(vx, g, j0, c0, ny, cx, vxC);
+        ld_row(vy, g, j0, c0, ny + 1, cy, vyC);
+        ld_row(en, g, j0, c0, ny + 1, cx, enC);
+        ld_row(ec, g, j0 - 1, c0, ny, cy, ecS);
+        ld_row(vx, g, j0 - 1, c0, ny, cx, vxS);
+        ld_row(vy, g, j0 - 1, c0, ny + 1, cy, vyS);
+        if (HASP) ld_row(p, g, j0 - 1, c0, ny, cy, pS);
+        const float vyw = shfl_up1(vyC[VW - 1]);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+            tyyS[k] = flux_n(coef_y(g, ecS[k]), vyC[k], vyS[k]);
+            shear_xy<SQM>(g, enC[k], vxC[k], vxS[k], vyC[k], k ? vyC[k - 1] : vyw, sxC[k], syC[k]);
+        }
+    }
+    CompSum rv, rp, ff;
+    for (int j = j0; j < j1; ++j) {
+        issue(j + JR_PD - 1);
+        cp_async_wait<JR_PD - 1>();
+        float vxN[VW], vyN[VW], enN[VW], ecC[VW], fxC[VW], fyC[VW], pC[VW], ivx[VW], ivy[VW];
+        take(0, j, cx, vxN);
+        take(1, j, cy, vyN);
+        take(2, j, cx, enN);
+        take(3, j, cy, ecC);
+        take(4, j, cx, fxC);
+        take(5, j, cy, fyC);
+        if (INV) {
+            take(EF::IX, j, cx, ivx);
+            take(EF::IY, j, cy, ivy);
+        }
+        if (HASP) take(EF::P, j, cy, pC);
+        float sxN[VW], syN[VW];
+        {
+            const float vyw = shfl_up1(vyN[VW - 1]);
+#pragma unroll
+            for (int k = 0; k < VW; ++k)
+                shear_xy<SQM>(g, enN[k], vxN[k], vxC[k], vyN[k], k ? vyN[k - 1] : vyw, sxN[k], syN[k]);
+        }
+        float tyy[VW], txx[VW];
+        const float vxe = shfl_dn1(vxC[0]);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+            tyy[k] = flux_n(coef_y(g, ecC[k]), vyN[k], vyC[k]);
+            txx[k] = flux_n(coef_x(g, ecC[k]), k + 1 < VW ? vxC[k + 1] : vxe, vxC[k]);
+        }
+        const float txw = shfl_up1(txx[VW - 1]), ecw = shfl_up1(ecC[VW - 1]);
+        const float sye = shfl_dn1(syC[0]), ene = shfl_dn1(enC[0]);
+        const float pw = HASP ? shfl_up1(pC[VW - 1]) : 0.f;
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+            const int col = c0 + k;
+            float tv = 0.f, tf = 0.f;
+            bool any = false;
+            if (j < ny && col >= 1 && col <= nx - 1) { // vx unknown
+                const float m = m_x(txx[k], k ? txx[k - 1] : txw, sxN[k], sxC[k]);
+                const float wi = -(INV ? ivx[k] : inv_diag(diag_x(g, ecC[k], k ? ecC[k - 1] : ecw, enN[k], enC[k])));
+                const float b = HASP ? r_fma(r_sub(pC[k], k ? pC[k - 1] : pw), g.ihx, fxC[k]) : fxC[k];
+                const float r = r_sub(b, m);
+                tv = r_mul(r_mul(r, r), wi);
+                tf = r_mul(r_mul(fxC[k], fxC[k]), wi);
+                any = true;
+            }
+            if (col < nx && j >= 1 && j <= ny - 1) { // vy unknown
+                const float m = m_y(k + 1 < VW ? syC[k + 1] : sye, syC[k], tyy[k], tyyS[k]);
+                const float wi =
+                    -(INV ? ivy[k] : inv_diag(diag_y(g, ecC[k], ecS[k], k + 1 < VW ? enC[k + 1] : ene, enC[k])));
+                const float b = HASP ? r_fma(r_sub(pC[k], pS[k]), g.ihy, fyC[k]) : fyC[k];
+                const float r = r_sub(b, m);
+                const float a = r_mul(r_mul(r, r), wi), cf = r_mul(r_mul(fyC[k], fyC[k]), wi);
+                tv = any ? r_add(tv, a) : a;
+                tf = any ? r_add(tf, cf) : cf;
+                any = true;
+            }
+            if (own && any) {
+                rv.add(tv);
+                ff.add(tf);
+            }
+            if (own && j < ny && col < nx) { // the cell's divergence
+                const float dv = r_fma(r_sub(k + 1 < VW ? vxC[k + 1] : vxe, vxC[k]), g.ihx,
+                                       r_mul(r_sub(vyN[k], vyC[k]), g.ihy));
+                rp.add(r_mul(r_mul(dv, dv), r_mul(ecC[k], ilap)));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+            vxC[k] = vxN[k];
+            vyC[k] = vyN[k];
+            enC[k] = enN[k];
+            ecS[k] = ecC[k];
+            tyyS[k] = tyy[k];
+            sxC[k] = sxN[k];
+            syC[k] = syN[k];
+            if (HASP) pS[k] = pC[k];
+        }
+    }
+    cp_async_wait<0>(); // no copy outlives the band
+    rv.flush(s_rv);
+    rp.flush(s_rp);
+    ff.flush(s_ff);
+}
+
+constexpr int ER_MAX_BLOCKS = 152 * 4; // partial sums (the context holds energy_partials() of them)
+
+// Work items (a group of JR_WARPS column strips, a band of rows) in a fixed
+// order per block, so the sums are repeatable bit for bit.
+template <int SQM, bool INV, bool HASP>
+__global__ void __launch_bounds__(JR_WARPS * 32) k_energy_rows(GridDesc<float> g, const float *__restrict__ ec,
+                                                               const float *__restrict__ en,
+                                                               const float *__restrict__ fx,
+                                                               const float *__restrict__ fy,
+                                                               const float *__restrict__ ix,
+                                                               const float *__restrict__ iy,
+                                                               const float *__restrict__ p,
+                                                               const float *__restrict__ vx,
+                                                               const float *__restrict__ vy, int rows, int ngx,
+                                                               int nitems, double *__restrict__ partials)
+{
+    extern __shared__ __align__(16) unsigned char er_smem[];
+    const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    float *stage = reinterpret_cast<float *>(er_smem + (size_t)w * JR_PD * ErFields<INV, HASP>::N * 32 * 16);
+    double s_rv = 0.0, s_rp = 0.0, s_ff = 0.0;
+    for (int it = (int)blockIdx.x; it < nitems; it += (int)gridDim.x) {
+        const int gx = it % ngx, band = it / ngx;
+        const int j0 = band * rows, j1 = min(j0 + rows, g.ny + 1);
+        energy_band<SQM, INV, HASP>(g, ec, en, fx, fy, ix, iy, p, vx, vy, j0, j1, gx * JR_WARPS + w, stage, s_rv, s_rp,
+                                    s_ff);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s_rv += __shfl_down_sync(0xffffffffu, s_rv, o);
+        s_rp += __shfl_down_sync(0xffffffffu, s_rp, o);
+        s_ff += __shfl_down_sync(0xffffffffu, s_ff, o);
+    }
+    __shared__ double sh[3][JR_WARPS];
+    if (lane == 0) {
+        sh[0][w] = s_rv;
+        sh[1][w] = s_rp;
+        sh[2][w] = s_ff;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int q = 0; q < JR_WARPS; ++q) t += sh[threadIdx.x][q];
+        partials[(size_t)blockIdx.x * 3 + threadIdx.x] = t;
+    }
+}
+
 } // namespace
+
+cudaError_t launch_energy_rows(const GridDesc<float> &g, const float *eta_c, const float *eta_n, const float *fx,
+                               const float *fy, const float *inv_dx, const float *inv_dy, const float *p,
+                               const float *vx, const float *vy, double *partials, int *nblocks, cudaStream_t s)
+{
+    constexpr int OWN = 30 * 4;
+    const int strips = (g.nx + OWN) / OWN;
+    const int ngx = (strips + JR_WARPS - 1) / JR_WARPS;
+    const int rows = jacobi_rows_per_warp(g.nx, g.ny, 4);
+    const int nband = (g.ny + rows) / rows;
+    const int nitems = ngx * nband;
+    const int grid = std::min(nitems, ER_MAX_BLOCKS);
+    const size_t smem = (size_t)JR_WARPS * JR_PD * ErFields<true, true>::N * 32 * 16;
+    const int sel = (g.square ? 4 : 0) | (inv_dx && inv_dy ? 2 : 0) | (p ? 1 : 0);
+    cudaError_t e = cudaSuccess;
+    auto go = [&](auto kern) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            kern<<<grid, JR_WARPS * 32, smem, s>>>(g, eta_c, eta_n, fx, fy, inv_dx, inv_dy, p, vx, vy, rows, ngx,
+                                                   nitems, partials);
+    };
+    switch (sel) {
+    case 0: go(k_energy_rows<0, false, false>); break;
+    case 1: go(k_energy_rows<0, false, true>); break;
+    case 2: go(k_energy_rows<0, true, false>); break;
+    case 3: go(k_energy_rows<0, true, true>); break;
+    case 4: go(k_energy_rows<1, false, false>); break;
+    case 5: go(k_energy_rows<1, false, true>); break;
+    case 6: go(k_energy_rows<1, true, false>); break;
+    default: go(k_energy_rows<1, true, true>); break;
+    }
+    if (e != cudaSuccess) return e;
+    *nblocks = grid;
+    return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_jacobi(const GridDesc<T> &g, const Coeffs<T> &c, T omega, const T *vx, const T *vy, T *ox, T *oy,
