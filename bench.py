@@ -72,7 +72,7 @@ def parse():
     ap.add_argument("--robust-n", type=int, default=256, help="grid of the smoother robustness comparison")
     ap.add_argument("--n3d", type=int, default=384, help="cells per side of the 3D smoothing leg")
     ap.add_argument("--only", choices=["solve", "batch", "autotune", "c2", "uzawa", "robustness", "fp32err",
-                                       "smoothers", "smooth3d"],
+                                       "smoothers", "smooth3d", "slabs"],
                     help="run one extra leg alone and print its JSON (for profiling it)")
     return ap.parse_args()
 
@@ -460,6 +460,7 @@ def run_ours(args):
         line["smoother_robustness"] = robustness_leg(args, api)
         line["smooth3d"] = smooth3d_leg(args, api)
         line["global_smoothers"] = smoothers_leg(args, api)
+        line["slabs"] = slabs_leg(args, api)
         line["cpu_baseline"] = {kk: vv for kk, vv in cpu_sample(args, args.cpu_seconds).items() if kk != "seconds"}
         line["cpu_baseline"]["all_cores"] = cpu_sample_all_cores(args, args.cpu_seconds / 2)
     ctx.close()
@@ -974,6 +975,59 @@ def smoothers_leg(args, api):
     return out
 
 
+def slabs_leg(args, api):
+    """The slab decomposition of RAS (one slab per GPU in a multi-GPU run; here
+    every slab on this GPU): the benchmark's smoothing (FP32 layered sinker at
+    --n, RAS 48 x 64, k = 8, overlap 7, 100 sweeps) split into 2, 4 and 8 row
+    slabs against one context.  Per slab count: the time of one smoothing call
+    (CUDA events, one warm-up call first), Gcell-updates/s, the halo copies and
+    bytes of one call, and whether the result equals the single context bit
+    for bit."""
+    import torch
+    from paper_2509_19061_gb300 import inputs
+    n, sweeps = args.n, 100
+    kw = dict(variant="ras", sweeps=sweeps, tile=(48, 64), k=8, overlap=7, seed=1)
+    prob = inputs.layered_sinker(n, seed=4)
+    ctx = api.StokesContext(n, n, 1.0, 1.0, "f32")
+    ctx.set_problem(prob)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ref = (ctx.field(), ctx.field())
+    ctx.smooth(*ref, None, **kw)
+    for v in ref:
+        v.zero_()
+    e0.record(stream)
+    ctx.smooth(*ref, None, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out = {"workload": "layered_sinker_%dx%d_ras_f32_48x64_k8_o7_%dsweeps" % (n, n, sweeps),
+           "single": {"ms_per_call": ms, "gcell_updates_per_s": n * n * sweeps / (ms / 1e3) / 1e9}}
+    eta_c, eta_n = ctx.pack(prob.eta_c, "eta_c"), ctx.pack(prob.eta_n, "eta_n")
+    fx, fy = ctx.pack(prob.fx, "fx"), ctx.pack(prob.fy, "fy")
+    for ns in (2, 4, 8):
+        sl = api.SlabContext(n, n, 1.0, 1.0, "f32", ns)
+        sl.set_viscosity_dev(eta_c, eta_n)
+        sl.set_rhs_dev(fx, fy)
+        vx, vy = ctx.field(), ctx.field()
+        sl.smooth(vx, vy, None, **kw)
+        vx.zero_()
+        vy.zero_()
+        c0 = sl.exchanges()
+        e0.record(stream)
+        sl.smooth(vx, vy, None, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        c1 = sl.exchanges()
+        out["slabs_%d" % ns] = {"ms_per_call": ms, "gcell_updates_per_s": n * n * sweeps / (ms / 1e3) / 1e9,
+                                "halo_copies_per_call": c1[0] - c0[0], "halo_bytes_per_call": c1[1] - c0[1],
+                                "bitwise_equal_single": bool(torch.equal(vx, ref[0]) and torch.equal(vy, ref[1]))}
+        sl.close()
+    ctx.close()
+    return out
+
+
 WORDS_PER_CELL_SWEEP_3D = 13  # read vx, vy, vz, eta_c, eta_xy, eta_xz, eta_yz, bx, by, bz; write vx, vy, vz
 
 
@@ -1074,7 +1128,7 @@ def run_only(args):
         return 0
     leg = {"solve": solve_times, "batch": batch_leg, "autotune": autotune_leg, "c2": c2_table,
            "uzawa": uzawa_leg, "robustness": robustness_leg, "smoothers": smoothers_leg,
-           "smooth3d": smooth3d_leg}[args.only]
+           "smooth3d": smooth3d_leg, "slabs": slabs_leg}[args.only]
     print(json.dumps({"leg": args.only, "result": leg(args, api)}))
     return 0
 
