@@ -679,10 +679,9 @@ __device__ __forceinline__ void energy_band(const GridDesc<float> &g, const floa
     ff.flush(s_ff);
 }
 
-constexpr int ER_MAX_BLOCKS = 152 * 4; // partial sums (the context holds energy_partials() of them)
-
 // Work items (a group of JR_WARPS column strips, a band of rows) in a fixed
-// order per block, so the sums are repeatable bit for bit.
+// order per block (at most energy_partials() blocks, one partial triple
+// each), so the sums are repeatable bit for bit.
 template <int SQM, bool INV, bool HASP>
 __global__ void __launch_bounds__(JR_WARPS * 32) k_energy_rows(GridDesc<float> g, const float *__restrict__ ec,
                                                                const float *__restrict__ en,
@@ -737,7 +736,7 @@ cudaError_t launch_energy_rows(const GridDesc<float> &g, const float *eta_c, con
     const int rows = jacobi_rows_per_warp(g.nx, g.ny, 4);
     const int nband = (g.ny + rows) / rows;
     const int nitems = ngx * nband;
-    const int grid = std::min(nitems, ER_MAX_BLOCKS);
+    const int grid = std::min(nitems, energy_partials()); // the partial triples the caller holds
     const size_t smem = (size_t)JR_WARPS * JR_PD * ErFields<true, true>::N * 32 * 16;
     const int sel = (g.square ? 4 : 0) | (inv_dx && inv_dy ? 2 : 0) | (p ? 1 : 0);
     cudaError_t e = cudaSuccess;
