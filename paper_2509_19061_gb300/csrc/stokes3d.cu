@@ -338,9 +338,9 @@ struct UAcc {
 // the same arithmetic without extent or unknown tests.  FP32 decides per
 // point (only warps at the domain's faces take both paths); FP64, bound by
 // its FP64 pipe, per block (measured: 4.8 against 3.9 Gcell-updates/s per
-// point at 192^3).
+// point at 192^3).  FP32 runs five blocks per SM (48 registers, no spills).
 template <typename T>
-__global__ void k3_jacobi(G3<T> g, GAcc<T> a, C3<T> c, T omega, T *__restrict__ ox, T *__restrict__ oy,
+__global__ void __launch_bounds__(B3X * B3Y * B3Z, sizeof(T) == 4 ? 5 : 4) k3_jacobi(G3<T> g, GAcc<T> a, C3<T> c, T omega, T *__restrict__ ox, T *__restrict__ oy,
                           T *__restrict__ oz)
 {
     const int i0 = blockIdx.x * B3X, j0 = blockIdx.y * B3Y, k0 = blockIdx.z * B3Z;
