@@ -137,6 +137,27 @@ def test_energy_norm_f32(api, with_p):
     assert r.ctx.energy(r.vx, r.vy, r.p) == got
 
 
+@pytest.mark.parametrize("n,l,with_p", [((1000, 1000), (1.0, 1.0), False), ((1000, 1000), (1.0, 1.0), True),
+                                        ((513, 301), (1.3, 0.9), True)])
+def test_energy_norm_f32_many_strips(api, n, l, with_p):
+    """The FP32 energy sums on grids of many column strips and row bands, on
+    square cells (the square-cell shear form) and on hx != hy, with and
+    without pressure: against the oracle on the FP32-rounded inputs (1e-5
+    relative) and repeatable bit for bit."""
+    nx, ny = n
+    prob = rand_problem(nx, ny, 7, lx=l[0], ly=l[1])
+    vx, vy = inputs.random_velocity(nx, ny, 8, 1e-3)
+    p = inputs.random_pressure(nx, ny, 9) if with_p else None
+    r = Run(api, prob, "f32", (vx, vy), p)
+    got = r.ctx.energy(r.vx, r.vy, r.p)
+    f32 = lambda a: None if a is None else np.asarray(a, dtype=np.float32).astype(np.float64)
+    g32 = ora.Grid(nx, ny, prob.hx, prob.hy, f32(prob.eta_c), f32(prob.eta_n))
+    want = ora.energy(g32, f32(prob.fx), f32(prob.fy), f32(p), f32(vx), f32(vy))
+    for a, b in zip(got, want):
+        assert abs(a - b) <= 1e-5 * abs(b), (a, b)
+    assert r.ctx.energy(r.vx, r.vy, r.p) == got
+
+
 def test_energy_norm_is_one_at_zero_state(api):
     prob = inputs.sinker_problem(64)
     r = Run(api, prob, "f64")

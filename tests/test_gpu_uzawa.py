@@ -113,6 +113,22 @@ def test_uzawa_f64_matches_the_oracle(api, case):
     assert abs(v[2].mean()) <= 1e-12 * np.abs(v[2]).max()
 
 
+def test_uzawa_fp32_context_follows_the_oracle(api):
+    """An FP32 context (FP32 fields, sweeps, energy sums with the continuation's
+    viscosity and 1/diag formed from it): thirty Uzawa cycles with
+    continuation follow the oracle's residual history to FP32 accuracy (each
+    cycle adds rounding of order 1e-7 relative to the iterate, which the
+    iteration carries along: measured 1.6e-5, bound 2e-4)."""
+    nx, ny = 96, 72
+    prob = inputs.sinker_problem(nx, ny, eta_in=1e2, ly=ny / nx)
+    sm = dict(variant="ras", tile=(16, 16), k=2, overlap=1, seed=3, nu_max=12)
+    st, hist, cyc, e, v = gpu_uzawa(api, prob, dtype="f32", cycles=30, theta_interval=8, inner="f32", **sm)
+    rx, ry, rp, rh = ora.uzawa(ogrid(prob), prob.fx, prob.fy, oracle_mg(sm), 30, theta_interval=8)
+    dev = float(np.max(np.abs(hist - rh) / rh))
+    print("fp32 context: max relative deviation of the residual history %.2e" % dev)
+    assert cyc == 30 and dev <= 2e-4
+
+
 @pytest.mark.parametrize("inner", ["f64", "f32"])
 def test_uzawa_with_continuation_converges_at_contrast_1e6(api, inner):
     """The configuration of Sec. 6.2 on the 128^2 sinker at contrast 1e6:
