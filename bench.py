@@ -248,6 +248,43 @@ def cpu_sample_all_cores(args, target_s, reps=5):
                                                                 sweeps)}
 
 
+def cpu_vcycle_solve(api, n=512):
+    """The V-cycle solve of the time-to-1e-8 workload on the host, bounded: the
+    FP64 oracle's flexible CG around its V-cycle (RAS 32 x 32, k = 4,
+    overlap 3, 5/5 sweeps x2.5 per level capped at 40, dense coarsest) to
+    E_v <= 1e-8 on the multi-sinker at n^2, one thread; beside it the GPU's
+    solve of the same instance with FP64 and with FP32 sweeps (the same
+    schedule, FP64 outer flexible CG)."""
+    import torch
+    import oracle as ora
+    from paper_2509_19061_gb300 import inputs
+    prob = inputs.multi_sinker(n, seed=3)
+    g = ora.Grid(n, n, prob.hx, prob.hy, prob.eta_c, prob.eta_n)
+    mg = ora.MG(variant=4, ti=32, tj=32, k=4, overlap=3, nu_max=40, seed=1)
+    t0 = time.perf_counter()
+    _, _, its, fe, _ = ora.mg_fcg(g, prob.fx, prob.fy, None, mg, 1e-8, 200)
+    cpu_s = time.perf_counter() - t0
+    out = {"workload": "multi_sinker_%dx%d_seed3" % (n, n), "tol": 1e-8,
+           "oracle": {"seconds": cpu_s, "cycles": its, "final_energy_residual": fe, "cores": 1}}
+    ctx = api.StokesContext(n, n, 1.0, 1.0, "f64")
+    ctx.set_problem(prob)
+    vx, vy = ctx.field(), ctx.field()
+    for inner in ("f64", "f32"):
+        kw = dict(variant="ras", tile=(32, 32), k=4, overlap=3, seed=1, nu_max=40, inner=inner, krylov=True,
+                  tol=1e-8, max_cycles=200)
+        ctx.vcycle(vx, vy, None, **kw)
+        vx.zero_()
+        vy.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, e, cyc = ctx.vcycle(vx, vy, None, **kw)
+        torch.cuda.synchronize()
+        out["gpu_" + inner + "_inner"] = {"seconds": time.perf_counter() - t0, "cycles": cyc, "final_energy_residual": e,
+                                          "status": st}
+    ctx.close()
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -463,6 +500,7 @@ def run_ours(args):
         line["slabs"] = slabs_leg(args, api)
         line["cpu_baseline"] = {kk: vv for kk, vv in cpu_sample(args, args.cpu_seconds).items() if kk != "seconds"}
         line["cpu_baseline"]["all_cores"] = cpu_sample_all_cores(args, args.cpu_seconds / 2)
+        line["cpu_baseline"]["vcycle_solve"] = cpu_vcycle_solve(api)
     ctx.close()
     if rank == 0:
         print(json.dumps(line))
