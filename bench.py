@@ -817,10 +817,13 @@ def robustness_leg(args, api):
     # unit square keeps hx != hy and four halvings' coarsest level (20 x 24,
     # 916 unknowns) within the dense coarsest solve.
     out["paper_schedule"] = robustness_run(api, 160, 192, cycles=1000, levels=4, nu_max=0)
+    # the same grid with the default hierarchy and eight CG steps (each one
+    # V-cycle) per Uzawa cycle: one step is too inexact a velocity solve there
+    out["hx_ne_hy_8_steps"] = robustness_run(api, 160, 192, cycles=300, levels=16, nu_max=40, vel_its=8)
     return out
 
 
-def robustness_run(api, nx, ny, cycles, levels, nu_max):
+def robustness_run(api, nx, ny, cycles, levels, nu_max, vel_its=1):
     import torch
     from paper_2509_19061_gb300 import inputs
     prob = inputs.sinker_problem(nx, ny, eta_in=1e8)
@@ -830,7 +833,7 @@ def robustness_run(api, nx, ny, cycles, levels, nu_max):
     marks = [c for c in (25, 50, 100, 150, 200, 300, 500, 750, 1000) if c <= cycles]
     out = {"workload": "sinker_%dx%d_contrast1e8" % (nx, ny), "cycles": cycles, "levels": levels,
            "sweeps": "5 x 2.5^level pre and post" + (", capped at %d" % nu_max if nu_max else ", uncapped"),
-           "uzawa": "continuation 5 x 25 cycles, 1 CG step of one V-cycle per cycle, omega_p 0.6",
+           "uzawa": "continuation 5 x 25 cycles, %d CG step(s) of one V-cycle per cycle, omega_p 0.6" % vel_its,
            "report": "worst seed: max over seeds of the residual at each mark; cycles to 1e-8 (-1: not reached)"}
     for name, sm, seeds in (("rbgs", dict(variant="rbgs"), [0]), ("jacobi", dict(variant="jacobi"), [0]),
                             ("ras", dict(variant="ras", tile=(32, 32), k=4, overlap=0), range(10)),
@@ -842,7 +845,7 @@ def robustness_run(api, nx, ny, cycles, levels, nu_max):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             st, hist, cyc, e = ctx.uzawa(vx, vy, p, cycles=cycles, theta_interval=25, inner="f32", nu_max=nu_max,
-                                         levels=levels, seed=sd, **sm)
+                                         levels=levels, seed=sd, vel_its=vel_its, **sm)
             torch.cuda.synchronize()
             secs += time.perf_counter() - t0
             h = np.asarray(hist)
