@@ -387,7 +387,7 @@ int stokes_tile_kernel_plan(int nx, int ny, int ti, int tj, int overlap, int dty
  * anything else returns STOKES_ERR_ARG, as do NULL inputs or a bad dtype.
  * The reduction writes one triple of partial sums per block: if the library's
  * energy reduction ran more than the array's 608 blocks, the call would
- * return STOKES_ERR_ARG (this build runs exactly 608).  CUDA failures return
+ * return STOKES_ERR_ARG (the library runs exactly 608).  CUDA failures return
  * STOKES_ERR_CUDA. */
 int stokes_energy_norm_noalloc(int nx, int ny, double lx, double ly, int dtype, int pitch, const void *eta_c,
                                const void *eta_n, const void *fx, const void *fy, const void *p, const void *vx,
