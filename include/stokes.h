@@ -14,8 +14,8 @@
  * (ny+1) rows x `pitch` elements of the context's dtype (row j starts at
  * element j*pitch), whatever the field; stokes_get_layout returns the pitch
  * and each field's own extent.  Every field buffer starts on a 16-byte
- * boundary (any cudaMalloc or torch allocation does; the smoothing entry
- * points return STOKES_ERR_ARG otherwise).  Entries outside a field's extent
+ * boundary (any cudaMalloc or torch allocation does; the smoothing, solve and
+ * energy entry points return STOKES_ERR_ARG otherwise).  Entries outside a field's extent
  * are padding: their values are never used (the kernels may read the bytes,
  * which lie inside the buffer), and output buffers get zeros there.  The unknowns are
  * vx with 1 <= i <= nx-1 and vy with 1 <= j <= ny-1; the wall entries
@@ -212,7 +212,8 @@ int stokes_smooth(stokes_ctx *ctx, void *vx, void *vy, const void *p, const stok
  *   out[2] = sum over velocity unknowns of f^2 / (-diag M)
  * The relative energy residual is sqrt((out[0] + out[1]) / out[2]).  p may be
  * NULL.  `out` is host memory; the call synchronises the context's stream.
- * The summation order is fixed, so repeated calls give identical bits. */
+ * The summation order is fixed, so repeated calls give identical bits.
+ * STOKES_ERR_ARG if vx, vy or p does not start on a 16-byte boundary. */
 int stokes_residual_energy_norm(stokes_ctx *ctx, const void *vx, const void *vy, const void *p, double out[3]);
 
 /* Solve M v = f - G p with a geometric-multigrid V-cycle B (Sec. 3.2) as the

@@ -1030,6 +1030,7 @@ int stokes_smooth(stokes_ctx *c, void *vx, void *vy, const void *p, const stokes
 int stokes_residual_energy_norm(stokes_ctx *c, const void *vx, const void *vy, const void *p, double out[3])
 {
     if (!c || !vx || !vy || !out) return STOKES_ERR_ARG;
+    if (!aligned16(vx) || !aligned16(vy) || !aligned16(p)) return STOKES_ERR_ARG; // vector row loads
     if (!c->have_eta || !c->have_f) return STOKES_ERR_STATE;
     if (c->dtype == STOKES_F64) return energy_impl<double>(c, (const double *)vx, (const double *)vy, (const double *)p, out);
     return energy_impl<float>(c, (const float *)vx, (const float *)vy, (const float *)p, out);

@@ -158,6 +158,26 @@ def test_energy_norm_f32_many_strips(api, n, l, with_p):
     assert r.ctx.energy(r.vx, r.vy, r.p) == got
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_entry_points_reject_buffers_off_16_byte_boundaries(api, dtype):
+    """The kernels read rows as 16-byte vectors and stage windows by tensor
+    copies, so a velocity or pressure buffer that does not start on a
+    16-byte boundary is refused (STOKES_ERR_ARG) before any kernel runs."""
+    prob = inputs.sinker_problem(64)
+    r = Run(api, prob, dtype)
+    off = r.vx.view(-1)[1:]  # one element past the allocation's start
+    for call in (lambda: r.ctx.smooth(off, r.vy, None, variant="fused", sweeps=1),
+                 lambda: r.ctx.smooth(r.vx, r.vy, off, variant="ras", sweeps=2, tile=(16, 16), k=2, overlap=1),
+                 lambda: r.ctx.energy(r.vx, off),
+                 lambda: r.ctx.energy(r.vx, r.vy, off),
+                 lambda: r.ctx.vcycle(off, r.vy, None, variant="fused", max_cycles=1)):
+        with pytest.raises(api.StokesError) as e:
+            call()
+        assert e.value.status == api.STOKES_ERR_ARG
+    rv, rp, ff = r.ctx.energy(r.vx, r.vy)  # the context stays usable
+    assert rp == 0.0 and ff > 0.0
+
+
 def test_energy_norm_is_one_at_zero_state(api):
     prob = inputs.sinker_problem(64)
     r = Run(api, prob, "f64")
