@@ -568,6 +568,267 @@ __global__ void __launch_bounds__(R3_THREADS) k3_ras(G3<T> g, GAcc<T> a, C3<T> c
     }
 }
 
+// ---- RAS-Jacobi on 3D tiles, column form ------------------------------------------
+// The same map as k3_ras (and, for overlap >= k - 1, as k3_jacobi), for windows
+// of 16 to 32 x at most WY x at most WZ cells: one warp per window row (lane =
+// x, warp = y), each thread holding its window column of WZ cells (z) of the
+// velocity and the four viscosities in registers.  Every flux is formed once
+// per sweep by the cell that owns it; x neighbours (velocity and flux) move by
+// shuffles, z neighbours are in the thread's own registers, and only the y
+// neighbours go through shared memory: the velocity (vx, vy, vz) and the
+// three fluxes read across rows (sigma'_xy, Tyy, sigma'_yz), one plane per
+// window level and field, rows padded by one on each side.  The right-hand
+// side and 1/diag of the levels 1 .. WZ - 2 are copied to shared memory once
+// per tile (cp.async, no registers), so the updates read no global memory
+// (from global memory they waited on L2 once per level).  A sweep is two
+// phases, a barrier after each: (A) the row-crossing fluxes from the staged
+// velocity, (B) the updates, the remaining fluxes carried along z in
+// registers, and the new velocity.  Both phases run over every level as
+// straight-line code (the sweep's region selects which results are kept), so
+// the compiler interleaves the levels' dependency chains; the window strides
+// are compile-time constants.  Every value is the rounded arithmetic of op3_*,
+// in its order, so the results equal those of the other kernels bit for bit.
+// Window cells outside the tile's window (lanes beyond 2 h + tile width, rows
+// and levels beyond 2 h + tile extent) are staged but never updated, and no
+// updated cell reads them.
+constexpr int RC_FIELDS = 6;
+constexpr size_t RC_SMEM_MAX = 227 * 1024;
+
+// one element global -> shared, asynchronously; zero-filled when !valid
+// (src must still be a valid address)
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *smem, const T *src, bool valid)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if (sizeof(T) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(s), "l"(src), "r"(valid ? 8 : 0) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(s), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+
+template <typename T, int WZ, int WY, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k3_ras_col(G3<T> g, GAcc<T> a, C3<T> c, T omega, Tiles3 tg, int ks,
+                                                      int overlap, T *__restrict__ ox, T *__restrict__ oy,
+                                                      T *__restrict__ oz)
+{
+    static_assert(32 * WY <= MAXT, "one warp per window row");
+    constexpr int PS = (WY + 2) * 32;      // one level of an exchange field
+    constexpr int FS = WZ * PS;            // one exchange field
+    constexpr int BS = (WZ - 2) * WY * 32; // one field of b / (1/diag)
+    extern __shared__ __align__(16) unsigned char rc_raw[];
+    T *const sm = reinterpret_cast<T *>(rc_raw);
+    const int lane = (int)threadIdx.x, w = (int)threadIdx.y;
+    const int tile = (int)blockIdx.x;
+    const int tbx = tile % tg.ntx, tby = (tile / tg.ntx) % tg.nty, tbz = tile / (tg.ntx * tg.nty);
+    int x0, x1, y0, y1, z0, z1;
+    tile_iv(g.nx, tg.ti, tg.si, tbx, x0, x1);
+    tile_iv(g.ny, tg.tj, tg.sj, tby, y0, y1);
+    tile_iv(g.nz, tg.tk, tg.sk, tbz, z0, z1);
+    const int h = overlap + 1;
+    const int ox0 = x0 - h, oy0 = y0 - h, oz0 = z0 - h;
+    const int gi = ox0 + lane, gj = oy0 + w;
+    // this thread's entries: exchange planes (row w + 1 of each level), and
+    // b / (1/diag) (row w of each level 1 .. WZ - 2; fields b_x, b_y, b_z,
+    // 1/diag_x, 1/diag_y, 1/diag_z)
+    T *const xv = sm + (w + 1) * 32 + lane;
+    T *const bw = sm + RC_FIELDS * FS + w * 32 + lane;
+    if (w >= 1 && w < WY - 1) { // the rows a sweep can update
+        const bool xv_ = gi >= 0 && gi <= g.nx, xc = gi >= 0 && gi < g.nx;
+        const bool yc = gj >= 0 && gj < g.ny, yv = gj >= 0 && gj <= g.ny;
+#pragma unroll
+        for (int kk = 1; kk < WZ - 1; ++kk) {
+            const int gk = oz0 + kk;
+            const bool zc = gk >= 0 && gk < g.nz, zv = gk >= 0 && gk <= g.nz;
+            const bool okx = xv_ && yc && zc, oky = xc && yv && zc, okz = xc && yc && zv;
+            const size_t q = (okx || oky || okz) ? g.at(gk, gj, gi) : 0;
+            T *const d = bw + (kk - 1) * WY * 32;
+            cp_async_elem(d, c.bx + (okx ? q : 0), okx);
+            cp_async_elem(d + BS, c.by + (oky ? q : 0), oky);
+            cp_async_elem(d + 2 * BS, c.bz + (okz ? q : 0), okz);
+            cp_async_elem(d + 3 * BS, c.ix + (okx ? q : 0), okx);
+            cp_async_elem(d + 4 * BS, c.iy + (oky ? q : 0), oky);
+            cp_async_elem(d + 5 * BS, c.iz + (okz ? q : 0), okz);
+        }
+    }
+    T vx[WZ], vy[WZ], vz[WZ], ec[WZ], exy[WZ], exz[WZ], eyz[WZ];
+    // stage the column (zero outside each field's extent); a window inside
+    // the cells of the grid lies inside every extent and is read without tests
+    const bool inside = ox0 >= 0 && oy0 >= 0 && oz0 >= 0 && ox0 + 32 <= g.nx && oy0 + WY <= g.ny && oz0 + WZ <= g.nz;
+    if (inside) {
+        const size_t q0 = g.at(oz0, gj, gi);
+#pragma unroll
+        for (int kk = 0; kk < WZ; ++kk) {
+            const size_t q = q0 + (size_t)kk * g.plane;
+            vx[kk] = a.x[q];
+            vy[kk] = a.y[q];
+            vz[kk] = a.z[q];
+            ec[kk] = a.c[q];
+            exy[kk] = a.xy[q];
+            exz[kk] = a.xz[q];
+            eyz[kk] = a.yz[q];
+        }
+    } else {
+#pragma unroll
+        for (int kk = 0; kk < WZ; ++kk) {
+            const int gk = oz0 + kk;
+            vx[kk] = a.vx(gk, gj, gi);
+            vy[kk] = a.vy(gk, gj, gi);
+            vz[kk] = a.vz(gk, gj, gi);
+            ec[kk] = a.ec(gk, gj, gi);
+            exy[kk] = a.exy(gk, gj, gi);
+            exz[kk] = a.exz(gk, gj, gi);
+            eyz[kk] = a.eyz(gk, gj, gi);
+        }
+    }
+#pragma unroll
+    for (int kk = 0; kk < WZ; ++kk) {
+        xv[kk * PS] = vx[kk];
+        xv[FS + kk * PS] = vy[kk];
+        xv[2 * FS + kk * PS] = vz[kk];
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    const int lx0 = max(x0 - overlap, 0), lx1 = min(x1 + overlap, g.nx);
+    const int ly0 = max(y0 - overlap, 0), ly1 = min(y1 + overlap, g.ny);
+    const int lz0 = max(z0 - overlap, 0), lz1 = min(z1 + overlap, g.nz);
+    const unsigned full = 0xffffffffu;
+    for (int s = 1; s <= ks; ++s) {
+        // cells within min(overlap, ks - s) of the tile are updated; in window
+        // coordinates the lanes [ax0, ax1), rows [ay0, ay1) and levels
+        // [az0, az1), all inside [1, extent - 1)
+        const int r = min(overlap, ks - s);
+        const int ax0 = max(x0 - r, lx0) - ox0, ax1 = min(x1 + r, lx1) - ox0;
+        const int ay0 = max(y0 - r, ly0) - oy0, ay1 = min(y1 + r, ly1) - oy0;
+        const int az0 = max(z0 - r, lz0) - oz0, az1 = min(z1 + r, lz1) - oz0;
+        // (A) sigma'_xy, Tyy and sigma'_yz of rows ay0 - 1 .. ay1, levels 1 .. WZ - 1
+        if (w >= ay0 - 1 && w <= ay1) {
+#pragma unroll
+            for (int kk = 1; kk < WZ; ++kk) {
+                const T vys = __shfl_up_sync(full, vy[kk], 1);
+                const T vxs = xv[kk * PS - 32], vyn = xv[FS + kk * PS + 32], vzs = xv[2 * FS + kk * PS - 32];
+                xv[3 * FS + kk * PS] = r_mul(exy[kk], r_fma(r_sub(vx[kk], vxs), g.ihy, r_mul(r_sub(vy[kk], vys), g.ihx)));
+                xv[4 * FS + kk * PS] = r_mul(r_mul(r_add(ec[kk], ec[kk]), g.ihy2), r_sub(vyn, vy[kk]));
+                xv[5 * FS + kk * PS] =
+                    r_mul(eyz[kk], r_fma(r_sub(vy[kk], vy[kk - 1]), g.ihz, r_mul(r_sub(vz[kk], vzs), g.ihy)));
+            }
+        }
+        __syncthreads();
+        // (B) the updates of rows ay0 .. ay1 - 1; sigma'_xz(kk) and Tzz(kk - 1)
+        // are carried from the level below, all formed from the velocity
+        // before this sweep (level kk's update reads no level below kk)
+        if (w >= ay0 && w < ay1) {
+            const bool xin = lane >= ax0 && lane < ax1;
+            const bool ux = xin && gi >= 1, uy = xin && gj >= 1;
+            T sxz = r_mul(exz[1], r_fma(r_sub(vx[1], vx[0]), g.ihz, r_mul(r_sub(vz[1], __shfl_up_sync(full, vz[1], 1)), g.ihx)));
+            T tzz_d = r_mul(r_mul(r_add(ec[0], ec[0]), g.ihz2), r_sub(vz[1], vz[0]));
+#pragma unroll
+            for (int kk = 1; kk < WZ - 1; ++kk) {
+                const T vxe = __shfl_down_sync(full, vx[kk], 1);
+                const T txx_c = r_mul(r_mul(r_add(ec[kk], ec[kk]), g.ihx2), r_sub(vxe, vx[kk]));
+                const T txx_w = __shfl_up_sync(full, txx_c, 1);
+                const T vzw_u = __shfl_up_sync(full, vz[kk + 1], 1);
+                const T sxz_u =
+                    r_mul(exz[kk + 1], r_fma(r_sub(vx[kk + 1], vx[kk]), g.ihz, r_mul(r_sub(vz[kk + 1], vzw_u), g.ihx)));
+                const T tzz_c = r_mul(r_mul(r_add(ec[kk], ec[kk]), g.ihz2), r_sub(vz[kk + 1], vz[kk]));
+                const T sxy_c = xv[3 * FS + kk * PS], sxy_n = xv[3 * FS + kk * PS + 32];
+                const T tyy_c = xv[4 * FS + kk * PS], tyy_s = xv[4 * FS + kk * PS - 32];
+                const T syz_c = xv[5 * FS + kk * PS], syz_n = xv[5 * FS + kk * PS + 32];
+                const T syz_u = xv[5 * FS + (kk + 1) * PS];
+                const T sxy_e = __shfl_down_sync(full, sxy_c, 1);
+                const T sxz_e = __shfl_down_sync(full, sxz, 1);
+                const T mx = r_add(r_add(r_sub(txx_c, txx_w), r_sub(r_mul(sxy_n, g.ihy), r_mul(sxy_c, g.ihy))),
+                                   r_sub(r_mul(sxz_u, g.ihz), r_mul(sxz, g.ihz)));
+                const T my = r_add(r_add(r_sub(r_mul(sxy_e, g.ihx), r_mul(sxy_c, g.ihx)), r_sub(tyy_c, tyy_s)),
+                                   r_sub(r_mul(syz_u, g.ihz), r_mul(syz_c, g.ihz)));
+                const T mz = r_add(r_add(r_sub(r_mul(sxz_e, g.ihx), r_mul(sxz, g.ihx)),
+                                         r_sub(r_mul(syz_n, g.ihy), r_mul(syz_c, g.ihy))),
+                                   r_sub(tzz_c, tzz_d));
+                sxz = sxz_u;
+                tzz_d = tzz_c;
+                const T *const e = bw + (kk - 1) * WY * 32;
+                const bool lev = kk >= az0 && kk < az1;
+                if (lev && ux) vx[kk] = jacobi_update(vx[kk], e[0], mx, jacobi_weight(omega, e[3 * BS]));
+                if (lev && uy) vy[kk] = jacobi_update(vy[kk], e[BS], my, jacobi_weight(omega, e[4 * BS]));
+                if (lev && xin && oz0 + kk >= 1)
+                    vz[kk] = jacobi_update(vz[kk], e[2 * BS], mz, jacobi_weight(omega, e[5 * BS]));
+                xv[kk * PS] = vx[kk];
+                xv[FS + kk * PS] = vy[kk];
+                xv[2 * FS + kk * PS] = vz[kk];
+            }
+        }
+        __syncthreads();
+    }
+    // write back the unknowns of the tile's own cells
+    if (w >= h && w < h + (y1 - y0) && lane >= h && lane < h + (x1 - x0)) {
+        const size_t q0 = g.at(oz0, gj, gi);
+#pragma unroll
+        for (int kk = 1; kk < WZ - 1; ++kk) {
+            if (kk >= h && kk < h + (z1 - z0)) {
+                const size_t q = q0 + (size_t)kk * g.plane;
+                if (gi >= 1) ox[q] = vx[kk];
+                if (gj >= 1) oy[q] = vy[kk];
+                if (oz0 + kk >= 1) oz[q] = vz[kk];
+            }
+        }
+    }
+}
+
+// the column kernels: FP32 up to 16 rows (8 levels) or 12 rows (12 levels), FP64 8 x 8
+template <typename T>
+struct RasCol {
+    static constexpr int MAXT = sizeof(T) == 4 ? 512 : 256;
+};
+
+size_t rc_smem(int wz, int wy, size_t es)
+{
+    return ((size_t)RC_FIELDS * wz * (wy + 2) + (size_t)6 * (wz - 2) * wy) * 32 * es;
+}
+
+// the column kernel's window (levels wz, rows wy) for a tile; wz = 0 when it
+// does not apply (the window must span 16 to 32 lanes and fit one of the
+// instantiated shapes and the shared memory)
+template <typename T>
+void ras_col_shape(int ti, int tj, int tk, int overlap, int nx, int ny, int nz, int &wz, int &wy)
+{
+    const int h = overlap + 1;
+    const int wx = std::min(ti, nx) + 2 * h, ny_ = std::min(tj, ny) + 2 * h, nz_ = std::min(tk, nz) + 2 * h;
+    wz = 0;
+    wy = 0;
+    if (wx < 16 || wx > 32) return;
+    if (sizeof(T) == 8) {
+        if (nz_ <= 8 && ny_ <= 8) wz = 8, wy = 8;
+    } else if (nz_ <= 8) {
+        wz = 8;
+        wy = ny_ <= 8 ? 8 : ny_ <= 12 ? 12 : ny_ <= 16 ? 16 : 0;
+    } else if (nz_ <= 12) {
+        wz = 12;
+        wy = ny_ <= 8 ? 8 : ny_ <= 12 ? 12 : 0;
+    }
+    if (!wy || rc_smem(wz, wy, sizeof(T)) > RC_SMEM_MAX) wz = wy = 0;
+}
+
+template <typename T>
+using ras_col_fn = void (*)(G3<T>, GAcc<T>, C3<T>, T, Tiles3, int, int, T *, T *, T *);
+
+template <typename T>
+ras_col_fn<T> ras_col_kernel(int wz, int wy);
+template <>
+ras_col_fn<float> ras_col_kernel<float>(int wz, int wy)
+{
+    if (wz == 8 && wy == 8) return k3_ras_col<float, 8, 8, 512>;
+    if (wz == 8 && wy == 12) return k3_ras_col<float, 8, 12, 512>;
+    if (wz == 8 && wy == 16) return k3_ras_col<float, 8, 16, 512>;
+    if (wz == 12 && wy == 8) return k3_ras_col<float, 12, 8, 512>;
+    if (wz == 12 && wy == 12) return k3_ras_col<float, 12, 12, 512>;
+    return nullptr;
+}
+template <>
+ras_col_fn<double> ras_col_kernel<double>(int wz, int wy)
+{
+    if (wz == 8 && wy == 8) return k3_ras_col<double, 8, 8, 256>;
+    return nullptr;
+}
+
 size_t r3_smem(int ti, int tj, int tk, int overlap, size_t es, int nx, int ny, int nz)
 {
     const int h = overlap + 1;
@@ -741,8 +1002,16 @@ int smooth_impl(stokes3d_ctx *c, T *vx, T *vy, T *vz, const T *p, const stokes3d
         }
     } else {
         const int ti = prm->tile_i, tj = prm->tile_j, tk = prm->tile_k;
-        const size_t smem = r3_smem(ti, tj, tk, prm->overlap, sizeof(T), c->nx, c->ny, c->nz);
-        CK(cudaFuncSetAttribute(k3_ras<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        // windows of 16 to 32 lanes take the column kernel, others the general one
+        int wz = 0, wyk = 0;
+        ras_col_shape<T>(ti, tj, tk, prm->overlap, c->nx, c->ny, c->nz, wz, wyk);
+        void (*col)(G3<T>, GAcc<T>, C3<T>, T, Tiles3, int, int, T *, T *, T *) = ras_col_kernel<T>(wz, wyk);
+        const size_t smem = col ? rc_smem(wz, wyk, sizeof(T))
+                                : r3_smem(ti, tj, tk, prm->overlap, sizeof(T), c->nx, c->ny, c->nz);
+        if (col)
+            CK(cudaFuncSetAttribute(col, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        else
+            CK(cudaFuncSetAttribute(k3_ras<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         // every unknown of the output is written by its tile; the scratch takes
         // the caller's wall values once
         const int n_outer = (prm->sweeps + prm->k - 1) / prm->k;
@@ -773,8 +1042,12 @@ int smooth_impl(stokes3d_ctx *c, T *vx, T *vy, T *vz, const T *p, const stokes3d
             tg.nty = tiles_of(c->ny, tj, sh[1]);
             tg.ntz = tiles_of(c->nz, tk, sh[2]);
             const GAcc<T> a = gacc<T>(g, A[0], A[1], A[2], k.ec, k.exy, k.exz, k.eyz);
-            k3_ras<T><<<tg.ntx * tg.nty * tg.ntz, R3_THREADS, smem, c->stream>>>(g, a, k, omega, tg, ks, prm->overlap,
-                                                                                B[0], B[1], B[2]);
+            if (col)
+                col<<<tg.ntx * tg.nty * tg.ntz, dim3(32, (unsigned)wyk), smem, c->stream>>>(
+                    g, a, k, omega, tg, ks, prm->overlap, B[0], B[1], B[2]);
+            else
+                k3_ras<T><<<tg.ntx * tg.nty * tg.ntz, R3_THREADS, smem, c->stream>>>(g, a, k, omega, tg, ks,
+                                                                                    prm->overlap, B[0], B[1], B[2]);
             ++c->kernels;
             std::swap(A[0], B[0]);
             std::swap(A[1], B[1]);
@@ -927,7 +1200,14 @@ int stokes3d_smooth(stokes3d_ctx *c, void *vx, void *vy, void *vz, const void *p
             cudaGetLastError();
             return STOKES_ERR_CUDA;
         }
-        if (r3_smem(prm->tile_i, prm->tile_j, prm->tile_k, prm->overlap, c->esize, c->nx, c->ny, c->nz) > (size_t)maxs)
+        int wz = 0, wy = 0;
+        if (c->dtype == STOKES_F64)
+            ras_col_shape<double>(prm->tile_i, prm->tile_j, prm->tile_k, prm->overlap, c->nx, c->ny, c->nz, wz, wy);
+        else
+            ras_col_shape<float>(prm->tile_i, prm->tile_j, prm->tile_k, prm->overlap, c->nx, c->ny, c->nz, wz, wy);
+        const bool col = wz > 0;
+        if (!col &&
+            r3_smem(prm->tile_i, prm->tile_j, prm->tile_k, prm->overlap, c->esize, c->nx, c->ny, c->nz) > (size_t)maxs)
             return STOKES_ERR_ARG;
     }
     if (!c->have_eta || !c->have_f) return STOKES_ERR_STATE;

@@ -183,6 +183,83 @@ def test_ras3d_explicit_shifts_and_exact_overlap(api, o3):
             assert np.array_equal(x, y), dtype
 
 
+# tiles whose window (tile + 2 (overlap + 1) per axis) spans 16 to 32 lanes in x
+# and fits the column kernel's rows and depth (FP64: 8 rows, 8 levels; FP32:
+# 16 rows, 12 levels), on grids with ragged edge tiles
+COL_F64 = [((45, 21, 17), (14, 4, 4), 2, 1), ((37, 9, 13), (28, 2, 2), 3, 1), ((50, 14, 11), (20, 6, 6), 4, 0),
+           ((33, 17, 9), (24, 3, 5), 2, 0), ((21, 8, 8), (18, 2, 2), 4, 2)]
+
+
+@pytest.mark.parametrize("n,tile,k,o", COL_F64)
+def test_ras3d_column_kernel_f64(api, o3, n, tile, k, o):
+    """RAS on tiles of the column kernel (lane = x, warp = y, the z column in
+    registers, each flux formed once) against the oracle: seeded shifts,
+    a ragged last pass, and overlaps 0 .. k - 1."""
+    prob = problem(*n, 21)
+    v0 = inputs.random_velocity3d(*n, 22, 0.1)
+    p = inputs.random_pressure3d(*n, 23, 0.2)
+    g = ogrid(o3, prob)
+    b = o3.rhs(g, prob.fx, prob.fy, prob.fz, p)
+    sweeps = 2 * k + 1
+    r = Run3(api, prob, "f64", v0, p)
+    r.smooth(variant="ras", sweeps=sweeps, tile=tile, k=k, overlap=o, seed=77)
+    want = o3.ras(g, b, 0.3, sweeps, tile, k, o, shift_mode=1, seed=77, v=v0)
+    assert rel(r.get(), want) <= F64_TOL, rel(r.get(), want)
+
+
+def test_ras3d_column_kernel_explicit_shifts(api, o3):
+    n = (40, 12, 10)
+    prob = problem(*n, 24)
+    v0 = inputs.random_velocity3d(*n, 25, 0.1)
+    g = ogrid(o3, prob)
+    b = o3.rhs(g, prob.fx, prob.fy, prob.fz)
+    sh = [[0, 0, 0], [13, 3, 5], [27, 1, 2], [5, 5, 1]]
+    r = Run3(api, prob, "f64", v0)
+    r.smooth(variant="ras", sweeps=8, tile=(28, 6, 6), k=2, overlap=0, shifts=sh)
+    want = o3.ras(g, b, 0.3, 8, (28, 6, 6), 2, 0, shift_mode=2, shifts=sh, v=v0)
+    assert rel(r.get(), want) <= F64_TOL
+
+
+@pytest.mark.parametrize("tile,k", [((28, 8, 8), 2), ((28, 4, 4), 2), ((26, 6, 6), 3), ((14, 2, 2), 2)])
+def test_ras3d_column_kernel_exact_overlap_is_jacobi(api, o3, tile, k):
+    """Overlap k - 1 on column-kernel tiles equals global fused Jacobi bit for
+    bit in FP64 and FP32 (the FP32 tiles up to 12 levels and rows)."""
+    n = (61, 27, 22)
+    prob = problem(*n, 26)
+    v0 = inputs.random_velocity3d(*n, 27, 0.1)
+    p = inputs.random_pressure3d(*n, 28, 0.2)
+    for dtype in ("f64", "f32"):
+        h = k
+        if dtype == "f64" and (tile[1] + 2 * h > 8 or tile[2] + 2 * h > 8):
+            continue
+        a = Run3(api, prob, dtype, v0, p)
+        a.smooth(variant="ras", sweeps=2 * k + 1, tile=tile, k=k, overlap=k - 1, seed=5)
+        c = Run3(api, prob, dtype, v0, p)
+        c.smooth(variant="fused", sweeps=2 * k + 1)
+        for x, y in zip(a.get(), c.get()):
+            assert np.array_equal(x, y), dtype
+
+
+@pytest.mark.parametrize("tile,k,o", [((30, 10, 10), 4, 0), ((28, 8, 8), 2, 1), ((30, 14, 6), 4, 0)])
+def test_ras3d_column_kernel_fp32_energy_error(api, o3, tile, k, o):
+    """FP32 column-kernel tiles that FP64 cannot take (12 levels, 16 rows):
+    the energy-norm error against the oracle on the FP32-rounded inputs."""
+    n = (64, 40, 36)
+    prob = inputs.sinker3d_problem(*n, eta_in=1e3)
+    g = ogrid(o3, prob, f32)
+    b = o3.rhs(g, f32(prob.fx), f32(prob.fy), f32(prob.fz))
+    r = Run3(api, prob, "f32")
+    r.smooth(variant="ras", sweeps=12, tile=tile, k=k, overlap=o, seed=8)
+    want = o3.ras(g, b, 0.3, 12, tile, k, o, shift_mode=1, seed=8)
+    got = r.get()
+    d = o3.diag_M(g)
+    num = sum(np.sum(-dd * (x - y) ** 2) for dd, x, y in zip(d, got, want))
+    den = sum(np.sum(-dd * y ** 2) for dd, y in zip(d, want))
+    err = float(np.sqrt(num / den))
+    print("3d fp32 column %s k%d o%d: energy error %.2e" % (tile, k, o, err))
+    assert err <= FP32_ENERGY_TOL
+
+
 @pytest.mark.parametrize("variant,kw", [("fused", {}), ("ras", dict(tile=(8, 8, 8), k=2, overlap=1)),
                                         ("ras", dict(tile=(8, 8, 4), k=4, overlap=0))])
 def test_fp32_energy_error_3d(api, o3, variant, kw):
