@@ -1087,10 +1087,14 @@ def smooth3d_leg(args, api):
         ctx = api.Stokes3DContext(n, n, n, 1.0, 1.0, 1.0, dt_name)
         ctx.set_problem(prob)
         v = [ctx.field() for _ in range(3)]
+        # 8^3 tiles run the general tile kernel; windows 16 to 32 cells wide
+        # (30 x 6 x 6 and 28 x 8 x 4 with one ring or overlap 1) the column kernel
         cases = [dict(variant="fused", sweeps=4), dict(variant="ras", sweeps=4, tile=(8, 8, 8), k=2, overlap=1),
-                 dict(variant="ras", sweeps=4, tile=(8, 8, 8), k=4, overlap=0)]
+                 dict(variant="ras", sweeps=4, tile=(8, 8, 8), k=4, overlap=0),
+                 dict(variant="ras", sweeps=4, tile=(30, 6, 6), k=4, overlap=0),
+                 dict(variant="ras", sweeps=4, tile=(28, 4, 4) if dt_name == "f64" else (28, 8, 4), k=2, overlap=1)]
         if dt_name == "f32":
-            cases.append(dict(variant="ras", sweeps=4, tile=(16, 8, 8), k=2, overlap=1))
+            cases.append(dict(variant="ras", sweeps=8, tile=(30, 14, 6), k=8, overlap=0))
         import torch
         stream = torch.cuda.current_stream()
         for kw in cases:

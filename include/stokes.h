@@ -580,8 +580,13 @@ int stokes3d_apply_operator(stokes3d_ctx *ctx, const void *vx, const void *vy, c
                             void *out_x, void *out_y, void *out_z);
 
 /* Smooth M v = f - G p in place on (vx, vy, vz) (p may be NULL).  Fused
- * Jacobi, or RAS-Jacobi on 3D tiles with the window of each tile in shared
- * memory: STOKES_ERR_ARG when that window does not fit. */
+ * Jacobi, or RAS-Jacobi on 3D tiles (Algorithm 2 on boxes of tile_i x tile_j
+ * x tile_k cells).  A window (the tile grown by overlap + 1 cells on every
+ * side) 16 to 32 cells wide in x with at most 8 levels in z and 16 rows in y
+ * (FP32; also 12 levels with at most 12 rows) or 8 levels and 8 rows (FP64)
+ * runs with the velocity in registers and the y neighbours in shared memory;
+ * any other window must fit shared memory whole (10 words per window cell):
+ * STOKES_ERR_ARG when it does not.  Both give the same values bit for bit. */
 int stokes3d_smooth(stokes3d_ctx *ctx, void *vx, void *vy, void *vz, const void *p,
                     const stokes3d_smooth_params *params);
 

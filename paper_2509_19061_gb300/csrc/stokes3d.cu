@@ -21,7 +21,10 @@
 //              staged in shared memory, the k local sweeps on chip (each sweep
 //              updates only the cells within min(overlap, k - s) of the tile),
 //              the tile's own unknowns written back.  Space and time are
-//              blocked together: the "4D blocking" of Sec. 9.
+//              blocked together: the "4D blocking" of Sec. 9;
+//   k3_ras_col the same map for windows 16 to 32 cells wide: a warp per
+//              window row, each thread's z column in registers, each flux
+//              formed once, y neighbours through shared memory.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -577,10 +580,15 @@ __global__ void __launch_bounds__(R3_THREADS) k3_ras(G3<T> g, GAcc<T> a, C3<T> c
 // shuffles, z neighbours are in the thread's own registers, and only the y
 // neighbours go through shared memory: the velocity (vx, vy, vz) and the
 // three fluxes read across rows (sigma'_xy, Tyy, sigma'_yz), one plane per
-// window level and field, rows padded by one on each side.  The right-hand
-// side and 1/diag of the levels 1 .. WZ - 2 are copied to shared memory once
-// per tile (cp.async, no registers), so the updates read no global memory
-// (from global memory they waited on L2 once per level).  A sweep is two
+// window level and field, rows padded by one on each side; values read
+// together sit side by side ({vx, vz}, {sigma'_xy, sigma'_yz}, {b, 1/diag})
+// and move as one 8- or 16-byte access.  The right-hand side and 1/diag of
+// the levels 1 .. WZ - 2 are copied to shared memory once per tile
+// (cp.async, no registers), so the updates read no global memory (from
+// global memory they waited on L2 once per level).  (Prefetching the
+// windows of the next wave of tiles into L2 with bulk prefetches, at the start
+// of a CTA or after its staging, made the kernel slower: 88 against 114
+// Gcell-updates/s on 30 x 6 x 6 tiles.)  A sweep is two
 // phases, a barrier after each: (A) the row-crossing fluxes from the staged
 // velocity, (B) the updates, the remaining fluxes carried along z in
 // registers, and the new velocity.  Both phases run over every level as
@@ -593,6 +601,19 @@ __global__ void __launch_bounds__(R3_THREADS) k3_ras(G3<T> g, GAcc<T> a, C3<T> c
 // updated cell reads them.
 constexpr int RC_FIELDS = 6;
 constexpr size_t RC_SMEM_MAX = 227 * 1024;
+
+template <typename T>
+struct V2;
+template <>
+struct V2<float> {
+    using type = float2;
+    static __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
+};
+template <>
+struct V2<double> {
+    using type = double2;
+    static __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
+};
 
 // one element global -> shared, asynchronously; zero-filled when !valid
 // (src must still be a valid address)
@@ -627,11 +648,16 @@ __global__ void __launch_bounds__(MAXT, 1) k3_ras_col(G3<T> g, GAcc<T> a, C3<T> 
     const int h = overlap + 1;
     const int ox0 = x0 - h, oy0 = y0 - h, oz0 = z0 - h;
     const int gi = ox0 + lane, gj = oy0 + w;
-    // this thread's entries: exchange planes (row w + 1 of each level), and
-    // b / (1/diag) (row w of each level 1 .. WZ - 2; fields b_x, b_y, b_z,
-    // 1/diag_x, 1/diag_y, 1/diag_z)
-    T *const xv = sm + (w + 1) * 32 + lane;
-    T *const bw = sm + RC_FIELDS * FS + w * 32 + lane;
+    // this thread's entries (level stride PS): the exchange planes {vx, vz},
+    // vy, {sigma'_xy, sigma'_yz} and Tyy at row w + 1 of each level, and the
+    // pairs {b, 1/diag} of x, y, z (component stride BS) at row w of each
+    // level 1 .. WZ - 2
+    using T2 = typename V2<T>::type;
+    T2 *const pxz = reinterpret_cast<T2 *>(sm) + (w + 1) * 32 + lane;
+    T *const pvy = sm + 2 * FS + (w + 1) * 32 + lane;
+    T2 *const pf = reinterpret_cast<T2 *>(sm + 3 * FS) + (w + 1) * 32 + lane;
+    T *const pyy = sm + 5 * FS + (w + 1) * 32 + lane;
+    T2 *const pbw = reinterpret_cast<T2 *>(sm + RC_FIELDS * FS) + w * 32 + lane;
     if (w >= 1 && w < WY - 1) { // the rows a sweep can update
         const bool xv_ = gi >= 0 && gi <= g.nx, xc = gi >= 0 && gi < g.nx;
         const bool yc = gj >= 0 && gj < g.ny, yv = gj >= 0 && gj <= g.ny;
@@ -641,13 +667,13 @@ __global__ void __launch_bounds__(MAXT, 1) k3_ras_col(G3<T> g, GAcc<T> a, C3<T> 
             const bool zc = gk >= 0 && gk < g.nz, zv = gk >= 0 && gk <= g.nz;
             const bool okx = xv_ && yc && zc, oky = xc && yv && zc, okz = xc && yc && zv;
             const size_t q = (okx || oky || okz) ? g.at(gk, gj, gi) : 0;
-            T *const d = bw + (kk - 1) * WY * 32;
+            T *const d = reinterpret_cast<T *>(pbw + (kk - 1) * WY * 32);
             cp_async_elem(d, c.bx + (okx ? q : 0), okx);
-            cp_async_elem(d + BS, c.by + (oky ? q : 0), oky);
-            cp_async_elem(d + 2 * BS, c.bz + (okz ? q : 0), okz);
-            cp_async_elem(d + 3 * BS, c.ix + (okx ? q : 0), okx);
-            cp_async_elem(d + 4 * BS, c.iy + (oky ? q : 0), oky);
-            cp_async_elem(d + 5 * BS, c.iz + (okz ? q : 0), okz);
+            cp_async_elem(d + 1, c.ix + (okx ? q : 0), okx);
+            cp_async_elem(d + 2 * BS, c.by + (oky ? q : 0), oky);
+            cp_async_elem(d + 2 * BS + 1, c.iy + (oky ? q : 0), oky);
+            cp_async_elem(d + 4 * BS, c.bz + (okz ? q : 0), okz);
+            cp_async_elem(d + 4 * BS + 1, c.iz + (okz ? q : 0), okz);
         }
     }
     T vx[WZ], vy[WZ], vz[WZ], ec[WZ], exy[WZ], exz[WZ], eyz[WZ];
@@ -682,9 +708,8 @@ __global__ void __launch_bounds__(MAXT, 1) k3_ras_col(G3<T> g, GAcc<T> a, C3<T> 
     }
 #pragma unroll
     for (int kk = 0; kk < WZ; ++kk) {
-        xv[kk * PS] = vx[kk];
-        xv[FS + kk * PS] = vy[kk];
-        xv[2 * FS + kk * PS] = vz[kk];
+        pxz[kk * PS] = V2<T>::make(vx[kk], vz[kk]);
+        pvy[kk * PS] = vy[kk];
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
@@ -705,11 +730,12 @@ __global__ void __launch_bounds__(MAXT, 1) k3_ras_col(G3<T> g, GAcc<T> a, C3<T> 
 #pragma unroll
             for (int kk = 1; kk < WZ; ++kk) {
                 const T vys = __shfl_up_sync(full, vy[kk], 1);
-                const T vxs = xv[kk * PS - 32], vyn = xv[FS + kk * PS + 32], vzs = xv[2 * FS + kk * PS - 32];
-                xv[3 * FS + kk * PS] = r_mul(exy[kk], r_fma(r_sub(vx[kk], vxs), g.ihy, r_mul(r_sub(vy[kk], vys), g.ihx)));
-                xv[4 * FS + kk * PS] = r_mul(r_mul(r_add(ec[kk], ec[kk]), g.ihy2), r_sub(vyn, vy[kk]));
-                xv[5 * FS + kk * PS] =
-                    r_mul(eyz[kk], r_fma(r_sub(vy[kk], vy[kk - 1]), g.ihz, r_mul(r_sub(vz[kk], vzs), g.ihy)));
+                const T2 xzs = pxz[kk * PS - 32]; // {vx, vz} of row w - 1
+                const T vyn = pvy[kk * PS + 32];
+                const T sxy = r_mul(exy[kk], r_fma(r_sub(vx[kk], xzs.x), g.ihy, r_mul(r_sub(vy[kk], vys), g.ihx)));
+                const T syz = r_mul(eyz[kk], r_fma(r_sub(vy[kk], vy[kk - 1]), g.ihz, r_mul(r_sub(vz[kk], xzs.y), g.ihy)));
+                pf[kk * PS] = V2<T>::make(sxy, syz);
+                pyy[kk * PS] = r_mul(r_mul(r_add(ec[kk], ec[kk]), g.ihy2), r_sub(vyn, vy[kk]));
             }
         }
         __syncthreads();
@@ -721,6 +747,7 @@ __global__ void __launch_bounds__(MAXT, 1) k3_ras_col(G3<T> g, GAcc<T> a, C3<T> 
             const bool ux = xin && gi >= 1, uy = xin && gj >= 1;
             T sxz = r_mul(exz[1], r_fma(r_sub(vx[1], vx[0]), g.ihz, r_mul(r_sub(vz[1], __shfl_up_sync(full, vz[1], 1)), g.ihx)));
             T tzz_d = r_mul(r_mul(r_add(ec[0], ec[0]), g.ihz2), r_sub(vz[1], vz[0]));
+            T2 fc = pf[PS]; // {sigma'_xy, sigma'_yz} of this row, carried up the levels
 #pragma unroll
             for (int kk = 1; kk < WZ - 1; ++kk) {
                 const T vxe = __shfl_down_sync(full, vx[kk], 1);
@@ -730,10 +757,10 @@ __global__ void __launch_bounds__(MAXT, 1) k3_ras_col(G3<T> g, GAcc<T> a, C3<T> 
                 const T sxz_u =
                     r_mul(exz[kk + 1], r_fma(r_sub(vx[kk + 1], vx[kk]), g.ihz, r_mul(r_sub(vz[kk + 1], vzw_u), g.ihx)));
                 const T tzz_c = r_mul(r_mul(r_add(ec[kk], ec[kk]), g.ihz2), r_sub(vz[kk + 1], vz[kk]));
-                const T sxy_c = xv[3 * FS + kk * PS], sxy_n = xv[3 * FS + kk * PS + 32];
-                const T tyy_c = xv[4 * FS + kk * PS], tyy_s = xv[4 * FS + kk * PS - 32];
-                const T syz_c = xv[5 * FS + kk * PS], syz_n = xv[5 * FS + kk * PS + 32];
-                const T syz_u = xv[5 * FS + (kk + 1) * PS];
+                const T2 fn = pf[kk * PS + 32], fu = pf[(kk + 1) * PS];
+                const T tyy_c = pyy[kk * PS], tyy_s = pyy[kk * PS - 32];
+                const T sxy_c = fc.x, sxy_n = fn.x, syz_c = fc.y, syz_n = fn.y, syz_u = fu.y;
+                fc = fu;
                 const T sxy_e = __shfl_down_sync(full, sxy_c, 1);
                 const T sxz_e = __shfl_down_sync(full, sxz, 1);
                 const T mx = r_add(r_add(r_sub(txx_c, txx_w), r_sub(r_mul(sxy_n, g.ihy), r_mul(sxy_c, g.ihy))),
@@ -745,15 +772,14 @@ __global__ void __launch_bounds__(MAXT, 1) k3_ras_col(G3<T> g, GAcc<T> a, C3<T> 
                                    r_sub(tzz_c, tzz_d));
                 sxz = sxz_u;
                 tzz_d = tzz_c;
-                const T *const e = bw + (kk - 1) * WY * 32;
+                const T2 *const e = pbw + (kk - 1) * WY * 32;
+                const T2 ex = e[0], ey = e[BS], ez = e[2 * BS];
                 const bool lev = kk >= az0 && kk < az1;
-                if (lev && ux) vx[kk] = jacobi_update(vx[kk], e[0], mx, jacobi_weight(omega, e[3 * BS]));
-                if (lev && uy) vy[kk] = jacobi_update(vy[kk], e[BS], my, jacobi_weight(omega, e[4 * BS]));
-                if (lev && xin && oz0 + kk >= 1)
-                    vz[kk] = jacobi_update(vz[kk], e[2 * BS], mz, jacobi_weight(omega, e[5 * BS]));
-                xv[kk * PS] = vx[kk];
-                xv[FS + kk * PS] = vy[kk];
-                xv[2 * FS + kk * PS] = vz[kk];
+                if (lev && ux) vx[kk] = jacobi_update(vx[kk], ex.x, mx, jacobi_weight(omega, ex.y));
+                if (lev && uy) vy[kk] = jacobi_update(vy[kk], ey.x, my, jacobi_weight(omega, ey.y));
+                if (lev && xin && oz0 + kk >= 1) vz[kk] = jacobi_update(vz[kk], ez.x, mz, jacobi_weight(omega, ez.y));
+                pxz[kk * PS] = V2<T>::make(vx[kk], vz[kk]);
+                pvy[kk * PS] = vy[kk];
             }
         }
         __syncthreads();
@@ -1005,7 +1031,7 @@ int smooth_impl(stokes3d_ctx *c, T *vx, T *vy, T *vz, const T *p, const stokes3d
         // windows of 16 to 32 lanes take the column kernel, others the general one
         int wz = 0, wyk = 0;
         ras_col_shape<T>(ti, tj, tk, prm->overlap, c->nx, c->ny, c->nz, wz, wyk);
-        void (*col)(G3<T>, GAcc<T>, C3<T>, T, Tiles3, int, int, T *, T *, T *) = ras_col_kernel<T>(wz, wyk);
+        const ras_col_fn<T> col = ras_col_kernel<T>(wz, wyk);
         const size_t smem = col ? rc_smem(wz, wyk, sizeof(T))
                                 : r3_smem(ti, tj, tk, prm->overlap, sizeof(T), c->nx, c->ny, c->nz);
         if (col)
