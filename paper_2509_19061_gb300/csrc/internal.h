@@ -57,6 +57,10 @@ cudaError_t launch_copy_eta(const GridDesc<T> &g, const T *eta_c_in, const T *et
 template <typename T>
 cudaError_t launch_inv_diag(const GridDesc<T> &g, const T *eta_c, const T *eta_n, T *inv_dx, T *inv_dy,
                             cudaStream_t s);
+// launch_copy_eta and launch_inv_diag in one pass (the same values)
+template <typename T>
+cudaError_t launch_set_eta(const GridDesc<T> &g, const T *eta_c_in, const T *eta_n_in, T *eta_c, T *eta_n, T *inv_dx,
+                           T *inv_dy, cudaStream_t s);
 template <typename T>
 cudaError_t launch_rhs(const GridDesc<T> &g, const T *fx, const T *fy, const T *p, T *bx, T *by, cudaStream_t s);
 template <typename T>

@@ -951,19 +951,15 @@ int stokes_get_layout(const stokes_ctx *c, int field, int *rows, int *cols, int 
 int stokes_set_viscosity(stokes_ctx *c, const void *eta_c, const void *eta_n)
 {
     if (!c || !eta_c || !eta_n) return STOKES_ERR_ARG;
-    if (c->dtype == STOKES_F64) {
-        RUN(STOKES_K_COPY, 1, launch_copy_eta<double>(grid_of<double>(c), (const double *)eta_c, (const double *)eta_n,
-                                   (double *)c->eta_c, (double *)c->eta_n, c->stream));
+    if (c->dtype == STOKES_F64)
         RUN(STOKES_K_COPY, 1,
-            launch_inv_diag<double>(grid_of<double>(c), (const double *)c->eta_c, (const double *)c->eta_n,
-                                    (double *)c->ivx, (double *)c->ivy, c->stream));
-    } else {
-        RUN(STOKES_K_COPY, 1, launch_copy_eta<float>(grid_of<float>(c), (const float *)eta_c, (const float *)eta_n, (float *)c->eta_c,
-                                  (float *)c->eta_n, c->stream));
+            launch_set_eta<double>(grid_of<double>(c), (const double *)eta_c, (const double *)eta_n,
+                                   (double *)c->eta_c, (double *)c->eta_n, (double *)c->ivx, (double *)c->ivy,
+                                   c->stream));
+    else
         RUN(STOKES_K_COPY, 1,
-            launch_inv_diag<float>(grid_of<float>(c), (const float *)c->eta_c, (const float *)c->eta_n,
-                                   (float *)c->ivx, (float *)c->ivy, c->stream));
-    }
+            launch_set_eta<float>(grid_of<float>(c), (const float *)eta_c, (const float *)eta_n, (float *)c->eta_c,
+                                  (float *)c->eta_n, (float *)c->ivx, (float *)c->ivy, c->stream));
     c->have_eta = true;
     mg_invalidate(c->mg);
     ++c->eta_version;
