@@ -100,12 +100,12 @@ struct Sub {
     const BSeg *map = nullptr;
     int nseg = 0, nblocks = 0;
 };
-
 struct Rect {
     int inst, w, h;
 };
 
-int make_sub(Owned &o, const std::vector<Rect> &r, Sub *out, cudaStream_t s)
+// block_rows = BATCH_BY * BATCH_TALL makes a tall map
+int make_sub(Owned &o, const std::vector<Rect> &r, Sub *out, cudaStream_t s, int block_rows = BATCH_BY)
 {
     std::vector<BSeg> m;
     int b = 0;
@@ -116,7 +116,7 @@ int make_sub(Owned &o, const std::vector<Rect> &r, Sub *out, cudaStream_t s)
         g.h = x.h;
         g.bxb = (x.w + BATCH_BX - 1) / BATCH_BX;
         g.block_begin = b;
-        b += g.bxb * ((x.h + BATCH_BY - 1) / BATCH_BY);
+        b += g.bxb * ((x.h + block_rows - 1) / block_rows);
         m.push_back(g);
     }
     out->nseg = (int)m.size();
@@ -157,7 +157,7 @@ template <typename T>
 struct Group {
     std::vector<TileLaunch<T>> launches;
     const BLevel<T> *lev = nullptr; // vx, vy, sx, sy per instance (copies)
-    Sub sub;                        // the instances over (nx+1) x (ny+1)
+    Sub sub;                        // the instances over (nx+1) x (ny+1), a tall map
     bool walls = false, back = false;
     T omega = T(0);
 };
@@ -174,7 +174,7 @@ int plan_group(Owned &o, const std::vector<GInst<T>> &gi, const RasForm &f, bool
     out->omega = (T)f.omega;
     std::vector<Rect> rects;
     for (const GInst<T> &x : gi) rects.push_back({x.inst, x.g.nx + 1, x.g.ny + 1});
-    ST(make_sub(o, rects, &out->sub, s));
+    ST(make_sub(o, rects, &out->sub, s, BATCH_BY * BATCH_TALL));
     const size_t n = gi.size();
     std::vector<T *> ax(n), ay(n), bx(n), by(n);
     for (size_t q = 0; q < n; ++q) {
@@ -256,7 +256,7 @@ int run_group(const Group<T> &G, const int *live, const RasRun &run, cudaStream_
 {
     if (G.launches.empty()) return STOKES_OK;
     if (G.walls) {
-        CK(batch_copy<T>(G.lev, G.sub.map, G.sub.nseg, G.sub.nblocks, true, true, live, s));
+        CK(batch_copy_walls<T>(G.lev, G.sub.map, G.sub.nseg, live, s));
         ++*nk;
     }
     for (const TileLaunch<T> &L : G.launches) {
@@ -265,7 +265,7 @@ int run_group(const Group<T> &G, const int *live, const RasRun &run, cudaStream_
         ++*nk;
     }
     if (G.back) {
-        CK(batch_copy<T>(G.lev, G.sub.map, G.sub.nseg, G.sub.nblocks, false, false, live, s));
+        CK(batch_copy<T>(G.lev, G.sub.map, G.sub.nseg, G.sub.nblocks, false, live, s));
         ++*nk;
     }
     return STOKES_OK;
@@ -335,6 +335,7 @@ struct stokes_batch {
     void *cax = nullptr, *cay = nullptr; // flux coefficients of the outer operator apply
     bool have_eta = false, have_f = false;
     Sub all;                        // every instance over (nx+1) x (ny+1)
+    Sub all_tall;                   // the same, a tall map (the right-hand side)
     double *partials = nullptr;     // 2 per block of `all`
     double *dsum = nullptr, *dpq = nullptr, *dzq = nullptr, *alpha = nullptr, *beta = nullptr;
     int *dactive = nullptr, *hactive = nullptr;
@@ -937,7 +938,7 @@ int ensure_outer(stokes_batch *b, const void *vx, const void *vy, const void *p)
 template <typename T>
 int rhs(stokes_batch *b)
 {
-    CK(batch_rhs<T>((const BRhs<T> *)b->rhs_tab, b->all.map, b->all.nseg, b->all.nblocks, b->stream));
+    CK(batch_rhs<T>((const BRhs<T> *)b->rhs_tab, b->all_tall.map, b->all_tall.nseg, b->all_tall.nblocks, b->stream));
     ++b->kernels;
     return STOKES_OK;
 }
@@ -1215,6 +1216,7 @@ int stokes_batch_create(int count, const int *nx, const int *ny, const double *l
         std::vector<Rect> r;
         for (int i = 0; i < count; ++i) r.push_back({i, b->d[i].nx + 1, b->d[i].ny + 1});
         st = make_sub(b->base, r, &b->all, b->stream);
+        if (st == STOKES_OK) st = make_sub(b->base, r, &b->all_tall, b->stream, BATCH_BY * BATCH_TALL);
     }
     if (st == STOKES_OK) {
         const size_t nb = (size_t)std::max(b->all.nblocks, 1);

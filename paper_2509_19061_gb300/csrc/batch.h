@@ -58,11 +58,16 @@ struct BRhs {
 };
 
 constexpr int BATCH_BX = 32, BATCH_BY = 8;
+// rows per thread of the tall element maps (blocks of 32 x BATCH_BY *
+// BATCH_TALL cells): the setup-like copies take them, so that a block's
+// segment lookup is shared by four times the cells and four rows' loads are
+// in flight together
+constexpr int BATCH_TALL = 4;
 
 // The multigrid level kernels take `active` (device, one flag per instance,
 // may be NULL): instances whose flag is 0 are skipped.
 
-template <typename T> // over (nx+1) x (ny+1) per instance
+template <typename T> // over (nx+1) x (ny+1) per instance, a tall map
 cudaError_t batch_rhs(const BRhs<T> *tab, const BSeg *map, int nseg, int nblocks, cudaStream_t s);
 
 template <typename T>
@@ -78,11 +83,15 @@ cudaError_t batch_prolong(const BLevel<T> *tab, const BSeg *map, int nseg, int n
 template <typename T>
 cudaError_t batch_zero_v(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, const int *active,
                          cudaStream_t s);
-// copy the wall entries (copy_walls) or the in-extent entries (copy_all) of
-// (vx, vy) into (sx, sy) when to_scratch, else the other way
+// copy the in-extent entries of (vx, vy) into (sx, sy) when to_scratch, else
+// the other way (a tall map)
 template <typename T>
-cudaError_t batch_copy(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, bool walls_only, bool to_scratch,
+cudaError_t batch_copy(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, bool to_scratch,
                        const int *active, cudaStream_t s);
+// copy the wall entries of (vx, vy) into (sx, sy): one block per segment of
+// the map (any block height)
+template <typename T>
+cudaError_t batch_copy_walls(const BLevel<T> *tab, const BSeg *map, int nseg, const int *active, cudaStream_t s);
 // dense coarsest solves: `rows` unknowns in total over `count` instances
 template <typename T>
 cudaError_t batch_dense(const BDense<T> *tab, int count, int rows, const int *active, cudaStream_t s);

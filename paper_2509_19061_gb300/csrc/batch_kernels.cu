@@ -44,6 +44,22 @@ __device__ __forceinline__ Pt point_of(const BSeg *__restrict__ m, int n)
     return p;
 }
 
+// first point of this thread in a tall map (rows p.j + r BATCH_BY, r <
+// BATCH_TALL); valid = the column lies inside the instance's rectangle, the
+// rows are checked one by one
+__device__ __forceinline__ Pt point_of_tall(const BSeg *__restrict__ m, int n, int &h)
+{
+    const BSeg sg = m[seg_of(m, n, blockIdx.x)];
+    const int lb = blockIdx.x - sg.block_begin;
+    Pt p;
+    p.inst = sg.inst;
+    p.i = (lb % sg.bxb) * BATCH_BX + threadIdx.x;
+    p.j = (lb / sg.bxb) * BATCH_BY * BATCH_TALL + threadIdx.y;
+    p.valid = p.i < sg.w;
+    h = sg.h;
+    return p;
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -93,21 +109,41 @@ __global__ void k_seg_final(const BSeg *__restrict__ m, int n, const double *__r
 template <typename T>
 __global__ void kb_rhs(const BRhs<T> *__restrict__ tab, const BSeg *__restrict__ m, int n)
 {
-    const Pt p = point_of(m, n);
+    int h;
+    const Pt p = point_of_tall(m, n, h);
     if (!p.valid) return;
     const BRhs<T> &r = tab[p.inst];
     const GridDesc<T> &g = r.g;
-    const int i = p.i, j = p.j;
-    const size_t P = (size_t)g.pitch, q = (size_t)j * P + i;
-    if (j < g.ny) {
-        T b = T(0);
-        if (vx_unknown(g, j, i)) b = r.p ? r_fma(r_sub(r.p[q], r.p[q - 1]), g.ihx, r.fx[q]) : r.fx[q];
-        r.bx[q] = b;
+    const int i = p.i;
+    const size_t P = (size_t)g.pitch;
+    // every row's loads first, then the stores
+    T fxr[BATCH_TALL], fyr[BATCH_TALL], pc[BATCH_TALL], pw[BATCH_TALL], ps[BATCH_TALL];
+#pragma unroll
+    for (int t = 0; t < BATCH_TALL; ++t) {
+        const int j = p.j + t * BATCH_BY;
+        const size_t q = (size_t)j * P + i;
+        const bool ux = j < h && vx_unknown(g, j, i), uy = j < h && vy_unknown(g, j, i);
+        fxr[t] = ux ? r.fx[q] : T(0);
+        fyr[t] = uy ? r.fy[q] : T(0);
+        pc[t] = (r.p && (ux || uy)) ? r.p[q] : T(0);
+        pw[t] = (r.p && ux) ? r.p[q - 1] : T(0);
+        ps[t] = (r.p && uy) ? r.p[q - P] : T(0);
     }
-    if (i < g.nx) {
-        T b = T(0);
-        if (vy_unknown(g, j, i)) b = r.p ? r_fma(r_sub(r.p[q], r.p[q - P]), g.ihy, r.fy[q]) : r.fy[q];
-        r.by[q] = b;
+#pragma unroll
+    for (int t = 0; t < BATCH_TALL; ++t) {
+        const int j = p.j + t * BATCH_BY;
+        if (j >= h) break;
+        const size_t q = (size_t)j * P + i;
+        if (j < g.ny) {
+            T b = T(0);
+            if (vx_unknown(g, j, i)) b = r.p ? r_fma(r_sub(pc[t], pw[t]), g.ihx, fxr[t]) : fxr[t];
+            r.bx[q] = b;
+        }
+        if (i < g.nx) {
+            T b = T(0);
+            if (vy_unknown(g, j, i)) b = r.p ? r_fma(r_sub(pc[t], ps[t]), g.ihy, fyr[t]) : fyr[t];
+            r.by[q] = b;
+        }
     }
 }
 
@@ -176,19 +212,56 @@ __global__ void kb_zero_v(const BLevel<T> *__restrict__ tab, const BSeg *__restr
 }
 
 template <typename T>
-__global__ void kb_copy(const BLevel<T> *__restrict__ tab, const BSeg *__restrict__ m, int n, bool walls_only,
-                        bool to_scratch, const int *__restrict__ active)
+__global__ void kb_copy(const BLevel<T> *__restrict__ tab, const BSeg *__restrict__ m, int n, bool to_scratch,
+                        const int *__restrict__ active)
 {
-    const Pt p = point_of(m, n);
+    int h;
+    const Pt p = point_of_tall(m, n, h);
     if (!p.valid || (active && !active[p.inst])) return;
     const BLevel<T> &l = tab[p.inst];
     const GridDesc<T> &g = l.g;
-    const int i = p.i, j = p.j;
-    const size_t q = (size_t)j * g.pitch + i;
+    const int i = p.i;
     T *sx = to_scratch ? l.sx : l.vx, *sy = to_scratch ? l.sy : l.vy;
     const T *ax = to_scratch ? l.vx : l.sx, *ay = to_scratch ? l.vy : l.sy;
-    if (j < g.ny && (!walls_only || i == 0 || i == g.nx)) sx[q] = ax[q];
-    if (i < g.nx && (!walls_only || j == 0 || j == g.ny)) sy[q] = ay[q];
+    T cx[BATCH_TALL], cy[BATCH_TALL];
+#pragma unroll
+    for (int t = 0; t < BATCH_TALL; ++t) {
+        const int j = p.j + t * BATCH_BY;
+        const size_t q = (size_t)j * g.pitch + i;
+        cx[t] = (j < h && j < g.ny) ? ax[q] : T(0);
+        cy[t] = (j < h && i < g.nx) ? ay[q] : T(0);
+    }
+#pragma unroll
+    for (int t = 0; t < BATCH_TALL; ++t) {
+        const int j = p.j + t * BATCH_BY;
+        if (j >= h) break;
+        const size_t q = (size_t)j * g.pitch + i;
+        if (j < g.ny) sx[q] = cx[t];
+        if (i < g.nx) sy[q] = cy[t];
+    }
+}
+
+// the wall entries of one instance per block: vx at i = 0 and nx, vy at j = 0 and ny
+template <typename T>
+__global__ void kb_copy_walls(const BLevel<T> *__restrict__ tab, const BSeg *__restrict__ m,
+                              const int *__restrict__ active)
+{
+    const int inst = m[blockIdx.x].inst;
+    if (active && !active[inst]) return;
+    const BLevel<T> &l = tab[inst];
+    const GridDesc<T> &g = l.g;
+    const size_t P = (size_t)g.pitch;
+    const int nwx = 2 * g.ny, nwy = 2 * g.nx;
+    for (int t = (int)threadIdx.x; t < nwx + nwy; t += (int)blockDim.x) {
+        if (t < nwx) {
+            const size_t q = (size_t)(t >> 1) * P + ((t & 1) ? g.nx : 0);
+            l.sx[q] = l.vx[q];
+        } else {
+            const int u = t - nwx;
+            const size_t q = (size_t)((u & 1) ? g.ny : 0) * P + (u >> 1);
+            l.sy[q] = l.vy[q];
+        }
+    }
 }
 
 template <typename T>
@@ -535,10 +608,16 @@ cudaError_t batch_zero_v(const BLevel<T> *tab, const BSeg *map, int nseg, int nb
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t batch_copy(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, bool walls_only, bool to_scratch,
+cudaError_t batch_copy(const BLevel<T> *tab, const BSeg *map, int nseg, int nblocks, bool to_scratch,
                        const int *active, cudaStream_t s)
 {
-    if (nblocks > 0) kb_copy<T><<<nblocks, BLOCK, 0, s>>>(tab, map, nseg, walls_only, to_scratch, active);
+    if (nblocks > 0) kb_copy<T><<<nblocks, BLOCK, 0, s>>>(tab, map, nseg, to_scratch, active);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t batch_copy_walls(const BLevel<T> *tab, const BSeg *map, int nseg, const int *active, cudaStream_t s)
+{
+    if (nseg > 0) kb_copy_walls<T><<<nseg, 256, 0, s>>>(tab, map, active);
     return cudaGetLastError();
 }
 template <typename T>
@@ -659,8 +738,9 @@ cudaError_t batch_scalars(int count, const double *pq_pr, const double *zq, cons
     template cudaError_t batch_restrict<T>(const BLevel<T> *, const BSeg *, int, int, const int *, cudaStream_t);  \
     template cudaError_t batch_prolong<T>(const BLevel<T> *, const BSeg *, int, int, const int *, cudaStream_t);   \
     template cudaError_t batch_zero_v<T>(const BLevel<T> *, const BSeg *, int, int, const int *, cudaStream_t);    \
-    template cudaError_t batch_copy<T>(const BLevel<T> *, const BSeg *, int, int, bool, bool, const int *,         \
+    template cudaError_t batch_copy<T>(const BLevel<T> *, const BSeg *, int, int, bool, const int *,               \
                                        cudaStream_t);                                                              \
+    template cudaError_t batch_copy_walls<T>(const BLevel<T> *, const BSeg *, int, const int *, cudaStream_t);     \
     template cudaError_t batch_dense<T>(const BDense<T> *, int, int, const int *, cudaStream_t);                   \
     template cudaError_t batch_residual_energy<T>(const BOuter<T> *, const BSeg *, int, int, double *, double *,   \
                                                   cudaStream_t);                                                   \
