@@ -185,7 +185,7 @@ def test_ras3d_explicit_shifts_and_exact_overlap(api, o3):
 
 # tiles whose window (tile + 2 (overlap + 1) per axis) spans 16 to 32 lanes in x
 # and fits the column kernel's rows and depth (FP64: 8 rows, 8 levels; FP32:
-# 16 rows, 12 levels), on grids with ragged edge tiles
+# 16 rows with 8 levels, 12 with 12), on grids with ragged edge tiles
 COL_F64 = [((45, 21, 17), (14, 4, 4), 2, 1), ((37, 9, 13), (28, 2, 2), 3, 1), ((50, 14, 11), (20, 6, 6), 4, 0),
            ((33, 17, 9), (24, 3, 5), 2, 0), ((21, 8, 8), (18, 2, 2), 4, 2)]
 
@@ -220,10 +220,12 @@ def test_ras3d_column_kernel_explicit_shifts(api, o3):
     assert rel(r.get(), want) <= F64_TOL
 
 
-@pytest.mark.parametrize("tile,k", [((28, 8, 8), 2), ((28, 4, 4), 2), ((26, 6, 6), 3), ((14, 2, 2), 2)])
+@pytest.mark.parametrize("tile,k", [((28, 8, 8), 2), ((28, 4, 4), 2), ((26, 6, 6), 3), ((14, 2, 2), 2),
+                                    ((28, 4, 8), 2), ((28, 8, 4), 2), ((28, 12, 4), 2)])
 def test_ras3d_column_kernel_exact_overlap_is_jacobi(api, o3, tile, k):
     """Overlap k - 1 on column-kernel tiles equals global fused Jacobi bit for
-    bit in FP64 and FP32 (the FP32 tiles up to 12 levels and rows)."""
+    bit in FP64 and FP32: every FP32 window shape instantiated (8 levels with
+    8, 12 or 16 rows, 12 levels with 8 or 12 rows) and the FP64 one."""
     n = (61, 27, 22)
     prob = problem(*n, 26)
     v0 = inputs.random_velocity3d(*n, 27, 0.1)
